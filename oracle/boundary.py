@@ -1,0 +1,99 @@
+"""Boundary conditions of the oracle (Sec. III A: wall by Grad's
+approximation, Eqs. fnoneq, gnoneq, strainrate and the zero-normal-gradient
+targets; inlet and outlet by equilibrium).
+
+Test infrastructure only (see the package docstring).
+
+Wall rows are i = 0 of an O-grid; far-field rows are i = Ni - 1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import kinetics as K
+from .ale import physical_gradient
+
+MISSING_TOL = 1e-12
+
+
+def wall_normals(mesh):
+    """Unit normal n0 at every wall node (row 0), pointing out of the body
+    into the fluid, in the undeformed frame.  The wall is the polygon of the
+    elements' straight wall edges (even-indexed wall nodes are its vertices):
+    an odd node takes its edge's normal, an even node the normalised sum of
+    the normals of its two edges."""
+    Nj = mesh.Nj
+    P = mesh.X[0]
+    n_edge = np.empty((Nj // 2, 2))
+    for k in range(Nj // 2):
+        a = P[2 * k]
+        b = P[(2 * k + 2) % Nj]
+        t = b - a
+        n_edge[k] = np.array([t[1], -t[0]]) / np.hypot(t[0], t[1])
+    n = np.empty((Nj, 2))
+    for j in range(Nj):
+        if j % 2:
+            n[j] = n_edge[j // 2]
+        else:
+            v = n_edge[j // 2] + n_edge[(j // 2 - 1) % (Nj // 2)]
+            n[j] = v / np.hypot(v[0], v[1])
+    return n
+
+
+def missing_mask(chat_wall, n0):
+    """Populations of a wall node whose departure point lies inside the body:
+    c_hat_i . n0 > 0 (reading R10; the departure point X - c_hat dt then lies
+    behind the supporting line of the convex wall polygon).  chat_wall has
+    shape [9, Nj, 2]."""
+    dot = chat_wall[..., 0] * n0[None, :, 0] + chat_wall[..., 1] * n0[None, :, 1]
+    return dot > MISSING_TOL
+
+
+def wall_targets(mesh, M_prev, n0, dt, F_wall):
+    """rho_tgt, T_tgt from the zero-normal-gradient condition: the values at
+    B = A + dt n0 (the largest distance the paper allows), interpolated with
+    second-order elements (Sec. III A).  Reading R19: the interpolated field is
+    the previous step's moment field.  Also returns grad u and grad T at the
+    wall nodes from the same field (first-order FE derivative, Eq. ddx+fem,
+    one-sided along the wall-normal index), mapped to the physical frame."""
+    Nj = mesh.Nj
+    j = np.arange(Nj)
+    i = np.zeros(Nj, dtype=np.int64)
+    B = mesh.X[0] + dt * n0
+    wa, wb, xi, eta, found = mesh.locate(B, i, j)
+    if not np.all(found):
+        raise RuntimeError("wall target point B outside the first element row")
+    rho_b = mesh.interpolate(M_prev[0], wa, wb, xi, eta)
+    T_b = mesh.interpolate(M_prev[3], wa, wb, xi, eta)
+    grads = []
+    for comp in (1, 2, 3):
+        dX, dY = mesh.grad_X(M_prev[comp])
+        gx, gy = physical_gradient(F_wall, dX[0], dY[0])
+        grads.append((gx, gy))
+    return rho_b, T_b, grads
+
+
+def grad_populations(rho, ux, uy, T, grads, Cv, mu, dt, Pr):
+    """Grad's approximation f^eq + dt f^(1), g^eq + dt g^(1) at the targets."""
+    (dudx, dudy), (dvdx, dvdy), (dTdx, dTdy) = grads
+    feq = K.f_eq(rho, ux, uy, T)
+    geq = K.g_eq(rho, ux, uy, T, Cv)
+    f1, g1 = K.grad_f1(rho, ux, uy, T, Cv, dudx, dudy, dvdx, dvdy, dTdx, dTdy, mu, dt, Pr)
+    return feq + f1, geq + g1
+
+
+def far_field_targets(mesh, M_prev, u_inf, rho_inf, T_inf):
+    """Inlet / outlet targets at the far-field row (Sec. III A 2).  Reading
+    R20: a far-field node is an inlet where the free stream enters
+    (U_inf . n_out < 0, n_out the outward radial direction), else an outlet;
+    inlet targets are the free stream, outlet targets are copied from the
+    radially inner neighbour (zero gradient of rho, u, T) of the previous step's
+    field."""
+    last = mesh.Ni - 1
+    n_out = mesh.X[last] - mesh.X[last - 1]
+    inlet = (u_inf[0] * n_out[:, 0] + u_inf[1] * n_out[:, 1]) < 0.0
+    rho = np.where(inlet, rho_inf, M_prev[0, last - 1])
+    ux = np.where(inlet, u_inf[0], M_prev[1, last - 1])
+    uy = np.where(inlet, u_inf[1], M_prev[2, last - 1])
+    T = np.where(inlet, T_inf, M_prev[3, last - 1])
+    return rho, ux, uy, T, inlet

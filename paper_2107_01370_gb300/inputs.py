@@ -1,0 +1,185 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module holds no arithmetic of the method. It only produces the geometry of
+the body-fitted meshes (node coordinates as 1-D tables) and the seeded initial
+macroscopic fields. Both implementations receive these arrays as inputs.
+
+Mesh shape (stand-in for the paper's unstructured second-order FE meshes,
+Sec. IV A, Sec. IV C): a structured O-grid around a circular cylinder.
+Node (i, j) sits at  X = centre + r[i] * e[j],  i radial (i = 0 on the wall),
+j angular (periodic).  Second-order elements are the 3x3-node windows whose
+corners have even indices.  The mesh is subparametric: odd-index radii are
+the midpoints of their even neighbours and odd-index direction vectors are the
+averages of their even neighbours, so every element is the bilinear image of
+the reference square and its 9 nodes sit at the bilinear positions of
+xi, eta in {-1, 0, 1}.  With an even number of radial nodes the last three
+radial spacings are equal (the last window overlaps its neighbour by one row).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def ogrid_radii(nr: int, radius: float, r_far: float, dr0: float) -> np.ndarray:
+    """Radial node table: element widths grow geometrically from 2*dr0 at the
+    wall so that the last node lands on r_far."""
+    if nr < 5:
+        raise ValueError("nr must be >= 5")
+    n_even = (nr - 1) // 2 + 1 if nr % 2 == 1 else (nr - 2) // 2 + 1
+    n_elem = n_even - 1
+
+    def last_radius(q: float) -> float:
+        w = 2.0 * dr0 * q ** np.arange(n_elem)
+        r_even = radius + np.concatenate([[0.0], np.cumsum(w)])
+        if nr % 2 == 1:
+            return r_even[-1]
+        return r_even[-1] + 0.5 * w[-1]
+
+    lo, hi = 1.0, 2.0
+    if last_radius(lo) > r_far:
+        raise ValueError("r_far too small for dr0 and nr")
+    while last_radius(hi) < r_far:
+        hi *= 1.5
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if last_radius(mid) < r_far:
+            lo = mid
+        else:
+            hi = mid
+    q = 0.5 * (lo + hi)
+    w = 2.0 * dr0 * q ** np.arange(n_elem)
+    r_even = radius + np.concatenate([[0.0], np.cumsum(w)])
+    r = np.empty(nr)
+    r[0:2 * n_even - 1:2] = r_even
+    r[1:2 * n_even - 2:2] = 0.5 * (r_even[:-1] + r_even[1:])
+    if nr % 2 == 0:
+        r[nr - 1] = r[nr - 2] + (r[nr - 2] - r[nr - 3])
+    return r
+
+
+def ogrid_directions(ntheta: int, theta0: float = 0.0) -> np.ndarray:
+    """Angular node table e[j] (shape [ntheta, 2]); even j on the unit circle,
+    odd j the average of the two even neighbours (chord midpoints)."""
+    if ntheta % 2 or ntheta < 4:
+        raise ValueError("ntheta must be even and >= 4")
+    e = np.empty((ntheta, 2))
+    th = theta0 + 2.0 * np.pi * np.arange(0, ntheta, 2) / ntheta
+    e[0::2, 0] = np.cos(th)
+    e[0::2, 1] = np.sin(th)
+    nxt = np.roll(e[0::2], -1, axis=0)
+    e[1::2] = 0.5 * (e[0::2] + nxt)
+    return e
+
+
+@dataclass
+class BodySpec:
+    """Rigid body on a spring (Sec. III, Sec. IV).  dof: 0 fixed,
+    1 transverse spring-mass(-damper), 2 pitch-plunge."""
+    dof: int = 0
+    xc: float = 0.0          # centre of the blend region (undeformed)
+    yc: float = 0.0
+    xp: float = 0.0          # reference point: cylinder centre / elastic axis
+    yp: float = 0.0
+    r_in: float = 0.75       # rigid-zone radius, measured from (xc, yc)
+    r_out: float = 2.5       # outer radius of the blended zone
+    length: float = 1.0      # D for cylinders, chord 2b for airfoils
+    m_star: float = 10.0
+    v_r: float = 5.0
+    zeta: float = 0.0
+    x_alpha: float = 0.0
+    r_alpha: float = 1.0
+    wh_wa: float = 1.0
+
+
+@dataclass
+class FlowSpec:
+    ma: float = 0.2
+    re: float = 100.0
+    t_inf: float = 1.0 / 3.0
+    gamma: float = 1.4
+    pr: float = 0.71
+    rho_inf: float = 1.0
+    dt: float = 0.0
+    length: float = 1.0
+
+    @property
+    def u_inf(self) -> float:
+        return self.ma * math.sqrt(self.gamma * self.t_inf)
+
+    @property
+    def mu(self) -> float:
+        return self.rho_inf * self.u_inf * self.length / self.re
+
+
+@dataclass
+class CylinderCase:
+    nr: int
+    ntheta: int
+    r: np.ndarray
+    e: np.ndarray
+    centre: tuple
+    flow: FlowSpec
+    bodies: list = field(default_factory=list)
+    steps: int = 0
+    name: str = ""
+
+    @property
+    def nodes(self) -> int:
+        return self.nr * self.ntheta
+
+
+def cylinder_case(nr: int, ntheta: int, *, radius: float = 0.5, r_far: float = 20.0,
+                  ma: float = 0.2, re: float = 100.0, t_inf: float = 1.0 / 3.0,
+                  gamma: float = 1.4, pr: float = 0.71, body: BodySpec | None = None,
+                  steps: int = 0, name: str = "") -> CylinderCase:
+    """O-grid around a cylinder of diameter 2*radius.  First radial spacing
+    equals the wall arc spacing; the time step is a third of it (the constant
+    near-wall CFL of the paper's cases, Sec. IV)."""
+    dr0 = 2.0 * np.pi * radius / ntheta
+    r = ogrid_radii(nr, radius, r_far, dr0)
+    e = ogrid_directions(ntheta)
+    flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr,
+                    dt=dr0 / 3.0, length=2.0 * radius)
+    b = body if body is not None else BodySpec(dof=0)
+    return CylinderCase(nr=nr, ntheta=ntheta, r=r, e=e, centre=(0.0, 0.0), flow=flow,
+                        bodies=[b], steps=steps, name=name)
+
+
+def fixed_cylinder_128x64(steps: int = 1000) -> CylinderCase:
+    """Fixed cylinder, 128 radial x 64 angular nodes, far field at 20 D,
+    Re 100, Ma 0.2 (FP64 parity workload)."""
+    return cylinder_case(128, 64, body=BodySpec(dof=0), steps=steps,
+                         name="fixed cylinder O-grid 128x64, Re 100, Ma 0.2")
+
+
+def viv_cylinder_512x256(steps: int = 20000, v_r: float = 5.0, m_star: float = 10.0) -> CylinderCase:
+    """1-DOF transverse VIV of a cylinder (m* 10, zeta 0, V_R 5) on a
+    512 x 256 O-grid deformed by the blending polynomial; Re 100, Ma 0.2."""
+    b = BodySpec(dof=1, r_in=0.75, r_out=2.5, m_star=m_star, v_r=v_r, zeta=0.0)
+    return cylinder_case(512, 256, body=b, steps=steps,
+                         name="1-DOF VIV cylinder O-grid 512x256, m* 10, V_R 5, Re 100, Ma 0.2")
+
+
+def initial_field(nr: int, ntheta: int, flow: FlowSpec, noise: float = 1e-3,
+                  seed: int = 0) -> np.ndarray:
+    """Uniform free stream (rho_inf, U_inf along +x, T_inf) plus seeded
+    uniform velocity noise of amplitude noise*U_inf.  Shape [4, nr, ntheta]:
+    rho, u_x, u_y, T."""
+    rng = np.random.default_rng(seed)
+    m = np.empty((4, nr, ntheta))
+    m[0] = flow.rho_inf
+    xi = rng.uniform(-1.0, 1.0, size=(2, nr, ntheta))
+    m[1] = flow.u_inf + noise * flow.u_inf * xi[0]
+    m[2] = noise * flow.u_inf * xi[1]
+    m[3] = flow.t_inf
+    return m
+
+
+def random_populations_like(shape, seed: int, scale: float = 0.02) -> np.ndarray:
+    """Seeded perturbation array used by tests to move populations off
+    equilibrium."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.uniform(-1.0, 1.0, size=shape)
