@@ -1,0 +1,171 @@
+/*
+ * lbfsi.h - C ABI of the GB300 implementation of the two-population
+ * compressible semi-Lagrangian lattice Boltzmann step with fluid-structure
+ * coupling on a blended body-fitted mesh (Bhadauria, Dorschner & Karlin,
+ * "Lattice Boltzmann method for fluid-structure interaction in compressible
+ * flow").
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an lbfsi_status (0 = success, negative = error) and
+ *    never aborts the process.  lbfsi_last_error() gives a thread-local
+ *    message for the last failing call of the calling thread.
+ *  - Host pointers passed in are borrowed for the duration of the call only
+ *    (their contents are copied before the call returns).  Host pointers passed
+ *    out must point to caller-owned memory of the stated size.
+ *  - All device memory belongs to the mesh handle and is released by
+ *    lbfsi_destroy_mesh.  Work is ordered on the CUDA stream given at creation
+ *    (NULL = legacy default stream).  lbfsi_step is asynchronous; errors that
+ *    the kernels detect (departure point outside the adjacent cells, a
+ *    non-physical state) are recorded in a device status word and returned by
+ *    the next synchronising call (lbfsi_synchronize, lbfsi_body_forces,
+ *    lbfsi_get_*).
+ *
+ * Mesh: structured O-grid, node (i, j) at X = (xc, yc) + r[i] e[j], i = 0 on
+ * the body wall, i = nr-1 on the far field, j periodic.  Node index
+ * n = i * ntheta + j.  Second-order elements are the 3x3-node windows whose
+ * first node has even indices (the last radial window is clamped to nr-3 when
+ * nr is even).  r and e must be subparametric (odd entries the average of
+ * their even neighbours), as produced by the package's mesh generator.
+ *
+ * Field layouts (host arrays, float64, C order):
+ *   macroscopic fields  [nbatch][4][nr*ntheta]   rho, u_x, u_y, T
+ *   populations         [nbatch][9][nr*ntheta]   D2Q9 order
+ *       i = 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1)
+ *           7:(-1,-1) 8:(1,-1)
+ *   loads               [nbatch][3]              F_x, F_y, M_z
+ */
+#ifndef LBFSI_H
+#define LBFSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbfsi_mesh_s* lbfsi_mesh;
+
+typedef enum {
+    LBFSI_OK = 0,
+    LBFSI_EINVAL = -1,      /* invalid argument */
+    LBFSI_ENOMEM = -2,      /* device or host allocation failed */
+    LBFSI_ECUDA = -3,       /* CUDA runtime error */
+    LBFSI_EDEPARTURE = -4,  /* departure point not in a cell adjacent to its node (CFL violated) */
+    LBFSI_ENONPHYS = -5,    /* rho <= 0, T <= 0 or NaN produced */
+    LBFSI_ETIMEOUT = -6,    /* a bounded device wait ran out */
+    LBFSI_ESTATE = -7       /* call out of order (e.g. step before init_fields) */
+} lbfsi_status;
+
+enum { LBFSI_FP64 = 0, LBFSI_FP32 = 1 };
+enum { LBFSI_BODY_FIXED = 0, LBFSI_BODY_TRANSVERSE = 1, LBFSI_BODY_PITCH_PLUNGE = 2 };
+
+/* One rigid body and its region of influence (Sec. II D, Sec. III).
+ * dof: LBFSI_BODY_*.  The blending region is centred at (xc, yc): nodes with
+ * |X - Xc| <= r_in move rigidly with the body, nodes beyond r_out stay fixed,
+ * the r5 polynomial blends in between (Eq. blendPol).  (xp, yp) is the
+ * reference point of the rigid map, of the moment and of the pitch rotation
+ * (cylinder centre / elastic axis).  length = D (cylinder) or chord 2b.
+ * Transverse: m_star = 4 m / (rho pi D^2), v_r = U / (f_N D), zeta a damping
+ * ratio (0 in the paper).  Pitch-plunge: m_star = m / (pi rho b^2),
+ * v_r = U / (b omega_alpha sqrt(m*)), x_alpha, r_alpha, wh_wa = omega_h/omega_alpha. */
+typedef struct {
+    int dof;
+    double xc, yc;
+    double xp, yp;
+    double r_in, r_out;
+    double length;
+    double m_star, v_r, zeta;
+    double x_alpha, r_alpha, wh_wa;
+} lbfsi_body_desc;
+
+/* Free stream and transport (Sec. II C): U_inf = ma sqrt(gamma t_inf) along +x,
+ * mu = rho_inf U_inf length / re, omega from mu = (1/omega - 1/2) rho T dt,
+ * omega_1 from Pr.  gamma > 1 (Cv = 1/(gamma - 1), R = 1). */
+typedef struct {
+    double ma, re, t_inf, gamma, pr, rho_inf, dt, length;
+} lbfsi_flow_params;
+
+typedef struct {
+    int nr, ntheta;             /* nr >= 5, ntheta even >= 4 */
+    const double* r;            /* [nr]        radial node table (host)        */
+    const double* e;            /* [ntheta][2] angular node directions (host)  */
+    double xc, yc;              /* mesh centre                                  */
+    int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations         */
+    int nbatch;                 /* independent solves sharing the mesh, >= 1    */
+    const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)  */
+} lbfsi_mesh_desc;
+
+/* Body state: plunge h (up), pitch alpha (counter-clockwise) and rates. */
+typedef struct {
+    double h, alpha, hdot, adot;
+} lbfsi_body_state;
+
+/* Create a mesh handle: copies the tables, derives the wall geometry, and
+ * allocates all device buffers (two population buffers, two moment fields,
+ * force partials, body states).  cuda_stream: a cudaStream_t or NULL. */
+int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* out);
+
+/* Release every device buffer of the handle (synchronises its stream). */
+int lbfsi_destroy_mesh(lbfsi_mesh m);
+
+/* Initial state (Sec. IV: uniform inflow plus seeded noise): populations set to
+ * f^eq, g^eq (Eqs. feq, geq) of the given macroscopic fields; the moment field of
+ * "the previous step" used by the boundary targets is that same field.  Body
+ * states reset to rest.  rho_u_T: host [nbatch][4][N], or NULL for the uniform
+ * free stream. */
+int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rho_u_T);
+
+/* Set the body states used by the next step's blended map (Sec. II D):
+ * state [nbatch] is the current one, prev [nbatch] the one of the previous
+ * step (V_G = (x(state) - x(prev)) / dt); prev may be NULL (= state). */
+int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_body_state* prev);
+
+/* Advance nsteps coupled time steps (Sec. III weak coupling): per step the
+ * blended-mesh kinematics, departure points and Q2 interpolation of f and g
+ * (Eqs. depPnt, SemiLagrProp), wall and far-field boundaries (Sec. III A), moments,
+ * correction terms, collision (Eq. f_boltz), wall force and moment (Sec. III) and
+ * the RK4 update of each body.  Asynchronous on the handle's stream. */
+int lbfsi_step(lbfsi_mesh m, int nsteps);
+
+/* Loads of the last completed step, host out [nbatch][3] = F_x, F_y, M_z
+ * (force on the body, moment about its reference point).  Synchronises. */
+int lbfsi_body_forces(lbfsi_mesh m, double* out);
+
+/* RK4 of the body ODEs only (Sec. III B), with the given host loads
+ * [nbatch][3] held constant over dt (NULL = the last step's loads).  Updates
+ * the body states (the current state becomes the previous one). */
+int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt);
+
+/* Body states after the structural update of the last step, host out [nbatch]. */
+int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out);
+
+/* Macroscopic fields rho, u_x, u_y, T of the last step's post-propagation
+ * state (far field: its targets), host out [nbatch][4][N] float64.  Synchronises. */
+int lbfsi_get_fields(lbfsi_mesh m, double* rho_u_T);
+
+/* Populations of the last step: which = 0 post-propagation (after the wall
+ * reconstruction, before collision; far-field rows hold their equilibria),
+ * which = 1 post-collision.  Host out [nbatch][9][N] each, float64. */
+int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g);
+
+/* Replace the post-propagation populations of the last step (host
+ * [nbatch][9][N] float64) and their moment field; used to restart from a
+ * checkpoint. */
+int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g,
+                          const double* rho_u_T);
+
+/* Wait for the handle's stream; returns the first device-detected error. */
+int lbfsi_synchronize(lbfsi_mesh m);
+
+/* Number of kernel launches issued on the handle's stream so far. */
+int64_t lbfsi_launch_count(lbfsi_mesh m);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* lbfsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBFSI_H */

@@ -1,0 +1,541 @@
+// C-ABI of the library (declared in include/lbfsi.h): handle, device memory,
+// host-side mesh geometry and the launch sequence of the coupled step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbfsi.h"
+#include "lbfsi_internal.h"
+
+namespace lbfsi {
+int tiles_j(int nt);
+}
+
+using lbfsi::BodyDev;
+using lbfsi::BodyStateDev;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(LBFSI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct lbfsi_mesh_s {
+    int nr = 0, nt = 0, N = 0, nbatch = 0, precision = 0, ntj = 0;
+    double xm = 0, ym = 0;
+    cudaStream_t stream = nullptr;
+    size_t esize = 8;
+    std::vector<double> r, e, n0, wall_geo;
+    std::vector<lbfsi_body_desc> bodies;
+    double* d_r = nullptr;
+    double* d_e = nullptr;
+    double* d_n0 = nullptr;
+    double* d_wall_geo = nullptr;
+    BodyDev* d_bodies = nullptr;
+    void* d_f[2] = {nullptr, nullptr};
+    void* d_g[2] = {nullptr, nullptr};
+    void* d_M[2] = {nullptr, nullptr};
+    void* d_fpost = nullptr;
+    void* d_gpost = nullptr;
+    double* d_stage = nullptr;  // [nbatch][4][N] float64 staging
+    BodyStateDev* d_S[2] = {nullptr, nullptr};
+    BodyStateDev* d_Sprev0 = nullptr;
+    BodyStateDev* d_Sforce = nullptr;
+    BodyStateDev* d_Stmp = nullptr;
+    double* d_part[2] = {nullptr, nullptr};
+    double* d_loads = nullptr;
+    unsigned* d_status = nullptr;
+    int cur = 0, curS = 0, curP = 0;
+    bool initialized = false, first = true, force_pending = false;
+    double dt = 0, mu = 0, Cv = 0, Pr = 0, rho_inf = 0, uinf = 0, T_inf = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+int check_status(lbfsi_mesh m) {
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    unsigned st = 0;
+    e = cudaMemcpy(&st, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st & lbfsi::ST_DEPARTURE)
+        return fail(LBFSI_EDEPARTURE, "departure point outside the cells adjacent to its node (CFL)");
+    if (st & lbfsi::ST_BPOINT)
+        return fail(LBFSI_EDEPARTURE, "wall target point outside the first element row");
+    if (st & lbfsi::ST_NONPHYS) return fail(LBFSI_ENONPHYS, "non-physical state (rho<=0, T<=0 or NaN)");
+    return LBFSI_OK;
+}
+
+void to_double(const void* src, double* dst, size_t n, int precision) {
+    if (precision == LBFSI_FP64) {
+        std::memcpy(dst, src, n * sizeof(double));
+    } else {
+        const float* s = static_cast<const float*>(src);
+        for (size_t k = 0; k < n; ++k) dst[k] = (double)s[k];
+    }
+}
+
+int download(lbfsi_mesh m, const void* dsrc, double* host, size_t n) {
+    std::vector<unsigned char> tmp(n * m->esize);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), dsrc, n * m->esize, cudaMemcpyDeviceToHost, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "download");
+    e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "download sync");
+    to_double(tmp.data(), host, n, m->precision);
+    return LBFSI_OK;
+}
+
+int upload(lbfsi_mesh m, const double* host, void* ddst, size_t n) {
+    std::vector<unsigned char> tmp(n * m->esize);
+    if (m->precision == LBFSI_FP64) {
+        std::memcpy(tmp.data(), host, n * sizeof(double));
+    } else {
+        float* t = reinterpret_cast<float*>(tmp.data());
+        for (size_t k = 0; k < n; ++k) t[k] = (float)host[k];
+    }
+    cudaError_t e = cudaMemcpyAsync(ddst, tmp.data(), n * m->esize, cudaMemcpyHostToDevice, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload");
+    e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload sync");
+    return LBFSI_OK;
+}
+
+// Wall polygon of the O-grid (Sec. III): the wall edges are the straight
+// element edges between even-indexed wall nodes.  For every wall node: the unit
+// normal n0 out of the body (odd node: its edge's normal; even node: the
+// normalised sum of its two edges' normals) and its Simpson share of the
+// adjacent edges (weight*length and edge normal, up to two edges).
+void wall_geometry(lbfsi_mesh m) {
+    const int nt = m->nt, ne = nt / 2;
+    std::vector<double> X(2 * nt);
+    for (int j = 0; j < nt; ++j) {
+        X[2 * j] = m->xm + m->r[0] * m->e[2 * j];
+        X[2 * j + 1] = m->ym + m->r[0] * m->e[2 * j + 1];
+    }
+    std::vector<double> en(2 * ne), ds(ne);
+    for (int k = 0; k < ne; ++k) {
+        const int a = 2 * k, c = (2 * k + 2) % nt;
+        const double tx = X[2 * c] - X[2 * a], ty = X[2 * c + 1] - X[2 * a + 1];
+        const double L = std::sqrt(tx * tx + ty * ty);
+        ds[k] = L;
+        en[2 * k] = ty / L;
+        en[2 * k + 1] = -tx / L;
+    }
+    m->n0.assign(2 * nt, 0.0);
+    m->wall_geo.assign(6 * nt, 0.0);
+    for (int j = 0; j < nt; ++j) {
+        double* g = &m->wall_geo[6 * j];
+        if (j % 2) {
+            const int k = j / 2;
+            m->n0[2 * j] = en[2 * k];
+            m->n0[2 * j + 1] = en[2 * k + 1];
+            g[0] = 4.0 / 6.0 * ds[k];
+            g[1] = en[2 * k];
+            g[2] = en[2 * k + 1];
+        } else {
+            const int k2 = j / 2, k1 = (j / 2 - 1 + ne) % ne;
+            const double vx = en[2 * k1] + en[2 * k2], vy = en[2 * k1 + 1] + en[2 * k2 + 1];
+            const double L = std::sqrt(vx * vx + vy * vy);
+            m->n0[2 * j] = vx / L;
+            m->n0[2 * j + 1] = vy / L;
+            g[0] = ds[k2] / 6.0;
+            g[1] = en[2 * k2];
+            g[2] = en[2 * k2 + 1];
+            g[3] = ds[k1] / 6.0;
+            g[4] = en[2 * k1];
+            g[5] = en[2 * k1 + 1];
+        }
+    }
+}
+
+// Dimensional ODE coefficients from the paper's nondimensional groups
+// (Sec. IV A for the transverse model, Sec. IV D for pitch-plunge).
+BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
+    BodyDev b{};
+    b.dof = d.dof;
+    b.xc = d.xc; b.yc = d.yc; b.xp = d.xp; b.yp = d.yp;
+    b.r_in = d.r_in; b.r_out = d.r_out;
+    const double pi = 3.14159265358979323846;
+    if (d.dof == LBFSI_BODY_TRANSVERSE) {
+        const double D = d.length;
+        b.m = d.m_star * rho * pi * D * D / 4.0;
+        const double wn = 2.0 * pi * U / (d.v_r * D);
+        b.k = b.m * wn * wn;
+        b.c = 2.0 * d.zeta * b.m * wn;
+    } else if (d.dof == LBFSI_BODY_PITCH_PLUNGE) {
+        const double bh = 0.5 * d.length;
+        b.m = d.m_star * pi * rho * bh * bh;
+        const double wa = U / (d.v_r * bh * std::sqrt(d.m_star));
+        const double wh = d.wh_wa * wa;
+        b.s_a = d.x_alpha * b.m * bh;
+        b.i_a = d.r_alpha * d.r_alpha * b.m * bh * bh;
+        b.k_h = b.m * wh * wh;
+        b.k_a = b.i_a * wa * wa;
+    }
+    return b;
+}
+
+void free_all(lbfsi_mesh m) {
+    void* ptrs[] = {m->d_r, m->d_e, m->d_n0, m->d_wall_geo, m->d_bodies, m->d_f[0], m->d_f[1],
+                    m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost, m->d_gpost, m->d_stage,
+                    m->d_S[0], m->d_S[1], m->d_Sprev0, m->d_Sforce, m->d_Stmp, m->d_part[0],
+                    m->d_part[1], m->d_loads, m->d_status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbfsi_last_error(void) { return g_last_error.c_str(); }
+
+int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* out) {
+    g_last_error.clear();
+    if (!d || !out) return fail(LBFSI_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->nr < 5) return fail(LBFSI_EINVAL, "nr must be >= 5");
+    if (d->ntheta < 4 || d->ntheta % 2) return fail(LBFSI_EINVAL, "ntheta must be even and >= 4");
+    if (d->precision != LBFSI_FP64 && d->precision != LBFSI_FP32)
+        return fail(LBFSI_EINVAL, "precision must be LBFSI_FP64 or LBFSI_FP32");
+    if (d->nbatch < 1) return fail(LBFSI_EINVAL, "nbatch must be >= 1");
+    if (!d->r || !d->e || !d->bodies) return fail(LBFSI_EINVAL, "null table or body pointer");
+    const long long Nll = (long long)d->nr * d->ntheta;
+    if (Nll * 9 * d->nbatch > (1ll << 31)) return fail(LBFSI_EINVAL, "mesh too large for 32-bit node indexing");
+    auto m = new lbfsi_mesh_s();
+    m->nr = d->nr;
+    m->nt = d->ntheta;
+    m->N = (int)Nll;
+    m->nbatch = d->nbatch;
+    m->precision = d->precision;
+    m->esize = d->precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
+    m->ntj = lbfsi::tiles_j(m->nt);
+    m->xm = d->xc;
+    m->ym = d->yc;
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    m->r.assign(d->r, d->r + d->nr);
+    m->e.assign(d->e, d->e + 2 * d->ntheta);
+    m->bodies.assign(d->bodies, d->bodies + d->nbatch);
+    for (int i = 1; i < m->nr; ++i)
+        if (!(m->r[i] > m->r[i - 1])) {
+            delete m;
+            return fail(LBFSI_EINVAL, "radial table must increase");
+        }
+    for (const auto& b : m->bodies) {
+        if (b.dof < 0 || b.dof > 2) {
+            delete m;
+            return fail(LBFSI_EINVAL, "body dof must be 0, 1 or 2");
+        }
+        if (b.dof != 0) {
+            if (!(b.r_out > b.r_in) || !(b.length > 0) || !(b.m_star > 0) || !(b.v_r > 0)) {
+                delete m;
+                return fail(LBFSI_EINVAL, "moving body needs r_out > r_in, length, m_star, v_r > 0");
+            }
+            for (int j = 0; j < m->nt; ++j) {
+                const double x = m->xm + m->r[0] * m->e[2 * j] - b.xc;
+                const double y = m->ym + m->r[0] * m->e[2 * j + 1] - b.yc;
+                if (std::sqrt(x * x + y * y) >= b.r_in) {
+                    delete m;
+                    return fail(LBFSI_EINVAL, "the wall must lie inside the rigid zone (r_in)");
+                }
+            }
+        }
+    }
+    wall_geometry(m);
+    const size_t N = (size_t)m->N, nb = (size_t)m->nbatch;
+    cudaError_t e = cudaSuccess;
+#define LB_ALLOC(ptr, cnt)                                   \
+    if (e == cudaSuccess) e = dalloc(&(ptr), (cnt));
+    LB_ALLOC(m->d_r, (size_t)m->nr);
+    LB_ALLOC(m->d_e, 2 * (size_t)m->nt);
+    LB_ALLOC(m->d_n0, 2 * (size_t)m->nt);
+    LB_ALLOC(m->d_wall_geo, 6 * (size_t)m->nt);
+    LB_ALLOC(m->d_bodies, nb);
+    LB_ALLOC(m->d_stage, nb * 4 * N);
+    LB_ALLOC(m->d_S[0], nb);
+    LB_ALLOC(m->d_S[1], nb);
+    LB_ALLOC(m->d_Sprev0, nb);
+    LB_ALLOC(m->d_Sforce, nb);
+    LB_ALLOC(m->d_Stmp, nb);
+    LB_ALLOC(m->d_part[0], nb * m->ntj * 3);
+    LB_ALLOC(m->d_part[1], nb * m->ntj * 3);
+    LB_ALLOC(m->d_loads, nb * 3);
+    LB_ALLOC(m->d_status, 1);
+#undef LB_ALLOC
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&m->d_f[k], nb * 9 * N * m->esize);
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_g[k], nb * 9 * N * m->esize);
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_M[k], nb * 4 * N * m->esize);
+    }
+    if (e != cudaSuccess) {
+        free_all(m);
+        delete m;
+        cudaGetLastError();
+        return fail(LBFSI_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(m->d_r, m->r.data(), m->nr * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_e, m->e.data(), 2 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_n0, m->n0.data(), 2 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->d_wall_geo, m->wall_geo.data(), 6 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        free_all(m);
+        delete m;
+        return cuda_fail(e, "create_mesh copy");
+    }
+    *out = m;
+    return LBFSI_OK;
+}
+
+int lbfsi_destroy_mesh(lbfsi_mesh m) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    cudaStreamSynchronize(m->stream);
+    free_all(m);
+    delete m;
+    return LBFSI_OK;
+}
+
+int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rho_u_T) {
+    if (!m || !p) return fail(LBFSI_EINVAL, "null argument");
+    if (!(p->gamma > 1.0) || !(p->t_inf > 0) || !(p->rho_inf > 0) || !(p->dt > 0) || !(p->re > 0) ||
+        !(p->pr > 0) || !(p->length > 0) || p->ma < 0)
+        return fail(LBFSI_EINVAL, "invalid flow parameters");
+    m->dt = p->dt;
+    m->Cv = 1.0 / (p->gamma - 1.0);
+    m->Pr = p->pr;
+    m->rho_inf = p->rho_inf;
+    m->T_inf = p->t_inf;
+    m->uinf = p->ma * std::sqrt(p->gamma * p->t_inf);
+    m->mu = p->rho_inf * m->uinf * p->length / p->re;
+    if (!(m->mu > 0)) return fail(LBFSI_EINVAL, "viscosity must be positive (Ma > 0)");
+    const size_t N = (size_t)m->N, nb = (size_t)m->nbatch;
+    std::vector<BodyDev> bd(nb);
+    for (size_t b = 0; b < nb; ++b) bd[b] = body_dev(m->bodies[b], m->rho_inf, m->uinf);
+    std::vector<double> M(nb * 4 * N);
+    if (rho_u_T) {
+        std::memcpy(M.data(), rho_u_T, M.size() * sizeof(double));
+    } else {
+        for (size_t b = 0; b < nb; ++b)
+            for (size_t n = 0; n < N; ++n) {
+                M[(b * 4 + 0) * N + n] = m->rho_inf;
+                M[(b * 4 + 1) * N + n] = m->uinf;
+                M[(b * 4 + 2) * N + n] = 0.0;
+                M[(b * 4 + 3) * N + n] = m->T_inf;
+            }
+    }
+    std::vector<BodyStateDev> zero(nb, BodyStateDev{0.0, 0.0, 0.0, 0.0});
+    std::vector<double> zp(nb * m->ntj * 3, 0.0);
+    cudaError_t e = cudaMemcpyAsync(m->d_bodies, bd.data(), nb * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemcpyAsync(m->d_S[k], zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m->d_part[k], zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_Sprev0, zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init_fields upload");
+    m->cur = m->curS = m->curP = 0;
+    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_f[0], m->d_g[0], m->d_M[0], m->N, m->nbatch,
+                           m->Cv, m->stream);
+    m->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init sync");
+    m->initialized = true;
+    m->first = true;
+    m->force_pending = false;
+    return LBFSI_OK;
+}
+
+int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_body_state* prev) {
+    if (!m || !state) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    const size_t nb = (size_t)m->nbatch;
+    static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
+    const lbfsi_body_state* pv = prev ? prev : state;
+    cudaError_t e;
+    if (m->first) {
+        e = cudaMemcpyAsync(m->d_S[m->curS], state, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m->d_Sprev0, pv, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+    } else {
+        e = cudaMemcpyAsync(m->d_S[m->curS], pv, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m->d_Sforce, state, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+        m->force_pending = true;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "blend_mesh");
+    return LBFSI_OK;
+}
+
+static lbfsi::StepArgs make_args(lbfsi_mesh m, int mode) {
+    lbfsi::StepArgs a{};
+    a.nr = m->nr; a.nt = m->nt; a.N = m->N; a.nbatch = m->nbatch; a.ntj = m->ntj;
+    a.xm = m->xm; a.ym = m->ym;
+    a.r = m->d_r; a.e = m->d_e; a.n0 = m->d_n0; a.wall_geo = m->d_wall_geo;
+    a.dt = m->dt; a.mu = m->mu; a.Cv = m->Cv; a.Pr = m->Pr; a.rho_inf = m->rho_inf;
+    a.uinf_x = m->uinf; a.uinf_y = 0.0; a.T_inf = m->T_inf;
+    a.f_in = m->d_f[m->cur]; a.g_in = m->d_g[m->cur];
+    a.f_out = m->d_f[m->cur ^ 1]; a.g_out = m->d_g[m->cur ^ 1];
+    a.M_in = m->d_M[m->cur]; a.M_out = m->d_M[m->cur ^ 1];
+    a.bodies = m->d_bodies;
+    a.S_in = m->d_S[m->curS]; a.S_out = m->d_S[m->curS ^ 1];
+    a.S_prev0 = m->d_Sprev0;
+    a.S_force = nullptr;
+    a.part_in = m->d_part[m->curP]; a.part_out = m->d_part[m->curP ^ 1];
+    a.loads_out = nullptr;
+    a.mode = mode;
+    a.status = m->d_status;
+    return a;
+}
+
+int lbfsi_step(lbfsi_mesh m, int nsteps) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
+    for (int s = 0; s < nsteps; ++s) {
+        lbfsi::StepArgs a = make_args(m, m->first ? lbfsi::MODE_STREAM_ONLY : lbfsi::MODE_COLLIDE_STREAM);
+        if (m->force_pending && !m->first) a.S_force = m->d_Sforce;
+        cudaError_t e = lbfsi::launch_step(a, m->precision, m->stream);
+        m->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        m->cur ^= 1;
+        m->curS ^= 1;
+        m->curP ^= 1;
+        m->first = false;
+        m->force_pending = false;
+    }
+    return LBFSI_OK;
+}
+
+int lbfsi_synchronize(lbfsi_mesh m) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    return check_status(m);
+}
+
+int lbfsi_body_forces(lbfsi_mesh m, double* out) {
+    if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    cudaError_t e = lbfsi::launch_reduce_loads(m->d_part[m->curP], m->ntj, m->nbatch, m->d_loads, m->stream);
+    m->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "reduce loads");
+    e = cudaMemcpyAsync(out, m->d_loads, (size_t)m->nbatch * 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "loads copy");
+    return check_status(m);
+}
+
+int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    const size_t nb = (size_t)m->nbatch;
+    cudaError_t e;
+    if (loads) {
+        e = cudaMemcpyAsync(m->d_loads, loads, nb * 3 * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+    } else {
+        e = lbfsi::launch_reduce_loads(m->d_part[m->curP], m->ntj, m->nbatch, m->d_loads, m->stream);
+        m->launches++;
+    }
+    if (e == cudaSuccess)
+        e = lbfsi::launch_advance(m->d_bodies, m->d_S[m->curS], m->d_loads, dt, m->nbatch, m->d_Stmp,
+                                  m->d_Sprev0, m->stream);
+    m->launches++;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_S[m->curS], m->d_Stmp, nb * sizeof(BodyStateDev), cudaMemcpyDeviceToDevice, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "advance_bodies");
+    return check_status(m);
+}
+
+int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out) {
+    if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    const size_t nb = (size_t)m->nbatch;
+    cudaError_t e = cudaSuccess;
+    const BodyStateDev* src = m->d_S[m->curS];
+    if (!m->first) {
+        // the state after the structural update of the last step
+        e = lbfsi::launch_reduce_loads(m->d_part[m->curP], m->ntj, m->nbatch, m->d_loads, m->stream);
+        if (e == cudaSuccess)
+            e = lbfsi::launch_advance(m->d_bodies, m->d_S[m->curS], m->d_loads, m->dt, m->nbatch,
+                                      m->d_Stmp, nullptr, m->stream);
+        m->launches += 2;
+        src = m->d_Stmp;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, src, nb * sizeof(BodyStateDev), cudaMemcpyDeviceToHost, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get_body_state");
+    return check_status(m);
+}
+
+int lbfsi_get_fields(lbfsi_mesh m, double* rho_u_T) {
+    if (!m || !rho_u_T) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    int rc = download(m, m->d_M[m->cur], rho_u_T, (size_t)m->nbatch * 4 * m->N);
+    if (rc) return rc;
+    return check_status(m);
+}
+
+int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
+    if (!m || !f || !g) return fail(LBFSI_EINVAL, "null argument");
+    if (which != 0 && which != 1) return fail(LBFSI_EINVAL, "which must be 0 or 1");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    const size_t cnt = (size_t)m->nbatch * 9 * m->N;
+    const void* fs = m->d_f[m->cur];
+    const void* gs = m->d_g[m->cur];
+    if (which == 1 && !m->first) {
+        cudaError_t e = cudaSuccess;
+        if (!m->d_fpost) e = cudaMalloc(&m->d_fpost, cnt * m->esize);
+        if (e == cudaSuccess && !m->d_gpost) e = cudaMalloc(&m->d_gpost, cnt * m->esize);
+        if (e != cudaSuccess) return fail(LBFSI_ENOMEM, "post-collision staging allocation failed");
+        lbfsi::StepArgs a = make_args(m, lbfsi::MODE_COLLIDE_ONLY);
+        a.f_out = m->d_fpost;
+        a.g_out = m->d_gpost;
+        e = lbfsi::launch_step(a, m->precision, m->stream);
+        m->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "collide kernel launch");
+        fs = m->d_fpost;
+        gs = m->d_gpost;
+    }
+    int rc = download(m, fs, f, cnt);
+    if (rc) return rc;
+    rc = download(m, gs, g, cnt);
+    if (rc) return rc;
+    return check_status(m);
+}
+
+int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const double* rho_u_T) {
+    if (!m || !f || !g || !rho_u_T) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    const size_t cnt = (size_t)m->nbatch * 9 * m->N;
+    int rc = upload(m, f, m->d_f[m->cur], cnt);
+    if (!rc) rc = upload(m, g, m->d_g[m->cur], cnt);
+    if (!rc) rc = upload(m, rho_u_T, m->d_M[m->cur], (size_t)m->nbatch * 4 * m->N);
+    if (rc) return rc;
+    m->first = false;
+    return LBFSI_OK;
+}
+
+int64_t lbfsi_launch_count(lbfsi_mesh m) { return m ? m->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,277 @@
+// Device-side physics of the two-population compressible lattice Boltzmann
+// step (Sec. II C of the paper): equilibria, correction terms, collision,
+// Grad's approximation (Sec. III A), blended-mesh kinematics (Sec. II A, II D)
+// and the rigid-body RK4 (Sec. III B).  Templated on the arithmetic type R
+// (double for the FP64 path, float for the FP32 path).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "lbfsi_internal.h"
+
+namespace lbfsi {
+
+// D2Q9 velocity of index q: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
+// 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).  Resolved at compile time in unrolled loops.
+__host__ __device__ constexpr int cxq(int q) {
+    return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cyq(int q) {
+    return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
+}
+
+template <typename R>
+struct Macro {
+    R rho, ux, uy, T, E;
+};
+
+// rho = sum f, rho u = sum f c, 2 rho E = sum g, T = (E - u^2/2) / Cv.
+template <typename R>
+__device__ __forceinline__ Macro<R> moments(const R* f, const R* g, R Cv) {
+    R rho = 0, jx = 0, jy = 0, s2 = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        rho += f[q];
+        jx += (R)cxq(q) * f[q];
+        jy += (R)cyq(q) * f[q];
+        s2 += g[q];
+    }
+    Macro<R> m;
+    m.rho = rho;
+    m.ux = jx / rho;
+    m.uy = jy / rho;
+    m.E = s2 / (R(2) * rho);
+    m.T = (m.E - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) / Cv;
+    return m;
+}
+
+// Product-form equilibrium f_i^eq = rho Phi_{cx}(u_x) Phi_{cy}(u_y) (Eq. feq).
+template <typename R>
+__device__ __forceinline__ void f_equilibrium(R rho, R ux, R uy, R T, R* f) {
+    R ax = ux * ux + T, ay = uy * uy + T;
+    R px[3] = {R(0.5) * (ax - ux), R(1) - ax, R(0.5) * (ax + ux)};   // index c+1
+    R py[3] = {R(0.5) * (ay - uy), R(1) - ay, R(0.5) * (ay + uy)};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = rho * px[cxq(q) + 1] * py[cyq(q) + 1];
+}
+
+// g = W_i (2 rho E + q.c/T + (R^eq - 2 rho E T I):(c c - T I)/(2T^2)) + Psi_i
+// (Eqs. geq, gstar).  H = E + T (energy flux of the enthalpy), R^eq as printed,
+// Psi_i = B_i . X with B_0 = (1,1), B_{1,3} = (-1/2,0), B_{2,4} = (0,-1/2).
+template <typename R>
+__device__ __forceinline__ void g_hermite(R rho, R ux, R uy, R T, R E, R qx, R qy, R* g) {
+    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    // A = R^eq - 2 rho E T I
+    const R axx = R(2) * rho * E * uxx + R(2) * rho * T * (T + R(2) * uxx);
+    const R ayy = R(2) * rho * E * uyy + R(2) * rho * T * (T + R(2) * uyy);
+    const R axy = R(2) * rho * E * uxy + R(4) * rho * T * uxy;
+    const R inv2T2 = R(1) / (R(2) * T * T);
+    const R invT = R(1) / T;
+    const R pre = rho * (R(1) - R(3) * T) * invT;
+    const R Xx = pre * (T * T + R(2) * uxx * T + E * uxx);
+    const R Xy = pre * (T * T + R(2) * uyy * T + E * uyy);
+    const R w[3] = {R(0.5) * T, R(1) - T, R(0.5) * T};
+    const R twoRhoE = R(2) * rho * E;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int cx = cxq(q), cy = cyq(q);
+        const R herm = (axx * (R(cx * cx) - T) + R(2) * axy * R(cx * cy) + ayy * (R(cy * cy) - T)) * inv2T2;
+        R v = w[cx + 1] * w[cy + 1] * (twoRhoE + (qx * R(cx) + qy * R(cy)) * invT + herm);
+        if (q == 0) v += Xx + Xy;
+        if (q == 1 || q == 3) v -= R(0.5) * Xx;
+        if (q == 2 || q == 4) v -= R(0.5) * Xy;
+        g[q] = v;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void g_equilibrium(R rho, R ux, R uy, R T, R Cv, R* g) {
+    const R E = Cv * T + R(0.5) * (ux * ux + uy * uy);
+    const R H2 = R(2) * rho * (E + T);
+    g_hermite(rho, ux, uy, T, E, H2 * ux, H2 * uy, g);
+}
+
+// Collision at one node (Eq. f_boltz): f* = f + w (f^eq - f) + dt phi,
+// g* = g + w (g^eq - g) + (w1 - w)(g^qe - g).  phi_i = -(1/2) c_i . Y on the
+// axis velocities; q* = q^eq + 2 u.(P - P^eq); 1/w = 1/2 + mu/(rho T dt),
+// 1/w1 = 1/2 + (1/w - 1/2)/Pr.
+template <typename R>
+__device__ __forceinline__ void collide_node(R* f, R* g, R Yx, R Yy, R mu, R dt, R Cv, R Pr) {
+    const Macro<R> m = moments(f, g, Cv);
+    const R tau = R(0.5) + mu / (m.rho * m.T * dt);
+    const R om = R(1) / tau;
+    const R om1 = R(1) / (R(0.5) + (tau - R(0.5)) / Pr);
+    R pxx = 0, pxy = 0, pyy = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        pxx += R(cxq(q) * cxq(q)) * f[q];
+        pxy += R(cxq(q) * cyq(q)) * f[q];
+        pyy += R(cyq(q) * cyq(q)) * f[q];
+    }
+    const R dxx = pxx - m.rho * (m.ux * m.ux + m.T);
+    const R dxy = pxy - m.rho * (m.ux * m.uy);
+    const R dyy = pyy - m.rho * (m.uy * m.uy + m.T);
+    const R H2 = R(2) * m.rho * (m.E + m.T);
+    const R qex = H2 * m.ux, qey = H2 * m.uy;
+    const R qsx = qex + R(2) * (m.ux * dxx + m.uy * dxy);
+    const R qsy = qey + R(2) * (m.ux * dxy + m.uy * dyy);
+    R feq[9], geq[9];
+    f_equilibrium(m.rho, m.ux, m.uy, m.T, feq);
+    g_hermite(m.rho, m.ux, m.uy, m.T, m.E, qex, qey, geq);
+    // g^qe differs from g^eq only in the heat-flux term
+    const R w[3] = {R(0.5) * m.T, R(1) - m.T, R(0.5) * m.T};
+    const R invT = R(1) / m.T;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int cx = cxq(q), cy = cyq(q);
+        const R gqe = geq[q] + w[cx + 1] * w[cy + 1] * ((qsx - qex) * R(cx) + (qsy - qey) * R(cy)) * invT;
+        R phi = 0;
+        if (q >= 1 && q <= 4) phi = -R(0.5) * (R(cx) * Yx + R(cy) * Yy);
+        f[q] = f[q] + om * (feq[q] - f[q]) + dt * phi;
+        g[q] = g[q] + om * (geq[q] - g[q]) + (om1 - om) * (gqe - g[q]);
+    }
+}
+
+// Grad's approximation at wall targets (Sec. III A, Eqs. fnoneq, gnoneq,
+// strainrate): f = f^eq + dt f1, g = g^eq + dt g1.  grad u as (d_x u_x, d_y u_x,
+// d_x u_y, d_y u_y), grad T as (d_x T, d_y T).
+template <typename R>
+__device__ __forceinline__ void grad_populations(R rho, R ux, R uy, R T, R dudx, R dudy, R dvdx,
+                                                 R dvdy, R dTdx, R dTdy, R mu, R dt, R Cv, R Pr,
+                                                 R* f, R* g) {
+    const R Cp = Cv + R(1);
+    const R tau = R(0.5) + mu / (rho * T * dt);
+    const R om = R(1) / tau;
+    const R om1 = R(1) / (R(0.5) + (tau - R(0.5)) / Pr);
+    const R E = Cv * T + R(0.5) * (ux * ux + uy * uy);
+    const R sxx = R(2) * dudx, syy = R(2) * dvdy, sxy = dvdx + dudy;
+    const R div = dudx + dvdy;
+    const R cP = -(R(1) / om) * rho * T;
+    const R p1xx = cP * (sxx - div / Cv), p1yy = cP * (syy - div / Cv), p1xy = cP * sxy;
+    const R dEdx = Cv * dTdx + ux * dudx + uy * dvdx;
+    const R dEdy = Cv * dTdy + ux * dudy + uy * dvdy;
+    const R cq = -(R(2) / om1) * rho * Cp * T;
+    const R q1x = cq * dTdx + R(2) * (ux * p1xx + uy * p1xy);
+    const R q1y = cq * dTdy + R(2) * (ux * p1xy + uy * p1yy);
+    const R cR = -(R(2) / om1) * rho * T;
+    const R EpT = E + R(2) * T;
+    const R r1xx = cR * (sxx * EpT + R(2) * ux * dEdx);
+    const R r1yy = cR * (syy * EpT + R(2) * uy * dEdy);
+    const R r1xy = cR * (sxy * EpT + ux * dEdy + dEdx * uy);
+    f_equilibrium(rho, ux, uy, T, f);
+    g_equilibrium(rho, ux, uy, T, Cv, g);
+    const R w[3] = {R(0.5) * T, R(1) - T, R(0.5) * T};
+    const R inv2T2 = R(1) / (R(2) * T * T);
+    const R invT = R(1) / T;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int cx = cxq(q), cy = cyq(q);
+        const R W = w[cx + 1] * w[cy + 1];
+        const R dxx = R(cx * cx) - T, dyy = R(cy * cy) - T, dxy = R(cx * cy);
+        const R hp = (p1xx * dxx + R(2) * p1xy * dxy + p1yy * dyy) * inv2T2;
+        const R hr = (r1xx * dxx + R(2) * r1xy * dxy + r1yy * dyy) * inv2T2;
+        f[q] += dt * W * hp;
+        g[q] += dt * W * ((q1x * R(cx) + q1y * R(cy)) * invT + hr);
+    }
+}
+
+// Blended rigid map of one body (Sec. II D) for one body state, in the
+// precision R:  d(X) = A (X - Xp) + t with A = R(alpha) - I, t = (0, h);
+// x = X + (1 - r_blend) d(X).  dA, dt_ are the (state - previous state)
+// differences divided by the time step, for V_G.
+template <typename R>
+struct BodyMap {
+    int active;
+    R xc, yc, xp, yp, r_in, inv_w;
+    R a00, a01, a10, a11, tx, ty;
+    R va00, va01, va10, va11, vtx, vty;
+};
+
+template <typename R>
+__host__ __device__ inline BodyMap<R> make_body_map(const BodyDev& b, const BodyStateDev& s,
+                                                    const BodyStateDev& sp, double dt) {
+    BodyMap<R> m;
+    m.active = b.dof != 0;
+    m.xc = (R)b.xc; m.yc = (R)b.yc; m.xp = (R)b.xp; m.yp = (R)b.yp;
+    m.r_in = (R)b.r_in;
+    m.inv_w = (R)(1.0 / (b.r_out - b.r_in));
+    const double sa = sin(s.alpha), cm1 = -2.0 * sin(0.5 * s.alpha) * sin(0.5 * s.alpha);
+    const double spa = sin(sp.alpha), spm1 = -2.0 * sin(0.5 * sp.alpha) * sin(0.5 * sp.alpha);
+    m.a00 = (R)cm1; m.a01 = (R)(-sa); m.a10 = (R)sa; m.a11 = (R)cm1;
+    m.tx = (R)0; m.ty = (R)s.h;
+    const double inv = 1.0 / dt;
+    m.va00 = (R)((cm1 - spm1) * inv); m.va01 = (R)(-(sa - spa) * inv);
+    m.va10 = (R)((sa - spa) * inv); m.va11 = (R)((cm1 - spm1) * inv);
+    m.vtx = (R)0; m.vty = (R)((s.h - sp.h) * inv);
+    return m;
+}
+
+// F = dx/dX of the blended map (analytic, includes the gradient of the blend
+// factor) and V_G at absolute position (X, Y).  Outside the blended region
+// F = I and V_G = 0 exactly.
+template <typename R>
+__device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F00, R& F01, R& F10,
+                                           R& F11, R& vx, R& vy) {
+    F00 = R(1); F01 = R(0); F10 = R(0); F11 = R(1); vx = R(0); vy = R(0);
+    if (!bm.active) return;
+    const R dx = X - bm.xc, dy = Y - bm.yc;
+    const R dist = sqrt(dx * dx + dy * dy);
+    const R s = (dist - bm.r_in) * bm.inv_w;
+    if (s > R(1)) return;
+    R w, drx = R(0), dry = R(0);
+    if (s < R(0)) {
+        w = R(1);
+    } else {
+        const R r5 = s * s * s * (R(10) - R(15) * s + R(6) * s * s);
+        const R d5 = R(30) * s * s * (R(1) - s) * (R(1) - s);
+        w = R(1) - r5;
+        const R gq = d5 * bm.inv_w / dist;
+        drx = gq * dx;
+        dry = gq * dy;
+    }
+    const R px = X - bm.xp, py = Y - bm.yp;
+    const R ux = bm.a00 * px + bm.a01 * py + bm.tx;
+    const R uy = bm.a10 * px + bm.a11 * py + bm.ty;
+    F00 = R(1) + w * bm.a00 - ux * drx;
+    F01 = w * bm.a01 - ux * dry;
+    F10 = w * bm.a10 - uy * drx;
+    F11 = R(1) + w * bm.a11 - uy * dry;
+    vx = w * (bm.va00 * px + bm.va01 * py + bm.vtx);
+    vy = w * (bm.va10 * px + bm.va11 * py + bm.vty);
+}
+
+// Classical RK4 of the body ODE over dt with the load (Fx, Fy, M) held fixed
+// (Sec. III B; weak coupling of Sec. III).
+__host__ __device__ inline BodyStateDev rk4_body(const BodyDev& b, BodyStateDev s, double fy,
+                                                 double mz, double dt) {
+    if (b.dof == 1) {
+        auto acc = [&](double h, double v) { return (fy - b.k * h - b.c * v) / b.m; };
+        const double h0 = s.h, v0 = s.hdot;
+        const double k1h = v0, k1v = acc(h0, v0);
+        const double k2h = v0 + 0.5 * dt * k1v, k2v = acc(h0 + 0.5 * dt * k1h, v0 + 0.5 * dt * k1v);
+        const double k3h = v0 + 0.5 * dt * k2v, k3v = acc(h0 + 0.5 * dt * k2h, v0 + 0.5 * dt * k2v);
+        const double k4h = v0 + dt * k3v, k4v = acc(h0 + dt * k3h, v0 + dt * k3v);
+        s.h = h0 + dt / 6.0 * (k1h + 2.0 * k2h + 2.0 * k3h + k4h);
+        s.hdot = v0 + dt / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+    } else if (b.dof == 2) {
+        const double det = b.m * b.i_a - b.s_a * b.s_a;
+        auto accel = [&](const double* y, double* a) {
+            const double r0 = fy - b.k_h * y[0], r1 = mz - b.k_a * y[1];
+            a[0] = (b.i_a * r0 - b.s_a * r1) / det;
+            a[1] = (-b.s_a * r0 + b.m * r1) / det;
+        };
+        double y0[4] = {s.h, s.alpha, s.hdot, s.adot}, k[4][4], yt[4], acc2[2];
+        for (int st = 0; st < 4; ++st) {
+            const double c = (st == 0) ? 0.0 : (st == 3 ? 1.0 : 0.5);
+            for (int n = 0; n < 4; ++n) yt[n] = y0[n] + (st ? c * dt * k[st - 1][n] : 0.0);
+            accel(yt, acc2);
+            k[st][0] = yt[2]; k[st][1] = yt[3]; k[st][2] = acc2[0]; k[st][3] = acc2[1];
+        }
+        double y1[4];
+        for (int n = 0; n < 4; ++n)
+            y1[n] = y0[n] + dt / 6.0 * (k[0][n] + 2.0 * k[1][n] + 2.0 * k[2][n] + k[3][n]);
+        s.h = y1[0]; s.alpha = y1[1]; s.hdot = y1[2]; s.adot = y1[3];
+    }
+    return s;
+}
+
+}  // namespace lbfsi

@@ -1,0 +1,203 @@
+"""Thin ctypes binding of liblbfsi.so (C ABI declared in include/lbfsi.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library is missing the import
+of this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbfsi.so")
+
+FP64 = 0
+FP32 = 1
+
+OK, EINVAL, ENOMEM, ECUDA, EDEPARTURE, ENONPHYS, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDEPARTURE: "EDEPARTURE",
+          ENONPHYS: "ENONPHYS", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
+
+EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbfsi_blend_mesh",
+            "lbfsi_step", "lbfsi_body_forces", "lbfsi_advance_bodies", "lbfsi_get_body_state",
+            "lbfsi_get_fields", "lbfsi_get_populations", "lbfsi_set_populations",
+            "lbfsi_synchronize", "lbfsi_launch_count", "lbfsi_last_error"]
+
+
+class LbfsiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("dof", ctypes.c_int), ("xc", ctypes.c_double), ("yc", ctypes.c_double),
+                ("xp", ctypes.c_double), ("yp", ctypes.c_double), ("r_in", ctypes.c_double),
+                ("r_out", ctypes.c_double), ("length", ctypes.c_double),
+                ("m_star", ctypes.c_double), ("v_r", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("x_alpha", ctypes.c_double), ("r_alpha", ctypes.c_double),
+                ("wh_wa", ctypes.c_double)]
+
+
+class FlowParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("ma", "re", "t_inf", "gamma", "pr", "rho_inf", "dt", "length")]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("r", ctypes.POINTER(ctypes.c_double)), ("e", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
+                ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class BodyState(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("alpha", ctypes.c_double), ("hdot", ctypes.c_double),
+                ("adot", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblbfsi.so and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblbfsi.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.lbfsi_create_mesh.argtypes = [ctypes.POINTER(MeshDesc), P, ctypes.POINTER(P)]
+    lib.lbfsi_destroy_mesh.argtypes = [P]
+    lib.lbfsi_init_fields.argtypes = [P, ctypes.POINTER(FlowParams), dp]
+    lib.lbfsi_blend_mesh.argtypes = [P, ctypes.POINTER(BodyState), ctypes.POINTER(BodyState)]
+    lib.lbfsi_step.argtypes = [P, ctypes.c_int]
+    lib.lbfsi_body_forces.argtypes = [P, dp]
+    lib.lbfsi_advance_bodies.argtypes = [P, dp, ctypes.c_double]
+    lib.lbfsi_get_body_state.argtypes = [P, ctypes.POINTER(BodyState)]
+    lib.lbfsi_get_fields.argtypes = [P, dp]
+    lib.lbfsi_get_populations.argtypes = [P, ctypes.c_int, dp, dp]
+    lib.lbfsi_set_populations.argtypes = [P, dp, dp, dp]
+    lib.lbfsi_synchronize.argtypes = [P]
+    lib.lbfsi_launch_count.argtypes = [P]
+    lib.lbfsi_launch_count.restype = ctypes.c_int64
+    lib.lbfsi_last_error.argtypes = []
+    lib.lbfsi_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("lbfsi_launch_count", "lbfsi_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise LbfsiError(rc, _lib.lbfsi_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def body_desc(spec) -> BodyDesc:
+    """BodyDesc from any object carrying the BodySpec attribute names."""
+    return BodyDesc(int(spec.dof), spec.xc, spec.yc, spec.xp, spec.yp, spec.r_in, spec.r_out,
+                    spec.length, spec.m_star, spec.v_r, spec.zeta, spec.x_alpha, spec.r_alpha,
+                    spec.wh_wa)
+
+
+def flow_params(flow) -> FlowParams:
+    return FlowParams(flow.ma, flow.re, flow.t_inf, flow.gamma, flow.pr, flow.rho_inf, flow.dt,
+                      flow.length)
+
+
+class Mesh:
+    """Handle of one O-grid mesh with nbatch independent solves."""
+
+    def __init__(self, r, e, bodies, precision=FP64, centre=(0.0, 0.0), stream=None):
+        lib = load()
+        self._lib = lib
+        self.r = np.ascontiguousarray(r, dtype=np.float64)
+        self.e = np.ascontiguousarray(e, dtype=np.float64).reshape(-1, 2)
+        self.nr, self.nt = self.r.size, self.e.shape[0]
+        self.N = self.nr * self.nt
+        self.nbatch = len(bodies)
+        self.precision = precision
+        self._bodies = (BodyDesc * self.nbatch)(*[body_desc(b) for b in bodies])
+        d = MeshDesc(self.nr, self.nt, _dptr(self.r), _dptr(self.e), centre[0], centre[1],
+                     precision, self.nbatch, self._bodies)
+        h = ctypes.c_void_p()
+        _check(lib.lbfsi_create_mesh(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _check(self._lib.lbfsi_destroy_mesh(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, flow, rho_u_T=None):
+        p = flow_params(flow)
+        if rho_u_T is None:
+            _check(self._lib.lbfsi_init_fields(self.h, ctypes.byref(p), None))
+        else:
+            a = np.ascontiguousarray(rho_u_T, dtype=np.float64).reshape(self.nbatch, 4, self.N)
+            _check(self._lib.lbfsi_init_fields(self.h, ctypes.byref(p), _dptr(a)))
+
+    def blend_mesh(self, states, prev=None):
+        s = (BodyState * self.nbatch)(*[BodyState(*x) for x in states])
+        pv = None if prev is None else (BodyState * self.nbatch)(*[BodyState(*x) for x in prev])
+        _check(self._lib.lbfsi_blend_mesh(self.h, s, pv))
+
+    def step(self, n=1):
+        _check(self._lib.lbfsi_step(self.h, int(n)))
+
+    def synchronize(self):
+        _check(self._lib.lbfsi_synchronize(self.h))
+
+    def body_forces(self, out=None):
+        out = np.empty((self.nbatch, 3)) if out is None else out
+        _check(self._lib.lbfsi_body_forces(self.h, _dptr(out)))
+        return out
+
+    def advance_bodies(self, loads=None, dt=0.0):
+        if loads is None:
+            _check(self._lib.lbfsi_advance_bodies(self.h, None, float(dt)))
+        else:
+            a = np.ascontiguousarray(loads, dtype=np.float64).reshape(self.nbatch, 3)
+            _check(self._lib.lbfsi_advance_bodies(self.h, _dptr(a), float(dt)))
+
+    def body_state(self):
+        out = (BodyState * self.nbatch)()
+        _check(self._lib.lbfsi_get_body_state(self.h, out))
+        return [dict(h=s.h, alpha=s.alpha, hdot=s.hdot, adot=s.adot) for s in out]
+
+    def get_fields(self):
+        out = np.empty((self.nbatch, 4, self.nr, self.nt))
+        _check(self._lib.lbfsi_get_fields(self.h, _dptr(out)))
+        return out
+
+    def get_populations(self, which=0):
+        f = np.empty((self.nbatch, 9, self.nr, self.nt))
+        g = np.empty_like(f)
+        _check(self._lib.lbfsi_get_populations(self.h, int(which), _dptr(f), _dptr(g)))
+        return f, g
+
+    def set_populations(self, f, g, rho_u_T):
+        fa = np.ascontiguousarray(f, dtype=np.float64)
+        ga = np.ascontiguousarray(g, dtype=np.float64)
+        ma = np.ascontiguousarray(rho_u_T, dtype=np.float64)
+        _check(self._lib.lbfsi_set_populations(self.h, _dptr(fa), _dptr(ga), _dptr(ma)))
+
+    def launch_count(self) -> int:
+        return int(self._lib.lbfsi_launch_count(self.h))

@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every entry point that
+include/lbfsi.h declares; the ctypes structures match the C layouts; invalid
+arguments are rejected before any CUDA call (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbfsi.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2107_01370_gb300 import build, lbfsi
+    if not os.path.exists(lbfsi.LIB_PATH):
+        build.build()
+    return lbfsi.load()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbfsi_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbfsi_create_mesh", "lbfsi_blend_mesh", "lbfsi_init_fields", "lbfsi_step",
+                     "lbfsi_body_forces", "lbfsi_advance_bodies"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True)
+    exported = set(re.findall(r" T (lbfsi_\w+)", out.stdout))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2107_01370_gb300 import lbfsi
+    assert set(declared_functions()) == set(lbfsi.EXPORTED)
+
+
+def test_struct_layouts_match_c(tmp_path):
+    from paper_2107_01370_gb300 import lbfsi
+    src = tmp_path / "sz.c"
+    src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbfsi_body_desc),'
+                   'sizeof(lbfsi_flow_params), sizeof(lbfsi_mesh_desc), sizeof(lbfsi_body_state),'
+                   'offsetof(lbfsi_mesh_desc, bodies), offsetof(lbfsi_body_desc, wh_wa));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(lbfsi.BodyDesc), ctypes.sizeof(lbfsi.FlowParams),
+                   ctypes.sizeof(lbfsi.MeshDesc), ctypes.sizeof(lbfsi.BodyState),
+                   lbfsi.MeshDesc.bodies.offset, lbfsi.BodyDesc.wh_wa.offset]
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    from paper_2107_01370_gb300 import lbfsi
+    h = ctypes.c_void_p()
+    assert lib.lbfsi_create_mesh(None, None, ctypes.byref(h)) == lbfsi.EINVAL
+    assert b"null" in lib.lbfsi_last_error()
+    r = (ctypes.c_double * 8)(*range(1, 9))
+    e = (ctypes.c_double * 14)()
+    body = lbfsi.BodyDesc()
+    d = lbfsi.MeshDesc(8, 7, r, e, 0.0, 0.0, 0, 1, ctypes.pointer(body))   # odd ntheta
+    assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
+    assert b"ntheta" in lib.lbfsi_last_error()
+    d = lbfsi.MeshDesc(8, 8, r, e, 0.0, 0.0, 5, 1, ctypes.pointer(body))   # bad precision
+    assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
+    assert lib.lbfsi_step(None, 1) == lbfsi.EINVAL
+    assert lib.lbfsi_launch_count(None) == -1
