@@ -1,0 +1,345 @@
+"""Benchmark of the fused coupled step (one JSON line on stdout, rank 0).
+
+Workload: 1-DOF vortex-induced vibration of a cylinder (m* 10, zeta 0, V_R 5,
+Re 100, Ma 0.2) on an O-grid of 512 radial x 256 angular nodes deformed by the
+blending polynomial, FP32 populations with FP64 loads, RK4 and blend
+displacement; a batch of independent solves per GPU (default 16, a
+302 MB ping-pong population set, larger than the 129 MB L2).  A step is one
+coupled time step of every solve of the batch: one launch of the fused kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+  python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+
+Under torchrun every rank runs its own batch (replicas: the solves are
+independent, no data-path collective); the timed region is bracketed by a
+barrier and a synchronize, the time is the max over ranks and the value is the
+node updates of all ranks divided by it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+if "reference" in sys.argv:
+    # the oracle baseline runs single-threaded; set before numpy loads
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
+
+from paper_2107_01370_gb300 import inputs  # noqa: E402
+
+METRIC = "fused-step MLUPS"
+UNIT = "MLUPS"
+BYTES_PER_NODE_FP32 = 144   # 18 populations read + 18 written, 4 bytes each
+KERNEL = "k_step<float>"
+
+
+def workload_name(batch):
+    return (f"1-DOF VIV cylinder, O-grid 512x256 (131072 nodes) blended mesh, m* 10, V_R 5, "
+            f"Re 100, Ma 0.2, FP32 populations / FP64 loads+RK4; batch of {batch} solves per GPU")
+
+
+def source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2107_01370_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_per_node():
+    """DRAM bytes per node update of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_step_fp32_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_sha") != source_sha():
+        return None
+    return float(d["dram_bytes_per_node"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(steps=4):
+    """Time the FP64 oracle on the bench mesh in a fresh single-threaded
+    process (a bounded sample of the workload: one solve, a few steps)."""
+    code = (
+        "import os,sys,time,json;sys.path.insert(0,%r);"
+        "from paper_2107_01370_gb300 import inputs;import oracle.mesh as OM, oracle.solver as OS;"
+        "c=inputs.viv_cylinder_512x256();M0=inputs.initial_field(c.nr,c.ntheta,c.flow,seed=0);"
+        "s=OS.Solver.from_case(OM.ogrid_mesh(c.r,c.e),c,M0);s.step();t=time.perf_counter();"
+        "[s.step() for _ in range(%d)];dt=time.perf_counter()-t;"
+        "print(json.dumps({'seconds':dt,'nodes':c.nodes,'steps':%d}))" % (ROOT, steps, steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-200:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["nodes"] * d["steps"] / d["seconds"] / 1e6, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{d['steps']} steps of one 512x256 solve (FP64 numpy, 1 thread), "
+                      f"{d['seconds']:.1f} s"}
+
+
+REF_ROWS = 33   # odd: the truncated radial table stays subparametric
+
+
+def reference_sample_case():
+    """Bounded sample of the bench workload for the oracle: the first 33
+    radial rows (all 256 angular nodes, 8448 nodes) of the 512x256 VIV mesh,
+    with the same body, blend region, flow and time step."""
+    case = inputs.viv_cylinder_512x256()
+    case.r = case.r[:REF_ROWS].copy()
+    case.nr = REF_ROWS
+    return case
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, same metric and workload; each step
+    is one oracle step of the bounded sample (reference_sample_case)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle.mesh as OM
+    import oracle.solver as OS
+    case = reference_sample_case()
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
+    s = OS.Solver.from_case(OM.ogrid_mesh(case.r, case.e), case, M0)
+    for _ in range(args.warmup):
+        s.step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = time.perf_counter() - t
+    value = case.nodes * args.steps / dt / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": workload_name(1) + " (oracle sample)", "l2": "host run"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} oracle steps (FP64 numpy, 1 thread) of the "
+                                      f"first {REF_ROWS} radial rows x 256 angular nodes "
+                                      f"({REF_ROWS * 256} nodes) of one 512x256 solve"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_2107_01370_gb300 import build, lbfsi
+    if not os.path.exists(lbfsi.LIB_PATH):
+        build.build()
+    lbfsi.load()
+
+    case = inputs.viv_cylinder_512x256()
+    B = args.batch
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=rank)
+    M0b = np.ascontiguousarray(np.broadcast_to(M0, (B,) + M0.shape))
+    stream = torch.cuda.Stream(device=dev)
+    mesh = lbfsi.Mesh(case.r, case.e, case.bodies * B, precision=lbfsi.FP32,
+                      stream=stream.cuda_stream)
+    mesh.init_fields(case.flow, M0b)
+    mesh.step(args.warmup)
+    mesh.synchronize()
+
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.4)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = mesh.launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        mesh.step(1)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = mesh.launch_count() - l0
+    mesh.synchronize()   # raises if the kernels flagged an error
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    region_ms = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([region_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        region_ms = float(t.item())
+    nodes = case.nodes * B
+    value = nodes * world * args.steps / (region_ms * 1e-3) / 1e6
+    kavg_s = statistics.mean(kern_ms) * 1e-3
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_NODE_FP32 * nodes / kavg_s / 1e9
+    tpn = traffic_per_node()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": None if tpn is None else round(tpn * nodes),
+                "peak_kind": peak_kind, "kernel": KERNEL,
+                "algorithmic_bytes_per_launch": BYTES_PER_NODE_FP32 * nodes,
+                "kernel_ms": round(kavg_s * 1e3, 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: upload the initial
+        # fields, K coupled steps with the loads read back to the host after
+        # every step, download the final fields.
+        K = args.steps
+        m2 = lbfsi.Mesh(case.r, case.e, case.bodies * B, precision=lbfsi.FP32,
+                        stream=stream.cuda_stream)
+        loads = np.empty((B, 3))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        m2.init_fields(case.flow, M0b)
+        for _ in range(K):
+            m2.step(1)
+            m2.body_forces(loads)
+        fields = m2.get_fields()
+        t1 = time.perf_counter()
+        el = t1 - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": nodes * world * K / el / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(M0b.nbytes / K),
+               "d2h_bytes_per_step": int((fields.nbytes + K * loads.nbytes) / K),
+               "note": "init_fields upload + per-step load readback + final get_fields"}
+        m2.close()
+        del fields
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(region_ms / args.steps, 4), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": workload_name(B), "nodes_per_gpu": nodes, "batch": B,
+                          "mesh": "O-grid 512x256, r 0.5..20 D", "steps_per_solve": case.steps,
+                          "l2": "inputs larger than L2 (ping-pong populations "
+                                f"{BYTES_PER_NODE_FP32 * nodes / 1e6:.0f} MB)",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clocks,
+               "solves_per_s": round(B * world / (case.steps * region_ms / args.steps * 1e-3), 4)}
+        print(json.dumps(out), flush=True)
+    mesh.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -238,6 +238,22 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
             delete m;
             return fail(LBFSI_EINVAL, "radial table must increase");
         }
+    // subparametric tables: odd entries are the averages of their even
+    // neighbours (and, for even nr, the clamped last window is uniform), so
+    // every window is the bilinear image of the reference square
+    auto near = [](double a, double b, double scale) { return std::fabs(a - b) <= 1e-12 * scale; };
+    bool sub = true;
+    for (int i = 1; i + 1 < m->nr; i += 2)
+        sub = sub && near(m->r[i], 0.5 * (m->r[i - 1] + m->r[i + 1]), std::fabs(m->r[i + 1]));
+    if (m->nr % 2 == 0)
+        sub = sub && near(m->r[m->nr - 2], 0.5 * (m->r[m->nr - 3] + m->r[m->nr - 1]), std::fabs(m->r[m->nr - 1]));
+    for (int j = 1; j < m->nt; j += 2)
+        for (int c = 0; c < 2; ++c)
+            sub = sub && near(m->e[2 * j + c], 0.5 * (m->e[2 * (j - 1) + c] + m->e[2 * ((j + 1) % m->nt) + c]), 1.0);
+    if (!sub) {
+        delete m;
+        return fail(LBFSI_EINVAL, "r and e tables must be subparametric (odd entries = mean of even neighbours)");
+    }
     for (const auto& b : m->bodies) {
         if (b.dof < 0 || b.dof > 2) {
             delete m;
