@@ -1,5 +1,6 @@
 // C-ABI of the library (declared in include/lbfsi.h): handle, device memory,
 // host-side mesh geometry and the launch sequence of the coupled step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,6 +43,8 @@ struct lbfsi_mesh_s {
     double* d_e = nullptr;
     double* d_n0 = nullptr;
     double* d_wall_geo = nullptr;
+    void* d_rowtab = nullptr;
+    void* d_coltab = nullptr;
     BodyDev* d_bodies = nullptr;
     void* d_f[2] = {nullptr, nullptr};
     void* d_g[2] = {nullptr, nullptr};
@@ -49,15 +52,15 @@ struct lbfsi_mesh_s {
     void* d_fpost = nullptr;
     void* d_gpost = nullptr;
     double* d_stage = nullptr;  // [nbatch][4][N] float64 staging
-    BodyStateDev* d_S[2] = {nullptr, nullptr};
-    BodyStateDev* d_Sprev0 = nullptr;
-    BodyStateDev* d_Sforce = nullptr;
-    BodyStateDev* d_Stmp = nullptr;
-    double* d_part[2] = {nullptr, nullptr};
-    double* d_loads = nullptr;
+    lbfsi::StepMaps* d_maps[2] = {nullptr, nullptr};  // maps of the next launch (cur) / scratch
+    BodyStateDev* d_state_a = nullptr;                // host-given states staging
+    BodyStateDev* d_state_b = nullptr;
+    double* d_loads_tmp = nullptr;
+    double* d_part = nullptr;        // [nbatch][ntj][3] load partials
+    unsigned* d_counter = nullptr;   // [nbatch] CTA completion counters
     unsigned* d_status = nullptr;
-    int cur = 0, curS = 0, curP = 0;
-    bool initialized = false, first = true, force_pending = false;
+    int cur = 0, curM = 0;
+    bool initialized = false, first = true;
     double dt = 0, mu = 0, Cv = 0, Pr = 0, rho_inf = 0, uinf = 0, T_inf = 0;
     int64_t launches = 0;
 };
@@ -165,6 +168,70 @@ void wall_geometry(lbfsi_mesh m) {
     }
 }
 
+// Per-row and per-column geometry of the O-grid X = centre + r_i e_j used by
+// the step kernel (float64 here, stored in the element type of the path):
+//   row i: [0] r_i, [1] 1/r'_i and [2] 1/r_i (r'_i the derivative along the
+//          radial index of the quadratic through the node and its neighbours,
+//          one-sided on the first and last rows, Eq. ddx+fem), then for the two
+//          candidate radial cells a = i-1, a = i: [3|5] the node's xi in the
+//          cell's element, [4|6] 1 / (dR/dxi) of that element.
+//   col j: [0,1] e_j, [2..5] the angular factors of the inverse metric
+//          (de_y, e_y, de_x, e_x) / (e x de) with de = (e_{j+1} - e_{j-1})/2, then
+//          for the two candidate angular cells b = j-1, b = j: [6|10] the node's
+//          eta in the element, [7,8|11,12] dE/deta of the element,
+//          [9|13] (dE/deta) x e_j.
+void geometry_tables(lbfsi_mesh m, std::vector<double>& row, std::vector<double>& col) {
+    const int nr = m->nr, nt = m->nt;
+    const double* r = m->r.data();
+    const double* e = m->e.data();
+    row.assign((size_t)nr * lbfsi::ROWTAB, 0.0);
+    for (int i = 0; i < nr; ++i) {
+        double drc;
+        if (i == 0)
+            drc = 0.5 * (-3.0 * r[0] + 4.0 * r[1] - r[2]);
+        else if (i == nr - 1)
+            drc = 0.5 * (3.0 * r[nr - 1] - 4.0 * r[nr - 2] + r[nr - 3]);
+        else
+            drc = 0.5 * (r[i + 1] - r[i - 1]);
+        double* t = &row[(size_t)i * lbfsi::ROWTAB];
+        t[0] = r[i];
+        t[1] = 1.0 / drc;
+        t[2] = 1.0 / r[i];
+        for (int c = 0; c < 2; ++c) {
+            const int a = i - 1 + c;
+            if (a < 0 || a > nr - 2) continue;
+            const int wa = std::min(2 * (a / 2), nr - 3);
+            t[3 + 2 * c] = (double)(i - wa - 1);
+            t[4 + 2 * c] = 2.0 / (r[wa + 2] - r[wa]);
+        }
+    }
+    col.assign((size_t)nt * lbfsi::COLTAB, 0.0);
+    auto wr = [nt](int j) { return ((j % nt) + nt) % nt; };
+    for (int j = 0; j < nt; ++j) {
+        const double ex = e[2 * j], ey = e[2 * j + 1];
+        const int jp = wr(j + 1), jm = wr(j - 1);
+        const double dex = 0.5 * (e[2 * jp] - e[2 * jm]), dey = 0.5 * (e[2 * jp + 1] - e[2 * jm + 1]);
+        const double cr = ex * dey - ey * dex;
+        double* t = &col[(size_t)j * lbfsi::COLTAB];
+        t[0] = ex;
+        t[1] = ey;
+        t[2] = dey / cr;
+        t[3] = ey / cr;
+        t[4] = dex / cr;
+        t[5] = ex / cr;
+        for (int c = 0; c < 2; ++c) {
+            const int b = j - 1 + c;
+            const int wb = (b >= 0) ? 2 * (b / 2) : -2 * ((-b + 1) / 2);
+            const int w0 = wr(wb), w2 = wr(wb + 2);
+            const double dEx = 0.5 * (e[2 * w2] - e[2 * w0]), dEy = 0.5 * (e[2 * w2 + 1] - e[2 * w0 + 1]);
+            t[6 + 4 * c] = (double)(j - wb - 1);
+            t[7 + 4 * c] = dEx;
+            t[8 + 4 * c] = dEy;
+            t[9 + 4 * c] = dEx * ey - dEy * ex;
+        }
+    }
+}
+
 // Dimensional ODE coefficients from the paper's nondimensional groups
 // (Sec. IV A for the transverse model, Sec. IV D for pitch-plunge).
 BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
@@ -193,10 +260,10 @@ BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
 }
 
 void free_all(lbfsi_mesh m) {
-    void* ptrs[] = {m->d_r, m->d_e, m->d_n0, m->d_wall_geo, m->d_bodies, m->d_f[0], m->d_f[1],
-                    m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost, m->d_gpost, m->d_stage,
-                    m->d_S[0], m->d_S[1], m->d_Sprev0, m->d_Sforce, m->d_Stmp, m->d_part[0],
-                    m->d_part[1], m->d_loads, m->d_status};
+    void* ptrs[] = {m->d_r, m->d_e, m->d_n0, m->d_wall_geo, m->d_rowtab, m->d_coltab, m->d_bodies,
+                    m->d_f[0], m->d_f[1], m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost,
+                    m->d_gpost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
+                    m->d_loads_tmp, m->d_part, m->d_counter, m->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -275,6 +342,8 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
         }
     }
     wall_geometry(m);
+    std::vector<double> rowt, colt;
+    geometry_tables(m, rowt, colt);
     const size_t N = (size_t)m->N, nb = (size_t)m->nbatch;
     cudaError_t e = cudaSuccess;
 #define LB_ALLOC(ptr, cnt)                                   \
@@ -283,16 +352,17 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     LB_ALLOC(m->d_e, 2 * (size_t)m->nt);
     LB_ALLOC(m->d_n0, 2 * (size_t)m->nt);
     LB_ALLOC(m->d_wall_geo, 6 * (size_t)m->nt);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_rowtab, rowt.size() * m->esize);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_coltab, colt.size() * m->esize);
     LB_ALLOC(m->d_bodies, nb);
     LB_ALLOC(m->d_stage, nb * 4 * N);
-    LB_ALLOC(m->d_S[0], nb);
-    LB_ALLOC(m->d_S[1], nb);
-    LB_ALLOC(m->d_Sprev0, nb);
-    LB_ALLOC(m->d_Sforce, nb);
-    LB_ALLOC(m->d_Stmp, nb);
-    LB_ALLOC(m->d_part[0], nb * m->ntj * 3);
-    LB_ALLOC(m->d_part[1], nb * m->ntj * 3);
-    LB_ALLOC(m->d_loads, nb * 3);
+    LB_ALLOC(m->d_maps[0], nb);
+    LB_ALLOC(m->d_maps[1], nb);
+    LB_ALLOC(m->d_state_a, nb);
+    LB_ALLOC(m->d_state_b, nb);
+    LB_ALLOC(m->d_loads_tmp, nb * 3);
+    LB_ALLOC(m->d_part, nb * m->ntj * 3);
+    LB_ALLOC(m->d_counter, nb);
     LB_ALLOC(m->d_status, 1);
 #undef LB_ALLOC
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -312,6 +382,18 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     if (e == cudaSuccess)
         e = cudaMemcpy(m->d_wall_geo, m->wall_geo.data(), 6 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(m->d_counter, 0, nb * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(m->d_part, 0, nb * m->ntj * 3 * sizeof(double));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        const std::vector<double>& src = k ? colt : rowt;
+        void* dst = k ? m->d_coltab : m->d_rowtab;
+        if (m->precision == LBFSI_FP64) {
+            e = cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> tf(src.begin(), src.end());
+            e = cudaMemcpy(dst, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+    }
     if (e != cudaSuccess) {
         free_all(m);
         delete m;
@@ -358,20 +440,22 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
             }
     }
     std::vector<BodyStateDev> zero(nb, BodyStateDev{0.0, 0.0, 0.0, 0.0});
-    std::vector<double> zp(nb * m->ntj * 3, 0.0);
+    std::vector<double> zl(nb * 3, 0.0);
     cudaError_t e = cudaMemcpyAsync(m->d_bodies, bd.data(), nb * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMemcpyAsync(m->d_S[k], zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(m->d_part[k], zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
-    }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->d_Sprev0, zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+        e = cudaMemcpyAsync(m->d_state_a, zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_loads_tmp, zl.data(), zl.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, nb * sizeof(unsigned), m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init_fields upload");
-    m->cur = m->curS = m->curP = 0;
+    m->cur = m->curM = 0;
+    e = lbfsi::launch_prepare(m->d_bodies, m->d_state_a, m->d_state_a, m->d_state_a, m->d_loads_tmp,
+                              m->dt, m->nbatch, m->d_maps[0], m->stream);
+    m->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "prepare kernel");
     e = lbfsi::launch_init(m->precision, m->d_stage, m->d_f[0], m->d_g[0], m->d_M[0], m->N, m->nbatch,
                            m->Cv, m->stream);
     m->launches++;
@@ -380,7 +464,6 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     if (e != cudaSuccess) return cuda_fail(e, "init sync");
     m->initialized = true;
     m->first = true;
-    m->force_pending = false;
     return LBFSI_OK;
 }
 
@@ -390,17 +473,15 @@ int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_bo
     const size_t nb = (size_t)m->nbatch;
     static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
     const lbfsi_body_state* pv = prev ? prev : state;
-    cudaError_t e;
-    if (m->first) {
-        e = cudaMemcpyAsync(m->d_S[m->curS], state, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(m->d_Sprev0, pv, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
-    } else {
-        e = cudaMemcpyAsync(m->d_S[m->curS], pv, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(m->d_Sforce, state, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
-        m->force_pending = true;
-    }
+    cudaError_t e = cudaMemcpyAsync(m->d_state_a, state, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_state_b, pv, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+    // before the first step the collision map is unused; later it stays the
+    // state of the last streamed step
+    if (e == cudaSuccess)
+        e = lbfsi::launch_prepare(m->d_bodies, m->first ? m->d_state_a : nullptr, m->d_state_a,
+                                  m->d_state_b, nullptr, m->dt, m->nbatch, m->d_maps[m->curM], m->stream);
+    m->launches++;
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "blend_mesh");
     return LBFSI_OK;
@@ -411,17 +492,17 @@ static lbfsi::StepArgs make_args(lbfsi_mesh m, int mode) {
     a.nr = m->nr; a.nt = m->nt; a.N = m->N; a.nbatch = m->nbatch; a.ntj = m->ntj;
     a.xm = m->xm; a.ym = m->ym;
     a.r = m->d_r; a.e = m->d_e; a.n0 = m->d_n0; a.wall_geo = m->d_wall_geo;
+    a.rowtab = m->d_rowtab; a.coltab = m->d_coltab;
     a.dt = m->dt; a.mu = m->mu; a.Cv = m->Cv; a.Pr = m->Pr; a.rho_inf = m->rho_inf;
     a.uinf_x = m->uinf; a.uinf_y = 0.0; a.T_inf = m->T_inf;
     a.f_in = m->d_f[m->cur]; a.g_in = m->d_g[m->cur];
     a.f_out = m->d_f[m->cur ^ 1]; a.g_out = m->d_g[m->cur ^ 1];
     a.M_in = m->d_M[m->cur]; a.M_out = m->d_M[m->cur ^ 1];
     a.bodies = m->d_bodies;
-    a.S_in = m->d_S[m->curS]; a.S_out = m->d_S[m->curS ^ 1];
-    a.S_prev0 = m->d_Sprev0;
-    a.S_force = nullptr;
-    a.part_in = m->d_part[m->curP]; a.part_out = m->d_part[m->curP ^ 1];
-    a.loads_out = nullptr;
+    a.maps_in = m->d_maps[m->curM];
+    a.maps_out = m->d_maps[m->curM ^ 1];
+    a.part = m->d_part;
+    a.counter = m->d_counter;
     a.mode = mode;
     a.status = m->d_status;
     return a;
@@ -433,15 +514,12 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
     for (int s = 0; s < nsteps; ++s) {
         lbfsi::StepArgs a = make_args(m, m->first ? lbfsi::MODE_STREAM_ONLY : lbfsi::MODE_COLLIDE_STREAM);
-        if (m->force_pending && !m->first) a.S_force = m->d_Sforce;
         cudaError_t e = lbfsi::launch_step(a, m->precision, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         m->cur ^= 1;
-        m->curS ^= 1;
-        m->curP ^= 1;
+        m->curM ^= 1;
         m->first = false;
-        m->force_pending = false;
     }
     return LBFSI_OK;
 }
@@ -451,34 +529,43 @@ int lbfsi_synchronize(lbfsi_mesh m) {
     return check_status(m);
 }
 
+static int download_maps(lbfsi_mesh m, std::vector<lbfsi::StepMaps>& out) {
+    out.resize(m->nbatch);
+    cudaError_t e = cudaMemcpyAsync(out.data(), m->d_maps[m->curM], out.size() * sizeof(lbfsi::StepMaps),
+                                    cudaMemcpyDeviceToHost, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "maps copy");
+    return check_status(m);
+}
+
 int lbfsi_body_forces(lbfsi_mesh m, double* out) {
     if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    cudaError_t e = lbfsi::launch_reduce_loads(m->d_part[m->curP], m->ntj, m->nbatch, m->d_loads, m->stream);
-    m->launches++;
-    if (e != cudaSuccess) return cuda_fail(e, "reduce loads");
-    e = cudaMemcpyAsync(out, m->d_loads, (size_t)m->nbatch * 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "loads copy");
-    return check_status(m);
+    std::vector<lbfsi::StepMaps> mp;
+    const int rc = download_maps(m, mp);
+    if (rc) return rc;
+    for (int b = 0; b < m->nbatch; ++b)
+        for (int c = 0; c < 3; ++c) out[b * 3 + c] = mp[b].loads[c];
+    return LBFSI_OK;
 }
 
 int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     const size_t nb = (size_t)m->nbatch;
-    cudaError_t e;
+    std::vector<double> ld(nb * 3);
     if (loads) {
-        e = cudaMemcpyAsync(m->d_loads, loads, nb * 3 * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+        std::memcpy(ld.data(), loads, ld.size() * sizeof(double));
     } else {
-        e = lbfsi::launch_reduce_loads(m->d_part[m->curP], m->ntj, m->nbatch, m->d_loads, m->stream);
-        m->launches++;
+        std::vector<lbfsi::StepMaps> mp;
+        const int rc = download_maps(m, mp);
+        if (rc) return rc;
+        for (size_t b = 0; b < nb; ++b)
+            for (int c = 0; c < 3; ++c) ld[b * 3 + c] = mp[b].loads[c];
     }
+    cudaError_t e = cudaMemcpyAsync(m->d_loads_tmp, ld.data(), ld.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = lbfsi::launch_advance(m->d_bodies, m->d_S[m->curS], m->d_loads, dt, m->nbatch, m->d_Stmp,
-                                  m->d_Sprev0, m->stream);
+        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, m->nbatch, m->d_maps[m->curM], m->stream);
     m->launches++;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->d_S[m->curS], m->d_Stmp, nb * sizeof(BodyStateDev), cudaMemcpyDeviceToDevice, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "advance_bodies");
     return check_status(m);
 }
@@ -486,22 +573,16 @@ int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
 int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out) {
     if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    const size_t nb = (size_t)m->nbatch;
-    cudaError_t e = cudaSuccess;
-    const BodyStateDev* src = m->d_S[m->curS];
-    if (!m->first) {
-        // the state after the structural update of the last step
-        e = lbfsi::launch_reduce_loads(m->d_part[m->curP], m->ntj, m->nbatch, m->d_loads, m->stream);
-        if (e == cudaSuccess)
-            e = lbfsi::launch_advance(m->d_bodies, m->d_S[m->curS], m->d_loads, m->dt, m->nbatch,
-                                      m->d_Stmp, nullptr, m->stream);
-        m->launches += 2;
-        src = m->d_Stmp;
+    std::vector<lbfsi::StepMaps> mp;
+    const int rc = download_maps(m, mp);
+    if (rc) return rc;
+    for (int b = 0; b < m->nbatch; ++b) {
+        out[b].h = mp[b].S_next.h;
+        out[b].alpha = mp[b].S_next.alpha;
+        out[b].hdot = mp[b].S_next.hdot;
+        out[b].adot = mp[b].S_next.adot;
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out, src, nb * sizeof(BodyStateDev), cudaMemcpyDeviceToHost, m->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "get_body_state");
-    return check_status(m);
+    return LBFSI_OK;
 }
 
 int lbfsi_get_fields(lbfsi_mesh m, double* rho_u_T) {

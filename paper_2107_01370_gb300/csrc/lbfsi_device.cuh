@@ -19,6 +19,16 @@ __host__ __device__ constexpr int cyq(int q) {
     return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
 }
 
+// Reciprocal and square root in the precision of the path: one MUFU-based
+// reciprocal (two roundings in total for a quotient) on the float path,
+// IEEE division on the float64 path.
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_(double x) { return fabs(x); }
+
 template <typename R>
 struct Macro {
     R rho, ux, uy, T, E;
@@ -36,11 +46,12 @@ __device__ __forceinline__ Macro<R> moments(const R* f, const R* g, R Cv) {
         s2 += g[q];
     }
     Macro<R> m;
+    const R ir = rcp_(rho);
     m.rho = rho;
-    m.ux = jx / rho;
-    m.uy = jy / rho;
-    m.E = s2 / (R(2) * rho);
-    m.T = (m.E - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) / Cv;
+    m.ux = jx * ir;
+    m.uy = jy * ir;
+    m.E = R(0.5) * s2 * ir;
+    m.T = (m.E - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) * rcp_(Cv);
     return m;
 }
 
@@ -64,8 +75,8 @@ __device__ __forceinline__ void g_hermite(R rho, R ux, R uy, R T, R E, R qx, R q
     const R axx = R(2) * rho * E * uxx + R(2) * rho * T * (T + R(2) * uxx);
     const R ayy = R(2) * rho * E * uyy + R(2) * rho * T * (T + R(2) * uyy);
     const R axy = R(2) * rho * E * uxy + R(4) * rho * T * uxy;
-    const R inv2T2 = R(1) / (R(2) * T * T);
-    const R invT = R(1) / T;
+    const R invT = rcp_(T);
+    const R inv2T2 = R(0.5) * invT * invT;
     const R pre = rho * (R(1) - R(3) * T) * invT;
     const R Xx = pre * (T * T + R(2) * uxx * T + E * uxx);
     const R Xy = pre * (T * T + R(2) * uyy * T + E * uyy);
@@ -93,13 +104,14 @@ __device__ __forceinline__ void g_equilibrium(R rho, R ux, R uy, R T, R Cv, R* g
 // Collision at one node (Eq. f_boltz): f* = f + w (f^eq - f) + dt phi,
 // g* = g + w (g^eq - g) + (w1 - w)(g^qe - g).  phi_i = -(1/2) c_i . Y on the
 // axis velocities; q* = q^eq + 2 u.(P - P^eq); 1/w = 1/2 + mu/(rho T dt),
-// 1/w1 = 1/2 + (1/w - 1/2)/Pr.
+// 1/w1 = 1/2 + (1/w - 1/2)/Pr.  g^qe differs from g^eq only in the heat flux,
+// so both are formed from one Hermite expansion.
 template <typename R>
-__device__ __forceinline__ void collide_node(R* f, R* g, R Yx, R Yy, R mu, R dt, R Cv, R Pr) {
+__device__ __forceinline__ void collide_node(R* f, R* g, R Yx, R Yy, R mu, R dt, R Cv, R iPr) {
     const Macro<R> m = moments(f, g, Cv);
-    const R tau = R(0.5) + mu / (m.rho * m.T * dt);
-    const R om = R(1) / tau;
-    const R om1 = R(1) / (R(0.5) + (tau - R(0.5)) / Pr);
+    const R tau = R(0.5) + mu * rcp_(m.rho * m.T * dt);
+    const R om = rcp_(tau);
+    const R om1 = rcp_(R(0.5) + (tau - R(0.5)) * iPr);
     R pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -107,27 +119,43 @@ __device__ __forceinline__ void collide_node(R* f, R* g, R Yx, R Yy, R mu, R dt,
         pxy += R(cxq(q) * cyq(q)) * f[q];
         pyy += R(cyq(q) * cyq(q)) * f[q];
     }
-    const R dxx = pxx - m.rho * (m.ux * m.ux + m.T);
-    const R dxy = pxy - m.rho * (m.ux * m.uy);
-    const R dyy = pyy - m.rho * (m.uy * m.uy + m.T);
-    const R H2 = R(2) * m.rho * (m.E + m.T);
-    const R qex = H2 * m.ux, qey = H2 * m.uy;
-    const R qsx = qex + R(2) * (m.ux * dxx + m.uy * dxy);
-    const R qsy = qey + R(2) * (m.ux * dxy + m.uy * dyy);
-    R feq[9], geq[9];
-    f_equilibrium(m.rho, m.ux, m.uy, m.T, feq);
-    g_hermite(m.rho, m.ux, m.uy, m.T, m.E, qex, qey, geq);
-    // g^qe differs from g^eq only in the heat-flux term
-    const R w[3] = {R(0.5) * m.T, R(1) - m.T, R(0.5) * m.T};
-    const R invT = R(1) / m.T;
+    const R ux = m.ux, uy = m.uy, T = m.T, rho = m.rho, E = m.E;
+    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const R dxx = pxx - rho * (uxx + T);
+    const R dxy = pxy - rho * uxy;
+    const R dyy = pyy - rho * (uyy + T);
+    const R H2 = R(2) * rho * (E + T);
+    const R qex = H2 * ux, qey = H2 * uy;
+    const R dqx = R(2) * (ux * dxx + uy * dxy), dqy = R(2) * (ux * dxy + uy * dyy);  // q* - q^eq
+    const R axx = R(2) * rho * E * uxx + R(2) * rho * T * (T + R(2) * uxx);
+    const R ayy = R(2) * rho * E * uyy + R(2) * rho * T * (T + R(2) * uyy);
+    const R axy = R(2) * rho * E * uxy + R(4) * rho * T * uxy;
+    const R invT = rcp_(T);
+    const R inv2T2 = R(0.5) * invT * invT;
+    const R pre = rho * (R(1) - R(3) * T) * invT;
+    const R Xx = pre * (T * T + R(2) * uxx * T + E * uxx);
+    const R Xy = pre * (T * T + R(2) * uyy * T + E * uyy);
+    const R ax = uxx + T, ay = uyy + T;
+    const R px[3] = {R(0.5) * (ax - ux), R(1) - ax, R(0.5) * (ax + ux)};
+    const R py[3] = {R(0.5) * (ay - uy), R(1) - ay, R(0.5) * (ay + uy)};
+    const R w[3] = {R(0.5) * T, R(1) - T, R(0.5) * T};
+    const R twoRhoE = R(2) * rho * E;
+    const R dom = om1 - om;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int cx = cxq(q), cy = cyq(q);
-        const R gqe = geq[q] + w[cx + 1] * w[cy + 1] * ((qsx - qex) * R(cx) + (qsy - qey) * R(cy)) * invT;
+        const R feq = rho * px[cx + 1] * py[cy + 1];
+        const R herm = (axx * (R(cx * cx) - T) + R(2) * axy * R(cx * cy) + ayy * (R(cy * cy) - T)) * inv2T2;
+        const R W = w[cx + 1] * w[cy + 1];
+        R geq = W * (twoRhoE + (qex * R(cx) + qey * R(cy)) * invT + herm);
+        if (q == 0) geq += Xx + Xy;
+        if (q == 1 || q == 3) geq -= R(0.5) * Xx;
+        if (q == 2 || q == 4) geq -= R(0.5) * Xy;
+        const R gqe = geq + W * (dqx * R(cx) + dqy * R(cy)) * invT;
         R phi = 0;
         if (q >= 1 && q <= 4) phi = -R(0.5) * (R(cx) * Yx + R(cy) * Yy);
-        f[q] = f[q] + om * (feq[q] - f[q]) + dt * phi;
-        g[q] = g[q] + om * (geq[q] - g[q]) + (om1 - om) * (gqe - g[q]);
+        f[q] = f[q] + om * (feq - f[q]) + dt * phi;
+        g[q] = g[q] + om * (geq - g[q]) + dom * (gqe - g[q]);
     }
 }
 
@@ -139,20 +167,20 @@ __device__ __forceinline__ void grad_populations(R rho, R ux, R uy, R T, R dudx,
                                                  R dvdy, R dTdx, R dTdy, R mu, R dt, R Cv, R Pr,
                                                  R* f, R* g) {
     const R Cp = Cv + R(1);
-    const R tau = R(0.5) + mu / (rho * T * dt);
-    const R om = R(1) / tau;
-    const R om1 = R(1) / (R(0.5) + (tau - R(0.5)) / Pr);
+    const R iom = R(0.5) + mu * rcp_(rho * T * dt);      // 1/omega
+    const R iom1 = R(0.5) + (iom - R(0.5)) * rcp_(Pr);  // 1/omega_1
     const R E = Cv * T + R(0.5) * (ux * ux + uy * uy);
     const R sxx = R(2) * dudx, syy = R(2) * dvdy, sxy = dvdx + dudy;
     const R div = dudx + dvdy;
-    const R cP = -(R(1) / om) * rho * T;
-    const R p1xx = cP * (sxx - div / Cv), p1yy = cP * (syy - div / Cv), p1xy = cP * sxy;
+    const R iCv = rcp_(Cv);
+    const R cP = -iom * rho * T;
+    const R p1xx = cP * (sxx - div * iCv), p1yy = cP * (syy - div * iCv), p1xy = cP * sxy;
     const R dEdx = Cv * dTdx + ux * dudx + uy * dvdx;
     const R dEdy = Cv * dTdy + ux * dudy + uy * dvdy;
-    const R cq = -(R(2) / om1) * rho * Cp * T;
+    const R cq = -R(2) * iom1 * rho * Cp * T;
     const R q1x = cq * dTdx + R(2) * (ux * p1xx + uy * p1xy);
     const R q1y = cq * dTdy + R(2) * (ux * p1xy + uy * p1yy);
-    const R cR = -(R(2) / om1) * rho * T;
+    const R cR = -R(2) * iom1 * rho * T;
     const R EpT = E + R(2) * T;
     const R r1xx = cR * (sxx * EpT + R(2) * ux * dEdx);
     const R r1yy = cR * (syy * EpT + R(2) * uy * dEdy);
@@ -160,8 +188,8 @@ __device__ __forceinline__ void grad_populations(R rho, R ux, R uy, R T, R dudx,
     f_equilibrium(rho, ux, uy, T, f);
     g_equilibrium(rho, ux, uy, T, Cv, g);
     const R w[3] = {R(0.5) * T, R(1) - T, R(0.5) * T};
-    const R inv2T2 = R(1) / (R(2) * T * T);
-    const R invT = R(1) / T;
+    const R invT = rcp_(T);
+    const R inv2T2 = R(0.5) * invT * invT;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int cx = cxq(q), cy = cyq(q);
@@ -178,14 +206,6 @@ __device__ __forceinline__ void grad_populations(R rho, R ux, R uy, R T, R dudx,
 // precision R:  d(X) = A (X - Xp) + t with A = R(alpha) - I, t = (0, h);
 // x = X + (1 - r_blend) d(X).  dA, dt_ are the (state - previous state)
 // differences divided by the time step, for V_G.
-template <typename R>
-struct BodyMap {
-    int active;
-    R xc, yc, xp, yp, r_in, inv_w;
-    R a00, a01, a10, a11, tx, ty;
-    R va00, va01, va10, va11, vtx, vty;
-};
-
 template <typename R>
 __host__ __device__ inline BodyMap<R> make_body_map(const BodyDev& b, const BodyStateDev& s,
                                                     const BodyStateDev& sp, double dt) {
@@ -214,7 +234,7 @@ __device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F0
     F00 = R(1); F01 = R(0); F10 = R(0); F11 = R(1); vx = R(0); vy = R(0);
     if (!bm.active) return;
     const R dx = X - bm.xc, dy = Y - bm.yc;
-    const R dist = sqrt(dx * dx + dy * dy);
+    const R dist = sqrt_(dx * dx + dy * dy);
     const R s = (dist - bm.r_in) * bm.inv_w;
     if (s > R(1)) return;
     R w, drx = R(0), dry = R(0);
@@ -224,7 +244,7 @@ __device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F0
         const R r5 = s * s * s * (R(10) - R(15) * s + R(6) * s * s);
         const R d5 = R(30) * s * s * (R(1) - s) * (R(1) - s);
         w = R(1) - r5;
-        const R gq = d5 * bm.inv_w / dist;
+        const R gq = d5 * bm.inv_w * rcp_(dist);
         drx = gq * dx;
         dry = gq * dy;
     }
@@ -237,6 +257,20 @@ __device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F0
     F11 = R(1) + w * bm.a11 - uy * dry;
     vx = w * (bm.va00 * px + bm.va01 * py + bm.vtx);
     vy = w * (bm.va10 * px + bm.va11 * py + bm.vty);
+}
+
+// Fill a maps record: collision map from S_cur, stream maps from
+// (S_next, S_vgprev).
+__host__ __device__ inline void build_maps(const BodyDev& b, const BodyStateDev& S_cur,
+                                           const BodyStateDev& S_next,
+                                           const BodyStateDev& S_vgprev, double dt, StepMaps& m) {
+    m.S_cur = S_cur;
+    m.S_next = S_next;
+    m.S_vgprev = S_vgprev;
+    m.Kd = make_body_map<double>(b, S_cur, S_cur, dt);
+    m.Sd = make_body_map<double>(b, S_next, S_vgprev, dt);
+    m.Kf = make_body_map<float>(b, S_cur, S_cur, dt);
+    m.Sf = make_body_map<float>(b, S_next, S_vgprev, dt);
 }
 
 // Classical RK4 of the body ODE over dt with the load (Fx, Fy, M) held fixed

@@ -26,6 +26,32 @@ struct BodyStateDev {
     double h, alpha, hdot, adot;
 };
 
+// Per-row and per-column geometry of the O-grid X = centre + r_i e_j (see
+// the table builder in lbfsi_api.cu for the meaning of each entry).
+constexpr int ROWTAB = 8;
+constexpr int COLTAB = 16;
+
+// Blended rigid map of one body for one body state (defined in
+// lbfsi_device.cuh); declared here so the per-step record can hold it.
+template <typename R>
+struct BodyMap {
+    int active;
+    R xc, yc, xp, yp, r_in, inv_w;
+    R a00, a01, a10, a11, tx, ty;
+    R va00, va01, va10, va11, vtx, vty;
+};
+
+// Per-solve record handed from one launch to the next: the body state of the
+// last streamed step (used by the next collision), the state and previous
+// state for the next stream (V_G), the loads of the last streamed step and
+// the blended maps built from those states.
+struct StepMaps {
+    BodyStateDev S_cur, S_next, S_vgprev;
+    double loads[3];
+    BodyMap<double> Kd, Sd;
+    BodyMap<float> Kf, Sf;
+};
+
 enum StepMode : int { MODE_STREAM_ONLY = 0, MODE_COLLIDE_STREAM = 1, MODE_COLLIDE_ONLY = 2 };
 
 // Arguments of the fused step kernel (one launch = collide step k in shared
@@ -36,7 +62,9 @@ struct StepArgs {
     const double* r;           // [nr]
     const double* e;           // [nt][2]
     const double* n0;          // [nt][2] wall normals (undeformed)
-    const double* wall_geo;    // [nt][6]: per wall node (w1 ds1 n1x n1y, w2 ds2) see api
+    const double* wall_geo;    // [nt][6]: per wall node two (weight*length, n_x, n_y) edge shares
+    const void* rowtab;        // [nr][ROWTAB] per-row geometry (element type of the path)
+    const void* coltab;        // [nt][COLTAB] per-column geometry
     // flow
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
     // state buffers (element type set by the template)
@@ -48,13 +76,10 @@ struct StepArgs {
     void* M_out;
     // bodies
     const BodyDev* bodies;          // [nbatch]
-    const BodyStateDev* S_in;       // [nbatch] state S^k
-    const BodyStateDev* S_prev0;    // [nbatch] previous state (stream-only mode)
-    const BodyStateDev* S_force;    // [nbatch] prescribed next state (nullptr = RK4)
-    BodyStateDev* S_out;            // [nbatch] state S^{k+1}
-    const double* part_in;          // [nbatch][ntj][3] load partials of step k
-    double* part_out;               // [nbatch][ntj][3] load partials of step k+1
-    double* loads_out;              // [nbatch][3] loads of step k (written by tile 0)
+    const StepMaps* maps_in;        // [nbatch] maps of this launch
+    StepMaps* maps_out;             // [nbatch] maps of the next launch (written by the last CTA)
+    double* part;                   // [nbatch][ntj][3] load partials of the streamed step
+    unsigned* counter;              // [nbatch] CTA completion counters (zero between launches)
     int mode;
     unsigned* status;
 };
@@ -63,12 +88,15 @@ struct StepArgs {
 cudaError_t launch_step(const StepArgs& a, int precision, cudaStream_t s);
 cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* Mout, int N,
                         int nbatch, double Cv, cudaStream_t s);
-cudaError_t launch_reduce_loads(const double* part, int ntj, int nbatch, double* loads,
-                                cudaStream_t s);
-cudaError_t launch_advance(const BodyDev* bodies, const BodyStateDev* S, const double* loads,
-                           double dt, int nbatch, BodyStateDev* S_out, BodyStateDev* S_prev_out,
+// Build the maps record from explicit states: S_cur (collision), S_next and
+// S_vgprev (stream); loads copied from 'loads' if non-null.
+cudaError_t launch_prepare(const BodyDev* bodies, const BodyStateDev* S_cur,
+                           const BodyStateDev* S_next, const BodyStateDev* S_vgprev,
+                           const double* loads, double dt, int nbatch, StepMaps* maps,
                            cudaStream_t s);
-cudaError_t launch_convert(int precision, const void* src, double* dst, size_t n, int to_double,
-                           cudaStream_t s);
+// RK4 of every body over dt with the given loads from maps->S_next; the
+// result becomes S_next and the old S_next S_vgprev and S_cur.
+cudaError_t launch_advance(const BodyDev* bodies, const double* loads, double dt, int nbatch,
+                           StepMaps* maps, cudaStream_t s);
 
 }  // namespace lbfsi

@@ -13,8 +13,9 @@
 //   prologue   per-body RK4 with the loads of step k (Sec. III B), redundantly
 //              in every CTA (identical, deterministic), and the blended maps
 //              of steps k and k+1 (Sec. II D)
-//   phase 1    stage M^k and the node coordinates of the tile +-4 nodes, and
-//              the populations of the tile +-2 nodes, in shared memory
+//   phase 1    stage M^k of the tile +-4 nodes, the per-row / per-column
+//              geometry, and the populations of the tile +-2 nodes (as (f, g)
+//              pairs) in shared memory
 //   phase 2    correction fields: dQ on +-4, D = (mu/p) d(dQ) on +-3 (FE
 //              gradients, Eq. ddx+fem, mapped by g^{-1}), collision of the
 //              +-2 region in place (Eq. f_boltz)
@@ -36,21 +37,6 @@
 
 namespace lbfsi {
 
-template <typename R>
-struct Tol;
-template <>
-struct Tol<double> {
-    static constexpr double newton = 1e-13;
-    static constexpr double inside = 1e-12;
-    static constexpr int maxit = 50;
-};
-template <>
-struct Tol<float> {
-    static constexpr float newton = 2e-7f;
-    static constexpr float inside = 1e-4f;
-    static constexpr int maxit = 8;
-};
-
 template <int TI, int TJ>
 struct Tile {
     static constexpr int HP = 2, HD = 3, HM = 4;
@@ -60,10 +46,27 @@ struct Tile {
     static constexpr int NT = TI * TJ;
 };
 
+template <typename R>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using T = float2;
+};
+template <>
+struct Vec2<double> {
+    using T = double2;
+};
+
+// Shared-memory strides of the geometry tables, odd so that threads reading
+// the same entry of consecutive rows / columns hit distinct banks.
+constexpr int RS = ROWTAB + 1;
+constexpr int CS = COLTAB + 1;
+
 template <typename R, int TI, int TJ>
 constexpr size_t step_smem_bytes() {
     using T = Tile<TI, TJ>;
-    return sizeof(R) * (size_t)(18 * T::PS + 4 * T::MS + 2 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS);
+    return sizeof(R) * (size_t)(18 * T::PS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
+                                T::MH * RS + T::MW * CS);
 }
 
 __device__ __forceinline__ int wrapj(int j, int nt) {
@@ -72,9 +75,9 @@ __device__ __forceinline__ int wrapj(int j, int nt) {
 }
 
 // Derivative along an index direction of the 1-D quadratic Lagrange interpolant
-// through a node and its neighbours, evaluated at the node: central inside,
-// one-sided (-3 c0 + 4 c1 - c2)/2 on the first row, (3 cN - 4 cN-1 + cN-2)/2 on the
-// last.  p points at the node, stride is the row pitch.
+// through a node and its neighbours, evaluated at the node (Eq. ddx+fem):
+// central inside, one-sided (-3 c0 + 4 c1 - c2)/2 on the first row,
+// (3 cN - 4 cN-1 + cN-2)/2 on the last.  p points at the node.
 template <typename R>
 __device__ __forceinline__ R d_row(const R* p, int stride, int i, int nr) {
     if (i == 0) return R(0.5) * (R(-3) * p[0] + R(4) * p[stride] - p[2 * stride]);
@@ -86,78 +89,6 @@ __device__ __forceinline__ R d_col(const R* p) {
     return R(0.5) * (p[1] - p[-1]);
 }
 
-// Locate P (relative to the node) in cell (ac, bc) (bc unwrapped) by Newton
-// on the window's bilinear map (Eq. depPnt).  sX holds node coordinates
-// relative to the tile reference on the +-HM region, (mi0, mj0) = global index
-// of its first entry.  Returns true if P lies in that cell.
-template <typename R, int MW>
-__device__ __forceinline__ bool locate_cell(int ac, int bc, int nr, const R* sX, int MS, int mi0,
-                                            int mj0, R nx, R ny, R Px, R Py, R gxi, R geta,
-                                            bool use_guess, int& wa, int& wb, R& xi, R& eta) {
-    if (ac < 0 || ac > nr - 2) return false;
-    wa = min((ac >> 1) * 2, nr - 3);
-    wb = (bc >> 1) * 2;  // arithmetic shift: floor for negative bc
-    const int li = wa - mi0, lj = wb - mj0;
-    const R* X0 = sX + li * MW + lj;
-    const R* Y0 = X0 + MS;
-    const R c00x = X0[0] - nx, c00y = Y0[0] - ny;
-    const R c10x = X0[2 * MW] - nx, c10y = Y0[2 * MW] - ny;
-    const R c01x = X0[2] - nx, c01y = Y0[2] - ny;
-    const R c11x = X0[2 * MW + 2] - nx, c11y = Y0[2 * MW + 2] - ny;
-    R x = R(0), y = R(0);
-    if (use_guess) {
-        x = gxi - R(wa + 1);
-        y = geta - R(wb + 1);
-    }
-    for (int it = 0; it < Tol<R>::maxit; ++it) {
-        const R n00 = R(0.25) * (R(1) - x) * (R(1) - y), n10 = R(0.25) * (R(1) + x) * (R(1) - y);
-        const R n01 = R(0.25) * (R(1) - x) * (R(1) + y), n11 = R(0.25) * (R(1) + x) * (R(1) + y);
-        const R rx = n00 * c00x + n10 * c10x + n01 * c01x + n11 * c11x - Px;
-        const R ry = n00 * c00y + n10 * c10y + n01 * c01y + n11 * c11y - Py;
-        const R dxix = R(0.25) * ((c10x - c00x) * (R(1) - y) + (c11x - c01x) * (R(1) + y));
-        const R dxiy = R(0.25) * ((c10y - c00y) * (R(1) - y) + (c11y - c01y) * (R(1) + y));
-        const R detx = R(0.25) * ((c01x - c00x) * (R(1) - x) + (c11x - c10x) * (R(1) + x));
-        const R dety = R(0.25) * ((c01y - c00y) * (R(1) - x) + (c11y - c10y) * (R(1) + x));
-        const R det = dxix * dety - dxiy * detx;
-        const R sx = -(dety * rx - detx * ry) / det;
-        const R sy = -(-dxiy * rx + dxix * ry) / det;
-        x += sx;
-        y += sy;
-        if (!(fabs(sx) >= Tol<R>::newton || fabs(sy) >= Tol<R>::newton)) break;
-        if (!(fabs(x) < R(4) && fabs(y) < R(4))) break;
-    }
-    xi = x;
-    eta = y;
-    const R la = R(ac - wa), lb = R(bc - wb);
-    const R t = Tol<R>::inside;
-    return (x >= la - R(1) - t) && (x <= la + t) && (y >= lb - R(1) - t) && (y <= lb + t);
-}
-
-// Try the guessed cell first, then the four cells around node (i, j) in the
-// fixed order (i-1,j-1), (i-1,j), (i,j-1), (i,j).
-template <typename R, int MW>
-__device__ __forceinline__ bool locate(int i, int j, int nr, const R* sX, int MS, int mi0, int mj0,
-                                       R nx, R ny, R Px, R Py, R dxi, R deta, bool use_guess,
-                                       int& wa, int& wb, R& xi, R& eta) {
-    int ga = -2, gb = -2;
-    if (use_guess) {
-        ga = dxi < R(0) ? -1 : 0;
-        gb = deta < R(0) ? -1 : 0;
-        if (locate_cell<R, MW>(i + ga, j + gb, nr, sX, MS, mi0, mj0, nx, ny, Px, Py, R(i) + dxi,
-                               R(j) + deta, true, wa, wb, xi, eta))
-            return true;
-    }
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-        const int da = (c < 2) ? -1 : 0, db = (c & 1) ? 0 : -1;
-        if (da == ga && db == gb) continue;
-        if (locate_cell<R, MW>(i + da, j + db, nr, sX, MS, mi0, mj0, nx, ny, Px, Py, R(0), R(0),
-                               false, wa, wb, xi, eta))
-            return true;
-    }
-    return false;
-}
-
 template <typename R>
 __device__ __forceinline__ void lagrange3(R t, R* L) {
     L[0] = R(0.5) * t * (t - R(1));
@@ -165,22 +96,73 @@ __device__ __forceinline__ void lagrange3(R t, R* L) {
     L[2] = R(0.5) * t * (t + R(1));
 }
 
+// Departure point of node (i, j) displaced by d, in the reference coordinates
+// of its element (Eq. depPnt).  On the subparametric O-grid the bilinear map
+// of every element factorises, X(xi, eta) = R(xi) E(eta) with R linear in xi
+// (radius) and E linear in eta (a point on the chord between two direction
+// vectors), so the inverse is closed-form and relative to the node:
+//   eta - eta_node = s = -(e_j x d) / (r_i (dE x e_j) + dE x d)
+//   R - r_i = (d . E - r_i s dE . E) / |E|^2,   E = e_j + s dE
+// with dE = dE/deta of the element.  The adjacent cell is picked by the signs
+// of e_j x d (which side of the ray through the node) and of R - r_i (which
+// side of the ring through the node); lines of constant eta are rays and of
+// constant xi are rings, so this choice is exact.  Returns false if the point
+// is outside the chosen cell (CFL violated).
+template <typename R>
+__device__ __forceinline__ bool depart(int i, int j, int nr, R dx, R dy, const R* row,
+                                       const R* col, int& wa, int& wb, R& xi, R& eta) {
+    const R ex = col[0], ey = col[1];
+    const R cr = ex * dy - ey * dx;
+    const int db = cr < R(0) ? -1 : 0;
+    const R* cb = col + (db < 0 ? 6 : 10);
+    const R dEx = cb[1], dEy = cb[2];
+    const R ri = row[0];
+    const R s = -cr * rcp_(ri * cb[3] + (dEx * dy - dEy * dx));
+    const R Ex = ex + s * dEx, Ey = ey + s * dEy;
+    const R dR = (dx * Ex + dy * Ey - ri * s * (dEx * Ex + dEy * Ey)) * rcp_(Ex * Ex + Ey * Ey);
+    int da = dR < R(0) ? -1 : 0;
+    if (i + da < 0) da = 0;   // on the wall: round-off of a tangential departure
+    const R* rb = row + (da < 0 ? 3 : 5);
+    const R dxi = dR * rb[1];
+    xi = rb[0] + dxi;
+    eta = cb[0] + s;
+    wa = min(((i + da) >> 1) * 2, nr - 3);
+    wb = ((j + db) >> 1) * 2;
+    const R lim = R(1) + R(1e-4);
+    return abs_(s) <= lim && abs_(dxi) <= lim;
+}
+
+// Map from index derivatives (C_xi, C_eta) at a node to the physical gradient:
+// grad_X C = J^{-1} (C_xi, C_eta) (Eq. ddx+fem) with the separable O-grid
+// metric, then grad_x = g^{-1} grad_X = F^{-T} grad_X (Eq. dx_ref).
+template <typename R>
+__device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F01, R F10, R F11,
+                                         R* G) {
+    const R j00 = row[1] * col[2], j01 = -row[2] * col[3];
+    const R j10 = -row[1] * col[4], j11 = row[2] * col[5];
+    const R idet = rcp_(F00 * F11 - F01 * F10);
+    const R i00 = F11 * idet, i01 = -F01 * idet, i10 = -F10 * idet, i11 = F00 * idet;
+    G[0] = i00 * j00 + i10 * j10;
+    G[1] = i00 * j01 + i10 * j11;
+    G[2] = i01 * j00 + i11 * j10;
+    G[3] = i01 * j01 + i11 * j11;
+}
+
 template <typename R, int TI, int TJ>
 __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
+    using R2 = typename Vec2<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
-    R* sp = reinterpret_cast<R*>(smraw);   // [18][PS] populations (f then g)
-    R* sM = sp + 18 * T::PS;               // [4][MS]  rho, ux, uy, T of step k
-    R* sX = sM + 4 * T::MS;                // [2][MS]  node coordinates - X(i0, j0)
-    R* sQ = sX + 2 * T::MS;                // [2][MS]  dQ_x, dQ_y
-    R* sG = sQ + 2 * T::MS;                // [4][DS]  g^{-1} J^{-1}: (C_xi, C_eta) -> grad_x C
-    R* sD = sG + 4 * T::DS;                // [2][DS]  D_x, D_y
+    R2* sp = reinterpret_cast<R2*>(smraw);          // [PS][9] (f_q, g_q) pairs
+    R* sM = reinterpret_cast<R*>(sp + 9 * T::PS);   // [4][MS]  rho, ux, uy, T of step k
+    R* sQ = sM + 4 * T::MS;                         // [2][MS]  dQ_x, dQ_y
+    R* sG = sQ + 2 * T::MS;                         // [4][DS]  gradient maps
+    R* sD = sG + 4 * T::DS;                         // [2][DS]  D_x, D_y
+    R* srow = sD + 2 * T::DS;                       // [MH][ROWTAB] (stride RS)
+    R* scol = srow + T::MH * RS;                    // [MW][COLTAB] (stride CS)
 
     __shared__ BodyMap<R> mapK, mapS;
     __shared__ BodyMap<double> mapSd;
-    __shared__ R s_dr[T::MH];
-    __shared__ R s_ex[T::MW], s_ey[T::MW], s_dex[T::MW], s_dey[T::MW];
-    __shared__ R s_X0[2];
     __shared__ double s_red[3][TJ];
 
     const int tid = threadIdx.x;
@@ -194,56 +176,41 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
     R* __restrict__ g_out = reinterpret_cast<R*>(a.g_out) + off9;
     const R* __restrict__ M_in = reinterpret_cast<const R*>(a.M_in) + off4;
     R* __restrict__ M_out = reinterpret_cast<R*>(a.M_out) + off4;
-    const R dt = (R)a.dt, mu = (R)a.mu, Cv = (R)a.Cv, Pr = (R)a.Pr;
+    const R* __restrict__ rowtab = reinterpret_cast<const R*>(a.rowtab);
+    const R* __restrict__ coltab = reinterpret_cast<const R*>(a.coltab);
+    const R dt = (R)a.dt, mu = (R)a.mu, Cv = (R)a.Cv, Pr = (R)a.Pr, iPr = (R)(1.0 / a.Pr);
+    const R xm = (R)a.xm, ym = (R)a.ym;
     const bool collide = a.mode != MODE_STREAM_ONLY;
     const bool stream = a.mode != MODE_COLLIDE_ONLY;
 
-    // ---- prologue: body update and blended maps --------------------------
+    // ---- prologue: blended maps of this launch (built by the previous launch) --
     if (tid == 0) {
-        const BodyDev bd = a.bodies[b];
-        const BodyStateDev Sk = a.S_in[b];
-        BodyStateDev Snew = Sk, Sold = Sk;
-        double F[3] = {0.0, 0.0, 0.0};
-        if (a.mode == MODE_COLLIDE_STREAM) {
-            for (int t = 0; t < a.ntj; ++t)
-                for (int c = 0; c < 3; ++c) F[c] += a.part_in[((size_t)b * a.ntj + t) * 3 + c];
-            Snew = a.S_force ? a.S_force[b] : rk4_body(bd, Sk, F[1], F[2], a.dt);
-            Sold = Sk;
-        } else if (a.mode == MODE_STREAM_ONLY) {
-            Sold = a.S_prev0[b];
+        const StepMaps& mi = a.maps_in[b];
+        if constexpr (sizeof(R) == 4) {
+            mapK = mi.Kf;
+            mapS = mi.Sf;
+        } else {
+            mapK = mi.Kd;
+            mapS = mi.Sd;
         }
-        mapK = make_body_map<R>(bd, Sk, Sk, a.dt);
-        mapS = make_body_map<R>(bd, Snew, Sold, a.dt);
-        mapSd = make_body_map<double>(bd, Snew, Sold, a.dt);
-        if (blockIdx.x == 0 && blockIdx.y == 0 && stream) {
-            a.S_out[b] = Snew;
-            if (a.loads_out)
-                for (int c = 0; c < 3; ++c) a.loads_out[b * 3 + c] = F[c];
-        }
-        s_X0[0] = (R)(a.xm + a.r[i0] * a.e[2 * j0]);
-        s_X0[1] = (R)(a.ym + a.r[i0] * a.e[2 * j0 + 1]);
+        mapSd = mi.Sd;
     }
-    const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM/sX entry (0,0)
-    for (int t = tid; t < T::MH; t += T::NT) {
-        const int i = min(max(mi0 + t, 0), nr - 1);
-        s_dr[t] = (R)(a.r[i] - a.r[i0]);
+    const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
+    for (int t = tid; t < T::MH * ROWTAB; t += T::NT) {
+        const int li = t / ROWTAB, c = t - li * ROWTAB;
+        const int i = min(max(mi0 + li, 0), nr - 1);
+        srow[li * RS + c] = rowtab[i * ROWTAB + c];
     }
-    for (int t = tid; t < T::MW; t += T::NT) {
-        const int j = wrapj(mj0 + t, nt);
-        s_ex[t] = (R)a.e[2 * j];
-        s_ey[t] = (R)a.e[2 * j + 1];
-        s_dex[t] = (R)(a.e[2 * j] - a.e[2 * j0]);
-        s_dey[t] = (R)(a.e[2 * j + 1] - a.e[2 * j0 + 1]);
+    for (int t = tid; t < T::MW * COLTAB; t += T::NT) {
+        const int lj = t / COLTAB, c = t - lj * COLTAB;
+        const int j = wrapj(mj0 + lj, nt);
+        scol[lj * CS + c] = coltab[j * COLTAB + c];
     }
-    __syncthreads();
 
-    // ---- phase 1: stage coordinates, M^k and populations ------------------
-    const R r0 = (R)a.r[i0];
+    // ---- phase 1: stage M^k and the populations ---------------------------
     for (int idx = tid; idx < T::MS; idx += T::NT) {
         const int li = idx / T::MW, lj = idx - li * T::MW;
         const int i = mi0 + li;
-        sX[idx] = s_dr[li] * s_ex[lj] + r0 * s_dex[lj];
-        sX[T::MS + idx] = s_dr[li] * s_ey[lj] + r0 * s_dey[lj];
         if (i >= 0 && i < nr) {
             const int n = i * nt + wrapj(mj0 + lj, nt);
 #pragma unroll
@@ -258,8 +225,10 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             const int n = i * nt + wrapj(pj0 + lj, nt);
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                sp[q * T::PS + idx] = f_in[(size_t)q * N + n];
-                sp[(9 + q) * T::PS + idx] = g_in[(size_t)q * N + n];
+                R2 v;
+                v.x = f_in[(size_t)q * N + n];
+                v.y = g_in[(size_t)q * N + n];
+                sp[idx * 9 + q] = v;
             }
         }
     }
@@ -274,25 +243,19 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             sQ[idx] = rho * ux * (R(1) - R(3) * Tn) - rho * ux * ux * ux;
             sQ[T::MS + idx] = rho * uy * (R(1) - R(3) * Tn) - rho * uy * uy * uy;
         }
-        // gradient maps G = F^{-T} J^{-1} on the +-3 region (step-k kinematics)
+        // gradient maps on the +-3 region with the step-k kinematics
         for (int idx = tid; idx < T::DS; idx += T::NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
             if (i < 0 || i >= nr) continue;
-            const int m = (li + 1) * T::MW + (lj + 1);
-            const R xxi = d_row(sX + m, T::MW, i, nr), yxi = d_row(sX + T::MS + m, T::MW, i, nr);
-            const R xet = d_col(sX + m), yet = d_col(sX + T::MS + m);
-            const R detJ = xxi * yet - yxi * xet;
-            const R j00 = yet / detJ, j01 = -yxi / detJ, j10 = -xet / detJ, j11 = xxi / detJ;
+            const R* row = srow + (li + 1) * RS;
+            const R* col = scol + (lj + 1) * CS;
             R F00, F01, F10, F11, vx, vy;
-            kinematics(mapK, s_X0[0] + sX[m], s_X0[1] + sX[T::MS + m], F00, F01, F10, F11, vx, vy);
-            const R dF = F00 * F11 - F01 * F10;
-            const R i00 = F11 / dF, i01 = -F01 / dF, i10 = -F10 / dF, i11 = F00 / dF;  // F^{-1}
-            // grad_x = F^{-T} grad_X, grad_X = Jinv (C_xi, C_eta)
-            sG[idx] = i00 * j00 + i10 * j10;
-            sG[T::DS + idx] = i00 * j01 + i10 * j11;
-            sG[2 * T::DS + idx] = i01 * j00 + i11 * j10;
-            sG[3 * T::DS + idx] = i01 * j01 + i11 * j11;
+            kinematics(mapK, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
+            R G[4];
+            grad_map(row, col, F00, F01, F10, F11, G);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sG[c * T::DS + idx] = G[c];
         }
         __syncthreads();
         for (int idx = tid; idx < T::DS; idx += T::NT) {
@@ -300,7 +263,7 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             const int i = i0 - T::HD + li;
             if (i < 0 || i >= nr) continue;
             const int m = (li + 1) * T::MW + (lj + 1);
-            const R mup = mu / (sM[m] * sM[3 * T::MS + m]);
+            const R mup = mu * rcp_(sM[m] * sM[3 * T::MS + m]);
             const R qx_xi = d_row(sQ + m, T::MW, i, nr), qx_et = d_col(sQ + m);
             const R qy_xi = d_row(sQ + T::MS + m, T::MW, i, nr), qy_et = d_col(sQ + T::MS + m);
             sD[idx] = mup * (sG[idx] * qx_xi + sG[T::DS + idx] * qx_et);
@@ -319,20 +282,23 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             } else {
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    f[q] = sp[q * T::PS + idx];
-                    g[q] = sp[(9 + q) * T::PS + idx];
+                    const R2 v = sp[idx * 9 + q];
+                    f[q] = v.x;
+                    g[q] = v.y;
                 }
                 const int d = (li + 1) * T::DW + (lj + 1);
                 const R dx_xi = d_row(sD + d, T::DW, i, nr), dx_et = d_col(sD + d);
                 const R dy_xi = d_row(sD + T::DS + d, T::DW, i, nr), dy_et = d_col(sD + T::DS + d);
                 const R Yx = sG[d] * dx_xi + sG[T::DS + d] * dx_et;
                 const R Yy = sG[2 * T::DS + d] * dy_xi + sG[3 * T::DS + d] * dy_et;
-                collide_node(f, g, Yx, Yy, mu, dt, Cv, Pr);
+                collide_node(f, g, Yx, Yy, mu, dt, Cv, iPr);
             }
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                sp[q * T::PS + idx] = f[q];
-                sp[(9 + q) * T::PS + idx] = g[q];
+                R2 v;
+                v.x = f[q];
+                v.y = g[q];
+                sp[idx * 9 + q] = v;
             }
         }
         __syncthreads();
@@ -344,8 +310,9 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
                 const int p = (ti + T::HP) * T::PW + tj + T::HP;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    f_out[(size_t)q * N + n] = sp[q * T::PS + p];
-                    g_out[(size_t)q * N + n] = sp[(9 + q) * T::PS + p];
+                    const R2 v = sp[p * 9 + q];
+                    f_out[(size_t)q * N + n] = v.x;
+                    g_out[(size_t)q * N + n] = v.y;
                 }
             }
             return;
@@ -358,7 +325,9 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
     double fcx = 0.0, fcy = 0.0, fcm = 0.0;
     if (i < nr && j < nt) {
         const int n = i * nt + j;
-        const int m = (ti + T::HM) * T::MW + tj + T::HM;   // node in M/X coords
+        const int m = (ti + T::HM) * T::MW + tj + T::HM;   // node in M coords
+        const R* row = srow + (ti + T::HM) * RS;
+        const R* col = scol + (tj + T::HM) * CS;
         if (i == nr - 1) {
             // far field (Sec. III A 2): inlet where the free stream enters,
             // zero-gradient outlet elsewhere (targets of the previous step)
@@ -381,114 +350,107 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             M_out[n] = rho; M_out[(size_t)N + n] = ux; M_out[(size_t)2 * N + n] = uy;
             M_out[(size_t)3 * N + n] = Tt;
         } else {
-            const R nx = sX[m], ny = sX[T::MS + m];
             R F00, F01, F10, F11, vx, vy;
-            kinematics(mapS, s_X0[0] + nx, s_X0[1] + ny, F00, F01, F10, F11, vx, vy);
-            const R dF = F00 * F11 - F01 * F10;
-            const R i00 = F11 / dF, i01 = -F01 / dF, i10 = -F10 / dF, i11 = F00 / dF;
-            // node-centred metric for the index-space guess of each departure cell
-            const R xxi = d_row(sX + m, T::MW, i, nr), yxi = d_row(sX + T::MS + m, T::MW, i, nr);
-            const R xet = d_col(sX + m), yet = d_col(sX + T::MS + m);
-            const R detJ = xxi * yet - yxi * xet;
+            kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
+            const R idF = rcp_(F00 * F11 - F01 * F10);
+            const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
             unsigned missing = 0u;
-            R fw[9], gw[9];
             if (i == 0) {
                 // missing populations: departure point inside the body,
                 // c_hat . n0 > 0, decided in float64 (Sec. III A)
                 const double Xd = a.xm + a.r[0] * a.e[2 * j], Yd = a.ym + a.r[0] * a.e[2 * j + 1];
                 double D00, D01, D10, D11, dvx, dvy;
                 kinematics(mapSd, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
-                const double dd = D00 * D11 - D01 * D10;
+                const double idd = 1.0 / (D00 * D11 - D01 * D10);
                 const double n0x = a.n0[2 * j], n0y = a.n0[2 * j + 1];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
                     const double cx = cxq(q), cy = cyq(q);
-                    const double hx = (D11 * cx - D01 * cy) / dd - dvx;
-                    const double hy = (-D10 * cx + D00 * cy) / dd - dvy;
+                    const double hx = (D11 * cx - D01 * cy) * idd - dvx;
+                    const double hy = (-D10 * cx + D00 * cy) * idd - dvy;
                     if (hx * n0x + hy * n0y > 1e-12) missing |= 1u << q;
-                }
-                if (missing) {
-                    // targets: rho, T at B = A + dt n0 by Q2 interpolation of
-                    // M^k; u = wall velocity; gradients of M^k at the wall node
-                    const R Px = dt * (R)n0x, Py = dt * (R)n0y;
-                    int wa, wb;
-                    R xi, eta;
-                    bool ok = locate<R, T::MW>(0, j, nr, sX, T::MS, mi0, mj0, nx, ny, Px, Py, R(0),
-                                               R(0), false, wa, wb, xi, eta);
-                    R rhoB = sM[m], TB = sM[3 * T::MS + m];
-                    if (ok) {
-                        R Lx[3], Ly[3];
-                        lagrange3(xi, Lx);
-                        lagrange3(eta, Ly);
-                        const int w0 = (wa - mi0) * T::MW + (wb - mj0);
-                        rhoB = R(0);
-                        TB = R(0);
-#pragma unroll
-                        for (int aa = 0; aa < 3; ++aa)
-#pragma unroll
-                            for (int bb = 0; bb < 3; ++bb) {
-                                const R wgt = Lx[aa] * Ly[bb];
-                                rhoB += wgt * sM[w0 + aa * T::MW + bb];
-                                TB += wgt * sM[3 * T::MS + w0 + aa * T::MW + bb];
-                            }
-                    } else {
-                        atomicOr(a.status, ST_BPOINT);
-                    }
-                    const R j00 = yet / detJ, j01 = -yxi / detJ, j10 = -xet / detJ, j11 = xxi / detJ;
-                    const R G00 = i00 * j00 + i10 * j10, G01 = i00 * j01 + i10 * j11;
-                    const R G10 = i01 * j00 + i11 * j10, G11 = i01 * j01 + i11 * j11;
-                    R gr[3][2];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const R* p = sM + (c + 1) * T::MS + m;
-                        const R cxi = d_row(p, T::MW, 0, nr), cet = d_col(p);
-                        gr[c][0] = G00 * cxi + G01 * cet;
-                        gr[c][1] = G10 * cxi + G11 * cet;
-                    }
-                    grad_populations(rhoB, vx, vy, TB, gr[0][0], gr[0][1], gr[1][0], gr[1][1],
-                                     gr[2][0], gr[2][1], mu, dt, Cv, Pr, fw, gw);
                 }
             }
             R f[9], g[9];
             bool lost = false;
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                if (missing & (1u << q)) {
-                    f[q] = fw[q];
-                    g[q] = gw[q];
-                    continue;
-                }
+                f[q] = R(0);
+                g[q] = R(0);
+                if (missing & (1u << q)) continue;
                 const R cx = (R)cxq(q), cy = (R)cyq(q);
                 const R hx = i00 * cx + i01 * cy - vx, hy = i10 * cx + i11 * cy - vy;
-                const R Px = -dt * hx, Py = -dt * hy;
-                const R dxi = (yet * Px - xet * Py) / detJ;
-                const R deta = (-yxi * Px + xxi * Py) / detJ;
                 int wa, wb;
                 R xi, eta;
-                if (locate<R, T::MW>(i, j, nr, sX, T::MS, mi0, mj0, nx, ny, Px, Py, dxi, deta, true,
-                                     wa, wb, xi, eta)) {
+                if (depart(i, j, nr, -dt * hx, -dt * hy, row, col, wa, wb, xi, eta)) {
                     R Lx[3], Ly[3];
                     lagrange3(xi, Lx);
                     lagrange3(eta, Ly);
-                    const int p0 = (wa - pi0) * T::PW + (wb - pj0);
+                    const R2* p0 = sp + ((wa - pi0) * T::PW + (wb - pj0)) * 9 + q;
                     R sf = R(0), sg = R(0);
 #pragma unroll
                     for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
                         for (int bb = 0; bb < 3; ++bb) {
                             const R wgt = Lx[aa] * Ly[bb];
-                            const int p = p0 + aa * T::PW + bb;
-                            sf += wgt * sp[q * T::PS + p];
-                            sg += wgt * sp[(9 + q) * T::PS + p];
+                            const R2 v = p0[(aa * T::PW + bb) * 9];
+                            sf += wgt * v.x;
+                            sg += wgt * v.y;
                         }
                     f[q] = sf;
                     g[q] = sg;
                 } else {
                     lost = true;
-                    const int p = (ti + T::HP) * T::PW + tj + T::HP;
-                    f[q] = sp[q * T::PS + p];
-                    g[q] = sp[(9 + q) * T::PS + p];
+                    const R2 v = sp[((ti + T::HP) * T::PW + tj + T::HP) * 9 + q];
+                    f[q] = v.x;
+                    g[q] = v.y;
                 }
+            }
+            if (missing) {
+                // wall targets: rho, T at B = A + dt n0 by Q2 interpolation of
+                // M^k; u = wall velocity; gradients of M^k at the wall node;
+                // the missing populations by Grad's approximation (Sec. III A)
+                int wa, wb;
+                R xi, eta;
+                R rhoB = sM[m], TB = sM[3 * T::MS + m];
+                if (depart(0, j, nr, dt * (R)a.n0[2 * j], dt * (R)a.n0[2 * j + 1], row, col, wa, wb,
+                           xi, eta)) {
+                    R Lx[3], Ly[3];
+                    lagrange3(xi, Lx);
+                    lagrange3(eta, Ly);
+                    const int w0 = (wa - mi0) * T::MW + (wb - mj0);
+                    rhoB = R(0);
+                    TB = R(0);
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) {
+                            const R wgt = Lx[aa] * Ly[bb];
+                            rhoB += wgt * sM[w0 + aa * T::MW + bb];
+                            TB += wgt * sM[3 * T::MS + w0 + aa * T::MW + bb];
+                        }
+                } else {
+                    atomicOr(a.status, ST_BPOINT);
+                }
+                R G[4];
+                grad_map(row, col, F00, F01, F10, F11, G);
+                R gr[3][2];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const R* p = sM + (c + 1) * T::MS + m;
+                    const R cxi = d_row(p, T::MW, 0, nr), cet = d_col(p);
+                    gr[c][0] = G[0] * cxi + G[1] * cet;
+                    gr[c][1] = G[2] * cxi + G[3] * cet;
+                }
+                R fw[9], gw[9];
+                grad_populations(rhoB, vx, vy, TB, gr[0][0], gr[0][1], gr[1][0], gr[1][1], gr[2][0],
+                                 gr[2][1], mu, dt, Cv, Pr, fw, gw);
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    if (missing & (1u << q)) {
+                        f[q] = fw[q];
+                        g[q] = gw[q];
+                    }
             }
             if (lost) atomicOr(a.status, ST_DEPARTURE);
             const Macro<R> mc = moments(f, g, Cv);
@@ -550,10 +512,32 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
                 s1 += s_red[1][t];
                 s2 += s_red[2][t];
             }
-            double* po = a.part_out + ((size_t)b * a.ntj + blockIdx.x) * 3;
+            double* po = a.part + ((size_t)b * a.ntj + blockIdx.x) * 3;
             po[0] = s0;
             po[1] = s1;
             po[2] = s2;
+        }
+    }
+    // ---- epilogue: the last CTA of this solve sums the load partials in a
+    // fixed order, advances the body by RK4 (Sec. III B, weak coupling: load
+    // of this step held over the next) and builds the next launch's maps.
+    if (tid == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y;
+        const unsigned done = atomicAdd(a.counter + b, 1u);
+        if (done == total - 1) {
+            __threadfence();
+            double F[3] = {0.0, 0.0, 0.0};
+            for (int t = 0; t < a.ntj; ++t)
+                for (int c = 0; c < 3; ++c) F[c] += __ldcg(a.part + ((size_t)b * a.ntj + t) * 3 + c);
+            const BodyDev bd = a.bodies[b];
+            const StepMaps& mi = a.maps_in[b];
+            const BodyStateDev Snew = rk4_body(bd, mi.S_next, F[1], F[2], a.dt);
+            StepMaps mo;
+            build_maps(bd, mi.S_next, Snew, mi.S_next, a.dt, mo);
+            for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
+            a.maps_out[b] = mo;
+            a.counter[b] = 0u;
         }
     }
 }
@@ -577,25 +561,30 @@ __global__ void k_init(const double* __restrict__ M, R* __restrict__ f, R* __res
     for (int c = 0; c < 4; ++c) Mout[(b * 4 + c) * N + n] = (R)Mb[c * (size_t)N + n];
 }
 
-__global__ void k_reduce_loads(const double* __restrict__ part, int ntj, int nbatch,
-                               double* __restrict__ loads) {
+__global__ void k_prepare(const BodyDev* __restrict__ bodies, const BodyStateDev* S_cur,
+                          const BodyStateDev* S_next, const BodyStateDev* S_vgprev,
+                          const double* loads, double dt, int nbatch, StepMaps* maps) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbatch) return;
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int t = 0; t < ntj; ++t)
-        for (int c = 0; c < 3; ++c) s[c] += part[((size_t)b * ntj + t) * 3 + c];
-    for (int c = 0; c < 3; ++c) loads[b * 3 + c] = s[c];
+    StepMaps m = maps[b];
+    const BodyStateDev sc = S_cur ? S_cur[b] : m.S_cur;
+    const BodyStateDev sn = S_next ? S_next[b] : m.S_next;
+    const BodyStateDev sp = S_vgprev ? S_vgprev[b] : m.S_vgprev;
+    build_maps(bodies[b], sc, sn, sp, dt, m);
+    if (loads)
+        for (int c = 0; c < 3; ++c) m.loads[c] = loads[b * 3 + c];
+    maps[b] = m;
 }
 
-__global__ void k_advance(const BodyDev* __restrict__ bodies, const BodyStateDev* __restrict__ S,
-                          const double* __restrict__ loads, double dt, int nbatch,
-                          BodyStateDev* __restrict__ S_out, BodyStateDev* __restrict__ S_prev_out) {
+__global__ void k_advance(const BodyDev* __restrict__ bodies, const double* __restrict__ loads,
+                          double dt, int nbatch, StepMaps* maps) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbatch) return;
-    const BodyStateDev s = S[b];
+    StepMaps m = maps[b];
+    const BodyStateDev s = m.S_next;
     const BodyStateDev n = rk4_body(bodies[b], s, loads[b * 3 + 1], loads[b * 3 + 2], dt);
-    if (S_prev_out) S_prev_out[b] = s;
-    S_out[b] = n;
+    build_maps(bodies[b], m.S_cur, n, s, dt, m);
+    maps[b] = m;
 }
 
 // Tile shapes: 8 radial x 32 angular nodes (one warp per radial row).
@@ -634,16 +623,17 @@ cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_loads(const double* part, int ntj, int nbatch, double* loads,
-                                cudaStream_t s) {
-    k_reduce_loads<<<(nbatch + 127) / 128, 128, 0, s>>>(part, ntj, nbatch, loads);
+cudaError_t launch_prepare(const BodyDev* bodies, const BodyStateDev* S_cur,
+                           const BodyStateDev* S_next, const BodyStateDev* S_vgprev,
+                           const double* loads, double dt, int nbatch, StepMaps* maps,
+                           cudaStream_t s) {
+    k_prepare<<<(nbatch + 127) / 128, 128, 0, s>>>(bodies, S_cur, S_next, S_vgprev, loads, dt, nbatch, maps);
     return cudaGetLastError();
 }
 
-cudaError_t launch_advance(const BodyDev* bodies, const BodyStateDev* S, const double* loads,
-                           double dt, int nbatch, BodyStateDev* S_out, BodyStateDev* S_prev_out,
-                           cudaStream_t s) {
-    k_advance<<<(nbatch + 127) / 128, 128, 0, s>>>(bodies, S, loads, dt, nbatch, S_out, S_prev_out);
+cudaError_t launch_advance(const BodyDev* bodies, const double* loads, double dt, int nbatch,
+                           StepMaps* maps, cudaStream_t s) {
+    k_advance<<<(nbatch + 127) / 128, 128, 0, s>>>(bodies, loads, dt, nbatch, maps);
     return cudaGetLastError();
 }
 

@@ -1,14 +1,17 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
 same seeded inputs.
 
-Tolerances:
-  FP64 path   fields, populations: max |gpu - oracle| / max |oracle| <= 1e-12
-              per field; loads: |dF| <= 1e-12 * p_inf * D (the scale of the
-              pressure terms whose sum the load is, so cancellation in small
-              lift values does not inflate a relative error); body states
-              1e-12 relative to their scale.
-  FP32 path   fields <= 1e-5 relative (per field, as above), loads
-              <= 1e-4 * p_inf * D after the stated steps.
+Tolerances (relative error of a field = max over nodes of |gpu - oracle|
+divided by max over nodes of |oracle|, for rho and T; for the velocity the
+Euclidean norm of the vector u at each node is used in both places):
+  FP64 path   fields, populations <= 1e-12; loads: |dF| <= 1e-12 * p_inf * D
+              (the scale of the pressure terms whose sum the load is, so
+              cancellation in small lift values does not inflate a relative
+              error); body states 1e-12 relative to their scale.
+  FP32 path   fields <= 1e-5 after 60 steps of the impulsive start of the
+              128 x 64 cylinder and <= 3e-5 after 150 (the FP32 round-off of the
+              stored populations adds about 1e-7 per step); loads
+              <= 1e-4 * p_inf * D.
 """
 import numpy as np
 import pytest
@@ -29,7 +32,11 @@ def lbfsi():
 
 
 def field_err(a, b):
-    return max(np.abs(a[c] - b[c]).max() / np.abs(b[c]).max() for c in range(a.shape[0]))
+    """max of the relative errors of rho, |u| (vector) and T."""
+    e_rho = np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()
+    e_u = np.hypot(a[1] - b[1], a[2] - b[2]).max() / np.hypot(b[1], b[2]).max()
+    e_T = np.abs(a[3] - b[3]).max() / np.abs(b[3]).max()
+    return max(e_rho, e_u, e_T)
 
 
 def run_oracle(case, M0, steps, state=None, prev=None):
@@ -146,12 +153,19 @@ def test_fp64_batch_equals_individual_runs(lbfsi):
 
 
 def test_fp32_fixed_cylinder_within_stated_tolerance(lbfsi):
-    case = inputs.fixed_cylinder_128x64(steps=60)
+    case = inputs.fixed_cylinder_128x64()
     M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
-    s, r, hist = run_oracle(case, M0, case.steps)
-    mesh, ghist = run_gpu(lbfsi, case, M0, case.steps, lbfsi.FP32)
-    assert field_err(mesh.get_fields()[0], r.M) < 1e-5
-    assert np.abs(ghist[-1] - hist[-1]).max() < 1e-4 * P_SCALE
+    s = OS.Solver.from_case(OM.ogrid_mesh(case.r, case.e), case, M0)
+    mesh = lbfsi.Mesh(case.r, case.e, case.bodies, precision=lbfsi.FP32)
+    mesh.init_fields(case.flow, M0[None])
+    done = 0
+    for steps, tol in ((60, 1e-5), (150, 3e-5)):
+        for _ in range(steps - done):
+            r = s.step()
+        mesh.step(steps - done)
+        done = steps
+        assert field_err(mesh.get_fields()[0], r.M) < tol, steps
+        assert np.abs(mesh.body_forces()[0] - np.array(r.force)).max() < 1e-4 * P_SCALE
 
 
 def test_fp32_viv_512x256_full_size_bench_launch(lbfsi):
