@@ -158,6 +158,35 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g,
 /* Wait for the handle's stream; returns the first device-detected error. */
 int lbfsi_synchronize(lbfsi_mesh m);
 
+/* Loads on the body of each solve from caller-provided post-propagation
+ * populations, without allocating anything.  The paper has no counterpart:
+ * this is the load reduction of lbfsi_step (wall stress, Simpson shares,
+ * fixed-order sum) for callers that cannot call cudaMalloc -- e.g. code that
+ * runs while a framework's caching allocator or a real-time loop owns all
+ * device memory, or that must avoid the device-wide synchronisation an
+ * allocation can cause.  Its scratch (per-CTA partial sums and per-solve
+ * completion counters) is a fixed file-scope device array of about 97 KB that
+ * every GPU which loads the library keeps until the process exits.
+ *   nr, ntheta, xc, yc, r, e   the O-grid as for lbfsi_create_mesh; r [nr] and
+ *                              e [ntheta][2] are DEVICE pointers (float64)
+ *   precision                  LBFSI_FP64 or LBFSI_FP32: element type of f, g
+ *   f, g                       DEVICE [nbatch][9][nr*ntheta] post-propagation
+ *                              populations (only the wall row is read)
+ *   body_ref                   DEVICE [nbatch][3]: x_p, y_p, alpha of each
+ *                              body (reference point, pitch angle)
+ *   mu, dt, gamma              viscosity, time step, adiabatic exponent
+ *   loads                      DEVICE out [nbatch][3]: F_x, F_y, M_z
+ * Limits: nbatch <= 256 and nbatch * ceil(ntheta / 32) <= 4096, else
+ * LBFSI_EINVAL.  Asynchronous on cuda_stream.  The first call on a device
+ * looks up the scratch array's device address and clears its counters (a
+ * blocking step), so make that first call before any stream capture.  Every
+ * call shares the one scratch array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+int lbfsi_wall_loads_noalloc(int nr, int ntheta, int nbatch, int precision, const double* r,
+                             const double* e, double xc, double yc, const void* f, const void* g,
+                             const double* body_ref, double mu, double dt, double gamma,
+                             double* loads, void* cuda_stream);
+
 /* Number of kernel launches issued on the handle's stream so far. */
 int64_t lbfsi_launch_count(lbfsi_mesh m);
 

@@ -32,6 +32,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 }  // namespace
 
+int lbfsi::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 struct lbfsi_mesh_s {
     int nr = 0, nt = 0, N = 0, nbatch = 0, precision = 0, ntj = 0;
     double xm = 0, ym = 0;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace lbfsi {
 
 // Status bits written by the kernels (OR-ed into a device word).
@@ -83,6 +85,10 @@ struct StepArgs {
     int mode;
     unsigned* status;
 };
+
+// Record msg as the calling thread's last error and return code (defined in
+// lbfsi_api.cu).
+int set_error(int code, const std::string& msg);
 
 // Launchers (defined in lbfsi_step.cu).
 cudaError_t launch_step(const StepArgs& a, int precision, cudaStream_t s);

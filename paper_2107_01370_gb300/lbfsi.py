@@ -24,7 +24,8 @@ _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDEPARTURE: "EDEPA
 EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbfsi_blend_mesh",
             "lbfsi_step", "lbfsi_body_forces", "lbfsi_advance_bodies", "lbfsi_get_body_state",
             "lbfsi_get_fields", "lbfsi_get_populations", "lbfsi_set_populations",
-            "lbfsi_synchronize", "lbfsi_launch_count", "lbfsi_last_error"]
+            "lbfsi_synchronize", "lbfsi_launch_count", "lbfsi_last_error",
+            "lbfsi_wall_loads_noalloc"]
 
 
 class LbfsiError(RuntimeError):
@@ -86,6 +87,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbfsi_synchronize.argtypes = [P]
     lib.lbfsi_launch_count.argtypes = [P]
     lib.lbfsi_launch_count.restype = ctypes.c_int64
+    lib.lbfsi_wall_loads_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             P, P, ctypes.c_double, ctypes.c_double, P, P, P,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             P, P]
     lib.lbfsi_last_error.argtypes = []
     lib.lbfsi_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -102,6 +107,16 @@ def _check(rc):
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def wall_loads_noalloc(nr, ntheta, nbatch, precision, r_dev, e_dev, centre, f_dev, g_dev,
+                       body_ref_dev, mu, dt, gamma, loads_dev, stream=0):
+    """Allocation-free wall loads; every array argument is a device pointer
+    (int) owned by the caller (see include/lbfsi.h)."""
+    lib = load()
+    _check(lib.lbfsi_wall_loads_noalloc(nr, ntheta, nbatch, precision, r_dev, e_dev, centre[0],
+                                        centre[1], f_dev, g_dev, body_ref_dev, mu, dt, gamma,
+                                        loads_dev, stream))
 
 
 def body_desc(spec) -> BodyDesc:
