@@ -3,16 +3,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "lbfsi.h"
 #include "lbfsi_internal.h"
-
-namespace lbfsi {
-int tiles_j(int nt);
-}
 
 using lbfsi::BodyDev;
 using lbfsi::BodyStateDev;
@@ -62,6 +59,7 @@ struct lbfsi_mesh_s {
     unsigned* d_counter = nullptr;   // [nbatch] CTA completion counters
     unsigned* d_status = nullptr;
     int cur = 0, curM = 0;
+    int variant = 0;                 // tile shape of the float step kernel
     bool initialized = false, first = true;
     double dt = 0, mu = 0, Cv = 0, Pr = 0, rho_inf = 0, uinf = 0, T_inf = 0;
     int64_t launches = 0;
@@ -299,6 +297,14 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     m->xm = d->xc;
     m->ym = d->yc;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
+    // tile shape of the float kernel (a tuning knob, every variant computes the
+    // same result): LBFSI_STEP_VARIANT 0: 8 x 32 nodes, 2 CTAs/SM; 1: 16 x 32,
+    // 2 CTAs/SM; 2: 8 x 32, 3 CTAs/SM; 3: 12 x 32, 384 threads (default)
+    m->variant = 3;
+    if (const char* v = std::getenv("LBFSI_STEP_VARIANT")) {
+        const int k = std::atoi(v);
+        m->variant = (k >= 0 && k <= 3) ? k : 3;
+    }
     m->r.assign(d->r, d->r + d->nr);
     m->e.assign(d->e, d->e + 2 * d->ntheta);
     m->bodies.assign(d->bodies, d->bodies + d->nbatch);
@@ -497,6 +503,10 @@ static lbfsi::StepArgs make_args(lbfsi_mesh m, int mode) {
     a.rowtab = m->d_rowtab; a.coltab = m->d_coltab;
     a.dt = m->dt; a.mu = m->mu; a.Cv = m->Cv; a.Pr = m->Pr; a.rho_inf = m->rho_inf;
     a.uinf_x = m->uinf; a.uinf_y = 0.0; a.T_inf = m->T_inf;
+    a.dt_f = (float)m->dt; a.mu_f = (float)m->mu; a.Cv_f = (float)m->Cv; a.Pr_f = (float)m->Pr;
+    a.iPr_f = (float)(1.0 / m->Pr); a.xm_f = (float)m->xm; a.ym_f = (float)m->ym;
+    a.rho_inf_f = (float)m->rho_inf; a.uinf_x_f = (float)m->uinf; a.uinf_y_f = 0.0f;
+    a.T_inf_f = (float)m->T_inf;
     a.f_in = m->d_f[m->cur]; a.g_in = m->d_g[m->cur];
     a.f_out = m->d_f[m->cur ^ 1]; a.g_out = m->d_g[m->cur ^ 1];
     a.M_in = m->d_M[m->cur]; a.M_out = m->d_M[m->cur ^ 1];
@@ -516,7 +526,7 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
     for (int s = 0; s < nsteps; ++s) {
         lbfsi::StepArgs a = make_args(m, m->first ? lbfsi::MODE_STREAM_ONLY : lbfsi::MODE_COLLIDE_STREAM);
-        cudaError_t e = lbfsi::launch_step(a, m->precision, m->stream);
+        cudaError_t e = lbfsi::launch_step(a, m->precision, m->variant, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         m->cur ^= 1;
@@ -610,7 +620,7 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
         lbfsi::StepArgs a = make_args(m, lbfsi::MODE_COLLIDE_ONLY);
         a.f_out = m->d_fpost;
         a.g_out = m->d_gpost;
-        e = lbfsi::launch_step(a, m->precision, m->stream);
+        e = lbfsi::launch_step(a, m->precision, m->variant, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "collide kernel launch");
         fs = m->d_fpost;

@@ -19,12 +19,20 @@ __host__ __device__ constexpr int cyq(int q) {
     return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
 }
 
-// Reciprocal and square root in the precision of the path: one MUFU-based
-// reciprocal (two roundings in total for a quotient) on the float path,
-// IEEE division on the float64 path.
-__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+// Reciprocal and square root in the precision of the path: the hardware
+// approximations (relative error about 2^-23) on the float path, IEEE
+// operations on the float64 path.
+__device__ __forceinline__ float rcp_(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
 __device__ __forceinline__ double abs_(double x) { return fabs(x); }

@@ -67,8 +67,10 @@ struct StepArgs {
     const double* wall_geo;    // [nt][6]: per wall node two (weight*length, n_x, n_y) edge shares
     const void* rowtab;        // [nr][ROWTAB] per-row geometry (element type of the path)
     const void* coltab;        // [nt][COLTAB] per-column geometry
-    // flow
+    // flow (float64, and float copies for the float path so that no thread
+    // converts or divides in float64)
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
+    float dt_f, mu_f, Cv_f, Pr_f, iPr_f, xm_f, ym_f, rho_inf_f, uinf_x_f, uinf_y_f, T_inf_f;
     // state buffers (element type set by the template)
     const void* f_in;
     const void* g_in;
@@ -90,8 +92,10 @@ struct StepArgs {
 // lbfsi_api.cu).
 int set_error(int code, const std::string& msg);
 
-// Launchers (defined in lbfsi_step.cu).
-cudaError_t launch_step(const StepArgs& a, int precision, cudaStream_t s);
+// Launchers (defined in lbfsi_step.cu).  variant selects the tile shape of
+// the step kernel (0: 8 x 32 nodes, 1: 16 x 32 nodes with two rows per thread).
+cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStream_t s);
+int tiles_j(int nt);
 cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* Mout, int N,
                         int nbatch, double Cv, cudaStream_t s);
 // Build the maps record from explicit states: S_cur (collision), S_next and

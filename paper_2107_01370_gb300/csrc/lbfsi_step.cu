@@ -91,9 +91,9 @@ __device__ __forceinline__ R d_col(const R* p) {
 
 template <typename R>
 __device__ __forceinline__ void lagrange3(R t, R* L) {
-    L[0] = R(0.5) * t * (t - R(1));
+    L[0] = t * (R(0.5) * t - R(0.5));
     L[1] = R(1) - t * t;
-    L[2] = R(0.5) * t * (t + R(1));
+    L[2] = t * (R(0.5) * t + R(0.5));
 }
 
 // Departure point of node (i, j) displaced by d, in the reference coordinates
@@ -106,28 +106,51 @@ __device__ __forceinline__ void lagrange3(R t, R* L) {
 // with dE = dE/deta of the element.  The adjacent cell is picked by the signs
 // of e_j x d (which side of the ray through the node) and of R - r_i (which
 // side of the ring through the node); lines of constant eta are rays and of
-// constant xi are rings, so this choice is exact.  Returns false if the point
-// is outside the chosen cell (CFL violated).
+// constant xi are rings, so this choice is exact.
+//
+// NodeGeo holds the table entries of one node and, for the four candidate
+// cells (da, db) in {-1, 0}^2, the shared-memory offset of their element's
+// first node, so that the nine directions only select among them.
 template <typename R>
-__device__ __forceinline__ bool depart(int i, int j, int nr, R dx, R dy, const R* row,
-                                       const R* col, int& wa, int& wb, R& xi, R& eta) {
-    const R ex = col[0], ey = col[1];
-    const R cr = ex * dy - ey * dx;
-    const int db = cr < R(0) ? -1 : 0;
-    const R* cb = col + (db < 0 ? 6 : 10);
-    const R dEx = cb[1], dEy = cb[2];
-    const R ri = row[0];
-    const R s = -cr * rcp_(ri * cb[3] + (dEx * dy - dEy * dx));
-    const R Ex = ex + s * dEx, Ey = ey + s * dEy;
-    const R dR = (dx * Ex + dy * Ey - ri * s * (dEx * Ex + dEy * Ey)) * rcp_(Ex * Ex + Ey * Ey);
-    int da = dR < R(0) ? -1 : 0;
-    if (i + da < 0) da = 0;   // on the wall: round-off of a tangential departure
-    const R* rb = row + (da < 0 ? 3 : 5);
-    const R dxi = dR * rb[1];
-    xi = rb[0] + dxi;
-    eta = cb[0] + s;
-    wa = min(((i + da) >> 1) * 2, nr - 3);
-    wb = ((j + db) >> 1) * 2;
+struct NodeGeo {
+    R ex, ey, ri;
+    R eta0, dEx0, dEy0, cq0, eta1, dEx1, dEy1, cq1;   // angular cells j-1 (0) and j (1)
+    R xin0, idR0, xin1, idR1;                       // radial cells i-1 (0) and i (1)
+    int b00, b01, b10, b11;                         // element origins, [da][db]
+};
+
+template <typename R>
+__device__ __forceinline__ void node_geo(int i, int j, int nr, const R* row, const R* col, int pi0,
+                                         int pj0, int PW, NodeGeo<R>& G) {
+    G.ex = col[0];
+    G.ey = col[1];
+    G.ri = row[0];
+    G.eta0 = col[6]; G.dEx0 = col[7]; G.dEy0 = col[8]; G.cq0 = col[9];
+    G.eta1 = col[10]; G.dEx1 = col[11]; G.dEy1 = col[12]; G.cq1 = col[13];
+    G.xin0 = row[3]; G.idR0 = row[4]; G.xin1 = row[5]; G.idR1 = row[6];
+    const int wa0 = min((max(i - 1, 0) >> 1) * 2, nr - 3);   // the wall row has no cell i-1
+    const int wa1 = min((i >> 1) * 2, nr - 3);
+    const int wb0 = ((j - 1) >> 1) * 2, wb1 = (j >> 1) * 2;
+    G.b00 = ((wa0 - pi0) * PW + (wb0 - pj0)) * 9;
+    G.b01 = ((wa0 - pi0) * PW + (wb1 - pj0)) * 9;
+    G.b10 = ((wa1 - pi0) * PW + (wb0 - pj0)) * 9;
+    G.b11 = ((wa1 - pi0) * PW + (wb1 - pj0)) * 9;
+}
+
+template <typename R>
+__device__ __forceinline__ bool depart(const NodeGeo<R>& G, int i, R dx, R dy, int& base, R& xi,
+                                       R& eta) {
+    const R cr = G.ex * dy - G.ey * dx;
+    const bool db = !(cr < R(0));
+    const R dEx = db ? G.dEx1 : G.dEx0, dEy = db ? G.dEy1 : G.dEy0;
+    const R s = -cr * rcp_(G.ri * (db ? G.cq1 : G.cq0) + (dEx * dy - dEy * dx));
+    const R Ex = G.ex + s * dEx, Ey = G.ey + s * dEy;
+    const R dR = (dx * Ex + dy * Ey - G.ri * s * (dEx * Ex + dEy * Ey)) * rcp_(Ex * Ex + Ey * Ey);
+    const bool da = !(dR < R(0)) || i == 0;   // on the wall: round-off of a tangential departure
+    const R dxi = dR * (da ? G.idR1 : G.idR0);
+    xi = (da ? G.xin1 : G.xin0) + dxi;
+    eta = (db ? G.eta1 : G.eta0) + s;
+    base = da ? (db ? G.b11 : G.b10) : (db ? G.b01 : G.b00);
     const R lim = R(1) + R(1e-4);
     return abs_(s) <= lim && abs_(dxi) <= lim;
 }
@@ -148,10 +171,62 @@ __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F0
     G[3] = i01 * j01 + i11 * j11;
 }
 
-template <typename R, int TI, int TJ>
-__global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
+template <typename R>
+__device__ __forceinline__ R pick(double d, float f);
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) {
+    return f;
+}
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) {
+    return d;
+}
+
+// Q2 interpolation of one (f, g) pair over a 3x3 window: separable sums
+// t_a = sum_b L_b(eta) v(a, b), then sum_a L_a(xi) t_a (Eq. SemiLagrProp);
+// on the float path with packed two-wide FMAs (f and g share the weights).
+template <typename R2>
+__device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const float* Lx, const float* Ly);
+template <>
+__device__ __forceinline__ float2 gather9<float2>(const float2* p, int rowstride, const float* Lx,
+                                                  const float* Ly) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+        const float2* pr = p + aa * rowstride;
+        float2 t = __fmul2_rn(make_float2(Ly[0], Ly[0]), pr[0]);
+        t = __ffma2_rn(make_float2(Ly[1], Ly[1]), pr[9], t);
+        t = __ffma2_rn(make_float2(Ly[2], Ly[2]), pr[18], t);
+        acc = __ffma2_rn(make_float2(Lx[aa], Lx[aa]), t, acc);
+    }
+    return acc;
+}
+template <typename R2>
+__device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const double* Lx, const double* Ly) {
+    R2 acc;
+    acc.x = 0.0;
+    acc.y = 0.0;
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+        const R2* pr = p + aa * rowstride;
+        double tx = 0.0, ty = 0.0;
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            tx += Ly[bb] * pr[9 * bb].x;
+            ty += Ly[bb] * pr[9 * bb].y;
+        }
+        acc.x += Lx[aa] * tx;
+        acc.y += Lx[aa] * ty;
+    }
+    return acc;
+}
+
+template <typename R, int TI, int TJ, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
     using R2 = typename Vec2<R>::T;
+    constexpr int NPT = TI * TJ / NT;   // tile nodes streamed per thread
+    static_assert(NPT * NT == TI * TJ && NT >= TJ, "tile / thread count");
     extern __shared__ __align__(16) unsigned char smraw[];
     R2* sp = reinterpret_cast<R2*>(smraw);          // [PS][9] (f_q, g_q) pairs
     R* sM = reinterpret_cast<R*>(sp + 9 * T::PS);   // [4][MS]  rho, ux, uy, T of step k
@@ -164,6 +239,7 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
     __shared__ BodyMap<R> mapK, mapS;
     __shared__ BodyMap<double> mapSd;
     __shared__ double s_red[3][TJ];
+    __shared__ int s_jw[T::MW];                     // wrapped angular index of each M column
 
     const int tid = threadIdx.x;
     const int b = blockIdx.z;
@@ -178,8 +254,9 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
     R* __restrict__ M_out = reinterpret_cast<R*>(a.M_out) + off4;
     const R* __restrict__ rowtab = reinterpret_cast<const R*>(a.rowtab);
     const R* __restrict__ coltab = reinterpret_cast<const R*>(a.coltab);
-    const R dt = (R)a.dt, mu = (R)a.mu, Cv = (R)a.Cv, Pr = (R)a.Pr, iPr = (R)(1.0 / a.Pr);
-    const R xm = (R)a.xm, ym = (R)a.ym;
+    const R dt = pick<R>(a.dt, a.dt_f), mu = pick<R>(a.mu, a.mu_f), Cv = pick<R>(a.Cv, a.Cv_f);
+    const R Pr = pick<R>(a.Pr, a.Pr_f), iPr = pick<R>(1.0 / a.Pr, a.iPr_f);
+    const R xm = pick<R>(a.xm, a.xm_f), ym = pick<R>(a.ym, a.ym_f);
     const bool collide = a.mode != MODE_STREAM_ONLY;
     const bool stream = a.mode != MODE_COLLIDE_ONLY;
 
@@ -196,33 +273,34 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
         mapSd = mi.Sd;
     }
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
-    for (int t = tid; t < T::MH * ROWTAB; t += T::NT) {
+    for (int t = tid; t < T::MW; t += NT) s_jw[t] = wrapj(mj0 + t, nt);
+    for (int t = tid; t < T::MH * ROWTAB; t += NT) {
         const int li = t / ROWTAB, c = t - li * ROWTAB;
         const int i = min(max(mi0 + li, 0), nr - 1);
         srow[li * RS + c] = rowtab[i * ROWTAB + c];
     }
-    for (int t = tid; t < T::MW * COLTAB; t += T::NT) {
+    __syncthreads();
+    for (int t = tid; t < T::MW * COLTAB; t += NT) {
         const int lj = t / COLTAB, c = t - lj * COLTAB;
-        const int j = wrapj(mj0 + lj, nt);
-        scol[lj * CS + c] = coltab[j * COLTAB + c];
+        scol[lj * CS + c] = coltab[s_jw[lj] * COLTAB + c];
     }
 
     // ---- phase 1: stage M^k and the populations ---------------------------
-    for (int idx = tid; idx < T::MS; idx += T::NT) {
+    for (int idx = tid; idx < T::MS; idx += NT) {
         const int li = idx / T::MW, lj = idx - li * T::MW;
         const int i = mi0 + li;
         if (i >= 0 && i < nr) {
-            const int n = i * nt + wrapj(mj0 + lj, nt);
+            const int n = i * nt + s_jw[lj];
 #pragma unroll
             for (int c = 0; c < 4; ++c) sM[c * T::MS + idx] = M_in[(size_t)c * N + n];
         }
     }
     const int pi0 = i0 - T::HP, pj0 = j0 - T::HP;
-    for (int idx = tid; idx < T::PS; idx += T::NT) {
+    for (int idx = tid; idx < T::PS; idx += NT) {
         const int li = idx / T::PW, lj = idx - li * T::PW;
         const int i = pi0 + li;
         if (i >= 0 && i < nr) {
-            const int n = i * nt + wrapj(pj0 + lj, nt);
+            const int n = i * nt + s_jw[lj + (T::HM - T::HP)];
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 R2 v;
@@ -236,7 +314,7 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
 
     // ---- phase 2: correction fields and collision of step k --------------
     if (collide) {
-        for (int idx = tid; idx < T::MS; idx += T::NT) {
+        for (int idx = tid; idx < T::MS; idx += NT) {
             const int i = mi0 + idx / T::MW;
             if (i < 0 || i >= nr) continue;
             const R rho = sM[idx], ux = sM[T::MS + idx], uy = sM[2 * T::MS + idx], Tn = sM[3 * T::MS + idx];
@@ -244,7 +322,7 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             sQ[T::MS + idx] = rho * uy * (R(1) - R(3) * Tn) - rho * uy * uy * uy;
         }
         // gradient maps on the +-3 region with the step-k kinematics
-        for (int idx = tid; idx < T::DS; idx += T::NT) {
+        for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
             if (i < 0 || i >= nr) continue;
@@ -258,7 +336,7 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             for (int c = 0; c < 4; ++c) sG[c * T::DS + idx] = G[c];
         }
         __syncthreads();
-        for (int idx = tid; idx < T::DS; idx += T::NT) {
+        for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
             if (i < 0 || i >= nr) continue;
@@ -270,7 +348,7 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             sD[T::DS + idx] = mup * (sG[2 * T::DS + idx] * qy_xi + sG[3 * T::DS + idx] * qy_et);
         }
         __syncthreads();
-        for (int idx = tid; idx < T::PS; idx += T::NT) {
+        for (int idx = tid; idx < T::PS; idx += NT) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
             const int i = pi0 + li;
             if (i < 0 || i >= nr) continue;
@@ -303,16 +381,19 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
         }
         __syncthreads();
         if (!stream) {
-            const int ti = tid / TJ, tj = tid - (tid / TJ) * TJ;
-            const int i = i0 + ti, j = j0 + tj;
-            if (i < nr && j < nt) {
-                const int n = i * nt + j;
-                const int p = (ti + T::HP) * T::PW + tj + T::HP;
+            for (int k = 0; k < NPT; ++k) {
+                const int t = tid + k * NT;
+                const int ti = t / TJ, tj = t - (t / TJ) * TJ;
+                const int i = i0 + ti, j = j0 + tj;
+                if (i < nr && j < nt) {
+                    const int n = i * nt + j;
+                    const int p = (ti + T::HP) * T::PW + tj + T::HP;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const R2 v = sp[p * 9 + q];
-                    f_out[(size_t)q * N + n] = v.x;
-                    g_out[(size_t)q * N + n] = v.y;
+                    for (int q = 0; q < 9; ++q) {
+                        const R2 v = sp[p * 9 + q];
+                        f_out[(size_t)q * N + n] = v.x;
+                        g_out[(size_t)q * N + n] = v.y;
+                    }
                 }
             }
             return;
@@ -320,10 +401,13 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
     }
 
     // ---- phase 3: stream step k+1 ----------------------------------------
-    const int ti = tid / TJ, tj = tid - (tid / TJ) * TJ;
-    const int i = i0 + ti, j = j0 + tj;
-    double fcx = 0.0, fcy = 0.0, fcm = 0.0;
-    if (i < nr && j < nt) {
+    double fcx = 0.0, fcy = 0.0, fcm = 0.0;   // this thread's wall share (node row 0)
+#pragma unroll 1
+    for (int k = 0; k < NPT; ++k) {
+        const int t = tid + k * NT;
+        const int ti = t / TJ, tj = t - (t / TJ) * TJ;
+        const int i = i0 + ti, j = j0 + tj;
+        if (i >= nr || j >= nt) continue;
         const int n = i * nt + j;
         const int m = (ti + T::HM) * T::MW + tj + T::HM;   // node in M coords
         const R* row = srow + (ti + T::HM) * RS;
@@ -334,7 +418,10 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             const double un = a.uinf_x * a.e[2 * j] + a.uinf_y * a.e[2 * j + 1];
             R rho, ux, uy, Tt;
             if (un < 0.0) {
-                rho = (R)a.rho_inf; ux = (R)a.uinf_x; uy = (R)a.uinf_y; Tt = (R)a.T_inf;
+                rho = pick<R>(a.rho_inf, a.rho_inf_f);
+                ux = pick<R>(a.uinf_x, a.uinf_x_f);
+                uy = pick<R>(a.uinf_y, a.uinf_y_f);
+                Tt = pick<R>(a.T_inf, a.T_inf_f);
             } else {
                 const int mm = m - T::MW;
                 rho = sM[mm]; ux = sM[T::MS + mm]; uy = sM[2 * T::MS + mm]; Tt = sM[3 * T::MS + mm];
@@ -349,160 +436,154 @@ __global__ void __launch_bounds__(TI* TJ) k_step(const StepArgs a) {
             }
             M_out[n] = rho; M_out[(size_t)N + n] = ux; M_out[(size_t)2 * N + n] = uy;
             M_out[(size_t)3 * N + n] = Tt;
-        } else {
-            R F00, F01, F10, F11, vx, vy;
-            kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
-            const R idF = rcp_(F00 * F11 - F01 * F10);
-            const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
-            unsigned missing = 0u;
-            if (i == 0) {
-                // missing populations: departure point inside the body,
-                // c_hat . n0 > 0, decided in float64 (Sec. III A)
-                const double Xd = a.xm + a.r[0] * a.e[2 * j], Yd = a.ym + a.r[0] * a.e[2 * j + 1];
-                double D00, D01, D10, D11, dvx, dvy;
-                kinematics(mapSd, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
-                const double idd = 1.0 / (D00 * D11 - D01 * D10);
-                const double n0x = a.n0[2 * j], n0y = a.n0[2 * j + 1];
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const double cx = cxq(q), cy = cyq(q);
-                    const double hx = (D11 * cx - D01 * cy) * idd - dvx;
-                    const double hy = (-D10 * cx + D00 * cy) * idd - dvy;
-                    if (hx * n0x + hy * n0y > 1e-12) missing |= 1u << q;
-                }
-            }
-            R f[9], g[9];
-            bool lost = false;
+            continue;
+        }
+        R F00, F01, F10, F11, vx, vy;
+        kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
+        NodeGeo<R> geo;
+        node_geo(i, j, nr, row, col, pi0, pj0, T::PW, geo);
+        const R idF = rcp_(F00 * F11 - F01 * F10);
+        const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
+        unsigned missing = 0u;
+        if (i == 0) {
+            // missing populations: departure point inside the body,
+            // c_hat . n0 > 0, decided in float64 (Sec. III A)
+            const double Xd = a.xm + a.r[0] * a.e[2 * j], Yd = a.ym + a.r[0] * a.e[2 * j + 1];
+            double D00, D01, D10, D11, dvx, dvy;
+            kinematics(mapSd, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
+            const double idd = 1.0 / (D00 * D11 - D01 * D10);
+            const double n0x = a.n0[2 * j], n0y = a.n0[2 * j + 1];
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                f[q] = R(0);
-                g[q] = R(0);
-                if (missing & (1u << q)) continue;
-                const R cx = (R)cxq(q), cy = (R)cyq(q);
-                const R hx = i00 * cx + i01 * cy - vx, hy = i10 * cx + i11 * cy - vy;
-                int wa, wb;
-                R xi, eta;
-                if (depart(i, j, nr, -dt * hx, -dt * hy, row, col, wa, wb, xi, eta)) {
-                    R Lx[3], Ly[3];
-                    lagrange3(xi, Lx);
-                    lagrange3(eta, Ly);
-                    const R2* p0 = sp + ((wa - pi0) * T::PW + (wb - pj0)) * 9 + q;
-                    R sf = R(0), sg = R(0);
-#pragma unroll
-                    for (int aa = 0; aa < 3; ++aa)
-#pragma unroll
-                        for (int bb = 0; bb < 3; ++bb) {
-                            const R wgt = Lx[aa] * Ly[bb];
-                            const R2 v = p0[(aa * T::PW + bb) * 9];
-                            sf += wgt * v.x;
-                            sg += wgt * v.y;
-                        }
-                    f[q] = sf;
-                    g[q] = sg;
-                } else {
-                    lost = true;
-                    const R2 v = sp[((ti + T::HP) * T::PW + tj + T::HP) * 9 + q];
-                    f[q] = v.x;
-                    g[q] = v.y;
-                }
+                const double cx = cxq(q), cy = cyq(q);
+                const double hx = (D11 * cx - D01 * cy) * idd - dvx;
+                const double hy = (-D10 * cx + D00 * cy) * idd - dvy;
+                if (hx * n0x + hy * n0y > 1e-12) missing |= 1u << q;
             }
-            if (missing) {
-                // wall targets: rho, T at B = A + dt n0 by Q2 interpolation of
-                // M^k; u = wall velocity; gradients of M^k at the wall node;
-                // the missing populations by Grad's approximation (Sec. III A)
-                int wa, wb;
-                R xi, eta;
-                R rhoB = sM[m], TB = sM[3 * T::MS + m];
-                if (depart(0, j, nr, dt * (R)a.n0[2 * j], dt * (R)a.n0[2 * j + 1], row, col, wa, wb,
-                           xi, eta)) {
-                    R Lx[3], Ly[3];
-                    lagrange3(xi, Lx);
-                    lagrange3(eta, Ly);
-                    const int w0 = (wa - mi0) * T::MW + (wb - mj0);
-                    rhoB = R(0);
-                    TB = R(0);
+        }
+        R f[9], g[9];
+        bool lost = false;
 #pragma unroll
-                    for (int aa = 0; aa < 3; ++aa)
+        for (int q = 0; q < 9; ++q) {
+            f[q] = R(0);
+            g[q] = R(0);
+            if (missing & (1u << q)) continue;
+            const R cx = (R)cxq(q), cy = (R)cyq(q);
+            const R hx = i00 * cx + i01 * cy - vx, hy = i10 * cx + i11 * cy - vy;
+            int base;
+            R xi, eta;
+            if (depart(geo, i, -dt * hx, -dt * hy, base, xi, eta)) {
+                R Lx[3], Ly[3];
+                lagrange3(xi, Lx);
+                lagrange3(eta, Ly);
+                const R2 v = gather9(sp + base + q, 9 * T::PW, Lx, Ly);
+                f[q] = v.x;
+                g[q] = v.y;
+            } else {
+                lost = true;
+                const R2 v = sp[((ti + T::HP) * T::PW + tj + T::HP) * 9 + q];
+                f[q] = v.x;
+                g[q] = v.y;
+            }
+        }
+        if (missing) {
+            // wall targets: rho, T at B = A + dt n0 by Q2 interpolation of
+            // M^k; u = wall velocity; gradients of M^k at the wall node; the
+            // missing populations by Grad's approximation (Sec. III A)
+            int base;
+            R xi, eta;
+            R rhoB = sM[m], TB = sM[3 * T::MS + m];
+            if (depart(geo, 0, dt * (R)a.n0[2 * j], dt * (R)a.n0[2 * j + 1], base, xi, eta)) {
+                R Lx[3], Ly[3];
+                lagrange3(xi, Lx);
+                lagrange3(eta, Ly);
+                // element origin in the staged tile -> in the moment tile
+                const int pn = base / 9;
+                const int wa = pn / T::PW + pi0, wb = pn - (pn / T::PW) * T::PW + pj0;
+                const int w0 = (wa - mi0) * T::MW + (wb - mj0);
+                rhoB = R(0);
+                TB = R(0);
 #pragma unroll
-                        for (int bb = 0; bb < 3; ++bb) {
-                            const R wgt = Lx[aa] * Ly[bb];
-                            rhoB += wgt * sM[w0 + aa * T::MW + bb];
-                            TB += wgt * sM[3 * T::MS + w0 + aa * T::MW + bb];
-                        }
-                } else {
-                    atomicOr(a.status, ST_BPOINT);
-                }
-                R G[4];
-                grad_map(row, col, F00, F01, F10, F11, G);
-                R gr[3][2];
+                for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const R* p = sM + (c + 1) * T::MS + m;
-                    const R cxi = d_row(p, T::MW, 0, nr), cet = d_col(p);
-                    gr[c][0] = G[0] * cxi + G[1] * cet;
-                    gr[c][1] = G[2] * cxi + G[3] * cet;
-                }
-                R fw[9], gw[9];
-                grad_populations(rhoB, vx, vy, TB, gr[0][0], gr[0][1], gr[1][0], gr[1][1], gr[2][0],
-                                 gr[2][1], mu, dt, Cv, Pr, fw, gw);
-#pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    if (missing & (1u << q)) {
-                        f[q] = fw[q];
-                        g[q] = gw[q];
+                    for (int bb = 0; bb < 3; ++bb) {
+                        const R wgt = Lx[aa] * Ly[bb];
+                        rhoB += wgt * sM[w0 + aa * T::MW + bb];
+                        TB += wgt * sM[3 * T::MS + w0 + aa * T::MW + bb];
                     }
+            } else {
+                atomicOr(a.status, ST_BPOINT);
             }
-            if (lost) atomicOr(a.status, ST_DEPARTURE);
-            const Macro<R> mc = moments(f, g, Cv);
-            if (!(mc.rho > R(0)) || !(mc.T > R(0)) || !isfinite(mc.ux) || !isfinite(mc.uy))
-                atomicOr(a.status, ST_NONPHYS);
+            R G[4];
+            grad_map(row, col, F00, F01, F10, F11, G);
+            R gr[3][2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R* p = sM + (c + 1) * T::MS + m;
+                const R cxi = d_row(p, T::MW, 0, nr), cet = d_col(p);
+                gr[c][0] = G[0] * cxi + G[1] * cet;
+                gr[c][1] = G[2] * cxi + G[3] * cet;
+            }
+            R fw[9], gw[9];
+            grad_populations(rhoB, vx, vy, TB, gr[0][0], gr[0][1], gr[1][0], gr[1][1], gr[2][0],
+                             gr[2][1], mu, dt, Cv, Pr, fw, gw);
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                if (missing & (1u << q)) {
+                    f[q] = fw[q];
+                    g[q] = gw[q];
+                }
+        }
+        if (lost) atomicOr(a.status, ST_DEPARTURE);
+        const Macro<R> mc = moments(f, g, Cv);
+        if (!(mc.rho > R(0)) || !(mc.T > R(0)) || !isfinite(mc.ux) || !isfinite(mc.uy))
+            atomicOr(a.status, ST_NONPHYS);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            f_out[(size_t)q * N + n] = f[q];
+            g_out[(size_t)q * N + n] = g[q];
+        }
+        M_out[n] = mc.rho; M_out[(size_t)N + n] = mc.ux; M_out[(size_t)2 * N + n] = mc.uy;
+        M_out[(size_t)3 * N + n] = mc.T;
+        if (i == 0) {
+            // wall stress sigma = -p I - (1 - omega/2) P^(1), P^(1) = sum (f - f^eq) c c
+            // (Sec. III), this node's Simpson share of its edges, float64
+            R feq[9];
+            f_equilibrium(mc.rho, mc.ux, mc.uy, mc.T, feq);
+            double pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                f_out[(size_t)q * N + n] = f[q];
-                g_out[(size_t)q * N + n] = g[q];
+                const double fn = (double)f[q] - (double)feq[q];
+                pxx += cxq(q) * cxq(q) * fn;
+                pxy += cxq(q) * cyq(q) * fn;
+                pyy += cyq(q) * cyq(q) * fn;
             }
-            M_out[n] = mc.rho; M_out[(size_t)N + n] = mc.ux; M_out[(size_t)2 * N + n] = mc.uy;
-            M_out[(size_t)3 * N + n] = mc.T;
-            if (i == 0) {
-                // wall stress sigma = -p I - (1 - omega/2) P^(1), P^(1) = sum (f - f^eq) c c
-                // (Sec. III), this node's Simpson share of its edges, float64
-                R feq[9];
-                f_equilibrium(mc.rho, mc.ux, mc.uy, mc.T, feq);
-                double pxx = 0, pxy = 0, pyy = 0;
+            const double rho = mc.rho, Tn = mc.T;
+            const double om = 1.0 / (0.5 + a.mu / (rho * Tn * a.dt));
+            const double p = rho * Tn, am = 1.0 - 0.5 * om;
+            const double sxx = -p - am * pxx, sxy = -am * pxy, syy = -p - am * pyy;
+            const double R00 = 1.0 + mapSd.a00, R01 = mapSd.a01, R10 = mapSd.a10, R11 = 1.0 + mapSd.a11;
+            const BodyDev& bd = a.bodies[b];
+            const double Xd = a.xm + a.r[0] * a.e[2 * j] - bd.xp;
+            const double Yd = a.ym + a.r[0] * a.e[2 * j + 1] - bd.yp;
+            const double rx = R00 * Xd + R01 * Yd, ry = R10 * Xd + R11 * Yd;
+            const double* wg = a.wall_geo + 6 * j;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const double fn = (double)f[q] - (double)feq[q];
-                    pxx += cxq(q) * cxq(q) * fn;
-                    pxy += cxq(q) * cyq(q) * fn;
-                    pyy += cyq(q) * cyq(q) * fn;
-                }
-                const double rho = mc.rho, Tn = mc.T;
-                const double om = 1.0 / (0.5 + a.mu / (rho * Tn * a.dt));
-                const double p = rho * Tn, am = 1.0 - 0.5 * om;
-                const double sxx = -p - am * pxx, sxy = -am * pxy, syy = -p - am * pyy;
-                const double R00 = 1.0 + mapSd.a00, R01 = mapSd.a01, R10 = mapSd.a10, R11 = 1.0 + mapSd.a11;
-                const BodyDev& bd = a.bodies[b];
-                const double Xd = a.xm + a.r[0] * a.e[2 * j] - bd.xp;
-                const double Yd = a.ym + a.r[0] * a.e[2 * j + 1] - bd.yp;
-                const double rx = R00 * Xd + R01 * Yd, ry = R10 * Xd + R11 * Yd;
-                const double* wg = a.wall_geo + 6 * j;
-#pragma unroll
-                for (int e2 = 0; e2 < 2; ++e2) {
-                    const double wds = wg[3 * e2], ex = wg[3 * e2 + 1], ey = wg[3 * e2 + 2];
-                    const double nxr = R00 * ex + R01 * ey, nyr = R10 * ex + R11 * ey;
-                    const double tx = sxx * nxr + sxy * nyr, ty = sxy * nxr + syy * nyr;
-                    fcx += wds * tx;
-                    fcy += wds * ty;
-                    fcm += wds * (rx * ty - ry * tx);
-                }
+            for (int e2 = 0; e2 < 2; ++e2) {
+                const double wds = wg[3 * e2], ex = wg[3 * e2 + 1], ey = wg[3 * e2 + 2];
+                const double nxr = R00 * ex + R01 * ey, nyr = R10 * ex + R11 * ey;
+                const double tx = sxx * nxr + sxy * nyr, ty = sxy * nxr + syy * nyr;
+                fcx += wds * tx;
+                fcy += wds * ty;
+                fcm += wds * (rx * ty - ry * tx);
             }
         }
     }
     if (blockIdx.y == 0) {
-        if (ti == 0) {
-            s_red[0][tj] = fcx;
-            s_red[1][tj] = fcy;
-            s_red[2][tj] = fcm;
+        if (tid < TJ) {
+            s_red[0][tid] = fcx;
+            s_red[1][tid] = fcy;
+            s_red[2][tid] = fcm;
         }
         __syncthreads();
         if (tid == 0) {
@@ -587,26 +668,32 @@ __global__ void k_advance(const BodyDev* __restrict__ bodies, const double* __re
     maps[b] = m;
 }
 
-// Tile shapes: 8 radial x 32 angular nodes (one warp per radial row).
-constexpr int TI = 8, TJ = 32;
+// Tile shapes of the step kernel (angular tile width one warp).
+constexpr int TJ = 32;
 
-template <typename R>
+template <typename R, int TI, int NT, int MINB>
 static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s) {
     const size_t smem = step_smem_bytes<R, TI, TJ>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ>,
+        cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ, NT, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((a.nt + TJ - 1) / TJ, (a.nr + TI - 1) / TI, a.nbatch);
-    k_step<R, TI, TJ><<<grid, TI * TJ, smem, s>>>(a);
+    k_step<R, TI, TJ, NT, MINB><<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepArgs& a, int precision, cudaStream_t s) {
-    return precision == 0 ? launch_step_t<double>(a, s) : launch_step_t<float>(a, s);
+cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStream_t s) {
+    if (precision == 0) return launch_step_t<double, 8, 256, 1>(a, s);
+    switch (variant) {
+        case 1: return launch_step_t<float, 16, 256, 2>(a, s);
+        case 2: return launch_step_t<float, 8, 256, 3>(a, s);
+        case 3: return launch_step_t<float, 12, 384, 2>(a, s);
+        default: return launch_step_t<float, 8, 256, 2>(a, s);
+    }
 }
 
 int tiles_j(int nt) { return (nt + TJ - 1) / TJ; }
