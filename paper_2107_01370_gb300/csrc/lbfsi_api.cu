@@ -1,18 +1,22 @@
-// C-ABI of the library (declared in include/lbfsi.h): handle, device memory,
-// host-side mesh geometry and the launch sequence of the coupled step.
+// C-ABI of the library (declared in include/lbfsi.h): the mesh handle (one
+// O-grid, nbatch independent solves advanced together), its device memory and
+// the launch sequence of the coupled step.
 #include <algorithm>
 #include <cmath>
-#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "lbfsi.h"
+#include "lbfsi_host.h"
 #include "lbfsi_internal.h"
 
 using lbfsi::BodyDev;
 using lbfsi::BodyStateDev;
+using lbfsi::SolveDev;
+using lbfsi::StepMaps;
+using lbfsi::TileDev;
 
 namespace {
 
@@ -32,37 +36,40 @@ int cuda_fail(cudaError_t e, const char* where) {
 int lbfsi::set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 struct lbfsi_mesh_s {
-    int nr = 0, nt = 0, N = 0, nbatch = 0, precision = 0, ntj = 0;
-    double xm = 0, ym = 0;
-    cudaStream_t stream = nullptr;
+    lbfsi::HostMesh host;
+    lbfsi::DeviceMesh dmesh;
+    lbfsi::CudaMallocMemory mem;
+    int nbatch = 0, precision = 0, variant = 3, tile_rows = 12, tiles_per_solve = 0;
     size_t esize = 8;
-    std::vector<double> r, e, n0, wall_geo;
+    cudaStream_t stream = nullptr;
     std::vector<lbfsi_body_desc> bodies;
-    double* d_r = nullptr;
-    double* d_e = nullptr;
-    double* d_n0 = nullptr;
-    double* d_wall_geo = nullptr;
-    void* d_rowtab = nullptr;
-    void* d_coltab = nullptr;
-    BodyDev* d_bodies = nullptr;
     void* d_f[2] = {nullptr, nullptr};
     void* d_g[2] = {nullptr, nullptr};
     void* d_M[2] = {nullptr, nullptr};
     void* d_fpost = nullptr;
     void* d_gpost = nullptr;
     double* d_stage = nullptr;  // [nbatch][4][N] float64 staging
-    lbfsi::StepMaps* d_maps[2] = {nullptr, nullptr};  // maps of the next launch (cur) / scratch
-    BodyStateDev* d_state_a = nullptr;                // host-given states staging
+    StepMaps* d_maps[2] = {nullptr, nullptr};  // [nbatch] each
+    BodyStateDev* d_state_a = nullptr;          // host-given states staging
     BodyStateDev* d_state_b = nullptr;
     double* d_loads_tmp = nullptr;
     double* d_part = nullptr;        // [nbatch][ntj][3] load partials
     unsigned* d_counter = nullptr;   // [nbatch] CTA completion counters
+    BodyDev* d_bodies = nullptr;     // [nbatch]
+    lbfsi::MeshDev* d_meshdev = nullptr;
+    SolveDev* d_solves = nullptr;    // [nbatch]
+    TileDev* d_tiles = nullptr;      // [nbatch * tiles_per_solve]
+    unsigned* d_launch = nullptr;    // [0] launch number, [1] grid completion counter
     unsigned* d_status = nullptr;
-    int cur = 0, curM = 0;
-    int variant = 0;                 // tile shape of the float step kernel
-    bool initialized = false, first = true;
-    double dt = 0, mu = 0, Cv = 0, Pr = 0, rho_inf = 0, uinf = 0, T_inf = 0;
+    std::vector<SolveDev> solves;
+    unsigned host_L = 0;             // step launches issued (mirror of d_launch[0])
+    unsigned admit = 0;              // launch number of the first step of every solve
+    bool initialized = false;
+    double dt = 0;
     int64_t launches = 0;
+
+    int cur() const { return (int)((host_L - admit) & 1u); }
+    bool first() const { return host_L == admit; }
 };
 
 namespace {
@@ -120,152 +127,76 @@ int upload(lbfsi_mesh m, const double* host, void* ddst, size_t n) {
     return LBFSI_OK;
 }
 
-// Wall polygon of the O-grid (Sec. III): the wall edges are the straight
-// element edges between even-indexed wall nodes.  For every wall node: the unit
-// normal n0 out of the body (odd node: its edge's normal; even node: the
-// normalised sum of its two edges' normals) and its Simpson share of the
-// adjacent edges (weight*length and edge normal, up to two edges).
-void wall_geometry(lbfsi_mesh m) {
-    const int nt = m->nt, ne = nt / 2;
-    std::vector<double> X(2 * nt);
-    for (int j = 0; j < nt; ++j) {
-        X[2 * j] = m->xm + m->r[0] * m->e[2 * j];
-        X[2 * j + 1] = m->ym + m->r[0] * m->e[2 * j + 1];
-    }
-    std::vector<double> en(2 * ne), ds(ne);
-    for (int k = 0; k < ne; ++k) {
-        const int a = 2 * k, c = (2 * k + 2) % nt;
-        const double tx = X[2 * c] - X[2 * a], ty = X[2 * c + 1] - X[2 * a + 1];
-        const double L = std::sqrt(tx * tx + ty * ty);
-        ds[k] = L;
-        en[2 * k] = ty / L;
-        en[2 * k + 1] = -tx / L;
-    }
-    m->n0.assign(2 * nt, 0.0);
-    m->wall_geo.assign(6 * nt, 0.0);
-    for (int j = 0; j < nt; ++j) {
-        double* g = &m->wall_geo[6 * j];
-        if (j % 2) {
-            const int k = j / 2;
-            m->n0[2 * j] = en[2 * k];
-            m->n0[2 * j + 1] = en[2 * k + 1];
-            g[0] = 4.0 / 6.0 * ds[k];
-            g[1] = en[2 * k];
-            g[2] = en[2 * k + 1];
-        } else {
-            const int k2 = j / 2, k1 = (j / 2 - 1 + ne) % ne;
-            const double vx = en[2 * k1] + en[2 * k2], vy = en[2 * k1 + 1] + en[2 * k2 + 1];
-            const double L = std::sqrt(vx * vx + vy * vy);
-            m->n0[2 * j] = vx / L;
-            m->n0[2 * j + 1] = vy / L;
-            g[0] = ds[k2] / 6.0;
-            g[1] = en[2 * k2];
-            g[2] = en[2 * k2 + 1];
-            g[3] = ds[k1] / 6.0;
-            g[4] = en[2 * k1];
-            g[5] = en[2 * k1 + 1];
-        }
-    }
-}
-
-// Per-row and per-column geometry of the O-grid X = centre + r_i e_j used by
-// the step kernel (float64 here, stored in the element type of the path):
-//   row i: [0] r_i, [1] 1/r'_i and [2] 1/r_i (r'_i the derivative along the
-//          radial index of the quadratic through the node and its neighbours,
-//          one-sided on the first and last rows, Eq. ddx+fem), then for the two
-//          candidate radial cells a = i-1, a = i: [3|5] the node's xi in the
-//          cell's element, [4|6] 1 / (dR/dxi) of that element.
-//   col j: [0,1] e_j, [2..5] the angular factors of the inverse metric
-//          (de_y, e_y, de_x, e_x) / (e x de) with de = (e_{j+1} - e_{j-1})/2, then
-//          for the two candidate angular cells b = j-1, b = j: [6|10] the node's
-//          eta in the element, [7,8|11,12] dE/deta of the element,
-//          [9|13] (dE/deta) x e_j.
-void geometry_tables(lbfsi_mesh m, std::vector<double>& row, std::vector<double>& col) {
-    const int nr = m->nr, nt = m->nt;
-    const double* r = m->r.data();
-    const double* e = m->e.data();
-    row.assign((size_t)nr * lbfsi::ROWTAB, 0.0);
-    for (int i = 0; i < nr; ++i) {
-        double drc;
-        if (i == 0)
-            drc = 0.5 * (-3.0 * r[0] + 4.0 * r[1] - r[2]);
-        else if (i == nr - 1)
-            drc = 0.5 * (3.0 * r[nr - 1] - 4.0 * r[nr - 2] + r[nr - 3]);
-        else
-            drc = 0.5 * (r[i + 1] - r[i - 1]);
-        double* t = &row[(size_t)i * lbfsi::ROWTAB];
-        t[0] = r[i];
-        t[1] = 1.0 / drc;
-        t[2] = 1.0 / r[i];
-        for (int c = 0; c < 2; ++c) {
-            const int a = i - 1 + c;
-            if (a < 0 || a > nr - 2) continue;
-            const int wa = std::min(2 * (a / 2), nr - 3);
-            t[3 + 2 * c] = (double)(i - wa - 1);
-            t[4 + 2 * c] = 2.0 / (r[wa + 2] - r[wa]);
-        }
-    }
-    col.assign((size_t)nt * lbfsi::COLTAB, 0.0);
-    auto wr = [nt](int j) { return ((j % nt) + nt) % nt; };
-    for (int j = 0; j < nt; ++j) {
-        const double ex = e[2 * j], ey = e[2 * j + 1];
-        const int jp = wr(j + 1), jm = wr(j - 1);
-        const double dex = 0.5 * (e[2 * jp] - e[2 * jm]), dey = 0.5 * (e[2 * jp + 1] - e[2 * jm + 1]);
-        const double cr = ex * dey - ey * dex;
-        double* t = &col[(size_t)j * lbfsi::COLTAB];
-        t[0] = ex;
-        t[1] = ey;
-        t[2] = dey / cr;
-        t[3] = ey / cr;
-        t[4] = dex / cr;
-        t[5] = ex / cr;
-        for (int c = 0; c < 2; ++c) {
-            const int b = j - 1 + c;
-            const int wb = (b >= 0) ? 2 * (b / 2) : -2 * ((-b + 1) / 2);
-            const int w0 = wr(wb), w2 = wr(wb + 2);
-            const double dEx = 0.5 * (e[2 * w2] - e[2 * w0]), dEy = 0.5 * (e[2 * w2 + 1] - e[2 * w0 + 1]);
-            t[6 + 4 * c] = (double)(j - wb - 1);
-            t[7 + 4 * c] = dEx;
-            t[8 + 4 * c] = dEy;
-            t[9 + 4 * c] = dEx * ey - dEy * ex;
-        }
-    }
-}
-
-// Dimensional ODE coefficients from the paper's nondimensional groups
-// (Sec. IV A for the transverse model, Sec. IV D for pitch-plunge).
-BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
-    BodyDev b{};
-    b.dof = d.dof;
-    b.xc = d.xc; b.yc = d.yc; b.xp = d.xp; b.yp = d.yp;
-    b.r_in = d.r_in; b.r_out = d.r_out;
-    const double pi = 3.14159265358979323846;
-    if (d.dof == LBFSI_BODY_TRANSVERSE) {
-        const double D = d.length;
-        b.m = d.m_star * rho * pi * D * D / 4.0;
-        const double wn = 2.0 * pi * U / (d.v_r * D);
-        b.k = b.m * wn * wn;
-        b.c = 2.0 * d.zeta * b.m * wn;
-    } else if (d.dof == LBFSI_BODY_PITCH_PLUNGE) {
-        const double bh = 0.5 * d.length;
-        b.m = d.m_star * pi * rho * bh * bh;
-        const double wa = U / (d.v_r * bh * std::sqrt(d.m_star));
-        const double wh = d.wh_wa * wa;
-        b.s_a = d.x_alpha * b.m * bh;
-        b.i_a = d.r_alpha * d.r_alpha * b.m * bh * bh;
-        b.k_h = b.m * wh * wh;
-        b.k_a = b.i_a * wa * wa;
-    }
-    return b;
-}
-
 void free_all(lbfsi_mesh m) {
-    void* ptrs[] = {m->d_r, m->d_e, m->d_n0, m->d_wall_geo, m->d_rowtab, m->d_coltab, m->d_bodies,
-                    m->d_f[0], m->d_f[1], m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost,
+    void* ptrs[] = {m->d_f[0], m->d_f[1], m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost,
                     m->d_gpost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
-                    m->d_loads_tmp, m->d_part, m->d_counter, m->d_status};
+                    m->d_loads_tmp, m->d_part, m->d_counter, m->d_bodies, m->d_meshdev, m->d_solves,
+                    m->d_tiles, m->d_launch, m->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    lbfsi::release_mesh(m->dmesh, m->mem);
+}
+
+// Per-solve descriptors of the handle: solve b's buffers are slices of the
+// batch-contiguous arrays.
+int upload_solves(lbfsi_mesh m) {
+    const size_t N = (size_t)m->host.N, es = m->esize;
+    for (int b = 0; b < m->nbatch; ++b) {
+        SolveDev& s = m->solves[b];
+        s.mesh = 0;
+        s.admit = m->admit;
+        s.ntiles = m->tiles_per_solve;
+        for (int p = 0; p < 2; ++p) {
+            s.f[p] = (char*)m->d_f[p] + (size_t)b * 9 * N * es;
+            s.g[p] = (char*)m->d_g[p] + (size_t)b * 9 * N * es;
+            s.M[p] = (char*)m->d_M[p] + (size_t)b * 4 * N * es;
+            s.maps[p] = m->d_maps[p] + b;
+        }
+        s.fpost = m->d_fpost ? (char*)m->d_fpost + (size_t)b * 9 * N * es : nullptr;
+        s.gpost = m->d_gpost ? (char*)m->d_gpost + (size_t)b * 9 * N * es : nullptr;
+        s.part = m->d_part + (size_t)b * m->host.ntj * 3;
+        s.counter = m->d_counter + b;
+        s.body = m->d_bodies + b;
+    }
+    std::vector<TileDev> tiles;
+    tiles.reserve((size_t)m->nbatch * m->tiles_per_solve);
+    const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows, ntj = m->host.ntj;
+    for (int b = 0; b < m->nbatch; ++b)
+        for (int ti = 0; ti < nti; ++ti)
+            for (int tj = 0; tj < ntj; ++tj) {
+                TileDev t{};
+                t.solve = b;
+                t.mesh = 0;
+                t.i0 = ti * m->tile_rows;
+                t.j0 = tj * lbfsi::TILE_J;
+                t.tj = tj;
+                t.admit = m->admit;
+                t.maps[0] = m->d_maps[0] + b;
+                t.maps[1] = m->d_maps[1] + b;
+                tiles.push_back(t);
+            }
+    cudaError_t e = cudaMemcpyAsync(m->d_solves, m->solves.data(), m->solves.size() * sizeof(SolveDev),
+                                    cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "solve descriptors upload");
+    return LBFSI_OK;
+}
+
+lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
+    lbfsi::StepArgs a{};
+    a.umesh = m->dmesh.dev;
+    a.usol = m->solves[0];
+    a.meshes = m->d_meshdev;
+    a.solves = m->d_solves;
+    a.tiles = m->d_tiles;
+    a.ntiles = m->nbatch * m->tiles_per_solve;
+    a.collide_only = collide_only;
+    a.launch_no = m->d_launch;
+    a.grid_done = m->d_launch + 1;
+    a.status = m->d_status;
+    return a;
 }
 
 }  // namespace
@@ -278,24 +209,23 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     g_last_error.clear();
     if (!d || !out) return fail(LBFSI_EINVAL, "null argument");
     *out = nullptr;
-    if (d->nr < 5) return fail(LBFSI_EINVAL, "nr must be >= 5");
-    if (d->ntheta < 4 || d->ntheta % 2) return fail(LBFSI_EINVAL, "ntheta must be even and >= 4");
     if (d->precision != LBFSI_FP64 && d->precision != LBFSI_FP32)
         return fail(LBFSI_EINVAL, "precision must be LBFSI_FP64 or LBFSI_FP32");
     if (d->nbatch < 1) return fail(LBFSI_EINVAL, "nbatch must be >= 1");
-    if (!d->r || !d->e || !d->bodies) return fail(LBFSI_EINVAL, "null table or body pointer");
+    if (!d->bodies) return fail(LBFSI_EINVAL, "null body pointer");
     const long long Nll = (long long)d->nr * d->ntheta;
-    if (Nll * 9 * d->nbatch > (1ll << 31)) return fail(LBFSI_EINVAL, "mesh too large for 32-bit node indexing");
+    if (d->nr > 0 && d->ntheta > 0 && Nll * 9 * d->nbatch > (1ll << 31))
+        return fail(LBFSI_EINVAL, "mesh too large for 32-bit node indexing");
     auto m = new lbfsi_mesh_s();
-    m->nr = d->nr;
-    m->nt = d->ntheta;
-    m->N = (int)Nll;
+    int rc = lbfsi::build_host_mesh(d->nr, d->ntheta, d->r, d->e, d->xc, d->yc, m->host);
+    if (!rc) rc = lbfsi::validate_bodies(m->host, d->bodies, d->nbatch);
+    if (rc) {
+        delete m;
+        return rc;
+    }
     m->nbatch = d->nbatch;
     m->precision = d->precision;
     m->esize = d->precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
-    m->ntj = lbfsi::tiles_j(m->nt);
-    m->xm = d->xc;
-    m->ym = d->yc;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     // tile shape of the float kernel (a tuning knob, every variant computes the
     // same result): LBFSI_STEP_VARIANT 0: 8 x 32 nodes, 2 CTAs/SM; 1: 16 x 32,
@@ -305,72 +235,34 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
         const int k = std::atoi(v);
         m->variant = (k >= 0 && k <= 3) ? k : 3;
     }
-    m->r.assign(d->r, d->r + d->nr);
-    m->e.assign(d->e, d->e + 2 * d->ntheta);
+    m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
+    const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows;
+    m->tiles_per_solve = nti * m->host.ntj;
     m->bodies.assign(d->bodies, d->bodies + d->nbatch);
-    for (int i = 1; i < m->nr; ++i)
-        if (!(m->r[i] > m->r[i - 1])) {
-            delete m;
-            return fail(LBFSI_EINVAL, "radial table must increase");
-        }
-    // subparametric tables: odd entries are the averages of their even
-    // neighbours (and, for even nr, the clamped last window is uniform), so
-    // every window is the bilinear image of the reference square
-    auto near = [](double a, double b, double scale) { return std::fabs(a - b) <= 1e-12 * scale; };
-    bool sub = true;
-    for (int i = 1; i + 1 < m->nr; i += 2)
-        sub = sub && near(m->r[i], 0.5 * (m->r[i - 1] + m->r[i + 1]), std::fabs(m->r[i + 1]));
-    if (m->nr % 2 == 0)
-        sub = sub && near(m->r[m->nr - 2], 0.5 * (m->r[m->nr - 3] + m->r[m->nr - 1]), std::fabs(m->r[m->nr - 1]));
-    for (int j = 1; j < m->nt; j += 2)
-        for (int c = 0; c < 2; ++c)
-            sub = sub && near(m->e[2 * j + c], 0.5 * (m->e[2 * (j - 1) + c] + m->e[2 * ((j + 1) % m->nt) + c]), 1.0);
-    if (!sub) {
+    m->solves.assign(m->nbatch, SolveDev{});
+    rc = lbfsi::upload_mesh(m->host, m->precision, m->mem, m->stream, m->dmesh);
+    if (rc) {
         delete m;
-        return fail(LBFSI_EINVAL, "r and e tables must be subparametric (odd entries = mean of even neighbours)");
+        return rc;
     }
-    for (const auto& b : m->bodies) {
-        if (b.dof < 0 || b.dof > 2) {
-            delete m;
-            return fail(LBFSI_EINVAL, "body dof must be 0, 1 or 2");
-        }
-        if (b.dof != 0) {
-            if (!(b.r_out > b.r_in) || !(b.length > 0) || !(b.m_star > 0) || !(b.v_r > 0)) {
-                delete m;
-                return fail(LBFSI_EINVAL, "moving body needs r_out > r_in, length, m_star, v_r > 0");
-            }
-            for (int j = 0; j < m->nt; ++j) {
-                const double x = m->xm + m->r[0] * m->e[2 * j] - b.xc;
-                const double y = m->ym + m->r[0] * m->e[2 * j + 1] - b.yc;
-                if (std::sqrt(x * x + y * y) >= b.r_in) {
-                    delete m;
-                    return fail(LBFSI_EINVAL, "the wall must lie inside the rigid zone (r_in)");
-                }
-            }
-        }
-    }
-    wall_geometry(m);
-    std::vector<double> rowt, colt;
-    geometry_tables(m, rowt, colt);
-    const size_t N = (size_t)m->N, nb = (size_t)m->nbatch;
+    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    const int ntj = m->host.ntj;
     cudaError_t e = cudaSuccess;
-#define LB_ALLOC(ptr, cnt)                                   \
+#define LB_ALLOC(ptr, cnt) \
     if (e == cudaSuccess) e = dalloc(&(ptr), (cnt));
-    LB_ALLOC(m->d_r, (size_t)m->nr);
-    LB_ALLOC(m->d_e, 2 * (size_t)m->nt);
-    LB_ALLOC(m->d_n0, 2 * (size_t)m->nt);
-    LB_ALLOC(m->d_wall_geo, 6 * (size_t)m->nt);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_rowtab, rowt.size() * m->esize);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_coltab, colt.size() * m->esize);
-    LB_ALLOC(m->d_bodies, nb);
     LB_ALLOC(m->d_stage, nb * 4 * N);
     LB_ALLOC(m->d_maps[0], nb);
     LB_ALLOC(m->d_maps[1], nb);
     LB_ALLOC(m->d_state_a, nb);
     LB_ALLOC(m->d_state_b, nb);
     LB_ALLOC(m->d_loads_tmp, nb * 3);
-    LB_ALLOC(m->d_part, nb * m->ntj * 3);
+    LB_ALLOC(m->d_part, nb * ntj * 3);
     LB_ALLOC(m->d_counter, nb);
+    LB_ALLOC(m->d_bodies, nb);
+    LB_ALLOC(m->d_meshdev, 1);
+    LB_ALLOC(m->d_solves, nb);
+    LB_ALLOC(m->d_tiles, nb * m->tiles_per_solve);
+    LB_ALLOC(m->d_launch, 2);
     LB_ALLOC(m->d_status, 1);
 #undef LB_ALLOC
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -384,24 +276,11 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
         cudaGetLastError();
         return fail(LBFSI_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
-    e = cudaMemcpy(m->d_r, m->r.data(), m->nr * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_e, m->e.data(), 2 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_n0, m->n0.data(), 2 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(m->d_wall_geo, m->wall_geo.data(), 6 * m->nt * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(m->d_meshdev, &m->dmesh.dev, sizeof(lbfsi::MeshDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(m->d_counter, 0, nb * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(m->d_part, 0, nb * m->ntj * 3 * sizeof(double));
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        const std::vector<double>& src = k ? colt : rowt;
-        void* dst = k ? m->d_coltab : m->d_rowtab;
-        if (m->precision == LBFSI_FP64) {
-            e = cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice);
-        } else {
-            std::vector<float> tf(src.begin(), src.end());
-            e = cudaMemcpy(dst, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
-        }
-    }
+    if (e == cudaSuccess) e = cudaMemset(m->d_launch, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(m->d_part, 0, nb * ntj * 3 * sizeof(double));
     if (e != cudaSuccess) {
         free_all(m);
         delete m;
@@ -421,30 +300,24 @@ int lbfsi_destroy_mesh(lbfsi_mesh m) {
 
 int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rho_u_T) {
     if (!m || !p) return fail(LBFSI_EINVAL, "null argument");
-    if (!(p->gamma > 1.0) || !(p->t_inf > 0) || !(p->rho_inf > 0) || !(p->dt > 0) || !(p->re > 0) ||
-        !(p->pr > 0) || !(p->length > 0) || p->ma < 0)
-        return fail(LBFSI_EINVAL, "invalid flow parameters");
+    SolveDev proto{};
+    int rc = lbfsi::fill_flow(*p, proto);
+    if (rc) return rc;
+    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    for (auto& s : m->solves) s = proto;
     m->dt = p->dt;
-    m->Cv = 1.0 / (p->gamma - 1.0);
-    m->Pr = p->pr;
-    m->rho_inf = p->rho_inf;
-    m->T_inf = p->t_inf;
-    m->uinf = p->ma * std::sqrt(p->gamma * p->t_inf);
-    m->mu = p->rho_inf * m->uinf * p->length / p->re;
-    if (!(m->mu > 0)) return fail(LBFSI_EINVAL, "viscosity must be positive (Ma > 0)");
-    const size_t N = (size_t)m->N, nb = (size_t)m->nbatch;
     std::vector<BodyDev> bd(nb);
-    for (size_t b = 0; b < nb; ++b) bd[b] = body_dev(m->bodies[b], m->rho_inf, m->uinf);
+    for (size_t b = 0; b < nb; ++b) bd[b] = lbfsi::body_dev(m->bodies[b], proto.rho_inf, proto.uinf_x);
     std::vector<double> M(nb * 4 * N);
     if (rho_u_T) {
         std::memcpy(M.data(), rho_u_T, M.size() * sizeof(double));
     } else {
         for (size_t b = 0; b < nb; ++b)
             for (size_t n = 0; n < N; ++n) {
-                M[(b * 4 + 0) * N + n] = m->rho_inf;
-                M[(b * 4 + 1) * N + n] = m->uinf;
+                M[(b * 4 + 0) * N + n] = proto.rho_inf;
+                M[(b * 4 + 1) * N + n] = proto.uinf_x;
                 M[(b * 4 + 2) * N + n] = 0.0;
-                M[(b * 4 + 3) * N + n] = m->T_inf;
+                M[(b * 4 + 3) * N + n] = proto.T_inf;
             }
     }
     std::vector<BodyStateDev> zero(nb, BodyStateDev{0.0, 0.0, 0.0, 0.0});
@@ -458,20 +331,23 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
         e = cudaMemcpyAsync(m->d_loads_tmp, zl.data(), zl.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, nb * sizeof(unsigned), m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_launch, 0, 2 * sizeof(unsigned), m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init_fields upload");
-    m->cur = m->curM = 0;
-    e = lbfsi::launch_prepare(m->d_bodies, m->d_state_a, m->d_state_a, m->d_state_a, m->d_loads_tmp,
-                              m->dt, m->nbatch, m->d_maps[0], m->stream);
-    m->launches++;
-    if (e != cudaSuccess) return cuda_fail(e, "prepare kernel");
-    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_f[0], m->d_g[0], m->d_M[0], m->N, m->nbatch,
-                           m->Cv, m->stream);
+    m->host_L = 0;
+    m->admit = 0;
+    rc = upload_solves(m);
+    if (rc) return rc;
+    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_f[0], m->d_g[0], m->d_M[0], m->host.N, m->nbatch,
+                           proto.Cv, m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    e = lbfsi::launch_prepare(m->d_bodies, m->d_state_a, m->d_state_a, m->d_state_a, m->d_loads_tmp, m->dt,
+                              m->nbatch, m->d_maps[0], m->stream);
+    m->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "prepare kernel");
     e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init sync");
     m->initialized = true;
-    m->first = true;
     return LBFSI_OK;
 }
 
@@ -487,51 +363,24 @@ int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_bo
     // before the first step the collision map is unused; later it stays the
     // state of the last streamed step
     if (e == cudaSuccess)
-        e = lbfsi::launch_prepare(m->d_bodies, m->first ? m->d_state_a : nullptr, m->d_state_a,
-                                  m->d_state_b, nullptr, m->dt, m->nbatch, m->d_maps[m->curM], m->stream);
+        e = lbfsi::launch_prepare(m->d_bodies, m->first() ? m->d_state_a : nullptr, m->d_state_a, m->d_state_b,
+                                  nullptr, m->dt, m->nbatch, m->d_maps[m->cur()], m->stream);
     m->launches++;
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "blend_mesh");
     return LBFSI_OK;
 }
 
-static lbfsi::StepArgs make_args(lbfsi_mesh m, int mode) {
-    lbfsi::StepArgs a{};
-    a.nr = m->nr; a.nt = m->nt; a.N = m->N; a.nbatch = m->nbatch; a.ntj = m->ntj;
-    a.xm = m->xm; a.ym = m->ym;
-    a.r = m->d_r; a.e = m->d_e; a.n0 = m->d_n0; a.wall_geo = m->d_wall_geo;
-    a.rowtab = m->d_rowtab; a.coltab = m->d_coltab;
-    a.dt = m->dt; a.mu = m->mu; a.Cv = m->Cv; a.Pr = m->Pr; a.rho_inf = m->rho_inf;
-    a.uinf_x = m->uinf; a.uinf_y = 0.0; a.T_inf = m->T_inf;
-    a.dt_f = (float)m->dt; a.mu_f = (float)m->mu; a.Cv_f = (float)m->Cv; a.Pr_f = (float)m->Pr;
-    a.iPr_f = (float)(1.0 / m->Pr); a.xm_f = (float)m->xm; a.ym_f = (float)m->ym;
-    a.rho_inf_f = (float)m->rho_inf; a.uinf_x_f = (float)m->uinf; a.uinf_y_f = 0.0f;
-    a.T_inf_f = (float)m->T_inf;
-    a.f_in = m->d_f[m->cur]; a.g_in = m->d_g[m->cur];
-    a.f_out = m->d_f[m->cur ^ 1]; a.g_out = m->d_g[m->cur ^ 1];
-    a.M_in = m->d_M[m->cur]; a.M_out = m->d_M[m->cur ^ 1];
-    a.bodies = m->d_bodies;
-    a.maps_in = m->d_maps[m->curM];
-    a.maps_out = m->d_maps[m->curM ^ 1];
-    a.part = m->d_part;
-    a.counter = m->d_counter;
-    a.mode = mode;
-    a.status = m->d_status;
-    return a;
-}
-
 int lbfsi_step(lbfsi_mesh m, int nsteps) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
+    const lbfsi::StepArgs a = make_args(m, 0);
     for (int s = 0; s < nsteps; ++s) {
-        lbfsi::StepArgs a = make_args(m, m->first ? lbfsi::MODE_STREAM_ONLY : lbfsi::MODE_COLLIDE_STREAM);
-        cudaError_t e = lbfsi::launch_step(a, m->precision, m->variant, m->stream);
+        cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        m->cur ^= 1;
-        m->curM ^= 1;
-        m->first = false;
+        m->host_L++;
     }
     return LBFSI_OK;
 }
@@ -541,9 +390,9 @@ int lbfsi_synchronize(lbfsi_mesh m) {
     return check_status(m);
 }
 
-static int download_maps(lbfsi_mesh m, std::vector<lbfsi::StepMaps>& out) {
+static int download_maps(lbfsi_mesh m, std::vector<StepMaps>& out) {
     out.resize(m->nbatch);
-    cudaError_t e = cudaMemcpyAsync(out.data(), m->d_maps[m->curM], out.size() * sizeof(lbfsi::StepMaps),
+    cudaError_t e = cudaMemcpyAsync(out.data(), m->d_maps[m->cur()], out.size() * sizeof(StepMaps),
                                     cudaMemcpyDeviceToHost, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "maps copy");
     return check_status(m);
@@ -552,7 +401,7 @@ static int download_maps(lbfsi_mesh m, std::vector<lbfsi::StepMaps>& out) {
 int lbfsi_body_forces(lbfsi_mesh m, double* out) {
     if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    std::vector<lbfsi::StepMaps> mp;
+    std::vector<StepMaps> mp;
     const int rc = download_maps(m, mp);
     if (rc) return rc;
     for (int b = 0; b < m->nbatch; ++b)
@@ -568,7 +417,7 @@ int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
     if (loads) {
         std::memcpy(ld.data(), loads, ld.size() * sizeof(double));
     } else {
-        std::vector<lbfsi::StepMaps> mp;
+        std::vector<StepMaps> mp;
         const int rc = download_maps(m, mp);
         if (rc) return rc;
         for (size_t b = 0; b < nb; ++b)
@@ -576,7 +425,7 @@ int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
     }
     cudaError_t e = cudaMemcpyAsync(m->d_loads_tmp, ld.data(), ld.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, m->nbatch, m->d_maps[m->curM], m->stream);
+        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, m->nbatch, m->d_maps[m->cur()], m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "advance_bodies");
     return check_status(m);
@@ -585,7 +434,7 @@ int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
 int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out) {
     if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    std::vector<lbfsi::StepMaps> mp;
+    std::vector<StepMaps> mp;
     const int rc = download_maps(m, mp);
     if (rc) return rc;
     for (int b = 0; b < m->nbatch; ++b) {
@@ -600,7 +449,7 @@ int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out) {
 int lbfsi_get_fields(lbfsi_mesh m, double* rho_u_T) {
     if (!m || !rho_u_T) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    int rc = download(m, m->d_M[m->cur], rho_u_T, (size_t)m->nbatch * 4 * m->N);
+    int rc = download(m, m->d_M[m->cur()], rho_u_T, (size_t)m->nbatch * 4 * m->host.N);
     if (rc) return rc;
     return check_status(m);
 }
@@ -609,18 +458,19 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
     if (!m || !f || !g) return fail(LBFSI_EINVAL, "null argument");
     if (which != 0 && which != 1) return fail(LBFSI_EINVAL, "which must be 0 or 1");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    const size_t cnt = (size_t)m->nbatch * 9 * m->N;
-    const void* fs = m->d_f[m->cur];
-    const void* gs = m->d_g[m->cur];
-    if (which == 1 && !m->first) {
+    const size_t cnt = (size_t)m->nbatch * 9 * m->host.N;
+    const void* fs = m->d_f[m->cur()];
+    const void* gs = m->d_g[m->cur()];
+    if (which == 1 && !m->first()) {
         cudaError_t e = cudaSuccess;
-        if (!m->d_fpost) e = cudaMalloc(&m->d_fpost, cnt * m->esize);
-        if (e == cudaSuccess && !m->d_gpost) e = cudaMalloc(&m->d_gpost, cnt * m->esize);
-        if (e != cudaSuccess) return fail(LBFSI_ENOMEM, "post-collision staging allocation failed");
-        lbfsi::StepArgs a = make_args(m, lbfsi::MODE_COLLIDE_ONLY);
-        a.f_out = m->d_fpost;
-        a.g_out = m->d_gpost;
-        e = lbfsi::launch_step(a, m->precision, m->variant, m->stream);
+        if (!m->d_fpost) {
+            e = cudaMalloc(&m->d_fpost, cnt * m->esize);
+            if (e == cudaSuccess) e = cudaMalloc(&m->d_gpost, cnt * m->esize);
+            if (e != cudaSuccess) return fail(LBFSI_ENOMEM, "post-collision staging allocation failed");
+            const int rc = upload_solves(m);
+            if (rc) return rc;
+        }
+        e = lbfsi::launch_step_uniform(make_args(m, 1), m->precision, m->variant, m->nbatch, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "collide kernel launch");
         fs = m->d_fpost;
@@ -636,13 +486,16 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
 int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const double* rho_u_T) {
     if (!m || !f || !g || !rho_u_T) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    const size_t cnt = (size_t)m->nbatch * 9 * m->N;
-    int rc = upload(m, f, m->d_f[m->cur], cnt);
-    if (!rc) rc = upload(m, g, m->d_g[m->cur], cnt);
-    if (!rc) rc = upload(m, rho_u_T, m->d_M[m->cur], (size_t)m->nbatch * 4 * m->N);
+    const size_t cnt = (size_t)m->nbatch * 9 * m->host.N;
+    const int c = m->cur();
+    int rc = upload(m, f, m->d_f[c], cnt);
+    if (!rc) rc = upload(m, g, m->d_g[c], cnt);
+    if (!rc) rc = upload(m, rho_u_T, m->d_M[c], (size_t)m->nbatch * 4 * m->host.N);
     if (rc) return rc;
-    m->first = false;
-    return LBFSI_OK;
+    // the restored state is post-propagation: make the next launch collide it
+    // (launch number - admit >= 2 with the same parity)
+    m->admit = m->host_L - 2u - (unsigned)c;
+    return upload_solves(m);
 }
 
 int64_t lbfsi_launch_count(lbfsi_mesh m) { return m ? m->launches : -1; }

@@ -1,0 +1,319 @@
+// Host-side helpers: mesh validation and derived geometry, body and flow
+// parameters, device allocation of a mesh's geometry.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "lbfsi_host.h"
+
+namespace lbfsi {
+
+namespace {
+
+// Wall polygon of the O-grid (Sec. III): the wall edges are the straight
+// element edges between even-indexed wall nodes.  For every wall node: the unit
+// normal n0 out of the body (odd node: its edge's normal; even node: the
+// normalised sum of its two edges' normals) and its Simpson share of the
+// adjacent edges (weight*length and edge normal, up to two edges).
+void wall_geometry(HostMesh& m) {
+    const int nt = m.nt, ne = nt / 2;
+    std::vector<double> X(2 * nt);
+    for (int j = 0; j < nt; ++j) {
+        X[2 * j] = m.xm + m.r[0] * m.e[2 * j];
+        X[2 * j + 1] = m.ym + m.r[0] * m.e[2 * j + 1];
+    }
+    std::vector<double> en(2 * ne), ds(ne);
+    for (int k = 0; k < ne; ++k) {
+        const int a = 2 * k, c = (2 * k + 2) % nt;
+        const double tx = X[2 * c] - X[2 * a], ty = X[2 * c + 1] - X[2 * a + 1];
+        const double L = std::sqrt(tx * tx + ty * ty);
+        ds[k] = L;
+        en[2 * k] = ty / L;
+        en[2 * k + 1] = -tx / L;
+    }
+    m.n0.assign(2 * nt, 0.0);
+    m.wall_geo.assign(6 * nt, 0.0);
+    for (int j = 0; j < nt; ++j) {
+        double* g = &m.wall_geo[6 * j];
+        if (j % 2) {
+            const int k = j / 2;
+            m.n0[2 * j] = en[2 * k];
+            m.n0[2 * j + 1] = en[2 * k + 1];
+            g[0] = 4.0 / 6.0 * ds[k];
+            g[1] = en[2 * k];
+            g[2] = en[2 * k + 1];
+        } else {
+            const int k2 = j / 2, k1 = (j / 2 - 1 + ne) % ne;
+            const double vx = en[2 * k1] + en[2 * k2], vy = en[2 * k1 + 1] + en[2 * k2 + 1];
+            const double L = std::sqrt(vx * vx + vy * vy);
+            m.n0[2 * j] = vx / L;
+            m.n0[2 * j + 1] = vy / L;
+            g[0] = ds[k2] / 6.0;
+            g[1] = en[2 * k2];
+            g[2] = en[2 * k2 + 1];
+            g[3] = ds[k1] / 6.0;
+            g[4] = en[2 * k1];
+            g[5] = en[2 * k1 + 1];
+        }
+    }
+}
+
+// Per-row and per-column geometry of the O-grid X = centre + r_i e_j used by
+// the step kernel:
+//   row i: [0] r_i, [1] 1/r'_i and [2] 1/r_i (r'_i the derivative along the
+//          radial index of the quadratic through the node and its neighbours,
+//          one-sided on the first and last rows, Eq. ddx+fem), then for the two
+//          candidate radial cells a = i-1, a = i: [3|5] the node's xi in the
+//          cell's element, [4|6] 1 / (dR/dxi) of that element.
+//   col j: [0,1] e_j, [2..5] the angular factors of the inverse metric
+//          (de_y, e_y, de_x, e_x) / (e x de) with de = (e_{j+1} - e_{j-1})/2, then
+//          for the two candidate angular cells b = j-1, b = j: [6|10] the node's
+//          eta in the element, [7,8|11,12] dE/deta of the element,
+//          [9|13] (dE/deta) x e_j.
+void geometry_tables(HostMesh& m) {
+    const int nr = m.nr, nt = m.nt;
+    const double* r = m.r.data();
+    const double* e = m.e.data();
+    m.rowtab.assign((size_t)nr * ROWTAB, 0.0);
+    for (int i = 0; i < nr; ++i) {
+        double drc;
+        if (i == 0)
+            drc = 0.5 * (-3.0 * r[0] + 4.0 * r[1] - r[2]);
+        else if (i == nr - 1)
+            drc = 0.5 * (3.0 * r[nr - 1] - 4.0 * r[nr - 2] + r[nr - 3]);
+        else
+            drc = 0.5 * (r[i + 1] - r[i - 1]);
+        double* t = &m.rowtab[(size_t)i * ROWTAB];
+        t[0] = r[i];
+        t[1] = 1.0 / drc;
+        t[2] = 1.0 / r[i];
+        for (int c = 0; c < 2; ++c) {
+            const int a = i - 1 + c;
+            if (a < 0 || a > nr - 2) continue;
+            const int wa = std::min(2 * (a / 2), nr - 3);
+            t[3 + 2 * c] = (double)(i - wa - 1);
+            t[4 + 2 * c] = 2.0 / (r[wa + 2] - r[wa]);
+        }
+    }
+    m.coltab.assign((size_t)nt * COLTAB, 0.0);
+    auto wr = [nt](int j) { return ((j % nt) + nt) % nt; };
+    for (int j = 0; j < nt; ++j) {
+        const double ex = e[2 * j], ey = e[2 * j + 1];
+        const int jp = wr(j + 1), jm = wr(j - 1);
+        const double dex = 0.5 * (e[2 * jp] - e[2 * jm]), dey = 0.5 * (e[2 * jp + 1] - e[2 * jm + 1]);
+        const double cr = ex * dey - ey * dex;
+        double* t = &m.coltab[(size_t)j * COLTAB];
+        t[0] = ex;
+        t[1] = ey;
+        t[2] = dey / cr;
+        t[3] = ey / cr;
+        t[4] = dex / cr;
+        t[5] = ex / cr;
+        for (int c = 0; c < 2; ++c) {
+            const int b = j - 1 + c;
+            const int wb = (b >= 0) ? 2 * (b / 2) : -2 * ((-b + 1) / 2);
+            const int w0 = wr(wb), w2 = wr(wb + 2);
+            const double dEx = 0.5 * (e[2 * w2] - e[2 * w0]), dEy = 0.5 * (e[2 * w2 + 1] - e[2 * w0 + 1]);
+            t[6 + 4 * c] = (double)(j - wb - 1);
+            t[7 + 4 * c] = dEx;
+            t[8 + 4 * c] = dEy;
+            t[9 + 4 * c] = dEx * ey - dEy * ex;
+        }
+    }
+}
+
+}  // namespace
+
+int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc, double yc,
+                    HostMesh& m) {
+    if (nr < 5) return set_error(LBFSI_EINVAL, "nr must be >= 5");
+    if (nt < 4 || nt % 2) return set_error(LBFSI_EINVAL, "ntheta must be even and >= 4");
+    if (!r || !e) return set_error(LBFSI_EINVAL, "null table pointer");
+    m.nr = nr;
+    m.nt = nt;
+    m.N = nr * nt;
+    m.ntj = tiles_j(nt);
+    m.xm = xc;
+    m.ym = yc;
+    m.r.assign(r, r + nr);
+    m.e.assign(e, e + 2 * nt);
+    for (int i = 1; i < nr; ++i)
+        if (!(m.r[i] > m.r[i - 1])) return set_error(LBFSI_EINVAL, "radial table must increase");
+    // subparametric tables: odd entries are the averages of their even
+    // neighbours (and, for even nr, the clamped last window is uniform), so
+    // every window is the bilinear image of the reference square
+    auto near = [](double a, double b, double scale) { return std::fabs(a - b) <= 1e-12 * scale; };
+    bool sub = true;
+    for (int i = 1; i + 1 < nr; i += 2)
+        sub = sub && near(m.r[i], 0.5 * (m.r[i - 1] + m.r[i + 1]), std::fabs(m.r[i + 1]));
+    if (nr % 2 == 0)
+        sub = sub && near(m.r[nr - 2], 0.5 * (m.r[nr - 3] + m.r[nr - 1]), std::fabs(m.r[nr - 1]));
+    for (int j = 1; j < nt; j += 2)
+        for (int c = 0; c < 2; ++c)
+            sub = sub && near(m.e[2 * j + c], 0.5 * (m.e[2 * (j - 1) + c] + m.e[2 * ((j + 1) % nt) + c]), 1.0);
+    if (!sub)
+        return set_error(LBFSI_EINVAL,
+                         "r and e tables must be subparametric (odd entries = mean of even neighbours)");
+    wall_geometry(m);
+    geometry_tables(m);
+    return LBFSI_OK;
+}
+
+int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
+    if (!bodies) return set_error(LBFSI_EINVAL, "null body pointer");
+    for (int k = 0; k < n; ++k) {
+        const lbfsi_body_desc& b = bodies[k];
+        if (b.dof < 0 || b.dof > 2) return set_error(LBFSI_EINVAL, "body dof must be 0, 1 or 2");
+        if (b.dof == 0) continue;
+        if (!(b.r_out > b.r_in) || !(b.length > 0) || !(b.m_star > 0) || !(b.v_r > 0))
+            return set_error(LBFSI_EINVAL, "moving body needs r_out > r_in, length, m_star, v_r > 0");
+        for (int j = 0; j < m.nt; ++j) {
+            const double x = m.xm + m.r[0] * m.e[2 * j] - b.xc;
+            const double y = m.ym + m.r[0] * m.e[2 * j + 1] - b.yc;
+            if (std::sqrt(x * x + y * y) >= b.r_in)
+                return set_error(LBFSI_EINVAL, "the wall must lie inside the rigid zone (r_in)");
+        }
+    }
+    return LBFSI_OK;
+}
+
+// Dimensional ODE coefficients from the paper's nondimensional groups
+// (Sec. IV A for the transverse model, Sec. IV D for pitch-plunge).
+BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
+    BodyDev b{};
+    b.dof = d.dof;
+    b.xc = d.xc; b.yc = d.yc; b.xp = d.xp; b.yp = d.yp;
+    b.r_in = d.r_in; b.r_out = d.r_out;
+    const double pi = 3.14159265358979323846;
+    if (d.dof == LBFSI_BODY_TRANSVERSE) {
+        const double D = d.length;
+        b.m = d.m_star * rho * pi * D * D / 4.0;
+        const double wn = 2.0 * pi * U / (d.v_r * D);
+        b.k = b.m * wn * wn;
+        b.c = 2.0 * d.zeta * b.m * wn;
+    } else if (d.dof == LBFSI_BODY_PITCH_PLUNGE) {
+        const double bh = 0.5 * d.length;
+        b.m = d.m_star * pi * rho * bh * bh;
+        const double wa = U / (d.v_r * bh * std::sqrt(d.m_star));
+        const double wh = d.wh_wa * wa;
+        b.s_a = d.x_alpha * b.m * bh;
+        b.i_a = d.r_alpha * d.r_alpha * b.m * bh * bh;
+        b.k_h = b.m * wh * wh;
+        b.k_a = b.i_a * wa * wa;
+    }
+    return b;
+}
+
+double flow_u_inf(const lbfsi_flow_params& p) { return p.ma * std::sqrt(p.gamma * p.t_inf); }
+
+int fill_flow(const lbfsi_flow_params& p, SolveDev& s) {
+    if (!(p.gamma > 1.0) || !(p.t_inf > 0) || !(p.rho_inf > 0) || !(p.dt > 0) || !(p.re > 0) ||
+        !(p.pr > 0) || !(p.length > 0) || p.ma < 0)
+        return set_error(LBFSI_EINVAL, "invalid flow parameters");
+    const double U = flow_u_inf(p);
+    const double mu = p.rho_inf * U * p.length / p.re;
+    if (!(mu > 0)) return set_error(LBFSI_EINVAL, "viscosity must be positive (Ma > 0)");
+    s.dt = p.dt;
+    s.mu = mu;
+    s.Cv = 1.0 / (p.gamma - 1.0);
+    s.Pr = p.pr;
+    s.rho_inf = p.rho_inf;
+    s.uinf_x = U;
+    s.uinf_y = 0.0;
+    s.T_inf = p.t_inf;
+    s.dt_f = (float)s.dt;
+    s.mu_f = (float)s.mu;
+    s.Cv_f = (float)s.Cv;
+    s.Pr_f = (float)s.Pr;
+    s.iPr_f = (float)(1.0 / s.Pr);
+    s.rho_inf_f = (float)s.rho_inf;
+    s.uinf_x_f = (float)s.uinf_x;
+    s.uinf_y_f = 0.0f;
+    s.T_inf_f = (float)s.T_inf;
+    return LBFSI_OK;
+}
+
+void* CudaMallocMemory::alloc(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void CudaMallocMemory::release(void* p) {
+    if (p) cudaFree(p);
+}
+
+int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s, DeviceMesh& out) {
+    const size_t es = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
+    auto put = [&](const std::vector<double>& v, bool typed, void** dst) -> int {
+        const size_t bytes = v.size() * (typed ? es : sizeof(double));
+        void* p = mem.alloc(bytes);
+        if (!p) return set_error(LBFSI_ENOMEM, "device allocation of the mesh geometry failed");
+        out.blocks.push_back(p);
+        out.bytes += bytes;
+        cudaError_t e;
+        if (typed && precision == LBFSI_FP32) {
+            std::vector<float> f(v.begin(), v.end());
+            e = cudaMemcpyAsync(p, f.data(), bytes, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        } else {
+            e = cudaMemcpyAsync(p, v.data(), bytes, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e != cudaSuccess) return set_error(LBFSI_ECUDA, std::string("mesh upload: ") + cudaGetErrorString(e));
+        *dst = p;
+        return LBFSI_OK;
+    };
+    MeshDev& d = out.dev;
+    d.nr = h.nr;
+    d.nt = h.nt;
+    d.N = h.N;
+    d.ntj = h.ntj;
+    d.xm = h.xm;
+    d.ym = h.ym;
+    d.xm_f = (float)h.xm;
+    d.ym_f = (float)h.ym;
+    void *pr, *pe, *pn, *pw, *prt, *pct;
+    int rc = put(h.r, false, &pr);
+    if (!rc) rc = put(h.e, false, &pe);
+    if (!rc) rc = put(h.n0, false, &pn);
+    if (!rc) rc = put(h.wall_geo, false, &pw);
+    if (!rc) rc = put(h.rowtab, true, &prt);
+    if (!rc) rc = put(h.coltab, true, &pct);
+    if (rc) {
+        release_mesh(out, mem);
+        return rc;
+    }
+    d.r = (const double*)pr;
+    d.e = (const double*)pe;
+    d.n0 = (const double*)pn;
+    d.wall_geo = (const double*)pw;
+    d.rowtab = prt;
+    d.coltab = pct;
+    return LBFSI_OK;
+}
+
+void release_mesh(DeviceMesh& m, DevMemory& mem) {
+    for (void* p : m.blocks) mem.release(p);
+    m.blocks.clear();
+    m.bytes = 0;
+}
+
+size_t solve_bytes(int N, int ntj, int precision) {
+    const size_t es = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
+    const size_t pops = 2 * 2 * 9 * (size_t)N * es;  // f, g ping-pong
+    const size_t mom = 2 * 4 * (size_t)N * es;
+    return pops + mom + 2 * sizeof(StepMaps) + (size_t)ntj * 3 * sizeof(double) + 256 +
+           sizeof(BodyDev) + 5 * 256;  // alignment slack
+}
+
+size_t mesh_bytes(int nr, int nt, int precision) {
+    const size_t es = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
+    return (size_t)nr * sizeof(double) + (size_t)nt * 10 * sizeof(double) +
+           ((size_t)nr * ROWTAB + (size_t)nt * COLTAB) * es + 6 * 256;
+}
+
+}  // namespace lbfsi

@@ -1,0 +1,68 @@
+// Host-side helpers shared by the mesh handle (lbfsi_api.cu) and the batch
+// runtime (lbfsi_batch.cu): mesh validation and derived geometry tables,
+// body and flow parameters, device allocation of a mesh's geometry.
+#pragma once
+
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "lbfsi.h"
+#include "lbfsi_internal.h"
+
+namespace lbfsi {
+
+// A validated O-grid shape with its derived tables (float64, host).
+struct HostMesh {
+    int nr = 0, nt = 0, N = 0, ntj = 0;
+    double xm = 0, ym = 0;
+    std::vector<double> r, e, n0, wall_geo, rowtab, coltab;
+};
+
+// Validate (sizes, increasing radii, subparametric tables) and derive the
+// wall geometry and the per-row / per-column tables.  Returns an lbfsi_status
+// and sets the thread's last error on failure.
+int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc, double yc,
+                    HostMesh& out);
+
+// Check bodies against a mesh (dof range, blend radii, wall inside the rigid zone).
+int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n);
+
+// Dimensional ODE coefficients from the nondimensional groups.
+BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U);
+
+// Validate flow parameters and fill the flow fields of a solve descriptor.
+int fill_flow(const lbfsi_flow_params& p, SolveDev& s);
+
+// Free-stream speed and viscosity of a flow.
+double flow_u_inf(const lbfsi_flow_params& p);
+
+// Simple device memory source: a plain cudaMalloc allocator, or a
+// first-fit arena carved from one cudaMalloc (the batch runtime's pool).
+struct DevMemory {
+    virtual ~DevMemory() {}
+    virtual void* alloc(size_t bytes) = 0;
+    virtual void release(void* p) = 0;
+};
+
+struct CudaMallocMemory : DevMemory {
+    void* alloc(size_t bytes) override;
+    void release(void* p) override;
+};
+
+// Device copy of a mesh's geometry (tables in the path's element type).
+struct DeviceMesh {
+    MeshDev dev{};
+    std::vector<void*> blocks;
+    size_t bytes = 0;
+};
+
+int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s, DeviceMesh& out);
+void release_mesh(DeviceMesh& m, DevMemory& mem);
+
+// Bytes of device memory one solve on an N-node mesh needs (populations,
+// moment fields, maps, partials, counter, body), and of a mesh's geometry.
+size_t solve_bytes(int N, int ntj, int precision);
+size_t mesh_bytes(int nr, int nt, int precision);
+
+}  // namespace lbfsi

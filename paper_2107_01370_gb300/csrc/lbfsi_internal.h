@@ -56,35 +56,68 @@ struct StepMaps {
 
 enum StepMode : int { MODE_STREAM_ONLY = 0, MODE_COLLIDE_STREAM = 1, MODE_COLLIDE_ONLY = 2 };
 
-// Arguments of the fused step kernel (one launch = collide step k in shared
-// memory, then stream step k+1).
-struct StepArgs {
-    int nr, nt, N, nbatch, ntj;
-    double xm, ym;             // mesh centre
-    const double* r;           // [nr]
-    const double* e;           // [nt][2]
-    const double* n0;          // [nt][2] wall normals (undeformed)
-    const double* wall_geo;    // [nt][6]: per wall node two (weight*length, n_x, n_y) edge shares
-    const void* rowtab;        // [nr][ROWTAB] per-row geometry (element type of the path)
-    const void* coltab;        // [nt][COLTAB] per-column geometry
-    // flow (float64, and float copies for the float path so that no thread
+// Geometry of one O-grid mesh shape, shared by every solve on it (device).
+struct MeshDev {
+    int nr, nt, N, ntj;
+    double xm, ym;                 // mesh centre
+    const double* r;               // [nr]
+    const double* e;               // [nt][2]
+    const double* n0;              // [nt][2] wall normals (undeformed)
+    const double* wall_geo;        // [nt][6] two (weight*length, n_x, n_y) edge shares per wall node
+    const void* rowtab;            // [nr][ROWTAB] per-row geometry (element type of the path)
+    const void* coltab;            // [nt][COLTAB] per-column geometry
+    float xm_f, ym_f;
+};
+
+// One solve (one body, one set of fields on one mesh).  Buffers are
+// ping-pong pairs; which one holds the current state follows from the launch
+// number: after (L - admit) step launches the state is in buffer
+// (L - admit) & 1, and the launch with L == admit streams from the initial
+// (post-collision) state without colliding.
+struct SolveDev {
+    int mesh;
+    unsigned admit;                // launch number of the solve's first step
+    int ntiles;                    // CTAs of this solve in every step launch
+    int tile_j0;                   // unused padding for alignment
+    // flow (float64 and float copies, so that no thread of the float path
     // converts or divides in float64)
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
-    float dt_f, mu_f, Cv_f, Pr_f, iPr_f, xm_f, ym_f, rho_inf_f, uinf_x_f, uinf_y_f, T_inf_f;
-    // state buffers (element type set by the template)
-    const void* f_in;
-    const void* g_in;
-    void* f_out;
-    void* g_out;
-    const void* M_in;
-    void* M_out;
-    // bodies
-    const BodyDev* bodies;          // [nbatch]
-    const StepMaps* maps_in;        // [nbatch] maps of this launch
-    StepMaps* maps_out;             // [nbatch] maps of the next launch (written by the last CTA)
-    double* part;                   // [nbatch][ntj][3] load partials of the streamed step
-    unsigned* counter;              // [nbatch] CTA completion counters (zero between launches)
-    int mode;
+    float dt_f, mu_f, Cv_f, Pr_f, iPr_f, rho_inf_f, uinf_x_f, uinf_y_f, T_inf_f, pad_f;
+    void* f[2];
+    void* g[2];
+    void* M[2];
+    StepMaps* maps[2];
+    void* fpost;                   // collide-only output (post-collision populations)
+    void* gpost;
+    double* part;                  // [ntj][3] load partials of the streamed step
+    unsigned* counter;             // CTA completion counter (zero between launches)
+    const BodyDev* body;
+};
+
+// One CTA of a step launch: a tile of one solve.  The entry repeats the
+// solve's mesh index, admission launch number and maps pointers so that a CTA
+// can fetch its solve, mesh and maps records in parallel after one load.
+struct TileDev {
+    int solve, mesh, i0, j0, tj;
+    unsigned admit;
+    StepMaps* maps[2];
+};
+
+// Step launch arguments.  Two forms: a uniform launch (every solve on one
+// mesh with the same flow; grid = (tiles_j, tiles_i, solves); mesh and solve 0
+// are kernel parameters and solve b's buffers are b strides further), and a
+// table launch (uneven batch; one CTA per entry of the tile table, descriptors
+// in device memory).
+struct StepArgs {
+    MeshDev umesh;                 // uniform launch: the mesh
+    SolveDev usol;                 // uniform launch: solve 0 (others by stride)
+    const MeshDev* meshes;
+    const SolveDev* solves;
+    const TileDev* tiles;
+    int ntiles;
+    int collide_only;              // 1: write the collided current state to fpost/gpost only
+    unsigned* launch_no;           // device launch counter, advanced by the grid's last CTA
+    unsigned* grid_done;           // grid completion counter (zero between launches)
     unsigned* status;
 };
 
@@ -93,9 +126,14 @@ struct StepArgs {
 int set_error(int code, const std::string& msg);
 
 // Launchers (defined in lbfsi_step.cu).  variant selects the tile shape of
-// the step kernel (0: 8 x 32 nodes, 1: 16 x 32 nodes with two rows per thread).
+// the float step kernel (see tile_rows); the float64 kernel has 8-row tiles.
 cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStream_t s);
-int tiles_j(int nt);
+// Uniform launch over nbatch solves of one mesh (see StepArgs).
+cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,
+                                cudaStream_t s);
+int tile_rows(int precision, int variant);
+constexpr int TILE_J = 32;
+inline int tiles_j(int nt) { return (nt + TILE_J - 1) / TILE_J; }
 cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* Mout, int N,
                         int nbatch, double Cv, cudaStream_t s);
 // Build the maps record from explicit states: S_cur (collision), S_next and

@@ -221,12 +221,12 @@ __device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const double* 
     return acc;
 }
 
-template <typename R, int TI, int TJ, int NT, int MINB>
+template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
     using R2 = typename Vec2<R>::T;
     constexpr int NPT = TI * TJ / NT;   // tile nodes streamed per thread
-    static_assert(NPT * NT == TI * TJ && NT >= TJ, "tile / thread count");
+    static_assert(NPT * NT == TI * TJ && NT >= TJ && NT >= 192, "tile / thread count");
     extern __shared__ __align__(16) unsigned char smraw[];
     R2* sp = reinterpret_cast<R2*>(smraw);          // [PS][9] (f_q, g_q) pairs
     R* sM = reinterpret_cast<R*>(sp + 9 * T::PS);   // [4][MS]  rho, ux, uy, T of step k
@@ -240,38 +240,81 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     __shared__ BodyMap<double> mapSd;
     __shared__ double s_red[3][TJ];
     __shared__ int s_jw[T::MW];                     // wrapped angular index of each M column
+    __shared__ TileDev s_tile;
+    __shared__ SolveDev s_sol;
+    __shared__ MeshDev s_mesh;
+    __shared__ int s_cur, s_mode;
 
     const int tid = threadIdx.x;
-    const int b = blockIdx.z;
-    const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * TI;
-    const int nr = a.nr, nt = a.nt, N = a.N;
-    const size_t off9 = (size_t)b * 9 * N, off4 = (size_t)b * 4 * N;
-    const R* __restrict__ f_in = reinterpret_cast<const R*>(a.f_in) + off9;
-    const R* __restrict__ g_in = reinterpret_cast<const R*>(a.g_in) + off9;
-    R* __restrict__ f_out = reinterpret_cast<R*>(a.f_out) + off9;
-    R* __restrict__ g_out = reinterpret_cast<R*>(a.g_out) + off9;
-    const R* __restrict__ M_in = reinterpret_cast<const R*>(a.M_in) + off4;
-    R* __restrict__ M_out = reinterpret_cast<R*>(a.M_out) + off4;
-    const R* __restrict__ rowtab = reinterpret_cast<const R*>(a.rowtab);
-    const R* __restrict__ coltab = reinterpret_cast<const R*>(a.coltab);
-    const R dt = pick<R>(a.dt, a.dt_f), mu = pick<R>(a.mu, a.mu_f), Cv = pick<R>(a.Cv, a.Cv_f);
-    const R Pr = pick<R>(a.Pr, a.Pr_f), iPr = pick<R>(1.0 / a.Pr, a.iPr_f);
-    const R xm = pick<R>(a.xm, a.xm_f), ym = pick<R>(a.ym, a.ym_f);
-    const bool collide = a.mode != MODE_STREAM_ONLY;
-    const bool stream = a.mode != MODE_COLLIDE_ONLY;
-
-    // ---- prologue: blended maps of this launch (built by the previous launch) --
-    if (tid == 0) {
-        const StepMaps& mi = a.maps_in[b];
-        if constexpr (sizeof(R) == 4) {
-            mapK = mi.Kf;
-            mapS = mi.Sf;
-        } else {
-            mapK = mi.Kd;
-            mapS = mi.Sd;
+    // ---- prologue: this CTA's tile; the solve's current buffer and mode
+    // from the launch number; the maps of this launch (built by the previous
+    // launch's epilogue); for a table launch also the solve and mesh records.
+    // Records are copied word by word by separate warps.
+    {
+        const TileDev* tg = a.tiles + blockIdx.x;
+        const unsigned admit = UNIFORM ? a.usol.admit : tg->admit;
+        const unsigned k = __ldcg(a.launch_no) - admit;
+        const int cur0 = (int)(k & 1u);
+        if (tid == 0) {
+            if (!UNIFORM) s_tile = *tg;
+            s_cur = cur0;
+            s_mode = a.collide_only ? MODE_COLLIDE_ONLY : (k == 0u ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM);
         }
-        mapSd = mi.Sd;
+        const int w = tid >> 5, l = tid & 31;
+        if (!UNIFORM && w == 1) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(a.solves + tg->solve);
+            unsigned* dst = reinterpret_cast<unsigned*>(&s_sol);
+            for (int q = l; q < (int)(sizeof(SolveDev) / 4); q += 32) dst[q] = src[q];
+        } else if (!UNIFORM && w == 2) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(a.meshes + tg->mesh);
+            unsigned* dst = reinterpret_cast<unsigned*>(&s_mesh);
+            for (int q = l; q < (int)(sizeof(MeshDev) / 4); q += 32) dst[q] = src[q];
+        } else if (w == 3 || w == 4 || w == 5) {
+            const StepMaps* mi = UNIFORM ? a.usol.maps[cur0] + blockIdx.z : tg->maps[cur0];
+            const void* srcv;
+            void* dstv;
+            int words;
+            if (w == 5) {
+                srcv = &mi->Sd;
+                dstv = &mapSd;
+                words = (int)(sizeof(BodyMap<double>) / 4);
+            } else {
+                if constexpr (sizeof(R) == 4)
+                    srcv = (w == 3) ? (const void*)&mi->Kf : (const void*)&mi->Sf;
+                else
+                    srcv = (w == 3) ? (const void*)&mi->Kd : (const void*)&mi->Sd;
+                dstv = (w == 3) ? (void*)&mapK : (void*)&mapS;
+                words = (int)(sizeof(BodyMap<R>) / 4);
+            }
+            const unsigned* src = reinterpret_cast<const unsigned*>(srcv);
+            unsigned* dst = reinterpret_cast<unsigned*>(dstv);
+            for (int q = l; q < words; q += 32) dst[q] = src[q];
+        }
     }
+    __syncthreads();
+    // solve / mesh fields: kernel parameters for a uniform launch, the copied
+    // records for a table launch
+#define SD(x) (UNIFORM ? a.usol.x : s_sol.x)
+#define MD(x) (UNIFORM ? a.umesh.x : s_mesh.x)
+    const int cur = s_cur, mode = s_mode;
+    const int sb = UNIFORM ? (int)blockIdx.z : 0;   // solve index within a uniform launch
+    const int j0 = UNIFORM ? (int)blockIdx.x * TJ : s_tile.j0;
+    const int i0 = UNIFORM ? (int)blockIdx.y * TI : s_tile.i0;
+    const int nr = MD(nr), nt = MD(nt), N = MD(N);
+    const size_t o9 = UNIFORM ? (size_t)sb * 9 * N : 0, o4 = UNIFORM ? (size_t)sb * 4 * N : 0;
+    const R* __restrict__ f_in = reinterpret_cast<const R*>(SD(f[cur])) + o9;
+    const R* __restrict__ g_in = reinterpret_cast<const R*>(SD(g[cur])) + o9;
+    R* __restrict__ f_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(fpost) : SD(f[cur ^ 1])) + o9;
+    R* __restrict__ g_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(gpost) : SD(g[cur ^ 1])) + o9;
+    const R* __restrict__ M_in = reinterpret_cast<const R*>(SD(M[cur])) + o4;
+    R* __restrict__ M_out = reinterpret_cast<R*>(SD(M[cur ^ 1])) + o4;
+    const R* __restrict__ rowtab = reinterpret_cast<const R*>(MD(rowtab));
+    const R* __restrict__ coltab = reinterpret_cast<const R*>(MD(coltab));
+    const R dt = pick<R>(SD(dt), SD(dt_f)), mu = pick<R>(SD(mu), SD(mu_f)), Cv = pick<R>(SD(Cv), SD(Cv_f));
+    const R Pr = pick<R>(SD(Pr), SD(Pr_f)), iPr = pick<R>(1.0 / SD(Pr), SD(iPr_f));
+    const R xm = pick<R>(MD(xm), MD(xm_f)), ym = pick<R>(MD(ym), MD(ym_f));
+    const bool collide = mode != MODE_STREAM_ONLY;
+    const bool stream = mode != MODE_COLLIDE_ONLY;
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
     for (int t = tid; t < T::MW; t += NT) s_jw[t] = wrapj(mj0 + t, nt);
     for (int t = tid; t < T::MH * ROWTAB; t += NT) {
@@ -415,13 +458,13 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         if (i == nr - 1) {
             // far field (Sec. III A 2): inlet where the free stream enters,
             // zero-gradient outlet elsewhere (targets of the previous step)
-            const double un = a.uinf_x * a.e[2 * j] + a.uinf_y * a.e[2 * j + 1];
+            const double un = SD(uinf_x) * MD(e)[2 * j] + SD(uinf_y) * MD(e)[2 * j + 1];
             R rho, ux, uy, Tt;
             if (un < 0.0) {
-                rho = pick<R>(a.rho_inf, a.rho_inf_f);
-                ux = pick<R>(a.uinf_x, a.uinf_x_f);
-                uy = pick<R>(a.uinf_y, a.uinf_y_f);
-                Tt = pick<R>(a.T_inf, a.T_inf_f);
+                rho = pick<R>(SD(rho_inf), SD(rho_inf_f));
+                ux = pick<R>(SD(uinf_x), SD(uinf_x_f));
+                uy = pick<R>(SD(uinf_y), SD(uinf_y_f));
+                Tt = pick<R>(SD(T_inf), SD(T_inf_f));
             } else {
                 const int mm = m - T::MW;
                 rho = sM[mm]; ux = sM[T::MS + mm]; uy = sM[2 * T::MS + mm]; Tt = sM[3 * T::MS + mm];
@@ -448,11 +491,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         if (i == 0) {
             // missing populations: departure point inside the body,
             // c_hat . n0 > 0, decided in float64 (Sec. III A)
-            const double Xd = a.xm + a.r[0] * a.e[2 * j], Yd = a.ym + a.r[0] * a.e[2 * j + 1];
+            const double Xd = MD(xm) + MD(r)[0] * MD(e)[2 * j], Yd = MD(ym) + MD(r)[0] * MD(e)[2 * j + 1];
             double D00, D01, D10, D11, dvx, dvy;
             kinematics(mapSd, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
             const double idd = 1.0 / (D00 * D11 - D01 * D10);
-            const double n0x = a.n0[2 * j], n0y = a.n0[2 * j + 1];
+            const double n0x = MD(n0)[2 * j], n0y = MD(n0)[2 * j + 1];
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 const double cx = cxq(q), cy = cyq(q);
@@ -493,7 +536,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             int base;
             R xi, eta;
             R rhoB = sM[m], TB = sM[3 * T::MS + m];
-            if (depart(geo, 0, dt * (R)a.n0[2 * j], dt * (R)a.n0[2 * j + 1], base, xi, eta)) {
+            if (depart(geo, 0, dt * (R)MD(n0)[2 * j], dt * (R)MD(n0)[2 * j + 1], base, xi, eta)) {
                 R Lx[3], Ly[3];
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
@@ -559,15 +602,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 pyy += cyq(q) * cyq(q) * fn;
             }
             const double rho = mc.rho, Tn = mc.T;
-            const double om = 1.0 / (0.5 + a.mu / (rho * Tn * a.dt));
+            const double om = 1.0 / (0.5 + SD(mu) / (rho * Tn * SD(dt)));
             const double p = rho * Tn, am = 1.0 - 0.5 * om;
             const double sxx = -p - am * pxx, sxy = -am * pxy, syy = -p - am * pyy;
             const double R00 = 1.0 + mapSd.a00, R01 = mapSd.a01, R10 = mapSd.a10, R11 = 1.0 + mapSd.a11;
-            const BodyDev& bd = a.bodies[b];
-            const double Xd = a.xm + a.r[0] * a.e[2 * j] - bd.xp;
-            const double Yd = a.ym + a.r[0] * a.e[2 * j + 1] - bd.yp;
+            const BodyDev& bd = *(SD(body) + sb);
+            const double Xd = MD(xm) + MD(r)[0] * MD(e)[2 * j] - bd.xp;
+            const double Yd = MD(ym) + MD(r)[0] * MD(e)[2 * j + 1] - bd.yp;
             const double rx = R00 * Xd + R01 * Yd, ry = R10 * Xd + R11 * Yd;
-            const double* wg = a.wall_geo + 6 * j;
+            const double* wg = MD(wall_geo) + 6 * j;
 #pragma unroll
             for (int e2 = 0; e2 < 2; ++e2) {
                 const double wds = wg[3 * e2], ex = wg[3 * e2 + 1], ey = wg[3 * e2 + 2];
@@ -579,7 +622,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
         }
     }
-    if (blockIdx.y == 0) {
+    if (i0 == 0) {
         if (tid < TJ) {
             s_red[0][tid] = fcx;
             s_red[1][tid] = fcy;
@@ -593,35 +636,47 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 s1 += s_red[1][t];
                 s2 += s_red[2][t];
             }
-            double* po = a.part + ((size_t)b * a.ntj + blockIdx.x) * 3;
+            double* po = SD(part) + (size_t)sb * MD(ntj) * 3 + (size_t)(UNIFORM ? (int)blockIdx.x : s_tile.tj) * 3;
             po[0] = s0;
             po[1] = s1;
             po[2] = s2;
         }
     }
-    // ---- epilogue: the last CTA of this solve sums the load partials in a
-    // fixed order, advances the body by RK4 (Sec. III B, weak coupling: load
-    // of this step held over the next) and builds the next launch's maps.
     if (tid == 0) {
+        // ---- epilogue: the last CTA of this solve sums the load partials in a
+        // fixed order, advances the body by RK4 (Sec. III B, weak coupling:
+        // load of this step held over the next) and builds the next launch's
+        // maps; the last CTA of the grid advances the launch number.
         __threadfence();
-        const unsigned total = gridDim.x * gridDim.y;
-        const unsigned done = atomicAdd(a.counter + b, 1u);
-        if (done == total - 1) {
+        unsigned* counter = SD(counter) + sb;
+        const unsigned ntiles = UNIFORM ? gridDim.x * gridDim.y : (unsigned)s_sol.ntiles;
+        const unsigned done = atomicAdd(counter, 1u);
+        if (done == ntiles - 1u) {
             __threadfence();
+            const int ntj = MD(ntj);
+            const double* part = SD(part) + (size_t)sb * ntj * 3;
             double F[3] = {0.0, 0.0, 0.0};
-            for (int t = 0; t < a.ntj; ++t)
-                for (int c = 0; c < 3; ++c) F[c] += __ldcg(a.part + ((size_t)b * a.ntj + t) * 3 + c);
-            const BodyDev bd = a.bodies[b];
-            const StepMaps& mi = a.maps_in[b];
-            const BodyStateDev Snew = rk4_body(bd, mi.S_next, F[1], F[2], a.dt);
+            for (int t = 0; t < ntj; ++t)
+                for (int c = 0; c < 3; ++c) F[c] += __ldcg(part + (size_t)t * 3 + c);
+            const BodyDev bd = *(SD(body) + sb);
+            const StepMaps& mi = *(SD(maps[cur]) + sb);
+            const BodyStateDev Snew = rk4_body(bd, mi.S_next, F[1], F[2], SD(dt));
             StepMaps mo;
-            build_maps(bd, mi.S_next, Snew, mi.S_next, a.dt, mo);
+            build_maps(bd, mi.S_next, Snew, mi.S_next, SD(dt), mo);
             for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
-            a.maps_out[b] = mo;
-            a.counter[b] = 0u;
+            *(SD(maps[cur ^ 1]) + sb) = mo;
+            *counter = 0u;
+        }
+        const unsigned gd = atomicAdd(a.grid_done, 1u);
+        if (gd == gridDim.x * gridDim.y * gridDim.z - 1u) {
+            *a.grid_done = 0u;
+            atomicAdd(a.launch_no, 1u);
         }
     }
 }
+
+#undef SD
+#undef MD
 
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -669,34 +724,55 @@ __global__ void k_advance(const BodyDev* __restrict__ bodies, const double* __re
 }
 
 // Tile shapes of the step kernel (angular tile width one warp).
-constexpr int TJ = 32;
+constexpr int TJ = TILE_J;
 
-template <typename R, int TI, int NT, int MINB>
-static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s) {
+template <typename R, int TI, int NT, int MINB, bool UNIFORM>
+static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) {
     const size_t smem = step_smem_bytes<R, TI, TJ>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ, NT, MINB>,
+        cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ, NT, MINB, UNIFORM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((a.nt + TJ - 1) / TJ, (a.nr + TI - 1) / TI, a.nbatch);
-    k_step<R, TI, TJ, NT, MINB><<<grid, NT, smem, s>>>(a);
+    if (UNIFORM) {
+        const dim3 grid(a.umesh.ntj, (a.umesh.nr + TI - 1) / TI, nbatch);
+        k_step<R, TI, TJ, NT, MINB, UNIFORM><<<grid, NT, smem, s>>>(a);
+    } else {
+        k_step<R, TI, TJ, NT, MINB, UNIFORM><<<a.ntiles, NT, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStream_t s) {
-    if (precision == 0) return launch_step_t<double, 8, 256, 1>(a, s);
+template <bool UNIFORM>
+static cudaError_t launch_any(const StepArgs& a, int precision, int variant, int nbatch, cudaStream_t s) {
+    if (precision == 0) return launch_step_t<double, 8, 256, 1, UNIFORM>(a, nbatch, s);
     switch (variant) {
-        case 1: return launch_step_t<float, 16, 256, 2>(a, s);
-        case 2: return launch_step_t<float, 8, 256, 3>(a, s);
-        case 3: return launch_step_t<float, 12, 384, 2>(a, s);
-        default: return launch_step_t<float, 8, 256, 2>(a, s);
+        case 1: return launch_step_t<float, 16, 256, 2, UNIFORM>(a, nbatch, s);
+        case 2: return launch_step_t<float, 8, 256, 3, UNIFORM>(a, nbatch, s);
+        case 3: return launch_step_t<float, 12, 384, 2, UNIFORM>(a, nbatch, s);
+        default: return launch_step_t<float, 8, 256, 2, UNIFORM>(a, nbatch, s);
     }
 }
 
-int tiles_j(int nt) { return (nt + TJ - 1) / TJ; }
+cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStream_t s) {
+    return launch_any<false>(a, precision, variant, 0, s);
+}
+
+cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,
+                                cudaStream_t s) {
+    return launch_any<true>(a, precision, variant, nbatch, s);
+}
+
+int tile_rows(int precision, int variant) {
+    if (precision == 0) return 8;
+    switch (variant) {
+        case 1: return 16;
+        case 3: return 12;
+        default: return 8;
+    }
+}
 
 cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* Mout, int N,
                         int nbatch, double Cv, cudaStream_t s) {
