@@ -187,6 +187,63 @@ int lbfsi_wall_loads_noalloc(int nr, int ntheta, int nbatch, int precision, cons
                              const double* body_ref, double mu, double dt, double gamma,
                              double* loads, void* cuda_stream);
 
+/* ---- Batch runtime: many solves on meshes of different sizes, admitted and
+ * retired while others run, advanced together (one launch per step for all
+ * active solves).  Device memory comes from one pool allocated at creation;
+ * a solve is admitted only if the pool can hold it (continuous batching with
+ * memory-based admission).  Solves on identical O-grids share one device copy
+ * of the mesh geometry.  The per-step physics is exactly that of lbfsi_step
+ * (same kernel), so a solve's result does not depend on what it is batched
+ * with. */
+typedef struct lbfsi_batch_s* lbfsi_batch;
+
+/* One solve for the batch runtime: its O-grid (as in lbfsi_mesh_desc, host
+ * tables borrowed for the call), its body, flow, initial macroscopic field
+ * (host [4][nr*ntheta] or NULL for the uniform free stream) and the number of
+ * steps after which it is finished (> 0). */
+typedef struct {
+    int nr, ntheta;
+    const double* r;
+    const double* e;
+    double xc, yc;
+    lbfsi_body_desc body;
+    lbfsi_flow_params flow;
+    const double* rho_u_T;
+    int steps;
+} lbfsi_solve_desc;
+
+/* Create a batch runtime whose solves live in a device pool of pool_bytes
+ * (one cudaMalloc now; none later except when the tile table outgrows its
+ * buffer).  precision: LBFSI_FP64 or LBFSI_FP32 for every solve of the batch. */
+int lbfsi_batch_create(size_t pool_bytes, int precision, void* cuda_stream, lbfsi_batch* out);
+int lbfsi_batch_destroy(lbfsi_batch b);
+
+/* Admit a solve; on success *slot is its id (>= 0).  LBFSI_ENOMEM means the
+ * pool has no room for it now (nothing changed; retry after removing finished
+ * solves).  The solve's first step happens in the next lbfsi_batch_step. */
+int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot);
+
+/* Advance every active solve by up to nsteps coupled steps (one launch per
+ * step covering all active solves; a solve stops when it reaches its step
+ * count).  *active_after (nullable) receives the number of unfinished solves.
+ * Asynchronous except when the set of active solves changes. */
+int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after);
+
+/* Steps done and finished flag of a slot (host-side bookkeeping, no sync). */
+int lbfsi_batch_poll(lbfsi_batch b, int slot, int* steps_done, int* finished);
+
+/* Results of a slot after its last step: macroscopic fields (host
+ * [4][nr*ntheta], nullable), loads of the last step (host [3], nullable) and
+ * body state after the structural update (nullable).  Synchronises; returns
+ * the batch's device error status as lbfsi_synchronize does. */
+int lbfsi_batch_get(lbfsi_batch b, int slot, double* rho_u_T, double* loads, lbfsi_body_state* state);
+
+/* Retire a slot: its device memory returns to the pool (synchronises). */
+int lbfsi_batch_remove(lbfsi_batch b, int slot);
+
+/* Free bytes of the pool and its largest free block. */
+int lbfsi_batch_memory(lbfsi_batch b, size_t* free_bytes, size_t* largest_free);
+
 /* Number of kernel launches issued on the handle's stream so far. */
 int64_t lbfsi_launch_count(lbfsi_mesh m);
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbfsi.so")
-SOURCES = ["lbfsi_step.cu", "lbfsi_api.cu", "lbfsi_host.cu", "lbfsi_noalloc.cu"]
+SOURCES = ["lbfsi_step.cu", "lbfsi_api.cu", "lbfsi_host.cu", "lbfsi_batch.cu", "lbfsi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

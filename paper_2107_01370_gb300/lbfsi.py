@@ -25,7 +25,9 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_step", "lbfsi_body_forces", "lbfsi_advance_bodies", "lbfsi_get_body_state",
             "lbfsi_get_fields", "lbfsi_get_populations", "lbfsi_set_populations",
             "lbfsi_synchronize", "lbfsi_launch_count", "lbfsi_last_error",
-            "lbfsi_wall_loads_noalloc"]
+            "lbfsi_wall_loads_noalloc", "lbfsi_batch_create", "lbfsi_batch_destroy",
+            "lbfsi_batch_add", "lbfsi_batch_step", "lbfsi_batch_poll", "lbfsi_batch_get",
+            "lbfsi_batch_remove", "lbfsi_batch_memory"]
 
 
 class LbfsiError(RuntimeError):
@@ -53,6 +55,14 @@ class MeshDesc(ctypes.Structure):
                 ("r", ctypes.POINTER(ctypes.c_double)), ("e", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class SolveDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("r", ctypes.POINTER(ctypes.c_double)), ("e", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("body", BodyDesc),
+                ("flow", FlowParams), ("rho_u_T", ctypes.POINTER(ctypes.c_double)),
+                ("steps", ctypes.c_int)]
 
 
 class BodyState(ctypes.Structure):
@@ -91,6 +101,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                              P, P, ctypes.c_double, ctypes.c_double, P, P, P,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              P, P]
+    sz = ctypes.c_size_t
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.lbfsi_batch_create.argtypes = [sz, ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.lbfsi_batch_destroy.argtypes = [P]
+    lib.lbfsi_batch_add.argtypes = [P, ctypes.POINTER(SolveDesc), ip]
+    lib.lbfsi_batch_step.argtypes = [P, ctypes.c_int, ip]
+    lib.lbfsi_batch_poll.argtypes = [P, ctypes.c_int, ip, ip]
+    lib.lbfsi_batch_get.argtypes = [P, ctypes.c_int, dp, dp, ctypes.POINTER(BodyState)]
+    lib.lbfsi_batch_remove.argtypes = [P, ctypes.c_int]
+    lib.lbfsi_batch_memory.argtypes = [P, ctypes.POINTER(sz), ctypes.POINTER(sz)]
     lib.lbfsi_last_error.argtypes = []
     lib.lbfsi_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -216,3 +236,74 @@ class Mesh:
 
     def launch_count(self) -> int:
         return int(self._lib.lbfsi_launch_count(self.h))
+
+
+class Batch:
+    """Batch runtime: solves on meshes of different sizes admitted into one
+    device pool and advanced together (see include/lbfsi.h)."""
+
+    def __init__(self, pool_bytes, precision=FP32, stream=None):
+        lib = load()
+        self._lib = lib
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(lib.lbfsi_batch_create(int(pool_bytes), precision, ctypes.c_void_p(stream or 0),
+                                      ctypes.byref(h)))
+        self.h = h
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _check(self._lib.lbfsi_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, r, e, body, flow, steps, rho_u_T=None, centre=(0.0, 0.0)):
+        """Admit a solve; returns its slot, or None if the pool has no room now."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        e = np.ascontiguousarray(e, dtype=np.float64).reshape(-1, 2)
+        m = None if rho_u_T is None else np.ascontiguousarray(rho_u_T, dtype=np.float64)
+        d = SolveDesc(r.size, e.shape[0], _dptr(r), _dptr(e), centre[0], centre[1], body_desc(body),
+                      flow_params(flow), None if m is None else _dptr(m), int(steps))
+        slot = ctypes.c_int(-1)
+        rc = self._lib.lbfsi_batch_add(self.h, ctypes.byref(d), ctypes.byref(slot))
+        if rc == ENOMEM:
+            return None
+        _check(rc)
+        self._shapes[slot.value] = (r.size, e.shape[0])
+        return slot.value
+
+    def step(self, n=1):
+        act = ctypes.c_int(0)
+        _check(self._lib.lbfsi_batch_step(self.h, int(n), ctypes.byref(act)))
+        return act.value
+
+    def poll(self, slot):
+        done = ctypes.c_int(0)
+        fin = ctypes.c_int(0)
+        _check(self._lib.lbfsi_batch_poll(self.h, slot, ctypes.byref(done), ctypes.byref(fin)))
+        return done.value, bool(fin.value)
+
+    def get(self, slot, fields=True):
+        nr, nt = self._shapes[slot]
+        f = np.empty((4, nr, nt)) if fields else None
+        loads = np.empty(3)
+        st = BodyState()
+        _check(self._lib.lbfsi_batch_get(self.h, slot, None if f is None else _dptr(f), _dptr(loads),
+                                         ctypes.byref(st)))
+        return f, loads, dict(h=st.h, alpha=st.alpha, hdot=st.hdot, adot=st.adot)
+
+    def remove(self, slot):
+        _check(self._lib.lbfsi_batch_remove(self.h, slot))
+        self._shapes.pop(slot, None)
+
+    def memory(self):
+        fb = ctypes.c_size_t(0)
+        lg = ctypes.c_size_t(0)
+        _check(self._lib.lbfsi_batch_memory(self.h, ctypes.byref(fb), ctypes.byref(lg)))
+        return fb.value, lg.value

@@ -1,0 +1,119 @@
+"""Batch runtime (continuous batching of uneven meshes): every solve gives the
+same result alone and in the mix, FP64 batches match the oracle, and
+admission is decided by the device memory pool."""
+import numpy as np
+import pytest
+
+import oracle.mesh as OM
+import oracle.solver as OS
+from paper_2107_01370_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2107_01370_gb300 import build, lbfsi
+    build.build()
+    lbfsi.load()
+    return lbfsi
+
+
+def _case(nr, nt, v_r, m_star, seed):
+    body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=m_star, v_r=v_r)
+    case = inputs.cylinder_case(nr, nt, r_far=8.0, body=body)
+    M0 = inputs.initial_field(nr, nt, case.flow, seed=seed)
+    return case, M0
+
+
+SPECS = [(32, 32, 3.0, 2.0, 1, 7), (48, 64, 5.0, 10.0, 2, 11), (64, 96, 8.0, 20.0, 3, 9)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_each_solve_same_alone_and_in_the_mix(L, precision):
+    """Three solves of different sizes and step counts, admitted at different
+    times into one batch, give bit-identical fields, loads and body states to
+    the same solves run alone through the single-mesh handle."""
+    prec = L.FP32 if precision == "fp32" else L.FP64
+    batch = L.Batch(256 << 20, precision=prec)
+    cases = [_case(nr, nt, vr, ms, seed) for nr, nt, vr, ms, seed, _ in SPECS]
+    steps = [s[5] for s in SPECS]
+    slots = [batch.add(cases[0][0].r, cases[0][0].e, cases[0][0].bodies[0], cases[0][0].flow, steps[0],
+                       cases[0][1])]
+    batch.step(2)                                   # solve 0 runs alone for 2 steps
+    slots.append(batch.add(cases[1][0].r, cases[1][0].e, cases[1][0].bodies[0], cases[1][0].flow,
+                           steps[1], cases[1][1]))
+    batch.step(3)
+    slots.append(batch.add(cases[2][0].r, cases[2][0].e, cases[2][0].bodies[0], cases[2][0].flow,
+                           steps[2], cases[2][1]))
+    while batch.step(1) > 0:
+        pass
+    for k, (case, M0) in enumerate(cases):
+        assert batch.poll(slots[k]) == (steps[k], True)
+        fb, lb, sb = batch.get(slots[k])
+        mesh = L.Mesh(case.r, case.e, case.bodies, precision=prec)
+        mesh.init_fields(case.flow, M0[None])
+        mesh.step(steps[k])
+        fa = mesh.get_fields()[0]
+        la = mesh.body_forces()[0]
+        sa = mesh.body_state()[0]
+        mesh.close()
+        assert np.array_equal(fa, fb), k
+        assert np.array_equal(la, lb), k
+        assert sa == sb, k
+    for s in slots:
+        batch.remove(s)
+    batch.close()
+
+
+def test_fp64_batch_matches_oracle(L):
+    batch = L.Batch(128 << 20, precision=L.FP64)
+    got = []
+    for nr, nt, vr, ms, seed, n in SPECS[:2]:
+        case, M0 = _case(nr, nt, vr, ms, seed)
+        got.append((batch.add(case.r, case.e, case.bodies[0], case.flow, n, M0), case, M0, n))
+    while batch.step(1) > 0:
+        pass
+    for slot, case, M0, n in got:
+        s = OS.Solver.from_case(OM.ogrid_mesh(case.r, case.e), case, M0)
+        for _ in range(n):
+            r = s.step()
+        f, loads, st = batch.get(slot)
+        err = max(np.abs(f[c] - r.M[c]).max() / np.abs(r.M[c]).max() for c in (0, 3))
+        err = max(err, np.hypot(f[1] - r.M[1], f[2] - r.M[2]).max() / np.hypot(r.M[1], r.M[2]).max())
+        assert err < 1e-12
+        assert np.abs(loads - np.array(r.force)).max() < 1e-12 / 3.0
+        assert abs(st["h"] - s.S[0]["h"]) < 1e-12
+    batch.close()
+
+
+def test_admission_by_device_memory(L):
+    """A pool sized for about two solves admits two, refuses the third until
+    one is removed, and returns all its memory at the end."""
+    case, M0 = _case(64, 96, 5.0, 5.0, 4)
+    probe = L.Batch(64 << 20, precision=L.FP32)
+    free0, _ = probe.memory()
+    s0 = probe.add(case.r, case.e, case.bodies[0], case.flow, 3, M0)
+    per_solve = free0 - probe.memory()[0]
+    probe.remove(s0)
+    assert probe.memory()[0] == free0
+    probe.close()
+    batch = L.Batch(int(2.5 * per_solve), precision=L.FP32)
+    free_start, _ = batch.memory()
+    a = batch.add(case.r, case.e, case.bodies[0], case.flow, 3, M0)
+    b = batch.add(case.r, case.e, case.bodies[0], case.flow, 3, M0)
+    c = batch.add(case.r, case.e, case.bodies[0], case.flow, 3, M0)
+    assert a is not None and b is not None and c is None
+    batch.step(3)
+    batch.remove(a)
+    c = batch.add(case.r, case.e, case.bodies[0], case.flow, 3, M0)
+    assert c is not None
+    while batch.step(1) > 0:
+        pass
+    f1 = batch.get(b)[0]
+    f2 = batch.get(c)[0]
+    assert np.array_equal(f1, f2)        # same inputs, admitted at different times
+    batch.remove(b)
+    batch.remove(c)
+    assert batch.memory()[0] == free_start
+    batch.close()
