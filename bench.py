@@ -168,6 +168,38 @@ def reference_sample_case():
     return case
 
 
+SERVING_POOL = 1 << 30   # 1 GiB: about half of what the 256 requests need at once
+
+
+def serving_bench(stream):
+    """Serving workload: 256 cylinder-VIV requests (O-grid sizes uniform over
+    64x32 .. 512x256, V_R in [3, 8], m* in [2, 20], seed 0, 2000 steps each,
+    FP32) admitted into a 1 GiB device pool.  Capacity: all requests at t = 0;
+    then a Poisson stream at 90% of capacity for p50/p99 time-to-solution;
+    baseline: the same requests one after another as plain solves."""
+    from paper_2107_01370_gb300 import serving
+    cache = serving.CaseCache()
+    reqs = serving.viv_requests(256, 2000, seed=0)
+    done_c, loads_c, wall_c, peak_c = serving.run_batched(reqs, SERVING_POOL, chunk=50,
+                                                          stream=stream, cache=cache)
+    capacity = len(reqs) / wall_c
+    reqs_p = serving.poisson_arrivals(serving.viv_requests(256, 2000, seed=0), 0.9 * capacity,
+                                      seed=1)
+    done_p, loads_p, wall_p, peak_p = serving.run_batched(reqs_p, SERVING_POOL, chunk=50,
+                                                          stream=stream, cache=cache)
+    p50, p99 = serving.latency_stats(done_p)
+    done_s, loads_s, wall_s = serving.run_sequential(reqs, stream=stream, cache=cache)
+    same = all(np.array_equal(loads_p[k], loads_s[k]) for k in loads_s)
+    return {"metric": "batched solves/s", "solves_per_s": round(len(reqs_p) / wall_p, 3),
+            "p50_s": round(p50, 4), "p99_s": round(p99, 4),
+            "capacity_solves_per_s": round(capacity, 3),
+            "sequential_solves_per_s": round(len(reqs) / wall_s, 3),
+            "speedup_vs_sequential": round(wall_s / wall_c, 2),
+            "requests": len(reqs), "steps_per_request": 2000, "arrival_rate": round(0.9 * capacity, 3),
+            "pool_bytes": SERVING_POOL, "peak_active": peak_p,
+            "results_equal_alone_and_in_mix": bool(same)}
+
+
 def run_reference(args):
     """The oracle timed on the host cores, same metric and workload; each step
     is one oracle step of the bounded sample (reference_sample_case)."""
@@ -209,6 +241,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -318,6 +351,10 @@ def main():
         m2.close()
         del fields
 
+    serving_out = None
+    if not args.no_serving:
+        serving_out = serving_bench(stream.cuda_stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -333,7 +370,7 @@ def main():
                                 f"{BYTES_PER_NODE_FP32 * nodes / 1e6:.0f} MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": launches, "clocks": clocks,
+               "gpu_launches": launches, "clocks": clocks, "serving": serving_out,
                "solves_per_s": round(B * world / (case.steps * region_ms / args.steps * 1e-3), 4)}
         print(json.dumps(out), flush=True)
     mesh.close()
