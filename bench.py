@@ -38,7 +38,7 @@ if "reference" in sys.argv:
 
 import numpy as np  # noqa: E402
 
-from paper_2107_01370_gb300 import inputs  # noqa: E402
+from paper_2107_01370_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "fused-step MLUPS"
 UNIT = "MLUPS"
@@ -303,12 +303,12 @@ def main():
     clocks = sampler.stop()
     region_ms = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist:
-        t = torch.tensor([region_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        region_ms = float(t.item())
+    # replicas: every rank advanced its own batch; the time is the slowest
+    # rank's, the work is that of all ranks
+    region_ms = replicas.max_over_ranks(region_ms, dist, device="cuda")
     nodes = case.nodes * B
-    value = nodes * world * args.steps / (region_ms * 1e-3) / 1e6
+    value = replicas.aggregate_mlups(replicas.sum_over_ranks(nodes * args.steps, dist, device="cuda"),
+                                     region_ms * 1e-3)
     kavg_s = statistics.mean(kern_ms) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_NODE_FP32 * nodes / kavg_s / 1e9
@@ -339,11 +339,7 @@ def main():
             m2.body_forces(loads)
         fields = m2.get_fields()
         t1 = time.perf_counter()
-        el = t1 - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = replicas.max_over_ranks(t1 - t0, dist, device="cuda")
         e2e = {"value": nodes * world * K / el / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(M0b.nbytes / K),
                "d2h_bytes_per_step": int((fields.nbytes + K * loads.nbytes) / K),
@@ -352,7 +348,7 @@ def main():
         del fields
 
     serving_out = None
-    if not args.no_serving:
+    if not args.no_serving and world == 1:
         serving_out = serving_bench(stream.cuda_stream)
 
     cpu = None
