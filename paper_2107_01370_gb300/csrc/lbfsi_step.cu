@@ -171,6 +171,19 @@ __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F0
     G[3] = i01 * j01 + i11 * j11;
 }
 
+// Asynchronous 4- or 8-byte copy global -> shared (cp.async, L2-only path).
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double* dst, const double* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename R>
 __device__ __forceinline__ R pick(double d, float f);
 template <>
@@ -329,13 +342,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     }
 
     // ---- phase 1: stage M^k and the populations ---------------------------
+    // asynchronous copies global -> shared (no register round trip), all in
+    // flight together, one wait before the barrier
     for (int idx = tid; idx < T::MS; idx += NT) {
         const int li = idx / T::MW, lj = idx - li * T::MW;
         const int i = mi0 + li;
         if (i >= 0 && i < nr) {
             const int n = i * nt + s_jw[lj];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) sM[c * T::MS + idx] = M_in[(size_t)c * N + n];
+            for (int c = 0; c < 4; ++c) cp_async(sM + c * T::MS + idx, M_in + (size_t)c * N + n);
         }
     }
     const int pi0 = i0 - T::HP, pj0 = j0 - T::HP;
@@ -344,15 +359,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const int i = pi0 + li;
         if (i >= 0 && i < nr) {
             const int n = i * nt + s_jw[lj + (T::HM - T::HP)];
+            R* dst = reinterpret_cast<R*>(sp + idx * 9);
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                R2 v;
-                v.x = f_in[(size_t)q * N + n];
-                v.y = g_in[(size_t)q * N + n];
-                sp[idx * 9 + q] = v;
+                cp_async(dst + 2 * q, f_in + (size_t)q * N + n);
+                cp_async(dst + 2 * q + 1, g_in + (size_t)q * N + n);
             }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- phase 2: correction fields and collision of step k --------------
