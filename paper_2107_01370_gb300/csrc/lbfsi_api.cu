@@ -54,22 +54,20 @@ struct lbfsi_mesh_s {
     BodyStateDev* d_state_b = nullptr;
     double* d_loads_tmp = nullptr;
     double* d_part = nullptr;        // [nbatch][ntj][3] load partials
-    unsigned* d_counter = nullptr;   // [nbatch] CTA completion counters
+    unsigned* d_counter = nullptr;   // [nbatch][2] CTA completion count, step number
     BodyDev* d_bodies = nullptr;     // [nbatch]
     lbfsi::MeshDev* d_meshdev = nullptr;
     SolveDev* d_solves = nullptr;    // [nbatch]
     TileDev* d_tiles = nullptr;      // [nbatch * tiles_per_solve]
-    unsigned* d_launch = nullptr;    // [0] launch number, [1] grid completion counter
     unsigned* d_status = nullptr;
     std::vector<SolveDev> solves;
-    unsigned host_L = 0;             // step launches issued (mirror of d_launch[0])
-    unsigned admit = 0;              // launch number of the first step of every solve
+    unsigned host_k = 0;             // step number of every solve (mirror of counter[1])
     bool initialized = false;
     double dt = 0;
     int64_t launches = 0;
 
-    int cur() const { return (int)((host_L - admit) & 1u); }
-    bool first() const { return host_L == admit; }
+    int cur() const { return (int)(host_k & 1u); }
+    bool first() const { return host_k == 0u; }
 };
 
 namespace {
@@ -131,7 +129,7 @@ void free_all(lbfsi_mesh m) {
     void* ptrs[] = {m->d_f[0], m->d_f[1], m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost,
                     m->d_gpost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
                     m->d_loads_tmp, m->d_part, m->d_counter, m->d_bodies, m->d_meshdev, m->d_solves,
-                    m->d_tiles, m->d_launch, m->d_status};
+                    m->d_tiles, m->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     lbfsi::release_mesh(m->dmesh, m->mem);
@@ -144,7 +142,6 @@ int upload_solves(lbfsi_mesh m) {
     for (int b = 0; b < m->nbatch; ++b) {
         SolveDev& s = m->solves[b];
         s.mesh = 0;
-        s.admit = m->admit;
         s.ntiles = m->tiles_per_solve;
         for (int p = 0; p < 2; ++p) {
             s.f[p] = (char*)m->d_f[p] + (size_t)b * 9 * N * es;
@@ -155,7 +152,7 @@ int upload_solves(lbfsi_mesh m) {
         s.fpost = m->d_fpost ? (char*)m->d_fpost + (size_t)b * 9 * N * es : nullptr;
         s.gpost = m->d_gpost ? (char*)m->d_gpost + (size_t)b * 9 * N * es : nullptr;
         s.part = m->d_part + (size_t)b * m->host.ntj * 3;
-        s.counter = m->d_counter + b;
+        s.counter = m->d_counter + 2 * b;
         s.body = m->d_bodies + b;
     }
     std::vector<TileDev> tiles;
@@ -170,7 +167,7 @@ int upload_solves(lbfsi_mesh m) {
                 t.i0 = ti * m->tile_rows;
                 t.j0 = tj * lbfsi::TILE_J;
                 t.tj = tj;
-                t.admit = m->admit;
+                t.counter = m->d_counter + 2 * b;
                 t.maps[0] = m->d_maps[0] + b;
                 t.maps[1] = m->d_maps[1] + b;
                 tiles.push_back(t);
@@ -193,8 +190,6 @@ lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
     a.tiles = m->d_tiles;
     a.ntiles = m->nbatch * m->tiles_per_solve;
     a.collide_only = collide_only;
-    a.launch_no = m->d_launch;
-    a.grid_done = m->d_launch + 1;
     a.status = m->d_status;
     return a;
 }
@@ -257,12 +252,11 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     LB_ALLOC(m->d_state_b, nb);
     LB_ALLOC(m->d_loads_tmp, nb * 3);
     LB_ALLOC(m->d_part, nb * ntj * 3);
-    LB_ALLOC(m->d_counter, nb);
+    LB_ALLOC(m->d_counter, 2 * nb);
     LB_ALLOC(m->d_bodies, nb);
     LB_ALLOC(m->d_meshdev, 1);
     LB_ALLOC(m->d_solves, nb);
     LB_ALLOC(m->d_tiles, nb * m->tiles_per_solve);
-    LB_ALLOC(m->d_launch, 2);
     LB_ALLOC(m->d_status, 1);
 #undef LB_ALLOC
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -278,8 +272,7 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     }
     e = cudaMemcpy(m->d_meshdev, &m->dmesh.dev, sizeof(lbfsi::MeshDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->d_status, 0, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(m->d_counter, 0, nb * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(m->d_launch, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(m->d_counter, 0, 2 * nb * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(m->d_part, 0, nb * ntj * 3 * sizeof(double));
     if (e != cudaSuccess) {
         free_all(m);
@@ -330,11 +323,9 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_loads_tmp, zl.data(), zl.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, nb * sizeof(unsigned), m->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_launch, 0, 2 * sizeof(unsigned), m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, 2 * nb * sizeof(unsigned), m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init_fields upload");
-    m->host_L = 0;
-    m->admit = 0;
+    m->host_k = 0;
     rc = upload_solves(m);
     if (rc) return rc;
     e = lbfsi::launch_init(m->precision, m->d_stage, m->d_f[0], m->d_g[0], m->d_M[0], m->host.N, m->nbatch,
@@ -380,7 +371,7 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
         cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-        m->host_L++;
+        m->host_k++;
     }
     return LBFSI_OK;
 }
@@ -493,9 +484,18 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const 
     if (!rc) rc = upload(m, rho_u_T, m->d_M[c], (size_t)m->nbatch * 4 * m->host.N);
     if (rc) return rc;
     // the restored state is post-propagation: make the next launch collide it
-    // (launch number - admit >= 2 with the same parity)
-    m->admit = m->host_L - 2u - (unsigned)c;
-    return upload_solves(m);
+    // (step number >= 2 with the same parity)
+    m->host_k = 2u + (unsigned)c;
+    std::vector<unsigned> ctr(2 * (size_t)m->nbatch);
+    for (int b = 0; b < m->nbatch; ++b) {
+        ctr[2 * b] = 0u;
+        ctr[2 * b + 1] = m->host_k;
+    }
+    cudaError_t e = cudaMemcpyAsync(m->d_counter, ctr.data(), ctr.size() * sizeof(unsigned),
+                                    cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step number upload");
+    return LBFSI_OK;
 }
 
 int64_t lbfsi_launch_count(lbfsi_mesh m) { return m ? m->launches : -1; }

@@ -122,11 +122,9 @@ struct lbfsi_batch_s {
     TileDev* d_tiles = nullptr;
     size_t tiles_cap = 0;
     int max_meshes = 256, max_slots = 4096;
-    unsigned* d_launch = nullptr;   // [0] launch number, [1] grid completion counter
     unsigned* d_status = nullptr;
     BodyStateDev* d_zero_state = nullptr;
     double* d_zero_loads = nullptr;
-    unsigned host_L = 0;
     int ntiles = 0;
     bool dirty = true;
 };
@@ -209,7 +207,7 @@ int rebuild_tiles(lbfsi_batch b) {
                 t.i0 = ti * b->tile_rows;
                 t.j0 = tj * lbfsi::TILE_J;
                 t.tj = tj;
-                t.admit = s.dev.admit;
+                t.counter = s.dev.counter;
                 t.maps[0] = s.dev.maps[0];
                 t.maps[1] = s.dev.maps[1];
                 tiles.push_back(t);
@@ -272,11 +270,9 @@ int lbfsi_batch_create(size_t pool_bytes, int precision, void* cuda_stream, lbfs
     }
     cudaError_t e = cudaMalloc(&b->d_meshes, b->max_meshes * sizeof(MeshDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_solves, b->max_slots * sizeof(SolveDev));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_launch, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_zero_state, sizeof(BodyStateDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_zero_loads, 3 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(b->d_launch, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_zero_state, 0, sizeof(BodyStateDev));
     if (e == cudaSuccess) e = cudaMemset(b->d_zero_loads, 0, 3 * sizeof(double));
@@ -291,7 +287,7 @@ int lbfsi_batch_create(size_t pool_bytes, int precision, void* cuda_stream, lbfs
 int lbfsi_batch_destroy(lbfsi_batch b) {
     if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
     cudaStreamSynchronize(b->stream);
-    void* ptrs[] = {b->d_meshes, b->d_solves, b->d_tiles, b->d_launch, b->d_status, b->d_zero_state,
+    void* ptrs[] = {b->d_meshes, b->d_solves, b->d_tiles, b->d_status, b->d_zero_state,
                     b->d_zero_loads};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -345,7 +341,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
         ok = ok && (sd.maps[p] = (StepMaps*)take(sizeof(StepMaps))) != nullptr;
     }
     ok = ok && (sd.part = (double*)take((size_t)h.ntj * 3 * sizeof(double))) != nullptr;
-    ok = ok && (sd.counter = (unsigned*)take(sizeof(unsigned))) != nullptr;
+    ok = ok && (sd.counter = (unsigned*)take(2 * sizeof(unsigned))) != nullptr;
     BodyDev* body = nullptr;
     ok = ok && (body = (BodyDev*)take(sizeof(BodyDev))) != nullptr;
     double* stage = nullptr;
@@ -357,7 +353,6 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     }
     sd.body = body;
     sd.mesh = mk;
-    sd.admit = b->host_L;
     sd.ntiles = ((h.nr + b->tile_rows - 1) / b->tile_rows) * h.ntj;
     sd.fpost = sd.gpost = nullptr;
     // initial state: equilibria of the initial field, bodies at rest
@@ -375,7 +370,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     const BodyDev bd = lbfsi::body_dev(d->body, sd.rho_inf, sd.uinf_x);
     cudaError_t e = cudaMemcpyAsync(stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(body, &bd, sizeof(BodyDev), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sd.counter, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sd.counter, 0, 2 * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = lbfsi::launch_init(b->precision, stage, sd.f[0], sd.g[0], sd.M[0], (int)N, 1, sd.Cv, b->stream);
     if (e == cudaSuccess)
         e = lbfsi::launch_prepare(body, b->d_zero_state, b->d_zero_state, b->d_zero_state, b->d_zero_loads, sd.dt,
@@ -419,12 +414,9 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
         a.tiles = b->d_tiles;
         a.ntiles = b->ntiles;
         a.collide_only = 0;
-        a.launch_no = b->d_launch;
-        a.grid_done = b->d_launch + 1;
         a.status = b->d_status;
         const cudaError_t e = lbfsi::launch_step(a, b->precision, b->variant, b->stream);
         if (e != cudaSuccess) return cuda_err(e, "batch step launch");
-        b->host_L++;
         for (auto& s : b->slots) {
             if (!s.used || s.finished) continue;
             if (++s.steps_done >= s.steps_target) {

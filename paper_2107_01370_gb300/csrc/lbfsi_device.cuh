@@ -210,26 +210,51 @@ __device__ __forceinline__ void grad_populations(R rho, R ux, R uy, R T, R dudx,
     }
 }
 
-// Blended rigid map of one body (Sec. II D) for one body state, in the
-// precision R:  d(X) = A (X - Xp) + t with A = R(alpha) - I, t = (0, h);
-// x = X + (1 - r_blend) d(X).  dA, dt_ are the (state - previous state)
-// differences divided by the time step, for V_G.
-template <typename R>
-__host__ __device__ inline BodyMap<R> make_body_map(const BodyDev& b, const BodyStateDev& s,
-                                                    const BodyStateDev& sp, double dt) {
-    BodyMap<R> m;
+// Rotation part of a body state: sin(alpha) and cos(alpha) - 1 written as
+// -2 sin^2(alpha/2) (no cancellation for small angles).  A state without
+// rotation (every state of a transverse body) takes no transcendental call:
+// sin(+-0) = +-0 exactly, so the values are the same.
+struct BodyRot {
+    double sa, cm1;
+};
+__host__ __device__ inline BodyRot body_rot(double alpha) {
+    double sa = alpha, h = 0.5 * alpha;
+    if (alpha != 0.0) {
+        sa = sin(alpha);
+        h = sin(0.5 * alpha);
+    }
+    return BodyRot{sa, -2.0 * h * h};
+}
+
+// Blended rigid map of one body (Sec. II D) for one body state s with
+// previous state sp:  d(X) = A (X - Xp) + t with A = R(alpha) - I,
+// t = (0, h);  x = X + (1 - r_blend) d(X).  The va.., vt. fields are the
+// (state - previous state) differences times inv_dt, for V_G.
+__host__ __device__ inline BodyMap<double> make_body_map(const BodyDev& b, const BodyStateDev& s,
+                                                         BodyRot rs, const BodyStateDev& sp,
+                                                         BodyRot rp, double inv_dt) {
+    BodyMap<double> m;
     m.active = b.dof != 0;
-    m.xc = (R)b.xc; m.yc = (R)b.yc; m.xp = (R)b.xp; m.yp = (R)b.yp;
-    m.r_in = (R)b.r_in;
-    m.inv_w = (R)(1.0 / (b.r_out - b.r_in));
-    const double sa = sin(s.alpha), cm1 = -2.0 * sin(0.5 * s.alpha) * sin(0.5 * s.alpha);
-    const double spa = sin(sp.alpha), spm1 = -2.0 * sin(0.5 * sp.alpha) * sin(0.5 * sp.alpha);
-    m.a00 = (R)cm1; m.a01 = (R)(-sa); m.a10 = (R)sa; m.a11 = (R)cm1;
-    m.tx = (R)0; m.ty = (R)s.h;
-    const double inv = 1.0 / dt;
-    m.va00 = (R)((cm1 - spm1) * inv); m.va01 = (R)(-(sa - spa) * inv);
-    m.va10 = (R)((sa - spa) * inv); m.va11 = (R)((cm1 - spm1) * inv);
-    m.vtx = (R)0; m.vty = (R)((s.h - sp.h) * inv);
+    m.xc = b.xc; m.yc = b.yc; m.xp = b.xp; m.yp = b.yp;
+    m.r_in = b.r_in;
+    m.inv_w = b.inv_w;
+    m.a00 = rs.cm1; m.a01 = -rs.sa; m.a10 = rs.sa; m.a11 = rs.cm1;
+    m.tx = 0.0; m.ty = s.h;
+    m.va00 = (rs.cm1 - rp.cm1) * inv_dt; m.va01 = -(rs.sa - rp.sa) * inv_dt;
+    m.va10 = (rs.sa - rp.sa) * inv_dt; m.va11 = (rs.cm1 - rp.cm1) * inv_dt;
+    m.vtx = 0.0; m.vty = (s.h - sp.h) * inv_dt;
+    return m;
+}
+
+__host__ __device__ inline BodyMap<float> to_float(const BodyMap<double>& d) {
+    BodyMap<float> m;
+    m.active = d.active;
+    m.xc = (float)d.xc; m.yc = (float)d.yc; m.xp = (float)d.xp; m.yp = (float)d.yp;
+    m.r_in = (float)d.r_in; m.inv_w = (float)d.inv_w;
+    m.a00 = (float)d.a00; m.a01 = (float)d.a01; m.a10 = (float)d.a10; m.a11 = (float)d.a11;
+    m.tx = (float)d.tx; m.ty = (float)d.ty;
+    m.va00 = (float)d.va00; m.va01 = (float)d.va01; m.va10 = (float)d.va10; m.va11 = (float)d.va11;
+    m.vtx = (float)d.vtx; m.vty = (float)d.vty;
     return m;
 }
 
@@ -268,17 +293,19 @@ __device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F0
 }
 
 // Fill a maps record: collision map from S_cur, stream maps from
-// (S_next, S_vgprev).
+// (S_next, S_vgprev); the float maps are the float64 ones rounded.
 __host__ __device__ inline void build_maps(const BodyDev& b, const BodyStateDev& S_cur,
                                            const BodyStateDev& S_next,
                                            const BodyStateDev& S_vgprev, double dt, StepMaps& m) {
     m.S_cur = S_cur;
     m.S_next = S_next;
     m.S_vgprev = S_vgprev;
-    m.Kd = make_body_map<double>(b, S_cur, S_cur, dt);
-    m.Sd = make_body_map<double>(b, S_next, S_vgprev, dt);
-    m.Kf = make_body_map<float>(b, S_cur, S_cur, dt);
-    m.Sf = make_body_map<float>(b, S_next, S_vgprev, dt);
+    const double inv_dt = 1.0 / dt;
+    const BodyRot rc = body_rot(S_cur.alpha), rn = body_rot(S_next.alpha), rp = body_rot(S_vgprev.alpha);
+    m.Kd = make_body_map(b, S_cur, rc, S_cur, rc, inv_dt);
+    m.Sd = make_body_map(b, S_next, rn, S_vgprev, rp, inv_dt);
+    m.Kf = to_float(m.Kd);
+    m.Sf = to_float(m.Sd);
 }
 
 // Classical RK4 of the body ODE over dt with the load (Fx, Fy, M) held fixed

@@ -184,6 +184,7 @@ BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
     b.dof = d.dof;
     b.xc = d.xc; b.yc = d.yc; b.xp = d.xp; b.yp = d.yp;
     b.r_in = d.r_in; b.r_out = d.r_out;
+    b.inv_w = 1.0 / (d.r_out - d.r_in);
     const double pi = 3.14159265358979323846;
     if (d.dof == LBFSI_BODY_TRANSVERSE) {
         const double D = d.length;

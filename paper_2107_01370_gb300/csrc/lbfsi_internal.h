@@ -19,7 +19,7 @@ enum : unsigned {
 struct BodyDev {
     int dof;                 // 0 fixed, 1 transverse, 2 pitch-plunge
     double xc, yc, xp, yp;   // blend centre, reference point
-    double r_in, r_out;
+    double r_in, r_out, inv_w;   // blend radii, 1 / (r_out - r_in)
     double m, k, c;          // transverse: m h'' + c h' + k h = F_y
     double s_a, i_a, k_h, k_a;  // pitch-plunge: [m S; S I] y'' + diag(k_h, k_a) y = [F_y; M]
 };
@@ -70,15 +70,15 @@ struct MeshDev {
 };
 
 // One solve (one body, one set of fields on one mesh).  Buffers are
-// ping-pong pairs; which one holds the current state follows from the launch
-// number: after (L - admit) step launches the state is in buffer
-// (L - admit) & 1, and the launch with L == admit streams from the initial
-// (post-collision) state without colliding.
+// ping-pong pairs; which one holds the current state follows from the solve's
+// step number k (counter[1]): after k step launches the state is in buffer
+// k & 1, and the launch with k == 0 streams from the initial (post-collision)
+// state without colliding.  counter[0] counts the CTAs of the solve that have
+// finished the current launch; the last one advances the body, resets
+// counter[0] and writes k + 1.
 struct SolveDev {
     int mesh;
-    unsigned admit;                // launch number of the solve's first step
     int ntiles;                    // CTAs of this solve in every step launch
-    int tile_j0;                   // unused padding for alignment
     // flow (float64 and float copies, so that no thread of the float path
     // converts or divides in float64)
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
@@ -90,24 +90,19 @@ struct SolveDev {
     void* fpost;                   // collide-only output (post-collision populations)
     void* gpost;
     double* part;                  // [ntj][3] load partials of the streamed step
-    unsigned* counter;             // CTA completion counter (zero between launches)
+    unsigned* counter;             // [2]: CTA completion count, step number k
     const BodyDev* body;
 };
 
 // One CTA of a step launch: a tile of one solve.  The entry repeats the
-// solve's mesh index, admission launch number and maps pointers so that a CTA
-// can fetch its solve, mesh and maps records in parallel after one load.
+// solve's counter and maps pointers so that a CTA can read its step number
+// and fetch its maps without first loading the solve record.
 struct TileDev {
-    int solve, mesh, i0, j0, tj;
-    unsigned admit;
+    int solve, mesh, i0, j0, tj, pad;
+    unsigned* counter;
     StepMaps* maps[2];
 };
 
-// Step launch arguments.  Two forms: a uniform launch (every solve on one
-// mesh with the same flow; grid = (tiles_j, tiles_i, solves); mesh and solve 0
-// are kernel parameters and solve b's buffers are b strides further), and a
-// table launch (uneven batch; one CTA per entry of the tile table, descriptors
-// in device memory).
 struct StepArgs {
     MeshDev umesh;                 // uniform launch: the mesh
     SolveDev usol;                 // uniform launch: solve 0 (others by stride)
@@ -116,8 +111,6 @@ struct StepArgs {
     const TileDev* tiles;
     int ntiles;
     int collide_only;              // 1: write the collided current state to fpost/gpost only
-    unsigned* launch_no;           // device launch counter, advanced by the grid's last CTA
-    unsigned* grid_done;           // grid completion counter (zero between launches)
     unsigned* status;
 };
 

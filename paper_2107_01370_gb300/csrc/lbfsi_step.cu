@@ -10,12 +10,11 @@
 // *current* step, Sec. II C) use the moment field written by the previous
 // launch, so the whole step is one kernel with no grid-wide dependency:
 //
-//   prologue   per-body RK4 with the loads of step k (Sec. III B), redundantly
-//              in every CTA (identical, deterministic), and the blended maps
-//              of steps k and k+1 (Sec. II D)
+//   prologue   the solve's step number; the blended maps of steps k and k+1
+//              (Sec. II D), built by the previous launch
 //   phase 1    stage M^k of the tile +-4 nodes, the per-row / per-column
 //              geometry, and the populations of the tile +-2 nodes (as (f, g)
-//              pairs) in shared memory
+//              pairs) in shared memory, all as asynchronous copies
 //   phase 2    correction fields: dQ on +-4, D = (mu/p) d(dQ) on +-3 (FE
 //              gradients, Eq. ddx+fem, mapped by g^{-1}), collision of the
 //              +-2 region in place (Eq. f_boltz)
@@ -26,6 +25,8 @@
 //              field nodes take equilibria at their targets; write the
 //              populations and M^{k+1}; wall nodes add their share of the
 //              force and moment (Sec. III) into a per-CTA partial.
+//   epilogue   the last CTA of each solve reduces the partials and advances
+//              the body by RK4 (Sec. III B) into the next launch's maps.
 //
 // The redundant work is the collision of the 2-node halo; the HBM traffic per
 // node is the 18 populations read and written once plus the 4-value moment
@@ -67,11 +68,6 @@ constexpr size_t step_smem_bytes() {
     using T = Tile<TI, TJ>;
     return sizeof(R) * (size_t)(18 * T::PS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
                                 T::MH * RS + T::MW * CS);
-}
-
-__device__ __forceinline__ int wrapj(int j, int nt) {
-    j %= nt;
-    return j < 0 ? j + nt : j;
 }
 
 // Derivative along an index direction of the 1-D quadratic Lagrange interpolant
@@ -171,17 +167,35 @@ __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F0
     G[3] = i01 * j01 + i11 * j11;
 }
 
-// Asynchronous 4- or 8-byte copy global -> shared (cp.async, L2-only path).
-__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+// Asynchronous 4- or 8-byte copy global -> shared (cp.async): no register
+// round trip, so every copy of the tile is in flight at once.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async(double* dst, const double* src) {
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async(float* dst, const float* src) { cp_async4(dst, src); }
+__device__ __forceinline__ void cp_async(double* dst, const double* src) { cp_async8(dst, src); }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+// A record of 4-byte words copied by the 32 lanes of one warp.
+__device__ __forceinline__ void cp_async_words(void* dst, const void* src, int words, int lane) {
+    for (int q = lane; q < words; q += 32)
+        cp_async4(static_cast<unsigned*>(dst) + q, static_cast<const unsigned*>(src) + q);
+}
+
+// Angular index modulo nt (the tile's halo may wrap more than once on very
+// coarse rings).
+__device__ __forceinline__ int wrap_nt(int j, int nt) {
+    if ((unsigned)j >= (unsigned)nt) {
+        j %= nt;
+        if (j < 0) j += nt;
+    }
+    return j;
 }
 
 template <typename R>
@@ -252,113 +266,95 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     __shared__ BodyMap<R> mapK, mapS;
     __shared__ BodyMap<double> mapSd;
     __shared__ double s_red[3][TJ];
-    __shared__ int s_jw[T::MW];                     // wrapped angular index of each M column
-    __shared__ TileDev s_tile;
     __shared__ SolveDev s_sol;
     __shared__ MeshDev s_mesh;
-    __shared__ int s_cur, s_mode;
 
-    const int tid = threadIdx.x;
-    // ---- prologue: this CTA's tile; the solve's current buffer and mode
-    // from the launch number; the maps of this launch (built by the previous
-    // launch's epilogue); for a table launch also the solve and mesh records.
-    // Records are copied word by word by separate warps.
-    {
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+    // ---- prologue: this CTA's tile and solve; the solve's step number k
+    // (current buffer k & 1; k == 0 streams the initial state without
+    // colliding).  Every thread reads what it needs to address its copies
+    // itself, so the whole staging below is one batch of asynchronous copies
+    // and one barrier.
+    int sb, i0, j0, tjx, nr, nt, N;
+    const SolveDev* sg = nullptr;   // table launch: the solve and mesh records
+    const MeshDev* mg = nullptr;
+    unsigned* ctr;
+    StepMaps* const* mptr;
+    if constexpr (UNIFORM) {
+        sb = (int)blockIdx.z;
+        tjx = (int)blockIdx.x;
+        j0 = tjx * TJ;
+        i0 = (int)blockIdx.y * TI;
+        nr = a.umesh.nr; nt = a.umesh.nt; N = a.umesh.N;
+        ctr = a.usol.counter + 2 * sb;
+        mptr = a.usol.maps;
+    } else {
         const TileDev* tg = a.tiles + blockIdx.x;
-        const unsigned admit = UNIFORM ? a.usol.admit : tg->admit;
-        const unsigned k = __ldcg(a.launch_no) - admit;
-        const int cur0 = (int)(k & 1u);
-        if (tid == 0) {
-            if (!UNIFORM) s_tile = *tg;
-            s_cur = cur0;
-            s_mode = a.collide_only ? MODE_COLLIDE_ONLY : (k == 0u ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM);
-        }
-        const int w = tid >> 5, l = tid & 31;
-        if (!UNIFORM && w == 1) {
-            const unsigned* src = reinterpret_cast<const unsigned*>(a.solves + tg->solve);
-            unsigned* dst = reinterpret_cast<unsigned*>(&s_sol);
-            for (int q = l; q < (int)(sizeof(SolveDev) / 4); q += 32) dst[q] = src[q];
-        } else if (!UNIFORM && w == 2) {
-            const unsigned* src = reinterpret_cast<const unsigned*>(a.meshes + tg->mesh);
-            unsigned* dst = reinterpret_cast<unsigned*>(&s_mesh);
-            for (int q = l; q < (int)(sizeof(MeshDev) / 4); q += 32) dst[q] = src[q];
-        } else if (w == 3 || w == 4 || w == 5) {
-            const StepMaps* mi = UNIFORM ? a.usol.maps[cur0] + blockIdx.z : tg->maps[cur0];
-            const void* srcv;
-            void* dstv;
-            int words;
-            if (w == 5) {
-                srcv = &mi->Sd;
-                dstv = &mapSd;
-                words = (int)(sizeof(BodyMap<double>) / 4);
-            } else {
-                if constexpr (sizeof(R) == 4)
-                    srcv = (w == 3) ? (const void*)&mi->Kf : (const void*)&mi->Sf;
-                else
-                    srcv = (w == 3) ? (const void*)&mi->Kd : (const void*)&mi->Sd;
-                dstv = (w == 3) ? (void*)&mapK : (void*)&mapS;
-                words = (int)(sizeof(BodyMap<R>) / 4);
-            }
-            const unsigned* src = reinterpret_cast<const unsigned*>(srcv);
-            unsigned* dst = reinterpret_cast<unsigned*>(dstv);
-            for (int q = l; q < words; q += 32) dst[q] = src[q];
-        }
+        sb = 0;
+        tjx = tg->tj; j0 = tg->j0; i0 = tg->i0;
+        sg = a.solves + tg->solve;
+        mg = a.meshes + tg->mesh;
+        nr = mg->nr; nt = mg->nt; N = mg->N;
+        ctr = tg->counter;
+        mptr = tg->maps;
     }
-    __syncthreads();
+    const unsigned kstep = __ldcg(ctr + 1);
+    const int cur = (int)(kstep & 1u);
+    const int mode = a.collide_only ? MODE_COLLIDE_ONLY : (kstep == 0u ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM);
+    {
+        const StepMaps* mi = (cur ? mptr[1] : mptr[0]) + sb;
+        if (!UNIFORM && w == 1) cp_async_words(&s_sol, sg, (int)(sizeof(SolveDev) / 4), l);
+        if (!UNIFORM && w == 2) cp_async_words(&s_mesh, mg, (int)(sizeof(MeshDev) / 4), l);
+        if (w == 3) {
+            if constexpr (sizeof(R) == 4) cp_async_words(&mapK, &mi->Kf, (int)(sizeof(BodyMap<R>) / 4), l);
+            else cp_async_words(&mapK, &mi->Kd, (int)(sizeof(BodyMap<R>) / 4), l);
+        }
+        if (w == 4) {
+            if constexpr (sizeof(R) == 4) cp_async_words(&mapS, &mi->Sf, (int)(sizeof(BodyMap<R>) / 4), l);
+            else cp_async_words(&mapS, &mi->Sd, (int)(sizeof(BodyMap<R>) / 4), l);
+        }
+        if (w == 5) cp_async_words(&mapSd, &mi->Sd, (int)(sizeof(BodyMap<double>) / 4), l);
+    }
     // solve / mesh fields: kernel parameters for a uniform launch, the copied
-    // records for a table launch
+    // records for a table launch (valid after the staging barrier)
 #define SD(x) (UNIFORM ? a.usol.x : s_sol.x)
 #define MD(x) (UNIFORM ? a.umesh.x : s_mesh.x)
-    const int cur = s_cur, mode = s_mode;
-    const int sb = UNIFORM ? (int)blockIdx.z : 0;   // solve index within a uniform launch
-    const int j0 = UNIFORM ? (int)blockIdx.x * TJ : s_tile.j0;
-    const int i0 = UNIFORM ? (int)blockIdx.y * TI : s_tile.i0;
-    const int nr = MD(nr), nt = MD(nt), N = MD(N);
-    const size_t o9 = UNIFORM ? (size_t)sb * 9 * N : 0, o4 = UNIFORM ? (size_t)sb * 4 * N : 0;
-    const R* __restrict__ f_in = reinterpret_cast<const R*>(SD(f[cur])) + o9;
-    const R* __restrict__ g_in = reinterpret_cast<const R*>(SD(g[cur])) + o9;
-    R* __restrict__ f_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(fpost) : SD(f[cur ^ 1])) + o9;
-    R* __restrict__ g_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(gpost) : SD(g[cur ^ 1])) + o9;
-    const R* __restrict__ M_in = reinterpret_cast<const R*>(SD(M[cur])) + o4;
-    R* __restrict__ M_out = reinterpret_cast<R*>(SD(M[cur ^ 1])) + o4;
-    const R* __restrict__ rowtab = reinterpret_cast<const R*>(MD(rowtab));
-    const R* __restrict__ coltab = reinterpret_cast<const R*>(MD(coltab));
-    const R dt = pick<R>(SD(dt), SD(dt_f)), mu = pick<R>(SD(mu), SD(mu_f)), Cv = pick<R>(SD(Cv), SD(Cv_f));
-    const R Pr = pick<R>(SD(Pr), SD(Pr_f)), iPr = pick<R>(1.0 / SD(Pr), SD(iPr_f));
-    const R xm = pick<R>(MD(xm), MD(xm_f)), ym = pick<R>(MD(ym), MD(ym_f));
-    const bool collide = mode != MODE_STREAM_ONLY;
-    const bool stream = mode != MODE_COLLIDE_ONLY;
+    const size_t o9 = (size_t)sb * 9 * N, o4 = (size_t)sb * 4 * N;
+    const void* fsrc = UNIFORM ? (cur ? a.usol.f[1] : a.usol.f[0]) : sg->f[cur];
+    const void* gsrc = UNIFORM ? (cur ? a.usol.g[1] : a.usol.g[0]) : sg->g[cur];
+    const void* Msrc = UNIFORM ? (cur ? a.usol.M[1] : a.usol.M[0]) : sg->M[cur];
+    const R* __restrict__ f_in = reinterpret_cast<const R*>(fsrc) + o9;
+    const R* __restrict__ g_in = reinterpret_cast<const R*>(gsrc) + o9;
+    const R* __restrict__ M_in = reinterpret_cast<const R*>(Msrc) + o4;
+    const R* __restrict__ rowtab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.rowtab : mg->rowtab);
+    const R* __restrict__ coltab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.coltab : mg->coltab);
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
-    for (int t = tid; t < T::MW; t += NT) s_jw[t] = wrapj(mj0 + t, nt);
+    const int pi0 = i0 - T::HP, pj0 = j0 - T::HP;   // global index of sp entry (0,0)
+
+    // ---- phase 1: stage the geometry tables, M^k and the populations ------
     for (int t = tid; t < T::MH * ROWTAB; t += NT) {
         const int li = t / ROWTAB, c = t - li * ROWTAB;
         const int i = min(max(mi0 + li, 0), nr - 1);
-        srow[li * RS + c] = rowtab[i * ROWTAB + c];
+        cp_async(srow + li * RS + c, rowtab + i * ROWTAB + c);
     }
-    __syncthreads();
     for (int t = tid; t < T::MW * COLTAB; t += NT) {
         const int lj = t / COLTAB, c = t - lj * COLTAB;
-        scol[lj * CS + c] = coltab[s_jw[lj] * COLTAB + c];
+        cp_async(scol + lj * CS + c, coltab + wrap_nt(mj0 + lj, nt) * COLTAB + c);
     }
-
-    // ---- phase 1: stage M^k and the populations ---------------------------
-    // asynchronous copies global -> shared (no register round trip), all in
-    // flight together, one wait before the barrier
     for (int idx = tid; idx < T::MS; idx += NT) {
         const int li = idx / T::MW, lj = idx - li * T::MW;
         const int i = mi0 + li;
         if (i >= 0 && i < nr) {
-            const int n = i * nt + s_jw[lj];
+            const int n = i * nt + wrap_nt(mj0 + lj, nt);
 #pragma unroll
             for (int c = 0; c < 4; ++c) cp_async(sM + c * T::MS + idx, M_in + (size_t)c * N + n);
         }
     }
-    const int pi0 = i0 - T::HP, pj0 = j0 - T::HP;
     for (int idx = tid; idx < T::PS; idx += NT) {
         const int li = idx / T::PW, lj = idx - li * T::PW;
         const int i = pi0 + li;
         if (i >= 0 && i < nr) {
-            const int n = i * nt + s_jw[lj + (T::HM - T::HP)];
+            const int n = i * nt + wrap_nt(pj0 + lj, nt);
             R* dst = reinterpret_cast<R*>(sp + idx * 9);
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
@@ -369,6 +365,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     }
     cp_async_wait_all();
     __syncthreads();
+    R* __restrict__ f_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(fpost) : SD(f[cur ^ 1])) + o9;
+    R* __restrict__ g_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(gpost) : SD(g[cur ^ 1])) + o9;
+    R* __restrict__ M_out = reinterpret_cast<R*>(SD(M[cur ^ 1])) + o4;
+    const R dt = pick<R>(SD(dt), SD(dt_f)), mu = pick<R>(SD(mu), SD(mu_f)), Cv = pick<R>(SD(Cv), SD(Cv_f));
+    const R Pr = pick<R>(SD(Pr), SD(Pr_f)), iPr = pick<R>(1.0 / SD(Pr), SD(iPr_f));
+    const R xm = pick<R>(MD(xm), MD(xm_f)), ym = pick<R>(MD(ym), MD(ym_f));
+    const bool collide = mode != MODE_STREAM_ONLY;
+    const bool stream = mode != MODE_COLLIDE_ONLY;
 
     // ---- phase 2: correction fields and collision of step k --------------
     if (collide) {
@@ -651,41 +655,47 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 s1 += s_red[1][t];
                 s2 += s_red[2][t];
             }
-            double* po = SD(part) + (size_t)sb * MD(ntj) * 3 + (size_t)(UNIFORM ? (int)blockIdx.x : s_tile.tj) * 3;
+            double* po = SD(part) + (size_t)sb * MD(ntj) * 3 + (size_t)tjx * 3;
             po[0] = s0;
             po[1] = s1;
             po[2] = s2;
         }
     }
-    if (tid == 0) {
+    if (w == 0) {
         // ---- epilogue: the last CTA of this solve sums the load partials in a
         // fixed order, advances the body by RK4 (Sec. III B, weak coupling:
-        // load of this step held over the next) and builds the next launch's
-        // maps; the last CTA of the grid advances the launch number.
-        __threadfence();
-        unsigned* counter = SD(counter) + sb;
+        // load of this step held over the next), builds the next launch's
+        // maps and advances the solve's step number.  The acquire-release
+        // count publishes this CTA's partial (written by thread 0) and, for
+        // the last CTA, makes every other CTA's partial visible.
         const unsigned ntiles = UNIFORM ? gridDim.x * gridDim.y : (unsigned)s_sol.ntiles;
-        const unsigned done = atomicAdd(counter, 1u);
+        unsigned done = 0u;
+        if (l == 0)
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(done) : "l"(ctr) : "memory");
+        done = __shfl_sync(0xffffffffu, done, 0);
         if (done == ntiles - 1u) {
-            __threadfence();
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             const int ntj = MD(ntj);
             const double* part = SD(part) + (size_t)sb * ntj * 3;
+            // lane t holds the partials of tiles t, t + 32, ...; the sum runs
+            // over lanes in order (for ntj <= 32: tile order)
+            double v[3] = {0.0, 0.0, 0.0};
+            for (int t = l; t < ntj; t += 32)
+                for (int c = 0; c < 3; ++c) v[c] += __ldcg(part + (size_t)t * 3 + c);
             double F[3] = {0.0, 0.0, 0.0};
-            for (int t = 0; t < ntj; ++t)
-                for (int c = 0; c < 3; ++c) F[c] += __ldcg(part + (size_t)t * 3 + c);
-            const BodyDev bd = *(SD(body) + sb);
-            const StepMaps& mi = *(SD(maps[cur]) + sb);
-            const BodyStateDev Snew = rk4_body(bd, mi.S_next, F[1], F[2], SD(dt));
-            StepMaps mo;
-            build_maps(bd, mi.S_next, Snew, mi.S_next, SD(dt), mo);
-            for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
-            *(SD(maps[cur ^ 1]) + sb) = mo;
-            *counter = 0u;
-        }
-        const unsigned gd = atomicAdd(a.grid_done, 1u);
-        if (gd == gridDim.x * gridDim.y * gridDim.z - 1u) {
-            *a.grid_done = 0u;
-            atomicAdd(a.launch_no, 1u);
+            for (int t = 0; t < 32; ++t)
+                for (int c = 0; c < 3; ++c) F[c] += __shfl_sync(0xffffffffu, v[c], t);
+            if (l == 0) {
+                const BodyDev bd = *(SD(body) + sb);
+                const BodyStateDev Sn = ((cur ? mptr[1] : mptr[0]) + sb)->S_next;
+                const BodyStateDev Snew = rk4_body(bd, Sn, F[1], F[2], SD(dt));
+                StepMaps mo;
+                build_maps(bd, Sn, Snew, Sn, SD(dt), mo);
+                for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
+                *((cur ? mptr[0] : mptr[1]) + sb) = mo;
+                ctr[0] = 0u;
+                ctr[1] = kstep + 1u;
+            }
         }
     }
 }
