@@ -111,6 +111,7 @@ struct StepArgs {
     const TileDev* tiles;
     int ntiles;
     int collide_only;              // 1: write the collided current state to fpost/gpost only
+    int pf_dist;                   // uniform launch: L2 prefetch distance in CTAs (set by the launcher)
     unsigned* status;
 };
 

@@ -363,6 +363,30 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
         }
     }
+    if constexpr (UNIFORM) {
+        // L2 prefetch of the tile that the CTA one resident wave later will
+        // stage (CTAs start in linear block order): its populations and
+        // moments move from HBM while this CTA computes, so its staging hits
+        // L2.  Two line addresses per row segment cover a segment that
+        // straddles lines; the prefetch is a hint and changes no result.
+        const unsigned nx = gridDim.x, ny = gridDim.y;
+        const unsigned lin = blockIdx.x + nx * (blockIdx.y + ny * blockIdx.z) + (unsigned)a.pf_dist;
+        if (a.pf_dist > 0 && lin < nx * ny * gridDim.z) {
+            const int xn = (int)(lin % nx), yn = (int)((lin / nx) % ny), zn = (int)(lin / (nx * ny));
+            const int jb = xn * TJ;
+            const int len = min(TJ, nt - jb);
+            for (int t = tid; t < 2 * 22 * TI; t += NT) {
+                const int c = t / (2 * TI), r = (t >> 1) % TI, end = t & 1;
+                const int i = yn * TI + r;
+                if (i >= nr) continue;
+                const size_t off = (size_t)i * nt + jb + (end ? len - 1 : 0);
+                const R* base = c < 9 ? reinterpret_cast<const R*>(fsrc) + ((size_t)zn * 9 + c) * N
+                              : c < 18 ? reinterpret_cast<const R*>(gsrc) + ((size_t)zn * 9 + c - 9) * N
+                                       : reinterpret_cast<const R*>(Msrc) + ((size_t)zn * 4 + c - 18) * N;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+            }
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
     R* __restrict__ f_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(fpost) : SD(f[cur ^ 1])) + o9;
@@ -762,8 +786,19 @@ static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) 
         configured = true;
     }
     if (UNIFORM) {
+        // prefetch distance: the CTAs resident on the whole GPU at once
+        static int resident = -1;
+        if (resident < 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<R, TI, TJ, NT, MINB, UNIFORM>, NT, smem);
+            resident = sms * per_sm;
+        }
+        StepArgs b = a;
+        b.pf_dist = resident;
         const dim3 grid(a.umesh.ntj, (a.umesh.nr + TI - 1) / TI, nbatch);
-        k_step<R, TI, TJ, NT, MINB, UNIFORM><<<grid, NT, smem, s>>>(a);
+        k_step<R, TI, TJ, NT, MINB, UNIFORM><<<grid, NT, smem, s>>>(b);
     } else {
         k_step<R, TI, TJ, NT, MINB, UNIFORM><<<a.ntiles, NT, smem, s>>>(a);
     }
