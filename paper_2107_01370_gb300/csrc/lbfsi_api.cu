@@ -43,11 +43,9 @@ struct lbfsi_mesh_s {
     size_t esize = 8;
     cudaStream_t stream = nullptr;
     std::vector<lbfsi_body_desc> bodies;
-    void* d_f[2] = {nullptr, nullptr};
-    void* d_g[2] = {nullptr, nullptr};
+    void* d_p[2] = {nullptr, nullptr};   // populations, (f_q, g_q) pairs [nbatch][9][N]
     void* d_M[2] = {nullptr, nullptr};
-    void* d_fpost = nullptr;
-    void* d_gpost = nullptr;
+    void* d_ppost = nullptr;             // collide-only output, same layout
     double* d_stage = nullptr;  // [nbatch][4][N] float64 staging
     StepMaps* d_maps[2] = {nullptr, nullptr};  // [nbatch] each
     BodyStateDev* d_state_a = nullptr;          // host-given states staging
@@ -126,8 +124,7 @@ int upload(lbfsi_mesh m, const double* host, void* ddst, size_t n) {
 }
 
 void free_all(lbfsi_mesh m) {
-    void* ptrs[] = {m->d_f[0], m->d_f[1], m->d_g[0], m->d_g[1], m->d_M[0], m->d_M[1], m->d_fpost,
-                    m->d_gpost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
+    void* ptrs[] = {m->d_p[0], m->d_p[1], m->d_M[0], m->d_M[1], m->d_ppost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
                     m->d_loads_tmp, m->d_part, m->d_counter, m->d_bodies, m->d_meshdev, m->d_solves,
                     m->d_tiles, m->d_status};
     for (void* p : ptrs)
@@ -144,13 +141,11 @@ int upload_solves(lbfsi_mesh m) {
         s.mesh = 0;
         s.ntiles = m->tiles_per_solve;
         for (int p = 0; p < 2; ++p) {
-            s.f[p] = (char*)m->d_f[p] + (size_t)b * 9 * N * es;
-            s.g[p] = (char*)m->d_g[p] + (size_t)b * 9 * N * es;
+            s.p[p] = (char*)m->d_p[p] + (size_t)b * 18 * N * es;
             s.M[p] = (char*)m->d_M[p] + (size_t)b * 4 * N * es;
             s.maps[p] = m->d_maps[p] + b;
         }
-        s.fpost = m->d_fpost ? (char*)m->d_fpost + (size_t)b * 9 * N * es : nullptr;
-        s.gpost = m->d_gpost ? (char*)m->d_gpost + (size_t)b * 9 * N * es : nullptr;
+        s.ppost = m->d_ppost ? (char*)m->d_ppost + (size_t)b * 18 * N * es : nullptr;
         s.part = m->d_part + (size_t)b * m->host.ntj * 3;
         s.counter = m->d_counter + 2 * b;
         s.body = m->d_bodies + b;
@@ -260,8 +255,7 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     LB_ALLOC(m->d_status, 1);
 #undef LB_ALLOC
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMalloc(&m->d_f[k], nb * 9 * N * m->esize);
-        if (e == cudaSuccess) e = cudaMalloc(&m->d_g[k], nb * 9 * N * m->esize);
+        e = cudaMalloc(&m->d_p[k], nb * 18 * N * m->esize);
         if (e == cudaSuccess) e = cudaMalloc(&m->d_M[k], nb * 4 * N * m->esize);
     }
     if (e != cudaSuccess) {
@@ -328,7 +322,7 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     m->host_k = 0;
     rc = upload_solves(m);
     if (rc) return rc;
-    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_f[0], m->d_g[0], m->d_M[0], m->host.N, m->nbatch,
+    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_p[0], m->d_M[0], m->host.N, m->nbatch,
                            proto.Cv, m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
@@ -450,13 +444,11 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
     if (which != 0 && which != 1) return fail(LBFSI_EINVAL, "which must be 0 or 1");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     const size_t cnt = (size_t)m->nbatch * 9 * m->host.N;
-    const void* fs = m->d_f[m->cur()];
-    const void* gs = m->d_g[m->cur()];
+    const void* ps = m->d_p[m->cur()];
     if (which == 1 && !m->first()) {
         cudaError_t e = cudaSuccess;
-        if (!m->d_fpost) {
-            e = cudaMalloc(&m->d_fpost, cnt * m->esize);
-            if (e == cudaSuccess) e = cudaMalloc(&m->d_gpost, cnt * m->esize);
+        if (!m->d_ppost) {
+            e = cudaMalloc(&m->d_ppost, 2 * cnt * m->esize);
             if (e != cudaSuccess) return fail(LBFSI_ENOMEM, "post-collision staging allocation failed");
             const int rc = upload_solves(m);
             if (rc) return rc;
@@ -464,13 +456,15 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
         e = lbfsi::launch_step_uniform(make_args(m, 1), m->precision, m->variant, m->nbatch, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "collide kernel launch");
-        fs = m->d_fpost;
-        gs = m->d_gpost;
+        ps = m->d_ppost;
     }
-    int rc = download(m, fs, f, cnt);
+    std::vector<double> pairs(2 * cnt);
+    int rc = download(m, ps, pairs.data(), 2 * cnt);
     if (rc) return rc;
-    rc = download(m, gs, g, cnt);
-    if (rc) return rc;
+    for (size_t k = 0; k < cnt; ++k) {
+        f[k] = pairs[2 * k];
+        g[k] = pairs[2 * k + 1];
+    }
     return check_status(m);
 }
 
@@ -479,8 +473,12 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const 
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     const size_t cnt = (size_t)m->nbatch * 9 * m->host.N;
     const int c = m->cur();
-    int rc = upload(m, f, m->d_f[c], cnt);
-    if (!rc) rc = upload(m, g, m->d_g[c], cnt);
+    std::vector<double> pairs(2 * cnt);
+    for (size_t k = 0; k < cnt; ++k) {
+        pairs[2 * k] = f[k];
+        pairs[2 * k + 1] = g[k];
+    }
+    int rc = upload(m, pairs.data(), m->d_p[c], 2 * cnt);
     if (!rc) rc = upload(m, rho_u_T, m->d_M[c], (size_t)m->nbatch * 4 * m->host.N);
     if (rc) return rc;
     // the restored state is post-propagation: make the next launch collide it

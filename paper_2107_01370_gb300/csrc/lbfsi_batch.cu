@@ -335,8 +335,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     };
     bool ok = true;
     for (int p = 0; p < 2 && ok; ++p) {
-        ok = ok && (sd.f[p] = take(9 * N * es)) != nullptr;
-        ok = ok && (sd.g[p] = take(9 * N * es)) != nullptr;
+        ok = ok && (sd.p[p] = take(18 * N * es)) != nullptr;
         ok = ok && (sd.M[p] = take(4 * N * es)) != nullptr;
         ok = ok && (sd.maps[p] = (StepMaps*)take(sizeof(StepMaps))) != nullptr;
     }
@@ -354,7 +353,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     sd.body = body;
     sd.mesh = mk;
     sd.ntiles = ((h.nr + b->tile_rows - 1) / b->tile_rows) * h.ntj;
-    sd.fpost = sd.gpost = nullptr;
+    sd.ppost = nullptr;
     // initial state: equilibria of the initial field, bodies at rest
     std::vector<double> M(4 * N);
     if (d->rho_u_T) {
@@ -371,7 +370,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     cudaError_t e = cudaMemcpyAsync(stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(body, &bd, sizeof(BodyDev), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sd.counter, 0, 2 * sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = lbfsi::launch_init(b->precision, stage, sd.f[0], sd.g[0], sd.M[0], (int)N, 1, sd.Cv, b->stream);
+    if (e == cudaSuccess) e = lbfsi::launch_init(b->precision, stage, sd.p[0], sd.M[0], (int)N, 1, sd.Cv, b->stream);
     if (e == cudaSuccess)
         e = lbfsi::launch_prepare(body, b->d_zero_state, b->d_zero_state, b->d_zero_state, b->d_zero_loads, sd.dt,
                                   1, sd.maps[0], b->stream);

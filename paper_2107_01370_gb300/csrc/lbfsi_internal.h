@@ -83,12 +83,10 @@ struct SolveDev {
     // converts or divides in float64)
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
     float dt_f, mu_f, Cv_f, Pr_f, iPr_f, rho_inf_f, uinf_x_f, uinf_y_f, T_inf_f, pad_f;
-    void* f[2];
-    void* g[2];
-    void* M[2];
+    void* p[2];                    // populations, (f_q, g_q) pairs [9][N]
+    void* M[2];                    // moments [4][N]
     StepMaps* maps[2];
-    void* fpost;                   // collide-only output (post-collision populations)
-    void* gpost;
+    void* ppost;                   // collide-only output (post-collision pairs)
     double* part;                  // [ntj][3] load partials of the streamed step
     unsigned* counter;             // [2]: CTA completion count, step number k
     const BodyDev* body;
@@ -128,8 +126,8 @@ cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, i
 int tile_rows(int precision, int variant);
 constexpr int TILE_J = 32;
 inline int tiles_j(int nt) { return (nt + TILE_J - 1) / TILE_J; }
-cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* Mout, int N,
-                        int nbatch, double Cv, cudaStream_t s);
+cudaError_t launch_init(int precision, const double* M, void* P, void* Mout, int N, int nbatch,
+                        double Cv, cudaStream_t s);
 // Build the maps record from explicit states: S_cur (collision), S_next and
 // S_vgprev (stream); loads copied from 'loads' if non-null.
 cudaError_t launch_prepare(const BodyDev* bodies, const BodyStateDev* S_cur,

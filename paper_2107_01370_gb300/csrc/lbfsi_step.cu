@@ -13,8 +13,8 @@
 //   prologue   the solve's step number; the blended maps of steps k and k+1
 //              (Sec. II D), built by the previous launch
 //   phase 1    stage M^k of the tile +-4 nodes, the per-row / per-column
-//              geometry, and the populations of the tile +-2 nodes (as (f, g)
-//              pairs) in shared memory, all as asynchronous copies
+//              geometry, and the populations of the tile +-2 nodes in shared
+//              memory, all as 16-byte asynchronous copies
 //   phase 2    correction fields: dQ on +-4, D = (mu/p) d(dQ) on +-3 (FE
 //              gradients, Eq. ddx+fem, mapped by g^{-1}), collision of the
 //              +-2 region in place (Eq. f_boltz)
@@ -28,9 +28,11 @@
 //   epilogue   the last CTA of each solve reduces the partials and advances
 //              the body by RK4 (Sec. III B) into the next launch's maps.
 //
-// The redundant work is the collision of the 2-node halo; the HBM traffic per
-// node is the 18 populations read and written once plus the 4-value moment
-// field.
+// Populations are kept in HBM as (f_q, g_q) pairs, [q][node] (both share the
+// departure point and the interpolation weights), so staging moves 16-byte
+// chunks and the stream writes one 64-bit pair per direction.  The redundant
+// work is the collision of the 2-node halo; the HBM traffic per node is the
+// 18 populations read and written once plus the 4-value moment field.
 #include <cstdio>
 
 #include "lbfsi_device.cuh"
@@ -42,6 +44,9 @@ template <int TI, int TJ>
 struct Tile {
     static constexpr int HP = 2, HD = 3, HM = 4;
     static constexpr int PH = TI + 2 * HP, PW = TJ + 2 * HP, PS = PH * PW;
+    // staged populations: rows of PWS nodes from j0 - 4 (16-byte aligned
+    // chunks), so the +-2 region starts at column 2 of a row
+    static constexpr int PWS = TJ + 8, PSS = PH * PWS, PC = 2;
     static constexpr int DH = TI + 2 * HD, DW = TJ + 2 * HD, DS = DH * DW;
     static constexpr int MH = TI + 2 * HM, MW = TJ + 2 * HM, MS = MH * MW;
     static constexpr int NT = TI * TJ;
@@ -66,7 +71,7 @@ constexpr int CS = COLTAB + 1;
 template <typename R, int TI, int TJ>
 constexpr size_t step_smem_bytes() {
     using T = Tile<TI, TJ>;
-    return sizeof(R) * (size_t)(18 * T::PS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
+    return sizeof(R) * (size_t)(18 * T::PSS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
                                 T::MH * RS + T::MW * CS);
 }
 
@@ -105,8 +110,8 @@ __device__ __forceinline__ void lagrange3(R t, R* L) {
 // constant xi are rings, so this choice is exact.
 //
 // NodeGeo holds the table entries of one node and, for the four candidate
-// cells (da, db) in {-1, 0}^2, the shared-memory offset of their element's
-// first node, so that the nine directions only select among them.
+// cells (da, db) in {-1, 0}^2, the shared-memory node offset of their
+// element's first node, so that the nine directions only select among them.
 template <typename R>
 struct NodeGeo {
     R ex, ey, ri;
@@ -117,7 +122,7 @@ struct NodeGeo {
 
 template <typename R>
 __device__ __forceinline__ void node_geo(int i, int j, int nr, const R* row, const R* col, int pi0,
-                                         int pj0, int PW, NodeGeo<R>& G) {
+                                         int sj0, int PWS, NodeGeo<R>& G) {
     G.ex = col[0];
     G.ey = col[1];
     G.ri = row[0];
@@ -127,10 +132,10 @@ __device__ __forceinline__ void node_geo(int i, int j, int nr, const R* row, con
     const int wa0 = min((max(i - 1, 0) >> 1) * 2, nr - 3);   // the wall row has no cell i-1
     const int wa1 = min((i >> 1) * 2, nr - 3);
     const int wb0 = ((j - 1) >> 1) * 2, wb1 = (j >> 1) * 2;
-    G.b00 = ((wa0 - pi0) * PW + (wb0 - pj0)) * 9;
-    G.b01 = ((wa0 - pi0) * PW + (wb1 - pj0)) * 9;
-    G.b10 = ((wa1 - pi0) * PW + (wb0 - pj0)) * 9;
-    G.b11 = ((wa1 - pi0) * PW + (wb1 - pj0)) * 9;
+    G.b00 = (wa0 - pi0) * PWS + (wb0 - sj0);
+    G.b01 = (wa0 - pi0) * PWS + (wb1 - sj0);
+    G.b10 = (wa1 - pi0) * PWS + (wb0 - sj0);
+    G.b11 = (wa1 - pi0) * PWS + (wb1 - sj0);
 }
 
 template <typename R>
@@ -177,6 +182,10 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async(float* dst, const float* src) { cp_async4(dst, src); }
 __device__ __forceinline__ void cp_async(double* dst, const double* src) { cp_async8(dst, src); }
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -209,9 +218,10 @@ __device__ __forceinline__ double pick<double>(double d, float) {
     return d;
 }
 
-// Q2 interpolation of one (f, g) pair over a 3x3 window: separable sums
-// t_a = sum_b L_b(eta) v(a, b), then sum_a L_a(xi) t_a (Eq. SemiLagrProp);
-// on the float path with packed two-wide FMAs (f and g share the weights).
+// Q2 interpolation of one (f, g) pair over a 3x3 window (rows rowstride
+// apart, columns adjacent): separable sums t_a = sum_b L_b(eta) v(a, b), then
+// sum_a L_a(xi) t_a (Eq. SemiLagrProp); on the float path with packed
+// two-wide FMAs (f and g share the weights).
 template <typename R2>
 __device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const float* Lx, const float* Ly);
 template <>
@@ -222,8 +232,8 @@ __device__ __forceinline__ float2 gather9<float2>(const float2* p, int rowstride
     for (int aa = 0; aa < 3; ++aa) {
         const float2* pr = p + aa * rowstride;
         float2 t = __fmul2_rn(make_float2(Ly[0], Ly[0]), pr[0]);
-        t = __ffma2_rn(make_float2(Ly[1], Ly[1]), pr[9], t);
-        t = __ffma2_rn(make_float2(Ly[2], Ly[2]), pr[18], t);
+        t = __ffma2_rn(make_float2(Ly[1], Ly[1]), pr[1], t);
+        t = __ffma2_rn(make_float2(Ly[2], Ly[2]), pr[2], t);
         acc = __ffma2_rn(make_float2(Lx[aa], Lx[aa]), t, acc);
     }
     return acc;
@@ -239,8 +249,8 @@ __device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const double* 
         double tx = 0.0, ty = 0.0;
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
-            tx += Ly[bb] * pr[9 * bb].x;
-            ty += Ly[bb] * pr[9 * bb].y;
+            tx += Ly[bb] * pr[bb].x;
+            ty += Ly[bb] * pr[bb].y;
         }
         acc.x += Lx[aa] * tx;
         acc.y += Lx[aa] * ty;
@@ -255,8 +265,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     constexpr int NPT = TI * TJ / NT;   // tile nodes streamed per thread
     static_assert(NPT * NT == TI * TJ && NT >= TJ && NT >= 192, "tile / thread count");
     extern __shared__ __align__(16) unsigned char smraw[];
-    R2* sp = reinterpret_cast<R2*>(smraw);          // [PS][9] (f_q, g_q) pairs
-    R* sM = reinterpret_cast<R*>(sp + 9 * T::PS);   // [4][MS]  rho, ux, uy, T of step k
+    R2* sp = reinterpret_cast<R2*>(smraw);          // [9][PH][PWS] (f_q, g_q) pairs
+    R* sM = reinterpret_cast<R*>(sp + 9 * T::PSS);  // [4][MS]  rho, ux, uy, T of step k
     R* sQ = sM + 4 * T::MS;                         // [2][MS]  dQ_x, dQ_y
     R* sG = sQ + 2 * T::MS;                         // [4][DS]  gradient maps
     R* sD = sG + 4 * T::DS;                         // [2][DS]  D_x, D_y
@@ -320,16 +330,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
 #define SD(x) (UNIFORM ? a.usol.x : s_sol.x)
 #define MD(x) (UNIFORM ? a.umesh.x : s_mesh.x)
     const size_t o9 = (size_t)sb * 9 * N, o4 = (size_t)sb * 4 * N;
-    const void* fsrc = UNIFORM ? (cur ? a.usol.f[1] : a.usol.f[0]) : sg->f[cur];
-    const void* gsrc = UNIFORM ? (cur ? a.usol.g[1] : a.usol.g[0]) : sg->g[cur];
+    const void* psrc = UNIFORM ? (cur ? a.usol.p[1] : a.usol.p[0]) : sg->p[cur];
     const void* Msrc = UNIFORM ? (cur ? a.usol.M[1] : a.usol.M[0]) : sg->M[cur];
-    const R* __restrict__ f_in = reinterpret_cast<const R*>(fsrc) + o9;
-    const R* __restrict__ g_in = reinterpret_cast<const R*>(gsrc) + o9;
+    const R2* __restrict__ p_in = reinterpret_cast<const R2*>(psrc) + o9;
     const R* __restrict__ M_in = reinterpret_cast<const R*>(Msrc) + o4;
     const R* __restrict__ rowtab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.rowtab : mg->rowtab);
     const R* __restrict__ coltab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.coltab : mg->coltab);
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
-    const int pi0 = i0 - T::HP, pj0 = j0 - T::HP;   // global index of sp entry (0,0)
+    const int pi0 = i0 - T::HP, sj0 = j0 - 4;       // global index of sp row 0, column 0
 
     // ---- phase 1: stage the geometry tables, M^k and the populations ------
     for (int t = tid; t < T::MH * ROWTAB; t += NT) {
@@ -341,25 +349,54 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const int lj = t / COLTAB, c = t - lj * COLTAB;
         cp_async(scol + lj * CS + c, coltab + wrap_nt(mj0 + lj, nt) * COLTAB + c);
     }
-    for (int idx = tid; idx < T::MS; idx += NT) {
-        const int li = idx / T::MW, lj = idx - li * T::MW;
-        const int i = mi0 + li;
-        if (i >= 0 && i < nr) {
-            const int n = i * nt + wrap_nt(mj0 + lj, nt);
+    // M^k in 16-byte chunks of consecutive columns (element-wise when Ntheta
+    // is not a multiple of the chunk); one thread per (row, chunk), the four
+    // components N apart
+    {
+        constexpr int CM = 16 / (int)sizeof(R), NCH = T::MW / CM;
+        const bool vec = nt % CM == 0;
+        for (int idx = tid; idx < T::MH * NCH; idx += NT) {
+            const int ch = idx % NCH, li = idx / NCH;
+            const int i = mi0 + li;
+            if (i < 0 || i >= nr) continue;
+            R* dst = sM + li * T::MW + ch * CM;
+            const R* src = M_in + (size_t)i * nt;
+            if (vec) {
+                src += wrap_nt(mj0 + ch * CM, nt);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) cp_async(sM + c * T::MS + idx, M_in + (size_t)c * N + n);
+                for (int c = 0; c < 4; ++c) cp_async16(dst + c * T::MS, src + (size_t)c * N);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int e = 0; e < CM; ++e)
+                        cp_async(dst + c * T::MS + e, src + (size_t)c * N + wrap_nt(mj0 + ch * CM + e, nt));
+            }
         }
     }
-    for (int idx = tid; idx < T::PS; idx += NT) {
-        const int li = idx / T::PW, lj = idx - li * T::PW;
-        const int i = pi0 + li;
-        if (i >= 0 && i < nr) {
-            const int n = i * nt + wrap_nt(pj0 + lj, nt);
-            R* dst = reinterpret_cast<R*>(sp + idx * 9);
+    // populations: rows of PWS (f, g) pairs per direction in 16-byte chunks
+    // (two float pairs or one double pair); one thread per (row, chunk), the
+    // nine directions N apart
+    {
+        constexpr int CP = 16 / (int)sizeof(R2), NCH = T::PWS / CP;
+        const bool vec = nt % CP == 0;
+        for (int idx = tid; idx < T::PH * NCH; idx += NT) {
+            const int ch = idx % NCH, li = idx / NCH;
+            const int i = pi0 + li;
+            if (i < 0 || i >= nr) continue;
+            R2* dst = sp + li * T::PWS + ch * CP;
+            const R2* src = p_in + (size_t)i * nt;
+            if (vec) {
+                src += wrap_nt(sj0 + ch * CP, nt);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                cp_async(dst + 2 * q, f_in + (size_t)q * N + n);
-                cp_async(dst + 2 * q + 1, g_in + (size_t)q * N + n);
+                for (int q = 0; q < 9; ++q) cp_async16(dst + q * T::PSS, src + (size_t)q * N);
+            } else {
+#pragma unroll
+                for (int e = 0; e < CP; ++e) {
+                    const R2* se = src + wrap_nt(sj0 + ch * CP + e, nt);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) cp_async8(dst + q * T::PSS + e, se + (size_t)q * N);
+                }
             }
         }
     }
@@ -367,30 +404,29 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // L2 prefetch of the tile that the CTA one resident wave later will
         // stage (CTAs start in linear block order): its populations and
         // moments move from HBM while this CTA computes, so its staging hits
-        // L2.  Two line addresses per row segment cover a segment that
-        // straddles lines; the prefetch is a hint and changes no result.
+        // L2.  The first and last address of every row segment cover its
+        // lines (a segment is at most two lines); the prefetch is a hint and
+        // changes no result.
         const unsigned nx = gridDim.x, ny = gridDim.y;
         const unsigned lin = blockIdx.x + nx * (blockIdx.y + ny * blockIdx.z) + (unsigned)a.pf_dist;
         if (a.pf_dist > 0 && lin < nx * ny * gridDim.z) {
             const int xn = (int)(lin % nx), yn = (int)((lin / nx) % ny), zn = (int)(lin / (nx * ny));
             const int jb = xn * TJ;
             const int len = min(TJ, nt - jb);
-            for (int t = tid; t < 2 * 22 * TI; t += NT) {
+            for (int t = tid; t < 2 * 13 * TI; t += NT) {
                 const int c = t / (2 * TI), r = (t >> 1) % TI, end = t & 1;
                 const int i = yn * TI + r;
                 if (i >= nr) continue;
                 const size_t off = (size_t)i * nt + jb + (end ? len - 1 : 0);
-                const R* base = c < 9 ? reinterpret_cast<const R*>(fsrc) + ((size_t)zn * 9 + c) * N
-                              : c < 18 ? reinterpret_cast<const R*>(gsrc) + ((size_t)zn * 9 + c - 9) * N
-                                       : reinterpret_cast<const R*>(Msrc) + ((size_t)zn * 4 + c - 18) * N;
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+                const void* ad = c < 9 ? (const void*)(reinterpret_cast<const R2*>(psrc) + ((size_t)zn * 9 + c) * N + off)
+                                       : (const void*)(reinterpret_cast<const R*>(Msrc) + ((size_t)zn * 4 + c - 9) * N + off);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(ad));
             }
         }
     }
     cp_async_wait_all();
     __syncthreads();
-    R* __restrict__ f_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(fpost) : SD(f[cur ^ 1])) + o9;
-    R* __restrict__ g_out = reinterpret_cast<R*>(mode == MODE_COLLIDE_ONLY ? SD(gpost) : SD(g[cur ^ 1])) + o9;
+    R2* __restrict__ p_out = reinterpret_cast<R2*>(mode == MODE_COLLIDE_ONLY ? SD(ppost) : SD(p[cur ^ 1])) + o9;
     R* __restrict__ M_out = reinterpret_cast<R*>(SD(M[cur ^ 1])) + o4;
     const R dt = pick<R>(SD(dt), SD(dt_f)), mu = pick<R>(SD(mu), SD(mu_f)), Cv = pick<R>(SD(Cv), SD(Cv_f));
     const R Pr = pick<R>(SD(Pr), SD(Pr_f)), iPr = pick<R>(1.0 / SD(Pr), SD(iPr_f));
@@ -438,6 +474,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
             const int i = pi0 + li;
             if (i < 0 || i >= nr) continue;
+            const int sn = li * T::PWS + lj + 2;   // staged node
             R f[9], g[9];
             if (i == nr - 1) {
                 const int m = (li + 2) * T::MW + (lj + 2);
@@ -446,7 +483,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             } else {
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    const R2 v = sp[idx * 9 + q];
+                    const R2 v = sp[q * T::PSS + sn];
                     f[q] = v.x;
                     g[q] = v.y;
                 }
@@ -462,7 +499,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R2 v;
                 v.x = f[q];
                 v.y = g[q];
-                sp[idx * 9 + q] = v;
+                sp[q * T::PSS + sn] = v;
             }
         }
         __syncthreads();
@@ -473,13 +510,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int i = i0 + ti, j = j0 + tj;
                 if (i < nr && j < nt) {
                     const int n = i * nt + j;
-                    const int p = (ti + T::HP) * T::PW + tj + T::HP;
+                    const int sn = (ti + T::HP) * T::PWS + tj + T::HP + 2;
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) {
-                        const R2 v = sp[p * 9 + q];
-                        f_out[(size_t)q * N + n] = v.x;
-                        g_out[(size_t)q * N + n] = v.y;
-                    }
+                    for (int q = 0; q < 9; ++q) p_out[(size_t)q * N + n] = sp[q * T::PSS + sn];
                 }
             }
             return;
@@ -517,8 +550,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             g_equilibrium(rho, ux, uy, Tt, Cv, g);
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                f_out[(size_t)q * N + n] = f[q];
-                g_out[(size_t)q * N + n] = g[q];
+                R2 v;
+                v.x = f[q];
+                v.y = g[q];
+                p_out[(size_t)q * N + n] = v;
             }
             M_out[n] = rho; M_out[(size_t)N + n] = ux; M_out[(size_t)2 * N + n] = uy;
             M_out[(size_t)3 * N + n] = Tt;
@@ -527,7 +562,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         R F00, F01, F10, F11, vx, vy;
         kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
         NodeGeo<R> geo;
-        node_geo(i, j, nr, row, col, pi0, pj0, T::PW, geo);
+        node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
         const R idF = rcp_(F00 * F11 - F01 * F10);
         const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
         unsigned missing = 0u;
@@ -562,12 +597,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R Lx[3], Ly[3];
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
-                const R2 v = gather9(sp + base + q, 9 * T::PW, Lx, Ly);
+                const R2 v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
                 f[q] = v.x;
                 g[q] = v.y;
             } else {
                 lost = true;
-                const R2 v = sp[((ti + T::HP) * T::PW + tj + T::HP) * 9 + q];
+                const R2 v = sp[q * T::PSS + (ti + T::HP) * T::PWS + tj + T::HP + 2];
                 f[q] = v.x;
                 g[q] = v.y;
             }
@@ -584,8 +619,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
                 // element origin in the staged tile -> in the moment tile
-                const int pn = base / 9;
-                const int wa = pn / T::PW + pi0, wb = pn - (pn / T::PW) * T::PW + pj0;
+                const int wa = base / T::PWS + pi0, wb = base - (base / T::PWS) * T::PWS + sj0;
                 const int w0 = (wa - mi0) * T::MW + (wb - mj0);
                 rhoB = R(0);
                 TB = R(0);
@@ -626,8 +660,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             atomicOr(a.status, ST_NONPHYS);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            f_out[(size_t)q * N + n] = f[q];
-            g_out[(size_t)q * N + n] = g[q];
+            R2 v;
+            v.x = f[q];
+            v.y = g[q];
+            p_out[(size_t)q * N + n] = v;
         }
         M_out[n] = mc.rho; M_out[(size_t)N + n] = mc.ux; M_out[(size_t)2 * N + n] = mc.uy;
         M_out[(size_t)3 * N + n] = mc.T;
@@ -729,7 +765,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
 
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_init(const double* __restrict__ M, R* __restrict__ f, R* __restrict__ g,
+__global__ void k_init(const double* __restrict__ M, typename Vec2<R>::T* __restrict__ P,
                        R* __restrict__ Mout, int N, int nbatch, double Cv) {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)N * nbatch) return;
@@ -740,8 +776,10 @@ __global__ void k_init(const double* __restrict__ M, R* __restrict__ f, R* __res
     f_equilibrium(rho, ux, uy, T, fe);
     g_equilibrium(rho, ux, uy, T, (R)Cv, ge);
     for (int q = 0; q < 9; ++q) {
-        f[(b * 9 + q) * N + n] = fe[q];
-        g[(b * 9 + q) * N + n] = ge[q];
+        typename Vec2<R>::T v;
+        v.x = fe[q];
+        v.y = ge[q];
+        P[(b * 9 + q) * N + n] = v;
     }
     for (int c = 0; c < 4; ++c) Mout[(b * 4 + c) * N + n] = (R)Mb[c * (size_t)N + n];
 }
@@ -834,15 +872,15 @@ int tile_rows(int precision, int variant) {
     }
 }
 
-cudaError_t launch_init(int precision, const double* M, void* f, void* g, void* Mout, int N,
-                        int nbatch, double Cv, cudaStream_t s) {
+cudaError_t launch_init(int precision, const double* M, void* P, void* Mout, int N, int nbatch,
+                        double Cv, cudaStream_t s) {
     const size_t total = (size_t)N * nbatch;
     const int bs = 256;
     const unsigned nb = (unsigned)((total + bs - 1) / bs);
     if (precision == 0)
-        k_init<double><<<nb, bs, 0, s>>>(M, (double*)f, (double*)g, (double*)Mout, N, nbatch, Cv);
+        k_init<double><<<nb, bs, 0, s>>>(M, (double2*)P, (double*)Mout, N, nbatch, Cv);
     else
-        k_init<float><<<nb, bs, 0, s>>>(M, (float*)f, (float*)g, (float*)Mout, N, nbatch, Cv);
+        k_init<float><<<nb, bs, 0, s>>>(M, (float2*)P, (float*)Mout, N, nbatch, Cv);
     return cudaGetLastError();
 }
 
