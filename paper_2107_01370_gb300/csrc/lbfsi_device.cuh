@@ -260,16 +260,16 @@ __host__ __device__ inline BodyMap<float> to_float(const BodyMap<double>& d) {
 
 // F = dx/dX of the blended map (analytic, includes the gradient of the blend
 // factor) and V_G at absolute position (X, Y).  Outside the blended region
-// F = I and V_G = 0 exactly.
+// F = I and V_G = 0 exactly, and the result is false.
 template <typename R>
-__device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F00, R& F01, R& F10,
+__device__ __forceinline__ bool kinematics(const BodyMap<R>& bm, R X, R Y, R& F00, R& F01, R& F10,
                                            R& F11, R& vx, R& vy) {
     F00 = R(1); F01 = R(0); F10 = R(0); F11 = R(1); vx = R(0); vy = R(0);
-    if (!bm.active) return;
+    if (!bm.active) return false;
     const R dx = X - bm.xc, dy = Y - bm.yc;
     const R dist = sqrt_(dx * dx + dy * dy);
     const R s = (dist - bm.r_in) * bm.inv_w;
-    if (s > R(1)) return;
+    if (s > R(1)) return false;
     R w, drx = R(0), dry = R(0);
     if (s < R(0)) {
         w = R(1);
@@ -290,6 +290,7 @@ __device__ __forceinline__ void kinematics(const BodyMap<R>& bm, R X, R Y, R& F0
     F11 = R(1) + w * bm.a11 - uy * dry;
     vx = w * (bm.va00 * px + bm.va01 * py + bm.vtx);
     vy = w * (bm.va10 * px + bm.va11 * py + bm.vty);
+    return true;
 }
 
 // Fill a maps record: collision map from S_cur, stream maps from

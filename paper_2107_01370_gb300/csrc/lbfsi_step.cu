@@ -34,6 +34,7 @@
 // work is the collision of the 2-node halo; the HBM traffic per node is the
 // 18 populations read and written once plus the 4-value moment field.
 #include <cstdio>
+#include <type_traits>
 
 #include "lbfsi_device.cuh"
 #include "lbfsi_internal.h"
@@ -148,6 +149,30 @@ __device__ __forceinline__ bool depart(const NodeGeo<R>& G, int i, R dx, R dy, i
     const R Ex = G.ex + s * dEx, Ey = G.ey + s * dEy;
     const R dR = (dx * Ex + dy * Ey - G.ri * s * (dEx * Ex + dEy * Ey)) * rcp_(Ex * Ex + Ey * Ey);
     const bool da = !(dR < R(0)) || i == 0;   // on the wall: round-off of a tangential departure
+    const R dxi = dR * (da ? G.idR1 : G.idR0);
+    xi = (da ? G.xin1 : G.xin0) + dxi;
+    eta = (db ? G.eta1 : G.eta0) + s;
+    base = da ? (db ? G.b11 : G.b10) : (db ? G.b01 : G.b00);
+    const R lim = R(1) + R(1e-4);
+    return abs_(s) <= lim && abs_(dxi) <= lim;
+}
+
+// The same solve for a node the blend does not move (g = I, V_G = 0), where
+// the displacement is the constant d = -dt c for the lattice velocity
+// c = (CX, CY): the products with d reduce to sums of table entries.
+template <int CX, int CY, typename R>
+__device__ __forceinline__ bool depart_static(const NodeGeo<R>& G, R dt, int& base, R& xi, R& eta) {
+    // e x c and dE x c for the two angular cells; d = -dt c
+    const R exc = (CY ? G.ex * R(CY) : R(0)) - (CX ? G.ey * R(CX) : R(0));
+    const R cr = -dt * exc;
+    const bool db = !(cr < R(0));
+    const R dEx = db ? G.dEx1 : G.dEx0, dEy = db ? G.dEy1 : G.dEy0;
+    const R dexc = (CY ? dEx * R(CY) : R(0)) - (CX ? dEy * R(CX) : R(0));
+    const R s = -cr * rcp_(G.ri * (db ? G.cq1 : G.cq0) - dt * dexc);
+    const R Ex = G.ex + s * dEx, Ey = G.ey + s * dEy;
+    const R cE = (CX ? R(CX) * Ex : R(0)) + (CY ? R(CY) * Ey : R(0));
+    const R dR = (-dt * cE - G.ri * s * (dEx * Ex + dEy * Ey)) * rcp_(Ex * Ex + Ey * Ey);
+    const bool da = !(dR < R(0));
     const R dxi = dR * (da ? G.idR1 : G.idR0);
     xi = (da ? G.xin1 : G.xin0) + dxi;
     eta = (db ? G.eta1 : G.eta0) + s;
@@ -560,7 +585,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             continue;
         }
         R F00, F01, F10, F11, vx, vy;
-        kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
+        const bool moved = kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
         NodeGeo<R> geo;
         node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
         const R idF = rcp_(F00 * F11 - F01 * F10);
@@ -584,6 +609,43 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         }
         R f[9], g[9];
         bool lost = false;
+        const int own = (ti + T::HP) * T::PWS + tj + T::HP + 2;   // this node in the staged tile
+        if (!moved && i > 0) {
+            // a node the blend does not move: c_hat = c, and the rest
+            // population's departure point is the node itself
+            {
+                const R2 v = sp[own];
+                f[0] = v.x;
+                g[0] = v.y;
+            }
+            auto pull = [&](auto cxc, auto cyc, int q) {
+                int base;
+                R xi, eta;
+                R2 v;
+                if (depart_static<decltype(cxc)::value, decltype(cyc)::value>(geo, dt, base, xi, eta)) {
+                    R Lx[3], Ly[3];
+                    lagrange3(xi, Lx);
+                    lagrange3(eta, Ly);
+                    v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
+                } else {
+                    lost = true;
+                    v = sp[q * T::PSS + own];
+                }
+                f[q] = v.x;
+                g[q] = v.y;
+            };
+            using P1 = std::integral_constant<int, 1>;
+            using Z0 = std::integral_constant<int, 0>;
+            using M1 = std::integral_constant<int, -1>;
+            pull(P1{}, Z0{}, 1);
+            pull(Z0{}, P1{}, 2);
+            pull(M1{}, Z0{}, 3);
+            pull(Z0{}, M1{}, 4);
+            pull(P1{}, P1{}, 5);
+            pull(M1{}, P1{}, 6);
+            pull(M1{}, M1{}, 7);
+            pull(P1{}, M1{}, 8);
+        } else {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             f[q] = R(0);
@@ -602,10 +664,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 g[q] = v.y;
             } else {
                 lost = true;
-                const R2 v = sp[q * T::PSS + (ti + T::HP) * T::PWS + tj + T::HP + 2];
+                const R2 v = sp[q * T::PSS + own];
                 f[q] = v.x;
                 g[q] = v.y;
             }
+        }
         }
         if (missing) {
             // wall targets: rho, T at B = A + dt n0 by Q2 interpolation of
@@ -850,6 +913,7 @@ static cudaError_t launch_any(const StepArgs& a, int precision, int variant, int
         case 1: return launch_step_t<float, 16, 256, 2, UNIFORM>(a, nbatch, s);
         case 2: return launch_step_t<float, 8, 256, 3, UNIFORM>(a, nbatch, s);
         case 3: return launch_step_t<float, 12, 384, 2, UNIFORM>(a, nbatch, s);
+        case 4: return launch_step_t<float, 16, 512, 2, UNIFORM>(a, nbatch, s);
         default: return launch_step_t<float, 8, 256, 2, UNIFORM>(a, nbatch, s);
     }
 }
@@ -868,6 +932,7 @@ int tile_rows(int precision, int variant) {
     switch (variant) {
         case 1: return 16;
         case 3: return 12;
+        case 4: return 16;
         default: return 8;
     }
 }
