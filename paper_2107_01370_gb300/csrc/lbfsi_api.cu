@@ -185,6 +185,7 @@ lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
     a.tiles = m->d_tiles;
     a.ntiles = m->nbatch * m->tiles_per_solve;
     a.collide_only = collide_only;
+    a.ustep = (int)m->host_k;
     a.status = m->d_status;
     return a;
 }
@@ -360,8 +361,9 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
-    const lbfsi::StepArgs a = make_args(m, 0);
+    lbfsi::StepArgs a = make_args(m, 0);
     for (int s = 0; s < nsteps; ++s) {
+        a.ustep = (int)m->host_k;
         cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
         m->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");

@@ -413,6 +413,7 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
         a.tiles = b->d_tiles;
         a.ntiles = b->ntiles;
         a.collide_only = 0;
+        a.ustep = -1;
         a.status = b->d_status;
         const cudaError_t e = lbfsi::launch_step(a, b->precision, b->variant, b->stream);
         if (e != cudaSuccess) return cuda_err(e, "batch step launch");

@@ -108,7 +108,9 @@ struct StepArgs {
     const SolveDev* solves;
     const TileDev* tiles;
     int ntiles;
-    int collide_only;              // 1: write the collided current state to fpost/gpost only
+    int collide_only;              // 1: write the collided current state to ppost only
+    int ustep;                     // uniform launch: the solves' step number (they advance
+                                   // together), or -1 to read it from the device counters
     int pf_dist;                   // uniform launch: L2 prefetch distance in CTAs (set by the launcher)
     unsigned* status;
 };

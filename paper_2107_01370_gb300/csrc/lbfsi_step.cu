@@ -333,7 +333,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         ctr = tg->counter;
         mptr = tg->maps;
     }
-    const unsigned kstep = __ldcg(ctr + 1);
+    // a uniform launch from the host knows the step number; otherwise it is
+    // the solve's device counter
+    const unsigned kstep = (UNIFORM && a.ustep >= 0) ? (unsigned)a.ustep : __ldcg(ctr + 1);
     const int cur = (int)(kstep & 1u);
     const int mode = a.collide_only ? MODE_COLLIDE_ONLY : (kstep == 0u ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM);
     {
@@ -790,13 +792,18 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // load of this step held over the next), builds the next launch's
         // maps and advances the solve's step number.  The acquire-release
         // count publishes this CTA's partial (written by thread 0) and, for
-        // the last CTA, makes every other CTA's partial visible.
-        const unsigned ntiles = UNIFORM ? gridDim.x * gridDim.y : (unsigned)s_sol.ntiles;
+        // the last CTA, makes every other CTA's partial visible.  When the
+        // step number is a launch argument no CTA reads the counter, so only
+        // the wall-row tiles (the ones with a partial) take part; otherwise
+        // every tile does, so that the step number advances after the last
+        // CTA of the solve has read it.
+        const bool host_step = UNIFORM && a.ustep >= 0;
+        const unsigned ntiles = host_step ? (unsigned)MD(ntj) : UNIFORM ? gridDim.x * gridDim.y : (unsigned)s_sol.ntiles;
         unsigned done = 0u;
-        if (l == 0)
+        if (l == 0 && (!host_step || i0 == 0))
             asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(done) : "l"(ctr) : "memory");
         done = __shfl_sync(0xffffffffu, done, 0);
-        if (done == ntiles - 1u) {
+        if ((!host_step || i0 == 0) && done == ntiles - 1u) {
             asm volatile("fence.acq_rel.gpu;" ::: "memory");
             const int ntj = MD(ntj);
             const double* part = SD(part) + (size_t)sb * ntj * 3;
