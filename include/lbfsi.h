@@ -244,8 +244,63 @@ int lbfsi_batch_remove(lbfsi_batch b, int slot);
 /* Free bytes of the pool and its largest free block. */
 int lbfsi_batch_memory(lbfsi_batch b, size_t* free_bytes, size_t* largest_free);
 
+/* Tile shape and tile-table order of a batch's step launches (the CTA
+ * schedule).  order 0: the tiles of each solve together, in slot order;
+ * order 1: tile rows outermost across all solves, so the wall and
+ * blending-region tiles (the most expensive) start first.  Synchronises. */
+int lbfsi_batch_set_schedule(lbfsi_batch b, int variant, int order);
+int lbfsi_batch_get_schedule(lbfsi_batch b, int* variant, int* order);
+
+/* graph_steps > 0: lbfsi_batch_step replays a CUDA graph of graph_steps
+ * launches over the current tile table for as long as no solve finishes
+ * (the graph is dropped whenever the table changes); 0: plain launches. */
+int lbfsi_batch_set_graph_steps(lbfsi_batch b, int graph_steps);
+
+/* Autotuner of the batch: like lbfsi_autotune over the active solves (the
+ * trial steps count toward their requested steps); the trials are compared
+ * by time per node update, since solves may finish during tuning.
+ * ns_per_node: nullable host array [lbfsi_step_variants][2]. */
+int lbfsi_batch_autotune(lbfsi_batch b, int steps_per_trial, int* best_variant, int* best_order,
+                         float* ns_per_node);
+
 /* Number of kernel launches issued on the handle's stream so far. */
 int64_t lbfsi_launch_count(lbfsi_mesh m);
+
+/* ---- Execution schedule, CUDA graphs and the autotuner.  The paper has no
+ * counterpart: these choose how the step of Sec. II-III is laid out on the
+ * GPU, not what it computes.  Every tile shape and CTA order computes
+ * bit-identical fields, loads and body states (each node is computed by the
+ * same code from the same inputs; load partials have fixed slots and a fixed
+ * summation order), so tuning never changes a solve's result. */
+
+/* Number of tile shapes ("step variants") of the step kernel for a
+ * precision (LBFSI_FP32: 5, LBFSI_FP64: 1), or LBFSI_EINVAL.  Float shapes,
+ * radial x angular nodes per CTA: 0: 8 x 32, 256 threads, 2 CTAs/SM;
+ * 1: 16 x 32, 256 threads; 2: 8 x 32, 3 CTAs/SM; 3: 12 x 32, 384 threads
+ * (default); 4: 16 x 32, 512 threads. */
+int lbfsi_step_variants(int precision);
+
+/* Tile shape (0 .. lbfsi_step_variants - 1) and CTA order of a mesh handle's
+ * step launches.  order 0: the tiles of one solve are consecutive CTAs;
+ * order 1: the solves of one tile are consecutive CTAs.  EINVAL when out of
+ * range.  Synchronises the handle's stream when it changes the schedule. */
+int lbfsi_set_schedule(lbfsi_mesh m, int variant, int order);
+int lbfsi_get_schedule(lbfsi_mesh m, int* variant, int* order);
+
+/* graph_steps > 0: lbfsi_step replays a CUDA graph of graph_steps step
+ * launches (captured at first use on a private stream, recaptured after a
+ * schedule change; its launches read the step number from the device),
+ * plain launches for the remainder; 0 (default): plain launches only. */
+int lbfsi_set_graph_steps(lbfsi_mesh m, int graph_steps);
+
+/* Autotuner: advances the handle's solves by 1 + steps_per_trial steps under
+ * every (variant, order) pair, times each trial with CUDA events on the
+ * handle's stream, and keeps the fastest pair.  The trial steps are real
+ * steps of the solves.  best_variant, best_order: outputs (nullable);
+ * ms_per_step: nullable host array [lbfsi_step_variants][2] receiving the
+ * measured ms per step.  Synchronises; returns the device status. */
+int lbfsi_autotune(lbfsi_mesh m, int steps_per_trial, int* best_variant, int* best_order,
+                   float* ms_per_step);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char* lbfsi_last_error(void);

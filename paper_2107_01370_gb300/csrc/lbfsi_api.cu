@@ -39,7 +39,7 @@ struct lbfsi_mesh_s {
     lbfsi::HostMesh host;
     lbfsi::DeviceMesh dmesh;
     lbfsi::CudaMallocMemory mem;
-    int nbatch = 0, precision = 0, variant = 3, tile_rows = 12, tiles_per_solve = 0;
+    int nbatch = 0, precision = 0, variant = 3, order = 0, tile_rows = 12, tiles_per_solve = 0;
     size_t esize = 8;
     cudaStream_t stream = nullptr;
     std::vector<lbfsi_body_desc> bodies;
@@ -56,13 +56,17 @@ struct lbfsi_mesh_s {
     BodyDev* d_bodies = nullptr;     // [nbatch]
     lbfsi::MeshDev* d_meshdev = nullptr;
     SolveDev* d_solves = nullptr;    // [nbatch]
-    TileDev* d_tiles = nullptr;      // [nbatch * tiles_per_solve]
     unsigned* d_status = nullptr;
     std::vector<SolveDev> solves;
     unsigned host_k = 0;             // step number of every solve (mirror of counter[1])
     bool initialized = false;
     double dt = 0;
     int64_t launches = 0;
+    // CUDA graph of graph_steps step launches (step number from the device
+    // counters), captured on a private stream and replayed on 'stream'
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
 
     int cur() const { return (int)(host_k & 1u); }
     bool first() const { return host_k == 0u; }
@@ -126,9 +130,11 @@ int upload(lbfsi_mesh m, const double* host, void* ddst, size_t n) {
 void free_all(lbfsi_mesh m) {
     void* ptrs[] = {m->d_p[0], m->d_p[1], m->d_M[0], m->d_M[1], m->d_ppost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
                     m->d_loads_tmp, m->d_part, m->d_counter, m->d_bodies, m->d_meshdev, m->d_solves,
-                    m->d_tiles, m->d_status};
+                    m->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     lbfsi::release_mesh(m->dmesh, m->mem);
 }
 
@@ -150,27 +156,8 @@ int upload_solves(lbfsi_mesh m) {
         s.counter = m->d_counter + 2 * b;
         s.body = m->d_bodies + b;
     }
-    std::vector<TileDev> tiles;
-    tiles.reserve((size_t)m->nbatch * m->tiles_per_solve);
-    const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows, ntj = m->host.ntj;
-    for (int b = 0; b < m->nbatch; ++b)
-        for (int ti = 0; ti < nti; ++ti)
-            for (int tj = 0; tj < ntj; ++tj) {
-                TileDev t{};
-                t.solve = b;
-                t.mesh = 0;
-                t.i0 = ti * m->tile_rows;
-                t.j0 = tj * lbfsi::TILE_J;
-                t.tj = tj;
-                t.counter = m->d_counter + 2 * b;
-                t.maps[0] = m->d_maps[0] + b;
-                t.maps[1] = m->d_maps[1] + b;
-                tiles.push_back(t);
-            }
     cudaError_t e = cudaMemcpyAsync(m->d_solves, m->solves.data(), m->solves.size() * sizeof(SolveDev),
                                     cudaMemcpyHostToDevice, m->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "solve descriptors upload");
     return LBFSI_OK;
@@ -182,12 +169,49 @@ lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
     a.usol = m->solves[0];
     a.meshes = m->d_meshdev;
     a.solves = m->d_solves;
-    a.tiles = m->d_tiles;
+    a.tiles = nullptr;
     a.ntiles = m->nbatch * m->tiles_per_solve;
     a.collide_only = collide_only;
     a.ustep = (int)m->host_k;
+    a.uorder = m->order;
     a.status = m->d_status;
     return a;
+}
+
+// Capture graph_steps step launches that take the step number from the
+// device counters (so the same graph serves every replay).
+int capture_graph(lbfsi_mesh m) {
+    cudaError_t e = lbfsi::prepare_step(m->precision, m->variant, true);
+    if (e == cudaSuccess && !m->cap_stream) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture setup");
+    lbfsi::StepArgs a = make_args(m, 0);
+    a.ustep = -1;
+    e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int g = 0; g < m->graph_steps && le == cudaSuccess; ++g)
+        le = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(m->cap_stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le != cudaSuccess ? le : e, "step capture");
+    }
+    e = cudaGraphInstantiate(&m->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        m->graph = nullptr;
+        return cuda_fail(e, "graph instantiate");
+    }
+    return LBFSI_OK;
+}
+
+void drop_graph(lbfsi_mesh m) {
+    if (m->graph) {
+        cudaStreamSynchronize(m->stream);
+        cudaGraphExecDestroy(m->graph);
+        m->graph = nullptr;
+    }
 }
 
 }  // namespace
@@ -219,13 +243,13 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     m->esize = d->precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     // tile shape of the float kernel (a tuning knob, every variant computes the
-    // same result): LBFSI_STEP_VARIANT 0: 8 x 32 nodes, 2 CTAs/SM; 1: 16 x 32,
-    // 2 CTAs/SM; 2: 8 x 32, 3 CTAs/SM; 3: 12 x 32, 384 threads (default)
+    // same result; see lbfsi_step_variants): default 3, or LBFSI_STEP_VARIANT
     m->variant = 3;
     if (const char* v = std::getenv("LBFSI_STEP_VARIANT")) {
         const int k = std::atoi(v);
-        m->variant = (k >= 0 && k <= 3) ? k : 3;
+        m->variant = (k >= 0 && k < lbfsi::step_variants(LBFSI_FP32)) ? k : 3;
     }
+    if (m->precision == LBFSI_FP64) m->variant = 0;
     m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
     const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows;
     m->tiles_per_solve = nti * m->host.ntj;
@@ -252,7 +276,6 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     LB_ALLOC(m->d_bodies, nb);
     LB_ALLOC(m->d_meshdev, 1);
     LB_ALLOC(m->d_solves, nb);
-    LB_ALLOC(m->d_tiles, nb * m->tiles_per_solve);
     LB_ALLOC(m->d_status, 1);
 #undef LB_ALLOC
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -361,8 +384,21 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
+    int s = 0;
+    if (m->graph_steps > 0 && nsteps >= m->graph_steps) {
+        if (!m->graph) {
+            const int rc = capture_graph(m);
+            if (rc) return rc;
+        }
+        for (; nsteps - s >= m->graph_steps; s += m->graph_steps) {
+            const cudaError_t e = cudaGraphLaunch(m->graph, m->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+            m->launches += m->graph_steps;
+            m->host_k += (unsigned)m->graph_steps;
+        }
+    }
     lbfsi::StepArgs a = make_args(m, 0);
-    for (int s = 0; s < nsteps; ++s) {
+    for (; s < nsteps; ++s) {
         a.ustep = (int)m->host_k;
         cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
         m->launches++;
@@ -499,5 +535,85 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const 
 }
 
 int64_t lbfsi_launch_count(lbfsi_mesh m) { return m ? m->launches : -1; }
+
+int lbfsi_step_variants(int precision) {
+    if (precision != LBFSI_FP32 && precision != LBFSI_FP64) return fail(LBFSI_EINVAL, "unknown precision");
+    return lbfsi::step_variants(precision);
+}
+
+int lbfsi_set_schedule(lbfsi_mesh m, int variant, int order) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    if (variant < 0 || variant >= lbfsi::step_variants(m->precision) || (order != 0 && order != 1))
+        return fail(LBFSI_EINVAL, "variant or order out of range");
+    if (variant == m->variant && order == m->order) return LBFSI_OK;
+    drop_graph(m);
+    m->variant = variant;
+    m->order = order;
+    m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
+    m->tiles_per_solve = ((m->host.nr + m->tile_rows - 1) / m->tile_rows) * m->host.ntj;
+    return m->initialized ? upload_solves(m) : LBFSI_OK;
+}
+
+int lbfsi_get_schedule(lbfsi_mesh m, int* variant, int* order) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    if (variant) *variant = m->variant;
+    if (order) *order = m->order;
+    return LBFSI_OK;
+}
+
+int lbfsi_set_graph_steps(lbfsi_mesh m, int graph_steps) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    if (graph_steps < 0) return fail(LBFSI_EINVAL, "graph_steps must be >= 0");
+    if (graph_steps != m->graph_steps) drop_graph(m);
+    m->graph_steps = graph_steps;
+    return LBFSI_OK;
+}
+
+int lbfsi_autotune(lbfsi_mesh m, int steps_per_trial, int* best_variant, int* best_order, float* ms_per_step) {
+    if (!m) return fail(LBFSI_EINVAL, "null mesh");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    if (steps_per_trial < 1) return fail(LBFSI_EINVAL, "steps_per_trial must be >= 1");
+    const int nv = lbfsi::step_variants(m->precision);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(e, "tuner events");
+    int bv = m->variant, bo = m->order, rc = LBFSI_OK;
+    float best = -1.0f;
+    const int graph_steps = m->graph_steps;   // trials use plain launches
+    lbfsi_set_graph_steps(m, 0);
+    for (int v = 0; v < nv && !rc; ++v)
+        for (int o = 0; o < 2 && !rc; ++o) {
+            rc = lbfsi_set_schedule(m, v, o);
+            if (rc) break;
+            lbfsi_step(m, 1);   // first launch of a shape configures it
+            cudaEventRecord(e0, m->stream);
+            rc = lbfsi_step(m, steps_per_trial);
+            cudaEventRecord(e1, m->stream);
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "tuner trial");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)steps_per_trial;
+            if (ms_per_step) ms_per_step[2 * v + o] = ms;
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                bv = v;
+                bo = o;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbfsi_set_graph_steps(m, graph_steps);
+    if (rc) return rc;
+    rc = lbfsi_set_schedule(m, bv, bo);
+    if (rc) return rc;
+    if (best_variant) *best_variant = bv;
+    if (best_order) *best_order = bo;
+    return check_status(m);
+}
 
 }  // extern "C"

@@ -112,7 +112,7 @@ struct Slot {
 
 struct lbfsi_batch_s {
     Pool pool;
-    int precision = LBFSI_FP32, variant = 3, tile_rows = 12;
+    int precision = LBFSI_FP32, variant = 3, order = 0, tile_rows = 12;
     size_t esize = 4;
     cudaStream_t stream = nullptr;
     std::vector<MeshEntry> meshes;
@@ -127,6 +127,11 @@ struct lbfsi_batch_s {
     double* d_zero_loads = nullptr;
     int ntiles = 0;
     bool dirty = true;
+    // CUDA graph of graph_steps launches over the current tile table,
+    // captured on a private stream, dropped whenever the table changes
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -191,26 +196,52 @@ void release_slot_memory(lbfsi_batch b, Slot& s) {
     s.blocks.clear();
 }
 
-// Tile table of the next launches: every tile of every active solve.
+void drop_graph(lbfsi_batch b) {
+    if (b->graph) {
+        cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+// Tile table of the next launches: every tile of every active solve, in the
+// batch's order: 0, the tiles of each solve together; 1, tile rows outermost
+// across all solves, so that the wall and blending-region rows (the most
+// expensive tiles) start first and the far-field rows fill the tail.
 int rebuild_tiles(lbfsi_batch b) {
+    drop_graph(b);
     std::vector<TileDev> tiles;
-    for (size_t k = 0; k < b->slots.size(); ++k) {
+    auto push = [&](size_t k, int ti, int tj) {
         const Slot& s = b->slots[k];
-        if (!s.used || s.finished) continue;
-        const lbfsi::HostMesh& h = b->meshes[s.mesh].host;
-        const int nti = (h.nr + b->tile_rows - 1) / b->tile_rows;
-        for (int ti = 0; ti < nti; ++ti)
-            for (int tj = 0; tj < h.ntj; ++tj) {
-                TileDev t{};
-                t.solve = (int)k;
-                t.mesh = s.mesh;
-                t.i0 = ti * b->tile_rows;
-                t.j0 = tj * lbfsi::TILE_J;
-                t.tj = tj;
-                t.counter = s.dev.counter;
-                t.maps[0] = s.dev.maps[0];
-                t.maps[1] = s.dev.maps[1];
-                tiles.push_back(t);
+        TileDev t{};
+        t.solve = (int)k;
+        t.mesh = s.mesh;
+        t.i0 = ti * b->tile_rows;
+        t.j0 = tj * lbfsi::TILE_J;
+        t.tj = tj;
+        t.counter = s.dev.counter;
+        t.maps[0] = s.dev.maps[0];
+        t.maps[1] = s.dev.maps[1];
+        tiles.push_back(t);
+    };
+    auto active = [&](size_t k) { return b->slots[k].used && !b->slots[k].finished; };
+    auto nti_of = [&](size_t k) { return (b->meshes[b->slots[k].mesh].host.nr + b->tile_rows - 1) / b->tile_rows; };
+    if (b->order == 0) {
+        for (size_t k = 0; k < b->slots.size(); ++k) {
+            if (!active(k)) continue;
+            const int nti = nti_of(k), ntj = b->meshes[b->slots[k].mesh].host.ntj;
+            for (int ti = 0; ti < nti; ++ti)
+                for (int tj = 0; tj < ntj; ++tj) push(k, ti, tj);
+        }
+    } else {
+        int max_nti = 0;
+        for (size_t k = 0; k < b->slots.size(); ++k)
+            if (active(k)) max_nti = std::max(max_nti, nti_of(k));
+        for (int ti = 0; ti < max_nti; ++ti)
+            for (size_t k = 0; k < b->slots.size(); ++k) {
+                if (!active(k) || ti >= nti_of(k)) continue;
+                const int ntj = b->meshes[b->slots[k].mesh].host.ntj;
+                for (int tj = 0; tj < ntj; ++tj) push(k, ti, tj);
             }
     }
     cudaError_t e = cudaSuccess;
@@ -248,6 +279,45 @@ int check_status(lbfsi_batch b) {
     return LBFSI_OK;
 }
 
+lbfsi::StepArgs step_args(lbfsi_batch b) {
+    lbfsi::StepArgs a{};
+    a.meshes = b->d_meshes;
+    a.solves = b->d_solves;
+    a.tiles = b->d_tiles;
+    a.ntiles = b->ntiles;
+    a.collide_only = 0;
+    a.ustep = -1;
+    a.status = b->d_status;
+    return a;
+}
+
+// Capture graph_steps launches over the current tile table (every launch
+// reads the step numbers from the device counters, so the graph is valid for
+// every replay until the table changes).
+int capture_graph(lbfsi_batch b, const lbfsi::StepArgs& a) {
+    cudaError_t e = lbfsi::prepare_step(b->precision, b->variant, false);
+    if (e == cudaSuccess && !b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_err(e, "graph capture setup");
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(e, "begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int g = 0; g < b->graph_steps && le == cudaSuccess; ++g)
+        le = lbfsi::launch_step(a, b->precision, b->variant, b->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_err(le != cudaSuccess ? le : e, "batch step capture");
+    }
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_err(e, "graph instantiate");
+    }
+    return LBFSI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,6 +332,7 @@ int lbfsi_batch_create(size_t pool_bytes, int precision, void* cuda_stream, lbfs
     b->precision = precision;
     b->esize = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
     b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == LBFSI_FP64) b->variant = 0;   // one tile shape
     b->tile_rows = lbfsi::tile_rows(precision, b->variant);
     int rc = b->pool.init(pool_bytes);
     if (rc) {
@@ -291,6 +362,8 @@ int lbfsi_batch_destroy(lbfsi_batch b) {
                     b->d_zero_loads};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;   // the pool frees its block
     return LBFSI_OK;
 }
@@ -401,25 +474,38 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
 int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
     if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
     if (nsteps < 0) return lbfsi::set_error(LBFSI_EINVAL, "nsteps must be >= 0");
-    for (int st = 0; st < nsteps; ++st) {
+    int st = 0;
+    while (st < nsteps) {
         if (b->dirty) {
             const int rc = rebuild_tiles(b);
             if (rc) return rc;
         }
         if (b->ntiles == 0) break;
-        lbfsi::StepArgs a{};
-        a.meshes = b->d_meshes;
-        a.solves = b->d_solves;
-        a.tiles = b->d_tiles;
-        a.ntiles = b->ntiles;
-        a.collide_only = 0;
-        a.ustep = -1;
-        a.status = b->d_status;
-        const cudaError_t e = lbfsi::launch_step(a, b->precision, b->variant, b->stream);
-        if (e != cudaSuccess) return cuda_err(e, "batch step launch");
+        // steps until the next solve finishes: the tile table is fixed over them
+        int run = nsteps - st;
+        for (auto& s : b->slots)
+            if (s.used && !s.finished) run = std::min(run, s.steps_target - s.steps_done);
+        lbfsi::StepArgs a = step_args(b);
+        int done = 0;
+        if (b->graph_steps > 0 && run >= b->graph_steps) {
+            if (!b->graph) {
+                const int rc = capture_graph(b, a);
+                if (rc) return rc;
+            }
+            for (; run - done >= b->graph_steps; done += b->graph_steps) {
+                const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+                if (e != cudaSuccess) return cuda_err(e, "batch graph launch");
+            }
+        }
+        for (; done < run; ++done) {
+            const cudaError_t e = lbfsi::launch_step(a, b->precision, b->variant, b->stream);
+            if (e != cudaSuccess) return cuda_err(e, "batch step launch");
+        }
+        st += run;
         for (auto& s : b->slots) {
             if (!s.used || s.finished) continue;
-            if (++s.steps_done >= s.steps_target) {
+            s.steps_done += run;
+            if (s.steps_done >= s.steps_target) {
                 s.finished = true;
                 b->dirty = true;
             }
@@ -431,6 +517,99 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
         *active_after = n;
     }
     return LBFSI_OK;
+}
+
+int lbfsi_batch_set_schedule(lbfsi_batch b, int variant, int order) {
+    if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
+    if (variant < 0 || variant >= lbfsi::step_variants(b->precision) || (order != 0 && order != 1))
+        return lbfsi::set_error(LBFSI_EINVAL, "variant or order out of range");
+    if (variant == b->variant && order == b->order) return LBFSI_OK;
+    drop_graph(b);
+    b->variant = variant;
+    b->order = order;
+    b->tile_rows = lbfsi::tile_rows(b->precision, variant);
+    // the per-solve CTA count of the completion counter follows the tile shape
+    for (size_t k = 0; k < b->slots.size(); ++k) {
+        Slot& s = b->slots[k];
+        if (!s.used) continue;
+        const lbfsi::HostMesh& h = b->meshes[s.mesh].host;
+        s.dev.ntiles = ((h.nr + b->tile_rows - 1) / b->tile_rows) * h.ntj;
+        s.ntiles = s.dev.ntiles;
+        const cudaError_t e = cudaMemcpyAsync(b->d_solves + k, &s.dev, sizeof(SolveDev), cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_err(e, "solve record upload");
+    }
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_err(e, "schedule change");
+    b->dirty = true;
+    return LBFSI_OK;
+}
+
+int lbfsi_batch_get_schedule(lbfsi_batch b, int* variant, int* order) {
+    if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
+    if (variant) *variant = b->variant;
+    if (order) *order = b->order;
+    return LBFSI_OK;
+}
+
+int lbfsi_batch_set_graph_steps(lbfsi_batch b, int graph_steps) {
+    if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
+    if (graph_steps < 0) return lbfsi::set_error(LBFSI_EINVAL, "graph_steps must be >= 0");
+    if (graph_steps != b->graph_steps) drop_graph(b);
+    b->graph_steps = graph_steps;
+    return LBFSI_OK;
+}
+
+int lbfsi_batch_autotune(lbfsi_batch b, int steps_per_trial, int* best_variant, int* best_order,
+                         float* ns_per_node) {
+    if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
+    if (steps_per_trial < 1) return lbfsi::set_error(LBFSI_EINVAL, "steps_per_trial must be >= 1");
+    const int nv = lbfsi::step_variants(b->precision);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_err(e, "tuner events");
+    const int graph_steps = b->graph_steps;   // trials use plain launches
+    lbfsi_batch_set_graph_steps(b, 0);
+    int bv = b->variant, bo = b->order, rc = LBFSI_OK;
+    float best = -1.0f;
+    for (int v = 0; v < nv && !rc; ++v)
+        for (int o = 0; o < 2 && !rc; ++o) {
+            rc = lbfsi_batch_set_schedule(b, v, o);
+            if (rc) break;
+            rc = lbfsi_batch_step(b, 1, nullptr);   // configures the shape, rebuilds the table
+            if (rc) break;
+            // node updates of the trial, from the steps each solve takes
+            std::vector<int> before(b->slots.size());
+            for (size_t k = 0; k < b->slots.size(); ++k) before[k] = b->slots[k].steps_done;
+            cudaEventRecord(e0, b->stream);
+            rc = lbfsi_batch_step(b, steps_per_trial, nullptr);
+            cudaEventRecord(e1, b->stream);
+            e = cudaEventSynchronize(e1);
+            if (!rc && e != cudaSuccess) rc = cuda_err(e, "tuner trial");
+            if (rc) break;
+            double nodes = 0.0;
+            for (size_t k = 0; k < b->slots.size(); ++k)
+                if (b->slots[k].used)
+                    nodes += (double)(b->slots[k].steps_done - before[k]) * b->meshes[b->slots[k].mesh].host.N;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float ns = nodes > 0.0 ? (float)(ms * 1e6 / nodes) : -1.0f;
+            if (ns_per_node) ns_per_node[2 * v + o] = ns;
+            if (ns > 0.0f && (best < 0.0f || ns < best)) {
+                best = ns;
+                bv = v;
+                bo = o;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbfsi_batch_set_graph_steps(b, graph_steps);
+    if (rc) return rc;
+    rc = lbfsi_batch_set_schedule(b, bv, bo);
+    if (rc) return rc;
+    if (best_variant) *best_variant = bv;
+    if (best_order) *best_order = bo;
+    return check_status(b);
 }
 
 int lbfsi_batch_poll(lbfsi_batch b, int slot, int* steps_done, int* finished) {

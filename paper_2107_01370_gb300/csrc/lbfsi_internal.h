@@ -111,6 +111,8 @@ struct StepArgs {
     int collide_only;              // 1: write the collided current state to ppost only
     int ustep;                     // uniform launch: the solves' step number (they advance
                                    // together), or -1 to read it from the device counters
+    int uorder;                    // uniform launch: CTA order, 0 = (tile column, tile row,
+                                   // solve), 1 = (solve, tile column, tile row)
     int pf_dist;                   // uniform launch: L2 prefetch distance in CTAs (set by the launcher)
     unsigned* status;
 };
@@ -126,6 +128,12 @@ cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStrea
 cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,
                                 cudaStream_t s);
 int tile_rows(int precision, int variant);
+// Number of tile shapes of the float step kernel (variants 0 .. n-1); the
+// float64 kernel has one.
+int step_variants(int precision);
+// One-time configuration of a step kernel (shared-memory limit, occupancy);
+// done by the first launch, and by this call before a stream capture.
+cudaError_t prepare_step(int precision, int variant, bool uniform);
 constexpr int TILE_J = 32;
 inline int tiles_j(int nt) { return (nt + TILE_J - 1) / TILE_J; }
 cudaError_t launch_init(int precision, const double* M, void* P, void* Mout, int N, int nbatch,

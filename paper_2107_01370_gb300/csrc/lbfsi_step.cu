@@ -316,10 +316,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     unsigned* ctr;
     StepMaps* const* mptr;
     if constexpr (UNIFORM) {
-        sb = (int)blockIdx.z;
-        tjx = (int)blockIdx.x;
+        sb = a.uorder ? (int)blockIdx.x : (int)blockIdx.z;
+        tjx = a.uorder ? (int)blockIdx.y : (int)blockIdx.x;
         j0 = tjx * TJ;
-        i0 = (int)blockIdx.y * TI;
+        i0 = (a.uorder ? (int)blockIdx.z : (int)blockIdx.y) * TI;
         nr = a.umesh.nr; nt = a.umesh.nt; N = a.umesh.N;
         ctr = a.usol.counter + 2 * sb;
         mptr = a.usol.maps;
@@ -437,7 +437,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const unsigned nx = gridDim.x, ny = gridDim.y;
         const unsigned lin = blockIdx.x + nx * (blockIdx.y + ny * blockIdx.z) + (unsigned)a.pf_dist;
         if (a.pf_dist > 0 && lin < nx * ny * gridDim.z) {
-            const int xn = (int)(lin % nx), yn = (int)((lin / nx) % ny), zn = (int)(lin / (nx * ny));
+            const int gx = (int)(lin % nx), gy = (int)((lin / nx) % ny), gz = (int)(lin / (nx * ny));
+            const int xn = a.uorder ? gy : gx, yn = a.uorder ? gz : gy, zn = a.uorder ? gx : gz;
             const int jb = xn * TJ;
             const int len = min(TJ, nt - jb);
             for (int t = tid; t < 2 * 13 * TI; t += NT) {
@@ -798,7 +799,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // every tile does, so that the step number advances after the last
         // CTA of the solve has read it.
         const bool host_step = UNIFORM && a.ustep >= 0;
-        const unsigned ntiles = host_step ? (unsigned)MD(ntj) : UNIFORM ? gridDim.x * gridDim.y : (unsigned)s_sol.ntiles;
+        const unsigned ntiles = host_step ? (unsigned)MD(ntj)
+                              : UNIFORM ? (unsigned)a.usol.ntiles : (unsigned)s_sol.ntiles;
         unsigned done = 0u;
         if (l == 0 && (!host_step || i0 == 0))
             asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(done) : "l"(ctr) : "memory");
@@ -884,34 +886,65 @@ __global__ void k_advance(const BodyDev* __restrict__ bodies, const double* __re
 constexpr int TJ = TILE_J;
 
 template <typename R, int TI, int NT, int MINB, bool UNIFORM>
-static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) {
-    const size_t smem = step_smem_bytes<R, TI, TJ>();
-    static bool configured = false;
-    if (!configured) {
+struct StepKernel {
+    static inline int resident = -1;   // CTAs resident on the whole GPU at once
+
+    static cudaError_t configure() {
+        if (resident >= 0) return cudaSuccess;
+        const size_t smem = step_smem_bytes<R, TI, TJ>();
         cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ, NT, MINB, UNIFORM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<R, TI, TJ, NT, MINB, UNIFORM>, NT, smem);
+        if (e != cudaSuccess) return e;
+        resident = sms * per_sm;
+        return cudaSuccess;
     }
-    if (UNIFORM) {
-        // prefetch distance: the CTAs resident on the whole GPU at once
-        static int resident = -1;
-        if (resident < 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<R, TI, TJ, NT, MINB, UNIFORM>, NT, smem);
-            resident = sms * per_sm;
+
+    static cudaError_t launch(const StepArgs& a, int nbatch, cudaStream_t s) {
+        cudaError_t e = configure();
+        if (e != cudaSuccess) return e;
+        const size_t smem = step_smem_bytes<R, TI, TJ>();
+        if (UNIFORM) {
+            // prefetch distance: one resident wave
+            StepArgs b = a;
+            b.pf_dist = resident;
+            const int nti = (a.umesh.nr + TI - 1) / TI;
+            const dim3 grid = a.uorder ? dim3(nbatch, a.umesh.ntj, nti) : dim3(a.umesh.ntj, nti, nbatch);
+            k_step<R, TI, TJ, NT, MINB, UNIFORM><<<grid, NT, smem, s>>>(b);
+        } else {
+            k_step<R, TI, TJ, NT, MINB, UNIFORM><<<a.ntiles, NT, smem, s>>>(a);
         }
-        StepArgs b = a;
-        b.pf_dist = resident;
-        const dim3 grid(a.umesh.ntj, (a.umesh.nr + TI - 1) / TI, nbatch);
-        k_step<R, TI, TJ, NT, MINB, UNIFORM><<<grid, NT, smem, s>>>(b);
-    } else {
-        k_step<R, TI, TJ, NT, MINB, UNIFORM><<<a.ntiles, NT, smem, s>>>(a);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+};
+
+template <typename R, int TI, int NT, int MINB, bool UNIFORM>
+static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) {
+    return StepKernel<R, TI, NT, MINB, UNIFORM>::launch(a, nbatch, s);
 }
+
+template <bool UNIFORM>
+static cudaError_t configure_any(int precision, int variant) {
+    if (precision == 0) return StepKernel<double, 8, 256, 1, UNIFORM>::configure();
+    switch (variant) {
+        case 1: return StepKernel<float, 16, 256, 2, UNIFORM>::configure();
+        case 2: return StepKernel<float, 8, 256, 3, UNIFORM>::configure();
+        case 3: return StepKernel<float, 12, 384, 2, UNIFORM>::configure();
+        case 4: return StepKernel<float, 16, 512, 2, UNIFORM>::configure();
+        default: return StepKernel<float, 8, 256, 2, UNIFORM>::configure();
+    }
+}
+
+cudaError_t prepare_step(int precision, int variant, bool uniform) {
+    return uniform ? configure_any<true>(precision, variant) : configure_any<false>(precision, variant);
+}
+
+int step_variants(int precision) { return precision == 0 ? 1 : 5; }
 
 template <bool UNIFORM>
 static cudaError_t launch_any(const StepArgs& a, int precision, int variant, int nbatch, cudaStream_t s) {

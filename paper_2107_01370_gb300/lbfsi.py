@@ -27,7 +27,10 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_synchronize", "lbfsi_launch_count", "lbfsi_last_error",
             "lbfsi_wall_loads_noalloc", "lbfsi_batch_create", "lbfsi_batch_destroy",
             "lbfsi_batch_add", "lbfsi_batch_step", "lbfsi_batch_poll", "lbfsi_batch_get",
-            "lbfsi_batch_remove", "lbfsi_batch_memory"]
+            "lbfsi_batch_remove", "lbfsi_batch_memory", "lbfsi_step_variants",
+            "lbfsi_set_schedule", "lbfsi_get_schedule", "lbfsi_set_graph_steps", "lbfsi_autotune",
+            "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
+            "lbfsi_batch_autotune"]
 
 
 class LbfsiError(RuntimeError):
@@ -151,6 +154,14 @@ def flow_params(flow) -> FlowParams:
                       flow.length)
 
 
+def step_variants(precision) -> int:
+    """Number of tile shapes of the step kernel for a precision."""
+    n = load().lbfsi_step_variants(int(precision))
+    if n < 0:
+        raise LbfsiError(n, _lib.lbfsi_last_error().decode())
+    return n
+
+
 class Mesh:
     """Handle of one O-grid mesh with nbatch independent solves."""
 
@@ -234,6 +245,25 @@ class Mesh:
         ma = np.ascontiguousarray(rho_u_T, dtype=np.float64)
         _check(self._lib.lbfsi_set_populations(self.h, _dptr(fa), _dptr(ga), _dptr(ma)))
 
+    def set_schedule(self, variant, order=0):
+        _check(self._lib.lbfsi_set_schedule(self.h, int(variant), int(order)))
+
+    def schedule(self):
+        v, o = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbfsi_get_schedule(self.h, ctypes.byref(v), ctypes.byref(o)))
+        return v.value, o.value
+
+    def set_graph_steps(self, n):
+        _check(self._lib.lbfsi_set_graph_steps(self.h, int(n)))
+
+    def autotune(self, steps_per_trial=20):
+        """Returns (variant, order, ms per step [variants][2])."""
+        nv = step_variants(self.precision)
+        ms = (ctypes.c_float * (2 * nv))()
+        v, o = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbfsi_autotune(self.h, int(steps_per_trial), ctypes.byref(v), ctypes.byref(o), ms))
+        return v.value, o.value, np.array(ms, dtype=np.float64).reshape(nv, 2)
+
     def launch_count(self) -> int:
         return int(self._lib.lbfsi_launch_count(self.h))
 
@@ -301,6 +331,25 @@ class Batch:
     def remove(self, slot):
         _check(self._lib.lbfsi_batch_remove(self.h, slot))
         self._shapes.pop(slot, None)
+
+    def set_schedule(self, variant, order=0):
+        _check(self._lib.lbfsi_batch_set_schedule(self.h, int(variant), int(order)))
+
+    def schedule(self):
+        v, o = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbfsi_batch_get_schedule(self.h, ctypes.byref(v), ctypes.byref(o)))
+        return v.value, o.value
+
+    def set_graph_steps(self, n):
+        _check(self._lib.lbfsi_batch_set_graph_steps(self.h, int(n)))
+
+    def autotune(self, steps_per_trial=20):
+        """Returns (variant, order, ns per node update [variants][2])."""
+        nv = step_variants(self.precision)
+        ns = (ctypes.c_float * (2 * nv))()
+        v, o = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbfsi_batch_autotune(self.h, int(steps_per_trial), ctypes.byref(v), ctypes.byref(o), ns))
+        return v.value, o.value, np.array(ns, dtype=np.float64).reshape(nv, 2)
 
     def memory(self):
         fb = ctypes.c_size_t(0)
