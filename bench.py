@@ -179,16 +179,19 @@ def serving_bench(stream):
     baseline: the same requests one after another as plain solves."""
     from paper_2107_01370_gb300 import serving
     cache = serving.CaseCache()
+    schedule = serving.tune_schedule(SERVING_POOL, stream=stream, cache=cache)
     reqs = serving.viv_requests(256, 2000, seed=0)
     done_c, loads_c, wall_c, peak_c = serving.run_batched(reqs, SERVING_POOL, chunk=50,
-                                                          stream=stream, cache=cache)
+                                                          stream=stream, cache=cache,
+                                                          schedule=schedule)
     capacity = len(reqs) / wall_c
     reqs_p = serving.poisson_arrivals(serving.viv_requests(256, 2000, seed=0), 0.9 * capacity,
                                       seed=1)
     done_p, loads_p, wall_p, peak_p = serving.run_batched(reqs_p, SERVING_POOL, chunk=50,
-                                                          stream=stream, cache=cache)
+                                                          stream=stream, cache=cache,
+                                                          schedule=schedule)
     p50, p99 = serving.latency_stats(done_p)
-    done_s, loads_s, wall_s = serving.run_sequential(reqs, stream=stream, cache=cache)
+    done_s, loads_s, wall_s = serving.run_sequential(reqs, stream=stream, cache=cache, schedule=schedule)
     same = all(np.array_equal(loads_p[k], loads_s[k]) for k in loads_s)
     return {"metric": "batched solves/s", "solves_per_s": round(len(reqs_p) / wall_p, 3),
             "p50_s": round(p50, 4), "p99_s": round(p99, 4),
@@ -197,6 +200,7 @@ def serving_bench(stream):
             "speedup_vs_sequential": round(wall_s / wall_c, 2),
             "requests": len(reqs), "steps_per_request": 2000, "arrival_rate": round(0.9 * capacity, 3),
             "pool_bytes": SERVING_POOL, "peak_active": peak_p,
+            "schedule": {"variant": schedule[0], "order": schedule[1]},
             "results_equal_alone_and_in_mix": bool(same)}
 
 
@@ -242,6 +246,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tile shape and CTA order")
+    ap.add_argument("--schedule", default=None,
+                    help="'variant,order': fixed tile shape and CTA order instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -275,8 +282,17 @@ def main():
     mesh = lbfsi.Mesh(case.r, case.e, case.bodies * B, precision=lbfsi.FP32,
                       stream=stream.cuda_stream)
     mesh.init_fields(case.flow, M0b)
+    # untimed: the autotuner picks the tile shape and CTA order on this GPU
+    # (its trial steps are real steps of the solves, so they count as warm-up)
+    tuned = None
+    if args.schedule:
+        mesh.set_schedule(*[int(x) for x in args.schedule.split(",")])
+    elif not args.no_tune:
+        v, o, ms = mesh.autotune(steps_per_trial=20)
+        tuned = {"variant": v, "order": o, "ms_per_step_by_variant_order": np.round(ms, 4).tolist()}
     mesh.step(args.warmup)
     mesh.synchronize()
+    variant, order = mesh.schedule()
 
     sampler = ClockSampler(dev)
     sampler.start()
@@ -328,6 +344,7 @@ def main():
         K = args.steps
         m2 = lbfsi.Mesh(case.r, case.e, case.bodies * B, precision=lbfsi.FP32,
                         stream=stream.cuda_stream)
+        m2.set_schedule(variant, order)
         loads = np.empty((B, 3))
         torch.cuda.synchronize()
         if dist:
@@ -364,7 +381,8 @@ def main():
                           "mesh": "O-grid 512x256, r 0.5..20 D", "steps_per_solve": case.steps,
                           "l2": "inputs larger than L2 (ping-pong populations "
                                 f"{BYTES_PER_NODE_FP32 * nodes / 1e6:.0f} MB)",
-                          "parallelism": f"replicas x{world}"},
+                          "parallelism": f"replicas x{world}",
+                          "schedule": {"variant": variant, "order": order, "autotuner": tuned}},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "serving": serving_out,
                "solves_per_s": round(B * world / (case.steps * region_ms / args.steps * 1e-3), 4)}

@@ -39,7 +39,7 @@ struct lbfsi_mesh_s {
     lbfsi::HostMesh host;
     lbfsi::DeviceMesh dmesh;
     lbfsi::CudaMallocMemory mem;
-    int nbatch = 0, precision = 0, variant = 3, order = 0, tile_rows = 12, tiles_per_solve = 0;
+    int nbatch = 0, precision = 0, variant = 4, order = 1, tile_rows = 16, tiles_per_solve = 0;
     size_t esize = 8;
     cudaStream_t stream = nullptr;
     std::vector<lbfsi_body_desc> bodies;
@@ -243,11 +243,14 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     m->esize = d->precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     // tile shape of the float kernel (a tuning knob, every variant computes the
-    // same result; see lbfsi_step_variants): default 3, or LBFSI_STEP_VARIANT
-    m->variant = 3;
+    // same result; see lbfsi_step_variants): default 4 with the solve-minor
+    // CTA order (the autotuner's choice on a GB300 for batched meshes), or
+    // LBFSI_STEP_VARIANT
+    m->variant = 4;
+    m->order = 1;
     if (const char* v = std::getenv("LBFSI_STEP_VARIANT")) {
         const int k = std::atoi(v);
-        m->variant = (k >= 0 && k < lbfsi::step_variants(LBFSI_FP32)) ? k : 3;
+        m->variant = (k >= 0 && k < lbfsi::step_variants(LBFSI_FP32)) ? k : 4;
     }
     if (m->precision == LBFSI_FP64) m->variant = 0;
     m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);

@@ -112,7 +112,7 @@ struct Slot {
 
 struct lbfsi_batch_s {
     Pool pool;
-    int precision = LBFSI_FP32, variant = 3, order = 0, tile_rows = 12;
+    int precision = LBFSI_FP32, variant = 4, order = 0, tile_rows = 16;
     size_t esize = 4;
     cudaStream_t stream = nullptr;
     std::vector<MeshEntry> meshes;

@@ -57,13 +57,34 @@ class CaseCache:
         return base, body, M0
 
 
-def run_batched(reqs, pool_bytes, precision=lbfsi.FP32, chunk=50, stream=None, cache=None,
-                clock=time.perf_counter):
-    """Serve the requests in arrival order with continuous batching.  Returns
-    per-request (arrival, completion) times relative to the start, the final
-    loads of each request and the wall time."""
+def tune_schedule(pool_bytes, precision=lbfsi.FP32, stream=None, cache=None, steps_per_trial=10,
+                  seed=12345):
+    """Tile shape and CTA order for the serving mix, from the batch
+    autotuner run on a small mix of the request sizes (two of each)."""
     cache = cache or CaseCache()
     batch = lbfsi.Batch(pool_bytes, precision=precision, stream=stream)
+    rng = np.random.default_rng(seed)
+    trial_steps = 2 * lbfsi.step_variants(precision) * (1 + steps_per_trial) + 1
+    for k, (nr, nt) in enumerate(SIZES * 2):
+        req = Request(10 ** 6 + k, nr, nt, float(rng.uniform(3, 8)), float(rng.uniform(2, 20)), trial_steps)
+        base, body, M0 = cache.case(req)
+        if batch.add(base.r, base.e, body, base.flow, req.steps, M0) is None:
+            break
+    v, o, _ = batch.autotune(steps_per_trial)
+    batch.close()
+    return v, o
+
+
+def run_batched(reqs, pool_bytes, precision=lbfsi.FP32, chunk=50, stream=None, cache=None,
+                clock=time.perf_counter, schedule=None):
+    """Serve the requests in arrival order with continuous batching (tile
+    shape and CTA order 'schedule', else the default).  Returns per-request
+    (arrival, completion) times relative to the start, the final loads of
+    each request and the wall time."""
+    cache = cache or CaseCache()
+    batch = lbfsi.Batch(pool_bytes, precision=precision, stream=stream)
+    if schedule is not None:
+        batch.set_schedule(*schedule)
     pending = sorted(reqs, key=lambda r: r.arrival)
     active = {}
     done = {}
@@ -100,8 +121,10 @@ def run_batched(reqs, pool_bytes, precision=lbfsi.FP32, chunk=50, stream=None, c
     return done, loads, wall, peak_active
 
 
-def run_sequential(reqs, precision=lbfsi.FP32, stream=None, cache=None, clock=time.perf_counter):
-    """The same requests one at a time, each a plain single-mesh solve."""
+def run_sequential(reqs, precision=lbfsi.FP32, stream=None, cache=None, clock=time.perf_counter,
+                   schedule=None):
+    """The same requests one at a time, each a plain single-mesh solve (with
+    the tile shape of 'schedule' when given)."""
     cache = cache or CaseCache()
     done = {}
     loads = {}
@@ -109,6 +132,8 @@ def run_sequential(reqs, precision=lbfsi.FP32, stream=None, cache=None, clock=ti
     for req in reqs:
         base, body, M0 = cache.case(req)
         mesh = lbfsi.Mesh(base.r, base.e, [body], precision=precision, stream=stream)
+        if schedule is not None:
+            mesh.set_schedule(*schedule)
         mesh.init_fields(base.flow, M0[None])
         mesh.step(req.steps)
         loads[req.rid] = mesh.body_forces()[0]
