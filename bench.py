@@ -204,6 +204,99 @@ def serving_bench(stream):
             "results_equal_alone_and_in_mix": bool(same)}
 
 
+# single-solve O-grids of 1, 4 and 16.8 M nodes (radial x angular, far-field
+# radius): 512 angular nodes (the impulsive start stays physical; at 1024 the
+# wall temperature of the uniform initial state goes negative within five
+# steps in the oracle and on the GPU alike), radial rows grown with the far
+# field pushed out as far as the geometric radial table needs
+SWEEP = ((2048, 512, 20.0), (8192, 512, 80.0), (32768, 512, 320.0))
+
+
+def roofline_sweep(stream, schedule, peak, steps=50):
+    """HBM roofline sweep: one 1-DOF VIV solve on O-grids of 1-16.8 M nodes
+    (the ping-pong populations, 151 MB - 2.4 GB, exceed L2), same schedule as
+    the main measurement; MLUPS and algorithmic GB/s per size."""
+    import torch
+    from paper_2107_01370_gb300 import lbfsi
+    out = []
+    body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.5, m_star=10.0, v_r=5.0)
+    for nr, nt, r_far in SWEEP:
+        case = inputs.cylinder_case(nr, nt, r_far=r_far, body=body)
+        M0 = inputs.initial_field(nr, nt, case.flow, seed=0)
+        row = {"mesh": f"{nr}x{nt}", "nodes": case.nodes, "r_far": r_far}
+        m = lbfsi.Mesh(case.r, case.e, case.bodies, precision=lbfsi.FP32, stream=stream.cuda_stream)
+        try:
+            m.set_schedule(*schedule)
+            m.init_fields(case.flow, M0[None])
+            m.step(5)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            m.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            gbs = BYTES_PER_NODE_FP32 * case.nodes / (ms * 1e-3) / 1e9
+            row.update({"ms_per_step": round(ms, 4), "MLUPS": round(case.nodes / ms / 1e3, 1),
+                        "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)})
+        except lbfsi.LbfsiError as ex:
+            row["error"] = str(ex)
+        finally:
+            m.close()
+        out.append(row)
+        del M0
+    return out
+
+
+def small_case_graphs(stream, steps=1000, graph_steps=100):
+    """BASELINE config 1 (fixed cylinder 128 x 64, FP64, 1000 steps): a
+    launch-bound case, timed with plain launches and with CUDA-graph replay."""
+    import torch
+    from paper_2107_01370_gb300 import lbfsi
+    case = inputs.fixed_cylinder_128x64(steps)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
+    res = {"workload": case.name + ", FP64", "nodes": case.nodes, "steps": steps}
+    for label, g in (("plain", 0), ("graph", graph_steps)):
+        m = lbfsi.Mesh(case.r, case.e, case.bodies, precision=lbfsi.FP64, stream=stream.cuda_stream)
+        m.init_fields(case.flow, M0[None])
+        m.set_graph_steps(g)
+        m.step(2 * max(g, 1))   # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        m.synchronize()
+        ms = e0.elapsed_time(e1)
+        m.close()
+        res[label] = {"ms_per_step": round(ms / steps, 5), "MLUPS": round(case.nodes * steps / ms / 1e3, 1)}
+    res["graph_steps"] = graph_steps
+    return res
+
+
+def issue_roofline(nodes, kernel_s, sm_mhz):
+    """Instruction-issue ceiling of the step kernel: warp instructions per
+    node from the committed ncu capture (current source only) against one
+    warp instruction per scheduler per cycle (152 SMs x 4 schedulers)."""
+    p = os.path.join(ROOT, "profiles", "k_step_fp32_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_sha") != source_sha() or "warp_inst_per_node" not in d:
+        return None
+    achieved = d["warp_inst_per_node"] * nodes / kernel_s / 1e9
+    peak = 152 * 4 * sm_mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_inst_per_node": d["warp_inst_per_node"],
+            "fp32_flop_per_node": d.get("fp32_flop_per_node"),
+            "peak_kind": "152 SMs x 4 schedulers x median SM clock of the timed region"}
+
+
 def run_reference(args):
     """The oracle timed on the host cores, same metric and workload; each step
     is one oracle step of the bounded sample (reference_sample_case)."""
@@ -247,6 +340,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile shape and CTA order")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 1-16 M-node roofline sweep and the small FP64 case")
     ap.add_argument("--schedule", default=None,
                     help="'variant,order': fixed tile shape and CTA order instead of the autotuner")
     args = ap.parse_args()
@@ -364,6 +458,12 @@ def main():
         m2.close()
         del fields
 
+    sweep = small = None
+    if not args.no_sweep and world == 1:
+        sweep = roofline_sweep(stream, (variant, order), peak)
+        small = small_case_graphs(stream)
+    issue = issue_roofline(nodes, kavg_s, clocks.get("sm_mhz") or 2070.0) if clocks else None
+
     serving_out = None
     if not args.no_serving and world == 1:
         serving_out = serving_bench(stream.cuda_stream)
@@ -385,6 +485,7 @@ def main():
                           "schedule": {"variant": variant, "order": order, "autotuner": tuned}},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "serving": serving_out,
+               "issue_roofline": issue, "roofline_sweep": sweep, "small_case": small,
                "solves_per_s": round(B * world / (case.steps * region_ms / args.steps * 1e-3), 4)}
         print(json.dumps(out), flush=True)
     mesh.close()

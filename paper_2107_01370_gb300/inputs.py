@@ -32,7 +32,8 @@ def ogrid_radii(nr: int, radius: float, r_far: float, dr0: float) -> np.ndarray:
     n_elem = n_even - 1
 
     def last_radius(q: float) -> float:
-        w = 2.0 * dr0 * q ** np.arange(n_elem)
+        with np.errstate(over="ignore"):   # trial growth factors of the bisection may overflow
+            w = 2.0 * dr0 * q ** np.arange(n_elem)
         r_even = radius + np.concatenate([[0.0], np.cumsum(w)])
         if nr % 2 == 1:
             return r_even[-1]
