@@ -249,6 +249,9 @@ __device__ __forceinline__ double pick<double>(double d, float) {
 // two-wide FMAs (f and g share the weights).
 template <typename R2>
 __device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const float* Lx, const float* Ly);
+// The float path reads the first two pairs of a window row with one 16-byte
+// load: window origins are even columns of a staged row that starts on a
+// 16-byte boundary.
 template <>
 __device__ __forceinline__ float2 gather9<float2>(const float2* p, int rowstride, const float* Lx,
                                                   const float* Ly) {
@@ -256,8 +259,9 @@ __device__ __forceinline__ float2 gather9<float2>(const float2* p, int rowstride
 #pragma unroll
     for (int aa = 0; aa < 3; ++aa) {
         const float2* pr = p + aa * rowstride;
-        float2 t = __fmul2_rn(make_float2(Ly[0], Ly[0]), pr[0]);
-        t = __ffma2_rn(make_float2(Ly[1], Ly[1]), pr[1], t);
+        const float4 p01 = *reinterpret_cast<const float4*>(pr);
+        float2 t = __fmul2_rn(make_float2(Ly[0], Ly[0]), make_float2(p01.x, p01.y));
+        t = __ffma2_rn(make_float2(Ly[1], Ly[1]), make_float2(p01.z, p01.w), t);
         t = __ffma2_rn(make_float2(Ly[2], Ly[2]), pr[2], t);
         acc = __ffma2_rn(make_float2(Lx[aa], Lx[aa]), t, acc);
     }
