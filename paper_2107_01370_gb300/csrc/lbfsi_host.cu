@@ -84,15 +84,15 @@ void geometry_tables(HostMesh& m) {
         else
             drc = 0.5 * (r[i + 1] - r[i - 1]);
         double* t = &m.rowtab[(size_t)i * ROWTAB];
-        t[0] = r[i];
-        t[1] = 1.0 / drc;
-        t[2] = 1.0 / r[i];
+        t[RT_R] = r[i];
+        t[RT_IDRC] = 1.0 / drc;
+        t[RT_IR] = 1.0 / r[i];
         for (int c = 0; c < 2; ++c) {
             const int a = i - 1 + c;
             if (a < 0 || a > nr - 2) continue;
             const int wa = std::min(2 * (a / 2), nr - 3);
-            t[3 + 2 * c] = (double)(i - wa - 1);
-            t[4 + 2 * c] = 2.0 / (r[wa + 2] - r[wa]);
+            t[RT_XIN0 + 2 * c] = (double)(i - wa - 1);
+            t[RT_IDR0 + 2 * c] = 2.0 / (r[wa + 2] - r[wa]);
         }
     }
     m.coltab.assign((size_t)nt * COLTAB, 0.0);
@@ -103,21 +103,22 @@ void geometry_tables(HostMesh& m) {
         const double dex = 0.5 * (e[2 * jp] - e[2 * jm]), dey = 0.5 * (e[2 * jp + 1] - e[2 * jm + 1]);
         const double cr = ex * dey - ey * dex;
         double* t = &m.coltab[(size_t)j * COLTAB];
-        t[0] = ex;
-        t[1] = ey;
-        t[2] = dey / cr;
-        t[3] = ey / cr;
-        t[4] = dex / cr;
-        t[5] = ex / cr;
+        t[CT_E] = ex;
+        t[CT_E + 1] = ey;
+        t[CT_G] = dey / cr;
+        t[CT_G + 1] = ey / cr;
+        t[CT_G + 2] = dex / cr;
+        t[CT_G + 3] = ex / cr;
         for (int c = 0; c < 2; ++c) {
             const int b = j - 1 + c;
             const int wb = (b >= 0) ? 2 * (b / 2) : -2 * ((-b + 1) / 2);
             const int w0 = wr(wb), w2 = wr(wb + 2);
             const double dEx = 0.5 * (e[2 * w2] - e[2 * w0]), dEy = 0.5 * (e[2 * w2 + 1] - e[2 * w0 + 1]);
-            t[6 + 4 * c] = (double)(j - wb - 1);
-            t[7 + 4 * c] = dEx;
-            t[8 + 4 * c] = dEy;
-            t[9 + 4 * c] = dEx * ey - dEy * ex;
+            double* tc = t + CT_C0 + 4 * c;
+            tc[0] = (double)(j - wb - 1);
+            tc[1] = dEx;
+            tc[2] = dEy;
+            tc[3] = dEx * ey - dEy * ex;
         }
     }
 }

@@ -30,8 +30,19 @@ struct BodyStateDev {
 
 // Per-row and per-column geometry of the O-grid X = centre + r_i e_j (see
 // the table builder in lbfsi_api.cu for the meaning of each entry).
+// Entries are grouped in fours so that a kernel reads each group with one
+// 16-byte load.
 constexpr int ROWTAB = 8;
 constexpr int COLTAB = 16;
+// row i: [0..3] xi of the node and 1 / (dR/dxi) in the cells i-1 and i
+// (element coordinates), [4] r_i, [5] 1 / (dr/dxi) at the node (centred),
+// [6] 1 / r_i, [7] unused
+enum : int { RT_XIN0 = 0, RT_IDR0 = 1, RT_XIN1 = 2, RT_IDR1 = 3, RT_R = 4, RT_IDRC = 5, RT_IR = 6 };
+// column j: [0..3] (de_y, e_y, de_x, e_x) / (e x de) with de the centred
+// difference of the direction vectors (inverse metric), [4..5] e_j, [6..7]
+// unused, [8..11] and [12..15] for the cells j-1 and j: eta of the node,
+// dE/deta (x, y) and dE x e_j
+enum : int { CT_G = 0, CT_E = 4, CT_C0 = 8, CT_C1 = 12 };
 
 // Blended rigid map of one body for one body state (defined in
 // lbfsi_device.cuh); declared here so the per-step record can hold it.

@@ -64,10 +64,22 @@ struct Vec2<double> {
     using T = double2;
 };
 
-// Shared-memory strides of the geometry tables, odd so that threads reading
-// the same entry of consecutive rows / columns hit distinct banks.
-constexpr int RS = ROWTAB + 1;
-constexpr int CS = COLTAB + 1;
+// Shared-memory strides of the geometry tables: a row is read by whole warps
+// (broadcast); consecutive columns are 20 words apart, so the 16-byte loads of
+// eight threads (one shared-memory wavefront) cover distinct banks.
+constexpr int RS = ROWTAB;
+constexpr int CS = COLTAB + 4;
+
+// Four consecutive table entries (16-byte aligned) in one or two loads.
+__device__ __forceinline__ void ld4(const float* p, float& a, float& b, float& c, float& d) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double& a, double& b, double& c, double& d) {
+    const double2 u = *reinterpret_cast<const double2*>(p);
+    const double2 v = *reinterpret_cast<const double2*>(p + 2);
+    a = u.x; b = u.y; c = v.x; d = v.y;
+}
 
 template <typename R, int TI, int TJ>
 constexpr size_t step_smem_bytes() {
@@ -124,12 +136,12 @@ struct NodeGeo {
 template <typename R>
 __device__ __forceinline__ void node_geo(int i, int j, int nr, const R* row, const R* col, int pi0,
                                          int sj0, int PWS, NodeGeo<R>& G) {
-    G.ex = col[0];
-    G.ey = col[1];
-    G.ri = row[0];
-    G.eta0 = col[6]; G.dEx0 = col[7]; G.dEy0 = col[8]; G.cq0 = col[9];
-    G.eta1 = col[10]; G.dEx1 = col[11]; G.dEy1 = col[12]; G.cq1 = col[13];
-    G.xin0 = row[3]; G.idR0 = row[4]; G.xin1 = row[5]; G.idR1 = row[6];
+    R u0, u1;
+    ld4(col + CT_E, G.ex, G.ey, u0, u1);
+    G.ri = row[RT_R];
+    ld4(col + CT_C0, G.eta0, G.dEx0, G.dEy0, G.cq0);
+    ld4(col + CT_C1, G.eta1, G.dEx1, G.dEy1, G.cq1);
+    ld4(row + RT_XIN0, G.xin0, G.idR0, G.xin1, G.idR1);
     const int wa0 = min((max(i - 1, 0) >> 1) * 2, nr - 3);   // the wall row has no cell i-1
     const int wa1 = min((i >> 1) * 2, nr - 3);
     const int wb0 = ((j - 1) >> 1) * 2, wb1 = (j >> 1) * 2;
@@ -187,8 +199,10 @@ __device__ __forceinline__ bool depart_static(const NodeGeo<R>& G, R dt, int& ba
 template <typename R>
 __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F01, R F10, R F11,
                                          R* G) {
-    const R j00 = row[1] * col[2], j01 = -row[2] * col[3];
-    const R j10 = -row[1] * col[4], j11 = row[2] * col[5];
+    R c0, c1, c2, c3;
+    ld4(col + CT_G, c0, c1, c2, c3);
+    const R j00 = row[RT_IDRC] * c0, j01 = -row[RT_IR] * c1;
+    const R j10 = -row[RT_IDRC] * c2, j11 = row[RT_IR] * c3;
     const R idet = rcp_(F00 * F11 - F01 * F10);
     const R i00 = F11 * idet, i01 = -F01 * idet, i10 = -F10 * idet, i11 = F00 * idet;
     G[0] = i00 * j00 + i10 * j10;
@@ -371,14 +385,17 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     const int pi0 = i0 - T::HP, sj0 = j0 - 4;       // global index of sp row 0, column 0
 
     // ---- phase 1: stage the geometry tables, M^k and the populations ------
-    for (int t = tid; t < T::MH * ROWTAB; t += NT) {
-        const int li = t / ROWTAB, c = t - li * ROWTAB;
-        const int i = min(max(mi0 + li, 0), nr - 1);
-        cp_async(srow + li * RS + c, rowtab + i * ROWTAB + c);
-    }
-    for (int t = tid; t < T::MW * COLTAB; t += NT) {
-        const int lj = t / COLTAB, c = t - lj * COLTAB;
-        cp_async(scol + lj * CS + c, coltab + wrap_nt(mj0 + lj, nt) * COLTAB + c);
+    {
+        constexpr int CE = 16 / (int)sizeof(R);   // table entries per 16-byte chunk
+        for (int t = tid; t < T::MH * (ROWTAB / CE); t += NT) {
+            const int li = t / (ROWTAB / CE), c = (t - li * (ROWTAB / CE)) * CE;
+            const int i = min(max(mi0 + li, 0), nr - 1);
+            cp_async16(srow + li * RS + c, rowtab + i * ROWTAB + c);
+        }
+        for (int t = tid; t < T::MW * (COLTAB / CE); t += NT) {
+            const int lj = t / (COLTAB / CE), c = (t - lj * (COLTAB / CE)) * CE;
+            cp_async16(scol + lj * CS + c, coltab + wrap_nt(mj0 + lj, nt) * COLTAB + c);
+        }
     }
     // M^k in 16-byte chunks of consecutive columns (element-wise when Ntheta
     // is not a multiple of the chunk); one thread per (row, chunk), the four
@@ -482,8 +499,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             if (i < 0 || i >= nr) continue;
             const R* row = srow + (li + 1) * RS;
             const R* col = scol + (lj + 1) * CS;
-            R F00, F01, F10, F11, vx, vy;
-            kinematics(mapK, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
+            R F00, F01, F10, F11, vx, vy, ex, ey, u0, u1;
+            ld4(col + CT_E, ex, ey, u0, u1);
+            kinematics(mapK, xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
             R G[4];
             grad_map(row, col, F00, F01, F10, F11, G);
 #pragma unroll
@@ -591,10 +609,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             M_out[(size_t)3 * N + n] = Tt;
             continue;
         }
-        R F00, F01, F10, F11, vx, vy;
-        const bool moved = kinematics(mapS, xm + row[0] * col[0], ym + row[0] * col[1], F00, F01, F10, F11, vx, vy);
         NodeGeo<R> geo;
         node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
+        R F00, F01, F10, F11, vx, vy;
+        const bool moved = kinematics(mapS, xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
         const R idF = rcp_(F00 * F11 - F01 * F10);
         const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
         unsigned missing = 0u;
