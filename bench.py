@@ -186,14 +186,38 @@ def cpu_baseline_sample(solves=16, steps=2):
 REF_ROWS = 33   # odd: the truncated radial table stays subparametric
 
 
-def reference_sample_case():
-    """Bounded sample of the bench workload for the oracle: the first 33
-    radial rows (all 256 angular nodes, 8448 nodes) of the 512x256 VIV mesh,
-    with the same body, blend region, flow and time step."""
+def reference_sample_case(rows=REF_ROWS):
+    """Bounded sample of the bench workload for the oracle: the first 'rows'
+    (odd) radial rows, all 256 angular nodes, of the 512x256 VIV mesh, with
+    the same body, blend region, flow and time step."""
     case = inputs.viv_cylinder_512x256()
-    case.r = case.r[:REF_ROWS].copy()
-    case.nr = REF_ROWS
+    case.r = case.r[:rows].copy()
+    case.nr = rows
     return case
+
+
+REF_BUDGET_S = 150.0   # wall-time target of the whole reference run
+
+
+def reference_rows(steps, warmup):
+    """Radial rows of the reference sample such that warm-up plus timed steps
+    take about REF_BUDGET_S: one calibration step of the 33-row sample, then
+    the rows scaled down (odd, at least 5) when the step count needs it."""
+    import oracle.mesh as OM
+    import oracle.solver as OS
+    case = reference_sample_case(REF_ROWS)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
+    s = OS.Solver.from_case(OM.ogrid_mesh(case.r, case.e), case, M0)
+    s.step()
+    t = time.perf_counter()
+    s.step()
+    t_step = time.perf_counter() - t
+    # the workers run in parallel and share the memory system: about half the
+    # single-process rate
+    budget = 0.5 * REF_BUDGET_S / max(1, steps + warmup)
+    rows = int(REF_ROWS * min(1.0, budget / max(t_step, 1e-6)))
+    rows = max(5, rows - (1 - rows % 2))   # odd: the truncated table stays subparametric
+    return min(rows, REF_ROWS)
 
 
 SERVING_POOL = 1 << 30   # 1 GiB: about half of what the 256 requests need at once
@@ -328,14 +352,14 @@ def issue_roofline(nodes, kernel_s, sm_mhz):
 def _reference_worker(args):
     """One oracle solve of the bounded reference sample in a spawned process:
     'warmup' untimed steps, then 'steps' timed steps."""
-    root, seed, warmup, steps = args
+    root, seed, warmup, steps, rows = args
     import time as _time
     sys.path.insert(0, root)
     from paper_2107_01370_gb300 import inputs as _inputs
     import oracle.mesh as OM
     import oracle.solver as OS
     import bench as _bench
-    case = _bench.reference_sample_case()
+    case = _bench.reference_sample_case(rows)
     M0 = _inputs.initial_field(case.nr, case.ntheta, case.flow, seed=seed)
     s = OS.Solver.from_case(OM.ogrid_mesh(case.r, case.e), case, M0)
     for _ in range(warmup):
@@ -358,14 +382,16 @@ def run_reference(args):
     cores = max(1, min(16, os.cpu_count() or 1))
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
+    rows = reference_rows(args.steps, args.warmup)
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_reference_worker, [(ROOT, k, args.warmup, args.steps) for k in range(cores)])
+        res = pool.map(_reference_worker, [(ROOT, k, args.warmup, args.steps, rows) for k in range(cores)])
     dt = max(r[0] for r in res)
     nodes = sum(r[1] for r in res)
     value = nodes * args.steps / dt / 1e6
     sample = (f"{cores} independent oracle solves (FP64 numpy, one spawned process and one thread "
-              f"each) of the first {REF_ROWS} radial rows x 256 angular nodes ({REF_ROWS * 256} "
-              f"nodes) of the 512x256 VIV solve; {args.steps} timed steps each")
+              f"each) of the first {rows} radial rows x 256 angular nodes ({rows * 256} "
+              f"nodes) of the 512x256 VIV solve (rows sized to the step count); "
+              f"{args.steps} timed steps each")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
