@@ -158,6 +158,29 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g,
 /* Wait for the handle's stream; returns the first device-detected error. */
 int lbfsi_synchronize(lbfsi_mesh m);
 
+/* ---- Checkpoint / resume (no counterpart in the paper).  A checkpoint is
+ * the whole state the next step reads, as raw device bytes: the
+ * post-propagation populations and their moment field, every solve's maps
+ * record (body state of the last stream, next state, the previous state for
+ * the mesh velocity of Sec. II D, last loads, blended maps) and the step
+ * number, behind a header naming precision, batch and mesh size.  Restoring
+ * it into a handle created with the same mesh and bodies and initialised
+ * with the same flow continues the run bit for bit. */
+
+/* Size in bytes of a checkpoint of this handle (0 for a null handle). */
+size_t lbfsi_checkpoint_bytes(lbfsi_mesh m);
+
+/* Write the checkpoint into the caller's host buffer of at least
+ * lbfsi_checkpoint_bytes bytes.  Synchronises; refuses (with the device
+ * status) to save a state the kernels flagged. */
+int lbfsi_checkpoint(lbfsi_mesh m, void* host_buf, size_t bytes);
+
+/* Replace the handle's state by a checkpoint (host buffer, borrowed).
+ * LBFSI_EINVAL if the buffer is not a checkpoint of a handle with the same
+ * precision, batch size and mesh dimensions; LBFSI_ESTATE before
+ * lbfsi_init_fields.  Clears the device status word.  Synchronises. */
+int lbfsi_restore(lbfsi_mesh m, const void* host_buf, size_t bytes);
+
 /* Loads on the body of each solve from caller-provided post-propagation
  * populations, without allocating anything.  The paper has no counterpart:
  * this is the load reduction of lbfsi_step (wall stress, Simpson shares,

@@ -539,6 +539,87 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const 
 
 int64_t lbfsi_launch_count(lbfsi_mesh m) { return m ? m->launches : -1; }
 
+namespace {
+struct CheckpointHeader {
+    char magic[8];
+    int32_t version, precision, nbatch, nr, nt, esize;
+    uint32_t step;
+    uint32_t pad;
+};
+constexpr char kMagic[8] = {'L', 'B', 'F', 'S', 'I', 'C', 'K', '1'};
+
+size_t checkpoint_bytes(lbfsi_mesh m) {
+    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    return sizeof(CheckpointHeader) + nb * 18 * N * m->esize + nb * 4 * N * m->esize + nb * sizeof(StepMaps);
+}
+}  // namespace
+
+size_t lbfsi_checkpoint_bytes(lbfsi_mesh m) { return m ? checkpoint_bytes(m) : 0; }
+
+int lbfsi_checkpoint(lbfsi_mesh m, void* buf, size_t bytes) {
+    if (!m || !buf) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    if (bytes < checkpoint_bytes(m)) return fail(LBFSI_EINVAL, "checkpoint buffer too small");
+    const int rc = check_status(m);   // a failed state is not saved
+    if (rc) return rc;
+    CheckpointHeader h{};
+    std::memcpy(h.magic, kMagic, sizeof(kMagic));
+    h.version = 1;
+    h.precision = m->precision;
+    h.nbatch = m->nbatch;
+    h.nr = m->host.nr;
+    h.nt = m->host.nt;
+    h.esize = (int32_t)m->esize;
+    h.step = m->host_k;
+    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const int c = m->cur();
+    cudaError_t e = cudaMemcpyAsync(p, m->d_p[c], nb * 18 * N * m->esize, cudaMemcpyDeviceToHost, m->stream);
+    p += nb * 18 * N * m->esize;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, m->d_M[c], nb * 4 * N * m->esize, cudaMemcpyDeviceToHost, m->stream);
+    p += nb * 4 * N * m->esize;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, m->d_maps[c], nb * sizeof(StepMaps), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+    return LBFSI_OK;
+}
+
+int lbfsi_restore(lbfsi_mesh m, const void* buf, size_t bytes) {
+    if (!m || !buf) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first (the flow of the checkpointed run)");
+    if (bytes < checkpoint_bytes(m)) return fail(LBFSI_EINVAL, "checkpoint buffer too small for this handle");
+    CheckpointHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != 1)
+        return fail(LBFSI_EINVAL, "not a checkpoint of this library");
+    if (h.precision != m->precision || h.nbatch != m->nbatch || h.nr != m->host.nr || h.nt != m->host.nt ||
+        h.esize != (int32_t)m->esize)
+        return fail(LBFSI_EINVAL, "checkpoint of a different mesh, batch or precision");
+    drop_graph(m);
+    m->host_k = h.step;
+    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    const char* p = static_cast<const char*>(buf) + sizeof(h);
+    const int c = m->cur();
+    cudaError_t e = cudaMemcpyAsync(m->d_p[c], p, nb * 18 * N * m->esize, cudaMemcpyHostToDevice, m->stream);
+    p += nb * 18 * N * m->esize;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_M[c], p, nb * 4 * N * m->esize, cudaMemcpyHostToDevice, m->stream);
+    p += nb * 4 * N * m->esize;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_maps[c], p, nb * sizeof(StepMaps), cudaMemcpyHostToDevice, m->stream);
+    std::vector<unsigned> ctr(2 * nb);
+    for (size_t b = 0; b < nb; ++b) {
+        ctr[2 * b] = 0u;
+        ctr[2 * b + 1] = m->host_k;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_counter, ctr.data(), ctr.size() * sizeof(unsigned), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+    return LBFSI_OK;
+}
+
 int lbfsi_step_variants(int precision) {
     if (precision != LBFSI_FP32 && precision != LBFSI_FP64) return fail(LBFSI_EINVAL, "unknown precision");
     return lbfsi::step_variants(precision);

@@ -30,7 +30,7 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_remove", "lbfsi_batch_memory", "lbfsi_step_variants",
             "lbfsi_set_schedule", "lbfsi_get_schedule", "lbfsi_set_graph_steps", "lbfsi_autotune",
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
-            "lbfsi_batch_autotune"]
+            "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore"]
 
 
 class LbfsiError(RuntimeError):
@@ -117,8 +117,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbfsi_last_error.argtypes = []
     lib.lbfsi_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("lbfsi_launch_count", "lbfsi_last_error"):
+        if name not in ("lbfsi_launch_count", "lbfsi_last_error", "lbfsi_checkpoint_bytes"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.lbfsi_checkpoint_bytes.restype = ctypes.c_size_t
+    lib.lbfsi_checkpoint_bytes.argtypes = [ctypes.c_void_p]
+    lib.lbfsi_checkpoint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    lib.lbfsi_restore.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
     _lib = lib
     return lib
 
@@ -244,6 +248,16 @@ class Mesh:
         ga = np.ascontiguousarray(g, dtype=np.float64)
         ma = np.ascontiguousarray(rho_u_T, dtype=np.float64)
         _check(self._lib.lbfsi_set_populations(self.h, _dptr(fa), _dptr(ga), _dptr(ma)))
+
+    def checkpoint(self) -> bytes:
+        """The handle's whole step state (see lbfsi_checkpoint)."""
+        n = self._lib.lbfsi_checkpoint_bytes(self.h)
+        buf = ctypes.create_string_buffer(n)
+        _check(self._lib.lbfsi_checkpoint(self.h, buf, n))
+        return buf.raw
+
+    def restore(self, ckpt: bytes):
+        _check(self._lib.lbfsi_restore(self.h, ckpt, len(ckpt)))
 
     def set_schedule(self, variant, order=0):
         _check(self._lib.lbfsi_set_schedule(self.h, int(variant), int(order)))
