@@ -181,6 +181,7 @@ lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
 // Capture graph_steps step launches that take the step number from the
 // device counters (so the same graph serves every replay).
 int capture_graph(lbfsi_mesh m) {
+    lbfsi::TraceRange trace_("lbfsi graph capture");
     cudaError_t e = lbfsi::prepare_step(m->precision, m->variant, true);
     if (e == cudaSuccess && !m->cap_stream) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture setup");
@@ -313,6 +314,7 @@ int lbfsi_destroy_mesh(lbfsi_mesh m) {
 }
 
 int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rho_u_T) {
+    lbfsi::TraceRange trace_("lbfsi_init_fields");
     if (!m || !p) return fail(LBFSI_EINVAL, "null argument");
     SolveDev proto{};
     int rc = lbfsi::fill_flow(*p, proto);
@@ -384,6 +386,7 @@ int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_bo
 }
 
 int lbfsi_step(lbfsi_mesh m, int nsteps) {
+    lbfsi::TraceRange trace_("lbfsi_step");
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
@@ -425,6 +428,7 @@ static int download_maps(lbfsi_mesh m, std::vector<StepMaps>& out) {
 }
 
 int lbfsi_body_forces(lbfsi_mesh m, double* out) {
+    lbfsi::TraceRange trace_("lbfsi_body_forces");
     if (!m || !out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     std::vector<StepMaps> mp;
@@ -557,6 +561,7 @@ size_t checkpoint_bytes(lbfsi_mesh m) {
 size_t lbfsi_checkpoint_bytes(lbfsi_mesh m) { return m ? checkpoint_bytes(m) : 0; }
 
 int lbfsi_checkpoint(lbfsi_mesh m, void* buf, size_t bytes) {
+    lbfsi::TraceRange trace_("lbfsi_checkpoint");
     if (!m || !buf) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (bytes < checkpoint_bytes(m)) return fail(LBFSI_EINVAL, "checkpoint buffer too small");
@@ -587,6 +592,7 @@ int lbfsi_checkpoint(lbfsi_mesh m, void* buf, size_t bytes) {
 }
 
 int lbfsi_restore(lbfsi_mesh m, const void* buf, size_t bytes) {
+    lbfsi::TraceRange trace_("lbfsi_restore");
     if (!m || !buf) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first (the flow of the checkpointed run)");
     if (bytes < checkpoint_bytes(m)) return fail(LBFSI_EINVAL, "checkpoint buffer too small for this handle");
@@ -654,6 +660,7 @@ int lbfsi_set_graph_steps(lbfsi_mesh m, int graph_steps) {
 }
 
 int lbfsi_autotune(lbfsi_mesh m, int steps_per_trial, int* best_variant, int* best_order, float* ms_per_step) {
+    lbfsi::TraceRange trace_("lbfsi_autotune");
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (steps_per_trial < 1) return fail(LBFSI_EINVAL, "steps_per_trial must be >= 1");

@@ -209,6 +209,7 @@ void drop_graph(lbfsi_batch b) {
 // across all solves, so that the wall and blending-region rows (the most
 // expensive tiles) start first and the far-field rows fill the tail.
 int rebuild_tiles(lbfsi_batch b) {
+    lbfsi::TraceRange trace_("lbfsi tile table");
     drop_graph(b);
     std::vector<TileDev> tiles;
     auto push = [&](size_t k, int ti, int tj) {
@@ -295,6 +296,7 @@ lbfsi::StepArgs step_args(lbfsi_batch b) {
 // reads the step numbers from the device counters, so the graph is valid for
 // every replay until the table changes).
 int capture_graph(lbfsi_batch b, const lbfsi::StepArgs& a) {
+    lbfsi::TraceRange trace_("lbfsi batch graph capture");
     cudaError_t e = lbfsi::prepare_step(b->precision, b->variant, false);
     if (e == cudaSuccess && !b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_err(e, "graph capture setup");
@@ -369,6 +371,7 @@ int lbfsi_batch_destroy(lbfsi_batch b) {
 }
 
 int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
+    lbfsi::TraceRange trace_("lbfsi_batch_add");
     if (!b || !d || !slot) return lbfsi::set_error(LBFSI_EINVAL, "null argument");
     *slot = -1;
     if (d->steps <= 0) return lbfsi::set_error(LBFSI_EINVAL, "steps must be > 0");
@@ -472,6 +475,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
 }
 
 int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
+    lbfsi::TraceRange trace_("lbfsi_batch_step");
     if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
     if (nsteps < 0) return lbfsi::set_error(LBFSI_EINVAL, "nsteps must be >= 0");
     int st = 0;
@@ -561,6 +565,7 @@ int lbfsi_batch_set_graph_steps(lbfsi_batch b, int graph_steps) {
 
 int lbfsi_batch_autotune(lbfsi_batch b, int steps_per_trial, int* best_variant, int* best_order,
                          float* ns_per_node) {
+    lbfsi::TraceRange trace_("lbfsi_batch_autotune");
     if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
     if (steps_per_trial < 1) return lbfsi::set_error(LBFSI_EINVAL, "steps_per_trial must be >= 1");
     const int nv = lbfsi::step_variants(b->precision);

@@ -3,6 +3,8 @@
 // body and flow parameters, device allocation of a mesh's geometry.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstddef>
 #include <string>
 #include <vector>
@@ -11,6 +13,15 @@
 #include "lbfsi_internal.h"
 
 namespace lbfsi {
+
+// NVTX range over a host call of the library (shown by profilers that
+// collect NVTX; without one attached, a push and a pop that do nothing).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // A validated O-grid shape with its derived tables (float64, host).
 struct HostMesh {
