@@ -106,6 +106,32 @@ typedef struct {
  * force partials, body states).  cuda_stream: a cudaStream_t or NULL. */
 int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* out);
 
+/* A structured O-grid given by its node coordinates (any body shape whose
+ * mesh is a ring topology: ellipses, airfoils, ...).  Ring i = 0 is the wall
+ * (the body polygon through the even-indexed wall nodes), ring nr - 1 the far
+ * field; the angular index is periodic.  The nodes must be subparametric
+ * (reading of Sec. II B with structured Q2 elements: each 3 x 3 window with
+ * even first indices -- the last radial window starts at nr - 3 when nr is
+ * even -- is the bilinear image of its four corner nodes), so the
+ * first-order departure solve of Eq. depPnt is exact for the Q2 geometry;
+ * the Jacobian of the index-to-space map must be positive at every node. */
+typedef struct {
+    int nr, ntheta;             /* nr >= 5, ntheta even >= 4 */
+    const double* X;            /* [nr][ntheta][2] node coordinates (host, borrowed) */
+    double xc, yc;              /* mesh centre (reference point of the geometry)   */
+    int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations             */
+    int nbatch;                 /* independent solves sharing the mesh, >= 1        */
+    const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)      */
+} lbfsi_mesh_xy_desc;
+
+/* Create a mesh handle on an O-grid given by node coordinates; otherwise as
+ * lbfsi_create_mesh.  The departure points are found by Newton's method on
+ * the bilinear element (Eq. depPnt) instead of the closed form of a
+ * separable O-grid; one tile shape (lbfsi_set_schedule accepts variant 0).
+ * LBFSI_EINVAL for a mesh that is not subparametric or not positively
+ * oriented. */
+int lbfsi_create_mesh_xy(const lbfsi_mesh_xy_desc* d, void* cuda_stream, lbfsi_mesh* out);
+
 /* Release every device buffer of the handle (synchronises its stream). */
 int lbfsi_destroy_mesh(lbfsi_mesh m);
 

@@ -182,7 +182,7 @@ lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
 // device counters (so the same graph serves every replay).
 int capture_graph(lbfsi_mesh m) {
     lbfsi::TraceRange trace_("lbfsi graph capture");
-    cudaError_t e = lbfsi::prepare_step(m->precision, m->variant, true);
+    cudaError_t e = lbfsi::prepare_step(m->precision, m->variant, true, m->host.general);
     if (e == cudaSuccess && !m->cap_stream) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture setup");
     lbfsi::StepArgs a = make_args(m, 0);
@@ -221,27 +221,66 @@ extern "C" {
 
 const char* lbfsi_last_error(void) { return g_last_error.c_str(); }
 
+namespace {
+
+int check_common(int nr, int nt, int precision, int nbatch, const lbfsi_body_desc* bodies, lbfsi_mesh* out) {
+    if (!out) return fail(LBFSI_EINVAL, "null argument");
+    *out = nullptr;
+    if (precision != LBFSI_FP64 && precision != LBFSI_FP32)
+        return fail(LBFSI_EINVAL, "precision must be LBFSI_FP64 or LBFSI_FP32");
+    if (nbatch < 1) return fail(LBFSI_EINVAL, "nbatch must be >= 1");
+    if (!bodies) return fail(LBFSI_EINVAL, "null body pointer");
+    const long long Nll = (long long)nr * nt;
+    if (nr > 0 && nt > 0 && Nll * 9 * nbatch > (1ll << 31))
+        return fail(LBFSI_EINVAL, "mesh too large for 32-bit node indexing");
+    return LBFSI_OK;
+}
+
+int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc* bodies, void* cuda_stream,
+                  lbfsi_mesh* out);
+
+}  // namespace
+
 int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* out) {
     g_last_error.clear();
-    if (!d || !out) return fail(LBFSI_EINVAL, "null argument");
-    *out = nullptr;
-    if (d->precision != LBFSI_FP64 && d->precision != LBFSI_FP32)
-        return fail(LBFSI_EINVAL, "precision must be LBFSI_FP64 or LBFSI_FP32");
-    if (d->nbatch < 1) return fail(LBFSI_EINVAL, "nbatch must be >= 1");
-    if (!d->bodies) return fail(LBFSI_EINVAL, "null body pointer");
-    const long long Nll = (long long)d->nr * d->ntheta;
-    if (d->nr > 0 && d->ntheta > 0 && Nll * 9 * d->nbatch > (1ll << 31))
-        return fail(LBFSI_EINVAL, "mesh too large for 32-bit node indexing");
+    if (!d) return fail(LBFSI_EINVAL, "null argument");
+    int rc = check_common(d->nr, d->ntheta, d->precision, d->nbatch, d->bodies, out);
+    if (rc) return rc;
     auto m = new lbfsi_mesh_s();
-    int rc = lbfsi::build_host_mesh(d->nr, d->ntheta, d->r, d->e, d->xc, d->yc, m->host);
-    if (!rc) rc = lbfsi::validate_bodies(m->host, d->bodies, d->nbatch);
+    rc = lbfsi::build_host_mesh(d->nr, d->ntheta, d->r, d->e, d->xc, d->yc, m->host);
     if (rc) {
         delete m;
         return rc;
     }
-    m->nbatch = d->nbatch;
-    m->precision = d->precision;
-    m->esize = d->precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
+    return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
+}
+
+int lbfsi_create_mesh_xy(const lbfsi_mesh_xy_desc* d, void* cuda_stream, lbfsi_mesh* out) {
+    g_last_error.clear();
+    if (!d) return fail(LBFSI_EINVAL, "null argument");
+    int rc = check_common(d->nr, d->ntheta, d->precision, d->nbatch, d->bodies, out);
+    if (rc) return rc;
+    auto m = new lbfsi_mesh_s();
+    rc = lbfsi::build_host_mesh_xy(d->nr, d->ntheta, d->X, d->xc, d->yc, m->host);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
+}
+
+namespace {
+
+int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc* bodies, void* cuda_stream,
+                  lbfsi_mesh* out) {
+    int rc = lbfsi::validate_bodies(m->host, bodies, nbatch);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    m->nbatch = nbatch;
+    m->precision = precision;
+    m->esize = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     // tile shape of the float kernel (a tuning knob, every variant computes the
     // same result; see lbfsi_step_variants): default 4 with the solve-minor
@@ -253,11 +292,11 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
         const int k = std::atoi(v);
         m->variant = (k >= 0 && k < lbfsi::step_variants(LBFSI_FP32)) ? k : 4;
     }
-    if (m->precision == LBFSI_FP64) m->variant = 0;
+    if (m->precision == LBFSI_FP64 || m->host.general) m->variant = 0;   // one tile shape
     m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
     const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows;
     m->tiles_per_solve = nti * m->host.ntj;
-    m->bodies.assign(d->bodies, d->bodies + d->nbatch);
+    m->bodies.assign(bodies, bodies + nbatch);
     m->solves.assign(m->nbatch, SolveDev{});
     rc = lbfsi::upload_mesh(m->host, m->precision, m->mem, m->stream, m->dmesh);
     if (rc) {
@@ -304,6 +343,8 @@ int lbfsi_create_mesh(const lbfsi_mesh_desc* d, void* cuda_stream, lbfsi_mesh* o
     *out = m;
     return LBFSI_OK;
 }
+
+}  // namespace
 
 int lbfsi_destroy_mesh(lbfsi_mesh m) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
@@ -633,7 +674,8 @@ int lbfsi_step_variants(int precision) {
 
 int lbfsi_set_schedule(lbfsi_mesh m, int variant, int order) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
-    if (variant < 0 || variant >= lbfsi::step_variants(m->precision) || (order != 0 && order != 1))
+    if (variant < 0 || variant >= (m->host.general ? 1 : lbfsi::step_variants(m->precision)) ||
+        (order != 0 && order != 1))
         return fail(LBFSI_EINVAL, "variant or order out of range");
     if (variant == m->variant && order == m->order) return LBFSI_OK;
     drop_graph(m);
@@ -664,7 +706,7 @@ int lbfsi_autotune(lbfsi_mesh m, int steps_per_trial, int* best_variant, int* be
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (steps_per_trial < 1) return fail(LBFSI_EINVAL, "steps_per_trial must be >= 1");
-    const int nv = lbfsi::step_variants(m->precision);
+    const int nv = m->host.general ? 1 : lbfsi::step_variants(m->precision);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);

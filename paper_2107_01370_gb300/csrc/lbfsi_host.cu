@@ -17,11 +17,7 @@ namespace {
 // adjacent edges (weight*length and edge normal, up to two edges).
 void wall_geometry(HostMesh& m) {
     const int nt = m.nt, ne = nt / 2;
-    std::vector<double> X(2 * nt);
-    for (int j = 0; j < nt; ++j) {
-        X[2 * j] = m.xm + m.r[0] * m.e[2 * j];
-        X[2 * j + 1] = m.ym + m.r[0] * m.e[2 * j + 1];
-    }
+    const std::vector<double>& X = m.xw;
     std::vector<double> en(2 * ne), ds(ne);
     for (int k = 0; k < ne; ++k) {
         const int a = 2 * k, c = (2 * k + 2) % nt;
@@ -155,8 +151,100 @@ int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc,
     if (!sub)
         return set_error(LBFSI_EINVAL,
                          "r and e tables must be subparametric (odd entries = mean of even neighbours)");
+    m.xw.assign(2 * (size_t)nt, 0.0);
+    m.fardir.assign(2 * (size_t)nt, 0.0);
+    for (int j = 0; j < nt; ++j)
+        for (int c = 0; c < 2; ++c) {
+            m.xw[2 * j + c] = (c ? m.ym : m.xm) + m.r[0] * m.e[2 * j + c];
+            m.fardir[2 * j + c] = (m.r[nr - 1] - m.r[nr - 2]) * m.e[2 * j + c];
+        }
     wall_geometry(m);
     geometry_tables(m);
+    return LBFSI_OK;
+}
+
+int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, HostMesh& m) {
+    if (nr < 5) return set_error(LBFSI_EINVAL, "nr must be >= 5");
+    if (nt < 4 || nt % 2) return set_error(LBFSI_EINVAL, "ntheta must be even and >= 4");
+    if (!X) return set_error(LBFSI_EINVAL, "null coordinate pointer");
+    m.general = true;
+    m.nr = nr;
+    m.nt = nt;
+    m.N = nr * nt;
+    m.ntj = tiles_j(nt);
+    m.xm = xc;
+    m.ym = yc;
+    m.X.assign(X, X + 2 * (size_t)m.N);
+    double scale = 0.0;
+    for (double v : m.X) {
+        if (!std::isfinite(v)) return set_error(LBFSI_EINVAL, "node coordinates must be finite");
+        scale = std::max(scale, std::fabs(v));
+    }
+    auto P = [&](int i, int j, int c) { return m.X[2 * ((size_t)i * nt + ((j % nt) + nt) % nt) + c]; };
+    // subparametric: every window is the bilinear image of its corner nodes
+    auto check_window = [&](int wa, int wb) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const double xi = a - 1.0, et = b - 1.0;
+                for (int c = 0; c < 2; ++c) {
+                    const double v = 0.25 * ((1 - xi) * (1 - et) * P(wa, wb, c) + (1 + xi) * (1 - et) * P(wa + 2, wb, c) +
+                                             (1 - xi) * (1 + et) * P(wa, wb + 2, c) + (1 + xi) * (1 + et) * P(wa + 2, wb + 2, c));
+                    if (std::fabs(v - P(wa + a, wb + b, c)) > 1e-12 * scale) return false;
+                }
+            }
+        return true;
+    };
+    for (int wa = 0; wa + 2 < nr; wa += 2)
+        for (int wb = 0; wb < nt; wb += 2)
+            if (!check_window(wa, wb) || (nr % 2 == 0 && !check_window(nr - 3, wb)))
+                return set_error(LBFSI_EINVAL, "node coordinates must be subparametric "
+                                               "(every window the bilinear image of its corners)");
+    m.xw.assign(2 * (size_t)nt, 0.0);
+    m.fardir.assign(2 * (size_t)nt, 0.0);
+    for (int j = 0; j < nt; ++j)
+        for (int c = 0; c < 2; ++c) {
+            m.xw[2 * j + c] = P(0, j, c);
+            m.fardir[2 * j + c] = P(nr - 1, j, c) - P(nr - 2, j, c);
+        }
+    wall_geometry(m);
+    // inverse metric at the nodes: derivatives of X along the index
+    // directions with the field's stencil (central; one-sided on the wall
+    // and far-field rows; periodic in j), then (y_j, -y_i, -x_j, x_i) / det
+    m.jinv.assign(4 * (size_t)m.N, 0.0);
+    for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < nt; ++j) {
+            double di[2], dj[2];
+            for (int c = 0; c < 2; ++c) {
+                if (i == 0)
+                    di[c] = 0.5 * (-3.0 * P(0, j, c) + 4.0 * P(1, j, c) - P(2, j, c));
+                else if (i == nr - 1)
+                    di[c] = 0.5 * (3.0 * P(nr - 1, j, c) - 4.0 * P(nr - 2, j, c) + P(nr - 3, j, c));
+                else
+                    di[c] = 0.5 * (P(i + 1, j, c) - P(i - 1, j, c));
+                dj[c] = 0.5 * (P(i, j + 1, c) - P(i, j - 1, c));
+            }
+            const double det = di[0] * dj[1] - di[1] * dj[0];
+            if (!(det > 0.0))
+                return set_error(LBFSI_EINVAL, "mesh not positively oriented (index-to-space Jacobian <= 0)");
+            double* t = &m.jinv[4 * ((size_t)i * nt + j)];
+            t[0] = dj[1] / det;
+            t[1] = -di[1] / det;
+            t[2] = -dj[0] / det;
+            t[3] = di[0] / det;
+        }
+    // element coefficients per cell
+    m.cellc.assign((size_t)(nr - 1) * nt * CELLC, 0.0);
+    for (int a = 0; a < nr - 1; ++a)
+        for (int b = 0; b < nt; ++b) {
+            const int wa = std::min(2 * (a / 2), nr - 3), wb = 2 * (b / 2);
+            double* t = &m.cellc[((size_t)a * nt + b) * CELLC];
+            for (int c = 0; c < 2; ++c) {
+                const double c00 = P(wa, wb, c), c10 = P(wa + 2, wb, c), c01 = P(wa, wb + 2, c), c11 = P(wa + 2, wb + 2, c);
+                t[0 + c] = 0.25 * (-c00 + c10 - c01 + c11);
+                t[2 + c] = 0.25 * (-c00 - c10 + c01 + c11);
+                t[4 + c] = 0.25 * (c00 - c10 - c01 + c11);
+            }
+        }
     return LBFSI_OK;
 }
 
@@ -169,8 +257,8 @@ int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
         if (!(b.r_out > b.r_in) || !(b.length > 0) || !(b.m_star > 0) || !(b.v_r > 0))
             return set_error(LBFSI_EINVAL, "moving body needs r_out > r_in, length, m_star, v_r > 0");
         for (int j = 0; j < m.nt; ++j) {
-            const double x = m.xm + m.r[0] * m.e[2 * j] - b.xc;
-            const double y = m.ym + m.r[0] * m.e[2 * j + 1] - b.yc;
+            const double x = m.xw[2 * j] - b.xc;
+            const double y = m.xw[2 * j + 1] - b.yc;
             if (std::sqrt(x * x + y * y) >= b.r_in)
                 return set_error(LBFSI_EINVAL, "the wall must lie inside the rigid zone (r_in)");
         }
@@ -278,13 +366,22 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.ym = h.ym;
     d.xm_f = (float)h.xm;
     d.ym_f = (float)h.ym;
-    void *pr, *pe, *pn, *pw, *prt, *pct;
-    int rc = put(h.r, false, &pr);
-    if (!rc) rc = put(h.e, false, &pe);
-    if (!rc) rc = put(h.n0, false, &pn);
+    void *pr = nullptr, *pe = nullptr, *pn = nullptr, *pw = nullptr, *prt = nullptr, *pct = nullptr;
+    void *pxw = nullptr, *pfd = nullptr, *px = nullptr, *pj = nullptr, *pc = nullptr;
+    int rc = put(h.n0, false, &pn);
     if (!rc) rc = put(h.wall_geo, false, &pw);
-    if (!rc) rc = put(h.rowtab, true, &prt);
-    if (!rc) rc = put(h.coltab, true, &pct);
+    if (!rc) rc = put(h.xw, false, &pxw);
+    if (!rc) rc = put(h.fardir, false, &pfd);
+    if (h.general) {
+        if (!rc) rc = put(h.X, true, &px);
+        if (!rc) rc = put(h.jinv, true, &pj);
+        if (!rc) rc = put(h.cellc, true, &pc);
+    } else {
+        if (!rc) rc = put(h.r, false, &pr);
+        if (!rc) rc = put(h.e, false, &pe);
+        if (!rc) rc = put(h.rowtab, true, &prt);
+        if (!rc) rc = put(h.coltab, true, &pct);
+    }
     if (rc) {
         release_mesh(out, mem);
         return rc;
@@ -295,6 +392,12 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.wall_geo = (const double*)pw;
     d.rowtab = prt;
     d.coltab = pct;
+    d.xw = (const double*)pxw;
+    d.fardir = (const double*)pfd;
+    d.general = h.general ? 1 : 0;
+    d.nodex = px;
+    d.jinv = pj;
+    d.cellc = pc;
     return LBFSI_OK;
 }
 
@@ -314,8 +417,8 @@ size_t solve_bytes(int N, int ntj, int precision) {
 
 size_t mesh_bytes(int nr, int nt, int precision) {
     const size_t es = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)nr * sizeof(double) + (size_t)nt * 10 * sizeof(double) +
-           ((size_t)nr * ROWTAB + (size_t)nt * COLTAB) * es + 6 * 256;
+    return (size_t)nr * sizeof(double) + (size_t)nt * 14 * sizeof(double) +
+           ((size_t)nr * ROWTAB + (size_t)nt * COLTAB) * es + 8 * 256;
 }
 
 }  // namespace lbfsi

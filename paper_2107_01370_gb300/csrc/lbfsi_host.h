@@ -23,18 +23,34 @@ struct TraceRange {
     TraceRange& operator=(const TraceRange&) = delete;
 };
 
-// A validated O-grid shape with its derived tables (float64, host).
+// A validated O-grid shape with its derived tables (float64, host).  Either
+// separable (X = centre + r_i e_j: r, e, rowtab, coltab) or general (node
+// coordinates X, per-node inverse metric jinv, per-cell element coefficients
+// cellc).  Both: wall node coordinates xw, far-field outward directions
+// fardir, wall normals n0 and Simpson shares wall_geo.
 struct HostMesh {
     int nr = 0, nt = 0, N = 0, ntj = 0;
     double xm = 0, ym = 0;
-    std::vector<double> r, e, n0, wall_geo, rowtab, coltab;
+    bool general = false;
+    std::vector<double> r, e, n0, wall_geo, rowtab, coltab, xw, fardir, X, jinv, cellc;
 };
+
+// Per-cell element coefficients of a general mesh: 8 entries per cell (a, b),
+// a in [0, nr-2], b in [0, nt-1], row-major: the bilinear map of the cell's
+// Q2 element, X(xi, eta) = X0 + b xi + c eta + d xi eta, as (b_x, b_y, c_x,
+// c_y, d_x, d_y, 0, 0).
+constexpr int CELLC = 8;
 
 // Validate (sizes, increasing radii, subparametric tables) and derive the
 // wall geometry and the per-row / per-column tables.  Returns an lbfsi_status
 // and sets the thread's last error on failure.
 int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc, double yc,
                     HostMesh& out);
+
+// The same for an O-grid given by its node coordinates X [nr][nt][2]
+// (subparametric, positive Jacobian): wall geometry, far-field directions,
+// per-node inverse metric and per-cell element coefficients.
+int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, HostMesh& out);
 
 // Check bodies against a mesh (dof range, blend radii, wall inside the rigid zone).
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n);

@@ -78,6 +78,13 @@ struct MeshDev {
     const void* rowtab;            // [nr][ROWTAB] per-row geometry (element type of the path)
     const void* coltab;            // [nt][COLTAB] per-column geometry
     float xm_f, ym_f;
+    const double* xw;              // [nt][2] wall node coordinates
+    const double* fardir;          // [nt][2] outward direction at the far-field row
+    // general meshes (node coordinates given): element type of the path
+    int general;
+    const void* nodex;             // [N][2] node coordinates
+    const void* jinv;              // [N][4] inverse metric (index derivatives -> d/dX, d/dY)
+    const void* cellc;             // [(nr-1) nt][8] element coefficients per cell
 };
 
 // One solve (one body, one set of fields on one mesh).  Buffers are
@@ -144,7 +151,7 @@ int tile_rows(int precision, int variant);
 int step_variants(int precision);
 // One-time configuration of a step kernel (shared-memory limit, occupancy);
 // done by the first launch, and by this call before a stream capture.
-cudaError_t prepare_step(int precision, int variant, bool uniform);
+cudaError_t prepare_step(int precision, int variant, bool uniform, bool general = false);
 constexpr int TILE_J = 32;
 inline int tiles_j(int nt) { return (nt + TILE_J - 1) / TILE_J; }
 cudaError_t launch_init(int precision, const double* M, void* P, void* Mout, int N, int nbatch,

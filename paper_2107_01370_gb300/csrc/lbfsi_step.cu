@@ -81,11 +81,14 @@ __device__ __forceinline__ void ld4(const double* p, double& a, double& b, doubl
     a = u.x; b = u.y; c = v.x; d = v.y;
 }
 
-template <typename R, int TI, int TJ>
+// Per-cell element coefficients of a general mesh (entries per cell).
+constexpr int CELLC = 8;
+
+template <typename R, int TI, int TJ, bool GEN>
 constexpr size_t step_smem_bytes() {
     using T = Tile<TI, TJ>;
     return sizeof(R) * (size_t)(18 * T::PSS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
-                                T::MH * RS + T::MW * CS);
+                                (GEN ? 6 * T::DS + (TI + 1) * (TJ + 1) * CELLC : T::MH * RS + T::MW * CS));
 }
 
 // Derivative along an index direction of the 1-D quadratic Lagrange interpolant
@@ -197,18 +200,97 @@ __device__ __forceinline__ bool depart_static(const NodeGeo<R>& G, R dt, int& ba
 // grad_X C = J^{-1} (C_xi, C_eta) (Eq. ddx+fem) with the separable O-grid
 // metric, then grad_x = g^{-1} grad_X = F^{-T} grad_X (Eq. dx_ref).
 template <typename R>
-__device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F01, R F10, R F11,
-                                         R* G) {
-    R c0, c1, c2, c3;
-    ld4(col + CT_G, c0, c1, c2, c3);
-    const R j00 = row[RT_IDRC] * c0, j01 = -row[RT_IR] * c1;
-    const R j10 = -row[RT_IDRC] * c2, j11 = row[RT_IR] * c3;
+__device__ __forceinline__ void grad_map_j(R j00, R j01, R j10, R j11, R F00, R F01, R F10, R F11,
+                                           R* G) {
     const R idet = rcp_(F00 * F11 - F01 * F10);
     const R i00 = F11 * idet, i01 = -F01 * idet, i10 = -F10 * idet, i11 = F00 * idet;
     G[0] = i00 * j00 + i10 * j10;
     G[1] = i00 * j01 + i10 * j11;
     G[2] = i01 * j00 + i11 * j10;
     G[3] = i01 * j01 + i11 * j11;
+}
+
+// J^{-1} of the separable O-grid from its row and column tables.
+template <typename R>
+__device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F01, R F10, R F11,
+                                         R* G) {
+    R c0, c1, c2, c3;
+    ld4(col + CT_G, c0, c1, c2, c3);
+    grad_map_j(row[RT_IDRC] * c0, -row[RT_IR] * c1, -row[RT_IDRC] * c2, row[RT_IR] * c3, F00, F01, F10,
+               F11, G);
+}
+
+// Departure point on a general mesh (Eq. depPnt): the node's Q2 element for
+// the adjacent cell (a, b) the displacement d points into (its index-space
+// direction J^{-1} d at the node), then Newton's method on the element's
+// bilinear map X0 + b xi + c eta + d xi eta relative to the node's own local
+// coordinates (xi0, eta0): (b + d eta0) u + (c + d xi0) v + d u v = d, which
+// involves no absolute coordinates.  If the point falls outside that element
+// the other adjacent cell is tried in the direction it left by; a point in no
+// adjacent cell is a CFL violation.  jn: the node's (j00, j01, j10, j11) with
+// d/dX = j00 d/di + j01 d/dj, d/dY = j10 d/di + j11 d/dj.
+template <typename R, int TJ>
+__device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int j, int i0, int j0,
+                                           int nr, int pi0, int sj0, int PWS, R dx, R dy, int& base,
+                                           R& xi, R& eta) {
+    const R di = jn[0] * dx + jn[2] * dy, dj = jn[1] * dx + jn[3] * dy;
+    int da = (!(di < R(0)) || i == 0) ? 0 : -1;
+    int db = !(dj < R(0)) ? 0 : -1;
+    // an element is taken when the point lies in it up to round-off (tin);
+    // failing that, the first candidate within the CFL margin (lim), as for
+    // a wall departure that grazes the body
+    const R tin = R(1) + (sizeof(R) == 4 ? R(1e-5) : R(1e-10));
+    const R lim = R(1) + R(1e-4);
+    bool have = false;
+    int b_base = 0;
+    R b_xi = R(0), b_eta = R(0), b_du = R(2);
+#pragma unroll 1
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        const int ca = i + da, cb = j + db;
+        const int wa = min((ca >> 1) * 2, nr - 3), wb = (cb >> 1) * 2;
+        const R* c = sC + ((ca - (i0 - 1)) * (TJ + 1) + (cb - (j0 - 1))) * CELLC;
+        const R xi0 = R(i - wa - 1), et0 = R(j - wb - 1);
+        const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
+        const R Cx = c[2] + c[4] * xi0, Cy = c[3] + c[5] * xi0;
+        R u = R(0), v = R(0);
+        constexpr int ITS = sizeof(R) == 4 ? 3 : 16;
+#pragma unroll 1
+        for (int it = 0; it < ITS; ++it) {
+            const R rx = Bx * u + Cx * v + c[4] * u * v - dx;
+            const R ry = By * u + Cy * v + c[5] * u * v - dy;
+            const R a11 = Bx + c[4] * v, a12 = Cx + c[4] * u, a21 = By + c[5] * v, a22 = Cy + c[5] * u;
+            const R idet = rcp_(a11 * a22 - a12 * a21);
+            const R du = (a22 * rx - a12 * ry) * idet, dv = (a11 * ry - a21 * rx) * idet;
+            u -= du;
+            v -= dv;
+            if (sizeof(R) == 8 && abs_(du) + abs_(dv) < R(1e-15)) break;
+        }
+        const R x = xi0 + u, e = et0 + v;
+        const R du = max(abs_(u), abs_(v));   // displacement in cells (CFL)
+        if (abs_(x) <= tin && abs_(e) <= tin) {
+            base = (wa - pi0) * PWS + (wb - sj0);
+            xi = x;
+            eta = e;
+            return du <= lim;
+        }
+        if (!have && abs_(x) <= lim && abs_(e) <= lim) {
+            have = true;
+            b_base = (wa - pi0) * PWS + (wb - sj0);
+            b_xi = x;
+            b_eta = e;
+            b_du = du;
+        }
+        bool next = false;
+        if (x > tin && da == -1) { da = 0; next = true; }
+        else if (x < -tin && da == 0 && i > 0) { da = -1; next = true; }
+        if (e > tin && db == -1) { db = 0; next = true; }
+        else if (e < -tin && db == 0) { db = -1; next = true; }
+        if (!next) break;
+    }
+    base = b_base;
+    xi = b_xi;
+    eta = b_eta;
+    return have && b_du <= lim;
 }
 
 // Asynchronous 4- or 8-byte copy global -> shared (cp.async): no register
@@ -301,7 +383,7 @@ __device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const double* 
     return acc;
 }
 
-template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM>
+template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
     using R2 = typename Vec2<R>::T;
@@ -313,8 +395,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     R* sQ = sM + 4 * T::MS;                         // [2][MS]  dQ_x, dQ_y
     R* sG = sQ + 2 * T::MS;                         // [4][DS]  gradient maps
     R* sD = sG + 4 * T::DS;                         // [2][DS]  D_x, D_y
-    R* srow = sD + 2 * T::DS;                       // [MH][ROWTAB] (stride RS)
-    R* scol = srow + T::MH * RS;                    // [MW][COLTAB] (stride CS)
+    R* srow = sD + 2 * T::DS;                       // separable: [MH][ROWTAB] (stride RS)
+    R* scol = srow + T::MH * RS;                    // separable: [MW][COLTAB] (stride CS)
+    R* sX = sD + 2 * T::DS;                         // general: [DS][2] node coordinates
+    R* sJ = sX + 2 * T::DS;                         // general: [DS][4] inverse metric
+    R* sC = sJ + 4 * T::DS;                         // general: [TI+1][TJ+1][CELLC] cells
 
     __shared__ BodyMap<R> mapK, mapS;
     __shared__ BodyMap<double> mapSd;
@@ -385,7 +470,36 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     const int pi0 = i0 - T::HP, sj0 = j0 - 4;       // global index of sp row 0, column 0
 
     // ---- phase 1: stage the geometry tables, M^k and the populations ------
-    {
+    if constexpr (GEN) {
+        // node coordinates and inverse metric on the +-3 region, element
+        // coefficients of the cells adjacent to the tile's nodes
+        const R* gx = reinterpret_cast<const R*>(UNIFORM ? a.umesh.nodex : mg->nodex);
+        const R* gj = reinterpret_cast<const R*>(UNIFORM ? a.umesh.jinv : mg->jinv);
+        const R* gc = reinterpret_cast<const R*>(UNIFORM ? a.umesh.cellc : mg->cellc);
+        for (int idx = tid; idx < T::DS; idx += NT) {
+            const int li = idx / T::DW, lj = idx - li * T::DW;
+            const int i = i0 - T::HD + li;
+            if (i < 0 || i >= nr) continue;
+            const size_t n = (size_t)i * nt + wrap_nt(j0 - T::HD + lj, nt);
+            if constexpr (sizeof(R) == 4) {
+                cp_async8(sX + 2 * idx, gx + 2 * n);
+                cp_async16(sJ + 4 * idx, gj + 4 * n);
+            } else {
+                cp_async16(sX + 2 * idx, gx + 2 * n);
+                cp_async16(sJ + 4 * idx, gj + 4 * n);
+                cp_async16(sJ + 4 * idx + 2, gj + 4 * n + 2);
+            }
+        }
+        constexpr int CE = 16 / (int)sizeof(R), NCC = CELLC / CE;
+        for (int t = tid; t < (TI + 1) * (TJ + 1) * NCC; t += NT) {
+            const int cell = t / NCC, ch = t - cell * NCC;
+            const int la = cell / (TJ + 1), lb = cell - la * (TJ + 1);
+            const int ca = i0 - 1 + la;
+            if (ca < 0 || ca > nr - 2) continue;
+            const size_t g = ((size_t)ca * nt + wrap_nt(j0 - 1 + lb, nt)) * CELLC + ch * CE;
+            cp_async16(sC + cell * CELLC + ch * CE, gc + g);
+        }
+    } else {
         constexpr int CE = 16 / (int)sizeof(R);   // table entries per 16-byte chunk
         for (int t = tid; t < T::MH * (ROWTAB / CE); t += NT) {
             const int li = t / (ROWTAB / CE), c = (t - li * (ROWTAB / CE)) * CE;
@@ -497,13 +611,21 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
             if (i < 0 || i >= nr) continue;
-            const R* row = srow + (li + 1) * RS;
-            const R* col = scol + (lj + 1) * CS;
-            R F00, F01, F10, F11, vx, vy, ex, ey, u0, u1;
-            ld4(col + CT_E, ex, ey, u0, u1);
-            kinematics(mapK, xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
+            R F00, F01, F10, F11, vx, vy;
             R G[4];
-            grad_map(row, col, F00, F01, F10, F11, G);
+            if constexpr (GEN) {
+                kinematics(mapK, sX[2 * idx], sX[2 * idx + 1], F00, F01, F10, F11, vx, vy);
+                R j00, j01, j10, j11;
+                ld4(sJ + 4 * idx, j00, j01, j10, j11);
+                grad_map_j(j00, j01, j10, j11, F00, F01, F10, F11, G);
+            } else {
+                const R* row = srow + (li + 1) * RS;
+                const R* col = scol + (lj + 1) * CS;
+                R ex, ey, u0, u1;
+                ld4(col + CT_E, ex, ey, u0, u1);
+                kinematics(mapK, xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
+                grad_map(row, col, F00, F01, F10, F11, G);
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c) sG[c * T::DS + idx] = G[c];
         }
@@ -584,7 +706,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         if (i == nr - 1) {
             // far field (Sec. III A 2): inlet where the free stream enters,
             // zero-gradient outlet elsewhere (targets of the previous step)
-            const double un = SD(uinf_x) * MD(e)[2 * j] + SD(uinf_y) * MD(e)[2 * j + 1];
+            const double un = SD(uinf_x) * MD(fardir)[2 * j] + SD(uinf_y) * MD(fardir)[2 * j + 1];
             R rho, ux, uy, Tt;
             if (un < 0.0) {
                 rho = pick<R>(SD(rho_inf), SD(rho_inf_f));
@@ -610,16 +732,22 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             continue;
         }
         NodeGeo<R> geo;
-        node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
         R F00, F01, F10, F11, vx, vy;
-        const bool moved = kinematics(mapS, xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
+        bool moved;
+        const int dn = (ti + T::HD) * T::DW + tj + T::HD;   // this node in the +-3 region
+        if constexpr (GEN) {
+            moved = kinematics(mapS, sX[2 * dn], sX[2 * dn + 1], F00, F01, F10, F11, vx, vy);
+        } else {
+            node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
+            moved = kinematics(mapS, xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
+        }
         const R idF = rcp_(F00 * F11 - F01 * F10);
         const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
         unsigned missing = 0u;
         if (i == 0) {
             // missing populations: departure point inside the body,
             // c_hat . n0 > 0, decided in float64 (Sec. III A)
-            const double Xd = MD(xm) + MD(r)[0] * MD(e)[2 * j], Yd = MD(ym) + MD(r)[0] * MD(e)[2 * j + 1];
+            const double Xd = MD(xw)[2 * j], Yd = MD(xw)[2 * j + 1];
             double D00, D01, D10, D11, dvx, dvy;
             kinematics(mapSd, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
             const double idd = 1.0 / (D00 * D11 - D01 * D10);
@@ -635,7 +763,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         R f[9], g[9];
         bool lost = false;
         const int own = (ti + T::HP) * T::PWS + tj + T::HP + 2;   // this node in the staged tile
-        if (!moved && i > 0) {
+        // departure solve of this node for a displacement (dx, dy)
+        auto departure = [&](int inode, R dx, R dy, int& base, R& xi, R& eta) -> bool {
+            if constexpr (GEN)
+                return depart_gen<R, TJ>(sC, sJ + 4 * dn, inode, j, i0, j0, nr, pi0, sj0, T::PWS, dx, dy, base, xi, eta);
+            else
+                return depart(geo, inode, dx, dy, base, xi, eta);
+        };
+        if (!GEN && !moved && i > 0) {
             // a node the blend does not move: c_hat = c, and the rest
             // population's departure point is the node itself
             {
@@ -680,7 +815,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const R hx = i00 * cx + i01 * cy - vx, hy = i10 * cx + i11 * cy - vy;
             int base;
             R xi, eta;
-            if (depart(geo, i, -dt * hx, -dt * hy, base, xi, eta)) {
+            if (departure(i, -dt * hx, -dt * hy, base, xi, eta)) {
                 R Lx[3], Ly[3];
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
@@ -702,7 +837,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             int base;
             R xi, eta;
             R rhoB = sM[m], TB = sM[3 * T::MS + m];
-            if (depart(geo, 0, dt * (R)MD(n0)[2 * j], dt * (R)MD(n0)[2 * j + 1], base, xi, eta)) {
+            if (departure(0, dt * (R)MD(n0)[2 * j], dt * (R)MD(n0)[2 * j + 1], base, xi, eta)) {
                 R Lx[3], Ly[3];
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
@@ -723,7 +858,13 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 atomicOr(a.status, ST_BPOINT);
             }
             R G[4];
-            grad_map(row, col, F00, F01, F10, F11, G);
+            if constexpr (GEN) {
+                R j00, j01, j10, j11;
+                ld4(sJ + 4 * dn, j00, j01, j10, j11);
+                grad_map_j(j00, j01, j10, j11, F00, F01, F10, F11, G);
+            } else {
+                grad_map(row, col, F00, F01, F10, F11, G);
+            }
             R gr[3][2];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -774,8 +915,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const double sxx = -p - am * pxx, sxy = -am * pxy, syy = -p - am * pyy;
             const double R00 = 1.0 + mapSd.a00, R01 = mapSd.a01, R10 = mapSd.a10, R11 = 1.0 + mapSd.a11;
             const BodyDev& bd = *(SD(body) + sb);
-            const double Xd = MD(xm) + MD(r)[0] * MD(e)[2 * j] - bd.xp;
-            const double Yd = MD(ym) + MD(r)[0] * MD(e)[2 * j + 1] - bd.yp;
+            const double Xd = MD(xw)[2 * j] - bd.xp;
+            const double Yd = MD(xw)[2 * j + 1] - bd.yp;
             const double rx = R00 * Xd + R01 * Yd, ry = R10 * Xd + R11 * Yd;
             const double* wg = MD(wall_geo) + 6 * j;
 #pragma unroll
@@ -907,21 +1048,21 @@ __global__ void k_advance(const BodyDev* __restrict__ bodies, const double* __re
 // Tile shapes of the step kernel (angular tile width one warp).
 constexpr int TJ = TILE_J;
 
-template <typename R, int TI, int NT, int MINB, bool UNIFORM>
+template <typename R, int TI, int NT, int MINB, bool UNIFORM, bool GEN = false>
 struct StepKernel {
     static inline int resident = -1;   // CTAs resident on the whole GPU at once
 
     static cudaError_t configure() {
         if (resident >= 0) return cudaSuccess;
-        const size_t smem = step_smem_bytes<R, TI, TJ>();
-        cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ, NT, MINB, UNIFORM>,
+        const size_t smem = step_smem_bytes<R, TI, TJ, GEN>();
+        cudaError_t e = cudaFuncSetAttribute(k_step<R, TI, TJ, NT, MINB, UNIFORM, GEN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<R, TI, TJ, NT, MINB, UNIFORM>, NT, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<R, TI, TJ, NT, MINB, UNIFORM, GEN>, NT, smem);
         if (e != cudaSuccess) return e;
         resident = sms * per_sm;
         return cudaSuccess;
@@ -930,16 +1071,16 @@ struct StepKernel {
     static cudaError_t launch(const StepArgs& a, int nbatch, cudaStream_t s) {
         cudaError_t e = configure();
         if (e != cudaSuccess) return e;
-        const size_t smem = step_smem_bytes<R, TI, TJ>();
+        const size_t smem = step_smem_bytes<R, TI, TJ, GEN>();
         if (UNIFORM) {
             // prefetch distance: one resident wave
             StepArgs b = a;
             b.pf_dist = resident;
             const int nti = (a.umesh.nr + TI - 1) / TI;
             const dim3 grid = a.uorder ? dim3(nbatch, a.umesh.ntj, nti) : dim3(a.umesh.ntj, nti, nbatch);
-            k_step<R, TI, TJ, NT, MINB, UNIFORM><<<grid, NT, smem, s>>>(b);
+            k_step<R, TI, TJ, NT, MINB, UNIFORM, GEN><<<grid, NT, smem, s>>>(b);
         } else {
-            k_step<R, TI, TJ, NT, MINB, UNIFORM><<<a.ntiles, NT, smem, s>>>(a);
+            k_step<R, TI, TJ, NT, MINB, UNIFORM, GEN><<<a.ntiles, NT, smem, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -948,6 +1089,12 @@ struct StepKernel {
 template <typename R, int TI, int NT, int MINB, bool UNIFORM>
 static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) {
     return StepKernel<R, TI, NT, MINB, UNIFORM>::launch(a, nbatch, s);
+}
+
+// General meshes (node coordinates given): uniform launches, one tile shape.
+static cudaError_t launch_general(const StepArgs& a, int precision, int nbatch, cudaStream_t s) {
+    if (precision == 0) return StepKernel<double, 8, 256, 1, true, true>::launch(a, nbatch, s);
+    return StepKernel<float, 8, 256, 2, true, true>::launch(a, nbatch, s);
 }
 
 template <bool UNIFORM>
@@ -962,7 +1109,10 @@ static cudaError_t configure_any(int precision, int variant) {
     }
 }
 
-cudaError_t prepare_step(int precision, int variant, bool uniform) {
+cudaError_t prepare_step(int precision, int variant, bool uniform, bool general) {
+    if (general)
+        return precision == 0 ? StepKernel<double, 8, 256, 1, true, true>::configure()
+                              : StepKernel<float, 8, 256, 2, true, true>::configure();
     return uniform ? configure_any<true>(precision, variant) : configure_any<false>(precision, variant);
 }
 
@@ -986,6 +1136,7 @@ cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStrea
 
 cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,
                                 cudaStream_t s) {
+    if (a.umesh.general) return launch_general(a, precision, nbatch, s);
     return launch_any<true>(a, precision, variant, nbatch, s);
 }
 

@@ -149,6 +149,90 @@ def cylinder_case(nr: int, ntheta: int, *, radius: float = 0.5, r_far: float = 2
                         bodies=[b], steps=steps, name=name)
 
 
+# ----- general (non-separable) O-grids given by node coordinates ----------
+
+def radial_fractions(nr: int, first: float) -> np.ndarray:
+    """Radial parameter t_i in [0, 1] of an O-grid ring (t_0 = 0 at the
+    wall, t_{nr-1} = 1 at the far field): element widths grow geometrically
+    from 2*first, odd rows at the midpoints (subparametric; for even nr the
+    last three spacings equal)."""
+    return ogrid_radii(nr, 0.0, 1.0, first)
+
+
+def closed_curve_midpoints(P: np.ndarray) -> np.ndarray:
+    """Points of a closed curve at the even indices; odd indices replaced by
+    the midpoints of their even neighbours (the straight element edges of
+    the subparametric mesh)."""
+    Q = np.array(P, dtype=np.float64)
+    Q[1::2] = 0.5 * (Q[0::2] + np.roll(Q[0::2], -1, axis=0))
+    return Q
+
+
+def algebraic_ogrid(wall: np.ndarray, nr: int, r_far: float, first: float,
+                    centre=(0.0, 0.0)) -> np.ndarray:
+    """O-grid between a closed wall curve (wall[ntheta, 2], counter-
+    clockwise, even points on the body at the curve parameter 2 pi j /
+    ntheta, odd points midpoints) and the circle of radius r_far about
+    'centre': X[i, j] = W_j + t_i (C_j - W_j) along straight lines, C_j the
+    circle point at the same parameter angle (midpoints likewise), so the
+    lines leave a smooth convex wall close to its normal.  Each 3x3 window is
+    then the bilinear image of its corners.  A circular wall about 'centre'
+    gives the separable O-grid."""
+    W = np.asarray(wall, dtype=np.float64)
+    nt = W.shape[0]
+    ang = 2.0 * np.pi * np.arange(0, nt, 2) / nt
+    C = np.empty_like(W)
+    C[0::2, 0] = centre[0] + r_far * np.cos(ang)
+    C[0::2, 1] = centre[1] + r_far * np.sin(ang)
+    C = closed_curve_midpoints(C)
+    t = radial_fractions(nr, first)
+    X = W[None, :, :] + t[:, None, None] * (C - W)[None, :, :]
+    return X
+
+
+def ellipse_wall(ntheta: int, a: float, b: float, centre=(0.0, 0.0)) -> np.ndarray:
+    """Elliptic body of semi-axes a (x) and b (y), wall nodes at equal
+    parameter angles (odd nodes: chord midpoints)."""
+    th = 2.0 * np.pi * np.arange(ntheta) / ntheta
+    P = np.stack([centre[0] + a * np.cos(th), centre[1] + b * np.sin(th)], axis=1)
+    return closed_curve_midpoints(P)
+
+
+@dataclass
+class XYCase:
+    """A case on a general O-grid: node coordinates X[nr, ntheta, 2]."""
+    nr: int
+    ntheta: int
+    X: np.ndarray
+    centre: tuple
+    flow: FlowSpec
+    bodies: list = field(default_factory=list)
+    steps: int = 0
+    name: str = ""
+
+    @property
+    def nodes(self) -> int:
+        return self.nr * self.ntheta
+
+
+def xy_case(wall: np.ndarray, nr: int, *, r_far: float = 8.0, centre=(0.0, 0.0),
+            length: float = 1.0, ma: float = 0.2, re: float = 100.0, t_inf: float = 1.0 / 3.0,
+            gamma: float = 1.4, pr: float = 0.71, body: BodySpec | None = None, steps: int = 0,
+            name: str = "") -> XYCase:
+    """General O-grid case: first radial spacing equal to the smallest wall
+    edge spacing, time step a third of it (the constant near-wall CFL of the
+    cylinder cases)."""
+    W = np.asarray(wall, dtype=np.float64)
+    d = np.hypot(*(np.roll(W, -1, axis=0) - W).T)
+    first = float(d.min())
+    span = float(np.min(np.hypot(W[:, 0] - centre[0], W[:, 1] - centre[1])))
+    X = algebraic_ogrid(W, nr, r_far, first / max(r_far - span, 1e-12), centre)
+    flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr, dt=first / 3.0, length=length)
+    b = body if body is not None else BodySpec(dof=0)
+    return XYCase(nr=nr, ntheta=W.shape[0], X=X, centre=tuple(centre), flow=flow, bodies=[b],
+                  steps=steps, name=name)
+
+
 def fixed_cylinder_128x64(steps: int = 1000) -> CylinderCase:
     """Fixed cylinder, 128 radial x 64 angular nodes, far field at 20 D,
     Re 100, Ma 0.2 (FP64 parity workload)."""

@@ -30,7 +30,8 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_remove", "lbfsi_batch_memory", "lbfsi_step_variants",
             "lbfsi_set_schedule", "lbfsi_get_schedule", "lbfsi_set_graph_steps", "lbfsi_autotune",
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
-            "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore"]
+            "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
+            "lbfsi_create_mesh_xy"]
 
 
 class LbfsiError(RuntimeError):
@@ -56,6 +57,13 @@ class FlowParams(ctypes.Structure):
 class MeshDesc(ctypes.Structure):
     _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
                 ("r", ctypes.POINTER(ctypes.c_double)), ("e", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
+                ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class MeshXYDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("X", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
 
@@ -184,6 +192,28 @@ class Mesh:
         h = ctypes.c_void_p()
         _check(lib.lbfsi_create_mesh(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
         self.h = h
+
+    @classmethod
+    def xy(cls, X, bodies, precision=FP64, centre=(0.0, 0.0), stream=None):
+        """Handle of an O-grid given by node coordinates X [nr, ntheta, 2]
+        (lbfsi_create_mesh_xy)."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.r = self.e = None
+        self.nr, self.nt = self.X.shape[0], self.X.shape[1]
+        self.N = self.nr * self.nt
+        self.nbatch = len(bodies)
+        self.precision = precision
+        self._bodies = (BodyDesc * self.nbatch)(*[body_desc(b) for b in bodies])
+        d = MeshXYDesc(self.nr, self.nt, _dptr(self.X), centre[0], centre[1], precision, self.nbatch,
+                       self._bodies)
+        h = ctypes.c_void_p()
+        self.h = None
+        _check(lib.lbfsi_create_mesh_xy(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        return self
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

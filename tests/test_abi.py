@@ -76,3 +76,43 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
     assert lib.lbfsi_step(None, 1) == lbfsi.EINVAL
     assert lib.lbfsi_launch_count(None) == -1
+
+
+def test_xy_mesh_struct_layout_matches_c(tmp_path):
+    from paper_2107_01370_gb300 import lbfsi
+    src = tmp_path / "xy.c"
+    src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu\\n", sizeof(lbfsi_mesh_xy_desc),'
+                   'offsetof(lbfsi_mesh_xy_desc, X), offsetof(lbfsi_mesh_xy_desc, bodies));return 0;}\n')
+    exe = tmp_path / "xy"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(lbfsi.MeshXYDesc), lbfsi.MeshXYDesc.X.offset,
+                   lbfsi.MeshXYDesc.bodies.offset]
+
+
+def test_general_mesh_validation_without_gpu(lib):
+    """lbfsi_create_mesh_xy rejects, before touching the device, a mesh whose
+    nodes are not subparametric and one that is not positively oriented."""
+    import numpy as np
+    from paper_2107_01370_gb300 import inputs, lbfsi
+    wall = inputs.ellipse_wall(16, 0.6, 0.4)
+    X = inputs.algebraic_ogrid(wall, 9, 4.0, 0.05)
+    body = lbfsi.BodyDesc()
+    h = ctypes.c_void_p()
+
+    def create(Xa):
+        Xa = np.ascontiguousarray(Xa)
+        d = lbfsi.MeshXYDesc(Xa.shape[0], Xa.shape[1], Xa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             0.0, 0.0, 0, 1, ctypes.pointer(body))
+        return lib.lbfsi_create_mesh_xy(ctypes.byref(d), None, ctypes.byref(h))
+
+    bad = X.copy()
+    bad[3, 5] += 1e-3                      # an odd node off its bilinear position
+    assert create(bad) == lbfsi.EINVAL
+    assert b"subparametric" in lib.lbfsi_last_error()
+    assert create(np.roll(X[:, ::-1], 1, axis=1)) == lbfsi.EINVAL   # clockwise: j -> -j
+    assert b"oriented" in lib.lbfsi_last_error()
+    nan = X.copy()
+    nan[0, 0, 0] = np.nan
+    assert create(nan) == lbfsi.EINVAL
