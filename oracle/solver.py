@@ -42,6 +42,8 @@ def body_dict(spec, flow_rho, u_inf):
          ("xc", "yc", "xp", "yp", "r_in", "r_out", "length", "m_star", "v_r", "zeta",
           "x_alpha", "r_alpha", "wh_wa")}
     b["dof"] = int(spec.dof)
+    b["pitch_amp"] = float(getattr(spec, "pitch_amp", 0.0))
+    b["forced_periods"] = float(getattr(spec, "forced_periods", 0.0))
     if b["dof"] == 1:
         b["m"], b["k"], b["c"] = structure.one_dof_parameters(
             b["m_star"], b["v_r"], b["zeta"], b["length"], flow_rho, u_inf)
@@ -49,6 +51,11 @@ def body_dict(spec, flow_rho, u_inf):
         (b["m"], b["s_a"], b["i_a"], b["k_h"], b["k_a"]) = structure.two_dof_parameters(
             b["m_star"], b["v_r"], b["x_alpha"], b["r_alpha"], b["wh_wa"],
             0.5 * b["length"], flow_rho, u_inf)
+        # forced pitching (Sec. IV D): alpha = pitch_amp sin(w_alpha t) for
+        # forced_periods periods of the uncoupled pitch frequency, then free
+        half = 0.5 * b["length"]
+        b["w_a"] = u_inf / (b["v_r"] * half * math.sqrt(b["m_star"]))
+        b["t_forced"] = b["forced_periods"] * 2.0 * math.pi / b["w_a"]
     return b
 
 
@@ -187,6 +194,11 @@ class Solver:
             if b["dof"] == 1:
                 s["h"], s["hdot"] = structure.advance_one_dof(
                     st["h"], st["hdot"], force[1], b["m"], b["k"], b["c"], dt)
+            elif b["dof"] == 2 and (self.n + 1) * dt <= b["t_forced"]:
+                # a step that ends within the forcing interval: pitch prescribed
+                s["h"], s["alpha"], s["hdot"], s["adot"] = structure.advance_plunge_forced_pitch(
+                    st["h"], st["hdot"], force[1], b["m"], b["s_a"], b["k_h"], b["pitch_amp"],
+                    b["w_a"], self.n, dt)
             elif b["dof"] == 2:
                 s["h"], s["alpha"], s["hdot"], s["adot"] = structure.advance_two_dof(
                     st["h"], st["alpha"], st["hdot"], st["adot"], force[1], force[2],

@@ -54,6 +54,27 @@ def advance_one_dof(h, hdot, fy, m, k, c, dt):
     return float(y[0]), float(y[1])
 
 
+def advance_plunge_forced_pitch(h, hdot, fy, m, s_a, k_h, amp, w, n, dt):
+    """Step n (from t = n dt to (n + 1) dt) of the pitch-plunge model (Eq.
+    2dofSM) with the pitch prescribed, alpha(t) = amp sin(w t) (the forced
+    pitching that starts the paper's flutter runs, Sec. IV D): the plunge row
+    m h'' + S_alpha alpha''(t) + k_h h = F_y integrated by RK4 with alpha''
+    evaluated at the stage times n dt, (n + 1/2) dt, (n + 1) dt; alpha and
+    its rate at (n + 1) dt are the prescribed values.  Returns h, alpha,
+    hdot, adot."""
+    def rhs(t, y):
+        acc_a = -amp * w * w * math.sin(w * t)
+        return np.array([y[1], (fy - k_h * y[0] - s_a * acc_a) / m])
+    t0, tm, t1 = n * dt, (n + 0.5) * dt, (n + 1) * dt
+    y = np.array([h, hdot], dtype=np.float64)
+    k1 = rhs(t0, y)
+    k2 = rhs(tm, y + 0.5 * dt * k1)
+    k3 = rhs(tm, y + 0.5 * dt * k2)
+    k4 = rhs(t1, y + dt * k3)
+    y = y + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    return float(y[0]), amp * math.sin(w * t1), float(y[1]), amp * w * math.cos(w * t1)
+
+
 def advance_two_dof(h, alpha, hdot, adot, fy, m_ea, m, s_a, i_a, k_h, k_a, dt):
     """[m S; S I] [h''; a''] + [k_h h; k_a a] = [F_y; M_EA]  (Eq. 2dofSM).
     Sign convention of this oracle: h positive up, alpha positive

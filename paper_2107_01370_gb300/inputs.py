@@ -93,6 +93,8 @@ class BodySpec:
     x_alpha: float = 0.0
     r_alpha: float = 1.0
     wh_wa: float = 1.0
+    pitch_amp: float = 0.0       # forced pitching amplitude [rad] (pitch-plunge)
+    forced_periods: float = 0.0  # duration of the forcing in uncoupled pitch periods
 
 
 @dataclass

@@ -171,3 +171,32 @@ def test_stress_at_equilibrium_is_pressure():
 
 def test_zero_state_helper():
     assert zero_state() == {"h": 0.0, "alpha": 0.0, "hdot": 0.0, "adot": 0.0}
+
+
+def test_forced_pitch_step_matches_the_driven_oscillator():
+    """Prescribed pitch alpha = A sin(w t) (Sec. IV D forcing): with no fluid
+    load the plunge row m h'' + k_h h = -S_alpha alpha''(t) is a driven
+    oscillator with the closed-form response from rest
+    h = C (sin(w t) - (w / w_h) sin(w_h t)),  C = S_alpha A w^2 / (k_h - m w^2);
+    RK4 reproduces it to its fourth-order error, and alpha, alpha' are the
+    prescribed values at every step end."""
+    import math
+    from oracle import structure as S
+    m, s_a, k_h, A, w = 2.0, 0.3, 5.0, 0.0175, 1.3
+    w_h = math.sqrt(k_h / m)
+    C = s_a * A * w * w / (k_h - m * w * w)
+    errs = []
+    for dt in (1e-2, 5e-3):
+        h = hd = 0.0
+        t = 0.0
+        n = int(round(3.0 / dt))
+        for k in range(n):
+            h, a, hd, ad = S.advance_plunge_forced_pitch(h, hd, 0.0, m, s_a, k_h, A, w, k, dt)
+            t = (k + 1) * dt
+            assert a == A * math.sin(w * t) and ad == A * w * math.cos(w * t)
+        exact = C * (math.sin(w * t) - (w / w_h) * math.sin(w_h * t))
+        exact_d = C * w * (math.cos(w * t) - math.cos(w_h * t))
+        assert abs(h - exact) < 1e-8 * abs(C) * (dt / 1e-2) ** 4
+        assert abs(hd - exact_d) < 1e-8 * abs(C * w) * (dt / 1e-2) ** 4
+        errs.append(abs(h - exact))
+    assert 12.0 < errs[0] / errs[1] < 20.0        # fourth order
