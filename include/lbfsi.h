@@ -77,6 +77,13 @@ typedef struct {
     double length;
     double m_star, v_r, zeta;
     double x_alpha, r_alpha, wh_wa;
+    /* Forced pitching (pitch-plunge, Sec. IV D): alpha(t) = pitch_amp
+     * sin(omega_alpha t) is prescribed during the first forced_periods
+     * periods 2 pi / omega_alpha (t = step number x dt; a step is forced when
+     * it ends within that time), the plunge responding to the load and to the
+     * prescribed pitch acceleration; the body is free afterwards.  0, 0: free
+     * from the start. */
+    double pitch_amp, forced_periods;
 } lbfsi_body_desc;
 
 /* Free stream and transport (Sec. II C): U_inf = ma sqrt(gamma t_inf) along +x,
@@ -160,7 +167,8 @@ int lbfsi_body_forces(lbfsi_mesh m, double* out);
 
 /* RK4 of the body ODEs only (Sec. III B), with the given host loads
  * [nbatch][3] held constant over dt (NULL = the last step's loads).  Updates
- * the body states (the current state becomes the previous one). */
+ * the body states (the current state becomes the previous one); a forced
+ * pitch is evaluated at the handle's step number x dt. */
 int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt);
 
 /* Body states after the structural update of the last step, host out [nbatch]. */

@@ -496,7 +496,8 @@ int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
     }
     cudaError_t e = cudaMemcpyAsync(m->d_loads_tmp, ld.data(), ld.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, m->nbatch, m->d_maps[m->cur()], m->stream);
+        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, (long long)m->host_k, m->nbatch,
+                                  m->d_maps[m->cur()], m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "advance_bodies");
     return check_status(m);

@@ -310,9 +310,31 @@ __host__ __device__ inline void build_maps(const BodyDev& b, const BodyStateDev&
 }
 
 // Classical RK4 of the body ODE over dt with the load (Fx, Fy, M) held fixed
-// (Sec. III B; weak coupling of Sec. III).
+// (Sec. III B; weak coupling of Sec. III), for step n (from n dt to (n+1) dt).
+// A pitch-plunge body in its forcing interval (Sec. IV D) has the pitch
+// prescribed, alpha = amp sin(w_a t): the plunge row is integrated with the
+// prescribed pitch acceleration at the stage times and alpha, alpha' are set
+// to their values at (n+1) dt.
 __host__ __device__ inline BodyStateDev rk4_body(const BodyDev& b, BodyStateDev s, double fy,
-                                                 double mz, double dt) {
+                                                 double mz, double dt, long long n) {
+    if (b.dof == 2 && (double)(n + 1) * dt <= b.t_forced) {
+        const double w = b.w_a, amp = b.pitch_amp;
+        auto acc = [&](double t, double h, double v) {
+            const double acc_a = -amp * w * w * sin(w * t);
+            return (fy - b.k_h * h - b.s_a * acc_a) / b.m;
+        };
+        const double t0 = (double)n * dt, tm = ((double)n + 0.5) * dt, t1 = (double)(n + 1) * dt;
+        const double h0 = s.h, v0 = s.hdot;
+        const double k1h = v0, k1v = acc(t0, h0, v0);
+        const double k2h = v0 + 0.5 * dt * k1v, k2v = acc(tm, h0 + 0.5 * dt * k1h, v0 + 0.5 * dt * k1v);
+        const double k3h = v0 + 0.5 * dt * k2v, k3v = acc(tm, h0 + 0.5 * dt * k2h, v0 + 0.5 * dt * k2v);
+        const double k4h = v0 + dt * k3v, k4v = acc(t1, h0 + dt * k3h, v0 + dt * k3v);
+        s.h = h0 + dt / 6.0 * (k1h + 2.0 * k2h + 2.0 * k3h + k4h);
+        s.hdot = v0 + dt / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+        s.alpha = amp * sin(w * t1);
+        s.adot = amp * w * cos(w * t1);
+        return s;
+    }
     if (b.dof == 1) {
         auto acc = [&](double h, double v) { return (fy - b.k * h - b.c * v) / b.m; };
         const double h0 = s.h, v0 = s.hdot;

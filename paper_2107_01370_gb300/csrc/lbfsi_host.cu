@@ -256,6 +256,8 @@ int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
         if (b.dof == 0) continue;
         if (!(b.r_out > b.r_in) || !(b.length > 0) || !(b.m_star > 0) || !(b.v_r > 0))
             return set_error(LBFSI_EINVAL, "moving body needs r_out > r_in, length, m_star, v_r > 0");
+        if (!(b.forced_periods >= 0.0) || !std::isfinite(b.pitch_amp) || !std::isfinite(b.forced_periods))
+            return set_error(LBFSI_EINVAL, "forced pitching needs a finite amplitude and forced_periods >= 0");
         for (int j = 0; j < m.nt; ++j) {
             const double x = m.xw[2 * j] - b.xc;
             const double y = m.xw[2 * j + 1] - b.yc;
@@ -290,6 +292,9 @@ BodyDev body_dev(const lbfsi_body_desc& d, double rho, double U) {
         b.i_a = d.r_alpha * d.r_alpha * b.m * bh * bh;
         b.k_h = b.m * wh * wh;
         b.k_a = b.i_a * wa * wa;
+        b.pitch_amp = d.pitch_amp;
+        b.w_a = wa;
+        b.t_forced = d.forced_periods * 2.0 * pi / wa;
     }
     return b;
 }

@@ -22,6 +22,7 @@ struct BodyDev {
     double r_in, r_out, inv_w;   // blend radii, 1 / (r_out - r_in)
     double m, k, c;          // transverse: m h'' + c h' + k h = F_y
     double s_a, i_a, k_h, k_a;  // pitch-plunge: [m S; S I] y'' + diag(k_h, k_a) y = [F_y; M]
+    double pitch_amp, w_a, t_forced;  // forced pitch amp sin(w_a t) while (n + 1) dt <= t_forced
 };
 
 struct BodyStateDev {
@@ -164,7 +165,7 @@ cudaError_t launch_prepare(const BodyDev* bodies, const BodyStateDev* S_cur,
                            cudaStream_t s);
 // RK4 of every body over dt with the given loads from maps->S_next; the
 // result becomes S_next and the old S_next S_vgprev and S_cur.
-cudaError_t launch_advance(const BodyDev* bodies, const double* loads, double dt, int nbatch,
-                           StepMaps* maps, cudaStream_t s);
+cudaError_t launch_advance(const BodyDev* bodies, const double* loads, double dt, long long n,
+                           int nbatch, StepMaps* maps, cudaStream_t s);
 
 }  // namespace lbfsi

@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             if (l == 0) {
                 const BodyDev bd = *(SD(body) + sb);
                 const BodyStateDev Sn = ((cur ? mptr[1] : mptr[0]) + sb)->S_next;
-                const BodyStateDev Snew = rk4_body(bd, Sn, F[1], F[2], SD(dt));
+                const BodyStateDev Snew = rk4_body(bd, Sn, F[1], F[2], SD(dt), (long long)kstep);
                 StepMaps mo;
                 build_maps(bd, Sn, Snew, Sn, SD(dt), mo);
                 for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
@@ -1035,13 +1035,13 @@ __global__ void k_prepare(const BodyDev* __restrict__ bodies, const BodyStateDev
 }
 
 __global__ void k_advance(const BodyDev* __restrict__ bodies, const double* __restrict__ loads,
-                          double dt, int nbatch, StepMaps* maps) {
+                          double dt, long long n, int nbatch, StepMaps* maps) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbatch) return;
     StepMaps m = maps[b];
     const BodyStateDev s = m.S_next;
-    const BodyStateDev n = rk4_body(bodies[b], s, loads[b * 3 + 1], loads[b * 3 + 2], dt);
-    build_maps(bodies[b], m.S_cur, n, s, dt, m);
+    const BodyStateDev ns = rk4_body(bodies[b], s, loads[b * 3 + 1], loads[b * 3 + 2], dt, n);
+    build_maps(bodies[b], m.S_cur, ns, s, dt, m);
     maps[b] = m;
 }
 
@@ -1170,9 +1170,9 @@ cudaError_t launch_prepare(const BodyDev* bodies, const BodyStateDev* S_cur,
     return cudaGetLastError();
 }
 
-cudaError_t launch_advance(const BodyDev* bodies, const double* loads, double dt, int nbatch,
-                           StepMaps* maps, cudaStream_t s) {
-    k_advance<<<(nbatch + 127) / 128, 128, 0, s>>>(bodies, loads, dt, nbatch, maps);
+cudaError_t launch_advance(const BodyDev* bodies, const double* loads, double dt, long long n,
+                           int nbatch, StepMaps* maps, cudaStream_t s) {
+    k_advance<<<(nbatch + 127) / 128, 128, 0, s>>>(bodies, loads, dt, n, nbatch, maps);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,8 @@ class BodyDesc(ctypes.Structure):
                 ("r_out", ctypes.c_double), ("length", ctypes.c_double),
                 ("m_star", ctypes.c_double), ("v_r", ctypes.c_double), ("zeta", ctypes.c_double),
                 ("x_alpha", ctypes.c_double), ("r_alpha", ctypes.c_double),
-                ("wh_wa", ctypes.c_double)]
+                ("wh_wa", ctypes.c_double), ("pitch_amp", ctypes.c_double),
+                ("forced_periods", ctypes.c_double)]
 
 
 class FlowParams(ctypes.Structure):
@@ -158,7 +159,7 @@ def body_desc(spec) -> BodyDesc:
     """BodyDesc from any object carrying the BodySpec attribute names."""
     return BodyDesc(int(spec.dof), spec.xc, spec.yc, spec.xp, spec.yp, spec.r_in, spec.r_out,
                     spec.length, spec.m_star, spec.v_r, spec.zeta, spec.x_alpha, spec.r_alpha,
-                    spec.wh_wa)
+                    spec.wh_wa, getattr(spec, "pitch_amp", 0.0), getattr(spec, "forced_periods", 0.0))
 
 
 def flow_params(flow) -> FlowParams:

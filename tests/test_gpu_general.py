@@ -140,3 +140,26 @@ def test_general_path_reports_cfl_violation(L):
         m.synchronize()
     assert ei.value.code == L.EDEPARTURE
     m.close()
+
+
+def test_fp64_forced_then_free_pitching_matches_oracle(L):
+    """Forced pitching (Sec. IV D): alpha = A sin(w_alpha t) prescribed over
+    the first steps, the plunge driven by the load and the pitch
+    acceleration, then the free pitch-plunge system; the switch falls between
+    steps 4 and 5 of the run, on the thin section's general O-grid."""
+    base = inputs.BodySpec(dof=2, xp=-0.25, yp=0.0, r_in=0.6, r_out=2.0, m_star=8.0, v_r=1.2,
+                           x_alpha=0.2, r_alpha=0.5, wh_wa=0.4, length=1.0)
+    case = inputs.xy_case(inputs.ellipse_wall(96, 0.5, 0.06), 40, r_far=8.0, body=base)
+    u_inf = case.flow.ma * np.sqrt(case.flow.gamma * case.flow.t_inf)
+    w_a = u_inf / (base.v_r * 0.5 * np.sqrt(base.m_star))
+    base.pitch_amp = 0.2
+    base.forced_periods = 5.5 * case.flow.dt * w_a / (2.0 * np.pi)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=23)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 10, L.FP64)
+    assert field_err(f, r.M) < 1e-12
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+    for k in ("h", "alpha", "hdot", "adot"):
+        assert abs(st[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+    # the pitch is free after the switch: not the prescribed sine any more
+    t = 10 * case.flow.dt
+    assert abs(s.S[0]["alpha"] - 0.2 * np.sin(w_a * t)) > 1e-9
