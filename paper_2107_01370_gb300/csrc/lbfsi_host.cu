@@ -371,6 +371,12 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.ym = h.ym;
     d.xm_f = (float)h.xm;
     d.ym_f = (float)h.ym;
+    d.emin = 0.0;
+    if (!h.general) {
+        d.emin = 1e300;
+        for (int j = 0; j < h.nt; ++j) d.emin = std::min(d.emin, std::hypot(h.e[2 * j], h.e[2 * j + 1]));
+    }
+    d.emin_f = (float)d.emin;
     void *pr = nullptr, *pe = nullptr, *pn = nullptr, *pw = nullptr, *prt = nullptr, *pct = nullptr;
     void *pxw = nullptr, *pfd = nullptr, *px = nullptr, *pj = nullptr, *pc = nullptr;
     int rc = put(h.n0, false, &pn);

@@ -79,6 +79,8 @@ struct MeshDev {
     const void* rowtab;            // [nr][ROWTAB] per-row geometry (element type of the path)
     const void* coltab;            // [nt][COLTAB] per-column geometry
     float xm_f, ym_f;
+    double emin;                   // separable O-grid: min over j of |e_j| (static-tile test)
+    float emin_f;
     const double* xw;              // [nt][2] wall node coordinates
     const double* fardir;          // [nt][2] outward direction at the far-field row
     // general meshes (node coordinates given): element type of the path

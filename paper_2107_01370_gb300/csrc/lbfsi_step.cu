@@ -596,6 +596,25 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     const R xm = pick<R>(MD(xm), MD(xm_f)), ym = pick<R>(MD(ym), MD(ym_f));
     const bool collide = mode != MODE_STREAM_ONLY;
     const bool stream = mode != MODE_COLLIDE_ONLY;
+    // static tile: no node of the tile's +-4 region lies in the blended
+    // region of the body (F = I, V_G = 0 there), from a lower bound of the
+    // distance to the blend centre on the separable O-grid (r of the first
+    // staged row x min |e_j| - |mesh centre - blend centre|) with a margin;
+    // such tiles skip the kinematics.  Tiles near the boundary take the
+    // general path, which gives the same result.
+    bool tile_static = false;
+    if constexpr (!GEN) {
+        if (!mapS.active) {
+            tile_static = true;
+        } else {
+            // in the element type of the path (no float64 on the float path),
+            // with a margin well above its rounding
+            const R rmin = srow[RT_R] * pick<R>(MD(emin), MD(emin_f));   // first staged row
+            const R ox = xm - mapS.xc, oy = ym - mapS.yc;
+            const R r_out = mapS.r_in + rcp_(mapS.inv_w);
+            tile_static = rmin - sqrt_(ox * ox + oy * oy) > r_out * (R(1) + R(1e-4)) + R(1e-5);
+        }
+    }
 
     // ---- phase 2: correction fields and collision of step k --------------
     if (collide) {
@@ -621,10 +640,20 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             } else {
                 const R* row = srow + (li + 1) * RS;
                 const R* col = scol + (lj + 1) * CS;
-                R ex, ey, u0, u1;
-                ld4(col + CT_E, ex, ey, u0, u1);
-                kinematics(mapK, xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
-                grad_map(row, col, F00, F01, F10, F11, G);
+                if (tile_static) {
+                    // F = I: the inverse metric of the mesh alone
+                    R c0, c1, c2, c3;
+                    ld4(col + CT_G, c0, c1, c2, c3);
+                    G[0] = row[RT_IDRC] * c0;
+                    G[1] = -row[RT_IR] * c1;
+                    G[2] = -row[RT_IDRC] * c2;
+                    G[3] = row[RT_IR] * c3;
+                } else {
+                    R ex, ey, u0, u1;
+                    ld4(col + CT_E, ex, ey, u0, u1);
+                    kinematics(mapK, xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
+                    grad_map(row, col, F00, F01, F10, F11, G);
+                }
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) sG[c * T::DS + idx] = G[c];
@@ -739,7 +768,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             moved = kinematics(mapS, sX[2 * dn], sX[2 * dn + 1], F00, F01, F10, F11, vx, vy);
         } else {
             node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
-            moved = kinematics(mapS, xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
+            if (tile_static) {
+                F00 = R(1); F01 = R(0); F10 = R(0); F11 = R(1); vx = R(0); vy = R(0);
+                moved = false;
+            } else {
+                moved = kinematics(mapS, xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
+            }
         }
         const R idF = rcp_(F00 * F11 - F01 * F10);
         const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
