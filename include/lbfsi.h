@@ -192,6 +192,16 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g,
 /* Wait for the handle's stream; returns the first device-detected error. */
 int lbfsi_synchronize(lbfsi_mesh m);
 
+/* Advance nsteps coupled steps (as lbfsi_step) and record every step's
+ * loads and, if states_out is not NULL, body states on the host:
+ * loads_out [nsteps][nbatch][3] (Fx, Fy, M as lbfsi_body_forces), states_out
+ * [nsteps][nbatch] (as lbfsi_get_body_state).  Each step's record is copied
+ * device -> host behind its launch (pinned staging owned by the handle), so
+ * the steps are not stalled by the reads; the call synchronises once at the
+ * end and returns the device status.  The load and displacement histories
+ * (C_D(t), C_L(t), h(t), alpha(t)) of Sec. IV come from this call. */
+int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_state* states_out);
+
 /* ---- Checkpoint / resume (no counterpart in the paper).  A checkpoint is
  * the whole state the next step reads, as raw device bytes: the
  * post-propagation populations and their moment field, every solve's maps

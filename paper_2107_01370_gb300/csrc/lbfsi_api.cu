@@ -67,6 +67,9 @@ struct lbfsi_mesh_s {
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // pinned staging of lbfsi_step_record
+    void* h_rec = nullptr;
+    size_t h_rec_bytes = 0;
 
     int cur() const { return (int)(host_k & 1u); }
     bool first() const { return host_k == 0u; }
@@ -135,6 +138,7 @@ void free_all(lbfsi_mesh m) {
         if (p) cudaFree(p);
     if (m->graph) cudaGraphExecDestroy(m->graph);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->h_rec) cudaFreeHost(m->h_rec);
     lbfsi::release_mesh(m->dmesh, m->mem);
 }
 
@@ -465,6 +469,56 @@ static int download_maps(lbfsi_mesh m, std::vector<StepMaps>& out) {
     cudaError_t e = cudaMemcpyAsync(out.data(), m->d_maps[m->cur()], out.size() * sizeof(StepMaps),
                                     cudaMemcpyDeviceToHost, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "maps copy");
+    return check_status(m);
+}
+
+int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_state* states_out) {
+    lbfsi::TraceRange trace_("lbfsi_step_record");
+    if (!m || !loads_out) return fail(LBFSI_EINVAL, "null argument");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
+    const size_t nb = (size_t)m->nbatch;
+    const size_t lb = nb * 3 * sizeof(double), sbytes = nb * sizeof(BodyStateDev);
+    const size_t need = (size_t)nsteps * (lb + (states_out ? sbytes : 0));
+    if (need > m->h_rec_bytes) {
+        cudaError_t e = cudaStreamSynchronize(m->stream);
+        if (m->h_rec) cudaFreeHost(m->h_rec);
+        m->h_rec = nullptr;
+        m->h_rec_bytes = 0;
+        if (e == cudaSuccess) e = cudaHostAlloc(&m->h_rec, need, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            m->h_rec = nullptr;
+            cudaGetLastError();
+            return fail(LBFSI_ENOMEM, "pinned staging for the step records");
+        }
+        m->h_rec_bytes = need;
+    }
+    char* hl = static_cast<char*>(m->h_rec);
+    char* hs = hl + (size_t)nsteps * lb;
+    lbfsi::StepArgs a = make_args(m, 0);
+    for (int s = 0; s < nsteps; ++s) {
+        a.ustep = (int)m->host_k;
+        cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
+        m->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        m->host_k++;
+        // the launch's epilogue wrote the step's loads and new body state into
+        // the maps record of the next launch: strided device -> pinned copies
+        const StepMaps* rec = m->d_maps[m->cur()];
+        e = cudaMemcpy2DAsync(hl + (size_t)s * lb, 3 * sizeof(double), &rec->loads[0], sizeof(StepMaps),
+                              3 * sizeof(double), nb, cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess && states_out)
+            e = cudaMemcpy2DAsync(hs + (size_t)s * sbytes, sizeof(BodyStateDev), &rec->S_next, sizeof(StepMaps),
+                                  sizeof(BodyStateDev), nb, cudaMemcpyDeviceToHost, m->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step record copy");
+    }
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step record sync");
+    std::memcpy(loads_out, hl, (size_t)nsteps * lb);
+    if (states_out) {
+        static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
+        std::memcpy(states_out, hs, (size_t)nsteps * sbytes);
+    }
     return check_status(m);
 }
 

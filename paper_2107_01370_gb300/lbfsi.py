@@ -31,7 +31,7 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_set_schedule", "lbfsi_get_schedule", "lbfsi_set_graph_steps", "lbfsi_autotune",
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
-            "lbfsi_create_mesh_xy"]
+            "lbfsi_create_mesh_xy", "lbfsi_step_record"]
 
 
 class LbfsiError(RuntimeError):
@@ -242,6 +242,17 @@ class Mesh:
 
     def step(self, n=1):
         _check(self._lib.lbfsi_step(self.h, int(n)))
+
+    def step_record(self, n, states=False):
+        """Advance n steps; per-step loads [n, nbatch, 3] (and body states
+        [n, nbatch, 4] as (h, alpha, hdot, adot) if states)."""
+        loads = np.empty((n, self.nbatch, 3))
+        st = (BodyState * (n * self.nbatch))() if states else None
+        _check(self._lib.lbfsi_step_record(self.h, int(n), _dptr(loads), st))
+        if not states:
+            return loads
+        arr = np.array([(s.h, s.alpha, s.hdot, s.adot) for s in st]).reshape(n, self.nbatch, 4)
+        return loads, arr
 
     def synchronize(self):
         _check(self._lib.lbfsi_synchronize(self.h))
