@@ -290,6 +290,26 @@ int lbfsi_batch_destroy(lbfsi_batch b);
  * solves).  The solve's first step happens in the next lbfsi_batch_step. */
 int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot);
 
+/* One solve on an O-grid given by its node coordinates (as in
+ * lbfsi_mesh_xy_desc: X [nr][ntheta][2] host, borrowed for the call), with
+ * its body, flow, initial field and step count as in lbfsi_solve_desc. */
+typedef struct {
+    int nr, ntheta;
+    const double* X;
+    double xc, yc;
+    lbfsi_body_desc body;
+    lbfsi_flow_params flow;
+    const double* rho_u_T;
+    int steps;
+} lbfsi_solve_xy_desc;
+
+/* Admit a solve on a general O-grid (same contract as lbfsi_batch_add).
+ * Identical coordinate sets share one device copy.  These solves run on the
+ * general-geometry kernel with its one tile shape, in a second launch of
+ * every lbfsi_batch_step; lbfsi_batch_set_schedule and the autotuner change
+ * the tiles of the separable-mesh solves only. */
+int lbfsi_batch_add_xy(lbfsi_batch b, const lbfsi_solve_xy_desc* d, int* slot);
+
 /* Advance every active solve by up to nsteps coupled steps (one launch per
  * step covering all active solves; a solve stops when it reaches its step
  * count).  *active_after (nullable) receives the number of unfinished solves.

@@ -101,6 +101,7 @@ struct MeshEntry {
 
 struct Slot {
     bool used = false, finished = false;
+    bool general = false;   // on a mesh given by node coordinates (GEN kernel, 8-row tiles)
     int mesh = -1;
     int steps_target = 0, steps_done = 0;
     int ntiles = 0;
@@ -125,7 +126,8 @@ struct lbfsi_batch_s {
     unsigned* d_status = nullptr;
     BodyStateDev* d_zero_state = nullptr;
     double* d_zero_loads = nullptr;
-    int ntiles = 0;
+    int ntiles = 0;    // separable-mesh tiles of the table (first part)
+    int ngtiles = 0;   // general-mesh tiles (second part)
     bool dirty = true;
     // CUDA graph of graph_steps launches over the current tile table,
     // captured on a private stream, dropped whenever the table changes
@@ -141,15 +143,23 @@ int cuda_err(cudaError_t e, const char* where) {
 }
 
 bool same_mesh(const lbfsi::HostMesh& h, const lbfsi_solve_desc& d) {
-    return h.nr == d.nr && h.nt == d.ntheta && h.xm == d.xc && h.ym == d.yc &&
+    return !h.general && h.nr == d.nr && h.nt == d.ntheta && h.xm == d.xc && h.ym == d.yc &&
            std::memcmp(h.r.data(), d.r, sizeof(double) * d.nr) == 0 &&
            std::memcmp(h.e.data(), d.e, sizeof(double) * 2 * d.ntheta) == 0;
 }
 
-// Find or create the device geometry of an O-grid; returns the mesh index.
-int acquire_mesh(lbfsi_batch b, const lbfsi_solve_desc& d, int* out) {
+bool same_mesh_xy(const lbfsi::HostMesh& h, const lbfsi_solve_xy_desc& d) {
+    return h.general && h.nr == d.nr && h.nt == d.ntheta && h.xm == d.xc && h.ym == d.yc &&
+           std::memcmp(h.X.data(), d.X, sizeof(double) * 2 * (size_t)d.nr * d.ntheta) == 0;
+}
+
+// Find or create the device geometry of a mesh (match: an existing entry's
+// host mesh equals the request; build: the host mesh of a new one); returns
+// the mesh index.
+template <typename Match, typename Build>
+int acquire_mesh(lbfsi_batch b, Match match, Build build_host, int* out) {
     for (size_t k = 0; k < b->meshes.size(); ++k)
-        if (b->meshes[k].used && same_mesh(b->meshes[k].host, d)) {
+        if (b->meshes[k].used && match(b->meshes[k].host)) {
             b->meshes[k].refs++;
             *out = (int)k;
             return LBFSI_OK;
@@ -167,7 +177,7 @@ int acquire_mesh(lbfsi_batch b, const lbfsi_solve_desc& d, int* out) {
     }
     MeshEntry& me = b->meshes[k];
     me = MeshEntry{};
-    int rc = lbfsi::build_host_mesh(d.nr, d.ntheta, d.r, d.e, d.xc, d.yc, me.host);
+    int rc = build_host(me.host);
     if (rc) return rc;
     rc = lbfsi::upload_mesh(me.host, b->precision, b->pool, b->stream, me.dev);
     if (rc) return rc;
@@ -211,40 +221,50 @@ void drop_graph(lbfsi_batch b) {
 int rebuild_tiles(lbfsi_batch b) {
     lbfsi::TraceRange trace_("lbfsi tile table");
     drop_graph(b);
+    // separable-mesh tiles first (tile rows of the batch's shape), then the
+    // general-mesh tiles (the GEN kernel's 8-row tile)
     std::vector<TileDev> tiles;
-    auto push = [&](size_t k, int ti, int tj) {
-        const Slot& s = b->slots[k];
-        TileDev t{};
-        t.solve = (int)k;
-        t.mesh = s.mesh;
-        t.i0 = ti * b->tile_rows;
-        t.j0 = tj * lbfsi::TILE_J;
-        t.tj = tj;
-        t.counter = s.dev.counter;
-        t.maps[0] = s.dev.maps[0];
-        t.maps[1] = s.dev.maps[1];
-        tiles.push_back(t);
-    };
-    auto active = [&](size_t k) { return b->slots[k].used && !b->slots[k].finished; };
-    auto nti_of = [&](size_t k) { return (b->meshes[b->slots[k].mesh].host.nr + b->tile_rows - 1) / b->tile_rows; };
-    if (b->order == 0) {
-        for (size_t k = 0; k < b->slots.size(); ++k) {
-            if (!active(k)) continue;
-            const int nti = nti_of(k), ntj = b->meshes[b->slots[k].mesh].host.ntj;
-            for (int ti = 0; ti < nti; ++ti)
-                for (int tj = 0; tj < ntj; ++tj) push(k, ti, tj);
-        }
-    } else {
-        int max_nti = 0;
-        for (size_t k = 0; k < b->slots.size(); ++k)
-            if (active(k)) max_nti = std::max(max_nti, nti_of(k));
-        for (int ti = 0; ti < max_nti; ++ti)
+    auto build = [&](bool general) {
+        const int rows = general ? lbfsi::GEN_TILE_ROWS : b->tile_rows;
+        auto push = [&](size_t k, int ti, int tj) {
+            const Slot& s = b->slots[k];
+            TileDev t{};
+            t.solve = (int)k;
+            t.mesh = s.mesh;
+            t.i0 = ti * rows;
+            t.j0 = tj * lbfsi::TILE_J;
+            t.tj = tj;
+            t.counter = s.dev.counter;
+            t.maps[0] = s.dev.maps[0];
+            t.maps[1] = s.dev.maps[1];
+            tiles.push_back(t);
+        };
+        auto active = [&](size_t k) {
+            return b->slots[k].used && !b->slots[k].finished && b->slots[k].general == general;
+        };
+        auto nti_of = [&](size_t k) { return (b->meshes[b->slots[k].mesh].host.nr + rows - 1) / rows; };
+        if (b->order == 0) {
             for (size_t k = 0; k < b->slots.size(); ++k) {
-                if (!active(k) || ti >= nti_of(k)) continue;
-                const int ntj = b->meshes[b->slots[k].mesh].host.ntj;
-                for (int tj = 0; tj < ntj; ++tj) push(k, ti, tj);
+                if (!active(k)) continue;
+                const int nti = nti_of(k), ntj = b->meshes[b->slots[k].mesh].host.ntj;
+                for (int ti = 0; ti < nti; ++ti)
+                    for (int tj = 0; tj < ntj; ++tj) push(k, ti, tj);
             }
-    }
+        } else {
+            int max_nti = 0;
+            for (size_t k = 0; k < b->slots.size(); ++k)
+                if (active(k)) max_nti = std::max(max_nti, nti_of(k));
+            for (int ti = 0; ti < max_nti; ++ti)
+                for (size_t k = 0; k < b->slots.size(); ++k) {
+                    if (!active(k) || ti >= nti_of(k)) continue;
+                    const int ntj = b->meshes[b->slots[k].mesh].host.ntj;
+                    for (int tj = 0; tj < ntj; ++tj) push(k, ti, tj);
+                }
+        }
+    };
+    build(false);
+    const size_t nsep = tiles.size();
+    build(true);
     cudaError_t e = cudaSuccess;
     if (tiles.size() > b->tiles_cap) {
         e = cudaStreamSynchronize(b->stream);
@@ -263,7 +283,8 @@ int rebuild_tiles(lbfsi_batch b) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return cuda_err(e, "tile table upload");
     }
-    b->ntiles = (int)tiles.size();
+    b->ntiles = (int)nsep;
+    b->ngtiles = (int)(tiles.size() - nsep);
     b->dirty = false;
     return LBFSI_OK;
 }
@@ -280,31 +301,40 @@ int check_status(lbfsi_batch b) {
     return LBFSI_OK;
 }
 
-lbfsi::StepArgs step_args(lbfsi_batch b) {
+lbfsi::StepArgs step_args(lbfsi_batch b, bool general) {
     lbfsi::StepArgs a{};
     a.meshes = b->d_meshes;
     a.solves = b->d_solves;
-    a.tiles = b->d_tiles;
-    a.ntiles = b->ntiles;
+    a.tiles = b->d_tiles + (general ? b->ntiles : 0);
+    a.ntiles = general ? b->ngtiles : b->ntiles;
     a.collide_only = 0;
     a.ustep = -1;
     a.status = b->d_status;
     return a;
 }
 
+// One step of every active solve: the separable-mesh table launch and the
+// general-mesh one (independent solves, so their order is free).
+cudaError_t launch_both(lbfsi_batch b, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (b->ntiles > 0) e = lbfsi::launch_step(step_args(b, false), b->precision, b->variant, s);
+    if (e == cudaSuccess && b->ngtiles > 0) e = lbfsi::launch_step_general_table(step_args(b, true), b->precision, s);
+    return e;
+}
+
 // Capture graph_steps launches over the current tile table (every launch
 // reads the step numbers from the device counters, so the graph is valid for
 // every replay until the table changes).
-int capture_graph(lbfsi_batch b, const lbfsi::StepArgs& a) {
+int capture_graph(lbfsi_batch b) {
     lbfsi::TraceRange trace_("lbfsi batch graph capture");
     cudaError_t e = lbfsi::prepare_step(b->precision, b->variant, false);
+    if (e == cudaSuccess && b->ngtiles > 0) e = lbfsi::prepare_step(b->precision, 0, false, true);
     if (e == cudaSuccess && !b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_err(e, "graph capture setup");
     e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(e, "begin capture");
     cudaError_t le = cudaSuccess;
-    for (int g = 0; g < b->graph_steps && le == cudaSuccess; ++g)
-        le = lbfsi::launch_step(a, b->precision, b->variant, b->cap_stream);
+    for (int g = 0; g < b->graph_steps && le == cudaSuccess; ++g) le = launch_both(b, b->cap_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->cap_stream, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -370,16 +400,22 @@ int lbfsi_batch_destroy(lbfsi_batch b) {
     return LBFSI_OK;
 }
 
-int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
-    lbfsi::TraceRange trace_("lbfsi_batch_add");
-    if (!b || !d || !slot) return lbfsi::set_error(LBFSI_EINVAL, "null argument");
+}  // extern "C"
+
+namespace {
+
+// Admission of one solve whose mesh is given by 'acquire' (which finds or
+// creates its device geometry): pool memory, initial state, slot.
+template <typename Acquire>
+int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_params& flow,
+              const double* rho_u_T, int steps, int nr, int nt, Acquire acquire, int* slot) {
+    if (!slot) return lbfsi::set_error(LBFSI_EINVAL, "null argument");
     *slot = -1;
-    if (d->steps <= 0) return lbfsi::set_error(LBFSI_EINVAL, "steps must be > 0");
-    const long long Nll = (long long)d->nr * d->ntheta;
-    if (d->nr < 5 || d->ntheta < 4 || Nll * 9 > (1ll << 31))
-        return lbfsi::set_error(LBFSI_EINVAL, "invalid mesh size");
+    if (steps <= 0) return lbfsi::set_error(LBFSI_EINVAL, "steps must be > 0");
+    const long long Nll = (long long)nr * nt;
+    if (nr < 5 || nt < 4 || Nll * 9 > (1ll << 31)) return lbfsi::set_error(LBFSI_EINVAL, "invalid mesh size");
     SolveDev sd{};
-    int rc = lbfsi::fill_flow(d->flow, sd);
+    int rc = lbfsi::fill_flow(flow, sd);
     if (rc) return rc;
     // a free slot
     int k = -1;
@@ -394,10 +430,10 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
         k = (int)b->slots.size() - 1;
     }
     int mk = -1;
-    rc = acquire_mesh(b, *d, &mk);
+    rc = acquire(&mk);
     if (rc) return rc;
     const lbfsi::HostMesh& h = b->meshes[mk].host;
-    rc = lbfsi::validate_bodies(h, &d->body, 1);
+    rc = lbfsi::validate_bodies(h, &body_desc, 1);
     if (rc) {
         drop_mesh(b, mk);
         return rc;
@@ -428,12 +464,13 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     }
     sd.body = body;
     sd.mesh = mk;
-    sd.ntiles = ((h.nr + b->tile_rows - 1) / b->tile_rows) * h.ntj;
+    const int rows = h.general ? lbfsi::GEN_TILE_ROWS : b->tile_rows;
+    sd.ntiles = ((h.nr + rows - 1) / rows) * h.ntj;
     sd.ppost = nullptr;
     // initial state: equilibria of the initial field, bodies at rest
     std::vector<double> M(4 * N);
-    if (d->rho_u_T) {
-        std::memcpy(M.data(), d->rho_u_T, M.size() * sizeof(double));
+    if (rho_u_T) {
+        std::memcpy(M.data(), rho_u_T, M.size() * sizeof(double));
     } else {
         for (size_t n = 0; n < N; ++n) {
             M[n] = sd.rho_inf;
@@ -442,7 +479,7 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
             M[3 * N + n] = sd.T_inf;
         }
     }
-    const BodyDev bd = lbfsi::body_dev(d->body, sd.rho_inf, sd.uinf_x);
+    const BodyDev bd = lbfsi::body_dev(body_desc, sd.rho_inf, sd.uinf_x);
     cudaError_t e = cudaMemcpyAsync(stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(body, &bd, sizeof(BodyDev), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sd.counter, 0, 2 * sizeof(unsigned), b->stream);
@@ -463,8 +500,9 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     }
     s.used = true;
     s.finished = false;
+    s.general = h.general;
     s.mesh = mk;
-    s.steps_target = d->steps;
+    s.steps_target = steps;
     s.steps_done = 0;
     s.ntiles = sd.ntiles;
     s.dev = sd;
@@ -472,6 +510,34 @@ int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
     b->dirty = true;
     *slot = k;
     return LBFSI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbfsi_batch_add(lbfsi_batch b, const lbfsi_solve_desc* d, int* slot) {
+    lbfsi::TraceRange trace_("lbfsi_batch_add");
+    if (!b || !d || !slot) return lbfsi::set_error(LBFSI_EINVAL, "null argument");
+    auto acquire = [&](int* mk) {
+        return acquire_mesh(
+            b, [&](const lbfsi::HostMesh& h) { return same_mesh(h, *d); },
+            [&](lbfsi::HostMesh& h) { return lbfsi::build_host_mesh(d->nr, d->ntheta, d->r, d->e, d->xc, d->yc, h); },
+            mk);
+    };
+    return add_solve(b, d->body, d->flow, d->rho_u_T, d->steps, d->nr, d->ntheta, acquire, slot);
+}
+
+int lbfsi_batch_add_xy(lbfsi_batch b, const lbfsi_solve_xy_desc* d, int* slot) {
+    lbfsi::TraceRange trace_("lbfsi_batch_add_xy");
+    if (!b || !d || !slot) return lbfsi::set_error(LBFSI_EINVAL, "null argument");
+    auto acquire = [&](int* mk) {
+        return acquire_mesh(
+            b, [&](const lbfsi::HostMesh& h) { return same_mesh_xy(h, *d); },
+            [&](lbfsi::HostMesh& h) { return lbfsi::build_host_mesh_xy(d->nr, d->ntheta, d->X, d->xc, d->yc, h); },
+            mk);
+    };
+    return add_solve(b, d->body, d->flow, d->rho_u_T, d->steps, d->nr, d->ntheta, acquire, slot);
 }
 
 int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
@@ -484,16 +550,15 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
             const int rc = rebuild_tiles(b);
             if (rc) return rc;
         }
-        if (b->ntiles == 0) break;
+        if (b->ntiles + b->ngtiles == 0) break;
         // steps until the next solve finishes: the tile table is fixed over them
         int run = nsteps - st;
         for (auto& s : b->slots)
             if (s.used && !s.finished) run = std::min(run, s.steps_target - s.steps_done);
-        lbfsi::StepArgs a = step_args(b);
         int done = 0;
         if (b->graph_steps > 0 && run >= b->graph_steps) {
             if (!b->graph) {
-                const int rc = capture_graph(b, a);
+                const int rc = capture_graph(b);
                 if (rc) return rc;
             }
             for (; run - done >= b->graph_steps; done += b->graph_steps) {
@@ -502,7 +567,7 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
             }
         }
         for (; done < run; ++done) {
-            const cudaError_t e = lbfsi::launch_step(a, b->precision, b->variant, b->stream);
+            const cudaError_t e = launch_both(b, b->stream);
             if (e != cudaSuccess) return cuda_err(e, "batch step launch");
         }
         st += run;
@@ -535,7 +600,7 @@ int lbfsi_batch_set_schedule(lbfsi_batch b, int variant, int order) {
     // the per-solve CTA count of the completion counter follows the tile shape
     for (size_t k = 0; k < b->slots.size(); ++k) {
         Slot& s = b->slots[k];
-        if (!s.used) continue;
+        if (!s.used || s.general) continue;   // general meshes keep their one tile shape
         const lbfsi::HostMesh& h = b->meshes[s.mesh].host;
         s.dev.ntiles = ((h.nr + b->tile_rows - 1) / b->tile_rows) * h.ntj;
         s.ntiles = s.dev.ntiles;

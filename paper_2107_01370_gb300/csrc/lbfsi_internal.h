@@ -149,6 +149,11 @@ cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStrea
 cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,
                                 cudaStream_t s);
 int tile_rows(int precision, int variant);
+// Tile rows of the general-geometry kernel (one shape).
+constexpr int GEN_TILE_ROWS = 8;
+// Table launch of the general-geometry kernel (the batch runtime's solves on
+// meshes given by node coordinates).
+cudaError_t launch_step_general_table(const StepArgs& a, int precision, cudaStream_t s);
 // Number of tile shapes of the float step kernel (variants 0 .. n-1); the
 // float64 kernel has one.
 int step_variants(int precision);

@@ -1125,8 +1125,9 @@ static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) 
     return StepKernel<R, TI, NT, MINB, UNIFORM>::launch(a, nbatch, s);
 }
 
-// General meshes (node coordinates given): uniform launches, one tile shape.
+// General meshes (node coordinates given): one tile shape (GEN_TILE_ROWS rows).
 static cudaError_t launch_general(const StepArgs& a, int precision, int nbatch, cudaStream_t s) {
+    static_assert(GEN_TILE_ROWS == 8, "tile shape of the general kernel");
     if (precision == 0) return StepKernel<double, 8, 256, 1, true, true>::launch(a, nbatch, s);
     return StepKernel<float, 8, 256, 2, true, true>::launch(a, nbatch, s);
 }
@@ -1143,7 +1144,15 @@ static cudaError_t configure_any(int precision, int variant) {
     }
 }
 
+cudaError_t launch_step_general_table(const StepArgs& a, int precision, cudaStream_t s) {
+    if (precision == 0) return StepKernel<double, 8, 256, 1, false, true>::launch(a, 0, s);
+    return StepKernel<float, 8, 256, 2, false, true>::launch(a, 0, s);
+}
+
 cudaError_t prepare_step(int precision, int variant, bool uniform, bool general) {
+    if (general && !uniform)
+        return precision == 0 ? StepKernel<double, 8, 256, 1, false, true>::configure()
+                              : StepKernel<float, 8, 256, 2, false, true>::configure();
     if (general)
         return precision == 0 ? StepKernel<double, 8, 256, 1, true, true>::configure()
                               : StepKernel<float, 8, 256, 2, true, true>::configure();

@@ -31,7 +31,7 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_set_schedule", "lbfsi_get_schedule", "lbfsi_set_graph_steps", "lbfsi_autotune",
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
-            "lbfsi_create_mesh_xy", "lbfsi_step_record"]
+            "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy"]
 
 
 class LbfsiError(RuntimeError):
@@ -67,6 +67,14 @@ class MeshXYDesc(ctypes.Structure):
                 ("X", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class SolveXYDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("X", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("body", BodyDesc),
+                ("flow", FlowParams), ("rho_u_T", ctypes.POINTER(ctypes.c_double)),
+                ("steps", ctypes.c_int)]
 
 
 class SolveDesc(ctypes.Structure):
@@ -362,6 +370,21 @@ class Batch:
             return None
         _check(rc)
         self._shapes[slot.value] = (r.size, e.shape[0])
+        return slot.value
+
+    def add_xy(self, X, body, flow, steps, rho_u_T=None, centre=(0.0, 0.0)):
+        """Admit a solve on an O-grid given by node coordinates X [nr, ntheta, 2];
+        returns its slot, or None if the pool has no room now."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        m = None if rho_u_T is None else np.ascontiguousarray(rho_u_T, dtype=np.float64)
+        d = SolveXYDesc(X.shape[0], X.shape[1], _dptr(X), centre[0], centre[1], body_desc(body),
+                        flow_params(flow), None if m is None else _dptr(m), int(steps))
+        slot = ctypes.c_int(-1)
+        rc = self._lib.lbfsi_batch_add_xy(self.h, ctypes.byref(d), ctypes.byref(slot))
+        if rc == ENOMEM:
+            return None
+        _check(rc)
+        self._shapes[slot.value] = (X.shape[0], X.shape[1])
         return slot.value
 
     def step(self, n=1):

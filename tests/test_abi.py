@@ -82,13 +82,15 @@ def test_xy_mesh_struct_layout_matches_c(tmp_path):
     from paper_2107_01370_gb300 import lbfsi
     src = tmp_path / "xy.c"
     src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu\\n", sizeof(lbfsi_mesh_xy_desc),'
-                   'offsetof(lbfsi_mesh_xy_desc, X), offsetof(lbfsi_mesh_xy_desc, bodies));return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lbfsi_mesh_xy_desc),'
+                   'offsetof(lbfsi_mesh_xy_desc, X), offsetof(lbfsi_mesh_xy_desc, bodies),'
+                   'sizeof(lbfsi_solve_xy_desc), offsetof(lbfsi_solve_xy_desc, steps));return 0;}\n')
     exe = tmp_path / "xy"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [ctypes.sizeof(lbfsi.MeshXYDesc), lbfsi.MeshXYDesc.X.offset,
-                   lbfsi.MeshXYDesc.bodies.offset]
+                   lbfsi.MeshXYDesc.bodies.offset, ctypes.sizeof(lbfsi.SolveXYDesc),
+                   lbfsi.SolveXYDesc.steps.offset]
 
 
 def test_general_mesh_validation_without_gpu(lib):

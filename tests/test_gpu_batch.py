@@ -117,3 +117,47 @@ def test_admission_by_device_memory(L):
     batch.remove(c)
     assert batch.memory()[0] == free_start
     batch.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_general_and_separable_meshes_in_one_batch(L, precision):
+    """Solves on O-grids given by node coordinates (an elliptic cylinder)
+    share the batch with separable O-grids: two launches per step, one per
+    geometry kind.  Every solve, admitted at a different time, ends bit for
+    bit like the same solve alone, also across a schedule change and with
+    graph replay."""
+    prec = L.FP32 if precision == "fp32" else L.FP64
+    ell_body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=3.0, v_r=4.0, length=1.2)
+    ell = inputs.xy_case(inputs.ellipse_wall(64, 0.6, 0.35), 40, r_far=8.0, length=1.2, body=ell_body)
+    M_ell = inputs.initial_field(ell.nr, ell.ntheta, ell.flow, seed=31)
+    sep = [_case(32, 32, 3.0, 2.0, 1), _case(48, 64, 5.0, 10.0, 2)]
+    steps = {"e": 30, "s0": 25, "s1": 34}
+    batch = L.Batch(256 << 20, precision=prec)
+    batch.set_graph_steps(4)
+    slots = {"s0": batch.add(sep[0][0].r, sep[0][0].e, sep[0][0].bodies[0], sep[0][0].flow, steps["s0"], sep[0][1])}
+    batch.step(3)
+    slots["e"] = batch.add_xy(ell.X, ell_body, ell.flow, steps["e"], M_ell, centre=ell.centre)
+    batch.step(5)
+    if prec == L.FP32:
+        batch.set_schedule(0, 1)
+    slots["s1"] = batch.add(sep[1][0].r, sep[1][0].e, sep[1][0].bodies[0], sep[1][0].flow, steps["s1"], sep[1][1])
+    while batch.step(7) > 0:
+        pass
+    got = {k: batch.get(v) for k, v in slots.items()}
+    batch.close()
+    # alone
+    m = L.Mesh.xy(ell.X, [ell_body], precision=prec, centre=ell.centre)
+    m.init_fields(ell.flow, M_ell[None])
+    m.step(steps["e"])
+    alone = {"e": (m.get_fields()[0], m.body_forces()[0], m.body_state()[0])}
+    m.close()
+    for k, (case, M0) in (("s0", sep[0]), ("s1", sep[1])):
+        m = L.Mesh(case.r, case.e, case.bodies, precision=prec)
+        m.init_fields(case.flow, M0[None])
+        m.step(steps[k])
+        alone[k] = (m.get_fields()[0], m.body_forces()[0], m.body_state()[0])
+        m.close()
+    for k in slots:
+        assert np.array_equal(got[k][0], alone[k][0]), k
+        assert np.array_equal(got[k][1], alone[k][1]), k
+        assert got[k][2] == alone[k][2], k
