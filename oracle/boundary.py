@@ -97,3 +97,68 @@ def far_field_targets(mesh, M_prev, u_inf, rho_inf, T_inf):
     uy = np.where(inlet, u_inf[1], M_prev[2, last - 1])
     T = np.where(inlet, T_inf, M_prev[3, last - 1])
     return rho, ux, uy, T, inlet
+
+
+# ----- C-grid (reading R29): open wall chain, outlet columns ---------------
+def wall_normals_cgrid(mesh):
+    """Unit normals of the wall nodes of a C-grid (columns jc .. Nj-1-jc of
+    row 0, counterclockwise, out of the body), zero on the cut.  The wall is
+    the open chain of straight edges between its even-offset nodes; its two
+    ends are the same point (the rear point), whose normal is the normalised
+    sum of the first and last edges' normals, as at every even node."""
+    Nj, jc = mesh.Nj, mesh.jc
+    P = mesh.X[0]
+    ne = (Nj - 1 - 2 * jc) // 2
+    n_edge = np.empty((ne, 2))
+    for k in range(ne):
+        t = P[jc + 2 * k + 2] - P[jc + 2 * k]
+        n_edge[k] = np.array([t[1], -t[0]]) / np.hypot(t[0], t[1])
+    n = np.zeros((Nj, 2))
+    for m in range(Nj - 2 * jc):
+        j = jc + m
+        if m % 2:
+            n[j] = n_edge[m // 2]
+        else:
+            k1 = m // 2 - 1 if m > 0 else ne - 1
+            k2 = m // 2 if m // 2 < ne else 0
+            v = n_edge[k1] + n_edge[k2]
+            n[j] = v / np.hypot(v[0], v[1])
+    return n
+
+
+def far_field_mask_cgrid(mesh):
+    """Far-field nodes of a C-grid: the last row and the outlet columns."""
+    far = np.zeros((mesh.Ni, mesh.Nj), dtype=bool)
+    far[mesh.Ni - 1, :] = True
+    far[:, 0] = True
+    far[:, mesh.Nj - 1] = True
+    return far
+
+
+def far_field_targets_cgrid(mesh, M_prev, u_inf, rho_inf, T_inf):
+    """Inlet / outlet targets on the far field of a C-grid (reading R20 on
+    each boundary): on the last row the outward direction and the inner
+    neighbour are along i, on the outlet columns (rows below the last) along
+    j.  Returns rho, ux, uy, T on the whole [Ni, Nj] grid (meaningful on the
+    far-field mask only) and the inlet mask."""
+    Ni, Nj = mesh.Ni, mesh.Nj
+    X = mesh.X
+    n_out = np.zeros((Ni, Nj, 2))
+    inner = np.zeros((Ni, Nj, 2), dtype=np.int64)
+    ii, jj = np.meshgrid(np.arange(Ni), np.arange(Nj), indexing="ij")
+    inner[..., 0] = ii
+    inner[..., 1] = jj
+    n_out[:, 0] = X[:, 0] - X[:, 1]
+    inner[:, 0, 1] = 1
+    n_out[:, Nj - 1] = X[:, Nj - 1] - X[:, Nj - 2]
+    inner[:, Nj - 1, 1] = Nj - 2
+    n_out[Ni - 1] = X[Ni - 1] - X[Ni - 2]
+    inner[Ni - 1, :, 0] = Ni - 2
+    inner[Ni - 1, :, 1] = np.arange(Nj)
+    inlet = (u_inf[0] * n_out[..., 0] + u_inf[1] * n_out[..., 1]) < 0.0
+    a, b = inner[..., 0], inner[..., 1]
+    rho = np.where(inlet, rho_inf, M_prev[0][a, b])
+    ux = np.where(inlet, u_inf[0], M_prev[1][a, b])
+    uy = np.where(inlet, u_inf[1], M_prev[2][a, b])
+    T = np.where(inlet, T_inf, M_prev[3][a, b])
+    return rho, ux, uy, T, inlet

@@ -29,16 +29,18 @@ def node_stress(f, g, Cv, mu, dt, Pr):
     return -p - a * pxx, -a * pxy, -p - a * pyy
 
 
-def wall_force(x_wall, sxx, sxy, syy, x_ref):
+def wall_force(x_wall, sxx, sxy, syy, x_ref, closed=True):
     """F = sum_j sigma . n ds over the wall edges j, and the moment
     M = sum_j (x - x_ref) x (sigma . n) ds, with Simpson weights (1, 4, 1)/6
     over the three nodes of each edge.  x_wall[Nj, 2] are the deformed wall
     node positions, ordered counter-clockwise (body on the left of increasing
-    j reversed, i.e. n = (t_y, -t_x)/|t| points out of the body)."""
+    j reversed, i.e. n = (t_y, -t_x)/|t| points out of the body).
+    closed=False: an open chain of Nj (odd) nodes whose two ends are the same
+    point (the wall of a C-grid), (Nj-1)/2 edges."""
     Nj = x_wall.shape[0]
     Fx = Fy = Mz = 0.0
     for k in range(Nj // 2):
-        ids = (2 * k, 2 * k + 1, (2 * k + 2) % Nj)
+        ids = (2 * k, 2 * k + 1, (2 * k + 2) % Nj if closed else 2 * k + 2)
         t = x_wall[ids[2]] - x_wall[ids[0]]
         ds = float(np.hypot(t[0], t[1]))
         n = np.array([t[1], -t[0]]) / ds

@@ -256,3 +256,115 @@ def periodic_box_mesh(ni, nj, lx, ly, skew=0.0):
     X[..., 1] = j * hy + 0.0 * i
     return Q2Mesh(X, periodic_i=True, periodic_j=True, shift_i=(lx, 0.0),
                   shift_j=(skew * ly, ly))
+
+
+class CGridMesh(Q2Mesh):
+    """C-grid around one body with a wake cut (the airfoil topology of
+    Sec. IV D; readings R28-R30).  Row 0 runs counterclockwise: the upper side
+    of the cut from the outlet towards the body (j < jc), the wall from its
+    rear point over the upper surface and the front back to the rear point
+    (jc <= j <= Nj-1-jc), then the lower side of the cut out to the outlet.
+    Rows grow away from row 0; columns 0 and Nj-1 are outlet boundaries (not
+    periodic).  Across the cut, row-0 nodes j and Nj-1-j are one point (for
+    j <= jc, the rear point of the wall included), and the mesh continues
+    below row 0 as its mirror: node (-k, c) is node (k, Nj-1-c).  A cell
+    below row 0 is the mirror of a cell of the other side of the cut, and so
+    is its element: all nine nodes of a window that starts below row 0, its
+    row 0 included, are the mirrored ones."""
+
+    def __init__(self, X, n_cut):
+        super().__init__(X, periodic_i=False, periodic_j=False)
+        Nj = self.Nj
+        if Nj % 2 == 0:
+            raise ValueError("a C-grid needs an odd node count along the C")
+        if n_cut < 2 or n_cut % 2 or 2 * n_cut >= Nj - 1:
+            raise ValueError("n_cut must be even, >= 2 and leave a wall of at least 3 nodes")
+        self.jc = int(n_cut)
+        scale = float(np.max(np.abs(self.X)))
+        for j in range(self.jc + 1):
+            if np.max(np.abs(self.X[0, j] - self.X[0, Nj - 1 - j])) > 1e-12 * scale:
+                raise ValueError("row-0 nodes j and Nj-1-j must coincide along the cut")
+
+    # ----- node sets ------------------------------------------------------
+    def cut_columns(self):
+        j = np.arange(self.Nj)
+        return (j < self.jc) | (j > self.Nj - 1 - self.jc)
+
+    def wall_columns(self):
+        return ~self.cut_columns()
+
+    def duplicate_columns(self):
+        """Row-0 columns whose node is a second copy of node (0, Nj-1-j): the
+        lower side of the cut and the rear point's second copy."""
+        return np.arange(self.Nj) >= self.Nj - 1 - self.jc
+
+    # ----- window nodes through the cut ------------------------------------
+    def window_node(self, wa, wb, a, b):
+        """Physical node of entry (a, b) of the window that starts at (wa, wb)."""
+        i = np.asarray(wa) + a
+        j = np.asarray(wb) + b
+        ghost = np.asarray(wa) < 0
+        return np.where(ghost, -i, i), np.where(ghost, self.Nj - 1 - j, j)
+
+    def valid_cell(self, a, b):
+        return (a >= -1) & (a <= self.Ni - 2) & (b >= 0) & (b <= self.Nj - 2)
+
+    def locate_in_cell(self, a, b, P):
+        wa, wb = self.window_of_cell(a, b)
+        corner = {}
+        for ca, cb in ((0, 0), (2, 0), (0, 2), (2, 2)):
+            ii, jj = self.window_node(wa, wb, ca, cb)
+            corner[ca, cb] = self.X[ii, jj]
+        xi, eta = self.bilinear_inverse(corner[0, 0], corner[2, 0], corner[0, 2], corner[2, 2], P)
+        la = a - wa
+        lb = b - wb
+        inside = ((xi >= la - 1 - XI_TOL) & (xi <= la + XI_TOL)
+                  & (eta >= lb - 1 - XI_TOL) & (eta <= lb + XI_TOL))
+        inside &= np.isfinite(xi) & np.isfinite(eta)
+        return wa, wb, xi, eta, inside
+
+    def interpolate(self, field, wa, wb, xi, eta):
+        N = self.q2_weights(xi, eta)
+        out = 0.0
+        for a in range(3):
+            for b in range(3):
+                ii, jj = self.window_node(wa, wb, a, b)
+                out = out + N[a][b] * field[..., ii, jj]
+        return out
+
+    # ----- gradients: central across the cut --------------------------------
+    def _d_rows(self, F):
+        """Derivative along i (reading R18) with the cut: at the row-0 cut
+        nodes and at the two copies of the rear point, the central difference
+        with the mirrored row below, (F(1, j) - F(1, Nj-1-j)) / 2; one-sided
+        on the rest of the wall (reading R30)."""
+        d = self._d_index(F, F.ndim - 2, False, None)
+        jc, Nj = self.jc, self.Nj
+        c = np.nonzero(self.cut_columns() | np.isin(np.arange(Nj), (jc, Nj - 1 - jc)))[0]
+        d[..., 0, c] = 0.5 * (F[..., 1, c] - F[..., 1, Nj - 1 - c])
+        return d
+
+    def _d_cols(self, F):
+        """Derivative along j: central, one-sided on the outlet columns; at
+        the rear point (reading R30) one-sided along the cut, the nodes both
+        copies share: backward at j = jc, forward at j = Nj-1-jc."""
+        d = self._d_index(F, F.ndim - 1, False, None)
+        jc, Nj = self.jc, self.Nj
+        d[..., 0, jc] = 0.5 * (3.0 * F[..., 0, jc] - 4.0 * F[..., 0, jc - 1] + F[..., 0, jc - 2])
+        k = Nj - 1 - jc
+        d[..., 0, k] = 0.5 * (-3.0 * F[..., 0, k] + 4.0 * F[..., 0, k + 1] - F[..., 0, k + 2])
+        return d
+
+    def metrics(self):
+        Xx = self.X[..., 0]
+        Xy = self.X[..., 1]
+        return self._d_rows(Xx), self._d_rows(Xy), self._d_cols(Xx), self._d_cols(Xy)
+
+    def grad_X(self, F):
+        x_xi, y_xi, x_eta, y_eta = self.metrics()
+        F_xi = self._d_rows(F)
+        F_eta = self._d_cols(F)
+        det = x_xi * y_eta - y_xi * x_eta
+        dX = (y_eta * F_xi - y_xi * F_eta) / det
+        dY = (-x_eta * F_xi + x_xi * F_eta) / det
+        return dX, dY

@@ -32,7 +32,7 @@ import numpy as np
 
 from . import kinetics as K
 from . import ale, boundary, forces, structure
-from .mesh import DepartureError
+from .mesh import CGridMesh, DepartureError
 
 
 def body_dict(spec, flow_rho, u_inf):
@@ -76,8 +76,10 @@ class StepResult:
 
 class Solver:
     """Coupled solver on one mesh.  walls=True: O-grid with the body wall on
-    row 0 and the far field on the last row; walls=False: no boundary rows
-    (doubly periodic box)."""
+    row 0 and the far field on the last row, or a C-grid (CGridMesh: the wall
+    on part of row 0, the wake cut on the rest, the far field on the last row
+    and the outlet columns); walls=False: no boundary rows (doubly periodic
+    box)."""
 
     def __init__(self, mesh, *, gamma, Pr, mu, dt, rho_inf, u_inf, T_inf, bodies, M0,
                  walls=True):
@@ -99,8 +101,9 @@ class Solver:
         self.S = [zero_state() for _ in self.bodies]
         self.S_prev = [dict(s) for s in self.S]
         self.n = 0
+        self.cgrid = isinstance(mesh, CGridMesh)
         if walls:
-            self.n0 = boundary.wall_normals(mesh)
+            self.n0 = boundary.wall_normals_cgrid(mesh) if self.cgrid else boundary.wall_normals(mesh)
 
     @classmethod
     def from_case(cls, mesh, case, M0):
@@ -118,6 +121,8 @@ class Solver:
         return ale.physical_gradient(F, dX, dY)
 
     def step(self) -> StepResult:
+        if self.cgrid:
+            return self._step_cgrid()
         mesh, dt, Cv = self.mesh, self.dt, self.Cv
         X = mesh.X
         Ni, Nj = mesh.Ni, mesh.Nj
@@ -204,6 +209,119 @@ class Solver:
                     st["h"], st["alpha"], st["hdot"], st["adot"], force[1], force[2],
                     b["m"], b["s_a"], b["i_a"], b["k_h"], b["k_a"], dt)
             new_S.append(s)
+        self.S_prev = [dict(s) for s in self.S]
+        self.S = new_S
+        self.f, self.g = f_post, g_post
+        self.M_prev = M
+        self.n += 1
+        return StepResult(f_pre, g_pre, f_post, g_post, M, force, missing)
+
+    def _advance_bodies(self, force):
+        """Step 8 (RK4 of every body with the load held, Sec. III B)."""
+        dt = self.dt
+        new_S = []
+        for b, st in zip(self.bodies, self.S):
+            s = dict(st)
+            if b["dof"] == 1:
+                s["h"], s["hdot"] = structure.advance_one_dof(
+                    st["h"], st["hdot"], force[1], b["m"], b["k"], b["c"], dt)
+            elif b["dof"] == 2 and (self.n + 1) * dt <= b["t_forced"]:
+                s["h"], s["alpha"], s["hdot"], s["adot"] = structure.advance_plunge_forced_pitch(
+                    st["h"], st["hdot"], force[1], b["m"], b["s_a"], b["k_h"], b["pitch_amp"],
+                    b["w_a"], self.n, dt)
+            elif b["dof"] == 2:
+                s["h"], s["alpha"], s["hdot"], s["adot"] = structure.advance_two_dof(
+                    st["h"], st["alpha"], st["hdot"], st["adot"], force[1], force[2],
+                    b["m"], b["s_a"], b["i_a"], b["k_h"], b["k_a"], dt)
+            new_S.append(s)
+        return new_S
+
+    def _step_cgrid(self) -> StepResult:
+        """One step on a C-grid: the O-grid step with the C-grid's node sets
+        (readings R28-R30).  Every node but the far field is streamed, the
+        row-0 cut nodes like interior nodes (their departure points may lie
+        across the cut); the wall columns of row 0 take the wall treatment;
+        the far field is the last row and the outlet columns.  The second
+        copies of the row-0 nodes along the cut take the values of the first
+        copies (j <= jc) after the propagation and after the collision."""
+        mesh, dt, Cv = self.mesh, self.dt, self.Cv
+        X = mesh.X
+        Ni, Nj, jc = mesh.Ni, mesh.Nj, mesh.jc
+        far = boundary.far_field_mask_cgrid(mesh)
+        wall = np.zeros((Ni, Nj), dtype=bool)
+        wall[0] = mesh.wall_columns()
+        dup = np.nonzero(mesh.duplicate_columns())[0]
+        own = Nj - 1 - dup
+        wcols = np.nonzero(mesh.wall_columns())[0]
+        # 1. kinematics
+        F = ale.deformation_gradient(X, self.bodies, self.S)
+        VG = ale.mesh_velocity(X, self.bodies, self.S, self.S_prev, dt)
+        chat = ale.transformed_velocities(F, VG)
+        # 2. departure points and interpolation at every node off the far field
+        ii, jj = np.meshgrid(np.arange(Ni), np.arange(Nj), indexing="ij")
+        f_pre = np.zeros((9, Ni, Nj))
+        g_pre = np.zeros((9, Ni, Nj))
+        missing = np.zeros((9, Ni, Nj), dtype=bool)
+        missing[:, 0, :] = boundary.missing_mask(chat[:, 0], self.n0) & wall[0][None, :]
+        for k in range(9):
+            P = X - dt * chat[k]
+            wa, wb, xi, eta, found = mesh.locate(P, ii, jj)
+            need = ~far & ~missing[k]
+            if np.any(need & ~found):
+                bad = np.argwhere(need & ~found)[0]
+                raise DepartureError(f"departure point of direction {k} at node "
+                                     f"{tuple(bad)} is not in an adjacent cell")
+            wa = np.where(need, wa, 0)
+            wb = np.where(need, wb, 0)
+            f_pre[k] = np.where(need, mesh.interpolate(self.f[k], wa, wb, xi, eta), 0.0)
+            g_pre[k] = np.where(need, mesh.interpolate(self.g[k], wa, wb, xi, eta), 0.0)
+        # 3. wall nodes: Grad's approximation at the targets
+        rho_b, T_b, grads = boundary.wall_targets(mesh, self.M_prev, self.n0, dt, F[0])
+        uw = VG[0]
+        fm, gm = boundary.grad_populations(rho_b, uw[:, 0], uw[:, 1], T_b, grads, Cv,
+                                           self.mu, dt, self.Pr)
+        f_pre[:, 0] = np.where(missing[:, 0], fm, f_pre[:, 0])
+        g_pre[:, 0] = np.where(missing[:, 0], gm, g_pre[:, 0])
+        # 4. moments; far-field targets (the far-field entries of f_pre are
+        # zero: their moments are replaced by the targets)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rho, ux, uy, E, T = K.moments(f_pre, g_pre, Cv)
+        M = np.stack([rho, ux, uy, T])
+        tr, tux, tuy, tT, _ = boundary.far_field_targets_cgrid(mesh, self.M_prev, self.u_inf,
+                                                               self.rho_inf, self.T_inf)
+        for c, t in enumerate((tr, tux, tuy, tT)):
+            M[c] = np.where(far, t, M[c])
+        f_pre[:, 0, dup] = f_pre[:, 0, own]
+        g_pre[:, 0, dup] = g_pre[:, 0, own]
+        missing[:, 0, dup] = missing[:, 0, own]
+        M[:, 0, dup] = M[:, 0, own]
+        # 5. correction fields
+        dqx, dqy = K.delta_q(M[0], M[1], M[2], M[3])
+        mu_p = self.mu / (M[0] * M[3])
+        ddx, _ = self._physical_grad(F, dqx)
+        _, ddy = self._physical_grad(F, dqy)
+        Yx, _ = self._physical_grad(F, mu_p * ddx)
+        _, Yy = self._physical_grad(F, mu_p * ddy)
+        # 6. collision; the far field takes the equilibria at its targets
+        with np.errstate(divide="ignore", invalid="ignore"):
+            f_post, g_post = K.collide(f_pre, g_pre, Yx, Yy, self.mu, dt, Cv, self.Pr)
+        f_far = K.f_eq(M[0], M[1], M[2], M[3])
+        g_far = K.g_eq(M[0], M[1], M[2], M[3], Cv)
+        f_post = np.where(far[None], f_far, f_post)
+        g_post = np.where(far[None], g_far, g_post)
+        f_post[:, 0, dup] = f_post[:, 0, own]
+        g_post[:, 0, dup] = g_post[:, 0, own]
+        # 7. force and moment on the wall chain
+        force = (0.0, 0.0, 0.0)
+        if self.bodies:
+            b, st = self.bodies[0], self.S[0]
+            sxx, sxy, syy = forces.node_stress(f_pre[:, 0, wcols], g_pre[:, 0, wcols], Cv,
+                                               self.mu, dt, self.Pr)
+            x_wall = ale.mesh_position(X[0, wcols], self.bodies, self.S)
+            x_ref = np.array([b["xp"], b["yp"] + st["h"]])
+            force = forces.wall_force(x_wall, sxx, sxy, syy, x_ref, closed=False)
+        # 8. structural update
+        new_S = self._advance_bodies(force)
         self.S_prev = [dict(s) for s in self.S]
         self.S = new_S
         self.f, self.g = f_post, g_post

@@ -235,6 +235,85 @@ def xy_case(wall: np.ndarray, nr: int, *, r_far: float = 8.0, centre=(0.0, 0.0),
                   steps=steps, name=name)
 
 
+@dataclass
+class CGridCase:
+    """A case on a C-grid: node coordinates X[nr, nt, 2] (nt odd), the first
+    n_cut row-0 nodes on each side of the wall lying on the wake cut."""
+    nr: int
+    ntheta: int
+    n_cut: int
+    X: np.ndarray
+    centre: tuple
+    flow: FlowSpec
+    bodies: list = field(default_factory=list)
+    steps: int = 0
+    name: str = ""
+
+    @property
+    def nodes(self) -> int:
+        return self.nr * self.ntheta
+
+
+def cgrid_ellipse(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
+                  wake: float = 6.0):
+    """C-grid around an elliptic section (semi-axes a along x, b along y,
+    centred at the origin) with a straight wake cut along y = 0 from the rear
+    point (a, 0) to x = a + wake.  Row 0, counterclockwise: the upper side of
+    the cut from the outlet to the rear point (j < n_cut), the wall (n_wall
+    nodes, odd, both ends at the rear point; even nodes on the ellipse at
+    equal parameter steps, odd nodes chord midpoints), the lower side of the
+    cut back to the outlet.  The cut's element lengths grow geometrically from
+    the wall's first edge.  Grid lines leave the cut at 45 degrees towards
+    the outlet (to the lines y = +-r_far), so that those leaving the wall near
+    the rear point are not tangent to it; the wall's lines end on the arc of
+    radius sqrt(2) r_far about (a, 0) at the angle pi/4 + 3 theta/4 for the
+    wall point of parameter angle theta.  X = W + t_i (C - W) along straight
+    lines (subparametric)."""
+    if n_wall % 2 == 0 or n_wall < 5:
+        raise ValueError("n_wall must be odd and >= 5")
+    if n_cut % 2 or n_cut < 4:
+        raise ValueError("n_cut must be even and >= 4")
+    nt = n_wall + 2 * n_cut
+    th = 2.0 * np.pi * np.arange(n_wall) / (n_wall - 1)
+    wall = np.stack([a * np.cos(th), b * np.sin(th)], axis=1)
+    wall[1::2] = 0.5 * (wall[0:-1:2] + wall[2::2])
+    wall[0] = (a, 0.0)
+    wall[-1] = (a, 0.0)
+    first = float(np.hypot(*(wall[2] - wall[0])))
+    s = ogrid_radii(n_cut + 1, 0.0, wake, 0.5 * first)       # s[0] = 0 at the rear point
+    W = np.empty((nt, 2))
+    C = np.empty((nt, 2))
+    for k in range(1, n_cut + 1):
+        for j, sgn in ((n_cut - k, 1.0), (nt - 1 - n_cut + k, -1.0)):
+            W[j] = (a + s[k], 0.0)
+            C[j] = (a + s[k] + r_far, sgn * r_far)
+    W[n_cut:n_cut + n_wall] = wall
+    psi = 0.25 * np.pi + 0.75 * th
+    C[n_cut:n_cut + n_wall, 0] = a + np.sqrt(2.0) * r_far * np.cos(psi)
+    C[n_cut:n_cut + n_wall, 1] = np.sqrt(2.0) * r_far * np.sin(psi)
+    C[n_cut] = (a + r_far, r_far)
+    C[n_cut + n_wall - 1] = (a + r_far, -r_far)
+    cw = C[n_cut:n_cut + n_wall]
+    cw[1::2] = 0.5 * (cw[0:-1:2] + cw[2::2])
+    t = radial_fractions(nr, first / r_far)
+    return W[None, :, :] + t[:, None, None] * (C - W)[None, :, :]
+
+
+def cgrid_case(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
+               wake: float = 6.0, length: float = 1.0, ma: float = 0.2, re: float = 100.0,
+               t_inf: float = 1.0 / 3.0, gamma: float = 1.4, pr: float = 0.71,
+               body: BodySpec | None = None, steps: int = 0, name: str = "") -> CGridCase:
+    """Elliptic section on a C-grid (cgrid_ellipse); time step a third of the
+    smallest row-0 spacing, as for the O-grid cases."""
+    X = cgrid_ellipse(n_wall, n_cut, nr, a, b, r_far=r_far, wake=wake)
+    d = np.hypot(*(X[0, 1:] - X[0, :-1]).T)
+    first = float(d[d > 0].min())
+    flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr, dt=first / 3.0, length=length)
+    bd = body if body is not None else BodySpec(dof=0)
+    return CGridCase(nr=nr, ntheta=X.shape[1], n_cut=n_cut, X=X, centre=(0.0, 0.0), flow=flow,
+                     bodies=[bd], steps=steps, name=name)
+
+
 def fixed_cylinder_128x64(steps: int = 1000) -> CylinderCase:
     """Fixed cylinder, 128 radial x 64 angular nodes, far field at 20 D,
     Re 100, Ma 0.2 (FP64 parity workload)."""

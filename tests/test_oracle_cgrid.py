@@ -1,0 +1,186 @@
+"""Pins of the oracle's C-grid (readings R28-R30) against facts that do not
+come from the oracle itself:
+- along the wake cut the generated elements are parallelograms (every cut
+  column's grid line has the same direction), so Q2 interpolation reproduces
+  any quadratic exactly, also at points in the mirrored cells across the cut;
+  the index-space gradient stencil across the cut gives a closed-form value;
+- wall normals of the open wall chain: unit, out of the ellipse, (1, 0) at the
+  rear point, where the chain's two ends meet;
+- wall force of the open chain: zero for a uniform stress, -A grad p for a
+  linear pressure (divergence theorem, A the area of the wall polygon);
+- a mirror-symmetric C-grid with a mirror-symmetric initial field stays
+  mirror-symmetric (f_q(i, j) = f_q'(i, Nj-1-j), q' the reflected velocity)."""
+import numpy as np
+import pytest
+
+import oracle.boundary as OB
+import oracle.forces as OF
+import oracle.mesh as OM
+import oracle.solver as OS
+from paper_2107_01370_gb300 import inputs
+
+
+def _case(n_wall=33, n_cut=8, nr=24, **kw):
+    return inputs.cgrid_case(n_wall, n_cut, nr, 0.6, 0.35, r_far=6.0, wake=4.0, **kw)
+
+
+def _quad(P):
+    x, y = P[..., 0], P[..., 1]
+    return 0.7 + 1.3 * x - 0.4 * y + 0.9 * x * x - 1.1 * x * y + 0.6 * y * y
+
+
+def _quad_grad(P):
+    x, y = P[..., 0], P[..., 1]
+    return 1.3 + 1.8 * x - 1.1 * y, -0.4 - 1.1 * x + 1.2 * y
+
+
+def test_generated_cgrid_shape_and_cut():
+    case = _case()
+    X = case.X
+    nt, jc = case.ntheta, case.n_cut
+    assert nt % 2 == 1 and X.shape == (case.nr, nt, 2)
+    for j in range(jc + 1):
+        assert np.array_equal(X[0, j], X[0, nt - 1 - j])
+    assert np.all(X[0, :jc + 1, 1] == 0.0)
+    # rear point is where the wall starts and ends
+    assert np.array_equal(X[0, jc], [0.6, 0.0])
+    m = OM.CGridMesh(X, jc)
+    x_xi, y_xi, x_eta, y_eta = m.metrics()
+    assert np.all(x_xi * y_eta - y_xi * x_eta > 0)
+    with pytest.raises(ValueError):
+        OM.CGridMesh(X, jc + 2)       # nodes jc+1.. of the two sides do not coincide
+
+
+@pytest.mark.parametrize("row", [0, 1, 2])
+def test_quadratic_reproduced_across_the_cut(row):
+    """Departure-type points around cut nodes in every direction, some of
+    them in the mirrored cells below row 0, interpolate a quadratic exactly."""
+    case = _case()
+    X = case.X
+    nt, jc = case.ntheta, case.n_cut
+    m = OM.CGridMesh(X, jc)
+    field = _quad(X)
+    cols = [j for j in range(1, nt - 1) if j < jc or j > nt - 1 - jc]
+    h = 0.3 * np.min(np.hypot(*(X[0, 1:jc + 1] - X[0, :jc]).T))
+    worst = 0.0
+    used_ghost = False
+    for j in cols:
+        for ang in np.linspace(0.0, 2.0 * np.pi, 16, endpoint=False):
+            P = X[row, j] + h * np.array([np.cos(ang), np.sin(ang)])
+            wa, wb, xi, eta, found = m.locate(P[None], np.array([row]), np.array([j]))
+            assert found[0], (row, j, ang)
+            used_ghost |= bool(wa[0] < 0)
+            v = m.interpolate(field, wa, wb, xi, eta)[0]
+            worst = max(worst, abs(v - _quad(P)))
+    assert worst < 1e-12
+    if row == 0:
+        assert used_ghost
+
+
+def test_gradient_across_the_cut():
+    """At a row-0 cut node (x, 0) the i-stencil differences the field between
+    its first rows on both sides of the cut, (x + h, h) and (x + h, -h) on the
+    45-degree grid lines, the j-stencil along the cut.  For F = y^2 + x y the
+    stencil gives exactly (dF/dX, dF/dY) = (0, x + h), the y-derivative at
+    the shifted point, which a wrong mirrored row would not.  Linear fields
+    are exact everywhere, the rear point included."""
+    case = _case()
+    X = case.X
+    nt, jc = case.ntheta, case.n_cut
+    m = OM.CGridMesh(X, jc)
+    dX, dY = m.grad_X(X[..., 1] ** 2 + X[..., 0] * X[..., 1])
+    for j in list(range(1, jc)) + list(range(nt - jc, nt - 1)):
+        assert abs(dX[0, j]) < 1e-12
+        assert abs(dY[0, j] - X[1, j, 0]) < 1e-12
+    lx, ly = m.grad_X(0.7 + 1.3 * X[..., 0] - 0.4 * X[..., 1])
+    assert np.abs(lx - 1.3).max() < 1e-11 and np.abs(ly + 0.4).max() < 1e-11
+
+
+def test_wrong_mirror_breaks_the_quadratic():
+    """Planted mistake: ghost rows read their values one column off.  The
+    quadratic across the cut is no longer reproduced, so the pin above has
+    teeth."""
+    case = _case()
+    X = case.X
+    m = OM.CGridMesh(X, case.n_cut)
+    bad = OM.CGridMesh(X, case.n_cut)
+    good = bad.window_node
+
+    def shifted(wa, wb, a, b):
+        i, j = good(wa, wb, a, b)
+        return i, np.where(np.asarray(wa) < 0, np.maximum(j - 1, 0), j)
+
+    bad.window_node = shifted
+    j = 3
+    P = X[0, j] - np.array([0.0, 0.3 * X[1, j, 1]])   # below the cut, within the first row
+    wa, wb, xi, eta, found = m.locate(P[None], np.array([0]), np.array([j]))
+    assert found[0] and wa[0] < 0
+    assert abs(m.interpolate(_quad(X), wa, wb, xi, eta)[0] - _quad(P)) < 1e-12
+    assert abs(bad.interpolate(_quad(X), wa, wb, xi, eta)[0] - _quad(P)) > 1e-6
+
+
+def test_wall_normals_of_the_open_chain():
+    case = _case()
+    m = OM.CGridMesh(case.X, case.n_cut)
+    n = OB.wall_normals_cgrid(m)
+    jc, nt = case.n_cut, case.ntheta
+    wall = np.arange(jc, nt - jc)
+    assert np.allclose(np.hypot(n[wall, 0], n[wall, 1]), 1.0, atol=1e-14)
+    P = case.X[0, wall]
+    grad = np.stack([2 * P[:, 0] / 0.6 ** 2, 2 * P[:, 1] / 0.35 ** 2], axis=1)
+    assert np.all(np.sum(n[wall] * grad, axis=1) > 0)
+    assert np.allclose(n[jc], [1.0, 0.0], atol=1e-14)
+    assert np.array_equal(n[jc], n[nt - 1 - jc])
+    assert np.all(n[:jc] == 0.0) and np.all(n[nt - jc:] == 0.0)
+
+
+def test_open_chain_force_closed_forms():
+    case = _case()
+    jc, nt = case.n_cut, case.ntheta
+    P = case.X[0, jc:nt - jc]
+    k = P.shape[0]
+    F = OF.wall_force(P, np.full(k, -2.0), np.full(k, 0.3), np.full(k, -0.7), np.zeros(2),
+                      closed=False)
+    assert max(abs(F[0]), abs(F[1]), abs(F[2])) < 1e-13
+    # linear pressure p = a . x: sigma = -p I; F = -sum p n ds = -A a (the
+    # outward normal of the fluid region is -n)
+    a = np.array([0.4, -0.25])
+    p = P @ a
+    F = OF.wall_force(P, -p, np.zeros(k), -p, np.zeros(2), closed=False)
+    V = P[0:-1:2]
+    area = 0.5 * np.sum(V[:, 0] * np.roll(V[:, 1], -1) - np.roll(V[:, 0], -1) * V[:, 1])
+    assert abs(F[0] + area * a[0]) < 1e-13 and abs(F[1] + area * a[1]) < 1e-13
+
+
+REFLECT = np.array([0, 1, 4, 3, 2, 8, 7, 6, 5])   # c_q -> (c_x, -c_y)
+
+
+def test_mirror_symmetric_flow_stays_symmetric():
+    case = _case(n_wall=29, n_cut=6, nr=16)
+    X = case.X
+    nt, jc = case.ntheta, case.n_cut
+    # the generator mirrors the two sides up to the round-off of cos/sin
+    assert np.allclose(X[:, ::-1, 0], X[:, :, 0], atol=1e-14)
+    assert np.allclose(X[:, ::-1, 1], -X[:, :, 1], atol=1e-14)
+    Xs = X.copy()
+    Xs[:, nt // 2 + 1:, 0] = X[:, :nt // 2, 0][:, ::-1]
+    Xs[:, nt // 2 + 1:, 1] = -X[:, :nt // 2, 1][:, ::-1]
+    Xs[:, nt // 2, 1] = 0.0
+    M0 = inputs.initial_field(case.nr, nt, case.flow, noise=1e-2, seed=7)
+    M = M0.copy()
+    M[0] = 0.5 * (M0[0] + M0[0, :, ::-1])
+    M[1] = 0.5 * (M0[1] + M0[1, :, ::-1])
+    M[2] = 0.5 * (M0[2] - M0[2, :, ::-1])
+    M[3] = 0.5 * (M0[3] + M0[3, :, ::-1])
+    M[2, 0, :jc + 1] = 0.0
+    M[2, 0, nt - 1 - jc:] = 0.0
+    m = OM.CGridMesh(Xs, jc)
+    s = OS.Solver.from_case(m, case, M)
+    for _ in range(4):
+        r = s.step()
+    f = r.f_post
+    scale = np.abs(f).max()
+    assert np.abs(f - f[REFLECT][:, :, ::-1]).max() < 1e-12 * scale
+    assert abs(r.force[1]) < 1e-12 and abs(r.force[2]) < 1e-12
+    # the lower copies of the cut nodes hold the upper copies' values
+    assert np.array_equal(r.M[:, 0, nt - 1 - jc:], r.M[:, 0, :jc + 1][:, ::-1])
