@@ -139,6 +139,37 @@ typedef struct {
  * oriented. */
 int lbfsi_create_mesh_xy(const lbfsi_mesh_xy_desc* d, void* cuda_stream, lbfsi_mesh* out);
 
+/* A C-grid around one body with a wake cut (the airfoil mesh type of
+ * Sec. IV D; node coordinates, subparametric and positively oriented as in
+ * lbfsi_mesh_xy_desc).  Row 0 runs counterclockwise: the upper side of the
+ * cut from the outlet to the body (j < n_cut), the wall from its rear point
+ * over the upper surface and the front back to the rear point
+ * (n_cut <= j <= ntheta-1-n_cut), then the lower side of the cut out to the
+ * outlet; row-0 nodes j and ntheta-1-j must be the same point for
+ * j <= n_cut.  Rows grow away from row 0; row nr - 1 and the columns j = 0
+ * and j = ntheta-1 are far field (inlet or outlet by the free stream's
+ * direction).  Across the cut the mesh continues as its mirror (the node of
+ * row -k, column j is the node of row k, column ntheta-1-j), so departure
+ * points of cut nodes may lie on the other side.  Fields read and written
+ * through the handle are [nr][ntheta] per component; the second copies of the
+ * row-0 nodes along the cut hold the first copies' values. */
+typedef struct {
+    int nr, ntheta;             /* nr >= 5; ntheta odd >= 7 */
+    int n_cut;                  /* row-0 nodes on each side of the cut (even, >= 2; the wall keeps >= 3 nodes) */
+    const double* X;            /* [nr][ntheta][2] node coordinates (host, borrowed) */
+    double xc, yc;              /* mesh centre (reference point of the geometry)   */
+    int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations             */
+    int nbatch;                 /* independent solves sharing the mesh, >= 1        */
+    const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)      */
+} lbfsi_mesh_cgrid_desc;
+
+/* Create a mesh handle on a C-grid; otherwise as lbfsi_create_mesh_xy (one
+ * tile shape).  A step is two launches here: the collision of step k into a
+ * post-collision buffer, then the stream of step k + 1 from it.
+ * LBFSI_EINVAL for an even ntheta, a bad n_cut, cut nodes that do not
+ * coincide, or a mesh that is not subparametric or not positively oriented. */
+int lbfsi_create_mesh_cgrid(const lbfsi_mesh_cgrid_desc* d, void* cuda_stream, lbfsi_mesh* out);
+
 /* Release every device buffer of the handle (synchronises its stream). */
 int lbfsi_destroy_mesh(lbfsi_mesh m);
 

@@ -95,6 +95,12 @@ class Solver:
         self.bodies = list(bodies)
         self.walls = walls
         M0 = np.asarray(M0, dtype=np.float64)
+        if isinstance(mesh, CGridMesh):
+            # reading R28: the two copies of a cut node start from the first
+            # copy's values
+            M0 = M0.copy()
+            dup = np.nonzero(mesh.duplicate_columns())[0]
+            M0[:, 0, dup] = M0[:, 0, mesh.Nj - 1 - dup]
         self.f = K.f_eq(M0[0], M0[1], M0[2], M0[3])
         self.g = K.g_eq(M0[0], M0[1], M0[2], M0[3], self.Cv)
         self.M_prev = M0.copy()

@@ -130,6 +130,56 @@ int upload(lbfsi_mesh m, const double* host, void* ddst, size_t n) {
     return LBFSI_OK;
 }
 
+// Field blocks of w values per node: the caller's [blocks][N] layout to the
+// device's [blocks][Nx] (a C-grid's mirrored rows below row 0 filled from
+// their nodes, node (-k, j) = node (k, nt-1-j)), and back.
+std::vector<double> expand_rows(const lbfsi::HostMesh& h, const double* user, size_t blocks, int w) {
+    const size_t N = (size_t)h.N, Nx = (size_t)h.Nx, nt = (size_t)h.nt, g0 = (size_t)h.G * nt;
+    std::vector<double> dev(blocks * Nx * w);
+    for (size_t b = 0; b < blocks; ++b) {
+        const double* u = user + b * N * w;
+        double* d = dev.data() + b * Nx * w;
+        std::memcpy(d + g0 * w, u, N * w * sizeof(double));
+        for (int k = 1; k <= h.G; ++k)
+            for (size_t j = 0; j < nt; ++j)
+                for (int c = 0; c < w; ++c)
+                    d[(g0 - k * nt + j) * w + c] = u[(k * nt + (nt - 1 - j)) * w + c];
+    }
+    return dev;
+}
+
+void compact_rows(const lbfsi::HostMesh& h, const double* dev, double* user, size_t blocks, int w) {
+    const size_t N = (size_t)h.N, Nx = (size_t)h.Nx, g0 = (size_t)h.G * h.nt;
+    for (size_t b = 0; b < blocks; ++b)
+        std::memcpy(user + b * N * w, dev + (b * Nx + g0) * w, N * w * sizeof(double));
+}
+
+// A C-grid's second copies of the row-0 cut nodes (and of the rear point)
+// take the first copies' values in caller-given fields of w values per node.
+void unify_cut_copies(const lbfsi::HostMesh& h, double* user, size_t blocks, int w) {
+    if (!h.cgrid) return;
+    for (size_t b = 0; b < blocks; ++b)
+        for (int j = 0; j <= h.jc; ++j)
+            for (int c = 0; c < w; ++c)
+                user[(b * h.N + (size_t)(h.nt - 1 - j)) * w + c] = user[(b * h.N + (size_t)j) * w + c];
+}
+
+// One coupled step of every solve: one launch (collide of step k, stream of
+// k + 1), or on a C-grid a collide-only launch into ppost and a stream-only
+// launch from it, because the mirrored rows of one side need the other
+// side's post-collision populations.
+int launches_per_step(lbfsi_mesh m) { return m->host.cgrid ? 2 : 1; }
+
+cudaError_t launch_one_step(lbfsi_mesh m, lbfsi::StepArgs a, cudaStream_t s) {
+    if (!m->host.cgrid) return lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, s);
+    lbfsi::StepArgs c = a;
+    c.collide_only = 1;
+    cudaError_t e = lbfsi::launch_step_uniform(c, m->precision, m->variant, m->nbatch, s);
+    if (e != cudaSuccess) return e;
+    a.stream_post = 1;
+    return lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, s);
+}
+
 void free_all(lbfsi_mesh m) {
     void* ptrs[] = {m->d_p[0], m->d_p[1], m->d_M[0], m->d_M[1], m->d_ppost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
                     m->d_loads_tmp, m->d_part, m->d_counter, m->d_bodies, m->d_meshdev, m->d_solves,
@@ -145,17 +195,18 @@ void free_all(lbfsi_mesh m) {
 // Per-solve descriptors of the handle: solve b's buffers are slices of the
 // batch-contiguous arrays.
 int upload_solves(lbfsi_mesh m) {
-    const size_t N = (size_t)m->host.N, es = m->esize;
+    // field pointers at row 0 of solve b (a C-grid's mirrored rows before it)
+    const size_t N = (size_t)m->host.Nx, es = m->esize, g0 = (size_t)m->host.G * m->host.nt;
     for (int b = 0; b < m->nbatch; ++b) {
         SolveDev& s = m->solves[b];
         s.mesh = 0;
         s.ntiles = m->tiles_per_solve;
         for (int p = 0; p < 2; ++p) {
-            s.p[p] = (char*)m->d_p[p] + (size_t)b * 18 * N * es;
-            s.M[p] = (char*)m->d_M[p] + (size_t)b * 4 * N * es;
+            s.p[p] = (char*)m->d_p[p] + ((size_t)b * 18 * N + 2 * g0) * es;
+            s.M[p] = (char*)m->d_M[p] + ((size_t)b * 4 * N + g0) * es;
             s.maps[p] = m->d_maps[p] + b;
         }
-        s.ppost = m->d_ppost ? (char*)m->d_ppost + (size_t)b * 18 * N * es : nullptr;
+        s.ppost = m->d_ppost ? (char*)m->d_ppost + ((size_t)b * 18 * N + 2 * g0) * es : nullptr;
         s.part = m->d_part + (size_t)b * m->host.ntj * 3;
         s.counter = m->d_counter + 2 * b;
         s.body = m->d_bodies + b;
@@ -194,8 +245,7 @@ int capture_graph(lbfsi_mesh m) {
     e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
     cudaError_t le = cudaSuccess;
-    for (int g = 0; g < m->graph_steps && le == cudaSuccess; ++g)
-        le = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->cap_stream);
+    for (int g = 0; g < m->graph_steps && le == cudaSuccess; ++g) le = launch_one_step(m, a, m->cap_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(m->cap_stream, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -273,6 +323,20 @@ int lbfsi_create_mesh_xy(const lbfsi_mesh_xy_desc* d, void* cuda_stream, lbfsi_m
     return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
 }
 
+int lbfsi_create_mesh_cgrid(const lbfsi_mesh_cgrid_desc* d, void* cuda_stream, lbfsi_mesh* out) {
+    g_last_error.clear();
+    if (!d) return fail(LBFSI_EINVAL, "null argument");
+    int rc = check_common(d->nr + lbfsi::CGRID_GHOST_ROWS, d->ntheta, d->precision, d->nbatch, d->bodies, out);
+    if (rc) return rc;
+    auto m = new lbfsi_mesh_s();
+    rc = lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->n_cut, d->X, d->xc, d->yc, m->host);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
+}
+
 namespace {
 
 int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc* bodies, void* cuda_stream,
@@ -307,7 +371,7 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
         delete m;
         return rc;
     }
-    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
     const int ntj = m->host.ntj;
     cudaError_t e = cudaSuccess;
 #define LB_ALLOC(ptr, cnt) \
@@ -329,6 +393,7 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
         e = cudaMalloc(&m->d_p[k], nb * 18 * N * m->esize);
         if (e == cudaSuccess) e = cudaMalloc(&m->d_M[k], nb * 4 * N * m->esize);
     }
+    if (e == cudaSuccess && m->host.cgrid) e = cudaMalloc(&m->d_ppost, nb * 18 * N * m->esize);
     if (e != cudaSuccess) {
         free_all(m);
         delete m;
@@ -383,6 +448,8 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     }
     std::vector<BodyStateDev> zero(nb, BodyStateDev{0.0, 0.0, 0.0, 0.0});
     std::vector<double> zl(nb * 3, 0.0);
+    unify_cut_copies(m->host, M.data(), nb * 4, 1);
+    if (m->host.G) M = expand_rows(m->host, M.data(), nb * 4, 1);
     cudaError_t e = cudaMemcpyAsync(m->d_bodies, bd.data(), nb * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
@@ -396,7 +463,7 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     m->host_k = 0;
     rc = upload_solves(m);
     if (rc) return rc;
-    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_p[0], m->d_M[0], m->host.N, m->nbatch,
+    e = lbfsi::launch_init(m->precision, m->d_stage, m->d_p[0], m->d_M[0], m->host.Nx, m->nbatch,
                            proto.Cv, m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
@@ -444,15 +511,15 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
         for (; nsteps - s >= m->graph_steps; s += m->graph_steps) {
             const cudaError_t e = cudaGraphLaunch(m->graph, m->stream);
             if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-            m->launches += m->graph_steps;
+            m->launches += (int64_t)m->graph_steps * launches_per_step(m);
             m->host_k += (unsigned)m->graph_steps;
         }
     }
     lbfsi::StepArgs a = make_args(m, 0);
     for (; s < nsteps; ++s) {
         a.ustep = (int)m->host_k;
-        cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
-        m->launches++;
+        cudaError_t e = launch_one_step(m, a, m->stream);
+        m->launches += launches_per_step(m);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         m->host_k++;
     }
@@ -498,8 +565,8 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
     lbfsi::StepArgs a = make_args(m, 0);
     for (int s = 0; s < nsteps; ++s) {
         a.ustep = (int)m->host_k;
-        cudaError_t e = lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, m->stream);
-        m->launches++;
+        cudaError_t e = launch_one_step(m, a, m->stream);
+        m->launches += launches_per_step(m);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         m->host_k++;
         // the launch's epilogue wrote the step's loads and new body state into
@@ -575,7 +642,14 @@ int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out) {
 int lbfsi_get_fields(lbfsi_mesh m, double* rho_u_T) {
     if (!m || !rho_u_T) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    int rc = download(m, m->d_M[m->cur()], rho_u_T, (size_t)m->nbatch * 4 * m->host.N);
+    int rc;
+    if (m->host.G) {
+        std::vector<double> all((size_t)m->nbatch * 4 * m->host.Nx);
+        rc = download(m, m->d_M[m->cur()], all.data(), all.size());
+        if (!rc) compact_rows(m->host, all.data(), rho_u_T, (size_t)m->nbatch * 4, 1);
+    } else {
+        rc = download(m, m->d_M[m->cur()], rho_u_T, (size_t)m->nbatch * 4 * m->host.N);
+    }
     if (rc) return rc;
     return check_status(m);
 }
@@ -584,12 +658,12 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
     if (!m || !f || !g) return fail(LBFSI_EINVAL, "null argument");
     if (which != 0 && which != 1) return fail(LBFSI_EINVAL, "which must be 0 or 1");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    const size_t cnt = (size_t)m->nbatch * 9 * m->host.N;
+    const size_t cnt = (size_t)m->nbatch * 9 * m->host.N, cntx = (size_t)m->nbatch * 9 * m->host.Nx;
     const void* ps = m->d_p[m->cur()];
     if (which == 1 && !m->first()) {
         cudaError_t e = cudaSuccess;
         if (!m->d_ppost) {
-            e = cudaMalloc(&m->d_ppost, 2 * cnt * m->esize);
+            e = cudaMalloc(&m->d_ppost, 2 * cntx * m->esize);
             if (e != cudaSuccess) return fail(LBFSI_ENOMEM, "post-collision staging allocation failed");
             const int rc = upload_solves(m);
             if (rc) return rc;
@@ -600,7 +674,14 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g) {
         ps = m->d_ppost;
     }
     std::vector<double> pairs(2 * cnt);
-    int rc = download(m, ps, pairs.data(), 2 * cnt);
+    int rc;
+    if (m->host.G) {
+        std::vector<double> all(2 * cntx);
+        rc = download(m, ps, all.data(), all.size());
+        if (!rc) compact_rows(m->host, all.data(), pairs.data(), (size_t)m->nbatch * 9, 2);
+    } else {
+        rc = download(m, ps, pairs.data(), 2 * cnt);
+    }
     if (rc) return rc;
     for (size_t k = 0; k < cnt; ++k) {
         f[k] = pairs[2 * k];
@@ -619,8 +700,19 @@ int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g, const 
         pairs[2 * k] = f[k];
         pairs[2 * k + 1] = g[k];
     }
-    int rc = upload(m, pairs.data(), m->d_p[c], 2 * cnt);
-    if (!rc) rc = upload(m, rho_u_T, m->d_M[c], (size_t)m->nbatch * 4 * m->host.N);
+    int rc;
+    if (m->host.G) {
+        std::vector<double> mu(rho_u_T, rho_u_T + (size_t)m->nbatch * 4 * m->host.N);
+        unify_cut_copies(m->host, pairs.data(), (size_t)m->nbatch * 9, 2);
+        unify_cut_copies(m->host, mu.data(), (size_t)m->nbatch * 4, 1);
+        const std::vector<double> px = expand_rows(m->host, pairs.data(), (size_t)m->nbatch * 9, 2);
+        const std::vector<double> mx = expand_rows(m->host, mu.data(), (size_t)m->nbatch * 4, 1);
+        rc = upload(m, px.data(), m->d_p[c], px.size());
+        if (!rc) rc = upload(m, mx.data(), m->d_M[c], mx.size());
+    } else {
+        rc = upload(m, pairs.data(), m->d_p[c], 2 * cnt);
+        if (!rc) rc = upload(m, rho_u_T, m->d_M[c], (size_t)m->nbatch * 4 * m->host.N);
+    }
     if (rc) return rc;
     // the restored state is post-propagation: make the next launch collide it
     // (step number >= 2 with the same parity)
@@ -649,7 +741,7 @@ struct CheckpointHeader {
 constexpr char kMagic[8] = {'L', 'B', 'F', 'S', 'I', 'C', 'K', '1'};
 
 size_t checkpoint_bytes(lbfsi_mesh m) {
-    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
     return sizeof(CheckpointHeader) + nb * 18 * N * m->esize + nb * 4 * N * m->esize + nb * sizeof(StepMaps);
 }
 }  // namespace
@@ -672,7 +764,7 @@ int lbfsi_checkpoint(lbfsi_mesh m, void* buf, size_t bytes) {
     h.nt = m->host.nt;
     h.esize = (int32_t)m->esize;
     h.step = m->host_k;
-    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
@@ -701,7 +793,7 @@ int lbfsi_restore(lbfsi_mesh m, const void* buf, size_t bytes) {
         return fail(LBFSI_EINVAL, "checkpoint of a different mesh, batch or precision");
     drop_graph(m);
     m->host_k = h.step;
-    const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
+    const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
     const char* p = static_cast<const char*>(buf) + sizeof(h);
     const int c = m->cur();
     cudaError_t e = cudaMemcpyAsync(m->d_p[c], p, nb * 18 * N * m->esize, cudaMemcpyHostToDevice, m->stream);

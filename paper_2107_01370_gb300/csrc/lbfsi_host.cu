@@ -129,6 +129,7 @@ int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc,
     m.nr = nr;
     m.nt = nt;
     m.N = nr * nt;
+    m.Nx = m.N;
     m.ntj = tiles_j(nt);
     m.xm = xc;
     m.ym = yc;
@@ -171,6 +172,7 @@ int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, Ho
     m.nr = nr;
     m.nt = nt;
     m.N = nr * nt;
+    m.Nx = m.N;
     m.ntj = tiles_j(nt);
     m.xm = xc;
     m.ym = yc;
@@ -248,6 +250,186 @@ int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, Ho
     return LBFSI_OK;
 }
 
+// Wall geometry of a C-grid: the open chain of row-0 columns jc .. nt-1-jc
+// (counterclockwise, straight edges between its even-offset nodes), whose two
+// ends are the rear point.  Normals as on a closed wall; the first copy of
+// the rear point takes the Simpson shares of both end edges, the second copy
+// none (its values are the first copy's).
+static void wall_geometry_chain(HostMesh& m) {
+    const int nt = m.nt, jc = m.jc, ne = (nt - 1 - 2 * jc) / 2;
+    const std::vector<double>& X = m.xw;
+    std::vector<double> en(2 * ne), ds(ne);
+    for (int k = 0; k < ne; ++k) {
+        const int a = jc + 2 * k, c = a + 2;
+        const double tx = X[2 * c] - X[2 * a], ty = X[2 * c + 1] - X[2 * a + 1];
+        const double L = std::sqrt(tx * tx + ty * ty);
+        ds[k] = L;
+        en[2 * k] = ty / L;
+        en[2 * k + 1] = -tx / L;
+    }
+    m.n0.assign(2 * nt, 0.0);
+    m.wall_geo.assign(6 * nt, 0.0);
+    for (int mm = 0; mm < nt - 2 * jc; ++mm) {
+        const int j = jc + mm;
+        double* g = &m.wall_geo[6 * j];
+        if (mm % 2) {
+            const int k = mm / 2;
+            m.n0[2 * j] = en[2 * k];
+            m.n0[2 * j + 1] = en[2 * k + 1];
+            g[0] = 4.0 / 6.0 * ds[k];
+            g[1] = en[2 * k];
+            g[2] = en[2 * k + 1];
+            continue;
+        }
+        const int k1 = mm > 0 ? mm / 2 - 1 : ne - 1, k2 = mm / 2 < ne ? mm / 2 : 0;
+        const double vx = en[2 * k1] + en[2 * k2], vy = en[2 * k1 + 1] + en[2 * k2 + 1];
+        const double L = std::sqrt(vx * vx + vy * vy);
+        m.n0[2 * j] = vx / L;
+        m.n0[2 * j + 1] = vy / L;
+        if (j == nt - 1 - jc) continue;   // second copy of the rear point
+        g[0] = ds[k2] / 6.0;
+        g[1] = en[2 * k2];
+        g[2] = en[2 * k2 + 1];
+        g[3] = ds[k1] / 6.0;
+        g[4] = en[2 * k1];
+        g[5] = en[2 * k1 + 1];
+    }
+}
+
+int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, double yc, HostMesh& m) {
+    if (nr < 5) return set_error(LBFSI_EINVAL, "nr must be >= 5");
+    if (nt < 7 || nt % 2 == 0) return set_error(LBFSI_EINVAL, "a C-grid needs an odd node count (>= 7) along the C");
+    if (n_cut < 2 || n_cut % 2 || 2 * n_cut > nt - 4)
+        return set_error(LBFSI_EINVAL, "n_cut must be even and >= 2 and leave a wall of at least 3 nodes");
+    if (!X) return set_error(LBFSI_EINVAL, "null coordinate pointer");
+    const int G = CGRID_GHOST_ROWS;
+    if (nr < G + 1) return set_error(LBFSI_EINVAL, "a C-grid needs nr > 4");
+    m.general = true;
+    m.cgrid = true;
+    m.jc = n_cut;
+    m.G = G;
+    m.nr = nr;
+    m.nt = nt;
+    m.N = nr * nt;
+    m.Nx = (nr + G) * nt;
+    m.ntj = tiles_j(nt);
+    m.xm = xc;
+    m.ym = yc;
+    std::vector<double> Xu(X, X + 2 * (size_t)m.N);
+    double scale = 0.0;
+    for (double v : Xu) {
+        if (!std::isfinite(v)) return set_error(LBFSI_EINVAL, "node coordinates must be finite");
+        scale = std::max(scale, std::fabs(v));
+    }
+    auto P = [&](int i, int j, int c) { return Xu[2 * ((size_t)i * nt + j) + c]; };
+    for (int j = 0; j <= n_cut; ++j)
+        for (int c = 0; c < 2; ++c)
+            if (std::fabs(P(0, j, c) - P(0, nt - 1 - j, c)) > 1e-12 * scale)
+                return set_error(LBFSI_EINVAL, "row-0 nodes j and ntheta-1-j must coincide along the cut (j <= n_cut)");
+    auto check_window = [&](int wa, int wb) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const double xi = a - 1.0, et = b - 1.0;
+                for (int c = 0; c < 2; ++c) {
+                    const double v = 0.25 * ((1 - xi) * (1 - et) * P(wa, wb, c) + (1 + xi) * (1 - et) * P(wa + 2, wb, c) +
+                                             (1 - xi) * (1 + et) * P(wa, wb + 2, c) + (1 + xi) * (1 + et) * P(wa + 2, wb + 2, c));
+                    if (std::fabs(v - P(wa + a, wb + b, c)) > 1e-12 * scale) return false;
+                }
+            }
+        return true;
+    };
+    for (int wa = 0; wa + 2 < nr; wa += 2)
+        for (int wb = 0; wb + 2 < nt; wb += 2)
+            if (!check_window(wa, wb) || (nr % 2 == 0 && !check_window(nr - 3, wb)))
+                return set_error(LBFSI_EINVAL, "node coordinates must be subparametric "
+                                               "(every window the bilinear image of its corners)");
+    m.xw.assign(2 * (size_t)nt, 0.0);
+    m.fardir.assign(2 * (size_t)nt, 0.0);
+    m.fardirj.assign(4 * (size_t)nr, 0.0);
+    for (int j = 0; j < nt; ++j)
+        for (int c = 0; c < 2; ++c) {
+            m.xw[2 * j + c] = P(0, j, c);
+            m.fardir[2 * j + c] = P(nr - 1, j, c) - P(nr - 2, j, c);
+        }
+    for (int i = 0; i < nr; ++i)
+        for (int c = 0; c < 2; ++c) {
+            m.fardirj[4 * i + c] = P(i, 0, c) - P(i, 1, c);
+            m.fardirj[4 * i + 2 + c] = P(i, nt - 1, c) - P(i, nt - 2, c);
+        }
+    wall_geometry_chain(m);
+    // node coordinates with the mirrored rows: X(-k, j) = X(k, nt-1-j)
+    const size_t g0 = (size_t)G * nt;
+    m.X.assign(2 * (size_t)m.Nx, 0.0);
+    for (int i = -G; i < nr; ++i)
+        for (int j = 0; j < nt; ++j)
+            for (int c = 0; c < 2; ++c)
+                m.X[2 * (g0 + (size_t)i * nt + j) + c] = i < 0 ? P(-i, nt - 1 - j, c) : P(i, j, c);
+    // inverse metric with the C-grid stencils (central across the cut on row
+    // 0 of the cut and at both copies of the rear point; one-sided along the
+    // cut at the rear point, along i on the rest of the wall and the far
+    // field, along j at the outlet columns); the mirrored rows carry the
+    // negated inverse metric of their node (both index directions reversed)
+    m.jinv.assign(4 * (size_t)m.Nx, 0.0);
+    for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < nt; ++j) {
+            const bool across = i == 0 && (j <= n_cut || j >= nt - 1 - n_cut);
+            double di[2], dj[2];
+            for (int c = 0; c < 2; ++c) {
+                if (across)
+                    di[c] = 0.5 * (P(1, j, c) - P(1, nt - 1 - j, c));
+                else if (i == 0)
+                    di[c] = 0.5 * (-3.0 * P(0, j, c) + 4.0 * P(1, j, c) - P(2, j, c));
+                else if (i == nr - 1)
+                    di[c] = 0.5 * (3.0 * P(nr - 1, j, c) - 4.0 * P(nr - 2, j, c) + P(nr - 3, j, c));
+                else
+                    di[c] = 0.5 * (P(i + 1, j, c) - P(i - 1, j, c));
+                if (j == 0 || (i == 0 && j == nt - 1 - n_cut))
+                    dj[c] = 0.5 * (-3.0 * P(i, j, c) + 4.0 * P(i, j + 1, c) - P(i, j + 2, c));
+                else if (j == nt - 1 || (i == 0 && j == n_cut))
+                    dj[c] = 0.5 * (3.0 * P(i, j, c) - 4.0 * P(i, j - 1, c) + P(i, j - 2, c));
+                else
+                    dj[c] = 0.5 * (P(i, j + 1, c) - P(i, j - 1, c));
+            }
+            const double det = di[0] * dj[1] - di[1] * dj[0];
+            if (!(det > 0.0))
+                return set_error(LBFSI_EINVAL, "mesh not positively oriented (index-to-space Jacobian <= 0)");
+            double* t = &m.jinv[4 * (g0 + (size_t)i * nt + j)];
+            t[0] = dj[1] / det;
+            t[1] = -di[1] / det;
+            t[2] = -dj[0] / det;
+            t[3] = di[0] / det;
+        }
+    for (int k = 1; k <= G; ++k)
+        for (int j = 0; j < nt; ++j)
+            for (int c = 0; c < 4; ++c)
+                m.jinv[4 * (g0 - (size_t)k * nt + j) + c] = -m.jinv[4 * (g0 + (size_t)k * nt + (nt - 1 - j)) + c];
+    // element coefficients per cell (a, b), a in [-G, nr-2], b in [0, nt-2];
+    // a mirrored cell is the cell (-a-1, nt-2-b) with both local coordinates
+    // reversed: (b, c, d) -> (-b, -c, d)
+    m.cellc.assign((size_t)(nr - 1 + G) * nt * CELLC, 0.0);
+    auto cell = [&](int a, int b) { return &m.cellc[(g0 + (size_t)a * nt + b) * CELLC]; };
+    for (int a = 0; a < nr - 1; ++a)
+        for (int b = 0; b < nt - 1; ++b) {
+            const int wa = std::min(2 * (a / 2), nr - 3), wb = std::min(2 * (b / 2), nt - 3);
+            double* t = cell(a, b);
+            for (int c = 0; c < 2; ++c) {
+                const double c00 = P(wa, wb, c), c10 = P(wa + 2, wb, c), c01 = P(wa, wb + 2, c), c11 = P(wa + 2, wb + 2, c);
+                t[0 + c] = 0.25 * (-c00 + c10 - c01 + c11);
+                t[2 + c] = 0.25 * (-c00 - c10 + c01 + c11);
+                t[4 + c] = 0.25 * (c00 - c10 - c01 + c11);
+            }
+        }
+    for (int k = 1; k <= G; ++k)
+        for (int b = 0; b < nt - 1; ++b) {
+            const double* src = cell(k - 1, nt - 2 - b);
+            double* t = cell(-k, b);
+            for (int c = 0; c < 4; ++c) t[c] = -src[c];
+            t[4] = src[4];
+            t[5] = src[5];
+        }
+    return LBFSI_OK;
+}
+
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
     if (!bodies) return set_error(LBFSI_EINVAL, "null body pointer");
     for (int k = 0; k < n; ++k) {
@@ -259,6 +441,7 @@ int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
         if (!(b.forced_periods >= 0.0) || !std::isfinite(b.pitch_amp) || !std::isfinite(b.forced_periods))
             return set_error(LBFSI_EINVAL, "forced pitching needs a finite amplitude and forced_periods >= 0");
         for (int j = 0; j < m.nt; ++j) {
+            if (m.cgrid && (j < m.jc || j > m.nt - 1 - m.jc)) continue;   // the cut
             const double x = m.xw[2 * j] - b.xc;
             const double y = m.xw[2 * j + 1] - b.yc;
             if (std::sqrt(x * x + y * y) >= b.r_in)
@@ -365,7 +548,7 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     MeshDev& d = out.dev;
     d.nr = h.nr;
     d.nt = h.nt;
-    d.N = h.N;
+    d.N = h.Nx;
     d.ntj = h.ntj;
     d.xm = h.xm;
     d.ym = h.ym;
@@ -378,7 +561,7 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     }
     d.emin_f = (float)d.emin;
     void *pr = nullptr, *pe = nullptr, *pn = nullptr, *pw = nullptr, *prt = nullptr, *pct = nullptr;
-    void *pxw = nullptr, *pfd = nullptr, *px = nullptr, *pj = nullptr, *pc = nullptr;
+    void *pxw = nullptr, *pfd = nullptr, *px = nullptr, *pj = nullptr, *pc = nullptr, *pfj = nullptr;
     int rc = put(h.n0, false, &pn);
     if (!rc) rc = put(h.wall_geo, false, &pw);
     if (!rc) rc = put(h.xw, false, &pxw);
@@ -387,6 +570,7 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
         if (!rc) rc = put(h.X, true, &px);
         if (!rc) rc = put(h.jinv, true, &pj);
         if (!rc) rc = put(h.cellc, true, &pc);
+        if (!rc && h.cgrid) rc = put(h.fardirj, false, &pfj);
     } else {
         if (!rc) rc = put(h.r, false, &pr);
         if (!rc) rc = put(h.e, false, &pe);
@@ -406,9 +590,14 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.xw = (const double*)pxw;
     d.fardir = (const double*)pfd;
     d.general = h.general ? 1 : 0;
-    d.nodex = px;
-    d.jinv = pj;
-    d.cellc = pc;
+    // general-mesh arrays: pointers at row 0 (a C-grid's mirrored rows before it)
+    const size_t g0 = (size_t)h.G * h.nt;
+    d.nodex = px ? (const char*)px + g0 * 2 * es : nullptr;
+    d.jinv = pj ? (const char*)pj + g0 * 4 * es : nullptr;
+    d.cellc = pc ? (const char*)pc + g0 * CELLC * es : nullptr;
+    d.cgrid = h.cgrid ? 1 : 0;
+    d.jc = h.jc;
+    d.fardirj = (const double*)pfj;
     return LBFSI_OK;
 }
 

@@ -30,10 +30,18 @@ struct TraceRange {
 // fardir, wall normals n0 and Simpson shares wall_geo.
 struct HostMesh {
     int nr = 0, nt = 0, N = 0, ntj = 0;
+    // node slots per field component: N, plus G mirrored rows below row 0 on
+    // a C-grid (row 0 starts at slot G nt)
+    int Nx = 0, G = 0;
     double xm = 0, ym = 0;
     bool general = false;
+    // C-grid: row-0 columns j < jc and j > nt-1-jc lie on the wake cut
+    bool cgrid = false;
+    int jc = 0;
     std::vector<double> r, e, n0, wall_geo, rowtab, coltab, xw, fardir, X, jinv, cellc;
+    std::vector<double> fardirj;   // C-grid: [nr][2][2] outward directions of the outlet columns
 };
+
 
 // Per-cell element coefficients of a general mesh: 8 entries per cell (a, b),
 // a in [0, nr-2], b in [0, nt-1], row-major: the bilinear map of the cell's
@@ -51,6 +59,12 @@ int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc,
 // (subparametric, positive Jacobian): wall geometry, far-field directions,
 // per-node inverse metric and per-cell element coefficients.
 int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, HostMesh& out);
+
+// The same for a C-grid given by its node coordinates X [nr][nt][2] (nt
+// odd, the first and last n_cut row-0 nodes on the wake cut, node j and
+// nt-1-j of row 0 one point for j <= n_cut): the arrays carry G mirrored
+// rows below row 0 (node (-k, j) = node (k, nt-1-j)).
+int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, double yc, HostMesh& out);
 
 // Check bodies against a mesh (dof range, blend radii, wall inside the rigid zone).
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n);

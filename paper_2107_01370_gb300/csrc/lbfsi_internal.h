@@ -68,9 +68,13 @@ struct StepMaps {
 
 enum StepMode : int { MODE_STREAM_ONLY = 0, MODE_COLLIDE_STREAM = 1, MODE_COLLIDE_ONLY = 2 };
 
+// Mirrored rows kept below row 0 of a C-grid (the +-4 staging halo).
+constexpr int CGRID_GHOST_ROWS = 4;
+
 // Geometry of one O-grid mesh shape, shared by every solve on it (device).
 struct MeshDev {
-    int nr, nt, N, ntj;
+    int nr, nt, N, ntj;            // N: node slots per field component (nr nt, plus the
+                                   // mirrored rows of a C-grid)
     double xm, ym;                 // mesh centre
     const double* r;               // [nr]
     const double* e;               // [nt][2]
@@ -88,6 +92,12 @@ struct MeshDev {
     const void* nodex;             // [N][2] node coordinates
     const void* jinv;              // [N][4] inverse metric (index derivatives -> d/dX, d/dY)
     const void* cellc;             // [(nr-1) nt][8] element coefficients per cell
+    // C-grid (general meshes only): the node, metric and cell arrays and every
+    // field component hold mirrored rows -4..-1 below row 0 (their pointers
+    // point at row 0); row-0 columns j < jc and j > nt-1-jc lie on the wake
+    // cut, columns 0 and nt-1 are outlets
+    int cgrid, jc;
+    const double* fardirj;         // [nr][2][2] outward directions of columns 0 and nt-1
 };
 
 // One solve (one body, one set of fields on one mesh).  Buffers are
@@ -135,6 +145,9 @@ struct StepArgs {
     int uorder;                    // uniform launch: CTA order, 0 = (tile column, tile row,
                                    // solve), 1 = (solve, tile column, tile row)
     int pf_dist;                   // uniform launch: L2 prefetch distance in CTAs (set by the launcher)
+    int stream_post;               // 1: stream from ppost (written by a collide-only launch of
+                                   // the same step) without colliding; the step with k == 0
+                                   // streams the initial state as always
     unsigned* status;
 };
 

@@ -105,6 +105,25 @@ template <typename R>
 __device__ __forceinline__ R d_col(const R* p) {
     return R(0.5) * (p[1] - p[-1]);
 }
+// The same stencils on a general mesh that may be a C-grid (cg): central
+// along i at row-0 nodes whose row below is the mirrored row across the cut
+// (across), one-sided along j at the outlet columns and, at the two copies of
+// the rear point, along the cut.  With cg == 0 and across == false they are
+// d_row and d_col.
+template <typename R>
+__device__ __forceinline__ R d_row_c(const R* p, int stride, int i, int nr, bool across) {
+    if (i == 0 && !across) return R(0.5) * (R(-3) * p[0] + R(4) * p[stride] - p[2 * stride]);
+    if (i == nr - 1) return R(0.5) * (R(3) * p[0] - R(4) * p[-stride] + p[-2 * stride]);
+    return R(0.5) * (p[stride] - p[-stride]);
+}
+template <typename R>
+__device__ __forceinline__ R d_col_c(const R* p, int i, int j, int nt, int jc, int cg) {
+    if (cg) {
+        if (j == 0 || (i == 0 && j == nt - 1 - jc)) return R(0.5) * (R(-3) * p[0] + R(4) * p[1] - p[2]);
+        if (j == nt - 1 || (i == 0 && j == jc)) return R(0.5) * (R(3) * p[0] - R(4) * p[-1] + p[-2]);
+    }
+    return R(0.5) * (p[1] - p[-1]);
+}
 
 template <typename R>
 __device__ __forceinline__ void lagrange3(R t, R* L) {
@@ -232,9 +251,12 @@ __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F0
 template <typename R, int TJ>
 __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int j, int i0, int j0,
                                            int nr, int pi0, int sj0, int PWS, R dx, R dy, int& base,
-                                           R& xi, R& eta) {
+                                           R& xi, R& eta, bool below = false) {
+    // below: the node has cells below row 0 (the mirrored cells across a
+    // C-grid's cut); otherwise a row-0 node only has the cells of row 0
     const R di = jn[0] * dx + jn[2] * dy, dj = jn[1] * dx + jn[3] * dy;
-    int da = (!(di < R(0)) || i == 0) ? 0 : -1;
+    const bool down = i > 0 || below;
+    int da = (!(di < R(0)) || !down) ? 0 : -1;
     int db = !(dj < R(0)) ? 0 : -1;
     // an element is taken when the point lies in it up to round-off (tin);
     // failing that, the first candidate within the CFL margin (lim), as for
@@ -282,7 +304,7 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
         }
         bool next = false;
         if (x > tin && da == -1) { da = 0; next = true; }
-        else if (x < -tin && da == 0 && i > 0) { da = -1; next = true; }
+        else if (x < -tin && da == 0 && down) { da = -1; next = true; }
         if (e > tin && db == -1) { db = 0; next = true; }
         else if (e < -tin && db == 0) { db = -1; next = true; }
         if (!next) break;
@@ -383,6 +405,27 @@ __device__ __forceinline__ R2 gather9(const R2* p, int rowstride, const double* 
     return acc;
 }
 
+// Q2 interpolation over a window whose last row is given (v20, v21, v22)
+// instead of read from the staged tile: the rear point's mirrored cell on a
+// C-grid, whose element's row 0 is the other side's (Eq. SemiLagrProp).
+template <typename R, typename R2>
+__device__ __forceinline__ R2 gather9_last(const R2* p, int rowstride, const R* Lx, const R* Ly, R2 v20,
+                                           R2 v21, R2 v22) {
+    R2 acc;
+    acc.x = R(0);
+    acc.y = R(0);
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+        const R2* pr = p + aa * rowstride;
+        const R2 u0 = aa == 2 ? v20 : pr[0], u1 = aa == 2 ? v21 : pr[1], u2 = aa == 2 ? v22 : pr[2];
+        const R tx = Ly[0] * u0.x + Ly[1] * u1.x + Ly[2] * u2.x;
+        const R ty = Ly[0] * u0.y + Ly[1] * u1.y + Ly[2] * u2.y;
+        acc.x += Lx[aa] * tx;
+        acc.y += Lx[aa] * ty;
+    }
+    return acc;
+}
+
 template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
@@ -436,11 +479,24 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         ctr = tg->counter;
         mptr = tg->maps;
     }
+    // C-grid (general meshes): rows from -4 are stored (the mirrored rows),
+    // the angular index does not wrap
+    int cg = 0, jc = 0;
+    if constexpr (GEN) {
+        cg = UNIFORM ? a.umesh.cgrid : mg->cgrid;
+        jc = UNIFORM ? a.umesh.jc : mg->jc;
+    }
+    const int rlo = cg ? -CGRID_GHOST_ROWS : 0;
     // a uniform launch from the host knows the step number; otherwise it is
     // the solve's device counter
     const unsigned kstep = (UNIFORM && a.ustep >= 0) ? (unsigned)a.ustep : __ldcg(ctr + 1);
     const int cur = (int)(kstep & 1u);
-    const int mode = a.collide_only ? MODE_COLLIDE_ONLY : (kstep == 0u ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM);
+    // general meshes: a stream-only launch after a collide-only one streams
+    // the collided state (the C-grid's two-launch step)
+    const bool split = GEN && a.stream_post;
+    const int mode = a.collide_only ? MODE_COLLIDE_ONLY
+                     : (kstep == 0u || split) ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM;
+    const bool from_post = split && kstep != 0u && !a.collide_only;
     {
         const StepMaps* mi = (cur ? mptr[1] : mptr[0]) + sb;
         if (!UNIFORM && w == 1) cp_async_words(&s_sol, sg, (int)(sizeof(SolveDev) / 4), l);
@@ -460,7 +516,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
 #define SD(x) (UNIFORM ? a.usol.x : s_sol.x)
 #define MD(x) (UNIFORM ? a.umesh.x : s_mesh.x)
     const size_t o9 = (size_t)sb * 9 * N, o4 = (size_t)sb * 4 * N;
-    const void* psrc = UNIFORM ? (cur ? a.usol.p[1] : a.usol.p[0]) : sg->p[cur];
+    const void* psrc = from_post ? (UNIFORM ? a.usol.ppost : sg->ppost)
+                                 : UNIFORM ? (cur ? a.usol.p[1] : a.usol.p[0]) : sg->p[cur];
     const void* Msrc = UNIFORM ? (cur ? a.usol.M[1] : a.usol.M[0]) : sg->M[cur];
     const R2* __restrict__ p_in = reinterpret_cast<const R2*>(psrc) + o9;
     const R* __restrict__ M_in = reinterpret_cast<const R*>(Msrc) + o4;
@@ -478,9 +535,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const R* gc = reinterpret_cast<const R*>(UNIFORM ? a.umesh.cellc : mg->cellc);
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
-            const int i = i0 - T::HD + li;
-            if (i < 0 || i >= nr) continue;
-            const size_t n = (size_t)i * nt + wrap_nt(j0 - T::HD + lj, nt);
+            const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
+            if (i < rlo || i >= nr || (cg && (unsigned)jj >= (unsigned)nt)) continue;
+            const ptrdiff_t n = (ptrdiff_t)i * nt + (cg ? jj : wrap_nt(jj, nt));
             if constexpr (sizeof(R) == 4) {
                 cp_async8(sX + 2 * idx, gx + 2 * n);
                 cp_async16(sJ + 4 * idx, gj + 4 * n);
@@ -494,9 +551,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int t = tid; t < (TI + 1) * (TJ + 1) * NCC; t += NT) {
             const int cell = t / NCC, ch = t - cell * NCC;
             const int la = cell / (TJ + 1), lb = cell - la * (TJ + 1);
-            const int ca = i0 - 1 + la;
-            if (ca < 0 || ca > nr - 2) continue;
-            const size_t g = ((size_t)ca * nt + wrap_nt(j0 - 1 + lb, nt)) * CELLC + ch * CE;
+            const int ca = i0 - 1 + la, cb = j0 - 1 + lb;
+            if (ca < (cg ? -1 : 0) || ca > nr - 2 || (cg && (unsigned)cb > (unsigned)(nt - 2))) continue;
+            const ptrdiff_t g = ((ptrdiff_t)ca * nt + (cg ? cb : wrap_nt(cb, nt))) * CELLC + ch * CE;
             cp_async16(sC + cell * CELLC + ch * CE, gc + g);
         }
     } else {
@@ -516,23 +573,26 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // components N apart
     {
         constexpr int CM = 16 / (int)sizeof(R), NCH = T::MW / CM;
-        const bool vec = nt % CM == 0;
+        const bool vec = nt % CM == 0 && !cg;
         for (int idx = tid; idx < T::MH * NCH; idx += NT) {
             const int ch = idx % NCH, li = idx / NCH;
             const int i = mi0 + li;
-            if (i < 0 || i >= nr) continue;
+            if (i < rlo || i >= nr) continue;
             R* dst = sM + li * T::MW + ch * CM;
-            const R* src = M_in + (size_t)i * nt;
+            const R* src = M_in + (ptrdiff_t)i * nt;
             if (vec) {
                 src += wrap_nt(mj0 + ch * CM, nt);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) cp_async16(dst + c * T::MS, src + (size_t)c * N);
             } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
+                for (int e = 0; e < CM; ++e) {
+                    const int jj = mj0 + ch * CM + e;
+                    if (cg && (unsigned)jj >= (unsigned)nt) continue;
 #pragma unroll
-                    for (int e = 0; e < CM; ++e)
-                        cp_async(dst + c * T::MS + e, src + (size_t)c * N + wrap_nt(mj0 + ch * CM + e, nt));
+                    for (int c = 0; c < 4; ++c)
+                        cp_async(dst + c * T::MS + e, src + (size_t)c * N + (cg ? jj : wrap_nt(jj, nt)));
+                }
             }
         }
     }
@@ -541,13 +601,13 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // nine directions N apart
     {
         constexpr int CP = 16 / (int)sizeof(R2), NCH = T::PWS / CP;
-        const bool vec = nt % CP == 0;
+        const bool vec = nt % CP == 0 && !cg;
         for (int idx = tid; idx < T::PH * NCH; idx += NT) {
             const int ch = idx % NCH, li = idx / NCH;
             const int i = pi0 + li;
-            if (i < 0 || i >= nr) continue;
+            if (i < rlo || i >= nr) continue;
             R2* dst = sp + li * T::PWS + ch * CP;
-            const R2* src = p_in + (size_t)i * nt;
+            const R2* src = p_in + (ptrdiff_t)i * nt;
             if (vec) {
                 src += wrap_nt(sj0 + ch * CP, nt);
 #pragma unroll
@@ -555,9 +615,16 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             } else {
 #pragma unroll
                 for (int e = 0; e < CP; ++e) {
-                    const R2* se = src + wrap_nt(sj0 + ch * CP + e, nt);
+                    const int jj = sj0 + ch * CP + e;
+                    if (cg && (unsigned)jj >= (unsigned)nt) continue;
+                    const R2* se = src + (cg ? jj : wrap_nt(jj, nt));
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) cp_async8(dst + q * T::PSS + e, se + (size_t)q * N);
+                    for (int q = 0; q < 9; ++q) {
+                        if constexpr (sizeof(R2) == 16)
+                            cp_async16(dst + q * T::PSS + e, se + (size_t)q * N);
+                        else
+                            cp_async8(dst + q * T::PSS + e, se + (size_t)q * N);
+                    }
                 }
             }
         }
@@ -620,7 +687,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     if (collide) {
         for (int idx = tid; idx < T::MS; idx += NT) {
             const int i = mi0 + idx / T::MW;
-            if (i < 0 || i >= nr) continue;
+            if (i < rlo || i >= nr) continue;
+            if (cg && (unsigned)(mj0 + idx % T::MW) >= (unsigned)nt) continue;
             const R rho = sM[idx], ux = sM[T::MS + idx], uy = sM[2 * T::MS + idx], Tn = sM[3 * T::MS + idx];
             sQ[idx] = rho * ux * (R(1) - R(3) * Tn) - rho * ux * ux * ux;
             sQ[T::MS + idx] = rho * uy * (R(1) - R(3) * Tn) - rho * uy * uy * uy;
@@ -629,7 +697,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
-            if (i < 0 || i >= nr) continue;
+            if (i < rlo || i >= nr) continue;
+            if (cg && (unsigned)(j0 - T::HD + lj) >= (unsigned)nt) continue;
             R F00, F01, F10, F11, vx, vy;
             R G[4];
             if constexpr (GEN) {
@@ -661,23 +730,36 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         __syncthreads();
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
-            const int i = i0 - T::HD + li;
-            if (i < 0 || i >= nr) continue;
+            const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
+            if (i < rlo || i >= nr) continue;
+            if (cg && (unsigned)jj >= (unsigned)nt) continue;
             const int m = (li + 1) * T::MW + (lj + 1);
             const R mup = mu * rcp_(sM[m] * sM[3 * T::MS + m]);
-            const R qx_xi = d_row(sQ + m, T::MW, i, nr), qx_et = d_col(sQ + m);
-            const R qy_xi = d_row(sQ + T::MS + m, T::MW, i, nr), qy_et = d_col(sQ + T::MS + m);
+            R qx_xi, qx_et, qy_xi, qy_et;
+            if constexpr (GEN) {
+                const bool across = cg && i == 0 && (jj <= jc || jj >= nt - 1 - jc);
+                qx_xi = d_row_c(sQ + m, T::MW, i, nr, across);
+                qx_et = d_col_c(sQ + m, i, jj, nt, jc, cg);
+                qy_xi = d_row_c(sQ + T::MS + m, T::MW, i, nr, across);
+                qy_et = d_col_c(sQ + T::MS + m, i, jj, nt, jc, cg);
+            } else {
+                qx_xi = d_row(sQ + m, T::MW, i, nr);
+                qx_et = d_col(sQ + m);
+                qy_xi = d_row(sQ + T::MS + m, T::MW, i, nr);
+                qy_et = d_col(sQ + T::MS + m);
+            }
             sD[idx] = mup * (sG[idx] * qx_xi + sG[T::DS + idx] * qx_et);
             sD[T::DS + idx] = mup * (sG[2 * T::DS + idx] * qy_xi + sG[3 * T::DS + idx] * qy_et);
         }
         __syncthreads();
         for (int idx = tid; idx < T::PS; idx += NT) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
-            const int i = pi0 + li;
+            const int i = pi0 + li, jj = j0 - T::HP + lj;
             if (i < 0 || i >= nr) continue;
+            if (cg && (unsigned)jj >= (unsigned)nt) continue;
             const int sn = li * T::PWS + lj + 2;   // staged node
             R f[9], g[9];
-            if (i == nr - 1) {
+            if (i == nr - 1 || (cg && (jj == 0 || jj == nt - 1))) {
                 const int m = (li + 2) * T::MW + (lj + 2);
                 f_equilibrium(sM[m], sM[T::MS + m], sM[2 * T::MS + m], sM[3 * T::MS + m], f);
                 g_equilibrium(sM[m], sM[T::MS + m], sM[2 * T::MS + m], sM[3 * T::MS + m], Cv, g);
@@ -689,8 +771,19 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                     g[q] = v.y;
                 }
                 const int d = (li + 1) * T::DW + (lj + 1);
-                const R dx_xi = d_row(sD + d, T::DW, i, nr), dx_et = d_col(sD + d);
-                const R dy_xi = d_row(sD + T::DS + d, T::DW, i, nr), dy_et = d_col(sD + T::DS + d);
+                R dx_xi, dx_et, dy_xi, dy_et;
+                if constexpr (GEN) {
+                    const bool across = cg && i == 0 && (jj <= jc || jj >= nt - 1 - jc);
+                    dx_xi = d_row_c(sD + d, T::DW, i, nr, across);
+                    dx_et = d_col_c(sD + d, i, jj, nt, jc, cg);
+                    dy_xi = d_row_c(sD + T::DS + d, T::DW, i, nr, across);
+                    dy_et = d_col_c(sD + T::DS + d, i, jj, nt, jc, cg);
+                } else {
+                    dx_xi = d_row(sD + d, T::DW, i, nr);
+                    dx_et = d_col(sD + d);
+                    dy_xi = d_row(sD + T::DS + d, T::DW, i, nr);
+                    dy_et = d_col(sD + T::DS + d);
+                }
                 const R Yx = sG[d] * dx_xi + sG[T::DS + d] * dx_et;
                 const R Yy = sG[2 * T::DS + d] * dy_xi + sG[3 * T::DS + d] * dy_et;
                 collide_node(f, g, Yx, Yy, mu, dt, Cv, iPr);
@@ -712,8 +805,18 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 if (i < nr && j < nt) {
                     const int n = i * nt + j;
                     const int sn = (ti + T::HP) * T::PWS + tj + T::HP + 2;
+                    // C-grid: the first copy of a cut node also writes the
+                    // second (which writes nothing), rows 1 and 2 their
+                    // mirrored slots (the next stream's rows below row 0)
+                    if (cg && i == 0 && j >= nt - 1 - jc) continue;
+                    const bool two = cg && ((i == 0 && j <= jc) || i == 1 || i == 2);
+                    const int n2 = i == 0 ? nt - 1 - j : -i * nt + (nt - 1 - j);
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) p_out[(size_t)q * N + n] = sp[q * T::PSS + sn];
+                    for (int q = 0; q < 9; ++q) {
+                        const R2 v = sp[q * T::PSS + sn];
+                        p_out[(ptrdiff_t)q * N + n] = v;
+                        if (two) p_out[(ptrdiff_t)q * N + n2] = v;
+                    }
                 }
             }
             return;
@@ -728,14 +831,32 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const int ti = t / TJ, tj = t - (t / TJ) * TJ;
         const int i = i0 + ti, j = j0 + tj;
         if (i >= nr || j >= nt) continue;
+        // C-grid: the second copies of the row-0 cut nodes (and of the rear
+        // point) are written by their first copies; rows 1-4 also write
+        // their moments into their mirrored slots below row 0
+        if (cg && i == 0 && j >= nt - 1 - jc) continue;
+        const bool dup2 = cg && i == 0 && j <= jc;
+        const bool mir = cg && i >= 1 && i <= CGRID_GHOST_ROWS;
+        const int n2 = i == 0 ? nt - 1 - j : -i * nt + (nt - 1 - j);
         const int n = i * nt + j;
         const int m = (ti + T::HM) * T::MW + tj + T::HM;   // node in M coords
         const R* row = srow + (ti + T::HM) * RS;
         const R* col = scol + (tj + T::HM) * CS;
-        if (i == nr - 1) {
+        const bool farj = cg && i < nr - 1 && (j == 0 || j == nt - 1);
+        if (i == nr - 1 || farj) {
             // far field (Sec. III A 2): inlet where the free stream enters,
-            // zero-gradient outlet elsewhere (targets of the previous step)
-            const double un = SD(uinf_x) * MD(fardir)[2 * j] + SD(uinf_y) * MD(fardir)[2 * j + 1];
+            // zero-gradient outlet elsewhere (targets of the previous step);
+            // on a C-grid also the outlet columns, inner neighbour along j
+            double un;
+            int mm;
+            if (farj) {
+                const double* fd = MD(fardirj) + 4 * i + (j == 0 ? 0 : 2);
+                un = SD(uinf_x) * fd[0] + SD(uinf_y) * fd[1];
+                mm = m + (j == 0 ? 1 : -1);
+            } else {
+                un = SD(uinf_x) * MD(fardir)[2 * j] + SD(uinf_y) * MD(fardir)[2 * j + 1];
+                mm = m - T::MW;
+            }
             R rho, ux, uy, Tt;
             if (un < 0.0) {
                 rho = pick<R>(SD(rho_inf), SD(rho_inf_f));
@@ -743,7 +864,6 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 uy = pick<R>(SD(uinf_y), SD(uinf_y_f));
                 Tt = pick<R>(SD(T_inf), SD(T_inf_f));
             } else {
-                const int mm = m - T::MW;
                 rho = sM[mm]; ux = sM[T::MS + mm]; uy = sM[2 * T::MS + mm]; Tt = sM[3 * T::MS + mm];
             }
             R f[9], g[9];
@@ -755,11 +875,21 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 v.x = f[q];
                 v.y = g[q];
                 p_out[(size_t)q * N + n] = v;
+                if (dup2) p_out[(ptrdiff_t)q * N + n2] = v;
             }
             M_out[n] = rho; M_out[(size_t)N + n] = ux; M_out[(size_t)2 * N + n] = uy;
             M_out[(size_t)3 * N + n] = Tt;
+            if (dup2 || mir) {
+                M_out[n2] = rho; M_out[(ptrdiff_t)N + n2] = ux; M_out[(ptrdiff_t)2 * N + n2] = uy;
+                M_out[(ptrdiff_t)3 * N + n2] = Tt;
+            }
             continue;
         }
+        const bool wall = i == 0 && (!cg || j >= jc);
+        // the rear point of a C-grid: its mirrored cell next to the wall has
+        // the other side's wall nodes as its element's row 0
+        const bool rear = cg && i == 0 && j == jc;
+        const int rbase = (-2 - pi0) * T::PWS + (jc - sj0);
         NodeGeo<R> geo;
         R F00, F01, F10, F11, vx, vy;
         bool moved;
@@ -778,7 +908,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const R idF = rcp_(F00 * F11 - F01 * F10);
         const R i00 = F11 * idF, i01 = -F01 * idF, i10 = -F10 * idF, i11 = F00 * idF;
         unsigned missing = 0u;
-        if (i == 0) {
+        if (wall) {
             // missing populations: departure point inside the body,
             // c_hat . n0 > 0, decided in float64 (Sec. III A)
             const double Xd = MD(xw)[2 * j], Yd = MD(xw)[2 * j + 1];
@@ -800,7 +930,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // departure solve of this node for a displacement (dx, dy)
         auto departure = [&](int inode, R dx, R dy, int& base, R& xi, R& eta) -> bool {
             if constexpr (GEN)
-                return depart_gen<R, TJ>(sC, sJ + 4 * dn, inode, j, i0, j0, nr, pi0, sj0, T::PWS, dx, dy, base, xi, eta);
+                return depart_gen<R, TJ>(sC, sJ + 4 * dn, inode, j, i0, j0, nr, pi0, sj0, T::PWS, dx, dy, base, xi, eta,
+                                         dup2);
             else
                 return depart(geo, inode, dx, dy, base, xi, eta);
         };
@@ -853,7 +984,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R Lx[3], Ly[3];
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
-                const R2 v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
+                R2 v;
+                if (GEN && rear && base == rbase)
+                    v = gather9_last(sp + q * T::PSS + base, T::PWS, Lx, Ly, sp[q * T::PSS + base + 2 * T::PWS],
+                                     p_in[(size_t)q * N + (nt - 2 - jc)], p_in[(size_t)q * N + (nt - 3 - jc)]);
+                else
+                    v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
                 f[q] = v.x;
                 g[q] = v.y;
             } else {
@@ -880,13 +1016,16 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int w0 = (wa - mi0) * T::MW + (wb - mj0);
                 rhoB = R(0);
                 TB = R(0);
+                const bool other = GEN && rear && base == rbase;   // row 0 from the other side
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
                     for (int bb = 0; bb < 3; ++bb) {
                         const R wgt = Lx[aa] * Ly[bb];
-                        rhoB += wgt * sM[w0 + aa * T::MW + bb];
-                        TB += wgt * sM[3 * T::MS + w0 + aa * T::MW + bb];
+                        const bool far = other && aa == 2 && bb > 0;
+                        const int c2 = nt - 1 - jc - bb;
+                        rhoB += wgt * (far ? M_in[c2] : sM[w0 + aa * T::MW + bb]);
+                        TB += wgt * (far ? M_in[(size_t)3 * N + c2] : sM[3 * T::MS + w0 + aa * T::MW + bb]);
                     }
             } else {
                 atomicOr(a.status, ST_BPOINT);
@@ -903,7 +1042,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const R* p = sM + (c + 1) * T::MS + m;
-                const R cxi = d_row(p, T::MW, 0, nr), cet = d_col(p);
+                R cxi, cet;
+                if constexpr (GEN) {
+                    cxi = d_row_c(p, T::MW, 0, nr, rear);
+                    cet = d_col_c(p, 0, j, nt, jc, cg);
+                } else {
+                    cxi = d_row(p, T::MW, 0, nr);
+                    cet = d_col(p);
+                }
                 gr[c][0] = G[0] * cxi + G[1] * cet;
                 gr[c][1] = G[2] * cxi + G[3] * cet;
             }
@@ -927,10 +1073,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             v.x = f[q];
             v.y = g[q];
             p_out[(size_t)q * N + n] = v;
+            if (dup2) p_out[(ptrdiff_t)q * N + n2] = v;
         }
         M_out[n] = mc.rho; M_out[(size_t)N + n] = mc.ux; M_out[(size_t)2 * N + n] = mc.uy;
         M_out[(size_t)3 * N + n] = mc.T;
-        if (i == 0) {
+        if (dup2 || mir) {
+            M_out[n2] = mc.rho; M_out[(ptrdiff_t)N + n2] = mc.ux; M_out[(ptrdiff_t)2 * N + n2] = mc.uy;
+            M_out[(ptrdiff_t)3 * N + n2] = mc.T;
+        }
+        if (wall) {
             // wall stress sigma = -p I - (1 - omega/2) P^(1), P^(1) = sum (f - f^eq) c c
             // (Sec. III), this node's Simpson share of its edges, float64
             R feq[9];

@@ -31,7 +31,8 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_set_schedule", "lbfsi_get_schedule", "lbfsi_set_graph_steps", "lbfsi_autotune",
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
-            "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy"]
+            "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy",
+            "lbfsi_create_mesh_cgrid"]
 
 
 class LbfsiError(RuntimeError):
@@ -64,6 +65,13 @@ class MeshDesc(ctypes.Structure):
 
 class MeshXYDesc(ctypes.Structure):
     _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("X", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
+                ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class MeshCGridDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("n_cut", ctypes.c_int),
                 ("X", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
@@ -221,6 +229,29 @@ class Mesh:
         h = ctypes.c_void_p()
         self.h = None
         _check(lib.lbfsi_create_mesh_xy(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        return self
+
+    @classmethod
+    def cgrid(cls, X, n_cut, bodies, precision=FP64, centre=(0.0, 0.0), stream=None):
+        """Handle of a C-grid given by node coordinates X [nr, ntheta, 2]
+        (ntheta odd) whose first and last n_cut row-0 nodes lie on the wake
+        cut (lbfsi_create_mesh_cgrid)."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.r = self.e = None
+        self.nr, self.nt = self.X.shape[0], self.X.shape[1]
+        self.N = self.nr * self.nt
+        self.nbatch = len(bodies)
+        self.precision = precision
+        self._bodies = (BodyDesc * self.nbatch)(*[body_desc(b) for b in bodies])
+        d = MeshCGridDesc(self.nr, self.nt, int(n_cut), _dptr(self.X), centre[0], centre[1], precision,
+                          self.nbatch, self._bodies)
+        h = ctypes.c_void_p()
+        self.h = None
+        _check(lib.lbfsi_create_mesh_cgrid(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
         self.h = h
         return self
 

@@ -118,3 +118,44 @@ def test_general_mesh_validation_without_gpu(lib):
     nan = X.copy()
     nan[0, 0, 0] = np.nan
     assert create(nan) == lbfsi.EINVAL
+
+
+def test_cgrid_struct_layout_and_validation_without_gpu(tmp_path, lib):
+    """lbfsi_mesh_cgrid_desc matches the binding; lbfsi_create_mesh_cgrid
+    rejects, before touching the device, cut nodes that do not coincide, an
+    even node count along the C, an odd or too long cut, and a mesh that is
+    not subparametric."""
+    import numpy as np
+    from paper_2107_01370_gb300 import inputs, lbfsi
+    src = tmp_path / "cg.c"
+    src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lbfsi_mesh_cgrid_desc),'
+                   'offsetof(lbfsi_mesh_cgrid_desc, X), offsetof(lbfsi_mesh_cgrid_desc, xc),'
+                   'offsetof(lbfsi_mesh_cgrid_desc, bodies));return 0;}\n')
+    exe = tmp_path / "cg"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(lbfsi.MeshCGridDesc), lbfsi.MeshCGridDesc.X.offset,
+                   lbfsi.MeshCGridDesc.xc.offset, lbfsi.MeshCGridDesc.bodies.offset]
+    X = inputs.cgrid_ellipse(17, 4, 9, 0.6, 0.35, r_far=4.0, wake=3.0)
+    body = lbfsi.BodyDesc()
+    h = ctypes.c_void_p()
+
+    def create(Xa, n_cut):
+        Xa = np.ascontiguousarray(Xa)
+        d = lbfsi.MeshCGridDesc(Xa.shape[0], Xa.shape[1], n_cut,
+                                Xa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0.0, 0.0, 0, 1,
+                                ctypes.pointer(body))
+        return lib.lbfsi_create_mesh_cgrid(ctypes.byref(d), None, ctypes.byref(h))
+
+    bad = X.copy()
+    bad[0, 1, 1] += 1e-3                   # an upper cut node off the lower one
+    assert create(bad, 4) == lbfsi.EINVAL
+    assert b"coincide" in lib.lbfsi_last_error()
+    assert create(X[:, :-1], 4) == lbfsi.EINVAL
+    assert create(X, 3) == lbfsi.EINVAL
+    assert create(X, 8) == lbfsi.EINVAL     # leaves no wall
+    bad = X.copy()
+    bad[3, 9] += 1e-3
+    assert create(bad, 4) == lbfsi.EINVAL
+    assert b"subparametric" in lib.lbfsi_last_error()

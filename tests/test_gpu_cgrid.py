@@ -1,0 +1,157 @@
+"""Parity of the C-grid path (a wake cut with mirrored cells across it,
+outlet columns, an open wall chain; readings R28-R30) with the FP64 oracle on
+the same meshes and seeded inputs: an elliptic section fixed, in 1-DOF
+plunge, in 2-DOF pitch-plunge with rotation, and across the switch from forced
+to free pitching.  A C-grid step is two launches (collision into a
+post-collision buffer, then the stream from it); graph replay and
+checkpoint / resume keep it bit for bit.  Tolerances as in test_gpu_parity."""
+import numpy as np
+import pytest
+
+import oracle.mesh as OM
+import oracle.solver as OS
+from paper_2107_01370_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+P_SCALE = 1.0 / 3.0   # p_inf * length
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2107_01370_gb300 import build, lbfsi
+    build.build()
+    lbfsi.load()
+    return lbfsi
+
+
+def field_err(a, b):
+    e_rho = np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()
+    e_u = np.hypot(a[1] - b[1], a[2] - b[2]).max() / np.hypot(b[1], b[2]).max()
+    e_T = np.abs(a[3] - b[3]).max() / np.abs(b[3]).max()
+    return max(e_rho, e_u, e_T)
+
+
+def to_tuple(d):
+    return (d["h"], d["alpha"], d["hdot"], d["adot"])
+
+
+def run_both(L, case, M0, steps, precision, state=None, prev=None):
+    s = OS.Solver.from_case(OM.CGridMesh(case.X, case.n_cut), case, M0)
+    if state is not None:
+        s.S = [dict(state)]
+        s.S_prev = [dict(prev if prev is not None else state)]
+    hist = []
+    for _ in range(steps):
+        r = s.step()
+        hist.append(r.force)
+    m = L.Mesh.cgrid(case.X, case.n_cut, case.bodies, precision=precision, centre=case.centre)
+    m.init_fields(case.flow, M0[None])
+    if state is not None:
+        m.blend_mesh([to_tuple(state)], None if prev is None else [to_tuple(prev)])
+    ghist = []
+    for _ in range(steps):
+        m.step(1)
+        ghist.append(m.body_forces()[0].copy())
+    out = (m.get_fields()[0], np.array(ghist), m.body_state()[0])
+    m.close()
+    return s, r, np.array(hist), out
+
+
+def _case(body, n_wall=49, n_cut=8, nr=32, **kw):
+    return inputs.cgrid_case(n_wall, n_cut, nr, 0.6, 0.35, r_far=6.0, wake=4.0, length=1.2, body=body, **kw)
+
+
+BODIES = {
+    0: (inputs.BodySpec(dof=0), None, None),
+    1: (inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=2.0, v_r=4.0, length=1.2),
+        {"h": 0.02, "alpha": 0.0, "hdot": 0.004, "adot": 0.0},
+        {"h": 0.0199, "alpha": 0.0, "hdot": 0.004, "adot": 0.0}),
+    2: (inputs.BodySpec(dof=2, xp=-0.2, yp=0.0, r_in=0.75, r_out=2.0, m_star=5.0, v_r=2.0,
+                        x_alpha=0.3, r_alpha=0.6, wh_wa=0.5, length=1.2),
+        {"h": -0.01, "alpha": 0.03, "hdot": 0.0, "adot": 0.01},
+        {"h": -0.0101, "alpha": 0.0299, "hdot": 0.0, "adot": 0.01}),
+}
+
+
+@pytest.mark.parametrize("dof", [0, 1, 2])
+def test_fp64_cgrid_matches_oracle(L, dof):
+    body, state, prev = BODIES[dof]
+    case = _case(body)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=31 + dof)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 10, L.FP64, state, prev)
+    assert field_err(f, r.M) < 1e-12
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+    for k in ("h", "alpha", "hdot", "adot"):
+        assert abs(st[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+    # the second copies of the cut nodes hold the first copies' values
+    jc, nt = case.n_cut, case.ntheta
+    assert np.array_equal(f[:, 0, nt - 1 - jc:], f[:, 0, :jc + 1][:, ::-1])
+
+
+def test_fp64_cgrid_forced_then_free_pitching_matches_oracle(L):
+    base = inputs.BodySpec(dof=2, xp=-0.25, yp=0.0, r_in=0.75, r_out=2.0, m_star=8.0, v_r=1.2,
+                           x_alpha=0.2, r_alpha=0.5, wh_wa=0.4, length=1.2)
+    case = _case(base)
+    u_inf = case.flow.ma * np.sqrt(case.flow.gamma * case.flow.t_inf)
+    w_a = u_inf / (base.v_r * 0.6 * np.sqrt(base.m_star))
+    base.pitch_amp = 0.2
+    base.forced_periods = 5.5 * case.flow.dt * w_a / (2.0 * np.pi)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=41)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 10, L.FP64)
+    assert field_err(f, r.M) < 1e-12
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+    for k in ("h", "alpha", "hdot", "adot"):
+        assert abs(st[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+
+
+def test_fp32_cgrid_within_stated_tolerance(L):
+    body, state, prev = BODIES[1]
+    case = _case(body)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=43)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 40, L.FP32, state, prev)
+    assert field_err(f, r.M) < 1e-5
+    assert np.abs(ghist - hist).max() < 1e-4 * P_SCALE
+
+
+def _state(m):
+    return m.get_fields(), m.body_forces(), m.body_state()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_cgrid_graph_replay_and_resume_are_bit_identical(L, precision):
+    prec = L.FP32 if precision == "fp32" else L.FP64
+    body = BODIES[2][0]
+    case = _case(body)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=47)
+    M2 = np.ascontiguousarray(np.broadcast_to(M0, (2,) + M0.shape))
+
+    def fresh():
+        m = L.Mesh.cgrid(case.X, case.n_cut, case.bodies * 2, precision=prec)
+        m.init_fields(case.flow, M2)
+        return m
+
+    a = fresh()
+    a.step(9)
+    ckpt = a.checkpoint()
+    a.step(14)
+    ref = _state(a)
+    n_launch = a.launch_count()
+    a.close()
+    b = fresh()
+    b.set_graph_steps(4)
+    b.step(23)
+    got = _state(b)
+    b.close()
+    for x, y in zip(ref[:2], got[:2]):
+        assert np.array_equal(x, y)
+    assert ref[2] == got[2]
+    c = fresh()
+    c.restore(ckpt)
+    c.step(14)
+    got = _state(c)
+    c.close()
+    for x, y in zip(ref[:2], got[:2]):
+        assert np.array_equal(x, y)
+    assert ref[2] == got[2]
+    assert n_launch >= 2 * 23
