@@ -330,6 +330,69 @@ def small_case_graphs(stream, steps=1000, graph_steps=100):
     return res
 
 
+def general_mesh_cases():
+    """Two general-mesh workloads (FP32, batch 8 per mesh, inputs above L2):
+    an elliptic cylinder on a 512 x 256 O-grid given by node coordinates
+    (1-DOF), and the airfoil-case shape: a 12%-thick elliptic section on a
+    192 x 769 C-grid (147,648 nodes, wake cut 128 nodes per side), 2-DOF
+    pitch-plunge (m* 100, w_h/w_a 0.3, x_a 1.8, r_a 1.87, V_R 0.5025, elastic
+    axis half a chord ahead of the leading edge), Ma 0.8, T_inf 0.2, Re 1e5,
+    1 degree forced pitching for two periods then free."""
+    from paper_2107_01370_gb300 import lbfsi
+    ell = inputs.xy_case(inputs.ellipse_wall(256, 0.6, 0.35), 512, r_far=20.0, length=1.2,
+                         body=inputs.BodySpec(dof=1, r_in=0.75, r_out=2.5, m_star=10.0, v_r=5.0,
+                                              length=1.2),
+                         name="elliptic cylinder (0.6 x 0.35) O-grid 512x256 by node coordinates, 1-DOF")
+    body = inputs.BodySpec(dof=2, xp=-1.0, yp=0.0, r_in=0.6, r_out=2.0, m_star=100.0, v_r=0.5025,
+                           x_alpha=1.8, r_alpha=1.87, wh_wa=0.3, length=1.0,
+                           pitch_amp=math.pi / 180.0, forced_periods=2.0)
+    cg = inputs.cgrid_case(513, 128, 192, 0.5, 0.06, r_far=10.0, wake=10.0, length=1.0, ma=0.8,
+                           t_inf=0.2, re=1e5, body=body,
+                           name="12% elliptic section C-grid 192x769 (cut 128), 2-DOF, Ma 0.8, forced pitch")
+    return ((ell, lambda prec, nb, st: lbfsi.Mesh.xy(ell.X, ell.bodies * nb, precision=prec, stream=st)),
+            (cg, lambda prec, nb, st: lbfsi.Mesh.cgrid(cg.X, cg.n_cut, cg.bodies * nb, precision=prec,
+                                                       stream=st)))
+
+
+def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8):
+    """MLUPS of the general-mesh step (Newton departure points, stored
+    metric) on the two workloads of general_mesh_cases, timed with CUDA events
+    on the library's stream; the C-grid step is two launches (collision, then
+    stream).  HBM fraction against the algorithmic 144 B per node update."""
+    import torch
+    from paper_2107_01370_gb300 import lbfsi
+    out = []
+    for case, make in general_mesh_cases():
+        M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
+        m = make(lbfsi.FP32, batch, stream.cuda_stream)
+        m.init_fields(case.flow, np.ascontiguousarray(np.broadcast_to(M0, (batch,) + M0.shape)))
+        m.step(warmup)
+        m.synchronize()
+        ls = m.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ok = True
+        try:
+            m.synchronize()
+        except lbfsi.LbfsiError as e:
+            ok = str(e)
+        launches = m.launch_count() - ls
+        m.close()
+        nodes = case.nodes * batch
+        gbs = BYTES_PER_NODE_FP32 * nodes * steps / (ms * 1e-3) / 1e9
+        out.append({"workload": case.name, "nodes": case.nodes, "batch": batch, "steps": steps,
+                    "launches_per_step": launches // steps, "ms_per_step": round(ms / steps, 4),
+                    "MLUPS": round(nodes * steps / ms / 1e3, 1),
+                    "hbm_frac_of_measured": round(gbs / peak, 4), "physical": ok})
+    return out
+
+
 def issue_roofline(nodes, kernel_s, sm_mhz):
     """Instruction-issue ceiling of the step kernel: warp instructions per
     node from the committed ncu capture (current source only) against one
@@ -532,10 +595,11 @@ def main():
         m2.close()
         del fields
 
-    sweep = small = None
+    sweep = small = general = None
     if not args.no_sweep and world == 1:
         sweep = roofline_sweep(stream, (variant, order), peak)
         small = small_case_graphs(stream)
+        general = general_mesh_throughput(stream, peak)
     issue = issue_roofline(nodes, kavg_s, clocks.get("sm_mhz") or 2070.0) if clocks else None
 
     serving_out = None
@@ -560,6 +624,7 @@ def main():
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "serving": serving_out,
                "issue_roofline": issue, "roofline_sweep": sweep, "small_case": small,
+               "general_meshes": general,
                "solves_per_s": round(B * world / (case.steps * region_ms / args.steps * 1e-3), 4)}
         print(json.dumps(out), flush=True)
     mesh.close()
