@@ -331,6 +331,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async(float* dst, const float* src) { cp_async4(dst, src); }
 __device__ __forceinline__ void cp_async(double* dst, const double* src) { cp_async8(dst, src); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -596,6 +602,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
         }
     }
+    // the copies so far (records, maps, geometry, M^k) form the first group:
+    // the correction fields need only them and start while the populations
+    // (the second group) are still arriving
+    cp_async_commit();
     // populations: rows of PWS (f, g) pairs per direction in 16-byte chunks
     // (two float pairs or one double pair); one thread per (row, chunk), the
     // nine directions N apart
@@ -654,7 +664,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
         }
     }
-    cp_async_wait_all();
+    cp_async_commit();
+    cp_async_wait_group<1>();
     __syncthreads();
     R2* __restrict__ p_out = reinterpret_cast<R2*>(mode == MODE_COLLIDE_ONLY ? SD(ppost) : SD(p[cur ^ 1])) + o9;
     R* __restrict__ M_out = reinterpret_cast<R*>(SD(M[cur ^ 1])) + o4;
@@ -751,6 +762,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             sD[idx] = mup * (sG[idx] * qx_xi + sG[T::DS + idx] * qx_et);
             sD[T::DS + idx] = mup * (sG[2 * T::DS + idx] * qy_xi + sG[3 * T::DS + idx] * qy_et);
         }
+        cp_async_wait_all();   // the populations
         __syncthreads();
         for (int idx = tid; idx < T::PS; idx += NT) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
@@ -824,6 +836,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     }
 
     // ---- phase 3: stream step k+1 ----------------------------------------
+    if (!collide) {
+        cp_async_wait_all();   // the populations
+        __syncthreads();
+    }
     double fcx = 0.0, fcy = 0.0, fcm = 0.0;   // this thread's wall share (node row 0)
 #pragma unroll 1
     for (int k = 0; k < NPT; ++k) {
