@@ -341,6 +341,24 @@ typedef struct {
  * the tiles of the separable-mesh solves only. */
 int lbfsi_batch_add_xy(lbfsi_batch b, const lbfsi_solve_xy_desc* d, int* slot);
 
+/* One solve on a C-grid (as in lbfsi_mesh_cgrid_desc: X [nr][ntheta][2]
+ * host, borrowed for the call, n_cut cut nodes per side), with its body,
+ * flow, initial field and step count as in lbfsi_solve_desc. */
+typedef struct {
+    int nr, ntheta, n_cut;
+    const double* X;
+    double xc, yc;
+    lbfsi_body_desc body;
+    lbfsi_flow_params flow;
+    const double* rho_u_T;
+    int steps;
+} lbfsi_solve_cgrid_desc;
+
+/* Admit a solve on a C-grid (same contract as lbfsi_batch_add).  Its tiles
+ * form a third part of every lbfsi_batch_step: a collide-only launch, then
+ * the stream launch from its output. */
+int lbfsi_batch_add_cgrid(lbfsi_batch b, const lbfsi_solve_cgrid_desc* d, int* slot);
+
 /* Advance every active solve by up to nsteps coupled steps (one launch per
  * step covering all active solves; a solve stops when it reaches its step
  * count).  *active_after (nullable) receives the number of unfinished solves.

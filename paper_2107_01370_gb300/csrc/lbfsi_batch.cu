@@ -102,6 +102,7 @@ struct MeshEntry {
 struct Slot {
     bool used = false, finished = false;
     bool general = false;   // on a mesh given by node coordinates (GEN kernel, 8-row tiles)
+    bool cgrid = false;     // on a C-grid (general; two launches per step)
     int mesh = -1;
     int steps_target = 0, steps_done = 0;
     int ntiles = 0;
@@ -128,6 +129,7 @@ struct lbfsi_batch_s {
     double* d_zero_loads = nullptr;
     int ntiles = 0;    // separable-mesh tiles of the table (first part)
     int ngtiles = 0;   // general-mesh tiles (second part)
+    int nctiles = 0;   // C-grid tiles (third part)
     bool dirty = true;
     // CUDA graph of graph_steps launches over the current tile table,
     // captured on a private stream, dropped whenever the table changes
@@ -149,8 +151,14 @@ bool same_mesh(const lbfsi::HostMesh& h, const lbfsi_solve_desc& d) {
 }
 
 bool same_mesh_xy(const lbfsi::HostMesh& h, const lbfsi_solve_xy_desc& d) {
-    return h.general && h.nr == d.nr && h.nt == d.ntheta && h.xm == d.xc && h.ym == d.yc &&
+    return h.general && !h.cgrid && h.nr == d.nr && h.nt == d.ntheta && h.xm == d.xc && h.ym == d.yc &&
            std::memcmp(h.X.data(), d.X, sizeof(double) * 2 * (size_t)d.nr * d.ntheta) == 0;
+}
+
+bool same_mesh_c(const lbfsi::HostMesh& h, const lbfsi_solve_cgrid_desc& d) {
+    // the stored coordinates carry the mirrored rows before row 0
+    return h.cgrid && h.nr == d.nr && h.nt == d.ntheta && h.jc == d.n_cut && h.xm == d.xc && h.ym == d.yc &&
+           std::memcmp(h.X.data() + 2 * (size_t)h.G * h.nt, d.X, sizeof(double) * 2 * (size_t)d.nr * d.ntheta) == 0;
 }
 
 // Find or create the device geometry of a mesh (match: an existing entry's
@@ -222,9 +230,10 @@ int rebuild_tiles(lbfsi_batch b) {
     lbfsi::TraceRange trace_("lbfsi tile table");
     drop_graph(b);
     // separable-mesh tiles first (tile rows of the batch's shape), then the
-    // general-mesh tiles (the GEN kernel's 8-row tile)
+    // general-mesh tiles and the C-grid tiles (the GEN kernel's 8-row tile)
     std::vector<TileDev> tiles;
-    auto build = [&](bool general) {
+    auto build = [&](int part) {
+        const bool general = part > 0;
         const int rows = general ? lbfsi::GEN_TILE_ROWS : b->tile_rows;
         auto push = [&](size_t k, int ti, int tj) {
             const Slot& s = b->slots[k];
@@ -240,7 +249,8 @@ int rebuild_tiles(lbfsi_batch b) {
             tiles.push_back(t);
         };
         auto active = [&](size_t k) {
-            return b->slots[k].used && !b->slots[k].finished && b->slots[k].general == general;
+            const Slot& s = b->slots[k];
+            return s.used && !s.finished && (s.cgrid ? 2 : s.general ? 1 : 0) == part;
         };
         auto nti_of = [&](size_t k) { return (b->meshes[b->slots[k].mesh].host.nr + rows - 1) / rows; };
         if (b->order == 0) {
@@ -262,9 +272,11 @@ int rebuild_tiles(lbfsi_batch b) {
                 }
         }
     };
-    build(false);
+    build(0);
     const size_t nsep = tiles.size();
-    build(true);
+    build(1);
+    const size_t ngen = tiles.size() - nsep;
+    build(2);
     cudaError_t e = cudaSuccess;
     if (tiles.size() > b->tiles_cap) {
         e = cudaStreamSynchronize(b->stream);
@@ -284,7 +296,8 @@ int rebuild_tiles(lbfsi_batch b) {
         if (e != cudaSuccess) return cuda_err(e, "tile table upload");
     }
     b->ntiles = (int)nsep;
-    b->ngtiles = (int)(tiles.size() - nsep);
+    b->ngtiles = (int)ngen;
+    b->nctiles = (int)(tiles.size() - nsep - ngen);
     b->dirty = false;
     return LBFSI_OK;
 }
@@ -301,24 +314,35 @@ int check_status(lbfsi_batch b) {
     return LBFSI_OK;
 }
 
-lbfsi::StepArgs step_args(lbfsi_batch b, bool general) {
+// Launch arguments of one part of the tile table (0 separable, 1 general, 2 C-grid).
+lbfsi::StepArgs step_args(lbfsi_batch b, int part) {
     lbfsi::StepArgs a{};
     a.meshes = b->d_meshes;
     a.solves = b->d_solves;
-    a.tiles = b->d_tiles + (general ? b->ntiles : 0);
-    a.ntiles = general ? b->ngtiles : b->ntiles;
+    a.tiles = b->d_tiles + (part == 0 ? 0 : part == 1 ? b->ntiles : b->ntiles + b->ngtiles);
+    a.ntiles = part == 0 ? b->ntiles : part == 1 ? b->ngtiles : b->nctiles;
     a.collide_only = 0;
     a.ustep = -1;
     a.status = b->d_status;
     return a;
 }
 
-// One step of every active solve: the separable-mesh table launch and the
-// general-mesh one (independent solves, so their order is free).
-cudaError_t launch_both(lbfsi_batch b, cudaStream_t s) {
+// One step of every active solve: the separable-mesh table launch, the
+// general-mesh one and, for C-grids, a collide-only launch followed by a
+// stream launch from its output (independent solves, so the order of the
+// parts is free).
+cudaError_t launch_all(lbfsi_batch b, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    if (b->ntiles > 0) e = lbfsi::launch_step(step_args(b, false), b->precision, b->variant, s);
-    if (e == cudaSuccess && b->ngtiles > 0) e = lbfsi::launch_step_general_table(step_args(b, true), b->precision, s);
+    if (b->ntiles > 0) e = lbfsi::launch_step(step_args(b, 0), b->precision, b->variant, s);
+    if (e == cudaSuccess && b->ngtiles > 0) e = lbfsi::launch_step_general_table(step_args(b, 1), b->precision, s);
+    if (e == cudaSuccess && b->nctiles > 0) {
+        lbfsi::StepArgs a = step_args(b, 2);
+        a.collide_only = 1;
+        e = lbfsi::launch_step_general_table(a, b->precision, s);
+        a.collide_only = 0;
+        a.stream_post = 1;
+        if (e == cudaSuccess) e = lbfsi::launch_step_general_table(a, b->precision, s);
+    }
     return e;
 }
 
@@ -328,13 +352,13 @@ cudaError_t launch_both(lbfsi_batch b, cudaStream_t s) {
 int capture_graph(lbfsi_batch b) {
     lbfsi::TraceRange trace_("lbfsi batch graph capture");
     cudaError_t e = lbfsi::prepare_step(b->precision, b->variant, false);
-    if (e == cudaSuccess && b->ngtiles > 0) e = lbfsi::prepare_step(b->precision, 0, false, true);
+    if (e == cudaSuccess && b->ngtiles + b->nctiles > 0) e = lbfsi::prepare_step(b->precision, 0, false, true);
     if (e == cudaSuccess && !b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_err(e, "graph capture setup");
     e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(e, "begin capture");
     cudaError_t le = cudaSuccess;
-    for (int g = 0; g < b->graph_steps && le == cudaSuccess; ++g) le = launch_both(b, b->cap_stream);
+    for (int g = 0; g < b->graph_steps && le == cudaSuccess; ++g) le = launch_all(b, b->cap_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->cap_stream, &graph);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -439,24 +463,42 @@ int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_
         return rc;
     }
     Slot s;
-    const size_t N = (size_t)h.N, es = b->esize;
+    // slots per component: nr nt, plus a C-grid's mirrored rows before row 0
+    const size_t N = (size_t)h.N, Nx = (size_t)h.Nx, es = b->esize, g0 = (size_t)h.G * h.nt;
     auto take = [&](size_t bytes) -> void* {
         void* p = b->pool.alloc(bytes);
         if (p) s.blocks.push_back(p);
         return p;
     };
     bool ok = true;
+    void* p0 = nullptr;   // first population block (the initial state is written there)
+    void* m0 = nullptr;
     for (int p = 0; p < 2 && ok; ++p) {
-        ok = ok && (sd.p[p] = take(18 * N * es)) != nullptr;
-        ok = ok && (sd.M[p] = take(4 * N * es)) != nullptr;
+        void* pb = take(18 * Nx * es);
+        void* mb = take(4 * Nx * es);
+        ok = ok && pb && mb;
+        if (p == 0) {
+            p0 = pb;
+            m0 = mb;
+        }
+        if (ok) {
+            sd.p[p] = (char*)pb + 2 * g0 * es;   // row 0
+            sd.M[p] = (char*)mb + g0 * es;
+        }
         ok = ok && (sd.maps[p] = (StepMaps*)take(sizeof(StepMaps))) != nullptr;
+    }
+    sd.ppost = nullptr;
+    if (ok && h.cgrid) {
+        void* pp = take(18 * Nx * es);
+        ok = pp != nullptr;
+        if (ok) sd.ppost = (char*)pp + 2 * g0 * es;
     }
     ok = ok && (sd.part = (double*)take((size_t)h.ntj * 3 * sizeof(double))) != nullptr;
     ok = ok && (sd.counter = (unsigned*)take(2 * sizeof(unsigned))) != nullptr;
     BodyDev* body = nullptr;
     ok = ok && (body = (BodyDev*)take(sizeof(BodyDev))) != nullptr;
     double* stage = nullptr;
-    ok = ok && (stage = (double*)take(4 * N * sizeof(double))) != nullptr;
+    ok = ok && (stage = (double*)take(4 * Nx * sizeof(double))) != nullptr;
     if (!ok) {
         release_slot_memory(b, s);
         drop_mesh(b, mk);
@@ -466,7 +508,6 @@ int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_
     sd.mesh = mk;
     const int rows = h.general ? lbfsi::GEN_TILE_ROWS : b->tile_rows;
     sd.ntiles = ((h.nr + rows - 1) / rows) * h.ntj;
-    sd.ppost = nullptr;
     // initial state: equilibria of the initial field, bodies at rest
     std::vector<double> M(4 * N);
     if (rho_u_T) {
@@ -479,11 +520,25 @@ int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_
             M[3 * N + n] = sd.T_inf;
         }
     }
+    if (h.cgrid) {
+        // the two copies of a cut node start from the first copy's values;
+        // the mirrored rows below row 0 from their nodes
+        for (int c = 0; c < 4; ++c)
+            for (int j = 0; j <= h.jc; ++j) M[c * N + (size_t)(h.nt - 1 - j)] = M[c * N + (size_t)j];
+        std::vector<double> Mx(4 * Nx);
+        for (int c = 0; c < 4; ++c) {
+            std::memcpy(&Mx[c * Nx + g0], &M[c * N], N * sizeof(double));
+            for (int k2 = 1; k2 <= h.G; ++k2)
+                for (int j = 0; j < h.nt; ++j)
+                    Mx[c * Nx + g0 - (size_t)k2 * h.nt + j] = M[c * N + (size_t)k2 * h.nt + (h.nt - 1 - j)];
+        }
+        M.swap(Mx);
+    }
     const BodyDev bd = lbfsi::body_dev(body_desc, sd.rho_inf, sd.uinf_x);
     cudaError_t e = cudaMemcpyAsync(stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(body, &bd, sizeof(BodyDev), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sd.counter, 0, 2 * sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = lbfsi::launch_init(b->precision, stage, sd.p[0], sd.M[0], (int)N, 1, sd.Cv, b->stream);
+    if (e == cudaSuccess) e = lbfsi::launch_init(b->precision, stage, p0, m0, (int)Nx, 1, sd.Cv, b->stream);
     if (e == cudaSuccess)
         e = lbfsi::launch_prepare(body, b->d_zero_state, b->d_zero_state, b->d_zero_state, b->d_zero_loads, sd.dt,
                                   1, sd.maps[0], b->stream);
@@ -501,6 +556,7 @@ int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_
     s.used = true;
     s.finished = false;
     s.general = h.general;
+    s.cgrid = h.cgrid;
     s.mesh = mk;
     s.steps_target = steps;
     s.steps_done = 0;
@@ -540,6 +596,20 @@ int lbfsi_batch_add_xy(lbfsi_batch b, const lbfsi_solve_xy_desc* d, int* slot) {
     return add_solve(b, d->body, d->flow, d->rho_u_T, d->steps, d->nr, d->ntheta, acquire, slot);
 }
 
+int lbfsi_batch_add_cgrid(lbfsi_batch b, const lbfsi_solve_cgrid_desc* d, int* slot) {
+    lbfsi::TraceRange trace_("lbfsi_batch_add_cgrid");
+    if (!b || !d || !slot) return lbfsi::set_error(LBFSI_EINVAL, "null argument");
+    auto acquire = [&](int* mk) {
+        return acquire_mesh(
+            b, [&](const lbfsi::HostMesh& h) { return same_mesh_c(h, *d); },
+            [&](lbfsi::HostMesh& h) {
+                return lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->n_cut, d->X, d->xc, d->yc, h);
+            },
+            mk);
+    };
+    return add_solve(b, d->body, d->flow, d->rho_u_T, d->steps, d->nr, d->ntheta, acquire, slot);
+}
+
 int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
     lbfsi::TraceRange trace_("lbfsi_batch_step");
     if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
@@ -550,7 +620,7 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
             const int rc = rebuild_tiles(b);
             if (rc) return rc;
         }
-        if (b->ntiles + b->ngtiles == 0) break;
+        if (b->ntiles + b->ngtiles + b->nctiles == 0) break;
         // steps until the next solve finishes: the tile table is fixed over them
         int run = nsteps - st;
         for (auto& s : b->slots)
@@ -567,7 +637,7 @@ int lbfsi_batch_step(lbfsi_batch b, int nsteps, int* active_after) {
             }
         }
         for (; done < run; ++done) {
-            const cudaError_t e = launch_both(b, b->stream);
+            const cudaError_t e = launch_all(b, b->stream);
             if (e != cudaSuccess) return cuda_err(e, "batch step launch");
         }
         st += run;
@@ -695,12 +765,14 @@ int lbfsi_batch_get(lbfsi_batch b, int slot, double* rho_u_T, double* loads, lbf
         return lbfsi::set_error(LBFSI_EINVAL, "invalid slot");
     const Slot& s = b->slots[slot];
     const int cur = s.steps_done & 1;
-    const size_t N = (size_t)b->meshes[s.mesh].host.N;
+    const size_t N = (size_t)b->meshes[s.mesh].host.N, Nx = (size_t)b->meshes[s.mesh].host.Nx;
     cudaError_t e = cudaSuccess;
     std::vector<unsigned char> raw;
     if (rho_u_T) {
+        // rows 0 .. nr-1 of the four components (Nx slots apart)
         raw.resize(4 * N * b->esize);
-        e = cudaMemcpyAsync(raw.data(), s.dev.M[cur], raw.size(), cudaMemcpyDeviceToHost, b->stream);
+        e = cudaMemcpy2DAsync(raw.data(), N * b->esize, s.dev.M[cur], Nx * b->esize, N * b->esize, 4,
+                              cudaMemcpyDeviceToHost, b->stream);
     }
     StepMaps mp{};
     if (e == cudaSuccess && (loads || state))

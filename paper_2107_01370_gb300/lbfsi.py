@@ -32,7 +32,7 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
             "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy",
-            "lbfsi_create_mesh_cgrid"]
+            "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid"]
 
 
 class LbfsiError(RuntimeError):
@@ -75,6 +75,14 @@ class MeshCGridDesc(ctypes.Structure):
                 ("X", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class SolveCGridDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("n_cut", ctypes.c_int),
+                ("X", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("body", BodyDesc),
+                ("flow", FlowParams), ("rho_u_T", ctypes.POINTER(ctypes.c_double)),
+                ("steps", ctypes.c_int)]
 
 
 class SolveXYDesc(ctypes.Structure):
@@ -412,6 +420,21 @@ class Batch:
                         flow_params(flow), None if m is None else _dptr(m), int(steps))
         slot = ctypes.c_int(-1)
         rc = self._lib.lbfsi_batch_add_xy(self.h, ctypes.byref(d), ctypes.byref(slot))
+        if rc == ENOMEM:
+            return None
+        _check(rc)
+        self._shapes[slot.value] = (X.shape[0], X.shape[1])
+        return slot.value
+
+    def add_cgrid(self, X, n_cut, body, flow, steps, rho_u_T=None, centre=(0.0, 0.0)):
+        """Admit a solve on a C-grid X [nr, ntheta, 2] with n_cut cut nodes
+        per side; returns its slot, or None if the pool has no room now."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        m = None if rho_u_T is None else np.ascontiguousarray(rho_u_T, dtype=np.float64)
+        d = SolveCGridDesc(X.shape[0], X.shape[1], int(n_cut), _dptr(X), centre[0], centre[1],
+                           body_desc(body), flow_params(flow), None if m is None else _dptr(m), int(steps))
+        slot = ctypes.c_int(-1)
+        rc = self._lib.lbfsi_batch_add_cgrid(self.h, ctypes.byref(d), ctypes.byref(slot))
         if rc == ENOMEM:
             return None
         _check(rc)

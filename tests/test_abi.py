@@ -129,14 +129,16 @@ def test_cgrid_struct_layout_and_validation_without_gpu(tmp_path, lib):
     from paper_2107_01370_gb300 import inputs, lbfsi
     src = tmp_path / "cg.c"
     src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lbfsi_mesh_cgrid_desc),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbfsi_mesh_cgrid_desc),'
                    'offsetof(lbfsi_mesh_cgrid_desc, X), offsetof(lbfsi_mesh_cgrid_desc, xc),'
-                   'offsetof(lbfsi_mesh_cgrid_desc, bodies));return 0;}\n')
+                   'offsetof(lbfsi_mesh_cgrid_desc, bodies), sizeof(lbfsi_solve_cgrid_desc),'
+                   'offsetof(lbfsi_solve_cgrid_desc, steps));return 0;}\n')
     exe = tmp_path / "cg"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [ctypes.sizeof(lbfsi.MeshCGridDesc), lbfsi.MeshCGridDesc.X.offset,
-                   lbfsi.MeshCGridDesc.xc.offset, lbfsi.MeshCGridDesc.bodies.offset]
+                   lbfsi.MeshCGridDesc.xc.offset, lbfsi.MeshCGridDesc.bodies.offset,
+                   ctypes.sizeof(lbfsi.SolveCGridDesc), lbfsi.SolveCGridDesc.steps.offset]
     X = inputs.cgrid_ellipse(17, 4, 9, 0.6, 0.35, r_far=4.0, wake=3.0)
     body = lbfsi.BodyDesc()
     h = ctypes.c_void_p()

@@ -161,3 +161,51 @@ def test_general_and_separable_meshes_in_one_batch(L, precision):
         assert np.array_equal(got[k][0], alone[k][0]), k
         assert np.array_equal(got[k][1], alone[k][1]), k
         assert got[k][2] == alone[k][2], k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_cgrid_solves_in_the_batch(L, precision):
+    """A C-grid solve (collide-only and stream table launches) shares the
+    batch with a separable and a general O-grid solve, admitted at different
+    times, with graph replay: each ends bit for bit like the same solve alone."""
+    prec = L.FP32 if precision == "fp32" else L.FP64
+    cb = inputs.BodySpec(dof=2, xp=-0.2, yp=0.0, r_in=0.75, r_out=2.0, m_star=5.0, v_r=2.0, x_alpha=0.3,
+                         r_alpha=0.6, wh_wa=0.5, length=1.2)
+    cgc = inputs.cgrid_case(49, 8, 32, 0.6, 0.35, r_far=6.0, wake=4.0, length=1.2, body=cb)
+    M_c = inputs.initial_field(cgc.nr, cgc.ntheta, cgc.flow, seed=51)
+    eb = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=3.0, v_r=4.0, length=1.2)
+    ell = inputs.xy_case(inputs.ellipse_wall(64, 0.6, 0.35), 40, r_far=8.0, length=1.2, body=eb)
+    M_e = inputs.initial_field(ell.nr, ell.ntheta, ell.flow, seed=52)
+    sep = _case(48, 64, 5.0, 10.0, 2)
+    steps = {"c": 27, "e": 22, "s": 31}
+    batch = L.Batch(256 << 20, precision=prec)
+    batch.set_graph_steps(3)
+    slots = {"s": batch.add(sep[0].r, sep[0].e, sep[0].bodies[0], sep[0].flow, steps["s"], sep[1])}
+    batch.step(4)
+    slots["c"] = batch.add_cgrid(cgc.X, cgc.n_cut, cb, cgc.flow, steps["c"], M_c)
+    batch.step(2)
+    slots["e"] = batch.add_xy(ell.X, eb, ell.flow, steps["e"], M_e)
+    while batch.step(5) > 0:
+        pass
+    got = {k: batch.get(v) for k, v in slots.items()}
+    batch.close()
+    alone = {}
+    m = L.Mesh.cgrid(cgc.X, cgc.n_cut, [cb], precision=prec)
+    m.init_fields(cgc.flow, M_c[None])
+    m.step(steps["c"])
+    alone["c"] = (m.get_fields()[0], m.body_forces()[0], m.body_state()[0])
+    m.close()
+    m = L.Mesh.xy(ell.X, [eb], precision=prec)
+    m.init_fields(ell.flow, M_e[None])
+    m.step(steps["e"])
+    alone["e"] = (m.get_fields()[0], m.body_forces()[0], m.body_state()[0])
+    m.close()
+    m = L.Mesh(sep[0].r, sep[0].e, sep[0].bodies, precision=prec)
+    m.init_fields(sep[0].flow, sep[1][None])
+    m.step(steps["s"])
+    alone["s"] = (m.get_fields()[0], m.body_forces()[0], m.body_state()[0])
+    m.close()
+    for k in slots:
+        assert np.array_equal(got[k][0], alone[k][0]), k
+        assert np.array_equal(got[k][1], alone[k][1]), k
+        assert got[k][2] == alone[k][2], k
