@@ -358,7 +358,7 @@ def general_mesh_cases():
                                                        stream=st)))
 
 
-def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8):
+def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8, only=None):
     """MLUPS of the general-mesh step (Newton departure points, stored
     metric) on the two workloads of general_mesh_cases, timed with CUDA events
     on the library's stream; the C-grid step is two launches (collision, then
@@ -366,7 +366,9 @@ def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8):
     import torch
     from paper_2107_01370_gb300 import lbfsi
     out = []
-    for case, make in general_mesh_cases():
+    for k, (case, make) in enumerate(general_mesh_cases()):
+        if only is not None and k != only:
+            continue
         M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
         m = make(lbfsi.FP32, batch, stream.cuda_stream)
         m.init_fields(case.flow, np.ascontiguousarray(np.broadcast_to(M0, (batch,) + M0.shape)))
@@ -485,6 +487,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1-16 M-node roofline sweep and the small FP64 case")
     ap.add_argument("--schedule", default=None,
                     help="'variant,order': fixed tile shape and CTA order instead of the autotuner")
+    ap.add_argument("--general-only", type=int, default=None, choices=[0, 1],
+                    help="time only one general-mesh workload (0: O-grid by coordinates, 1: C-grid) "
+                         "with --steps, --warmup and --batch, print its JSON and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -509,6 +514,13 @@ def main():
     if not os.path.exists(lbfsi.LIB_PATH):
         build.build()
     lbfsi.load()
+
+    if args.general_only is not None:
+        peak, _ = measured_peaks()
+        res = general_mesh_throughput(torch.cuda.Stream(device=dev), peak, steps=args.steps,
+                                      warmup=args.warmup, batch=args.batch, only=args.general_only)
+        print(json.dumps(res[0]), flush=True)
+        return
 
     case = inputs.viv_cylinder_512x256()
     B = args.batch
