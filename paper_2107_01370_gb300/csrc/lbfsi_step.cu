@@ -695,11 +695,19 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     }
 
     // ---- phase 2: correction fields and collision of step k --------------
+    // a collide-only launch of a general mesh (a C-grid's first launch)
+    // writes the tile's nodes only: the collision is needed there, the
+    // correction field D and the gradient maps on +-1, dQ on +-2
+    const bool shrink = GEN && mode == MODE_COLLIDE_ONLY;
+    auto outside = [&](int li, int lj, int h, int w) {
+        return shrink && (li < h - w || li >= h + TI + w || lj < h - w || lj >= h + TJ + w);
+    };
     if (collide) {
         for (int idx = tid; idx < T::MS; idx += NT) {
             const int i = mi0 + idx / T::MW;
             if (i < rlo || i >= nr) continue;
             if (cg && (unsigned)(mj0 + idx % T::MW) >= (unsigned)nt) continue;
+            if (outside(idx / T::MW, idx % T::MW, T::HM, 2)) continue;
             const R rho = sM[idx], ux = sM[T::MS + idx], uy = sM[2 * T::MS + idx], Tn = sM[3 * T::MS + idx];
             sQ[idx] = rho * ux * (R(1) - R(3) * Tn) - rho * ux * ux * ux;
             sQ[T::MS + idx] = rho * uy * (R(1) - R(3) * Tn) - rho * uy * uy * uy;
@@ -710,6 +718,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = i0 - T::HD + li;
             if (i < rlo || i >= nr) continue;
             if (cg && (unsigned)(j0 - T::HD + lj) >= (unsigned)nt) continue;
+            if (outside(li, lj, T::HD, 1)) continue;
             R F00, F01, F10, F11, vx, vy;
             R G[4];
             if constexpr (GEN) {
@@ -744,6 +753,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
             if (i < rlo || i >= nr) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
+            if (outside(li, lj, T::HD, 1)) continue;
             const int m = (li + 1) * T::MW + (lj + 1);
             const R mup = mu * rcp_(sM[m] * sM[3 * T::MS + m]);
             R qx_xi, qx_et, qy_xi, qy_et;
@@ -769,6 +779,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = pi0 + li, jj = j0 - T::HP + lj;
             if (i < 0 || i >= nr) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
+            if (outside(li, lj, T::HP, 0)) continue;
             const int sn = li * T::PWS + lj + 2;   // staged node
             R f[9], g[9];
             if (i == nr - 1 || (cg && (jj == 0 || jj == nt - 1))) {
