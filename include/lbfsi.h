@@ -220,6 +220,25 @@ int lbfsi_get_populations(lbfsi_mesh m, int which, double* f, double* g);
 int lbfsi_set_populations(lbfsi_mesh m, const double* f, const double* g,
                           const double* rho_u_T);
 
+enum { LBFSI_FIELD_MOMENTS = 0, LBFSI_FIELD_POPULATIONS = 1 };
+
+/* Zero-copy device view of the current state (for other GPU code, e.g. a
+ * torch tensor over the same memory): which = LBFSI_FIELD_MOMENTS gives the
+ * moment field rho, u_x, u_y, T of the last step, [nbatch][4][slots];
+ * LBFSI_FIELD_POPULATIONS its post-propagation populations as (f, g) pairs,
+ * [nbatch][9][slots][2].  Elements are double (LBFSI_FP64) or float
+ * (LBFSI_FP32).  *slots (nullable) receives the slots per component: nr *
+ * ntheta, plus 4 * ntheta mirrored rows before row 0 on a C-grid; *row0
+ * (nullable) the slot where node (0, 0) starts (0, or 4 * ntheta).  The
+ * memory belongs to the handle; the pointer is valid until the handle is
+ * destroyed, but the state it holds is the current one only until the next
+ * step (the step writes the other buffer of a ping-pong pair and that one
+ * becomes current).  Reads must be ordered after the handle's stream
+ * (lbfsi_synchronize, or work on the same stream); writes change the next
+ * step's input.  LBFSI_EINVAL for a bad 'which' or null ptr,
+ * LBFSI_ESTATE before lbfsi_init_fields. */
+int lbfsi_field_ptr(lbfsi_mesh m, int which, void** ptr, int64_t* slots, int64_t* row0);
+
 /* Wait for the handle's stream; returns the first device-detected error. */
 int lbfsi_synchronize(lbfsi_mesh m);
 

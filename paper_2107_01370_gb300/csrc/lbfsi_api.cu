@@ -526,6 +526,17 @@ int lbfsi_step(lbfsi_mesh m, int nsteps) {
     return LBFSI_OK;
 }
 
+int lbfsi_field_ptr(lbfsi_mesh m, int which, void** ptr, int64_t* slots, int64_t* row0) {
+    if (!m || !ptr) return fail(LBFSI_EINVAL, "null argument");
+    if (which != LBFSI_FIELD_MOMENTS && which != LBFSI_FIELD_POPULATIONS)
+        return fail(LBFSI_EINVAL, "which must be LBFSI_FIELD_MOMENTS or LBFSI_FIELD_POPULATIONS");
+    if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
+    *ptr = which == LBFSI_FIELD_MOMENTS ? m->d_M[m->cur()] : m->d_p[m->cur()];
+    if (slots) *slots = (int64_t)m->host.Nx;
+    if (row0) *row0 = (int64_t)m->host.G * m->host.nt;
+    return LBFSI_OK;
+}
+
 int lbfsi_synchronize(lbfsi_mesh m) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     return check_status(m);

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "liblbfsi.so")
 
 FP64 = 0
 FP32 = 1
+FIELD_MOMENTS, FIELD_POPULATIONS = 0, 1
 
 OK, EINVAL, ENOMEM, ECUDA, EDEPARTURE, ENONPHYS, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDEPARTURE: "EDEPARTURE",
@@ -32,7 +33,7 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
             "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy",
-            "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid"]
+            "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid", "lbfsi_field_ptr"]
 
 
 class LbfsiError(RuntimeError):
@@ -68,6 +69,17 @@ class MeshXYDesc(ctypes.Structure):
                 ("X", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class _DeviceArray:
+    """Device memory of a handle exposed through __cuda_array_interface__
+    (keeps the handle alive); row0: slot of node (0, 0) in each component."""
+
+    def __init__(self, ptr, shape, typestr, owner, row0):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+        self.owner = owner
+        self.row0 = row0
 
 
 class MeshCGridDesc(ctypes.Structure):
@@ -152,6 +164,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in EXPORTED:
         if name not in ("lbfsi_launch_count", "lbfsi_last_error", "lbfsi_checkpoint_bytes"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.lbfsi_field_ptr.argtypes = [P, ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)]
     lib.lbfsi_checkpoint_bytes.restype = ctypes.c_size_t
     lib.lbfsi_checkpoint_bytes.argtypes = [ctypes.c_void_p]
     lib.lbfsi_checkpoint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
@@ -303,6 +317,26 @@ class Mesh:
 
     def synchronize(self):
         _check(self._lib.lbfsi_synchronize(self.h))
+
+    def field_ptr(self, which=FIELD_MOMENTS):
+        """Device pointer, slots per component and the slot of node (0, 0) of
+        the current moment field or populations (lbfsi_field_ptr)."""
+        ptr = ctypes.c_void_p()
+        slots = ctypes.c_int64()
+        row0 = ctypes.c_int64()
+        _check(self._lib.lbfsi_field_ptr(self.h, int(which), ctypes.byref(ptr), ctypes.byref(slots),
+                                         ctypes.byref(row0)))
+        return ptr.value, slots.value, row0.value
+
+    def field_view(self, which=FIELD_MOMENTS):
+        """The current moment field [nbatch, 4, slots] or populations
+        [nbatch, 9, slots, 2] as a CUDA array interface over the handle's own
+        memory (torch.as_tensor(view, device="cuda") wraps it without a copy);
+        valid as the current state until the next step, read after
+        synchronize()."""
+        ptr, slots, row0 = self.field_ptr(which)
+        shape = (self.nbatch, 4, slots) if which == FIELD_MOMENTS else (self.nbatch, 9, slots, 2)
+        return _DeviceArray(ptr, shape, "<f8" if self.precision == FP64 else "<f4", self, row0)
 
     def body_forces(self, out=None):
         out = np.empty((self.nbatch, 3)) if out is None else out

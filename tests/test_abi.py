@@ -76,6 +76,8 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
     assert lib.lbfsi_step(None, 1) == lbfsi.EINVAL
     assert lib.lbfsi_launch_count(None) == -1
+    ptr = ctypes.c_void_p()
+    assert lib.lbfsi_field_ptr(None, lbfsi.FIELD_MOMENTS, ctypes.byref(ptr), None, None) == lbfsi.EINVAL
 
 
 def test_xy_mesh_struct_layout_matches_c(tmp_path):

@@ -155,3 +155,21 @@ def test_cgrid_graph_replay_and_resume_are_bit_identical(L, precision):
         assert np.array_equal(x, y)
     assert ref[2] == got[2]
     assert n_launch >= 2 * 23
+
+
+def test_cgrid_reports_cfl_violation(L):
+    """A time step eight times the C-grid's CFL step: departure points leave
+    the cells adjacent to their nodes; the kernel records it and the next
+    synchronising call reports EDEPARTURE (the oracle raises likewise)."""
+    case = _case(BODIES[0][0], n_wall=33, n_cut=8, nr=24)
+    case.flow.dt *= 8.0
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=3)
+    with pytest.raises(OM.DepartureError):
+        OS.Solver.from_case(OM.CGridMesh(case.X, case.n_cut), case, M0).step()
+    m = L.Mesh.cgrid(case.X, case.n_cut, case.bodies, precision=L.FP32)
+    m.init_fields(case.flow, M0[None])
+    m.step(2)
+    with pytest.raises(L.LbfsiError) as ei:
+        m.synchronize()
+    assert ei.value.code == L.EDEPARTURE
+    m.close()
