@@ -163,6 +163,28 @@ typedef struct {
     const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)      */
 } lbfsi_mesh_cgrid_desc;
 
+/* A doubly periodic box (SURVEY's Cartesian periodic kind; the mesh of the
+ * Taylor-Green and acoustic checks of Sec. II C): node coordinates of one
+ * period, X [ni][nj][2] (subparametric, positively oriented), and the
+ * period vectors: node (i + ni, j) is node (i, j) + shift_i, node (i, j + nj)
+ * is node (i, j) + shift_j (a parallelogram box when shift_j has an x part).
+ * Every node is interior: no wall, no far field, so the bodies must be fixed
+ * (dof 0) and the loads are zero. */
+typedef struct {
+    int ni, nj;                 /* even, >= 4 */
+    const double* X;            /* [ni][nj][2] node coordinates (host, borrowed) */
+    double shift_i[2], shift_j[2];
+    int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations             */
+    int nbatch;                 /* independent solves sharing the mesh, >= 1        */
+    const lbfsi_body_desc* bodies;  /* [nbatch], dof 0 (host)                       */
+} lbfsi_mesh_box_desc;
+
+/* Create a mesh handle on a periodic box; otherwise as lbfsi_create_mesh_xy
+ * (general-mesh kernel, one tile shape).  LBFSI_EINVAL for odd or too small
+ * sizes, a mesh that is not subparametric or not positively oriented, or a
+ * moving body. */
+int lbfsi_create_mesh_box(const lbfsi_mesh_box_desc* d, void* cuda_stream, lbfsi_mesh* out);
+
 /* Create a mesh handle on a C-grid; otherwise as lbfsi_create_mesh_xy (one
  * tile shape).  A step is two launches here: the collision of step k into a
  * post-collision buffer, then the stream of step k + 1 from it.

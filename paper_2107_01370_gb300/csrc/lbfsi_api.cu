@@ -323,6 +323,20 @@ int lbfsi_create_mesh_xy(const lbfsi_mesh_xy_desc* d, void* cuda_stream, lbfsi_m
     return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
 }
 
+int lbfsi_create_mesh_box(const lbfsi_mesh_box_desc* d, void* cuda_stream, lbfsi_mesh* out) {
+    g_last_error.clear();
+    if (!d) return fail(LBFSI_EINVAL, "null argument");
+    int rc = check_common(d->ni, d->nj, d->precision, d->nbatch, d->bodies, out);
+    if (rc) return rc;
+    auto m = new lbfsi_mesh_s();
+    rc = lbfsi::build_host_mesh_box(d->ni, d->nj, d->X, d->shift_i, d->shift_j, m->host);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
+}
+
 int lbfsi_create_mesh_cgrid(const lbfsi_mesh_cgrid_desc* d, void* cuda_stream, lbfsi_mesh* out) {
     g_last_error.clear();
     if (!d) return fail(LBFSI_EINVAL, "null argument");

@@ -430,12 +430,92 @@ int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, dou
     return LBFSI_OK;
 }
 
+int build_host_mesh_box(int ni, int nj, const double* X, const double* shift_i, const double* shift_j,
+                        HostMesh& m) {
+    if (ni < 4 || nj < 4 || ni % 2 || nj % 2) return set_error(LBFSI_EINVAL, "a periodic box needs even ni, nj >= 4");
+    if (!X || !shift_i || !shift_j) return set_error(LBFSI_EINVAL, "null argument");
+    m.general = true;
+    m.box = true;
+    m.nr = ni;
+    m.nt = nj;
+    m.N = ni * nj;
+    m.Nx = m.N;
+    m.ntj = tiles_j(nj);
+    m.X.assign(X, X + 2 * (size_t)m.N);
+    double scale = 0.0;
+    for (double v : m.X) {
+        if (!std::isfinite(v)) return set_error(LBFSI_EINVAL, "node coordinates must be finite");
+        scale = std::max(scale, std::fabs(v));
+    }
+    for (int c = 0; c < 2; ++c) {
+        if (!std::isfinite(shift_i[c]) || !std::isfinite(shift_j[c]))
+            return set_error(LBFSI_EINVAL, "period vectors must be finite");
+        scale = std::max(scale, std::max(std::fabs(shift_i[c]), std::fabs(shift_j[c])));
+    }
+    // coordinates of any index pair: the node of the period plus the shifts
+    auto P = [&](int i, int j, int c) {
+        const int ki = (int)std::floor((double)i / ni), kj = (int)std::floor((double)j / nj);
+        return m.X[2 * ((size_t)(i - ki * ni) * nj + (j - kj * nj)) + c] + ki * shift_i[c] + kj * shift_j[c];
+    };
+    for (int wa = 0; wa < ni; wa += 2)
+        for (int wb = 0; wb < nj; wb += 2)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    for (int c = 0; c < 2; ++c) {
+                        const double xi = a - 1.0, et = b - 1.0;
+                        const double v = 0.25 * ((1 - xi) * (1 - et) * P(wa, wb, c) + (1 + xi) * (1 - et) * P(wa + 2, wb, c) +
+                                                 (1 - xi) * (1 + et) * P(wa, wb + 2, c) +
+                                                 (1 + xi) * (1 + et) * P(wa + 2, wb + 2, c));
+                        if (std::fabs(v - P(wa + a, wb + b, c)) > 1e-12 * scale)
+                            return set_error(LBFSI_EINVAL, "node coordinates must be subparametric "
+                                                           "(every window the bilinear image of its corners)");
+                    }
+    // no wall and no far field: empty per-column tables
+    m.xw.assign(2 * (size_t)nj, 0.0);
+    m.fardir.assign(2 * (size_t)nj, 0.0);
+    m.n0.assign(2 * (size_t)nj, 0.0);
+    m.wall_geo.assign(6 * (size_t)nj, 0.0);
+    // inverse metric with central differences in both (periodic) directions
+    m.jinv.assign(4 * (size_t)m.N, 0.0);
+    for (int i = 0; i < ni; ++i)
+        for (int j = 0; j < nj; ++j) {
+            double di[2], dj[2];
+            for (int c = 0; c < 2; ++c) {
+                di[c] = 0.5 * (P(i + 1, j, c) - P(i - 1, j, c));
+                dj[c] = 0.5 * (P(i, j + 1, c) - P(i, j - 1, c));
+            }
+            const double det = di[0] * dj[1] - di[1] * dj[0];
+            if (!(det > 0.0))
+                return set_error(LBFSI_EINVAL, "mesh not positively oriented (index-to-space Jacobian <= 0)");
+            double* t = &m.jinv[4 * ((size_t)i * nj + j)];
+            t[0] = dj[1] / det;
+            t[1] = -di[1] / det;
+            t[2] = -dj[0] / det;
+            t[3] = di[0] / det;
+        }
+    // element coefficients of every cell (windows wrap, corners shifted)
+    m.cellc.assign((size_t)ni * nj * CELLC, 0.0);
+    for (int a = 0; a < ni; ++a)
+        for (int b = 0; b < nj; ++b) {
+            const int wa = 2 * (a / 2), wb = 2 * (b / 2);
+            double* t = &m.cellc[((size_t)a * nj + b) * CELLC];
+            for (int c = 0; c < 2; ++c) {
+                const double c00 = P(wa, wb, c), c10 = P(wa + 2, wb, c), c01 = P(wa, wb + 2, c), c11 = P(wa + 2, wb + 2, c);
+                t[0 + c] = 0.25 * (-c00 + c10 - c01 + c11);
+                t[2 + c] = 0.25 * (-c00 - c10 + c01 + c11);
+                t[4 + c] = 0.25 * (c00 - c10 - c01 + c11);
+            }
+        }
+    return LBFSI_OK;
+}
+
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
     if (!bodies) return set_error(LBFSI_EINVAL, "null body pointer");
     for (int k = 0; k < n; ++k) {
         const lbfsi_body_desc& b = bodies[k];
         if (b.dof < 0 || b.dof > 2) return set_error(LBFSI_EINVAL, "body dof must be 0, 1 or 2");
         if (b.dof == 0) continue;
+        if (m.box) return set_error(LBFSI_EINVAL, "a periodic box has no wall: bodies must be fixed (dof 0)");
         if (!(b.r_out > b.r_in) || !(b.length > 0) || !(b.m_star > 0) || !(b.v_r > 0))
             return set_error(LBFSI_EINVAL, "moving body needs r_out > r_in, length, m_star, v_r > 0");
         if (!(b.forced_periods >= 0.0) || !std::isfinite(b.pitch_amp) || !std::isfinite(b.forced_periods))
@@ -597,6 +677,7 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.cellc = pc ? (const char*)pc + g0 * CELLC * es : nullptr;
     d.cgrid = h.cgrid ? 1 : 0;
     d.jc = h.jc;
+    d.box = h.box ? 1 : 0;
     d.fardirj = (const double*)pfj;
     return LBFSI_OK;
 }

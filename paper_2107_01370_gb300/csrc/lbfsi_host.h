@@ -38,6 +38,8 @@ struct HostMesh {
     // C-grid: row-0 columns j < jc and j > nt-1-jc lie on the wake cut
     bool cgrid = false;
     int jc = 0;
+    // doubly periodic box (no wall, no far field): rows wrap as well
+    bool box = false;
     std::vector<double> r, e, n0, wall_geo, rowtab, coltab, xw, fardir, X, jinv, cellc;
     std::vector<double> fardirj;   // C-grid: [nr][2][2] outward directions of the outlet columns
 };
@@ -65,6 +67,12 @@ int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, Ho
 // nt-1-j of row 0 one point for j <= n_cut): the arrays carry G mirrored
 // rows below row 0 (node (-k, j) = node (k, nt-1-j)).
 int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, double yc, HostMesh& out);
+
+// A doubly periodic box given by the node coordinates X [ni][nj][2] of one
+// period and the period vectors along i and j (node (i + ni, j) = node (i, j)
+// + shift_i): no wall, no far field; bodies must be fixed.
+int build_host_mesh_box(int ni, int nj, const double* X, const double* shift_i, const double* shift_j,
+                        HostMesh& out);
 
 // Check bodies against a mesh (dof range, blend radii, wall inside the rigid zone).
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n);

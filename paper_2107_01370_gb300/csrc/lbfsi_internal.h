@@ -98,6 +98,9 @@ struct MeshDev {
     // cut, columns 0 and nt-1 are outlets
     int cgrid, jc;
     const double* fardirj;         // [nr][2][2] outward directions of columns 0 and nt-1
+    // doubly periodic box (general meshes only): rows wrap like columns,
+    // every node is interior (no wall, no far field)
+    int box;
 };
 
 // One solve (one body, one set of fields on one mesh).  Buffers are

@@ -111,9 +111,11 @@ __device__ __forceinline__ R d_col(const R* p) {
 // the rear point, along the cut.  With cg == 0 and across == false they are
 // d_row and d_col.
 template <typename R>
-__device__ __forceinline__ R d_row_c(const R* p, int stride, int i, int nr, bool across) {
-    if (i == 0 && !across) return R(0.5) * (R(-3) * p[0] + R(4) * p[stride] - p[2 * stride]);
-    if (i == nr - 1) return R(0.5) * (R(3) * p[0] - R(4) * p[-stride] + p[-2 * stride]);
+__device__ __forceinline__ R d_row_c(const R* p, int stride, int i, int nr, bool across, bool wrap_rows = false) {
+    if (!wrap_rows) {   // a periodic box has no first or last row
+        if (i == 0 && !across) return R(0.5) * (R(-3) * p[0] + R(4) * p[stride] - p[2 * stride]);
+        if (i == nr - 1) return R(0.5) * (R(3) * p[0] - R(4) * p[-stride] + p[-2 * stride]);
+    }
     return R(0.5) * (p[stride] - p[-stride]);
 }
 template <typename R>
@@ -251,9 +253,10 @@ __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F0
 template <typename R, int TJ>
 __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int j, int i0, int j0,
                                            int nr, int pi0, int sj0, int PWS, R dx, R dy, int& base,
-                                           R& xi, R& eta, bool below = false) {
+                                           R& xi, R& eta, bool below = false, bool wrap_rows = false) {
     // below: the node has cells below row 0 (the mirrored cells across a
-    // C-grid's cut); otherwise a row-0 node only has the cells of row 0
+    // C-grid's cut, or the wrapped rows of a periodic box); otherwise a row-0
+    // node only has the cells of row 0.  wrap_rows: no last window to clamp to
     const R di = jn[0] * dx + jn[2] * dy, dj = jn[1] * dx + jn[3] * dy;
     const bool down = i > 0 || below;
     int da = (!(di < R(0)) || !down) ? 0 : -1;
@@ -269,7 +272,7 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
 #pragma unroll 1
     for (int attempt = 0; attempt < 3; ++attempt) {
         const int ca = i + da, cb = j + db;
-        const int wa = min((ca >> 1) * 2, nr - 3), wb = (cb >> 1) * 2;
+        const int wa = wrap_rows ? (ca >> 1) * 2 : min((ca >> 1) * 2, nr - 3), wb = (cb >> 1) * 2;
         const R* c = sC + ((ca - (i0 - 1)) * (TJ + 1) + (cb - (j0 - 1))) * CELLC;
         const R xi0 = R(i - wa - 1), et0 = R(j - wb - 1);
         const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
@@ -487,12 +490,16 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     }
     // C-grid (general meshes): rows from -4 are stored (the mirrored rows),
     // the angular index does not wrap
-    int cg = 0, jc = 0;
+    int cg = 0, jc = 0, pb = 0;
     if constexpr (GEN) {
         cg = UNIFORM ? a.umesh.cgrid : mg->cgrid;
         jc = UNIFORM ? a.umesh.jc : mg->jc;
+        pb = UNIFORM ? a.umesh.box : mg->box;
     }
     const int rlo = cg ? -CGRID_GHOST_ROWS : 0;
+    // rows that exist (a periodic box: all, wrapped) and their stored index
+    auto rowok = [&](int i) { return pb || (i >= rlo && i < nr); };
+    auto rw = [&](int i) { return pb ? wrap_nt(i, nr) : i; };
     // a uniform launch from the host knows the step number; otherwise it is
     // the solve's device counter
     const unsigned kstep = (UNIFORM && a.ustep >= 0) ? (unsigned)a.ustep : __ldcg(ctr + 1);
@@ -542,8 +549,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
-            if (i < rlo || i >= nr || (cg && (unsigned)jj >= (unsigned)nt)) continue;
-            const ptrdiff_t n = (ptrdiff_t)i * nt + (cg ? jj : wrap_nt(jj, nt));
+            if (!rowok(i) || (cg && (unsigned)jj >= (unsigned)nt)) continue;
+            const ptrdiff_t n = (ptrdiff_t)rw(i) * nt + (cg ? jj : wrap_nt(jj, nt));
             if constexpr (sizeof(R) == 4) {
                 cp_async8(sX + 2 * idx, gx + 2 * n);
                 cp_async16(sJ + 4 * idx, gj + 4 * n);
@@ -558,8 +565,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int cell = t / NCC, ch = t - cell * NCC;
             const int la = cell / (TJ + 1), lb = cell - la * (TJ + 1);
             const int ca = i0 - 1 + la, cb = j0 - 1 + lb;
-            if (ca < (cg ? -1 : 0) || ca > nr - 2 || (cg && (unsigned)cb > (unsigned)(nt - 2))) continue;
-            const ptrdiff_t g = ((ptrdiff_t)ca * nt + (cg ? cb : wrap_nt(cb, nt))) * CELLC + ch * CE;
+            if (!pb && (ca < (cg ? -1 : 0) || ca > nr - 2)) continue;
+            if (cg && (unsigned)cb > (unsigned)(nt - 2)) continue;
+            const ptrdiff_t g = ((ptrdiff_t)rw(ca) * nt + (cg ? cb : wrap_nt(cb, nt))) * CELLC + ch * CE;
             cp_async16(sC + cell * CELLC + ch * CE, gc + g);
         }
     } else {
@@ -583,9 +591,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::MH * NCH; idx += NT) {
             const int ch = idx % NCH, li = idx / NCH;
             const int i = mi0 + li;
-            if (i < rlo || i >= nr) continue;
+            if (!rowok(i)) continue;
             R* dst = sM + li * T::MW + ch * CM;
-            const R* src = M_in + (ptrdiff_t)i * nt;
+            const R* src = M_in + (ptrdiff_t)rw(i) * nt;
             if (vec) {
                 src += wrap_nt(mj0 + ch * CM, nt);
 #pragma unroll
@@ -615,9 +623,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::PH * NCH; idx += NT) {
             const int ch = idx % NCH, li = idx / NCH;
             const int i = pi0 + li;
-            if (i < rlo || i >= nr) continue;
+            if (!rowok(i)) continue;
             R2* dst = sp + li * T::PWS + ch * CP;
-            const R2* src = p_in + (ptrdiff_t)i * nt;
+            const R2* src = p_in + (ptrdiff_t)rw(i) * nt;
             if (vec) {
                 src += wrap_nt(sj0 + ch * CP, nt);
 #pragma unroll
@@ -705,7 +713,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     if (collide) {
         for (int idx = tid; idx < T::MS; idx += NT) {
             const int i = mi0 + idx / T::MW;
-            if (i < rlo || i >= nr) continue;
+            if (!rowok(i)) continue;
             if (cg && (unsigned)(mj0 + idx % T::MW) >= (unsigned)nt) continue;
             if (outside(idx / T::MW, idx % T::MW, T::HM, 2)) continue;
             const R rho = sM[idx], ux = sM[T::MS + idx], uy = sM[2 * T::MS + idx], Tn = sM[3 * T::MS + idx];
@@ -716,7 +724,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
-            if (i < rlo || i >= nr) continue;
+            if (!rowok(i)) continue;
             if (cg && (unsigned)(j0 - T::HD + lj) >= (unsigned)nt) continue;
             if (outside(li, lj, T::HD, 1)) continue;
             R F00, F01, F10, F11, vx, vy;
@@ -751,7 +759,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
-            if (i < rlo || i >= nr) continue;
+            if (!rowok(i)) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
             if (outside(li, lj, T::HD, 1)) continue;
             const int m = (li + 1) * T::MW + (lj + 1);
@@ -759,9 +767,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             R qx_xi, qx_et, qy_xi, qy_et;
             if constexpr (GEN) {
                 const bool across = cg && i == 0 && (jj <= jc || jj >= nt - 1 - jc);
-                qx_xi = d_row_c(sQ + m, T::MW, i, nr, across);
+                qx_xi = d_row_c(sQ + m, T::MW, i, nr, across, pb);
                 qx_et = d_col_c(sQ + m, i, jj, nt, jc, cg);
-                qy_xi = d_row_c(sQ + T::MS + m, T::MW, i, nr, across);
+                qy_xi = d_row_c(sQ + T::MS + m, T::MW, i, nr, across, pb);
                 qy_et = d_col_c(sQ + T::MS + m, i, jj, nt, jc, cg);
             } else {
                 qx_xi = d_row(sQ + m, T::MW, i, nr);
@@ -777,12 +785,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::PS; idx += NT) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
             const int i = pi0 + li, jj = j0 - T::HP + lj;
-            if (i < 0 || i >= nr) continue;
+            if (!(pb || (i >= 0 && i < nr))) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
             if (outside(li, lj, T::HP, 0)) continue;
             const int sn = li * T::PWS + lj + 2;   // staged node
             R f[9], g[9];
-            if (i == nr - 1 || (cg && (jj == 0 || jj == nt - 1))) {
+            if ((!pb && i == nr - 1) || (cg && (jj == 0 || jj == nt - 1))) {
                 const int m = (li + 2) * T::MW + (lj + 2);
                 f_equilibrium(sM[m], sM[T::MS + m], sM[2 * T::MS + m], sM[3 * T::MS + m], f);
                 g_equilibrium(sM[m], sM[T::MS + m], sM[2 * T::MS + m], sM[3 * T::MS + m], Cv, g);
@@ -797,9 +805,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R dx_xi, dx_et, dy_xi, dy_et;
                 if constexpr (GEN) {
                     const bool across = cg && i == 0 && (jj <= jc || jj >= nt - 1 - jc);
-                    dx_xi = d_row_c(sD + d, T::DW, i, nr, across);
+                    dx_xi = d_row_c(sD + d, T::DW, i, nr, across, pb);
                     dx_et = d_col_c(sD + d, i, jj, nt, jc, cg);
-                    dy_xi = d_row_c(sD + T::DS + d, T::DW, i, nr, across);
+                    dy_xi = d_row_c(sD + T::DS + d, T::DW, i, nr, across, pb);
                     dy_et = d_col_c(sD + T::DS + d, i, jj, nt, jc, cg);
                 } else {
                     dx_xi = d_row(sD + d, T::DW, i, nr);
@@ -870,7 +878,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const R* row = srow + (ti + T::HM) * RS;
         const R* col = scol + (tj + T::HM) * CS;
         const bool farj = cg && i < nr - 1 && (j == 0 || j == nt - 1);
-        if (i == nr - 1 || farj) {
+        if ((!pb && i == nr - 1) || farj) {
             // far field (Sec. III A 2): inlet where the free stream enters,
             // zero-gradient outlet elsewhere (targets of the previous step);
             // on a C-grid also the outlet columns, inner neighbour along j
@@ -912,7 +920,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
             continue;
         }
-        const bool wall = i == 0 && (!cg || j >= jc);
+        const bool wall = !pb && i == 0 && (!cg || j >= jc);
         // the rear point of a C-grid: its mirrored cell next to the wall has
         // the other side's wall nodes as its element's row 0
         const bool rear = cg && i == 0 && j == jc;
@@ -958,7 +966,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         auto departure = [&](int inode, R dx, R dy, int& base, R& xi, R& eta) -> bool {
             if constexpr (GEN)
                 return depart_gen<R, TJ>(sC, sJ + 4 * dn, inode, j, i0, j0, nr, pi0, sj0, T::PWS, dx, dy, base, xi, eta,
-                                         dup2);
+                                         dup2 || pb, pb);
             else
                 return depart(geo, inode, dx, dy, base, xi, eta);
         };

@@ -314,6 +314,18 @@ def cgrid_case(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: f
                      bodies=[bd], steps=steps, name=name)
 
 
+def box_mesh(ni: int, nj: int, lx: float, ly: float, skew: float = 0.0):
+    """One period of a doubly periodic box: X[i, j] = (i lx/ni + skew j ly/nj,
+    j ly/nj) (a parallelogram box when skew != 0) and its period vectors
+    shift_i = (lx, 0), shift_j = (skew ly, ly)."""
+    i = np.arange(ni)[:, None]
+    j = np.arange(nj)[None, :]
+    X = np.empty((ni, nj, 2))
+    X[..., 0] = i * (lx / ni) + skew * j * (ly / nj)
+    X[..., 1] = j * (ly / nj) + 0.0 * i
+    return X, (lx, 0.0), (skew * ly, ly)
+
+
 def fixed_cylinder_128x64(steps: int = 1000) -> CylinderCase:
     """Fixed cylinder, 128 radial x 64 angular nodes, far field at 20 D,
     Re 100, Ma 0.2 (FP64 parity workload)."""

@@ -33,7 +33,8 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_set_schedule", "lbfsi_batch_get_schedule", "lbfsi_batch_set_graph_steps",
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
             "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy",
-            "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid", "lbfsi_field_ptr"]
+            "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid", "lbfsi_field_ptr",
+            "lbfsi_create_mesh_box"]
 
 
 class LbfsiError(RuntimeError):
@@ -80,6 +81,12 @@ class _DeviceArray:
                                          "version": 3, "strides": None, "stream": None}
         self.owner = owner
         self.row0 = row0
+
+
+class MeshBoxDesc(ctypes.Structure):
+    _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("X", ctypes.POINTER(ctypes.c_double)),
+                ("shift_i", ctypes.c_double * 2), ("shift_j", ctypes.c_double * 2),
+                ("precision", ctypes.c_int), ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
 
 
 class MeshCGridDesc(ctypes.Structure):
@@ -251,6 +258,29 @@ class Mesh:
         h = ctypes.c_void_p()
         self.h = None
         _check(lib.lbfsi_create_mesh_xy(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        return self
+
+    @classmethod
+    def box(cls, X, shift_i, shift_j, nbatch=1, precision=FP64, stream=None):
+        """Handle of a doubly periodic box: node coordinates X [ni, nj, 2] of
+        one period and the period vectors (lbfsi_create_mesh_box); no wall,
+        fixed bodies."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.r = self.e = None
+        self.nr, self.nt = self.X.shape[0], self.X.shape[1]
+        self.N = self.nr * self.nt
+        self.nbatch = int(nbatch)
+        self.precision = precision
+        self._bodies = (BodyDesc * self.nbatch)()
+        d = MeshBoxDesc(self.nr, self.nt, _dptr(self.X), (ctypes.c_double * 2)(*shift_i),
+                        (ctypes.c_double * 2)(*shift_j), precision, self.nbatch, self._bodies)
+        h = ctypes.c_void_p()
+        self.h = None
+        _check(lib.lbfsi_create_mesh_box(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
         self.h = h
         return self
 

@@ -163,3 +163,37 @@ def test_cgrid_struct_layout_and_validation_without_gpu(tmp_path, lib):
     bad[3, 9] += 1e-3
     assert create(bad, 4) == lbfsi.EINVAL
     assert b"subparametric" in lib.lbfsi_last_error()
+
+
+def test_box_struct_layout_and_validation_without_gpu(tmp_path, lib):
+    """lbfsi_mesh_box_desc matches the binding; lbfsi_create_mesh_box rejects,
+    before touching the device, odd sizes, a moving body and a box that is not
+    positively oriented."""
+    import numpy as np
+    from paper_2107_01370_gb300 import inputs, lbfsi
+    src = tmp_path / "bx.c"
+    src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lbfsi_mesh_box_desc),'
+                   'offsetof(lbfsi_mesh_box_desc, shift_i), offsetof(lbfsi_mesh_box_desc, precision),'
+                   'offsetof(lbfsi_mesh_box_desc, bodies));return 0;}\n')
+    exe = tmp_path / "bx"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(lbfsi.MeshBoxDesc), lbfsi.MeshBoxDesc.shift_i.offset,
+                   lbfsi.MeshBoxDesc.precision.offset, lbfsi.MeshBoxDesc.bodies.offset]
+    h = ctypes.c_void_p()
+
+    def create(X, si, sj, dof=0):
+        X = np.ascontiguousarray(X)
+        body = lbfsi.BodyDesc()
+        body.dof = dof
+        body.r_in, body.r_out, body.length, body.m_star, body.v_r = 1.0, 2.0, 1.0, 1.0, 1.0
+        d = lbfsi.MeshBoxDesc(X.shape[0], X.shape[1], X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              (ctypes.c_double * 2)(*si), (ctypes.c_double * 2)(*sj), 0, 1, ctypes.pointer(body))
+        return lib.lbfsi_create_mesh_box(ctypes.byref(d), None, ctypes.byref(h))
+
+    X, si, sj = inputs.box_mesh(8, 6, 8.0, 6.0, skew=0.2)
+    assert create(X[:7], si, sj) == lbfsi.EINVAL                       # odd ni
+    assert create(X, si, sj, dof=1) == lbfsi.EINVAL
+    assert b"fixed" in lib.lbfsi_last_error()
+    assert create(X, si, (0.0, -6.0)) == lbfsi.EINVAL                   # period against the node order
