@@ -337,8 +337,8 @@ def small_case_graphs(stream, steps=1000, graph_steps=100):
 def general_mesh_cases():
     """Two general-mesh workloads (FP32, batch 8 per mesh, inputs above L2):
     an elliptic cylinder on a 512 x 256 O-grid given by node coordinates
-    (1-DOF), and the airfoil-case shape: a 12%-thick elliptic section on a
-    192 x 769 C-grid (147,648 nodes, wake cut 128 nodes per side), 2-DOF
+    (1-DOF), and the airfoil case: a NACA 0012 section on a 192 x 769 C-grid
+    (147,648 nodes, wake cut 128 nodes per side), 2-DOF
     pitch-plunge (m* 100, w_h/w_a 0.3, x_a 1.8, r_a 1.87, V_R 0.5025, elastic
     axis half a chord ahead of the leading edge), Ma 0.8, T_inf 0.2, Re 1e5,
     1 degree forced pitching for two periods then free."""
@@ -351,8 +351,8 @@ def general_mesh_cases():
                            x_alpha=1.8, r_alpha=1.87, wh_wa=0.3, length=1.0,
                            pitch_amp=math.pi / 180.0, forced_periods=2.0)
     cg = inputs.cgrid_case(513, 128, 192, 0.5, 0.06, r_far=10.0, wake=10.0, length=1.0, ma=0.8,
-                           t_inf=0.2, re=1e5, body=body,
-                           name="12% elliptic section C-grid 192x769 (cut 128), 2-DOF, Ma 0.8, forced pitch")
+                           t_inf=0.2, re=1e5, body=body, naca=0.12,
+                           name="NACA 0012 C-grid 192x769 (cut 128), 2-DOF, Ma 0.8, forced pitch")
     return ((ell, lambda prec, nb, st: lbfsi.Mesh.xy(ell.X, ell.bodies * nb, precision=prec, stream=st)),
             (cg, lambda prec, nb, st: lbfsi.Mesh.cgrid(cg.X, cg.n_cut, cg.bodies * nb, precision=prec,
                                                        stream=st)))

@@ -254,8 +254,31 @@ class CGridCase:
         return self.nr * self.ntheta
 
 
+def naca4_thickness(x: np.ndarray, t: float) -> np.ndarray:
+    """Half thickness of a symmetric NACA 4-digit section of chord 1 and
+    thickness ratio t at chord fraction x (the public formula, closed
+    trailing edge: last coefficient -0.1036)."""
+    return 5.0 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+
+
+def naca_wall_chain(n_wall: int, t: float = 0.12) -> np.ndarray:
+    """Open wall chain of a symmetric NACA section of chord 1 centred at the
+    origin, counterclockwise from the trailing edge (0.5, 0) over the upper
+    surface and the leading edge back to the trailing edge: even nodes at
+    chord fractions x = (1 + cos theta)/2, theta = 2 pi m / (n_wall - 1)
+    (clustered at both edges), odd nodes chord midpoints."""
+    th = 2.0 * np.pi * np.arange(n_wall) / (n_wall - 1)
+    xc = 0.5 * (1.0 + np.cos(th))
+    y = naca4_thickness(xc, t) * np.where(th <= np.pi, 1.0, -1.0)
+    W = np.stack([xc - 0.5, y], axis=1)
+    W[1::2] = 0.5 * (W[0:-1:2] + W[2::2])
+    W[0] = (0.5, 0.0)
+    W[-1] = (0.5, 0.0)
+    return W
+
+
 def cgrid_ellipse(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
-                  wake: float = 6.0):
+                  wake: float = 6.0, wall: np.ndarray | None = None):
     """C-grid around an elliptic section (semi-axes a along x, b along y,
     centred at the origin) with a straight wake cut along y = 0 from the rear
     point (a, 0) to x = a + wake.  Row 0, counterclockwise: the upper side of
@@ -275,10 +298,14 @@ def cgrid_ellipse(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far
         raise ValueError("n_cut must be even and >= 4")
     nt = n_wall + 2 * n_cut
     th = 2.0 * np.pi * np.arange(n_wall) / (n_wall - 1)
-    wall = np.stack([a * np.cos(th), b * np.sin(th)], axis=1)
-    wall[1::2] = 0.5 * (wall[0:-1:2] + wall[2::2])
-    wall[0] = (a, 0.0)
-    wall[-1] = (a, 0.0)
+    if wall is None:
+        wall = np.stack([a * np.cos(th), b * np.sin(th)], axis=1)
+        wall[1::2] = 0.5 * (wall[0:-1:2] + wall[2::2])
+        wall[0] = (a, 0.0)
+        wall[-1] = (a, 0.0)
+    else:
+        # another section with its rear point at (a, 0), given as its chain
+        wall = np.asarray(wall, dtype=np.float64)
     first = float(np.hypot(*(wall[2] - wall[0])))
     s = ogrid_radii(n_cut + 1, 0.0, wake, 0.5 * first)       # s[0] = 0 at the rear point
     W = np.empty((nt, 2))
@@ -302,10 +329,15 @@ def cgrid_ellipse(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far
 def cgrid_case(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
                wake: float = 6.0, length: float = 1.0, ma: float = 0.2, re: float = 100.0,
                t_inf: float = 1.0 / 3.0, gamma: float = 1.4, pr: float = 0.71,
-               body: BodySpec | None = None, steps: int = 0, name: str = "") -> CGridCase:
-    """Elliptic section on a C-grid (cgrid_ellipse); time step a third of the
-    smallest row-0 spacing, as for the O-grid cases."""
-    X = cgrid_ellipse(n_wall, n_cut, nr, a, b, r_far=r_far, wake=wake)
+               body: BodySpec | None = None, steps: int = 0, name: str = "",
+               naca: float | None = None) -> CGridCase:
+    """Elliptic section (or, with naca = t, the symmetric NACA 4-digit
+    section of thickness t and chord 2a) on a C-grid (cgrid_ellipse); time
+    step a third of the smallest row-0 spacing, as for the O-grid cases."""
+    wall = None
+    if naca is not None:
+        wall = naca_wall_chain(n_wall, naca) * (2.0 * a)
+    X = cgrid_ellipse(n_wall, n_cut, nr, a, b, r_far=r_far, wake=wake, wall=wall)
     d = np.hypot(*(X[0, 1:] - X[0, :-1]).T)
     first = float(d[d > 0].min())
     flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr, dt=first / 3.0, length=length)

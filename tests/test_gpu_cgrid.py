@@ -173,3 +173,38 @@ def test_cgrid_reports_cfl_violation(L):
         m.synchronize()
     assert ei.value.code == L.EDEPARTURE
     m.close()
+
+
+def _naca_case(nr=32, n_wall=97, n_cut=24, ma=0.8, t_inf=0.2):
+    body = inputs.BodySpec(dof=2, xp=-1.0, yp=0.0, r_in=0.6, r_out=2.0, m_star=100.0, v_r=0.5025,
+                           x_alpha=1.8, r_alpha=1.87, wh_wa=0.3, length=1.0)
+    case = inputs.cgrid_case(n_wall, n_cut, nr, 0.5, 0.06, r_far=6.0, wake=4.0, length=1.0, ma=ma,
+                             t_inf=t_inf, re=1e5, body=body, naca=0.12)
+    u_inf = case.flow.ma * np.sqrt(case.flow.gamma * case.flow.t_inf)
+    w_a = u_inf / (body.v_r * 0.5 * np.sqrt(body.m_star))
+    body.pitch_amp = np.pi / 180.0
+    body.forced_periods = 4.5 * case.flow.dt * w_a / (2.0 * np.pi)
+    return case
+
+
+def test_fp64_naca0012_cgrid_matches_oracle(L):
+    """NACA 0012 (public thickness formula, closed trailing edge) on a C-grid,
+    the airfoil case's flow (Ma 0.8, T_inf 0.2, Re 1e5) and structure (2-DOF,
+    m* 100, w_h/w_a 0.3, x_a 1.8, r_a 1.87, V_R 0.5025), 1-degree forced
+    pitching that ends between steps 4 and 5: the sharp trailing edge is the
+    point where the wall meets the cut."""
+    case = _naca_case()
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=61)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 8, L.FP64)
+    assert field_err(f, r.M) < 1e-12
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+    for k in ("h", "alpha", "hdot", "adot"):
+        assert abs(st[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+
+
+def test_fp32_naca0012_cgrid_within_stated_tolerance(L):
+    case = _naca_case()
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=62)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 30, L.FP32)
+    assert field_err(f, r.M) < 1e-5
+    assert np.abs(ghist - hist).max() < 1e-4 * P_SCALE
