@@ -101,27 +101,35 @@ def far_field_targets(mesh, M_prev, u_inf, rho_inf, T_inf):
 
 # ----- C-grid (reading R29): open wall chain, outlet columns ---------------
 def wall_normals_cgrid(mesh):
-    """Unit normals of the wall nodes of a C-grid (columns jc .. Nj-1-jc of
-    row 0, counterclockwise, out of the body), zero on the cut.  The wall is
-    the open chain of straight edges between its even-offset nodes; its two
-    ends are the same point (the rear point), whose normal is the normalised
-    sum of the first and last edges' normals, as at every even node."""
-    Nj, jc = mesh.Nj, mesh.jc
+    """Unit normals of the wall nodes of a C-grid (its wall chains, each
+    counterclockwise around its body, out of the body), zero on the cut.  A
+    chain is the open polygon of straight edges between its even-offset
+    nodes; interior nodes as on a closed wall.  A chain's end is a junction,
+    one point with the mirrored column's node, which ends the mirrored chain
+    (the same chain for a body that row 0 wraps around): its normal is the
+    normalised sum of the normals of the two edges that meet there."""
+    Nj = mesh.Nj
     P = mesh.X[0]
-    ne = (Nj - 1 - 2 * jc) // 2
-    n_edge = np.empty((ne, 2))
-    for k in range(ne):
-        t = P[jc + 2 * k + 2] - P[jc + 2 * k]
-        n_edge[k] = np.array([t[1], -t[0]]) / np.hypot(t[0], t[1])
+
+    def edge_normal(a, b):
+        t = P[b] - P[a]
+        return np.array([t[1], -t[0]]) / np.hypot(t[0], t[1])
+
     n = np.zeros((Nj, 2))
-    for m in range(Nj - 2 * jc):
-        j = jc + m
-        if m % 2:
-            n[j] = n_edge[m // 2]
-        else:
-            k1 = m // 2 - 1 if m > 0 else ne - 1
-            k2 = m // 2 if m // 2 < ne else 0
-            v = n_edge[k1] + n_edge[k2]
+    for a, b in mesh.walls:
+        for j in range(a, b + 1):
+            m = j - a
+            if m % 2:
+                n[j] = edge_normal(j - 1, j + 1)
+                continue
+            if a < j < b:
+                v = edge_normal(j - 2, j) + edge_normal(j, j + 2)
+            else:
+                # the junction: this chain's end edge and the mirrored chain's
+                k = Nj - 1 - j
+                mine = edge_normal(j, j + 2) if j == a else edge_normal(j - 2, j)
+                other = edge_normal(k - 2, k) if j == a else edge_normal(k, k + 2)
+                v = mine + other
             n[j] = v / np.hypot(v[0], v[1])
     return n
 

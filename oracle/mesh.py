@@ -259,44 +259,72 @@ def periodic_box_mesh(ni, nj, lx, ly, skew=0.0):
 
 
 class CGridMesh(Q2Mesh):
-    """C-grid around one body with a wake cut (the airfoil topology of
-    Sec. IV D; readings R28-R30).  Row 0 runs counterclockwise: the upper side
-    of the cut from the outlet towards the body (j < jc), the wall from its
-    rear point over the upper surface and the front back to the rear point
-    (jc <= j <= Nj-1-jc), then the lower side of the cut out to the outlet.
-    Rows grow away from row 0; columns 0 and Nj-1 are outlet boundaries (not
-    periodic).  Across the cut, row-0 nodes j and Nj-1-j are one point (for
-    j <= jc, the rear point of the wall included), and the mesh continues
-    below row 0 as its mirror: node (-k, c) is node (k, Nj-1-c).  A cell
-    below row 0 is the mirror of a cell of the other side of the cut, and so
-    is its element: all nine nodes of a window that starts below row 0, its
-    row 0 included, are the mirrored ones."""
+    """C-grid with a wake cut (the airfoil topology of Sec. IV D; readings
+    R28-R31).  Row 0 runs counterclockwise around the bodies: cut segments
+    (parts of row 0 that lie on cut lines in the fluid) and wall chains.  With
+    one wall (n_cut given) row 0 is the upper side of the cut from the outlet
+    to the body (j < jc), the wall from its rear point over the upper surface
+    and the front back to the rear point (jc <= j <= Nj-1-jc), then the lower
+    side of the cut; with several bodies in tandem (walls given: inclusive
+    column ranges of the wall chains) the cut also runs along the gaps
+    between the bodies, and a downstream body's wall is split into an upper
+    and a lower chain.  Row 0 is palindromic: its cut nodes j and Nj-1-j are
+    one point, and so are the ends of the wall chains that border the cut
+    (the junctions).  Rows grow away from row 0; columns 0 and Nj-1 are
+    outlet boundaries (not periodic).  Across the cut the mesh continues below
+    row 0 as its mirror: node (-k, c) is node (k, Nj-1-c).  A cell below row 0
+    is the mirror of a cell of the other side, and so is its element: all
+    nine nodes of a window that starts below row 0, its row 0 included, are
+    the mirrored ones."""
 
-    def __init__(self, X, n_cut):
+    def __init__(self, X, n_cut=None, walls=None):
         super().__init__(X, periodic_i=False, periodic_j=False)
         Nj = self.Nj
         if Nj % 2 == 0:
             raise ValueError("a C-grid needs an odd node count along the C")
-        if n_cut < 2 or n_cut % 2 or 2 * n_cut >= Nj - 1:
-            raise ValueError("n_cut must be even, >= 2 and leave a wall of at least 3 nodes")
-        self.jc = int(n_cut)
+        if walls is None:
+            if n_cut is None or n_cut < 2 or n_cut % 2 or 2 * n_cut >= Nj - 1:
+                raise ValueError("n_cut must be even, >= 2 and leave a wall of at least 3 nodes")
+            walls = [(n_cut, Nj - 1 - n_cut)]
+        self.walls = [(int(a), int(b)) for a, b in walls]
+        wall = np.zeros(Nj, dtype=bool)
+        for a, b in self.walls:
+            if a < 1 or b > Nj - 2 or a % 2 or b % 2 or b - a < 2:
+                raise ValueError("wall chains must run between even columns inside the outlets")
+            if np.any(wall[a:b + 1]):
+                raise ValueError("wall chains overlap")
+            wall[a:b + 1] = True
+        if not np.array_equal(wall, wall[::-1]):
+            raise ValueError("the cut and the wall chains must be symmetric in j -> Nj-1-j")
+        self.wall_mask = wall
+        cut = ~wall
+        jj = np.arange(Nj)
+        nb_cut = np.zeros(Nj, dtype=bool)
+        nb_cut[1:] |= cut[:-1]
+        nb_cut[:-1] |= cut[1:]
+        self.junction = wall & nb_cut
+        # one wall: jc is the first copy of the rear point
+        self.jc = self.walls[0][0] if len(self.walls) == 1 else None
         scale = float(np.max(np.abs(self.X)))
-        for j in range(self.jc + 1):
+        for j in np.nonzero(cut | self.junction)[0]:
             if np.max(np.abs(self.X[0, j] - self.X[0, Nj - 1 - j])) > 1e-12 * scale:
                 raise ValueError("row-0 nodes j and Nj-1-j must coincide along the cut")
+        # a junction's one-sided derivative along j points to its cut neighbour
+        self.junction_dir = np.zeros(Nj, dtype=np.int64)
+        for j in np.nonzero(self.junction)[0]:
+            self.junction_dir[j] = -1 if (j > 0 and cut[j - 1]) else 1
 
     # ----- node sets ------------------------------------------------------
     def cut_columns(self):
-        j = np.arange(self.Nj)
-        return (j < self.jc) | (j > self.Nj - 1 - self.jc)
+        return ~self.wall_mask
 
     def wall_columns(self):
-        return ~self.cut_columns()
+        return self.wall_mask.copy()
 
     def duplicate_columns(self):
         """Row-0 columns whose node is a second copy of node (0, Nj-1-j): the
-        lower side of the cut and the rear point's second copy."""
-        return np.arange(self.Nj) >= self.Nj - 1 - self.jc
+        cut and junction columns past the middle of row 0."""
+        return (self.cut_columns() | self.junction) & (np.arange(self.Nj) > (self.Nj - 1) // 2)
 
     # ----- window nodes through the cut ------------------------------------
     def window_node(self, wa, wb, a, b):
@@ -335,24 +363,25 @@ class CGridMesh(Q2Mesh):
     # ----- gradients: central across the cut --------------------------------
     def _d_rows(self, F):
         """Derivative along i (reading R18) with the cut: at the row-0 cut
-        nodes and at the two copies of the rear point, the central difference
-        with the mirrored row below, (F(1, j) - F(1, Nj-1-j)) / 2; one-sided
-        on the rest of the wall (reading R30)."""
+        nodes and at the junctions (both copies), the central difference with
+        the mirrored row below, (F(1, j) - F(1, Nj-1-j)) / 2; one-sided on the
+        rest of the wall (reading R30)."""
         d = self._d_index(F, F.ndim - 2, False, None)
-        jc, Nj = self.jc, self.Nj
-        c = np.nonzero(self.cut_columns() | np.isin(np.arange(Nj), (jc, Nj - 1 - jc)))[0]
+        Nj = self.Nj
+        c = np.nonzero(self.cut_columns() | self.junction)[0]
         d[..., 0, c] = 0.5 * (F[..., 1, c] - F[..., 1, Nj - 1 - c])
         return d
 
     def _d_cols(self, F):
-        """Derivative along j: central, one-sided on the outlet columns; at
-        the rear point (reading R30) one-sided along the cut, the nodes both
-        copies share: backward at j = jc, forward at j = Nj-1-jc."""
+        """Derivative along j: central, one-sided on the outlet columns; at a
+        junction (reading R30) one-sided along the cut, the nodes both copies
+        share: backward where the cut lies before it, forward where after."""
         d = self._d_index(F, F.ndim - 1, False, None)
-        jc, Nj = self.jc, self.Nj
-        d[..., 0, jc] = 0.5 * (3.0 * F[..., 0, jc] - 4.0 * F[..., 0, jc - 1] + F[..., 0, jc - 2])
-        k = Nj - 1 - jc
-        d[..., 0, k] = 0.5 * (-3.0 * F[..., 0, k] + 4.0 * F[..., 0, k + 1] - F[..., 0, k + 2])
+        for k in np.nonzero(self.junction)[0]:
+            if self.junction_dir[k] < 0:
+                d[..., 0, k] = 0.5 * (3.0 * F[..., 0, k] - 4.0 * F[..., 0, k - 1] + F[..., 0, k - 2])
+            else:
+                d[..., 0, k] = 0.5 * (-3.0 * F[..., 0, k] + 4.0 * F[..., 0, k + 1] - F[..., 0, k + 2])
         return d
 
     def metrics(self):

@@ -252,13 +252,12 @@ class Solver:
         copies (j <= jc) after the propagation and after the collision."""
         mesh, dt, Cv = self.mesh, self.dt, self.Cv
         X = mesh.X
-        Ni, Nj, jc = mesh.Ni, mesh.Nj, mesh.jc
+        Ni, Nj = mesh.Ni, mesh.Nj
         far = boundary.far_field_mask_cgrid(mesh)
         wall = np.zeros((Ni, Nj), dtype=bool)
         wall[0] = mesh.wall_columns()
         dup = np.nonzero(mesh.duplicate_columns())[0]
         own = Nj - 1 - dup
-        wcols = np.nonzero(mesh.wall_columns())[0]
         # 1. kinematics
         F = ale.deformation_gradient(X, self.bodies, self.S)
         VG = ale.mesh_velocity(X, self.bodies, self.S, self.S_prev, dt)
@@ -317,15 +316,20 @@ class Solver:
         g_post = np.where(far[None], g_far, g_post)
         f_post[:, 0, dup] = f_post[:, 0, own]
         g_post[:, 0, dup] = g_post[:, 0, own]
-        # 7. force and moment on the wall chain
+        # 7. force and moment on the wall chains (summed: the bodies of a
+        # C-grid move as one, reading R31)
         force = (0.0, 0.0, 0.0)
         if self.bodies:
             b, st = self.bodies[0], self.S[0]
-            sxx, sxy, syy = forces.node_stress(f_pre[:, 0, wcols], g_pre[:, 0, wcols], Cv,
-                                               self.mu, dt, self.Pr)
-            x_wall = ale.mesh_position(X[0, wcols], self.bodies, self.S)
             x_ref = np.array([b["xp"], b["yp"] + st["h"]])
-            force = forces.wall_force(x_wall, sxx, sxy, syy, x_ref, closed=False)
+            tot = np.zeros(3)
+            for a_, b_ in mesh.walls:
+                cols = np.arange(a_, b_ + 1)
+                sxx, sxy, syy = forces.node_stress(f_pre[:, 0, cols], g_pre[:, 0, cols], Cv,
+                                                   self.mu, dt, self.Pr)
+                x_wall = ale.mesh_position(X[0, cols], self.bodies, self.S)
+                tot += np.array(forces.wall_force(x_wall, sxx, sxy, syy, x_ref, closed=False))
+            force = tuple(float(v) for v in tot)
         # 8. structural update
         new_S = self._advance_bodies(force)
         self.S_prev = [dict(s) for s in self.S]

@@ -326,6 +326,95 @@ def cgrid_ellipse(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far
     return W[None, :, :] + t[:, None, None] * (C - W)[None, :, :]
 
 
+def tandem_cgrid(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *, spacing: float = 4.0,
+                 radius: float = 0.5, envelope: float = 1.0, r_far: float = 6.0, wake: float = 6.0,
+                 n_inner: int = 8):
+    """C-grid around two circular cylinders in tandem (centres (0, 0) and
+    (spacing, 0)), the cut along y = 0 through the gap and the wake.  Row 0,
+    upper half (then mirrored): the wake from the outlet to the rear body's
+    rear point (n_wake nodes), the rear body's upper half from its rear to its
+    front point (n_rear nodes, odd), the gap (n_gap nodes strictly between the
+    bodies), the front body from its rear point to its front (n_front nodes;
+    the middle column of row 0 is its front).  Returns X [nr, nt, 2] and the
+    wall chains as inclusive column ranges: the rear body's upper and lower
+    halves and the front body.  Grid lines are straight in two stages, kinked
+    at row n_inner on an envelope y = +-envelope (around the front body an arc
+    about its rear point): from the gap they fan from 45 degrees towards the
+    rear body's front to 45 degrees away from the front body's rear (so they
+    do not cross below the envelope), from the rear body's surface they reach
+    the envelope above the same angle, beyond it they continue at 45 degrees
+    (radially around the front), so no two lines cross and none leaves a
+    wall tangentially.  Subparametric: odd rows and columns at midpoints."""
+    r, L, h = radius, spacing, envelope
+    if n_rear % 2 == 0 or n_wake % 2 or n_gap % 2 == 0 or n_inner % 2:
+        raise ValueError("n_rear and n_gap odd, n_wake and n_inner even")
+    th_f = np.pi * np.arange(n_front) / (n_front - 1)
+    th_r = np.pi * np.arange(n_rear) / (n_rear - 1)
+    first = r * (th_f[2] - th_f[0])
+    s = ogrid_radii(n_wake + 1, 0.0, wake, 2.0 * first)
+    W, E = [], []
+    for x in (L + r + s[1:])[::-1]:
+        W.append((x, 0.0))
+        E.append((x + h, h))
+    for t in th_r:
+        W.append((L + r * np.cos(t), r * np.sin(t)))
+        E.append((L + (r + h) * np.cos(t), h))
+    for x in np.linspace(L - r, r, n_gap + 2)[1:-1]:
+        f = (x - r) / (L - 2.0 * r)
+        W.append((x, 0.0))
+        E.append((x + h * (1.0 - 2.0 * f), h))
+    for t in th_f:
+        W.append((r * np.cos(t), r * np.sin(t)))
+        psi = 0.25 * np.pi + 0.75 * t
+        E.append((r + np.sqrt(2.0) * h * np.cos(psi), np.sqrt(2.0) * h * np.sin(psi)))
+    W = np.array(W)
+    E = np.array(E)
+    up = W.shape[0]
+    nt = 2 * up - 1
+    flip = np.array([1.0, -1.0])
+    Wf = np.concatenate([W, (W[:-1] * flip)[::-1]])
+    Ef = np.concatenate([E, (E[:-1] * flip)[::-1]])
+    C = np.empty((nt, 2))
+    for j in range(nt):
+        e = Ef[j]
+        if abs(e[1]) >= h - 1e-12 and e[0] >= r + h - 1e-12:
+            C[j] = (e[0] + (r_far - h), np.sign(e[1]) * r_far)
+        else:
+            d = e - np.array([r, 0.0])
+            C[j] = np.array([r, 0.0]) + d / np.hypot(d[0], d[1]) * np.sqrt(2.0) * r_far
+    for A in (Wf, Ef, C):
+        A[1::2] = 0.5 * (A[0:-1:2] + A[2::2])
+    t1 = radial_fractions(n_inner + 1, 0.05)
+    t2 = radial_fractions(nr - n_inner, 0.02)
+    X = np.empty((nr, nt, 2))
+    for i in range(n_inner + 1):
+        X[i] = Wf + t1[i] * (Ef - Wf)
+    for i in range(n_inner, nr):
+        X[i] = Ef + t2[i - n_inner] * (C - Ef)
+    a_r = n_wake
+    b_r = n_wake + n_rear - 1
+    a_f = b_r + n_gap + 1
+    walls = [(a_r, b_r), (a_f, nt - 1 - a_f), (nt - 1 - b_r, nt - 1 - a_r)]
+    return X, walls
+
+
+def tandem_case(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *, spacing: float = 4.0,
+                ma: float = 0.2, re: float = 100.0, t_inf: float = 1.0 / 3.0, gamma: float = 1.4,
+                pr: float = 0.71, body: BodySpec | None = None, steps: int = 0, name: str = "") -> CGridCase:
+    """Two cylinders of diameter 1 in tandem on a C-grid (tandem_cgrid); the
+    time step a third of the smallest row-0 spacing.  The case's n_cut is
+    None; its walls give the chains."""
+    X, walls = tandem_cgrid(n_front, n_rear, n_gap, n_wake, nr, spacing=spacing)
+    d = np.hypot(*(X[0, 1:] - X[0, :-1]).T)
+    first = float(d[d > 0].min())
+    flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr, dt=first / 3.0, length=1.0)
+    bd = body if body is not None else BodySpec(dof=0)
+    c = CGridCase(nr=nr, ntheta=X.shape[1], n_cut=None, X=X, centre=(0.0, 0.0), flow=flow, bodies=[bd],
+                  steps=steps, name=name)
+    c.walls = walls
+    return c
+
+
 def cgrid_case(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
                wake: float = 6.0, length: float = 1.0, ma: float = 0.2, re: float = 100.0,
                t_inf: float = 1.0 / 3.0, gamma: float = 1.4, pr: float = 0.71,

@@ -184,3 +184,102 @@ def test_mirror_symmetric_flow_stays_symmetric():
     assert abs(r.force[1]) < 1e-12 and abs(r.force[2]) < 1e-12
     # the lower copies of the cut nodes hold the upper copies' values
     assert np.array_equal(r.M[:, 0, nt - 1 - jc:], r.M[:, 0, :jc + 1][:, ::-1])
+
+
+# ----- several wall chains: two cylinders in tandem (reading R31) ---------
+def _tandem(nr=17):
+    return inputs.tandem_cgrid(34, 17, 11, 16, nr)
+
+
+def test_tandem_mesh_chains_and_normals():
+    X, walls = _tandem()
+    nt = X.shape[1]
+    assert walls == [(16, 32), (44, nt - 1 - 44), (nt - 1 - 32, nt - 1 - 16)]
+    m = OM.CGridMesh(X, walls=walls)
+    x_xi, y_xi, x_eta, y_eta = m.metrics()
+    assert np.all(x_xi * y_eta - y_xi * x_eta > 0)
+    n = OB.wall_normals_cgrid(m)
+    for (a, b), c in zip(walls, ((4.0, 0.0), (0.0, 0.0), (4.0, 0.0))):
+        cols = np.arange(a, b + 1)
+        assert np.allclose(np.hypot(n[cols, 0], n[cols, 1]), 1.0, atol=1e-14)
+        out = X[0, cols] - np.array(c)
+        assert np.all(np.sum(n[cols] * out, axis=1) > 0)        # out of each cylinder
+    # junctions: the rear points face downstream, the rear body's front upstream
+    assert np.allclose(n[16], [1.0, 0.0], atol=1e-14) and np.allclose(n[44], [1.0, 0.0], atol=1e-14)
+    assert np.allclose(n[32], [-1.0, 0.0], atol=1e-14)
+    assert m.junction_dir[16] == -1 and m.junction_dir[32] == 1 and m.junction_dir[44] == -1
+    # the one-chain form of the constructor is the single C-grid
+    Xc = inputs.cgrid_ellipse(17, 4, 9, 0.6, 0.35, r_far=4.0, wake=3.0)
+    a1, a2 = OM.CGridMesh(Xc, 4), OM.CGridMesh(Xc, walls=[(4, Xc.shape[1] - 5)])
+    assert np.array_equal(a1.junction, a2.junction) and np.array_equal(a1.metrics()[0], a2.metrics()[0])
+
+
+def test_tandem_forces_closed_forms():
+    """Summed over the three chains: zero for a uniform stress; -(A_f + A_r) a
+    for a linear pressure a . x (both cylinders' polygon areas)."""
+    X, walls = _tandem()
+    P0 = X[0]
+    a = np.array([0.4, -0.25])
+    tot_u = np.zeros(3)
+    tot_p = np.zeros(3)
+    for s_, e_ in walls:
+        P = P0[s_:e_ + 1]
+        k = P.shape[0]
+        tot_u += OF.wall_force(P, np.full(k, -2.0), np.full(k, 0.3), np.full(k, -0.7), np.zeros(2),
+                               closed=False)
+        p = P @ a
+        tot_p += OF.wall_force(P, -p, np.zeros(k), -p, np.zeros(2), closed=False)
+    assert np.abs(tot_u).max() < 1e-13
+
+    def area(V):
+        return 0.5 * np.sum(V[:, 0] * np.roll(V[:, 1], -1) - np.roll(V[:, 0], -1) * V[:, 1])
+
+    (r0, r1), (f0, f1), (l0, l1) = walls
+    A_front = area(P0[f0:f1 + 1:2][:-1])
+    A_rear = area(np.concatenate([P0[r0:r1 + 1:2], P0[l0:l1 + 1:2][1:-1]]))
+    assert abs(tot_p[0] + (A_front + A_rear) * a[0]) < 1e-13
+    assert abs(tot_p[1] + (A_front + A_rear) * a[1]) < 1e-13
+
+
+def test_tandem_linear_fields_reproduced_across_the_gap():
+    """Points around the gap's and the wake's cut nodes, many of them in the
+    mirrored cells below row 0, interpolate a linear field exactly (it lies in
+    the Q2 space of every bilinear element); a window read one column off
+    below row 0 does not."""
+    X, walls = _tandem()
+    m = OM.CGridMesh(X, walls=walls)
+    field = 0.3 + 1.7 * X[..., 0] - 0.9 * X[..., 1]
+    cut = [j for j in range(1, (X.shape[1] - 1) // 2) if m.cut_columns()[j]]
+    ghost = 0
+    for j in cut:
+        h = 0.3 * abs(X[1, j, 1])
+        for ang in np.linspace(0.0, 2.0 * np.pi, 12, endpoint=False):
+            P = X[0, j] + h * np.array([np.cos(ang), np.sin(ang)])
+            wa, wb, xi, eta, found = m.locate(P[None], np.array([0]), np.array([j]))
+            assert found[0], (j, ang)
+            ghost += int(wa[0] < 0)
+            v = m.interpolate(field, wa, wb, xi, eta)[0]
+            assert abs(v - (0.3 + 1.7 * P[0] - 0.9 * P[1])) < 1e-12
+    assert ghost > 0
+
+
+def test_tandem_symmetric_flow_stays_symmetric():
+    X, walls = _tandem(nr=13)
+    nt = X.shape[1]
+    flow = inputs.FlowSpec(ma=0.2, re=100.0, dt=float(np.hypot(*(X[0, 45] - X[0, 44]))) / 3.0)
+    case = inputs.CGridCase(nr=X.shape[0], ntheta=nt, n_cut=None, X=X, centre=(0.0, 0.0), flow=flow,
+                            bodies=[inputs.BodySpec(dof=0)])
+    M0 = inputs.initial_field(case.nr, nt, flow, noise=1e-2, seed=9)
+    M = M0.copy()
+    M[0] = 0.5 * (M0[0] + M0[0, :, ::-1])
+    M[1] = 0.5 * (M0[1] + M0[1, :, ::-1])
+    M[2] = 0.5 * (M0[2] - M0[2, :, ::-1])
+    M[3] = 0.5 * (M0[3] + M0[3, :, ::-1])
+    m = OM.CGridMesh(X, walls=walls)
+    M[2, 0, m.cut_columns() | m.junction] = 0.0
+    s = OS.Solver.from_case(m, case, M)
+    for _ in range(4):
+        r = s.step()
+    f = r.f_post
+    assert np.abs(f - f[REFLECT][:, :, ::-1]).max() < 1e-12 * np.abs(f).max()
+    assert abs(r.force[1]) < 1e-12 and abs(r.force[2]) < 1e-12
