@@ -185,6 +185,35 @@ typedef struct {
  * moving body. */
 int lbfsi_create_mesh_box(const lbfsi_mesh_box_desc* d, void* cuda_stream, lbfsi_mesh* out);
 
+/* A C-grid around several bodies (bodies in tandem: the cut runs along the
+ * gaps and the wake), given by its node coordinates as in
+ * lbfsi_mesh_cgrid_desc and its wall chains: walls[2 k], walls[2 k + 1] are
+ * the first and last row-0 column of chain k (even, inside the outlet
+ * columns, not overlapping), counterclockwise around its body; every other
+ * row-0 column is on the cut.  The layout must be symmetric in
+ * j -> ntheta-1-j, the cut nodes and the chains' ends (the junctions) one
+ * point with their mirrors.  A body that row 0 wraps around is one chain
+ * (the single C-grid: walls = {n_cut, ntheta-1-n_cut}); a body downstream of
+ * another is an upper and a lower chain.  The load of a solve is the sum
+ * over all chains, so all walls belong to the solve's one body: rigidly
+ * linked bodies (its rigid zone must contain every wall). */
+typedef struct {
+    int nr, ntheta;             /* nr >= 5; ntheta odd >= 7 */
+    int nwalls;                 /* wall chains, >= 1 */
+    const int* walls;           /* [nwalls][2] inclusive column ranges (host, borrowed) */
+    const double* X;            /* [nr][ntheta][2] node coordinates (host, borrowed) */
+    double xc, yc;              /* mesh centre (reference point of the geometry)   */
+    int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations             */
+    int nbatch;                 /* independent solves sharing the mesh, >= 1        */
+    const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)      */
+} lbfsi_mesh_cgrid_walls_desc;
+
+/* Create a mesh handle on a C-grid with several wall chains; otherwise as
+ * lbfsi_create_mesh_cgrid.  LBFSI_EINVAL for chains with odd ends, outside
+ * the outlets or overlapping, an asymmetric layout, cut or junction nodes
+ * that do not coincide with their mirrors, or a bad mesh. */
+int lbfsi_create_mesh_cgrid_walls(const lbfsi_mesh_cgrid_walls_desc* d, void* cuda_stream, lbfsi_mesh* out);
+
 /* Create a mesh handle on a C-grid; otherwise as lbfsi_create_mesh_xy (one
  * tile shape).  A step is two launches here: the collision of step k into a
  * post-collision buffer, then the stream of step k + 1 from it.

@@ -61,17 +61,22 @@ def rigid_displacement(X, body, state):
     return gx - X[..., 0], gy - X[..., 1]
 
 
-def mesh_position(X, bodies, states):
-    """x = X + sum_b (1 - r_b)(G'_b(X) - X)."""
-    x = X.copy()
+def mesh_displacement(X, bodies, states):
+    """x - X = sum_b (1 - r_b)(G'_b(X) - X)."""
+    d = np.zeros_like(X)
     for body, st in zip(bodies, states):
         if body["dof"] == 0:
             continue
         _, rb, _, _ = blend(X, body)
         ux, uy = rigid_displacement(X, body, st)
-        x[..., 0] = x[..., 0] + (1.0 - rb) * ux
-        x[..., 1] = x[..., 1] + (1.0 - rb) * uy
-    return x
+        d[..., 0] = d[..., 0] + (1.0 - rb) * ux
+        d[..., 1] = d[..., 1] + (1.0 - rb) * uy
+    return d
+
+
+def mesh_position(X, bodies, states):
+    """x = X + sum_b (1 - r_b)(G'_b(X) - X)."""
+    return X + mesh_displacement(X, bodies, states)
 
 
 def deformation_gradient(X, bodies, states):
@@ -99,10 +104,12 @@ def deformation_gradient(X, bodies, states):
 
 def mesh_velocity(X, bodies, states, states_prev, dt):
     """V_G = (x^n - x^{n-1}) / dt: first-order backward difference of the
-    blended map in time at fixed X (Sec. II D; reading R4)."""
-    xn = mesh_position(X, bodies, states)
-    xp = mesh_position(X, bodies, states_prev)
-    return (xn - xp) / dt
+    blended map in time at fixed X (Sec. II D; reading R4), formed as the
+    difference of the two displacements x - X, the same quantity without
+    the round-off of X itself (which 1/dt would amplify)."""
+    dn = mesh_displacement(X, bodies, states)
+    dp = mesh_displacement(X, bodies, states_prev)
+    return (dn - dp) / dt
 
 
 def inverse2(F):

@@ -159,9 +159,10 @@ void compact_rows(const lbfsi::HostMesh& h, const double* dev, double* user, siz
 void unify_cut_copies(const lbfsi::HostMesh& h, double* user, size_t blocks, int w) {
     if (!h.cgrid) return;
     for (size_t b = 0; b < blocks; ++b)
-        for (int j = 0; j <= h.jc; ++j)
-            for (int c = 0; c < w; ++c)
-                user[(b * h.N + (size_t)(h.nt - 1 - j)) * w + c] = user[(b * h.N + (size_t)j) * w + c];
+        for (int j = 0; j < h.nt; ++j)
+            if (h.coltype[j] & lbfsi::CT_DUP)
+                for (int c = 0; c < w; ++c)
+                    user[(b * h.N + (size_t)j) * w + c] = user[(b * h.N + (size_t)(h.nt - 1 - j)) * w + c];
 }
 
 // One coupled step of every solve: one launch (collide of step k, stream of
@@ -343,7 +344,22 @@ int lbfsi_create_mesh_cgrid(const lbfsi_mesh_cgrid_desc* d, void* cuda_stream, l
     int rc = check_common(d->nr + lbfsi::CGRID_GHOST_ROWS, d->ntheta, d->precision, d->nbatch, d->bodies, out);
     if (rc) return rc;
     auto m = new lbfsi_mesh_s();
-    rc = lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->n_cut, d->X, d->xc, d->yc, m->host);
+    const int walls[2] = {d->n_cut, d->ntheta - 1 - d->n_cut};
+    rc = lbfsi::build_host_mesh_c(d->nr, d->ntheta, 1, walls, d->X, d->xc, d->yc, m->host);
+    if (rc) {
+        delete m;
+        return rc;
+    }
+    return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
+}
+
+int lbfsi_create_mesh_cgrid_walls(const lbfsi_mesh_cgrid_walls_desc* d, void* cuda_stream, lbfsi_mesh* out) {
+    g_last_error.clear();
+    if (!d) return fail(LBFSI_EINVAL, "null argument");
+    int rc = check_common(d->nr + lbfsi::CGRID_GHOST_ROWS, d->ntheta, d->precision, d->nbatch, d->bodies, out);
+    if (rc) return rc;
+    auto m = new lbfsi_mesh_s();
+    rc = lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->nwalls, d->walls, d->X, d->xc, d->yc, m->host);
     if (rc) {
         delete m;
         return rc;

@@ -157,7 +157,8 @@ bool same_mesh_xy(const lbfsi::HostMesh& h, const lbfsi_solve_xy_desc& d) {
 
 bool same_mesh_c(const lbfsi::HostMesh& h, const lbfsi_solve_cgrid_desc& d) {
     // the stored coordinates carry the mirrored rows before row 0
-    return h.cgrid && h.nr == d.nr && h.nt == d.ntheta && h.jc == d.n_cut && h.xm == d.xc && h.ym == d.yc &&
+    return h.cgrid && h.nr == d.nr && h.nt == d.ntheta && h.walls.size() == 2 && h.walls[0] == d.n_cut &&
+           h.xm == d.xc && h.ym == d.yc &&
            std::memcmp(h.X.data() + 2 * (size_t)h.G * h.nt, d.X, sizeof(double) * 2 * (size_t)d.nr * d.ntheta) == 0;
 }
 
@@ -524,7 +525,8 @@ int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_
         // the two copies of a cut node start from the first copy's values;
         // the mirrored rows below row 0 from their nodes
         for (int c = 0; c < 4; ++c)
-            for (int j = 0; j <= h.jc; ++j) M[c * N + (size_t)(h.nt - 1 - j)] = M[c * N + (size_t)j];
+            for (int j = 0; j < h.nt; ++j)
+                if (h.coltype[j] & lbfsi::CT_DUP) M[c * N + (size_t)j] = M[c * N + (size_t)(h.nt - 1 - j)];
         std::vector<double> Mx(4 * Nx);
         for (int c = 0; c < 4; ++c) {
             std::memcpy(&Mx[c * Nx + g0], &M[c * N], N * sizeof(double));
@@ -603,7 +605,8 @@ int lbfsi_batch_add_cgrid(lbfsi_batch b, const lbfsi_solve_cgrid_desc* d, int* s
         return acquire_mesh(
             b, [&](const lbfsi::HostMesh& h) { return same_mesh_c(h, *d); },
             [&](lbfsi::HostMesh& h) {
-                return lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->n_cut, d->X, d->xc, d->yc, h);
+                const int walls[2] = {d->n_cut, d->ntheta - 1 - d->n_cut};
+                return lbfsi::build_host_mesh_c(d->nr, d->ntheta, 1, walls, d->X, d->xc, d->yc, h);
             },
             mk);
     };

@@ -250,63 +250,98 @@ int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, Ho
     return LBFSI_OK;
 }
 
-// Wall geometry of a C-grid: the open chain of row-0 columns jc .. nt-1-jc
-// (counterclockwise, straight edges between its even-offset nodes), whose two
-// ends are the rear point.  Normals as on a closed wall; the first copy of
-// the rear point takes the Simpson shares of both end edges, the second copy
-// none (its values are the first copy's).
-static void wall_geometry_chain(HostMesh& m) {
-    const int nt = m.nt, jc = m.jc, ne = (nt - 1 - 2 * jc) / 2;
+// Wall geometry of a C-grid: open chains of straight edges between their
+// even-offset nodes, counterclockwise around each body.  Interior nodes as
+// on a closed wall; a chain's end is a junction, one point with the mirrored
+// column's node, which ends the mirrored chain (the same chain for a body
+// that row 0 wraps around): its normal is the normalised sum of the normals
+// of the two edges that meet there, and the first copy carries the Simpson
+// shares of both edges (the second copy none: its values are the first's).
+static void wall_geometry_chains(HostMesh& m) {
+    const int nt = m.nt;
     const std::vector<double>& X = m.xw;
-    std::vector<double> en(2 * ne), ds(ne);
-    for (int k = 0; k < ne; ++k) {
-        const int a = jc + 2 * k, c = a + 2;
+    auto edge = [&](int a, int c, double& L, double& nx, double& ny) {
         const double tx = X[2 * c] - X[2 * a], ty = X[2 * c + 1] - X[2 * a + 1];
-        const double L = std::sqrt(tx * tx + ty * ty);
-        ds[k] = L;
-        en[2 * k] = ty / L;
-        en[2 * k + 1] = -tx / L;
-    }
+        L = std::sqrt(tx * tx + ty * ty);
+        nx = ty / L;
+        ny = -tx / L;
+    };
     m.n0.assign(2 * nt, 0.0);
     m.wall_geo.assign(6 * nt, 0.0);
-    for (int mm = 0; mm < nt - 2 * jc; ++mm) {
-        const int j = jc + mm;
-        double* g = &m.wall_geo[6 * j];
-        if (mm % 2) {
-            const int k = mm / 2;
-            m.n0[2 * j] = en[2 * k];
-            m.n0[2 * j + 1] = en[2 * k + 1];
-            g[0] = 4.0 / 6.0 * ds[k];
-            g[1] = en[2 * k];
-            g[2] = en[2 * k + 1];
-            continue;
+    for (size_t w = 0; w + 1 < m.walls.size(); w += 2) {
+        const int a = m.walls[w], b = m.walls[w + 1];
+        for (int j = a; j <= b; ++j) {
+            double* g = &m.wall_geo[6 * j];
+            double L1, x1, y1, L2, x2, y2;
+            if ((j - a) % 2) {
+                edge(j - 1, j + 1, L1, x1, y1);
+                m.n0[2 * j] = x1;
+                m.n0[2 * j + 1] = y1;
+                g[0] = 4.0 / 6.0 * L1;
+                g[1] = x1;
+                g[2] = y1;
+                continue;
+            }
+            if (a < j && j < b) {
+                edge(j, j + 2, L1, x1, y1);
+                edge(j - 2, j, L2, x2, y2);
+            } else {
+                const int k = nt - 1 - j;   // the mirrored copy of this junction
+                if (j == a) {
+                    edge(j, j + 2, L1, x1, y1);
+                    edge(k - 2, k, L2, x2, y2);
+                } else {
+                    edge(j - 2, j, L1, x1, y1);
+                    edge(k, k + 2, L2, x2, y2);
+                }
+            }
+            const double vx = x1 + x2, vy = y1 + y2, L = std::sqrt(vx * vx + vy * vy);
+            m.n0[2 * j] = vx / L;
+            m.n0[2 * j + 1] = vy / L;
+            if (m.coltype[j] & CT_DUP) continue;
+            g[0] = L1 / 6.0;
+            g[1] = x1;
+            g[2] = y1;
+            g[3] = L2 / 6.0;
+            g[4] = x2;
+            g[5] = y2;
         }
-        const int k1 = mm > 0 ? mm / 2 - 1 : ne - 1, k2 = mm / 2 < ne ? mm / 2 : 0;
-        const double vx = en[2 * k1] + en[2 * k2], vy = en[2 * k1 + 1] + en[2 * k2 + 1];
-        const double L = std::sqrt(vx * vx + vy * vy);
-        m.n0[2 * j] = vx / L;
-        m.n0[2 * j + 1] = vy / L;
-        if (j == nt - 1 - jc) continue;   // second copy of the rear point
-        g[0] = ds[k2] / 6.0;
-        g[1] = en[2 * k2];
-        g[2] = en[2 * k2 + 1];
-        g[3] = ds[k1] / 6.0;
-        g[4] = en[2 * k1];
-        g[5] = en[2 * k1 + 1];
     }
 }
 
-int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, double yc, HostMesh& m) {
+int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double* X, double xc, double yc,
+                      HostMesh& m) {
     if (nr < 5) return set_error(LBFSI_EINVAL, "nr must be >= 5");
     if (nt < 7 || nt % 2 == 0) return set_error(LBFSI_EINVAL, "a C-grid needs an odd node count (>= 7) along the C");
-    if (n_cut < 2 || n_cut % 2 || 2 * n_cut > nt - 4)
-        return set_error(LBFSI_EINVAL, "n_cut must be even and >= 2 and leave a wall of at least 3 nodes");
-    if (!X) return set_error(LBFSI_EINVAL, "null coordinate pointer");
+    if (!X || !walls) return set_error(LBFSI_EINVAL, "null coordinate or wall pointer");
+    if (nwalls < 1) return set_error(LBFSI_EINVAL, "a C-grid needs at least one wall chain");
     const int G = CGRID_GHOST_ROWS;
     if (nr < G + 1) return set_error(LBFSI_EINVAL, "a C-grid needs nr > 4");
+    // column classes: wall chains (even ends inside the outlets, no overlap),
+    // cut elsewhere, symmetric in j -> nt-1-j
+    m.coltype.assign(nt, CT_CUT);
+    m.walls.assign(walls, walls + 2 * (size_t)nwalls);
+    for (int w = 0; w < nwalls; ++w) {
+        const int a = walls[2 * w], b = walls[2 * w + 1];
+        if (a < 1 || b > nt - 2 || a % 2 || b % 2 || b - a < 2)
+            return set_error(LBFSI_EINVAL, "wall chains must run between even columns inside the outlets");
+        for (int j = a; j <= b; ++j) {
+            if (m.coltype[j] & CT_WALL) return set_error(LBFSI_EINVAL, "wall chains overlap");
+            m.coltype[j] = CT_WALL;
+        }
+    }
+    for (int j = 0; j < nt; ++j)
+        if (m.coltype[j] != m.coltype[nt - 1 - j])
+            return set_error(LBFSI_EINVAL, "the cut and the wall chains must be symmetric in j -> ntheta-1-j");
+    for (int j = 0; j < nt; ++j) {
+        if (!(m.coltype[j] & CT_WALL)) continue;
+        const bool before = j > 0 && (m.coltype[j - 1] & CT_CUT), after = j < nt - 1 && (m.coltype[j + 1] & CT_CUT);
+        if (before || after) m.coltype[j] |= CT_JUNC | (before ? 0 : CT_JFWD);
+    }
+    for (int j = (nt - 1) / 2 + 1; j < nt; ++j)
+        if (m.coltype[j] & (CT_CUT | CT_JUNC)) m.coltype[j] |= CT_DUP;
     m.general = true;
     m.cgrid = true;
-    m.jc = n_cut;
     m.G = G;
     m.nr = nr;
     m.nt = nt;
@@ -322,10 +357,12 @@ int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, dou
         scale = std::max(scale, std::fabs(v));
     }
     auto P = [&](int i, int j, int c) { return Xu[2 * ((size_t)i * nt + j) + c]; };
-    for (int j = 0; j <= n_cut; ++j)
-        for (int c = 0; c < 2; ++c)
-            if (std::fabs(P(0, j, c) - P(0, nt - 1 - j, c)) > 1e-12 * scale)
-                return set_error(LBFSI_EINVAL, "row-0 nodes j and ntheta-1-j must coincide along the cut (j <= n_cut)");
+    for (int j = 0; j < nt; ++j)
+        if (m.coltype[j] & (CT_CUT | CT_JUNC))
+            for (int c = 0; c < 2; ++c)
+                if (std::fabs(P(0, j, c) - P(0, nt - 1 - j, c)) > 1e-12 * scale)
+                    return set_error(LBFSI_EINVAL, "row-0 nodes j and ntheta-1-j must coincide along the cut "
+                                                   "(and at the chains' ends)");
     auto check_window = [&](int wa, int wb) {
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
@@ -356,7 +393,7 @@ int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, dou
             m.fardirj[4 * i + c] = P(i, 0, c) - P(i, 1, c);
             m.fardirj[4 * i + 2 + c] = P(i, nt - 1, c) - P(i, nt - 2, c);
         }
-    wall_geometry_chain(m);
+    wall_geometry_chains(m);
     // node coordinates with the mirrored rows: X(-k, j) = X(k, nt-1-j)
     const size_t g0 = (size_t)G * nt;
     m.X.assign(2 * (size_t)m.Nx, 0.0);
@@ -372,7 +409,10 @@ int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, dou
     m.jinv.assign(4 * (size_t)m.Nx, 0.0);
     for (int i = 0; i < nr; ++i)
         for (int j = 0; j < nt; ++j) {
-            const bool across = i == 0 && (j <= n_cut || j >= nt - 1 - n_cut);
+            const int ct = m.coltype[j];
+            const bool across = i == 0 && (ct & (CT_CUT | CT_JUNC));
+            const bool jfwd = i == 0 && (ct & CT_JUNC) && (ct & CT_JFWD);
+            const bool jbwd = i == 0 && (ct & CT_JUNC) && !(ct & CT_JFWD);
             double di[2], dj[2];
             for (int c = 0; c < 2; ++c) {
                 if (across)
@@ -383,9 +423,9 @@ int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, dou
                     di[c] = 0.5 * (3.0 * P(nr - 1, j, c) - 4.0 * P(nr - 2, j, c) + P(nr - 3, j, c));
                 else
                     di[c] = 0.5 * (P(i + 1, j, c) - P(i - 1, j, c));
-                if (j == 0 || (i == 0 && j == nt - 1 - n_cut))
+                if (j == 0 || jfwd)
                     dj[c] = 0.5 * (-3.0 * P(i, j, c) + 4.0 * P(i, j + 1, c) - P(i, j + 2, c));
-                else if (j == nt - 1 || (i == 0 && j == n_cut))
+                else if (j == nt - 1 || jbwd)
                     dj[c] = 0.5 * (3.0 * P(i, j, c) - 4.0 * P(i, j - 1, c) + P(i, j - 2, c));
                 else
                     dj[c] = 0.5 * (P(i, j + 1, c) - P(i, j - 1, c));
@@ -521,7 +561,7 @@ int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
         if (!(b.forced_periods >= 0.0) || !std::isfinite(b.pitch_amp) || !std::isfinite(b.forced_periods))
             return set_error(LBFSI_EINVAL, "forced pitching needs a finite amplitude and forced_periods >= 0");
         for (int j = 0; j < m.nt; ++j) {
-            if (m.cgrid && (j < m.jc || j > m.nt - 1 - m.jc)) continue;   // the cut
+            if (m.cgrid && !(m.coltype[j] & CT_WALL)) continue;   // the cut
             const double x = m.xw[2 * j] - b.xc;
             const double y = m.xw[2 * j + 1] - b.yc;
             if (std::sqrt(x * x + y * y) >= b.r_in)
@@ -642,6 +682,7 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.emin_f = (float)d.emin;
     void *pr = nullptr, *pe = nullptr, *pn = nullptr, *pw = nullptr, *prt = nullptr, *pct = nullptr;
     void *pxw = nullptr, *pfd = nullptr, *px = nullptr, *pj = nullptr, *pc = nullptr, *pfj = nullptr;
+    void* pct_ = nullptr;
     int rc = put(h.n0, false, &pn);
     if (!rc) rc = put(h.wall_geo, false, &pw);
     if (!rc) rc = put(h.xw, false, &pxw);
@@ -651,6 +692,19 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
         if (!rc) rc = put(h.jinv, true, &pj);
         if (!rc) rc = put(h.cellc, true, &pc);
         if (!rc && h.cgrid) rc = put(h.fardirj, false, &pfj);
+        if (!rc && h.cgrid) {
+            const size_t bytes = h.coltype.size() * sizeof(int);
+            pct_ = mem.alloc(bytes);
+            if (!pct_) {
+                rc = set_error(LBFSI_ENOMEM, "device allocation of the mesh geometry failed");
+            } else {
+                out.blocks.push_back(pct_);
+                out.bytes += bytes;
+                cudaError_t e = cudaMemcpyAsync(pct_, h.coltype.data(), bytes, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) rc = set_error(LBFSI_ECUDA, std::string("mesh upload: ") + cudaGetErrorString(e));
+            }
+        }
     } else {
         if (!rc) rc = put(h.r, false, &pr);
         if (!rc) rc = put(h.e, false, &pe);
@@ -676,9 +730,9 @@ int upload_mesh(const HostMesh& h, int precision, DevMemory& mem, cudaStream_t s
     d.jinv = pj ? (const char*)pj + g0 * 4 * es : nullptr;
     d.cellc = pc ? (const char*)pc + g0 * CELLC * es : nullptr;
     d.cgrid = h.cgrid ? 1 : 0;
-    d.jc = h.jc;
     d.box = h.box ? 1 : 0;
     d.fardirj = (const double*)pfj;
+    d.coltype = (const int*)pct_;
     return LBFSI_OK;
 }
 

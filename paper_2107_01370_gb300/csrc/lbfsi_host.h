@@ -35,9 +35,10 @@ struct HostMesh {
     int Nx = 0, G = 0;
     double xm = 0, ym = 0;
     bool general = false;
-    // C-grid: row-0 columns j < jc and j > nt-1-jc lie on the wake cut
+    // C-grid: the wall chains (inclusive row-0 column ranges) and the class
+    // of every row-0 column (CT_*)
     bool cgrid = false;
-    int jc = 0;
+    std::vector<int> walls, coltype;
     // doubly periodic box (no wall, no far field): rows wrap as well
     bool box = false;
     std::vector<double> r, e, n0, wall_geo, rowtab, coltab, xw, fardir, X, jinv, cellc;
@@ -63,10 +64,13 @@ int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc,
 int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, HostMesh& out);
 
 // The same for a C-grid given by its node coordinates X [nr][nt][2] (nt
-// odd, the first and last n_cut row-0 nodes on the wake cut, node j and
-// nt-1-j of row 0 one point for j <= n_cut): the arrays carry G mirrored
-// rows below row 0 (node (-k, j) = node (k, nt-1-j)).
-int build_host_mesh_c(int nr, int nt, int n_cut, const double* X, double xc, double yc, HostMesh& out);
+// odd) and its wall chains walls[2 k], walls[2 k + 1] (inclusive row-0
+// column ranges, even ends; the rest of row 0 is cut, symmetric in
+// j -> nt-1-j, its nodes and the chains' ends one point with their mirrors):
+// the arrays carry G mirrored rows below row 0 (node (-k, j) = node
+// (k, nt-1-j)).
+int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double* X, double xc, double yc,
+                      HostMesh& out);
 
 // A doubly periodic box given by the node coordinates X [ni][nj][2] of one
 // period and the period vectors along i and j (node (i + ni, j) = node (i, j)

@@ -70,6 +70,12 @@ enum StepMode : int { MODE_STREAM_ONLY = 0, MODE_COLLIDE_STREAM = 1, MODE_COLLID
 
 // Mirrored rows kept below row 0 of a C-grid (the +-4 staging halo).
 constexpr int CGRID_GHOST_ROWS = 4;
+// Classes of a C-grid's row-0 columns: on the cut, on a wall chain, a
+// junction (a chain's end next to the cut, one point with its mirror), a
+// second copy of the mirrored column's node (past the middle of row 0), and
+// for a junction whether its cut neighbour is the next column (else the
+// previous one).
+enum : int { CT_CUT = 1, CT_WALL = 2, CT_JUNC = 4, CT_DUP = 8, CT_JFWD = 16 };
 
 // Geometry of one O-grid mesh shape, shared by every solve on it (device).
 struct MeshDev {
@@ -94,9 +100,10 @@ struct MeshDev {
     const void* cellc;             // [(nr-1) nt][8] element coefficients per cell
     // C-grid (general meshes only): the node, metric and cell arrays and every
     // field component hold mirrored rows -4..-1 below row 0 (their pointers
-    // point at row 0); row-0 columns j < jc and j > nt-1-jc lie on the wake
-    // cut, columns 0 and nt-1 are outlets
-    int cgrid, jc;
+    // point at row 0); coltype classes the row-0 columns (CT_*); columns 0
+    // and nt-1 are outlets
+    int cgrid;
+    const int* coltype;            // [nt]
     const double* fardirj;         // [nr][2][2] outward directions of columns 0 and nt-1
     // doubly periodic box (general meshes only): rows wrap like columns,
     // every node is interior (no wall, no far field)

@@ -118,11 +118,13 @@ __device__ __forceinline__ R d_row_c(const R* p, int stride, int i, int nr, bool
     }
     return R(0.5) * (p[stride] - p[-stride]);
 }
+// jdir: at a row-0 junction of a C-grid, +1 (the cut is the next column) or
+// -1 (the previous one); 0 elsewhere.
 template <typename R>
-__device__ __forceinline__ R d_col_c(const R* p, int i, int j, int nt, int jc, int cg) {
+__device__ __forceinline__ R d_col_c(const R* p, int j, int nt, int cg, int jdir) {
     if (cg) {
-        if (j == 0 || (i == 0 && j == nt - 1 - jc)) return R(0.5) * (R(-3) * p[0] + R(4) * p[1] - p[2]);
-        if (j == nt - 1 || (i == 0 && j == jc)) return R(0.5) * (R(3) * p[0] - R(4) * p[-1] + p[-2]);
+        if (j == 0 || jdir > 0) return R(0.5) * (R(-3) * p[0] + R(4) * p[1] - p[2]);
+        if (j == nt - 1 || jdir < 0) return R(0.5) * (R(3) * p[0] - R(4) * p[-1] + p[-2]);
     }
     return R(0.5) * (p[1] - p[-1]);
 }
@@ -264,7 +266,7 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
     // an element is taken when the point lies in it up to round-off (tin);
     // failing that, the first candidate within the CFL margin (lim), as for
     // a wall departure that grazes the body
-    const R tin = R(1) + (sizeof(R) == 4 ? R(1e-5) : R(1e-10));
+    const R tin = R(1) + (sizeof(R) == 4 ? R(1e-5) : R(1e-12));
     const R lim = R(1) + R(1e-4);
     bool have = false;
     int b_base = 0;
@@ -490,12 +492,17 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     }
     // C-grid (general meshes): rows from -4 are stored (the mirrored rows),
     // the angular index does not wrap
-    int cg = 0, jc = 0, pb = 0;
+    int cg = 0, pb = 0;
+    const int* ctab = nullptr;
     if constexpr (GEN) {
         cg = UNIFORM ? a.umesh.cgrid : mg->cgrid;
-        jc = UNIFORM ? a.umesh.jc : mg->jc;
+        ctab = UNIFORM ? a.umesh.coltype : mg->coltype;
         pb = UNIFORM ? a.umesh.box : mg->box;
     }
+    // class of a C-grid's row-0 column (CT_*); the one-sided direction of a
+    // row-0 junction's derivative along j
+    auto ctype = [&](int j) -> int { return cg ? __ldg(ctab + j) : 0; };
+    auto jdir_of = [&](int c) -> int { return (c & CT_JUNC) ? ((c & CT_JFWD) ? 1 : -1) : 0; };
     const int rlo = cg ? -CGRID_GHOST_ROWS : 0;
     // rows that exist (a periodic box: all, wrapped) and their stored index
     auto rowok = [&](int i) { return pb || (i >= rlo && i < nr); };
@@ -705,7 +712,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // ---- phase 2: correction fields and collision of step k --------------
     // a collide-only launch of a general mesh (a C-grid's first launch)
     // writes the tile's nodes only: the collision is needed there, the
-    // correction field D and the gradient maps on +-1, dQ on +-2
+    // correction field D and the gradient maps on +-2 (a junction's or an
+    // outlet's one-sided stencil along j reaches two nodes), dQ on +-4
     const bool shrink = GEN && mode == MODE_COLLIDE_ONLY;
     auto outside = [&](int li, int lj, int h, int w) {
         return shrink && (li < h - w || li >= h + TI + w || lj < h - w || lj >= h + TJ + w);
@@ -715,7 +723,6 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = mi0 + idx / T::MW;
             if (!rowok(i)) continue;
             if (cg && (unsigned)(mj0 + idx % T::MW) >= (unsigned)nt) continue;
-            if (outside(idx / T::MW, idx % T::MW, T::HM, 2)) continue;
             const R rho = sM[idx], ux = sM[T::MS + idx], uy = sM[2 * T::MS + idx], Tn = sM[3 * T::MS + idx];
             sQ[idx] = rho * ux * (R(1) - R(3) * Tn) - rho * ux * ux * ux;
             sQ[T::MS + idx] = rho * uy * (R(1) - R(3) * Tn) - rho * uy * uy * uy;
@@ -726,7 +733,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = i0 - T::HD + li;
             if (!rowok(i)) continue;
             if (cg && (unsigned)(j0 - T::HD + lj) >= (unsigned)nt) continue;
-            if (outside(li, lj, T::HD, 1)) continue;
+            if (outside(li, lj, T::HD, 2)) continue;
             R F00, F01, F10, F11, vx, vy;
             R G[4];
             if constexpr (GEN) {
@@ -761,16 +768,17 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
             if (!rowok(i)) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
-            if (outside(li, lj, T::HD, 1)) continue;
+            if (outside(li, lj, T::HD, 2)) continue;
             const int m = (li + 1) * T::MW + (lj + 1);
             const R mup = mu * rcp_(sM[m] * sM[3 * T::MS + m]);
             R qx_xi, qx_et, qy_xi, qy_et;
             if constexpr (GEN) {
-                const bool across = cg && i == 0 && (jj <= jc || jj >= nt - 1 - jc);
+                const int ct = (cg && i == 0) ? ctype(jj) : 0;
+                const bool across = (ct & (CT_CUT | CT_JUNC)) != 0;
                 qx_xi = d_row_c(sQ + m, T::MW, i, nr, across, pb);
-                qx_et = d_col_c(sQ + m, i, jj, nt, jc, cg);
+                qx_et = d_col_c(sQ + m, jj, nt, cg, jdir_of(ct));
                 qy_xi = d_row_c(sQ + T::MS + m, T::MW, i, nr, across, pb);
-                qy_et = d_col_c(sQ + T::MS + m, i, jj, nt, jc, cg);
+                qy_et = d_col_c(sQ + T::MS + m, jj, nt, cg, jdir_of(ct));
             } else {
                 qx_xi = d_row(sQ + m, T::MW, i, nr);
                 qx_et = d_col(sQ + m);
@@ -804,11 +812,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int d = (li + 1) * T::DW + (lj + 1);
                 R dx_xi, dx_et, dy_xi, dy_et;
                 if constexpr (GEN) {
-                    const bool across = cg && i == 0 && (jj <= jc || jj >= nt - 1 - jc);
+                    const int ct = (cg && i == 0) ? ctype(jj) : 0;
+                    const bool across = (ct & (CT_CUT | CT_JUNC)) != 0;
                     dx_xi = d_row_c(sD + d, T::DW, i, nr, across, pb);
-                    dx_et = d_col_c(sD + d, i, jj, nt, jc, cg);
+                    dx_et = d_col_c(sD + d, jj, nt, cg, jdir_of(ct));
                     dy_xi = d_row_c(sD + T::DS + d, T::DW, i, nr, across, pb);
-                    dy_et = d_col_c(sD + T::DS + d, i, jj, nt, jc, cg);
+                    dy_et = d_col_c(sD + T::DS + d, jj, nt, cg, jdir_of(ct));
                 } else {
                     dx_xi = d_row(sD + d, T::DW, i, nr);
                     dx_et = d_col(sD + d);
@@ -839,8 +848,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                     // C-grid: the first copy of a cut node also writes the
                     // second (which writes nothing), rows 1 and 2 their
                     // mirrored slots (the next stream's rows below row 0)
-                    if (cg && i == 0 && j >= nt - 1 - jc) continue;
-                    const bool two = cg && ((i == 0 && j <= jc) || i == 1 || i == 2);
+                    const int ct = (cg && i == 0) ? ctype(j) : 0;
+                    if (ct & CT_DUP) continue;
+                    const bool two = (ct & (CT_CUT | CT_JUNC)) || (cg && (i == 1 || i == 2));
                     const int n2 = i == 0 ? nt - 1 - j : -i * nt + (nt - 1 - j);
 #pragma unroll
                     for (int q = 0; q < 9; ++q) {
@@ -869,8 +879,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // C-grid: the second copies of the row-0 cut nodes (and of the rear
         // point) are written by their first copies; rows 1-4 also write
         // their moments into their mirrored slots below row 0
-        if (cg && i == 0 && j >= nt - 1 - jc) continue;
-        const bool dup2 = cg && i == 0 && j <= jc;
+        const int ct = (cg && i == 0) ? ctype(j) : 0;
+        if (ct & CT_DUP) continue;
+        const bool dup2 = (ct & (CT_CUT | CT_JUNC)) != 0;
         const bool mir = cg && i >= 1 && i <= CGRID_GHOST_ROWS;
         const int n2 = i == 0 ? nt - 1 - j : -i * nt + (nt - 1 - j);
         const int n = i * nt + j;
@@ -920,11 +931,23 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
             continue;
         }
-        const bool wall = !pb && i == 0 && (!cg || j >= jc);
-        // the rear point of a C-grid: its mirrored cell next to the wall has
-        // the other side's wall nodes as its element's row 0
-        const bool rear = cg && i == 0 && j == jc;
-        const int rbase = (-2 - pi0) * T::PWS + (jc - sj0);
+        const bool wall = !pb && i == 0 && (!cg || (ct & CT_WALL));
+        const bool rear = (ct & CT_JUNC) != 0;   // a junction (first copy)
+        // a window below row 0 is the mirror of one on the other side of the
+        // cut, its row 0 included: where that row lies on a wall (next to a
+        // junction) its nodes are the other side's, read from global memory
+        // (mask bit b for window column b)
+        auto mirror_mask = [&](int base) -> unsigned {
+            unsigned mw = 0u;
+            if (GEN && dup2 && base / T::PWS + pi0 == -2) {
+                const int wb = base - (base / T::PWS) * T::PWS + sj0;
+                for (int b2 = 0; b2 < 3; ++b2) {
+                    const int c2 = ctype(wb + b2);
+                    if ((c2 & CT_WALL) && !(c2 & CT_JUNC)) mw |= 1u << b2;
+                }
+            }
+            return mw;
+        };
         NodeGeo<R> geo;
         R F00, F01, F10, F11, vx, vy;
         bool moved;
@@ -1020,11 +1043,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
                 R2 v;
-                if (GEN && rear && base == rbase)
-                    v = gather9_last(sp + q * T::PSS + base, T::PWS, Lx, Ly, sp[q * T::PSS + base + 2 * T::PWS],
-                                     p_in[(size_t)q * N + (nt - 2 - jc)], p_in[(size_t)q * N + (nt - 3 - jc)]);
-                else
+                const unsigned mw = mirror_mask(base);
+                if (mw) {
+                    const int wb = base - (base / T::PWS) * T::PWS + sj0;
+                    const R2* r0 = sp + q * T::PSS + base + 2 * T::PWS;
+                    auto e0 = [&](int b2) { return (mw >> b2) & 1u ? p_in[(size_t)q * N + (nt - 1 - wb - b2)] : r0[b2]; };
+                    v = gather9_last(sp + q * T::PSS + base, T::PWS, Lx, Ly, e0(0), e0(1), e0(2));
+                } else {
                     v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
+                }
                 f[q] = v.x;
                 g[q] = v.y;
             } else {
@@ -1051,14 +1078,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int w0 = (wa - mi0) * T::MW + (wb - mj0);
                 rhoB = R(0);
                 TB = R(0);
-                const bool other = GEN && rear && base == rbase;   // row 0 from the other side
+                const unsigned mw = mirror_mask(base);   // row 0 from the other side
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
                     for (int bb = 0; bb < 3; ++bb) {
                         const R wgt = Lx[aa] * Ly[bb];
-                        const bool far = other && aa == 2 && bb > 0;
-                        const int c2 = nt - 1 - jc - bb;
+                        const bool far = aa == 2 && ((mw >> bb) & 1u);
+                        const int c2 = nt - 1 - wb - bb;
                         rhoB += wgt * (far ? M_in[c2] : sM[w0 + aa * T::MW + bb]);
                         TB += wgt * (far ? M_in[(size_t)3 * N + c2] : sM[3 * T::MS + w0 + aa * T::MW + bb]);
                     }
@@ -1080,7 +1107,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R cxi, cet;
                 if constexpr (GEN) {
                     cxi = d_row_c(p, T::MW, 0, nr, rear);
-                    cet = d_col_c(p, 0, j, nt, jc, cg);
+                    cet = d_col_c(p, j, nt, cg, jdir_of(ct));
                 } else {
                     cxi = d_row(p, T::MW, 0, nr);
                     cet = d_col(p);

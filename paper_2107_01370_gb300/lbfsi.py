@@ -34,7 +34,7 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
             "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy",
             "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid", "lbfsi_field_ptr",
-            "lbfsi_create_mesh_box"]
+            "lbfsi_create_mesh_box", "lbfsi_create_mesh_cgrid_walls"]
 
 
 class LbfsiError(RuntimeError):
@@ -87,6 +87,13 @@ class MeshBoxDesc(ctypes.Structure):
     _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("X", ctypes.POINTER(ctypes.c_double)),
                 ("shift_i", ctypes.c_double * 2), ("shift_j", ctypes.c_double * 2),
                 ("precision", ctypes.c_int), ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+
+
+class MeshCGridWallsDesc(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nwalls", ctypes.c_int),
+                ("walls", ctypes.POINTER(ctypes.c_int)), ("X", ctypes.POINTER(ctypes.c_double)),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
+                ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
 
 
 class MeshCGridDesc(ctypes.Structure):
@@ -304,6 +311,32 @@ class Mesh:
         h = ctypes.c_void_p()
         self.h = None
         _check(lib.lbfsi_create_mesh_cgrid(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+        return self
+
+    @classmethod
+    def cgrid_walls(cls, X, walls, bodies, precision=FP64, centre=(0.0, 0.0), stream=None):
+        """Handle of a C-grid around several bodies: node coordinates X
+        [nr, ntheta, 2] and the wall chains as inclusive column ranges
+        [(first, last), ...] (lbfsi_create_mesh_cgrid_walls); the walls move
+        as the solve's one body."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.r = self.e = None
+        self.nr, self.nt = self.X.shape[0], self.X.shape[1]
+        self.N = self.nr * self.nt
+        self.nbatch = len(bodies)
+        self.precision = precision
+        self._bodies = (BodyDesc * self.nbatch)(*[body_desc(b) for b in bodies])
+        w = [int(v) for ab in walls for v in ab]
+        self._walls = (ctypes.c_int * len(w))(*w)
+        d = MeshCGridWallsDesc(self.nr, self.nt, len(walls), self._walls, _dptr(self.X), centre[0], centre[1],
+                               precision, self.nbatch, self._bodies)
+        h = ctypes.c_void_p()
+        self.h = None
+        _check(lib.lbfsi_create_mesh_cgrid_walls(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
         self.h = h
         return self
 

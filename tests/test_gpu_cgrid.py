@@ -37,7 +37,9 @@ def to_tuple(d):
 
 
 def run_both(L, case, M0, steps, precision, state=None, prev=None):
-    s = OS.Solver.from_case(OM.CGridMesh(case.X, case.n_cut), case, M0)
+    walls = getattr(case, "walls", None)
+    mesh = OM.CGridMesh(case.X, walls=walls) if walls else OM.CGridMesh(case.X, case.n_cut)
+    s = OS.Solver.from_case(mesh, case, M0)
     if state is not None:
         s.S = [dict(state)]
         s.S_prev = [dict(prev if prev is not None else state)]
@@ -45,7 +47,10 @@ def run_both(L, case, M0, steps, precision, state=None, prev=None):
     for _ in range(steps):
         r = s.step()
         hist.append(r.force)
-    m = L.Mesh.cgrid(case.X, case.n_cut, case.bodies, precision=precision, centre=case.centre)
+    if walls:
+        m = L.Mesh.cgrid_walls(case.X, walls, case.bodies, precision=precision, centre=case.centre)
+    else:
+        m = L.Mesh.cgrid(case.X, case.n_cut, case.bodies, precision=precision, centre=case.centre)
     m.init_fields(case.flow, M0[None])
     if state is not None:
         m.blend_mesh([to_tuple(state)], None if prev is None else [to_tuple(prev)])
@@ -205,6 +210,35 @@ def test_fp64_naca0012_cgrid_matches_oracle(L):
 def test_fp32_naca0012_cgrid_within_stated_tolerance(L):
     case = _naca_case()
     M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=62)
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 30, L.FP32)
+    assert field_err(f, r.M) < 1e-5
+    assert np.abs(ghist - hist).max() < 1e-4 * P_SCALE
+
+
+LINKED = inputs.BodySpec(dof=1, xc=2.0, yc=0.0, xp=2.0, yp=0.0, r_in=2.7, r_out=4.5, m_star=4.0, v_r=5.0,
+                         length=1.0)
+
+
+@pytest.mark.parametrize("moving", [False, True])
+def test_fp64_linked_tandem_cylinders_match_oracle(L, moving):
+    """Two cylinders in tandem (4 D apart) rigidly linked on one transverse
+    DOF (reading R31): a C-grid with three wall chains (the front body, the
+    rear body's upper and lower halves), the cut through the gap and the wake;
+    one rigid zone holds both walls and the load is their sum."""
+    case = inputs.tandem_case(34, 17, 11, 16, 33, body=LINKED)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=71)
+    state = {"h": 0.02, "alpha": 0.0, "hdot": 0.004, "adot": 0.0} if moving else None
+    prev = {"h": 0.0199, "alpha": 0.0, "hdot": 0.004, "adot": 0.0} if moving else None
+    s, r, hist, (f, ghist, st) = run_both(L, case, M0, 10, L.FP64, state, prev)
+    assert field_err(f, r.M) < 1e-12
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+    for k in ("h", "hdot"):
+        assert abs(st[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+
+
+def test_fp32_linked_tandem_within_stated_tolerance(L):
+    case = inputs.tandem_case(34, 17, 11, 16, 33, body=LINKED)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=72)
     s, r, hist, (f, ghist, st) = run_both(L, case, M0, 30, L.FP32)
     assert field_err(f, r.M) < 1e-5
     assert np.abs(ghist - hist).max() < 1e-4 * P_SCALE
