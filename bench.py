@@ -353,12 +353,19 @@ def general_mesh_cases():
     cg = inputs.cgrid_case(513, 128, 192, 0.5, 0.06, r_far=10.0, wake=10.0, length=1.0, ma=0.8,
                            t_inf=0.2, re=1e5, body=body, naca=0.12,
                            name="NACA 0012 C-grid 192x769 (cut 128), 2-DOF, Ma 0.8, forced pitch")
+    linked = inputs.BodySpec(dof=1, xc=2.0, yc=0.0, xp=2.0, yp=0.0, r_in=2.7, r_out=4.5, m_star=4.0,
+                             v_r=5.0, length=1.0)
+    tc = inputs.tandem_case(257, 257, 255, 256, 512, body=linked,
+                            name="two cylinders in tandem 4 D apart, rigidly linked (1 DOF, V_R 5), "
+                                 "C-grid 512x2049 with three wall chains, Re 100, Ma 0.2")
     return ((ell, lambda prec, nb, st: lbfsi.Mesh.xy(ell.X, ell.bodies * nb, precision=prec, stream=st)),
             (cg, lambda prec, nb, st: lbfsi.Mesh.cgrid(cg.X, cg.n_cut, cg.bodies * nb, precision=prec,
-                                                       stream=st)))
+                                                       stream=st)),
+            (tc, lambda prec, nb, st: lbfsi.Mesh.cgrid_walls(tc.X, tc.walls, tc.bodies * nb, precision=prec,
+                                                             stream=st)))
 
 
-def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8, only=None):
+def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=(8, 8, 1), only=None):
     """MLUPS of the general-mesh step (Newton departure points, stored
     metric) on the two workloads of general_mesh_cases, timed with CUDA events
     on the library's stream; the C-grid step is two launches (collision, then
@@ -369,9 +376,10 @@ def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8, only=Non
     for k, (case, make) in enumerate(general_mesh_cases()):
         if only is not None and k != only:
             continue
+        nb = batch[k] if isinstance(batch, tuple) else batch
         M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
-        m = make(lbfsi.FP32, batch, stream.cuda_stream)
-        m.init_fields(case.flow, np.ascontiguousarray(np.broadcast_to(M0, (batch,) + M0.shape)))
+        m = make(lbfsi.FP32, nb, stream.cuda_stream)
+        m.init_fields(case.flow, np.ascontiguousarray(np.broadcast_to(M0, (nb,) + M0.shape)))
         m.step(warmup)
         m.synchronize()
         ls = m.launch_count()
@@ -390,9 +398,9 @@ def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=8, only=Non
             ok = str(e)
         launches = m.launch_count() - ls
         m.close()
-        nodes = case.nodes * batch
+        nodes = case.nodes * nb
         gbs = BYTES_PER_NODE_FP32 * nodes * steps / (ms * 1e-3) / 1e9
-        out.append({"workload": case.name, "nodes": case.nodes, "batch": batch, "steps": steps,
+        out.append({"workload": case.name, "nodes": case.nodes, "batch": nb, "steps": steps,
                     "launches_per_step": launches // steps, "ms_per_step": round(ms / steps, 4),
                     "MLUPS": round(nodes * steps / ms / 1e3, 1),
                     "hbm_frac_of_measured": round(gbs / peak, 4), "physical": ok})
@@ -487,8 +495,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1-16 M-node roofline sweep and the small FP64 case")
     ap.add_argument("--schedule", default=None,
                     help="'variant,order': fixed tile shape and CTA order instead of the autotuner")
-    ap.add_argument("--general-only", type=int, default=None, choices=[0, 1],
-                    help="time only one general-mesh workload (0: O-grid by coordinates, 1: C-grid) "
+    ap.add_argument("--general-only", type=int, default=None, choices=[0, 1, 2],
+                    help="time only one general-mesh workload (0: O-grid by coordinates, 1: NACA C-grid, "
+                         "2: linked tandem cylinders) "
                          "with --steps, --warmup and --batch, print its JSON and exit")
     args = ap.parse_args()
     if args.warmup < 3:

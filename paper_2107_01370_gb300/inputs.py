@@ -351,7 +351,7 @@ def tandem_cgrid(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *,
     th_f = np.pi * np.arange(n_front) / (n_front - 1)
     th_r = np.pi * np.arange(n_rear) / (n_rear - 1)
     first = r * (th_f[2] - th_f[0])
-    s = ogrid_radii(n_wake + 1, 0.0, wake, 2.0 * first)
+    s = ogrid_radii(n_wake + 1, 0.0, wake, min(2.0 * first, 0.45 * wake / n_wake))
     W, E = [], []
     for x in (L + r + s[1:])[::-1]:
         W.append((x, 0.0))
@@ -384,8 +384,8 @@ def tandem_cgrid(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *,
             C[j] = np.array([r, 0.0]) + d / np.hypot(d[0], d[1]) * np.sqrt(2.0) * r_far
     for A in (Wf, Ef, C):
         A[1::2] = 0.5 * (A[0:-1:2] + A[2::2])
-    t1 = radial_fractions(n_inner + 1, 0.05)
-    t2 = radial_fractions(nr - n_inner, 0.02)
+    t1 = radial_fractions(n_inner + 1, min(0.05, 0.4 / n_inner))
+    t2 = radial_fractions(nr - n_inner, min(0.02, 0.4 / (nr - n_inner)))
     X = np.empty((nr, nt, 2))
     for i in range(n_inner + 1):
         X[i] = Wf + t1[i] * (Ef - Wf)
@@ -404,7 +404,8 @@ def tandem_case(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *, 
     """Two cylinders of diameter 1 in tandem on a C-grid (tandem_cgrid); the
     time step a third of the smallest row-0 spacing.  The case's n_cut is
     None; its walls give the chains."""
-    X, walls = tandem_cgrid(n_front, n_rear, n_gap, n_wake, nr, spacing=spacing)
+    X, walls = tandem_cgrid(n_front, n_rear, n_gap, n_wake, nr, spacing=spacing,
+                            n_inner=max(8, 2 * (nr // 16)))
     d = np.hypot(*(X[0, 1:] - X[0, :-1]).T)
     first = float(d[d > 0].min())
     flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr, dt=first / 3.0, length=1.0)
