@@ -405,9 +405,12 @@ def tandem_case(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *, 
     time step a third of the smallest row-0 spacing.  The case's n_cut is
     None; its walls give the chains."""
     X, walls = tandem_cgrid(n_front, n_rear, n_gap, n_wake, nr, spacing=spacing,
-                            n_inner=max(8, 2 * (nr // 16)))
-    d = np.hypot(*(X[0, 1:] - X[0, :-1]).T)
-    first = float(d[d > 0].min())
+                            n_inner=min(16, max(8, 2 * (nr // 16))))
+    # the smallest edge of the whole mesh (the layer between the wall and
+    # the envelope can be thinner than the wall spacing)
+    di = np.hypot(*(X[1:] - X[:-1]).reshape(-1, 2).T)
+    dj = np.hypot(*(X[:, 1:] - X[:, :-1]).reshape(-1, 2).T)
+    first = float(min(di[di > 0].min(), dj[dj > 0].min()))
     flow = FlowSpec(ma=ma, re=re, t_inf=t_inf, gamma=gamma, pr=pr, dt=first / 3.0, length=1.0)
     bd = body if body is not None else BodySpec(dof=0)
     c = CGridCase(nr=nr, ntheta=X.shape[1], n_cut=None, X=X, centre=(0.0, 0.0), flow=flow, bodies=[bd],
