@@ -437,6 +437,24 @@ __device__ __forceinline__ R2 gather9_last(const R2* p, int rowstride, const R* 
     return acc;
 }
 
+// The same over a window below row 0 at a C-grid junction, whose row 0 may
+// hold the other side's wall nodes (read from the node's own global row 0,
+// p0, at the mirrored column): out of line, since only junction nodes take
+// it and an inline copy in each of the nine directions would only swell
+// the kernel.
+template <typename R, typename R2>
+__device__ __noinline__ R2 gather9_mirror(const R2* p, int rowstride, R lx0, R lx1, R lx2, R ly0, R ly1, R ly2,
+                                          const R2* p0, const int* ctab, int wb, int nt) {
+    R2 e[3];
+#pragma unroll
+    for (int b2 = 0; b2 < 3; ++b2) {
+        const int c = wb + b2, ct = ctab[c];
+        e[b2] = ((ct & CT_WALL) && !(ct & CT_JUNC)) ? p0[nt - 1 - c] : p[2 * rowstride + b2];
+    }
+    const R Lx[3] = {lx0, lx1, lx2}, Ly[3] = {ly0, ly1, ly2};
+    return gather9_last(p, rowstride, Lx, Ly, e[0], e[1], e[2]);
+}
+
 template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
@@ -934,20 +952,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const bool wall = !pb && i == 0 && (!cg || (ct & CT_WALL));
         const bool rear = (ct & CT_JUNC) != 0;   // a junction (first copy)
         // a window below row 0 is the mirror of one on the other side of the
-        // cut, its row 0 included: where that row lies on a wall (next to a
-        // junction) its nodes are the other side's, read from global memory
-        // (mask bit b for window column b)
-        auto mirror_mask = [&](int base) -> unsigned {
-            unsigned mw = 0u;
-            if (GEN && dup2 && base / T::PWS + pi0 == -2) {
-                const int wb = base - (base / T::PWS) * T::PWS + sj0;
-                for (int b2 = 0; b2 < 3; ++b2) {
-                    const int c2 = ctype(wb + b2);
-                    if ((c2 & CT_WALL) && !(c2 & CT_JUNC)) mw |= 1u << b2;
-                }
-            }
-            return mw;
-        };
+        // cut, its row 0 included: next to a junction that row can lie on the
+        // other side's wall, whose nodes are then read from global memory (only
+        // a junction's windows can reach a wall column)
+        const int rbase_row = -2 - pi0;   // staged row of global row -2
         NodeGeo<R> geo;
         R F00, F01, F10, F11, vx, vy;
         bool moved;
@@ -1043,15 +1051,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 lagrange3(xi, Lx);
                 lagrange3(eta, Ly);
                 R2 v;
-                const unsigned mw = mirror_mask(base);
-                if (mw) {
-                    const int wb = base - (base / T::PWS) * T::PWS + sj0;
-                    const R2* r0 = sp + q * T::PSS + base + 2 * T::PWS;
-                    auto e0 = [&](int b2) { return (mw >> b2) & 1u ? p_in[(size_t)q * N + (nt - 1 - wb - b2)] : r0[b2]; };
-                    v = gather9_last(sp + q * T::PSS + base, T::PWS, Lx, Ly, e0(0), e0(1), e0(2));
-                } else {
+                if (GEN && rear && base / T::PWS == rbase_row)
+                    v = gather9_mirror<R, R2>(sp + q * T::PSS + base, T::PWS, Lx[0], Lx[1], Lx[2], Ly[0], Ly[1], Ly[2],
+                                              p_in + (size_t)q * N, ctab, base - rbase_row * T::PWS + sj0, nt);
+                else
                     v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
-                }
                 f[q] = v.x;
                 g[q] = v.y;
             } else {
@@ -1078,7 +1082,13 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int w0 = (wa - mi0) * T::MW + (wb - mj0);
                 rhoB = R(0);
                 TB = R(0);
-                const unsigned mw = mirror_mask(base);   // row 0 from the other side
+                // row 0 from the other side (a junction's window below row 0)
+                unsigned mw = 0u;
+                if (GEN && rear && wa == -2)
+                    for (int b2 = 0; b2 < 3; ++b2) {
+                        const int c2 = ctype(wb + b2);
+                        if ((c2 & CT_WALL) && !(c2 & CT_JUNC)) mw |= 1u << b2;
+                    }
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
