@@ -54,7 +54,9 @@ typedef enum {
     LBFSI_EDEPARTURE = -4,  /* departure point not in a cell adjacent to its node (CFL violated) */
     LBFSI_ENONPHYS = -5,    /* rho <= 0, T <= 0 or NaN produced */
     LBFSI_ETIMEOUT = -6,    /* a bounded device wait ran out */
-    LBFSI_ESTATE = -7       /* call out of order (e.g. step before init_fields) */
+    LBFSI_ESTATE = -7,      /* call out of order (e.g. step before init_fields) */
+    LBFSI_EBOUNDS = -8      /* bounds-checked build only: an index of the step outside its
+                               buffer (the access was skipped, the results are invalid) */
 } lbfsi_status;
 
 enum { LBFSI_FP64 = 0, LBFSI_FP32 = 1 };

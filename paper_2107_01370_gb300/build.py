@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbfsi.so")
+# the bounds-checked variant (LBFSI_BOUNDS_CHECK: every shared-memory window
+# and global slot of the step checked, a violation reported as LBFSI_EBOUNDS)
+BUILD_BOUNDS = os.path.join(ROOT, "_build_bounds")
+LIB_BOUNDS = os.path.join(PKG, "liblbfsi_bounds.so")
 SOURCES = ["lbfsi_step.cu", "lbfsi_api.cu", "lbfsi_host.cu", "lbfsi_batch.cu", "lbfsi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -37,8 +41,10 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, bounds: bool = False) -> str:
+    build_dir, lib = (BUILD_BOUNDS, LIB_BOUNDS) if bounds else (BUILD, LIB)
+    extra = ["-DLBFSI_BOUNDS_CHECK"] if bounds else []
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "lbfsi.h"))
     cc = nvcc()
@@ -46,10 +52,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([cc, *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o])
+            jobs.append([cc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -61,9 +67,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        run([cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
-    return LIB
+    if force or jobs or _stale(lib, objs):
+        run([cc, *ARCH, "-shared", "-o", lib, *objs, "-lcudart"])
+    return lib
 
 
 if __name__ == "__main__":

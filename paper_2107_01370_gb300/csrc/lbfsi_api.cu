@@ -88,6 +88,8 @@ int check_status(lbfsi_mesh m) {
     unsigned st = 0;
     e = cudaMemcpy(&st, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st & lbfsi::ST_BOUNDS)
+        return lbfsi::set_error(LBFSI_EBOUNDS, "an index of the step outside its buffer (bounds-checked build)");
     if (st & lbfsi::ST_DEPARTURE)
         return fail(LBFSI_EDEPARTURE, "departure point outside the cells adjacent to its node (CFL)");
     if (st & lbfsi::ST_BPOINT)

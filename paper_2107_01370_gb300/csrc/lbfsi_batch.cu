@@ -309,6 +309,8 @@ int check_status(lbfsi_batch b) {
     unsigned st = 0;
     e = cudaMemcpy(&st, b->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(e, "status read");
+    if (st & lbfsi::ST_BOUNDS)
+        return lbfsi::set_error(LBFSI_EBOUNDS, "an index of the step outside its buffer (bounds-checked build)");
     if (st & (lbfsi::ST_DEPARTURE | lbfsi::ST_BPOINT))
         return lbfsi::set_error(LBFSI_EDEPARTURE, "departure point outside the cells adjacent to its node (CFL)");
     if (st & lbfsi::ST_NONPHYS) return lbfsi::set_error(LBFSI_ENONPHYS, "non-physical state (rho<=0, T<=0 or NaN)");

@@ -13,6 +13,7 @@ enum : unsigned {
     ST_DEPARTURE = 1u,   // departure point outside the adjacent cells
     ST_NONPHYS = 2u,     // rho <= 0, T <= 0 or NaN
     ST_BPOINT = 4u,      // wall target point outside the first element row
+    ST_BOUNDS = 8u,      // bounds-checked build: an index outside its buffer (access skipped)
 };
 
 // Body model with dimensional ODE coefficients (Sec. III, Sec. IV).

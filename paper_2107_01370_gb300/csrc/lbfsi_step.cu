@@ -91,6 +91,19 @@ constexpr size_t step_smem_bytes() {
                                 (GEN ? 6 * T::DS + (TI + 1) * (TJ + 1) * CELLC : T::MH * RS + T::MW * CS));
 }
 
+// Bounds-checked build (LBFSI_BOUNDS_CHECK): the shared-memory windows the
+// step reads and the global slots it writes are checked; an index outside
+// its buffer sets ST_BOUNDS and the access is skipped.  The substitute for a
+// memory checker where none can run; without the macro every check is true.
+#ifdef LBFSI_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(bool ok, unsigned* st) {
+    if (!ok) atomicOr(st, ST_BOUNDS);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool in_bounds(bool, unsigned*) { return true; }
+#endif
+
 // Derivative along an index direction of the 1-D quadratic Lagrange interpolant
 // through a node and its neighbours, evaluated at the node (Eq. ddx+fem):
 // central inside, one-sided (-3 c0 + 4 c1 - c2)/2 on the first row,
@@ -252,10 +265,11 @@ __device__ __forceinline__ void grad_map(const R* row, const R* col, R F00, R F0
 // the other adjacent cell is tried in the direction it left by; a point in no
 // adjacent cell is a CFL violation.  jn: the node's (j00, j01, j10, j11) with
 // d/dX = j00 d/di + j01 d/dj, d/dY = j10 d/di + j11 d/dj.
-template <typename R, int TJ>
+template <typename R, int TI, int TJ>
 __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int j, int i0, int j0,
                                            int nr, int pi0, int sj0, int PWS, R dx, R dy, int& base,
-                                           R& xi, R& eta, bool below = false, bool wrap_rows = false) {
+                                           R& xi, R& eta, bool below = false, bool wrap_rows = false,
+                                           unsigned* st = nullptr) {
     // below: the node has cells below row 0 (the mirrored cells across a
     // C-grid's cut, or the wrapped rows of a periodic box); otherwise a row-0
     // node only has the cells of row 0.  wrap_rows: no last window to clamp to
@@ -275,6 +289,8 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
     for (int attempt = 0; attempt < 3; ++attempt) {
         const int ca = i + da, cb = j + db;
         const int wa = wrap_rows ? (ca >> 1) * 2 : min((ca >> 1) * 2, nr - 3), wb = (cb >> 1) * 2;
+        if (!in_bounds(ca - (i0 - 1) >= 0 && ca - (i0 - 1) <= TI && cb - (j0 - 1) >= 0 && cb - (j0 - 1) <= TJ, st))
+            break;
         const R* c = sC + ((ca - (i0 - 1)) * (TJ + 1) + (cb - (j0 - 1))) * CELLC;
         const R xi0 = R(i - wa - 1), et0 = R(j - wb - 1);
         const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
@@ -371,6 +387,7 @@ template <>
 __device__ __forceinline__ double pick<double>(double d, float) {
     return d;
 }
+
 
 // Q2 interpolation of one (f, g) pair over a 3x3 window (rows rowstride
 // apart, columns adjacent): separable sums t_a = sum_b L_b(eta) v(a, b), then
@@ -576,6 +593,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
             if (!rowok(i) || (cg && (unsigned)jj >= (unsigned)nt)) continue;
             const ptrdiff_t n = (ptrdiff_t)rw(i) * nt + (cg ? jj : wrap_nt(jj, nt));
+            if (!in_bounds(n >= (ptrdiff_t)rlo * nt && n < (ptrdiff_t)nr * nt, a.status)) continue;
             if constexpr (sizeof(R) == 4) {
                 cp_async8(sX + 2 * idx, gx + 2 * n);
                 cp_async16(sJ + 4 * idx, gj + 4 * n);
@@ -593,6 +611,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             if (!pb && (ca < (cg ? -1 : 0) || ca > nr - 2)) continue;
             if (cg && (unsigned)cb > (unsigned)(nt - 2)) continue;
             const ptrdiff_t g = ((ptrdiff_t)rw(ca) * nt + (cg ? cb : wrap_nt(cb, nt))) * CELLC + ch * CE;
+            if (!in_bounds(g >= (ptrdiff_t)(cg ? -nt : 0) * CELLC && g < (ptrdiff_t)nr * nt * CELLC, a.status)) continue;
             cp_async16(sC + cell * CELLC + ch * CE, gc + g);
         }
     } else {
@@ -868,8 +887,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                     // mirrored slots (the next stream's rows below row 0)
                     const int ct = (cg && i == 0) ? ctype(j) : 0;
                     if (ct & CT_DUP) continue;
-                    const bool two = (ct & (CT_CUT | CT_JUNC)) || (cg && (i == 1 || i == 2));
                     const int n2 = i == 0 ? nt - 1 - j : -i * nt + (nt - 1 - j);
+                    const bool two = ((ct & (CT_CUT | CT_JUNC)) || (cg && (i == 1 || i == 2))) &&
+                                     in_bounds(n2 >= rlo * nt && n2 < nr * nt, a.status);
 #pragma unroll
                     for (int q = 0; q < 9; ++q) {
                         const R2 v = sp[q * T::PSS + sn];
@@ -899,9 +919,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // their moments into their mirrored slots below row 0
         const int ct = (cg && i == 0) ? ctype(j) : 0;
         if (ct & CT_DUP) continue;
-        const bool dup2 = (ct & (CT_CUT | CT_JUNC)) != 0;
-        const bool mir = cg && i >= 1 && i <= CGRID_GHOST_ROWS;
         const int n2 = i == 0 ? nt - 1 - j : -i * nt + (nt - 1 - j);
+        const bool dup2_ = (ct & (CT_CUT | CT_JUNC)) != 0, mir_ = cg && i >= 1 && i <= CGRID_GHOST_ROWS;
+        const bool n2ok = !(dup2_ || mir_) || in_bounds(n2 >= rlo * nt && n2 < nr * nt, a.status);
+        const bool dup2 = dup2_ && n2ok;
+        const bool mir = mir_ && n2ok;
         const int n = i * nt + j;
         const int m = (ti + T::HM) * T::MW + tj + T::HM;   // node in M coords
         const R* row = srow + (ti + T::HM) * RS;
@@ -996,10 +1018,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         // departure solve of this node for a displacement (dx, dy)
         auto departure = [&](int inode, R dx, R dy, int& base, R& xi, R& eta) -> bool {
             if constexpr (GEN)
-                return depart_gen<R, TJ>(sC, sJ + 4 * dn, inode, j, i0, j0, nr, pi0, sj0, T::PWS, dx, dy, base, xi, eta,
-                                         dup2 || pb, pb);
+                return depart_gen<R, TI, TJ>(sC, sJ + 4 * dn, inode, j, i0, j0, nr, pi0, sj0, T::PWS, dx, dy, base, xi, eta,
+                                         dup2 || pb, pb, a.status) &&
+                       in_bounds(base >= 0 && base + 2 * T::PWS + 2 < T::PSS, a.status);
             else
-                return depart(geo, inode, dx, dy, base, xi, eta);
+                return depart(geo, inode, dx, dy, base, xi, eta) &&
+                       in_bounds(base >= 0 && base + 2 * T::PWS + 2 < T::PSS, a.status);
         };
         if (!GEN && !moved && i > 0) {
             // a node the blend does not move: c_hat = c, and the rest
@@ -1013,7 +1037,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 int base;
                 R xi, eta;
                 R2 v;
-                if (depart_static<decltype(cxc)::value, decltype(cyc)::value>(geo, dt, base, xi, eta)) {
+                if (depart_static<decltype(cxc)::value, decltype(cyc)::value>(geo, dt, base, xi, eta) &&
+                    in_bounds(base >= 0 && base + 2 * T::PWS + 2 < T::PSS, a.status)) {
                     R Lx[3], Ly[3];
                     lagrange3(xi, Lx);
                     lagrange3(eta, Ly);
@@ -1089,10 +1114,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                         const int c2 = ctype(wb + b2);
                         if ((c2 & CT_WALL) && !(c2 & CT_JUNC)) mw |= 1u << b2;
                     }
+                const bool wok = in_bounds(w0 >= 0 && w0 + 2 * T::MW + 2 < T::MS, a.status);
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
                     for (int bb = 0; bb < 3; ++bb) {
+                        if (!wok) continue;
                         const R wgt = Lx[aa] * Ly[bb];
                         const bool far = aa == 2 && ((mw >> bb) & 1u);
                         const int c2 = nt - 1 - wb - bb;

@@ -18,9 +18,9 @@ FP64 = 0
 FP32 = 1
 FIELD_MOMENTS, FIELD_POPULATIONS = 0, 1
 
-OK, EINVAL, ENOMEM, ECUDA, EDEPARTURE, ENONPHYS, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, EDEPARTURE, ENONPHYS, ETIMEOUT, ESTATE, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7, -8
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDEPARTURE: "EDEPARTURE",
-          ENONPHYS: "ENONPHYS", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
+          ENONPHYS: "ENONPHYS", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE", EBOUNDS: "EBOUNDS"}
 
 EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbfsi_blend_mesh",
             "lbfsi_step", "lbfsi_body_forces", "lbfsi_advance_bodies", "lbfsi_get_body_state",
