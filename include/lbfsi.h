@@ -196,9 +196,20 @@ int lbfsi_create_mesh_box(const lbfsi_mesh_box_desc* d, void* cuda_stream, lbfsi
  * j -> ntheta-1-j, the cut nodes and the chains' ends (the junctions) one
  * point with their mirrors.  A body that row 0 wraps around is one chain
  * (the single C-grid: walls = {n_cut, ntheta-1-n_cut}); a body downstream of
- * another is an upper and a lower chain.  The load of a solve is the sum
- * over all chains, so all walls belong to the solve's one body: rigidly
- * linked bodies (its rigid zone must contain every wall). */
+ * another is an upper and a lower chain.
+ * With nbody <= 1 every chain belongs to the solve's one body: its load is
+ * the sum over all chains (rigidly linked bodies; the rigid zone must
+ * contain every wall).  With nbody in 2..4 the bodies are independent
+ * (Sec. II D, one blended map per body, the mesh displacements adding):
+ * wall_body[k] names chain k's body (mirrored chains, e.g. the upper and
+ * lower chain of a downstream body, name the same one; every body owns a
+ * chain), each body has its own degrees of freedom, load (summed over its
+ * chains, moment about its own reference point) and RK4 update, and bodies
+ * and every per-solve body array are [nbatch][nbody]: lbfsi_blend_mesh,
+ * lbfsi_body_forces, lbfsi_advance_bodies, lbfsi_get_body_state and
+ * lbfsi_step_record take one entry per (solve, body).  Each wall must lie in
+ * its body's rigid zone and outside every other body's blended region
+ * (r_out), and the blended regions of moving bodies must not overlap. */
 typedef struct {
     int nr, ntheta;             /* nr >= 5; ntheta odd >= 7 */
     int nwalls;                 /* wall chains, >= 1 */
@@ -207,7 +218,9 @@ typedef struct {
     double xc, yc;              /* mesh centre (reference point of the geometry)   */
     int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations             */
     int nbatch;                 /* independent solves sharing the mesh, >= 1        */
-    const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)      */
+    const lbfsi_body_desc* bodies;  /* [nbatch][max(nbody, 1)] (host)               */
+    int nbody;                  /* independent bodies per solve (0 or 1: one)       */
+    const int* wall_body;       /* [nwalls] body of each chain, or NULL (all body 0) */
 } lbfsi_mesh_cgrid_walls_desc;
 
 /* Create a mesh handle on a C-grid with several wall chains; otherwise as

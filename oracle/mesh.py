@@ -277,7 +277,7 @@ class CGridMesh(Q2Mesh):
     nine nodes of a window that starts below row 0, its row 0 included, are
     the mirrored ones."""
 
-    def __init__(self, X, n_cut=None, walls=None):
+    def __init__(self, X, n_cut=None, walls=None, wall_body=None):
         super().__init__(X, periodic_i=False, periodic_j=False)
         Nj = self.Nj
         if Nj % 2 == 0:
@@ -287,6 +287,10 @@ class CGridMesh(Q2Mesh):
                 raise ValueError("n_cut must be even, >= 2 and leave a wall of at least 3 nodes")
             walls = [(n_cut, Nj - 1 - n_cut)]
         self.walls = [(int(a), int(b)) for a, b in walls]
+        # the body each chain belongs to (reading R32: independent bodies)
+        self.wall_body = [0] * len(self.walls) if wall_body is None else [int(b) for b in wall_body]
+        if len(self.wall_body) != len(self.walls):
+            raise ValueError("one body index per wall chain")
         wall = np.zeros(Nj, dtype=bool)
         for a, b in self.walls:
             if a < 1 or b > Nj - 2 or a % 2 or b % 2 or b - a < 2:

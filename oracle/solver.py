@@ -72,6 +72,7 @@ class StepResult:
     M: np.ndarray
     force: tuple
     missing: np.ndarray
+    forces: list = None      # per body (C-grids with several bodies)
 
 
 class Solver:
@@ -222,11 +223,11 @@ class Solver:
         self.n += 1
         return StepResult(f_pre, g_pre, f_post, g_post, M, force, missing)
 
-    def _advance_bodies(self, force):
-        """Step 8 (RK4 of every body with the load held, Sec. III B)."""
+    def _advance_bodies(self, forces):
+        """Step 8 (RK4 of every body with its load held, Sec. III B)."""
         dt = self.dt
         new_S = []
-        for b, st in zip(self.bodies, self.S):
+        for b, st, force in zip(self.bodies, self.S, forces):
             s = dict(st)
             if b["dof"] == 1:
                 s["h"], s["hdot"] = structure.advance_one_dof(
@@ -316,28 +317,32 @@ class Solver:
         g_post = np.where(far[None], g_far, g_post)
         f_post[:, 0, dup] = f_post[:, 0, own]
         g_post[:, 0, dup] = g_post[:, 0, own]
-        # 7. force and moment on the wall chains (summed: the bodies of a
-        # C-grid move as one, reading R31)
-        force = (0.0, 0.0, 0.0)
-        if self.bodies:
-            b, st = self.bodies[0], self.S[0]
+        # 7. force and moment on each body: the sum over its wall chains
+        # (one body holding several chains: rigidly linked bodies, reading
+        # R31; several bodies: reading R32), the moment about its own
+        # reference point
+        per_body = []
+        for k, (b, st) in enumerate(zip(self.bodies, self.S)):
             x_ref = np.array([b["xp"], b["yp"] + st["h"]])
             tot = np.zeros(3)
-            for a_, b_ in mesh.walls:
+            for (a_, b_), owner in zip(mesh.walls, mesh.wall_body):
+                if owner != k:
+                    continue
                 cols = np.arange(a_, b_ + 1)
                 sxx, sxy, syy = forces.node_stress(f_pre[:, 0, cols], g_pre[:, 0, cols], Cv,
                                                    self.mu, dt, self.Pr)
                 x_wall = ale.mesh_position(X[0, cols], self.bodies, self.S)
                 tot += np.array(forces.wall_force(x_wall, sxx, sxy, syy, x_ref, closed=False))
-            force = tuple(float(v) for v in tot)
+            per_body.append(tuple(float(v) for v in tot))
+        force = per_body[0] if per_body else (0.0, 0.0, 0.0)
         # 8. structural update
-        new_S = self._advance_bodies(force)
+        new_S = self._advance_bodies(per_body)
         self.S_prev = [dict(s) for s in self.S]
         self.S = new_S
         self.f, self.g = f_post, g_post
         self.M_prev = M
         self.n += 1
-        return StepResult(f_pre, g_pre, f_post, g_post, M, force, missing)
+        return StepResult(f_pre, g_pre, f_post, g_post, M, force, missing, per_body)
 
     def run(self, nsteps):
         res = None

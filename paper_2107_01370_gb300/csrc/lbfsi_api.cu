@@ -40,6 +40,8 @@ struct lbfsi_mesh_s {
     lbfsi::DeviceMesh dmesh;
     lbfsi::CudaMallocMemory mem;
     int nbatch = 0, precision = 0, variant = 4, order = 1, tile_rows = 16, tiles_per_solve = 0;
+    int nbody = 1;                       // bodies per solve (independent bodies of a C-grid)
+    size_t slots() const { return (size_t)nbatch * (size_t)nbody; }   // body records
     size_t esize = 8;
     cudaStream_t stream = nullptr;
     std::vector<lbfsi_body_desc> bodies;
@@ -47,13 +49,13 @@ struct lbfsi_mesh_s {
     void* d_M[2] = {nullptr, nullptr};
     void* d_ppost = nullptr;             // collide-only output, same layout
     double* d_stage = nullptr;  // [nbatch][4][N] float64 staging
-    StepMaps* d_maps[2] = {nullptr, nullptr};  // [nbatch] each
+    StepMaps* d_maps[2] = {nullptr, nullptr};  // [nbatch][nbody] each
     BodyStateDev* d_state_a = nullptr;          // host-given states staging
     BodyStateDev* d_state_b = nullptr;
     double* d_loads_tmp = nullptr;
-    double* d_part = nullptr;        // [nbatch][ntj][3] load partials
+    double* d_part = nullptr;        // [nbatch][nbody][ntj][3] load partials
     unsigned* d_counter = nullptr;   // [nbatch][2] CTA completion count, step number
-    BodyDev* d_bodies = nullptr;     // [nbatch]
+    BodyDev* d_bodies = nullptr;     // [nbatch][nbody]
     lbfsi::MeshDev* d_meshdev = nullptr;
     SolveDev* d_solves = nullptr;    // [nbatch]
     unsigned* d_status = nullptr;
@@ -204,15 +206,17 @@ int upload_solves(lbfsi_mesh m) {
         SolveDev& s = m->solves[b];
         s.mesh = 0;
         s.ntiles = m->tiles_per_solve;
+        s.nbody = m->nbody;
+        const size_t bb = (size_t)b * m->nbody;
         for (int p = 0; p < 2; ++p) {
             s.p[p] = (char*)m->d_p[p] + ((size_t)b * 18 * N + 2 * g0) * es;
             s.M[p] = (char*)m->d_M[p] + ((size_t)b * 4 * N + g0) * es;
-            s.maps[p] = m->d_maps[p] + b;
+            s.maps[p] = m->d_maps[p] + bb;
         }
         s.ppost = m->d_ppost ? (char*)m->d_ppost + ((size_t)b * 18 * N + 2 * g0) * es : nullptr;
-        s.part = m->d_part + (size_t)b * m->host.ntj * 3;
+        s.part = m->d_part + bb * m->host.ntj * 3;
         s.counter = m->d_counter + 2 * b;
-        s.body = m->d_bodies + b;
+        s.body = m->d_bodies + bb;
     }
     cudaError_t e = cudaMemcpyAsync(m->d_solves, m->solves.data(), m->solves.size() * sizeof(SolveDev),
                                     cudaMemcpyHostToDevice, m->stream);
@@ -361,11 +365,14 @@ int lbfsi_create_mesh_cgrid_walls(const lbfsi_mesh_cgrid_walls_desc* d, void* cu
     int rc = check_common(d->nr + lbfsi::CGRID_GHOST_ROWS, d->ntheta, d->precision, d->nbatch, d->bodies, out);
     if (rc) return rc;
     auto m = new lbfsi_mesh_s();
-    rc = lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->nwalls, d->walls, d->X, d->xc, d->yc, m->host);
+    const int nbody = d->nbody < 1 ? 1 : d->nbody;
+    rc = lbfsi::build_host_mesh_c(d->nr, d->ntheta, d->nwalls, d->walls, d->X, d->xc, d->yc, m->host, nbody,
+                                  d->wall_body);
     if (rc) {
         delete m;
         return rc;
     }
+    m->nbody = nbody;
     return create_common(m, d->precision, d->nbatch, d->bodies, cuda_stream, out);
 }
 
@@ -396,27 +403,27 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
     m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
     const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows;
     m->tiles_per_solve = nti * m->host.ntj;
-    m->bodies.assign(bodies, bodies + nbatch);
+    m->bodies.assign(bodies, bodies + m->slots());
     m->solves.assign(m->nbatch, SolveDev{});
     rc = lbfsi::upload_mesh(m->host, m->precision, m->mem, m->stream, m->dmesh);
     if (rc) {
         delete m;
         return rc;
     }
-    const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
+    const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch, ns = m->slots();
     const int ntj = m->host.ntj;
     cudaError_t e = cudaSuccess;
 #define LB_ALLOC(ptr, cnt) \
     if (e == cudaSuccess) e = dalloc(&(ptr), (cnt));
     LB_ALLOC(m->d_stage, nb * 4 * N);
-    LB_ALLOC(m->d_maps[0], nb);
-    LB_ALLOC(m->d_maps[1], nb);
-    LB_ALLOC(m->d_state_a, nb);
-    LB_ALLOC(m->d_state_b, nb);
-    LB_ALLOC(m->d_loads_tmp, nb * 3);
-    LB_ALLOC(m->d_part, nb * ntj * 3);
+    LB_ALLOC(m->d_maps[0], ns);
+    LB_ALLOC(m->d_maps[1], ns);
+    LB_ALLOC(m->d_state_a, ns);
+    LB_ALLOC(m->d_state_b, ns);
+    LB_ALLOC(m->d_loads_tmp, ns * 3);
+    LB_ALLOC(m->d_part, ns * ntj * 3);
     LB_ALLOC(m->d_counter, 2 * nb);
-    LB_ALLOC(m->d_bodies, nb);
+    LB_ALLOC(m->d_bodies, ns);
     LB_ALLOC(m->d_meshdev, 1);
     LB_ALLOC(m->d_solves, nb);
     LB_ALLOC(m->d_status, 1);
@@ -435,7 +442,7 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
     e = cudaMemcpy(m->d_meshdev, &m->dmesh.dev, sizeof(lbfsi::MeshDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(m->d_counter, 0, 2 * nb * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(m->d_part, 0, nb * ntj * 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(m->d_part, 0, ns * ntj * 3 * sizeof(double));
     if (e != cudaSuccess) {
         free_all(m);
         delete m;
@@ -464,8 +471,9 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     const size_t N = (size_t)m->host.N, nb = (size_t)m->nbatch;
     for (auto& s : m->solves) s = proto;
     m->dt = p->dt;
-    std::vector<BodyDev> bd(nb);
-    for (size_t b = 0; b < nb; ++b) bd[b] = lbfsi::body_dev(m->bodies[b], proto.rho_inf, proto.uinf_x);
+    const size_t ns = m->slots();
+    std::vector<BodyDev> bd(ns);
+    for (size_t b = 0; b < ns; ++b) bd[b] = lbfsi::body_dev(m->bodies[b], proto.rho_inf, proto.uinf_x);
     std::vector<double> M(nb * 4 * N);
     if (rho_u_T) {
         std::memcpy(M.data(), rho_u_T, M.size() * sizeof(double));
@@ -478,15 +486,15 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
                 M[(b * 4 + 3) * N + n] = proto.T_inf;
             }
     }
-    std::vector<BodyStateDev> zero(nb, BodyStateDev{0.0, 0.0, 0.0, 0.0});
-    std::vector<double> zl(nb * 3, 0.0);
+    std::vector<BodyStateDev> zero(ns, BodyStateDev{0.0, 0.0, 0.0, 0.0});
+    std::vector<double> zl(ns * 3, 0.0);
     unify_cut_copies(m->host, M.data(), nb * 4, 1);
     if (m->host.G) M = expand_rows(m->host, M.data(), nb * 4, 1);
-    cudaError_t e = cudaMemcpyAsync(m->d_bodies, bd.data(), nb * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
+    cudaError_t e = cudaMemcpyAsync(m->d_bodies, bd.data(), ns * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->d_state_a, zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
+        e = cudaMemcpyAsync(m->d_state_a, zero.data(), ns * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_loads_tmp, zl.data(), zl.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream);
@@ -500,7 +508,7 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     e = lbfsi::launch_prepare(m->d_bodies, m->d_state_a, m->d_state_a, m->d_state_a, m->d_loads_tmp, m->dt,
-                              m->nbatch, m->d_maps[0], m->stream);
+                              (int)ns, m->d_maps[0], m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "prepare kernel");
     e = cudaStreamSynchronize(m->stream);
@@ -512,7 +520,7 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
 int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_body_state* prev) {
     if (!m || !state) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    const size_t nb = (size_t)m->nbatch;
+    const size_t nb = m->slots();
     static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
     const lbfsi_body_state* pv = prev ? prev : state;
     cudaError_t e = cudaMemcpyAsync(m->d_state_a, state, nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
@@ -522,7 +530,7 @@ int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_bo
     // state of the last streamed step
     if (e == cudaSuccess)
         e = lbfsi::launch_prepare(m->d_bodies, m->first() ? m->d_state_a : nullptr, m->d_state_a, m->d_state_b,
-                                  nullptr, m->dt, m->nbatch, m->d_maps[m->cur()], m->stream);
+                                  nullptr, m->dt, (int)nb, m->d_maps[m->cur()], m->stream);
     m->launches++;
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "blend_mesh");
@@ -575,7 +583,7 @@ int lbfsi_synchronize(lbfsi_mesh m) {
 }
 
 static int download_maps(lbfsi_mesh m, std::vector<StepMaps>& out) {
-    out.resize(m->nbatch);
+    out.resize(m->slots());
     cudaError_t e = cudaMemcpyAsync(out.data(), m->d_maps[m->cur()], out.size() * sizeof(StepMaps),
                                     cudaMemcpyDeviceToHost, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "maps copy");
@@ -587,7 +595,7 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
     if (!m || !loads_out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
-    const size_t nb = (size_t)m->nbatch;
+    const size_t nb = m->slots();   // one record per (solve, body)
     const size_t lb = nb * 3 * sizeof(double), sbytes = nb * sizeof(BodyStateDev);
     const size_t need = (size_t)nsteps * (lb + (states_out ? sbytes : 0));
     if (need > m->h_rec_bytes) {
@@ -639,7 +647,7 @@ int lbfsi_body_forces(lbfsi_mesh m, double* out) {
     std::vector<StepMaps> mp;
     const int rc = download_maps(m, mp);
     if (rc) return rc;
-    for (int b = 0; b < m->nbatch; ++b)
+    for (size_t b = 0; b < m->slots(); ++b)
         for (int c = 0; c < 3; ++c) out[b * 3 + c] = mp[b].loads[c];
     return LBFSI_OK;
 }
@@ -647,7 +655,7 @@ int lbfsi_body_forces(lbfsi_mesh m, double* out) {
 int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
     if (!m) return fail(LBFSI_EINVAL, "null mesh");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
-    const size_t nb = (size_t)m->nbatch;
+    const size_t nb = m->slots();
     std::vector<double> ld(nb * 3);
     if (loads) {
         std::memcpy(ld.data(), loads, ld.size() * sizeof(double));
@@ -660,7 +668,7 @@ int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt) {
     }
     cudaError_t e = cudaMemcpyAsync(m->d_loads_tmp, ld.data(), ld.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, (long long)m->host_k, m->nbatch,
+        e = lbfsi::launch_advance(m->d_bodies, m->d_loads_tmp, dt, (long long)m->host_k, (int)nb,
                                   m->d_maps[m->cur()], m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "advance_bodies");
@@ -673,7 +681,7 @@ int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out) {
     std::vector<StepMaps> mp;
     const int rc = download_maps(m, mp);
     if (rc) return rc;
-    for (int b = 0; b < m->nbatch; ++b) {
+    for (size_t b = 0; b < m->slots(); ++b) {
         out[b].h = mp[b].S_next.h;
         out[b].alpha = mp[b].S_next.alpha;
         out[b].hdot = mp[b].S_next.hdot;
@@ -779,13 +787,13 @@ struct CheckpointHeader {
     char magic[8];
     int32_t version, precision, nbatch, nr, nt, esize;
     uint32_t step;
-    uint32_t pad;
+    uint32_t nbody;   // 0 in checkpoints of one-body handles
 };
 constexpr char kMagic[8] = {'L', 'B', 'F', 'S', 'I', 'C', 'K', '1'};
 
 size_t checkpoint_bytes(lbfsi_mesh m) {
     const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
-    return sizeof(CheckpointHeader) + nb * 18 * N * m->esize + nb * 4 * N * m->esize + nb * sizeof(StepMaps);
+    return sizeof(CheckpointHeader) + nb * 18 * N * m->esize + nb * 4 * N * m->esize + m->slots() * sizeof(StepMaps);
 }
 }  // namespace
 
@@ -807,6 +815,7 @@ int lbfsi_checkpoint(lbfsi_mesh m, void* buf, size_t bytes) {
     h.nt = m->host.nt;
     h.esize = (int32_t)m->esize;
     h.step = m->host_k;
+    h.nbody = m->nbody > 1 ? (uint32_t)m->nbody : 0u;
     const size_t N = (size_t)m->host.Nx, nb = (size_t)m->nbatch;
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &h, sizeof(h));
@@ -816,7 +825,8 @@ int lbfsi_checkpoint(lbfsi_mesh m, void* buf, size_t bytes) {
     p += nb * 18 * N * m->esize;
     if (e == cudaSuccess) e = cudaMemcpyAsync(p, m->d_M[c], nb * 4 * N * m->esize, cudaMemcpyDeviceToHost, m->stream);
     p += nb * 4 * N * m->esize;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p, m->d_maps[c], nb * sizeof(StepMaps), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p, m->d_maps[c], m->slots() * sizeof(StepMaps), cudaMemcpyDeviceToHost, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
     return LBFSI_OK;
@@ -832,7 +842,7 @@ int lbfsi_restore(lbfsi_mesh m, const void* buf, size_t bytes) {
     if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != 1)
         return fail(LBFSI_EINVAL, "not a checkpoint of this library");
     if (h.precision != m->precision || h.nbatch != m->nbatch || h.nr != m->host.nr || h.nt != m->host.nt ||
-        h.esize != (int32_t)m->esize)
+        h.esize != (int32_t)m->esize || (h.nbody > 1 ? (int)h.nbody : 1) != m->nbody)
         return fail(LBFSI_EINVAL, "checkpoint of a different mesh, batch or precision");
     drop_graph(m);
     m->host_k = h.step;
@@ -843,7 +853,8 @@ int lbfsi_restore(lbfsi_mesh m, const void* buf, size_t bytes) {
     p += nb * 18 * N * m->esize;
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_M[c], p, nb * 4 * N * m->esize, cudaMemcpyHostToDevice, m->stream);
     p += nb * 4 * N * m->esize;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_maps[c], p, nb * sizeof(StepMaps), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_maps[c], p, m->slots() * sizeof(StepMaps), cudaMemcpyHostToDevice, m->stream);
     std::vector<unsigned> ctr(2 * nb);
     for (size_t b = 0; b < nb; ++b) {
         ctr[2 * b] = 0u;

@@ -293,6 +293,27 @@ __device__ __forceinline__ bool kinematics(const BodyMap<R>& bm, R X, R Y, R& F0
     return true;
 }
 
+// Kinematics of several bodies' blended maps: the displacements add
+// (Sec. II D), so F = I + sum_b (F_b - I) and V_G = sum_b V_b; a body whose
+// blended region does not hold the point adds nothing.
+template <typename R>
+__device__ __forceinline__ bool kinematics_sum(const BodyMap<R>* bm, int nb, R X, R Y, R& F00, R& F01,
+                                               R& F10, R& F11, R& vx, R& vy) {
+    bool moved = kinematics(bm[0], X, Y, F00, F01, F10, F11, vx, vy);
+    for (int b = 1; b < nb; ++b) {
+        R g00, g01, g10, g11, wx, wy;
+        if (!kinematics(bm[b], X, Y, g00, g01, g10, g11, wx, wy)) continue;
+        if (moved) {
+            F00 += g00 - R(1); F01 += g01; F10 += g10; F11 += g11 - R(1);
+            vx += wx; vy += wy;
+        } else {
+            F00 = g00; F01 = g01; F10 = g10; F11 = g11; vx = wx; vy = wy;
+        }
+        moved = true;
+    }
+    return moved;
+}
+
 // Fill a maps record: collision map from S_cur, stream maps from
 // (S_next, S_vgprev); the float maps are the float64 ones rounded.
 __host__ __device__ inline void build_maps(const BodyDev& b, const BodyStateDev& S_cur,

@@ -310,11 +310,21 @@ static void wall_geometry_chains(HostMesh& m) {
 }
 
 int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double* X, double xc, double yc,
-                      HostMesh& m) {
+                      HostMesh& m, int nbody, const int* wall_body) {
     if (nr < 5) return set_error(LBFSI_EINVAL, "nr must be >= 5");
     if (nt < 7 || nt % 2 == 0) return set_error(LBFSI_EINVAL, "a C-grid needs an odd node count (>= 7) along the C");
     if (!X || !walls) return set_error(LBFSI_EINVAL, "null coordinate or wall pointer");
     if (nwalls < 1) return set_error(LBFSI_EINVAL, "a C-grid needs at least one wall chain");
+    if (nbody < 1 || nbody > MAX_BODIES) return set_error(LBFSI_EINVAL, "nbody must be in 1 .. 4");
+    if (nbody > 1 && !wall_body) return set_error(LBFSI_EINVAL, "several bodies need the body of each wall chain");
+    std::vector<int> owned(nbody, 0);
+    for (int w = 0; w < nwalls && wall_body; ++w) {
+        if (wall_body[w] < 0 || wall_body[w] >= nbody) return set_error(LBFSI_EINVAL, "wall_body out of range");
+        owned[wall_body[w]] = 1;
+    }
+    for (int k = 0; k < nbody; ++k)
+        if (!owned[k] && wall_body) return set_error(LBFSI_EINVAL, "every body needs a wall chain");
+    m.nbody = nbody;
     const int G = CGRID_GHOST_ROWS;
     if (nr < G + 1) return set_error(LBFSI_EINVAL, "a C-grid needs nr > 4");
     // column classes: wall chains (even ends inside the outlets, no overlap),
@@ -327,12 +337,13 @@ int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double
             return set_error(LBFSI_EINVAL, "wall chains must run between even columns inside the outlets");
         for (int j = a; j <= b; ++j) {
             if (m.coltype[j] & CT_WALL) return set_error(LBFSI_EINVAL, "wall chains overlap");
-            m.coltype[j] = CT_WALL;
+            m.coltype[j] = CT_WALL | ((wall_body ? wall_body[w] : 0) << CT_BODY_SHIFT);
         }
     }
     for (int j = 0; j < nt; ++j)
         if (m.coltype[j] != m.coltype[nt - 1 - j])
-            return set_error(LBFSI_EINVAL, "the cut and the wall chains must be symmetric in j -> ntheta-1-j");
+            return set_error(LBFSI_EINVAL, "the cut and the wall chains (and their bodies) must be symmetric "
+                                           "in j -> ntheta-1-j");
     for (int j = 0; j < nt; ++j) {
         if (!(m.coltype[j] & CT_WALL)) continue;
         const bool before = j > 0 && (m.coltype[j - 1] & CT_CUT), after = j < nt - 1 && (m.coltype[j + 1] & CT_CUT);
@@ -551,8 +562,10 @@ int build_host_mesh_box(int ni, int nj, const double* X, const double* shift_i, 
 
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
     if (!bodies) return set_error(LBFSI_EINVAL, "null body pointer");
-    for (int k = 0; k < n; ++k) {
+    const int nbody = m.nbody;
+    for (int k = 0; k < n * nbody; ++k) {
         const lbfsi_body_desc& b = bodies[k];
+        const int own = k % nbody;
         if (b.dof < 0 || b.dof > 2) return set_error(LBFSI_EINVAL, "body dof must be 0, 1 or 2");
         if (b.dof == 0) continue;
         if (m.box) return set_error(LBFSI_EINVAL, "a periodic box has no wall: bodies must be fixed (dof 0)");
@@ -562,10 +575,20 @@ int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n) {
             return set_error(LBFSI_EINVAL, "forced pitching needs a finite amplitude and forced_periods >= 0");
         for (int j = 0; j < m.nt; ++j) {
             if (m.cgrid && !(m.coltype[j] & CT_WALL)) continue;   // the cut
+            const int owner = m.cgrid ? (m.coltype[j] >> CT_BODY_SHIFT) & (MAX_BODIES - 1) : 0;
             const double x = m.xw[2 * j] - b.xc;
             const double y = m.xw[2 * j + 1] - b.yc;
-            if (std::sqrt(x * x + y * y) >= b.r_in)
+            const double dist = std::sqrt(x * x + y * y);
+            if (owner == own && dist >= b.r_in)
                 return set_error(LBFSI_EINVAL, "the wall must lie inside the rigid zone (r_in)");
+            if (owner != own && dist <= b.r_out)
+                return set_error(LBFSI_EINVAL, "another body's wall lies inside this body's blended region (r_out)");
+        }
+        for (int o = k - own; o < k; ++o) {
+            const lbfsi_body_desc& c = bodies[o];
+            if (c.dof == 0) continue;
+            if (std::hypot(b.xc - c.xc, b.yc - c.yc) < b.r_out + c.r_out)
+                return set_error(LBFSI_EINVAL, "the blended regions of two moving bodies overlap");
         }
     }
     return LBFSI_OK;

@@ -36,9 +36,11 @@ struct HostMesh {
     double xm = 0, ym = 0;
     bool general = false;
     // C-grid: the wall chains (inclusive row-0 column ranges) and the class
-    // of every row-0 column (CT_*)
+    // of every row-0 column (CT_*, a wall column's body from CT_BODY_SHIFT);
+    // nbody: bodies per solve (the chains' owners)
     bool cgrid = false;
     std::vector<int> walls, coltype;
+    int nbody = 1;
     // doubly periodic box (no wall, no far field): rows wrap as well
     bool box = false;
     std::vector<double> r, e, n0, wall_geo, rowtab, coltab, xw, fardir, X, jinv, cellc;
@@ -68,9 +70,10 @@ int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, Ho
 // column ranges, even ends; the rest of row 0 is cut, symmetric in
 // j -> nt-1-j, its nodes and the chains' ends one point with their mirrors):
 // the arrays carry G mirrored rows below row 0 (node (-k, j) = node
-// (k, nt-1-j)).
+// (k, nt-1-j)).  wall_body (NULL: every chain body 0) names the body of each
+// chain among nbody independent bodies; mirrored chains share their body.
 int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double* X, double xc, double yc,
-                      HostMesh& out);
+                      HostMesh& out, int nbody = 1, const int* wall_body = nullptr);
 
 // A doubly periodic box given by the node coordinates X [ni][nj][2] of one
 // period and the period vectors along i and j (node (i + ni, j) = node (i, j)
@@ -78,7 +81,9 @@ int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double
 int build_host_mesh_box(int ni, int nj, const double* X, const double* shift_i, const double* shift_j,
                         HostMesh& out);
 
-// Check bodies against a mesh (dof range, blend radii, wall inside the rigid zone).
+// Check the bodies of n solves ([n][m.nbody]) against a mesh: dof range,
+// blend radii, each wall inside its own body's rigid zone and outside every
+// other body's blended region, blended regions of moving bodies disjoint.
 int validate_bodies(const HostMesh& m, const lbfsi_body_desc* bodies, int n);
 
 // Dimensional ODE coefficients from the nondimensional groups.

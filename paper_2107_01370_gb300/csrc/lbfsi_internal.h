@@ -77,6 +77,10 @@ constexpr int CGRID_GHOST_ROWS = 4;
 // for a junction whether its cut neighbour is the next column (else the
 // previous one).
 enum : int { CT_CUT = 1, CT_WALL = 2, CT_JUNC = 4, CT_DUP = 8, CT_JFWD = 16 };
+// A wall column's body (C-grids with independent bodies): bits from
+// CT_BODY_SHIFT of its class.  At most MAX_BODIES bodies per solve.
+constexpr int MAX_BODIES = 4;
+enum : int { CT_BODY_SHIFT = 5 };
 
 // Geometry of one O-grid mesh shape, shared by every solve on it (device).
 struct MeshDev {
@@ -111,7 +115,9 @@ struct MeshDev {
     int box;
 };
 
-// One solve (one body, one set of fields on one mesh).  Buffers are
+// One solve (one set of fields on one mesh and its bodies: nbody > 1 only on
+// general meshes, where the maps, body and load-partial arrays hold nbody
+// consecutive records).  Buffers are
 // ping-pong pairs; which one holds the current state follows from the solve's
 // step number k (counter[1]): after k step launches the state is in buffer
 // k & 1, and the launch with k == 0 streams from the initial (post-collision)
@@ -121,17 +127,18 @@ struct MeshDev {
 struct SolveDev {
     int mesh;
     int ntiles;                    // CTAs of this solve in every step launch
+    int nbody = 1;                 // bodies (maps / body records per solve)
     // flow (float64 and float copies, so that no thread of the float path
     // converts or divides in float64)
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
     float dt_f, mu_f, Cv_f, Pr_f, iPr_f, rho_inf_f, uinf_x_f, uinf_y_f, T_inf_f, pad_f;
     void* p[2];                    // populations, (f_q, g_q) pairs [9][N]
     void* M[2];                    // moments [4][N]
-    StepMaps* maps[2];
+    StepMaps* maps[2];             // [nbody] each
     void* ppost;                   // collide-only output (post-collision pairs)
-    double* part;                  // [ntj][3] load partials of the streamed step
+    double* part;                  // [nbody][ntj][3] load partials of the streamed step
     unsigned* counter;             // [2]: CTA completion count, step number k
-    const BodyDev* body;
+    const BodyDev* body;           // [nbody]
 };
 
 // One CTA of a step launch: a tile of one solve.  The entry repeats the

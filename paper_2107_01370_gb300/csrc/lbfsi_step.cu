@@ -490,9 +490,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     R* sJ = sX + 2 * T::DS;                         // general: [DS][4] inverse metric
     R* sC = sJ + 4 * T::DS;                         // general: [TI+1][TJ+1][CELLC] cells
 
-    __shared__ BodyMap<R> mapK, mapS;
-    __shared__ BodyMap<double> mapSd;
+    // blended maps of the solve's bodies (several only on general meshes)
+    constexpr int MB = GEN ? MAX_BODIES : 1;
+    __shared__ BodyMap<R> mapK[MB], mapS[MB];
+    __shared__ BodyMap<double> mapSd[MB];
     __shared__ double s_red[3][TJ];
+    __shared__ int s_bid[GEN ? TJ : 1];
     __shared__ SolveDev s_sol;
     __shared__ MeshDev s_mesh;
 
@@ -525,6 +528,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         ctr = tg->counter;
         mptr = tg->maps;
     }
+    // bodies of the solve (maps, body records and load partials per body)
+    int nb = 1;
+    if constexpr (GEN) nb = UNIFORM ? a.usol.nbody : __ldg(&sg->nbody);
     // C-grid (general meshes): rows from -4 are stored (the mirrored rows),
     // the angular index does not wrap
     int cg = 0, pb = 0;
@@ -553,18 +559,20 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                      : (kstep == 0u || split) ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM;
     const bool from_post = split && kstep != 0u && !a.collide_only;
     {
-        const StepMaps* mi = (cur ? mptr[1] : mptr[0]) + sb;
+        const StepMaps* mi = (cur ? mptr[1] : mptr[0]) + (size_t)sb * nb;
         if (!UNIFORM && w == 1) cp_async_words(&s_sol, sg, (int)(sizeof(SolveDev) / 4), l);
         if (!UNIFORM && w == 2) cp_async_words(&s_mesh, mg, (int)(sizeof(MeshDev) / 4), l);
-        if (w == 3) {
-            if constexpr (sizeof(R) == 4) cp_async_words(&mapK, &mi->Kf, (int)(sizeof(BodyMap<R>) / 4), l);
-            else cp_async_words(&mapK, &mi->Kd, (int)(sizeof(BodyMap<R>) / 4), l);
+        for (int b = 0; b < nb; ++b) {
+            if (w == 3) {
+                if constexpr (sizeof(R) == 4) cp_async_words(&mapK[b], &mi[b].Kf, (int)(sizeof(BodyMap<R>) / 4), l);
+                else cp_async_words(&mapK[b], &mi[b].Kd, (int)(sizeof(BodyMap<R>) / 4), l);
+            }
+            if (w == 4) {
+                if constexpr (sizeof(R) == 4) cp_async_words(&mapS[b], &mi[b].Sf, (int)(sizeof(BodyMap<R>) / 4), l);
+                else cp_async_words(&mapS[b], &mi[b].Sd, (int)(sizeof(BodyMap<R>) / 4), l);
+            }
+            if (w == 5) cp_async_words(&mapSd[b], &mi[b].Sd, (int)(sizeof(BodyMap<double>) / 4), l);
         }
-        if (w == 4) {
-            if constexpr (sizeof(R) == 4) cp_async_words(&mapS, &mi->Sf, (int)(sizeof(BodyMap<R>) / 4), l);
-            else cp_async_words(&mapS, &mi->Sd, (int)(sizeof(BodyMap<R>) / 4), l);
-        }
-        if (w == 5) cp_async_words(&mapSd, &mi->Sd, (int)(sizeof(BodyMap<double>) / 4), l);
     }
     // solve / mesh fields: kernel parameters for a uniform launch, the copied
     // records for a table launch (valid after the staging barrier)
@@ -734,14 +742,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // general path, which gives the same result.
     bool tile_static = false;
     if constexpr (!GEN) {
-        if (!mapS.active) {
+        if (!mapS[0].active) {
             tile_static = true;
         } else {
             // in the element type of the path (no float64 on the float path),
             // with a margin well above its rounding
             const R rmin = srow[RT_R] * pick<R>(MD(emin), MD(emin_f));   // first staged row
-            const R ox = xm - mapS.xc, oy = ym - mapS.yc;
-            const R r_out = mapS.r_in + rcp_(mapS.inv_w);
+            const R ox = xm - mapS[0].xc, oy = ym - mapS[0].yc;
+            const R r_out = mapS[0].r_in + rcp_(mapS[0].inv_w);
             tile_static = rmin - sqrt_(ox * ox + oy * oy) > r_out * (R(1) + R(1e-4)) + R(1e-5);
         }
     }
@@ -774,7 +782,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             R F00, F01, F10, F11, vx, vy;
             R G[4];
             if constexpr (GEN) {
-                kinematics(mapK, sX[2 * idx], sX[2 * idx + 1], F00, F01, F10, F11, vx, vy);
+                kinematics_sum(mapK, nb, sX[2 * idx], sX[2 * idx + 1], F00, F01, F10, F11, vx, vy);
                 R j00, j01, j10, j11;
                 ld4(sJ + 4 * idx, j00, j01, j10, j11);
                 grad_map_j(j00, j01, j10, j11, F00, F01, F10, F11, G);
@@ -792,7 +800,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 } else {
                     R ex, ey, u0, u1;
                     ld4(col + CT_E, ex, ey, u0, u1);
-                    kinematics(mapK, xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
+                    kinematics(mapK[0], xm + row[RT_R] * ex, ym + row[RT_R] * ey, F00, F01, F10, F11, vx, vy);
                     grad_map(row, col, F00, F01, F10, F11, G);
                 }
             }
@@ -908,6 +916,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         __syncthreads();
     }
     double fcx = 0.0, fcy = 0.0, fcm = 0.0;   // this thread's wall share (node row 0)
+    int fbid = 0;                              // the body of that wall node
 #pragma unroll 1
     for (int k = 0; k < NPT; ++k) {
         const int t = tid + k * NT;
@@ -983,14 +992,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         bool moved;
         const int dn = (ti + T::HD) * T::DW + tj + T::HD;   // this node in the +-3 region
         if constexpr (GEN) {
-            moved = kinematics(mapS, sX[2 * dn], sX[2 * dn + 1], F00, F01, F10, F11, vx, vy);
+            moved = kinematics_sum(mapS, nb, sX[2 * dn], sX[2 * dn + 1], F00, F01, F10, F11, vx, vy);
         } else {
             node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, geo);
             if (tile_static) {
                 F00 = R(1); F01 = R(0); F10 = R(0); F11 = R(1); vx = R(0); vy = R(0);
                 moved = false;
             } else {
-                moved = kinematics(mapS, xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
+                moved = kinematics(mapS[0], xm + geo.ri * geo.ex, ym + geo.ri * geo.ey, F00, F01, F10, F11, vx, vy);
             }
         }
         const R idF = rcp_(F00 * F11 - F01 * F10);
@@ -1001,7 +1010,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             // c_hat . n0 > 0, decided in float64 (Sec. III A)
             const double Xd = MD(xw)[2 * j], Yd = MD(xw)[2 * j + 1];
             double D00, D01, D10, D11, dvx, dvy;
-            kinematics(mapSd, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
+            if constexpr (GEN) kinematics_sum(mapSd, nb, Xd, Yd, D00, D01, D10, D11, dvx, dvy);
+            else kinematics(mapSd[0], Xd, Yd, D00, D01, D10, D11, dvx, dvy);
             const double idd = 1.0 / (D00 * D11 - D01 * D10);
             const double n0x = MD(n0)[2 * j], n0y = MD(n0)[2 * j + 1];
 #pragma unroll
@@ -1197,8 +1207,13 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             const double om = 1.0 / (0.5 + SD(mu) / (rho * Tn * SD(dt)));
             const double p = rho * Tn, am = 1.0 - 0.5 * om;
             const double sxx = -p - am * pxx, sxy = -am * pxy, syy = -p - am * pyy;
-            const double R00 = 1.0 + mapSd.a00, R01 = mapSd.a01, R10 = mapSd.a10, R11 = 1.0 + mapSd.a11;
-            const BodyDev& bd = *(SD(body) + sb);
+            // the wall node moves with its own body (its chain's body on a
+            // C-grid with several bodies): rotation and moment reference of
+            // that body
+            if constexpr (GEN) fbid = (ct >> CT_BODY_SHIFT) & (MAX_BODIES - 1);
+            const BodyMap<double>& mw = mapSd[fbid];
+            const double R00 = 1.0 + mw.a00, R01 = mw.a01, R10 = mw.a10, R11 = 1.0 + mw.a11;
+            const BodyDev& bd = *(SD(body) + (size_t)sb * nb + fbid);
             const double Xd = MD(xw)[2 * j] - bd.xp;
             const double Yd = MD(xw)[2 * j + 1] - bd.yp;
             const double rx = R00 * Xd + R01 * Yd, ry = R10 * Xd + R11 * Yd;
@@ -1219,19 +1234,24 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             s_red[0][tid] = fcx;
             s_red[1][tid] = fcy;
             s_red[2][tid] = fcm;
+            if constexpr (GEN) s_bid[tid] = fbid;
         }
         __syncthreads();
         if (tid == 0) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-            for (int t = 0; t < TJ; ++t) {
-                s0 += s_red[0][t];
-                s1 += s_red[1][t];
-                s2 += s_red[2][t];
+            // per body, in column order
+            for (int b = 0; b < nb; ++b) {
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                for (int t = 0; t < TJ; ++t) {
+                    if (GEN && s_bid[GEN ? t : 0] != b) continue;
+                    s0 += s_red[0][t];
+                    s1 += s_red[1][t];
+                    s2 += s_red[2][t];
+                }
+                double* po = SD(part) + ((size_t)sb * nb + b) * MD(ntj) * 3 + (size_t)tjx * 3;
+                po[0] = s0;
+                po[1] = s1;
+                po[2] = s2;
             }
-            double* po = SD(part) + (size_t)sb * MD(ntj) * 3 + (size_t)tjx * 3;
-            po[0] = s0;
-            po[1] = s1;
-            po[2] = s2;
         }
     }
     if (w == 0) {
@@ -1255,23 +1275,28 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         if ((!host_step || i0 == 0) && done == ntiles - 1u) {
             asm volatile("fence.acq_rel.gpu;" ::: "memory");
             const int ntj = MD(ntj);
-            const double* part = SD(part) + (size_t)sb * ntj * 3;
-            // lane t holds the partials of tiles t, t + 32, ...; the sum runs
-            // over lanes in order (for ntj <= 32: tile order)
-            double v[3] = {0.0, 0.0, 0.0};
-            for (int t = l; t < ntj; t += 32)
-                for (int c = 0; c < 3; ++c) v[c] += __ldcg(part + (size_t)t * 3 + c);
-            double F[3] = {0.0, 0.0, 0.0};
-            for (int t = 0; t < 32; ++t)
-                for (int c = 0; c < 3; ++c) F[c] += __shfl_sync(0xffffffffu, v[c], t);
+            for (int b = 0; b < nb; ++b) {
+                const size_t sbb = (size_t)sb * nb + b;
+                const double* part = SD(part) + sbb * ntj * 3;
+                // lane t holds the partials of tiles t, t + 32, ...; the sum
+                // runs over lanes in order (for ntj <= 32: tile order)
+                double v[3] = {0.0, 0.0, 0.0};
+                for (int t = l; t < ntj; t += 32)
+                    for (int c = 0; c < 3; ++c) v[c] += __ldcg(part + (size_t)t * 3 + c);
+                double F[3] = {0.0, 0.0, 0.0};
+                for (int t = 0; t < 32; ++t)
+                    for (int c = 0; c < 3; ++c) F[c] += __shfl_sync(0xffffffffu, v[c], t);
+                if (l == 0) {
+                    const BodyDev bd = *(SD(body) + sbb);
+                    const BodyStateDev Sn = ((cur ? mptr[1] : mptr[0]) + sbb)->S_next;
+                    const BodyStateDev Snew = rk4_body(bd, Sn, F[1], F[2], SD(dt), (long long)kstep);
+                    StepMaps mo;
+                    build_maps(bd, Sn, Snew, Sn, SD(dt), mo);
+                    for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
+                    *((cur ? mptr[0] : mptr[1]) + sbb) = mo;
+                }
+            }
             if (l == 0) {
-                const BodyDev bd = *(SD(body) + sb);
-                const BodyStateDev Sn = ((cur ? mptr[1] : mptr[0]) + sb)->S_next;
-                const BodyStateDev Snew = rk4_body(bd, Sn, F[1], F[2], SD(dt), (long long)kstep);
-                StepMaps mo;
-                build_maps(bd, Sn, Snew, Sn, SD(dt), mo);
-                for (int c = 0; c < 3; ++c) mo.loads[c] = F[c];
-                *((cur ? mptr[0] : mptr[1]) + sb) = mo;
                 ctr[0] = 0u;
                 ctr[1] = kstep + 1u;
             }

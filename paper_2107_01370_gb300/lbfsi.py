@@ -93,7 +93,8 @@ class MeshCGridWallsDesc(ctypes.Structure):
     _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nwalls", ctypes.c_int),
                 ("walls", ctypes.POINTER(ctypes.c_int)), ("X", ctypes.POINTER(ctypes.c_double)),
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
-                ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc))]
+                ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc)),
+                ("nbody", ctypes.c_int), ("wall_body", ctypes.POINTER(ctypes.c_int))]
 
 
 class MeshCGridDesc(ctypes.Structure):
@@ -230,6 +231,17 @@ def step_variants(precision) -> int:
 class Mesh:
     """Handle of one O-grid mesh with nbatch independent solves."""
 
+    nbody = 1   # bodies per solve (several: independent bodies of a C-grid)
+
+    @property
+    def _bshape(self):
+        # leading shape of the per-(solve, body) arrays
+        return (self.nbatch,) if self.nbody == 1 else (self.nbatch, self.nbody)
+
+    @property
+    def _nslots(self):
+        return self.nbatch * self.nbody
+
     def __init__(self, r, e, bodies, precision=FP64, centre=(0.0, 0.0), stream=None):
         lib = load()
         self._lib = lib
@@ -315,11 +327,14 @@ class Mesh:
         return self
 
     @classmethod
-    def cgrid_walls(cls, X, walls, bodies, precision=FP64, centre=(0.0, 0.0), stream=None):
+    def cgrid_walls(cls, X, walls, bodies, precision=FP64, centre=(0.0, 0.0), stream=None, wall_body=None):
         """Handle of a C-grid around several bodies: node coordinates X
         [nr, ntheta, 2] and the wall chains as inclusive column ranges
-        [(first, last), ...] (lbfsi_create_mesh_cgrid_walls); the walls move
-        as the solve's one body."""
+        [(first, last), ...] (lbfsi_create_mesh_cgrid_walls).  Without
+        wall_body the walls move as the solve's one body (bodies: one per
+        solve); with wall_body (the body index of each chain) the bodies are
+        independent and bodies holds one list of nbody bodies per solve; the
+        body accessors then take and return [nbatch, nbody, ...]."""
         self = cls.__new__(cls)
         lib = load()
         self._lib = lib
@@ -329,11 +344,20 @@ class Mesh:
         self.N = self.nr * self.nt
         self.nbatch = len(bodies)
         self.precision = precision
-        self._bodies = (BodyDesc * self.nbatch)(*[body_desc(b) for b in bodies])
+        if wall_body is None:
+            flat, wb = list(bodies), None
+        else:
+            self.nbody = len(bodies[0])
+            if any(len(bs) != self.nbody for bs in bodies):
+                raise ValueError("the same number of bodies for every solve")
+            flat = [b for bs in bodies for b in bs]
+            wb = (ctypes.c_int * len(wall_body))(*[int(k) for k in wall_body])
+        self._wall_body = wb
+        self._bodies = (BodyDesc * len(flat))(*[body_desc(b) for b in flat])
         w = [int(v) for ab in walls for v in ab]
         self._walls = (ctypes.c_int * len(w))(*w)
         d = MeshCGridWallsDesc(self.nr, self.nt, len(walls), self._walls, _dptr(self.X), centre[0], centre[1],
-                               precision, self.nbatch, self._bodies)
+                               precision, self.nbatch, self._bodies, self.nbody, wb)
         h = ctypes.c_void_p()
         self.h = None
         _check(lib.lbfsi_create_mesh_cgrid_walls(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
@@ -360,8 +384,10 @@ class Mesh:
             _check(self._lib.lbfsi_init_fields(self.h, ctypes.byref(p), _dptr(a)))
 
     def blend_mesh(self, states, prev=None):
-        s = (BodyState * self.nbatch)(*[BodyState(*x) for x in states])
-        pv = None if prev is None else (BodyState * self.nbatch)(*[BodyState(*x) for x in prev])
+        """states, prev: one (h, alpha, hdot, adot) per solve (per solve and
+        body, flat in that order, for independent bodies)."""
+        s = (BodyState * self._nslots)(*[BodyState(*x) for x in states])
+        pv = None if prev is None else (BodyState * self._nslots)(*[BodyState(*x) for x in prev])
         _check(self._lib.lbfsi_blend_mesh(self.h, s, pv))
 
     def step(self, n=1):
@@ -369,13 +395,14 @@ class Mesh:
 
     def step_record(self, n, states=False):
         """Advance n steps; per-step loads [n, nbatch, 3] (and body states
-        [n, nbatch, 4] as (h, alpha, hdot, adot) if states)."""
-        loads = np.empty((n, self.nbatch, 3))
-        st = (BodyState * (n * self.nbatch))() if states else None
+        [n, nbatch, 4] as (h, alpha, hdot, adot) if states); [n, nbatch,
+        nbody, ...] for independent bodies."""
+        loads = np.empty((n, *self._bshape, 3))
+        st = (BodyState * (n * self._nslots))() if states else None
         _check(self._lib.lbfsi_step_record(self.h, int(n), _dptr(loads), st))
         if not states:
             return loads
-        arr = np.array([(s.h, s.alpha, s.hdot, s.adot) for s in st]).reshape(n, self.nbatch, 4)
+        arr = np.array([(s.h, s.alpha, s.hdot, s.adot) for s in st]).reshape(n, *self._bshape, 4)
         return loads, arr
 
     def synchronize(self):
@@ -402,7 +429,7 @@ class Mesh:
         return _DeviceArray(ptr, shape, "<f8" if self.precision == FP64 else "<f4", self, row0)
 
     def body_forces(self, out=None):
-        out = np.empty((self.nbatch, 3)) if out is None else out
+        out = np.empty((*self._bshape, 3)) if out is None else out
         _check(self._lib.lbfsi_body_forces(self.h, _dptr(out)))
         return out
 
@@ -410,13 +437,16 @@ class Mesh:
         if loads is None:
             _check(self._lib.lbfsi_advance_bodies(self.h, None, float(dt)))
         else:
-            a = np.ascontiguousarray(loads, dtype=np.float64).reshape(self.nbatch, 3)
+            a = np.ascontiguousarray(loads, dtype=np.float64).reshape(self._nslots, 3)
             _check(self._lib.lbfsi_advance_bodies(self.h, _dptr(a), float(dt)))
 
     def body_state(self):
-        out = (BodyState * self.nbatch)()
+        """Body states, one dict per solve (a list of nbody dicts per solve
+        for independent bodies)."""
+        out = (BodyState * self._nslots)()
         _check(self._lib.lbfsi_get_body_state(self.h, out))
-        return [dict(h=s.h, alpha=s.alpha, hdot=s.hdot, adot=s.adot) for s in out]
+        d = [dict(h=s.h, alpha=s.alpha, hdot=s.hdot, adot=s.adot) for s in out]
+        return d if self.nbody == 1 else [d[k * self.nbody:(k + 1) * self.nbody] for k in range(self.nbatch)]
 
     def get_fields(self):
         out = np.empty((self.nbatch, 4, self.nr, self.nt))

@@ -197,3 +197,43 @@ def test_box_struct_layout_and_validation_without_gpu(tmp_path, lib):
     assert create(X, si, sj, dof=1) == lbfsi.EINVAL
     assert b"fixed" in lib.lbfsi_last_error()
     assert create(X, si, (0.0, -6.0)) == lbfsi.EINVAL                   # period against the node order
+
+
+def test_cgrid_walls_struct_layout_and_independent_bodies_validation_without_gpu(tmp_path, lib):
+    """lbfsi_mesh_cgrid_walls_desc matches the binding (nbody and wall_body
+    appended); lbfsi_create_mesh_cgrid_walls rejects, before touching the
+    device, a chain body out of range, a body without a chain, mirrored
+    chains on different bodies, another body's wall inside a moving body's
+    blended region and overlapping blended regions of two moving bodies."""
+    from paper_2107_01370_gb300 import inputs, lbfsi
+    src = tmp_path / "cw.c"
+    src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lbfsi_mesh_cgrid_walls_desc),'
+                   'offsetof(lbfsi_mesh_cgrid_walls_desc, bodies), offsetof(lbfsi_mesh_cgrid_walls_desc, nbody),'
+                   'offsetof(lbfsi_mesh_cgrid_walls_desc, wall_body));return 0;}\n')
+    exe = tmp_path / "cw"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    D = lbfsi.MeshCGridWallsDesc
+    assert got == [ctypes.sizeof(D), D.bodies.offset, D.nbody.offset, D.wall_body.offset]
+    X, walls = inputs.tandem_cgrid(34, 17, 11, 16, 17)
+    front = inputs.BodySpec(dof=1, xc=0.0, r_in=0.7, r_out=1.8)
+    rear = inputs.BodySpec(dof=1, xc=4.0, r_in=0.7, r_out=1.8)
+
+    def create(bodies, wall_body):
+        try:
+            lbfsi.Mesh.cgrid_walls(X, walls, bodies, wall_body=wall_body)
+        except lbfsi.LbfsiError as e:
+            return e.code, str(e)
+        raise AssertionError("accepted")
+
+    assert create([[front, rear]], [1, 0, 2])[0] == lbfsi.EINVAL
+    assert create([[front, rear, rear]], [1, 0, 1])[0] == lbfsi.EINVAL     # body 2 owns no chain
+    assert "symmetric" in create([[front, rear]], [1, 0, 0])[1]
+    wide = inputs.BodySpec(dof=1, xc=0.0, r_in=0.7, r_out=3.6)
+    assert "blended region" in create([[wide, inputs.BodySpec(dof=0)]], [1, 0, 1])[1]
+    near = inputs.BodySpec(dof=1, xc=4.0, r_in=0.7, r_out=2.3)
+    assert "overlap" in create([[inputs.BodySpec(dof=1, xc=0.0, r_in=0.7, r_out=1.9), near]], [1, 0, 1])[1]
+    assert create([[rear, front]], [1, 0, 1])[0] == lbfsi.EINVAL               # bodies swapped
+    small_front = inputs.BodySpec(dof=1, xc=0.0, r_in=0.45, r_out=1.8)
+    assert "rigid zone" in create([[small_front, inputs.BodySpec(dof=0)]], [1, 0, 1])[1]

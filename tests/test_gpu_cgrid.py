@@ -242,3 +242,112 @@ def test_fp32_linked_tandem_within_stated_tolerance(L):
     s, r, hist, (f, ghist, st) = run_both(L, case, M0, 30, L.FP32)
     assert field_err(f, r.M) < 1e-5
     assert np.abs(ghist - hist).max() < 1e-4 * P_SCALE
+
+
+# ----- independent bodies (reading R32) -----------------------------------
+FRONT = inputs.BodySpec(dof=1, xc=0.0, yc=0.0, xp=0.0, yp=0.0, r_in=0.7, r_out=1.8, m_star=2.0, v_r=4.0,
+                        length=1.0)
+REAR = inputs.BodySpec(dof=2, xc=4.0, yc=0.0, xp=3.9, yp=0.0, r_in=0.7, r_out=1.8, m_star=5.0, v_r=2.0,
+                       x_alpha=0.3, r_alpha=0.6, wh_wa=0.5, length=1.0)
+WALL_BODY = [1, 0, 1]   # chains: rear lower half, front, rear upper half
+IND_STATE = [{"h": 0.02, "alpha": 0.0, "hdot": 0.004, "adot": 0.0},
+             {"h": -0.01, "alpha": 0.02, "hdot": -0.002, "adot": 0.01}]
+IND_PREV = [{"h": 0.0199, "alpha": 0.0, "hdot": 0.004, "adot": 0.0},
+            {"h": -0.0099, "alpha": 0.0199, "hdot": -0.002, "adot": 0.01}]
+
+
+def _independent(L, precision, steps, seed, moving=True):
+    case = inputs.tandem_case(34, 17, 11, 16, 33)
+    case.bodies = [FRONT, REAR]
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=seed)
+    s = OS.Solver.from_case(OM.CGridMesh(case.X, walls=case.walls, wall_body=WALL_BODY), case, M0)
+    if moving:
+        s.S = [dict(x) for x in IND_STATE]
+        s.S_prev = [dict(x) for x in IND_PREV]
+    hist = []
+    for _ in range(steps):
+        r = s.step()
+        hist.append(r.forces)
+    m = L.Mesh.cgrid_walls(case.X, case.walls, [[FRONT, REAR]], precision=precision, wall_body=WALL_BODY)
+    m.init_fields(case.flow, M0[None])
+    if moving:
+        m.blend_mesh([to_tuple(x) for x in IND_STATE], [to_tuple(x) for x in IND_PREV])
+    ghist = []
+    for _ in range(steps):
+        m.step(1)
+        ghist.append(m.body_forces()[0].copy())
+    out = (m.get_fields()[0], np.array(ghist), m.body_state()[0])
+    m.close()
+    return s, r, np.array(hist), out
+
+
+def test_fp64_independent_tandem_bodies_match_oracle(L):
+    """The two cylinders as independent bodies: the front one in transverse
+    VIV, the rear one in pitch-plunge about its own elastic axis, each with
+    its own blended region, load (its chains only) and RK4 update."""
+    s, r, hist, (f, ghist, st) = _independent(L, L.FP64, 10, 73)
+    assert field_err(f, r.M) < 1e-12
+    assert ghist.shape == (10, 2, 3)
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+    # each body carries a load of its own (not a copy of the other's)
+    assert np.abs(ghist[:, 0] - ghist[:, 1]).max() > 1e-4 * P_SCALE
+    for b in range(2):
+        for k in ("h", "alpha", "hdot", "adot"):
+            assert abs(st[b][k] - s.S[b][k]) < 1e-12 * (1 + abs(s.S[b][k])), (b, k)
+    assert st[0]["alpha"] == 0.0   # the transverse body does not rotate
+
+
+def test_fp64_independent_fixed_bodies_match_oracle(L):
+    s, r, hist, (f, ghist, st) = _independent(L, L.FP64, 6, 74, moving=False)
+    assert field_err(f, r.M) < 1e-12
+    assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
+
+
+def test_fp32_independent_tandem_bodies_within_stated_tolerance(L):
+    s, r, hist, (f, ghist, st) = _independent(L, L.FP32, 30, 75)
+    assert field_err(f, r.M) < 1e-5
+    assert np.abs(ghist - hist).max() < 1e-4 * P_SCALE
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_independent_bodies_graph_replay_resume_and_record(L, precision):
+    """Two solves of the independent pair: graph replay and checkpoint /
+    resume are bit for bit, and lbfsi_step_record's per-(solve, body)
+    records equal body_forces / body_state after each step."""
+    prec = L.FP32 if precision == "fp32" else L.FP64
+    case = inputs.tandem_case(34, 17, 11, 16, 33)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=76)
+    M2 = np.ascontiguousarray(np.broadcast_to(M0, (2,) + M0.shape))
+    rear_b = inputs.BodySpec(**{**REAR.__dict__, "m_star": 3.0})
+
+    def fresh():
+        m = L.Mesh.cgrid_walls(case.X, case.walls, [[FRONT, REAR], [FRONT, rear_b]], precision=prec,
+                               wall_body=WALL_BODY)
+        m.init_fields(case.flow, M2)
+        m.blend_mesh([to_tuple(x) for x in IND_STATE] * 2, [to_tuple(x) for x in IND_PREV] * 2)
+        return m
+
+    a = fresh()
+    a.step(7)
+    ckpt = a.checkpoint()
+    loads, states = a.step_record(9, states=True)
+    assert loads.shape == (9, 2, 2, 3) and states.shape == (9, 2, 2, 4)
+    ref = (a.get_fields(), a.body_forces(), a.body_state())
+    assert np.array_equal(loads[-1], ref[1])
+    assert states[-1, 1, 1, 0] == ref[2][1][1]["h"]
+    # the two solves differ only in the rear body's mass: the rear bodies'
+    # states part, their loads follow
+    assert states[-1, 0, 1, 0] != states[-1, 1, 1, 0]
+    a.close()
+    b = fresh()
+    b.set_graph_steps(4)
+    b.step(16)
+    got = (b.get_fields(), b.body_forces(), b.body_state())
+    b.close()
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]) and ref[2] == got[2]
+    c = fresh()
+    c.restore(ckpt)
+    c.step(9)
+    got = (c.get_fields(), c.body_forces(), c.body_state())
+    c.close()
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]) and ref[2] == got[2]

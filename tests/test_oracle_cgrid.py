@@ -9,7 +9,11 @@ come from the oracle itself:
 - wall force of the open chain: zero for a uniform stress, -A grad p for a
   linear pressure (divergence theorem, A the area of the wall polygon);
 - a mirror-symmetric C-grid with a mirror-symmetric initial field stays
-  mirror-symmetric (f_q(i, j) = f_q'(i, Nj-1-j), q' the reflected velocity)."""
+  mirror-symmetric (f_q(i, j) = f_q'(i, Nj-1-j), q' the reflected velocity);
+- independent bodies (reading R32): fixed bodies' loads transfer to the
+  linked pair's (forces add, moments by M + (r_b - r) x F_b), relabelling
+  the bodies permutes their loads, and on a symmetric flow neither body has
+  lift or moment and a free body stays at rest."""
 import numpy as np
 import pytest
 
@@ -283,3 +287,75 @@ def test_tandem_symmetric_flow_stays_symmetric():
     f = r.f_post
     assert np.abs(f - f[REFLECT][:, :, ::-1]).max() < 1e-12 * np.abs(f).max()
     assert abs(r.force[1]) < 1e-12 and abs(r.force[2]) < 1e-12
+
+
+# ----- independent bodies on one C-grid (reading R32) ----------------------
+def _tandem_flow(X):
+    return inputs.FlowSpec(ma=0.2, re=100.0, dt=float(np.hypot(*(X[0, 45] - X[0, 44]))) / 3.0)
+
+
+def _run(X, walls, bodies, M, steps, wall_body=None):
+    flow = _tandem_flow(X)
+    case = inputs.CGridCase(nr=X.shape[0], ntheta=X.shape[1], n_cut=None, X=X, centre=(0.0, 0.0), flow=flow,
+                            bodies=bodies)
+    s = OS.Solver.from_case(OM.CGridMesh(X, walls=walls, wall_body=wall_body), case, M)
+    out = [s.step() for _ in range(steps)]
+    return s, out
+
+
+def _cross(r, F):
+    return r[0] * F[1] - r[1] * F[0]
+
+
+def test_independent_fixed_bodies_transfer_to_the_linked_load():
+    """Two fixed cylinders as independent bodies see the flow of the linked
+    pair (fixed walls: the same step), so their loads add up to the linked
+    load: the forces sum, and the moments about each body's own reference
+    point, moved to the linked reference point (M + (r_b - r) x F_b), sum to
+    the linked moment.  Relabelling the bodies permutes the loads exactly."""
+    X, walls = _tandem(nr=13)
+    M0 = inputs.initial_field(X.shape[0], X.shape[1], _tandem_flow(X), noise=1e-2, seed=21)
+    r_lin, r_f, r_r = np.array([1.0, 0.2]), np.array([0.0, 0.1]), np.array([4.0, -0.3])
+    _, lin = _run(X, walls, [inputs.BodySpec(dof=0, xp=r_lin[0], yp=r_lin[1])], M0, 3)
+    front = inputs.BodySpec(dof=0, xp=r_f[0], yp=r_f[1])
+    rear = inputs.BodySpec(dof=0, xp=r_r[0], yp=r_r[1])
+    _, ind = _run(X, walls, [front, rear], M0, 3, wall_body=[1, 0, 1])
+    _, swp = _run(X, walls, [rear, front], M0, 3, wall_body=[0, 1, 0])
+    for a, b, c in zip(lin, ind, swp):
+        assert np.array_equal(a.f_post, b.f_post)
+        Ff, Fr = np.array(b.forces[0]), np.array(b.forces[1])
+        F = np.array(a.force)
+        scale = np.abs(F[:2]).max()
+        assert np.abs(Ff[:2] + Fr[:2] - F[:2]).max() < 1e-13 * scale
+        m_t = Ff[2] + _cross(r_f - r_lin, Ff[:2]) + Fr[2] + _cross(r_r - r_lin, Fr[:2])
+        assert abs(m_t - F[2]) < 1e-13 * scale
+        # each body takes a share of its own (the rear body's drag sign is
+        # not the front's: it sits in the front body's wake)
+        assert np.abs(Ff).max() > 1e-3 * scale and np.abs(Fr).max() > 1e-3 * scale
+        assert c.forces[0] == b.forces[1] and c.forces[1] == b.forces[0]
+
+
+def test_independent_bodies_symmetric_flow_no_lift_on_either():
+    """A mirror-symmetric field on the symmetric tandem mesh: each body's
+    lift and its moment about a reference point on the axis vanish, and a
+    free transverse body next to a fixed one is not driven (its state stays
+    at rest); the fixed body's state never changes."""
+    X, walls = _tandem(nr=13)
+    flow = _tandem_flow(X)
+    M0 = inputs.initial_field(X.shape[0], X.shape[1], flow, noise=1e-2, seed=9)
+    M = M0.copy()
+    M[0] = 0.5 * (M0[0] + M0[0, :, ::-1])
+    M[1] = 0.5 * (M0[1] + M0[1, :, ::-1])
+    M[2] = 0.5 * (M0[2] - M0[2, :, ::-1])
+    M[3] = 0.5 * (M0[3] + M0[3, :, ::-1])
+    m = OM.CGridMesh(X, walls=walls)
+    M[2, 0, m.cut_columns() | m.junction] = 0.0
+    free = inputs.BodySpec(dof=1, xc=0.0, yc=0.0, xp=0.0, yp=0.0, r_in=0.7, r_out=1.8, m_star=2.0, v_r=4.0)
+    fixed = inputs.BodySpec(dof=0, xp=4.0, yp=0.0)
+    s, out = _run(X, walls, [free, fixed], M, 3, wall_body=[1, 0, 1])
+    for r in out:
+        for Fb in r.forces:
+            assert abs(Fb[1]) < 1e-12 and abs(Fb[2]) < 1e-12
+        assert abs(r.forces[0][0]) > 1e-6 and abs(r.forces[1][0]) > 1e-6
+    assert abs(s.S[0]["h"]) < 1e-15 and abs(s.S[0]["hdot"]) < 1e-13
+    assert all(v == 0.0 for v in s.S[1].values())
