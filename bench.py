@@ -18,7 +18,6 @@ node updates of all ranks divided by it.
 from __future__ import annotations
 
 import argparse
-import copy
 import hashlib
 import json
 import math
@@ -343,8 +342,8 @@ def general_mesh_cases():
     x_a 1.8, r_a 1.87, V_R 0.5025, elastic axis half a chord ahead of the
     leading edge), Ma 0.8, T_inf 0.2, Re 1e5, 1 degree forced pitching for
     two periods then free (batch 8); two cylinders in tandem on a 512 x 2049
-    C-grid, rigidly linked on one DOF and as two independent 1-DOF bodies
-    (one solve each)."""
+    C-grid, rigidly linked on one DOF (one solve) and as two independent
+    1-DOF bodies swept over six reduced velocities (six solves)."""
     from paper_2107_01370_gb300 import lbfsi
     ell = inputs.xy_case(inputs.ellipse_wall(256, 0.6, 0.35), 512, r_far=20.0, length=1.2,
                          body=inputs.BodySpec(dof=1, r_in=0.75, r_out=2.5, m_star=10.0, v_r=5.0,
@@ -361,24 +360,22 @@ def general_mesh_cases():
     tc = inputs.tandem_case(257, 257, 255, 256, 512, body=linked,
                             name="two cylinders in tandem 4 D apart, rigidly linked (1 DOF, V_R 5), "
                                  "C-grid 512x2049 with three wall chains, Re 100, Ma 0.2")
-    # the same mesh and flow, the cylinders as independent bodies (chains:
-    # rear lower half, front, rear upper half), each in transverse VIV
-    pair = [inputs.BodySpec(dof=1, xc=x, yc=0.0, xp=x, yp=0.0, r_in=0.7, r_out=1.8, m_star=4.0, v_r=5.0,
-                            length=1.0) for x in (0.0, 4.0)]
-    ti = copy.copy(tc)
-    ti.bodies = pair
-    ti.name = ("two cylinders in tandem 4 D apart, independent bodies (1 DOF each, V_R 5), "
-               "C-grid 512x2049 with three wall chains, Re 100, Ma 0.2")
+    # the same mesh and flow, the cylinders as independent 1-DOF bodies, one
+    # solve per reduced velocity of the sweep
+    ti = inputs.tandem_1m_independent()
+    ti.name += ", V_R swept " + "/".join(f"{v:g}" for v in inputs.TANDEM_VR_SWEEP) + " (one solve each)"
+    sweep = inputs.TANDEM_VR_SWEEP
     return ((ell, lambda prec, nb, st: lbfsi.Mesh.xy(ell.X, ell.bodies * nb, precision=prec, stream=st)),
             (cg, lambda prec, nb, st: lbfsi.Mesh.cgrid(cg.X, cg.n_cut, cg.bodies * nb, precision=prec,
                                                        stream=st)),
             (tc, lambda prec, nb, st: lbfsi.Mesh.cgrid_walls(tc.X, tc.walls, tc.bodies * nb, precision=prec,
                                                              stream=st)),
-            (ti, lambda prec, nb, st: lbfsi.Mesh.cgrid_walls(ti.X, ti.walls, [pair] * nb, precision=prec,
-                                                             stream=st, wall_body=[1, 0, 1])))
+            (ti, lambda prec, nb, st: lbfsi.Mesh.cgrid_walls(
+                ti.X, ti.walls, [inputs.tandem_independent_pair(sweep[k % len(sweep)]) for k in range(nb)],
+                precision=prec, stream=st, wall_body=ti.wall_body)))
 
 
-def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=(8, 8, 1, 1), only=None):
+def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=(8, 8, 1, 6), only=None):
     """MLUPS of the general-mesh step (Newton departure points, stored
     metric) on the two workloads of general_mesh_cases, timed with CUDA events
     on the library's stream; the C-grid step is two launches (collision, then

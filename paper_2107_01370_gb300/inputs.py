@@ -419,6 +419,33 @@ def tandem_case(n_front: int, n_rear: int, n_gap: int, n_wake: int, nr: int, *, 
     return c
 
 
+# reduced velocities of the tandem sweep (one solve each)
+TANDEM_VR_SWEEP = (3.0, 4.0, 5.0, 6.0, 7.0, 8.0)
+# chains of tandem_cgrid: rear body's lower half, front body, rear body's upper half
+TANDEM_WALL_BODY = (1, 0, 1)
+
+
+def tandem_independent_pair(v_r: float, m_star: float = 10.0) -> list:
+    """The front (x = 0) and rear (x = 4) cylinders as independent 1-DOF
+    transverse bodies, each with its own blended region (r_in 0.75, r_out
+    1.9 about its centre: the regions of the two stay apart)."""
+    return [BodySpec(dof=1, xc=x, yc=0.0, xp=x, yp=0.0, r_in=0.75, r_out=1.9, m_star=m_star, v_r=v_r,
+                     zeta=0.0, length=1.0) for x in (0.0, 4.0)]
+
+
+def tandem_1m_independent(v_r: float = 5.0, steps: int = 0) -> CGridCase:
+    """Two cylinders 4 D apart as independent 1-DOF bodies on a 512 x 2049
+    C-grid (1,049,088 nodes, three wall chains), Re 100, Ma 0.2, m* 10,
+    zeta 0: the tandem workload at its full size (a sweep over
+    TANDEM_VR_SWEEP runs one solve per reduced velocity)."""
+    c = tandem_case(257, 257, 255, 256, 512, steps=steps,
+                    name="two cylinders in tandem 4 D apart, independent 1-DOF bodies (m* 10), "
+                         "C-grid 512x2049 with three wall chains, Re 100, Ma 0.2")
+    c.bodies = tandem_independent_pair(v_r)
+    c.wall_body = list(TANDEM_WALL_BODY)
+    return c
+
+
 def cgrid_case(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
                wake: float = 6.0, length: float = 1.0, ma: float = 0.2, re: float = 100.0,
                t_inf: float = 1.0 / 3.0, gamma: float = 1.4, pr: float = 0.71,

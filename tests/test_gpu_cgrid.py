@@ -351,3 +351,45 @@ def test_independent_bodies_graph_replay_resume_and_record(L, precision):
     got = (c.get_fields(), c.body_forces(), c.body_state())
     c.close()
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]) and ref[2] == got[2]
+
+
+def test_fp32_tandem_1m_independent_sweep_full_size_bench_launch(L):
+    """The tandem workload at full size (512 x 2049 C-grid, two independent
+    1-DOF bodies) in the bench's launch configuration (one solve per reduced
+    velocity of the sweep, FP32): after one step every solve matches the
+    oracle's stored first step at the sampled nodes (FP32 tolerance), each
+    body's load matches, and each solve's RK4 update matches the oracle's
+    for its reduced velocity (tests/golden/make_tandem_1m_step1.py)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tandem_1m_step1.json")))
+    case = inputs.tandem_1m_independent()
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
+    sweep = inputs.TANDEM_VR_SWEEP
+    nb = len(sweep)
+    m = L.Mesh.cgrid_walls(case.X, case.walls, [inputs.tandem_independent_pair(v) for v in sweep],
+                           precision=L.FP32, wall_body=case.wall_body)
+    m.init_fields(case.flow, np.broadcast_to(M0, (nb,) + M0.shape))
+    st = [to_tuple(x) for x in gold["initial_states"]]
+    pv = [(h - hd * case.flow.dt, a, hd, ad) for h, a, hd, ad in st]
+    m.blend_mesh(st * nb, pv * nb)
+    m.step(1)
+    fields = m.get_fields()
+    loads = m.body_forces()
+    states = m.body_state()
+    m.close()
+    ii, jj = np.array(gold["samples"]).T
+    ref = np.array(gold["M"])
+    s_rho, s_u, s_T = gold["scale"]
+    for k, v in enumerate(sweep):
+        got = fields[k][:, ii, jj].T
+        err = max(np.abs(got[:, 0] - ref[:, 0]).max() / s_rho,
+                  np.hypot(got[:, 1] - ref[:, 1], got[:, 2] - ref[:, 2]).max() / s_u,
+                  np.abs(got[:, 3] - ref[:, 3]).max() / s_T)
+        assert err < 1e-5, (v, err)
+        assert np.abs(loads[k] - np.array(gold["loads"])).max() < 1e-4 * P_SCALE
+        for b in range(2):
+            want = gold["states"][repr(v)][b]
+            assert abs(states[k][b]["h"] - want[0]) < 1e-9 and abs(states[k][b]["hdot"] - want[2]) < 1e-8
+    # the flow of the step does not depend on the reduced velocity
+    assert np.array_equal(fields[0], fields[nb - 1])
