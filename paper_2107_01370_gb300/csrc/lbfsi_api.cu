@@ -179,6 +179,7 @@ cudaError_t launch_one_step(lbfsi_mesh m, lbfsi::StepArgs a, cudaStream_t s) {
     if (!m->host.cgrid) return lbfsi::launch_step_uniform(a, m->precision, m->variant, m->nbatch, s);
     lbfsi::StepArgs c = a;
     c.collide_only = 1;
+    c.cgrid_pre = 1;
     cudaError_t e = lbfsi::launch_step_uniform(c, m->precision, m->variant, m->nbatch, s);
     if (e != cudaSuccess) return e;
     a.stream_post = 1;

@@ -130,6 +130,7 @@ struct lbfsi_batch_s {
     int ntiles = 0;    // separable-mesh tiles of the table (first part)
     int ngtiles = 0;   // general-mesh tiles (second part)
     int nctiles = 0;   // C-grid tiles (third part)
+    int ncpre = 0;     // leading C-grid tiles that hold every tile of rows < CGRID_PRE_ROWS
     bool dirty = true;
     // CUDA graph of graph_steps launches over the current tile table,
     // captured on a private stream, dropped whenever the table changes
@@ -299,6 +300,14 @@ int rebuild_tiles(lbfsi_batch b) {
     b->ntiles = (int)nsep;
     b->ngtiles = (int)ngen;
     b->nctiles = (int)(tiles.size() - nsep - ngen);
+    // tile rows outermost: the tiles of the first rows come first; otherwise
+    // the collide-only launch runs over the whole part (the others return)
+    b->ncpre = b->nctiles;
+    if (b->order == 1) {
+        int k = 0;
+        while (k < b->nctiles && tiles[nsep + ngen + k].i0 < lbfsi::CGRID_PRE_ROWS) ++k;
+        b->ncpre = k;
+    }
     b->dirty = false;
     return LBFSI_OK;
 }
@@ -341,8 +350,10 @@ cudaError_t launch_all(lbfsi_batch b, cudaStream_t s) {
     if (e == cudaSuccess && b->nctiles > 0) {
         lbfsi::StepArgs a = step_args(b, 2);
         a.collide_only = 1;
+        a.cgrid_pre = 1;
+        a.ntiles = b->ncpre;   // the tiles of rows < CGRID_PRE_ROWS lead the C-grid part
         e = lbfsi::launch_step_general_table(a, b->precision, s);
-        a.collide_only = 0;
+        a = step_args(b, 2);
         a.stream_post = 1;
         if (e == cudaSuccess) e = lbfsi::launch_step_general_table(a, b->precision, s);
     }

@@ -71,6 +71,11 @@ enum StepMode : int { MODE_STREAM_ONLY = 0, MODE_COLLIDE_STREAM = 1, MODE_COLLID
 
 // Mirrored rows kept below row 0 of a C-grid (the +-4 staging halo).
 constexpr int CGRID_GHOST_ROWS = 4;
+// Rows whose post-collision state a C-grid step's first launch writes: the
+// tiles of the first row of tiles stream from it (their +-2 window reaches
+// the mirrored rows, i.e. the other side's collided nodes); every other tile
+// collides its own window in the second launch.
+constexpr int CGRID_PRE_ROWS = 16;
 // Classes of a C-grid's row-0 columns: on the cut, on a wall chain, a
 // junction (a chain's end next to the cut, one point with its mirror), a
 // second copy of the mirrored column's node (past the middle of row 0), and
@@ -163,9 +168,14 @@ struct StepArgs {
     int uorder;                    // uniform launch: CTA order, 0 = (tile column, tile row,
                                    // solve), 1 = (solve, tile column, tile row)
     int pf_dist;                   // uniform launch: L2 prefetch distance in CTAs (set by the launcher)
-    int stream_post;               // 1: stream from ppost (written by a collide-only launch of
-                                   // the same step) without colliding; the step with k == 0
-                                   // streams the initial state as always
+    int stream_post;               // C-grid step, second launch: the tiles next to the cut
+                                   // (rows < CGRID_PRE_ROWS - tile - 2) stream from ppost
+                                   // (written by the step's collide-only launch) without
+                                   // colliding, every other tile collides and streams in one
+                                   // pass; the step with k == 0 streams the initial state as
+                                   // always
+    int cgrid_pre;                 // C-grid collide-only launch of a step: only the tiles of
+                                   // rows < CGRID_PRE_ROWS (the others return at once)
     unsigned* status;
 };
 

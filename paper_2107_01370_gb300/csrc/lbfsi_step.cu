@@ -552,9 +552,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // the solve's device counter
     const unsigned kstep = (UNIFORM && a.ustep >= 0) ? (unsigned)a.ustep : __ldcg(ctr + 1);
     const int cur = (int)(kstep & 1u);
-    // general meshes: a stream-only launch after a collide-only one streams
-    // the collided state (the C-grid's two-launch step)
-    const bool split = GEN && a.stream_post;
+    // C-grid step (general meshes), two launches: the first collides the
+    // rows below CGRID_PRE_ROWS into ppost; in the second the first row of
+    // tiles, whose +-2 window reaches across the cut, streams that collided
+    // state, and every other tile collides and streams in one pass
+    if (GEN && a.collide_only && a.cgrid_pre && i0 >= CGRID_PRE_ROWS) return;
+    const bool split = GEN && a.stream_post && i0 + TI + 2 <= CGRID_PRE_ROWS;
     const int mode = a.collide_only ? MODE_COLLIDE_ONLY
                      : (kstep == 0u || split) ? MODE_STREAM_ONLY : MODE_COLLIDE_STREAM;
     const bool from_post = split && kstep != 0u && !a.collide_only;
@@ -1385,7 +1388,8 @@ struct StepKernel {
             // prefetch distance: one resident wave
             StepArgs b = a;
             b.pf_dist = resident;
-            const int nti = (a.umesh.nr + TI - 1) / TI;
+            int nti = (a.umesh.nr + TI - 1) / TI;
+            if (GEN && a.collide_only && a.cgrid_pre) nti = std::min(nti, CGRID_PRE_ROWS / TI);
             const dim3 grid = a.uorder ? dim3(nbatch, a.umesh.ntj, nti) : dim3(a.umesh.ntj, nti, nbatch);
             k_step<R, TI, TJ, NT, MINB, UNIFORM, GEN><<<grid, NT, smem, s>>>(b);
         } else {
