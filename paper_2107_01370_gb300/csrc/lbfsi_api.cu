@@ -48,6 +48,8 @@ struct lbfsi_mesh_s {
     void* d_p[2] = {nullptr, nullptr};   // populations, (f_q, g_q) pairs [nbatch][9][N]
     void* d_M[2] = {nullptr, nullptr};
     void* d_ppost = nullptr;             // collide-only output, same layout
+    void* d_dep = nullptr;               // general meshes: cached static departures ((xi, eta)
+                                         // [9][Nx], then codes [Nx]; see SolveDev::dep_xe)
     double* d_stage = nullptr;  // [nbatch][4][N] float64 staging
     StepMaps* d_maps[2] = {nullptr, nullptr};  // [nbatch][nbody] each
     BodyStateDev* d_state_a = nullptr;          // host-given states staging
@@ -187,7 +189,7 @@ cudaError_t launch_one_step(lbfsi_mesh m, lbfsi::StepArgs a, cudaStream_t s) {
 }
 
 void free_all(lbfsi_mesh m) {
-    void* ptrs[] = {m->d_p[0], m->d_p[1], m->d_M[0], m->d_M[1], m->d_ppost, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
+    void* ptrs[] = {m->d_p[0], m->d_p[1], m->d_M[0], m->d_M[1], m->d_ppost, m->d_dep, m->d_stage, m->d_maps[0], m->d_maps[1], m->d_state_a, m->d_state_b,
                     m->d_loads_tmp, m->d_part, m->d_counter, m->d_bodies, m->d_meshdev, m->d_solves,
                     m->d_status};
     for (void* p : ptrs)
@@ -218,6 +220,9 @@ int upload_solves(lbfsi_mesh m) {
         s.part = m->d_part + bb * m->host.ntj * 3;
         s.counter = m->d_counter + 2 * b;
         s.body = m->d_bodies + bb;
+        s.dep_xe = m->d_dep ? (char*)m->d_dep + g0 * 2 * es : nullptr;
+        s.dep_code = m->d_dep ? reinterpret_cast<unsigned long long*>((char*)m->d_dep + 9 * N * 2 * es) + g0
+                              : nullptr;
     }
     cudaError_t e = cudaMemcpyAsync(m->d_solves, m->solves.data(), m->solves.size() * sizeof(SolveDev),
                                     cudaMemcpyHostToDevice, m->stream);
@@ -434,6 +439,12 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
         if (e == cudaSuccess) e = cudaMalloc(&m->d_M[k], nb * 4 * N * m->esize);
     }
     if (e == cudaSuccess && m->host.cgrid) e = cudaMalloc(&m->d_ppost, nb * 18 * N * m->esize);
+    // general meshes: departures of the static nodes, solved once per time
+    // step size (LBFSI_NO_DEPARTURE_CACHE=1 solves them every step instead;
+    // the results are the same)
+    const char* nc = std::getenv("LBFSI_NO_DEPARTURE_CACHE");
+    if (e == cudaSuccess && m->host.general && !(nc && std::atoi(nc) != 0))
+        e = cudaMalloc(&m->d_dep, 9 * N * 2 * m->esize + N * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         free_all(m);
         delete m;
@@ -512,6 +523,19 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
                               (int)ns, m->d_maps[0], m->stream);
     m->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "prepare kernel");
+    if (m->d_dep) {
+        // the static nodes' departures for this dt (one pass of the step
+        // kernel over solve 0 that writes nothing else)
+        const size_t Nx = (size_t)m->host.Nx;
+        e = cudaMemsetAsync((char*)m->d_dep + 9 * Nx * 2 * m->esize, 0xff, Nx * sizeof(unsigned long long),
+                            m->stream);
+        lbfsi::StepArgs a = make_args(m, 0);
+        a.ustep = 0;
+        a.record = 1;
+        if (e == cudaSuccess) e = lbfsi::launch_step_uniform(a, m->precision, m->variant, 1, m->stream);
+        m->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "departure cache");
+    }
     e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init sync");
     m->initialized = true;

@@ -144,6 +144,15 @@ struct SolveDev {
     double* part;                  // [nbody][ntj][3] load partials of the streamed step
     unsigned* counter;             // [2]: CTA completion count, step number k
     const BodyDev* body;           // [nbody]
+    // general meshes, uniform launches: departure points of the nodes the
+    // blend does not move (g = I, V_G = 0, so the displacement of direction q
+    // is -dt c_q for every step): (xi, eta) pairs [9][N] in the element type
+    // of the path and per node a code [N] (5 bits per direction: the window
+    // origin relative to the node, row and column offsets in -3..0, or a lost
+    // departure; all ones: not cached), shared by the solves of the handle
+    // (one mesh, one dt), or null
+    void* dep_xe = nullptr;
+    unsigned long long* dep_code = nullptr;
 };
 
 // One CTA of a step launch: a tile of one solve.  The entry repeats the
@@ -176,6 +185,8 @@ struct StepArgs {
                                    // always
     int cgrid_pre;                 // C-grid collide-only launch of a step: only the tiles of
                                    // rows < CGRID_PRE_ROWS (the others return at once)
+    int record;                    // general meshes, uniform: fill usol.dep_* (departures of
+                                   // the static nodes of solve 0) and write nothing else
     unsigned* status;
 };
 

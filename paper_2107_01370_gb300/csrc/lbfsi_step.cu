@@ -88,7 +88,8 @@ template <typename R, int TI, int TJ, bool GEN>
 constexpr size_t step_smem_bytes() {
     using T = Tile<TI, TJ>;
     return sizeof(R) * (size_t)(18 * T::PSS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
-                                (GEN ? 6 * T::DS + (TI + 1) * (TJ + 1) * CELLC : T::MH * RS + T::MW * CS));
+                                (GEN ? 6 * T::DS + (TI + 1) * (TJ + 1) * CELLC : T::MH * RS + T::MW * CS)) +
+           (GEN ? (size_t)TI * TJ * (9 * 2 * sizeof(R) + sizeof(unsigned long long)) : 0);
 }
 
 // Bounds-checked build (LBFSI_BOUNDS_CHECK): the shared-memory windows the
@@ -489,6 +490,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     R* sX = sD + 2 * T::DS;                         // general: [DS][2] node coordinates
     R* sJ = sX + 2 * T::DS;                         // general: [DS][4] inverse metric
     R* sC = sJ + 4 * T::DS;                         // general: [TI+1][TJ+1][CELLC] cells
+    R2* sDep = reinterpret_cast<R2*>(sC + (TI + 1) * (TJ + 1) * CELLC);   // general: [9][TI TJ] cached departures
+    unsigned long long* sCode = reinterpret_cast<unsigned long long*>(sDep + 9 * TI * TJ);   // [TI TJ]
 
     // blended maps of the solve's bodies (several only on general meshes)
     constexpr int MB = GEN ? MAX_BODIES : 1;
@@ -699,6 +702,23 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                             cp_async8(dst + q * T::PSS + e, se + (size_t)q * N);
                     }
                 }
+            }
+        }
+    }
+    // general meshes: the tile's cached static departures (uniform launches)
+    const bool dcache = GEN && UNIFORM && !a.record && mode != MODE_COLLIDE_ONLY && a.usol.dep_code != nullptr;
+    if (dcache) {
+        const R2* gxe = reinterpret_cast<const R2*>(a.usol.dep_xe);
+        for (int idx = tid; idx < 10 * TI * TJ; idx += NT) {
+            const int q = idx / (TI * TJ), t = idx - q * (TI * TJ);
+            const int i = i0 + t / TJ, j = j0 + t % TJ;
+            if (i <= 0 || i >= nr || j >= nt) continue;
+            const ptrdiff_t n = (ptrdiff_t)i * nt + j;
+            if (q == 9) {
+                cp_async8(sCode + t, a.usol.dep_code + n);
+            } else {
+                if constexpr (sizeof(R2) == 16) cp_async16(sDep + idx, gxe + (size_t)q * N + n);
+                else cp_async8(sDep + idx, gxe + (size_t)q * N + n);
             }
         }
     }
@@ -942,6 +962,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const R* col = scol + (tj + T::HM) * CS;
         const bool farj = cg && i < nr - 1 && (j == 0 || j == nt - 1);
         if ((!pb && i == nr - 1) || farj) {
+            if (GEN && a.record) continue;
             // far field (Sec. III A 2): inlet where the free stream enters,
             // zero-gradient outlet elsewhere (targets of the previous step);
             // on a C-grid also the outlet columns, inner neighbour along j
@@ -1038,7 +1059,56 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 return depart(geo, inode, dx, dy, base, xi, eta) &&
                        in_bounds(base >= 0 && base + 2 * T::PWS + 2 < T::PSS, a.status);
         };
-        if (!GEN && !moved && i > 0) {
+        // general meshes: a node the blend does not move takes its cached
+        // departures (the same solves, made once for the handle's dt)
+        unsigned long long dcode = ~0ull;
+        if constexpr (GEN) {
+            if (a.record) {
+                if (!moved && i > 0) {
+                    R2* gxe = reinterpret_cast<R2*>(a.usol.dep_xe);
+                    unsigned long long code = 0ull;
+                    bool ok = true;
+#pragma unroll 1
+                    for (int q = 0; q < 9; ++q) {
+                        const R cx = (R)cxq(q), cy = (R)cyq(q);
+                        const R hx = i00 * cx + i01 * cy - vx, hy = i10 * cx + i11 * cy - vy;
+                        int base;
+                        R2 xe;
+                        unsigned nib = 16u;   // a lost departure
+                        if (departure(i, -dt * hx, -dt * hy, base, xe.x, xe.y)) {
+                            const int dr = base / T::PWS - (i - pi0), dc = base % T::PWS - (j - sj0);
+                            if (dr < -3 || dr > 0 || dc < -3 || dc > 0) ok = false;
+                            nib = (unsigned)(((dr + 3) << 2) | (dc + 3));
+                        }
+                        code |= (unsigned long long)nib << (5 * q);
+                        gxe[(size_t)q * N + n] = xe;
+                    }
+                    a.usol.dep_code[n] = ok ? code : ~0ull;
+                }
+                continue;
+            }
+            if (dcache && !moved && i > 0) dcode = sCode[(ti)*TJ + tj];
+        }
+        if (GEN && dcode != ~0ull) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const unsigned nib = (unsigned)(dcode >> (5 * q)) & 31u;
+                R2 v;
+                if (nib & 16u) {
+                    lost = true;
+                    v = sp[q * T::PSS + own];
+                } else {
+                    const int base = own + ((int)(nib >> 2) - 3) * T::PWS + ((int)(nib & 3u) - 3);
+                    const R2 xe = sDep[q * (TI * TJ) + ti * TJ + tj];
+                    R Lx[3], Ly[3];
+                    lagrange3(xe.x, Lx);
+                    lagrange3(xe.y, Ly);
+                    v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
+                }
+                f[q] = v.x;
+                g[q] = v.y;
+            }
+        } else if (!GEN && !moved && i > 0) {
             // a node the blend does not move: c_hat = c, and the rest
             // population's departure point is the node itself
             {
@@ -1232,6 +1302,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
         }
     }
+    if (GEN && a.record) return;
     if (i0 == 0) {
         if (tid < TJ) {
             s_red[0][tid] = fcx;
