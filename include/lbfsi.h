@@ -243,7 +243,12 @@ int lbfsi_destroy_mesh(lbfsi_mesh m);
  * f^eq, g^eq (Eqs. feq, geq) of the given macroscopic fields; the moment field of
  * "the previous step" used by the boundary targets is that same field.  Body
  * states reset to rest.  rho_u_T: host [nbatch][4][N], or NULL for the uniform
- * free stream. */
+ * free stream.  On a mesh given by node coordinates (xy, C-grid, box) this
+ * also solves, once for the flow's dt, the departure points of the nodes that
+ * no blended region moves (a device buffer of 80 B per node in FP32, 152 B in
+ * FP64, allocated at creation unless the environment sets
+ * LBFSI_NO_DEPARTURE_CACHE=1; the steps then read them back instead of
+ * solving them, with the same results). */
 int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rho_u_T);
 
 /* Set the body states used by the next step's blended map (Sec. II D):
@@ -259,7 +264,8 @@ int lbfsi_blend_mesh(lbfsi_mesh m, const lbfsi_body_state* state, const lbfsi_bo
 int lbfsi_step(lbfsi_mesh m, int nsteps);
 
 /* Loads of the last completed step, host out [nbatch][3] = F_x, F_y, M_z
- * (force on the body, moment about its reference point).  Synchronises. */
+ * (force on the body, moment about its reference point; [nbatch][nbody][3]
+ * for independent bodies).  Synchronises. */
 int lbfsi_body_forces(lbfsi_mesh m, double* out);
 
 /* RK4 of the body ODEs only (Sec. III B), with the given host loads
@@ -268,7 +274,8 @@ int lbfsi_body_forces(lbfsi_mesh m, double* out);
  * pitch is evaluated at the handle's step number x dt. */
 int lbfsi_advance_bodies(lbfsi_mesh m, const double* loads, double dt);
 
-/* Body states after the structural update of the last step, host out [nbatch]. */
+/* Body states after the structural update of the last step, host out [nbatch]
+ * ([nbatch][nbody] for independent bodies). */
 int lbfsi_get_body_state(lbfsi_mesh m, lbfsi_body_state* out);
 
 /* Macroscopic fields rho, u_x, u_y, T of the last step's post-propagation
