@@ -376,10 +376,12 @@ def general_mesh_cases():
 
 
 def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=(8, 8, 1, 6), only=None):
-    """MLUPS of the general-mesh step (Newton departure points, stored
-    metric) on the two workloads of general_mesh_cases, timed with CUDA events
-    on the library's stream; the C-grid step is two launches (collision, then
-    stream).  HBM fraction against the algorithmic 144 B per node update."""
+    """MLUPS of the general-mesh step (Newton departure points, cached for
+    the nodes no blend moves; stored metric) on the workloads of
+    general_mesh_cases, timed with CUDA events on the library's stream; the
+    C-grid step is two launches (the collision of the rows next to the cut,
+    then the step).  HBM fraction against the algorithmic 144 B per node
+    update."""
     import torch
     from paper_2107_01370_gb300 import lbfsi
     out = []

@@ -230,8 +230,10 @@ typedef struct {
 int lbfsi_create_mesh_cgrid_walls(const lbfsi_mesh_cgrid_walls_desc* d, void* cuda_stream, lbfsi_mesh* out);
 
 /* Create a mesh handle on a C-grid; otherwise as lbfsi_create_mesh_xy (one
- * tile shape).  A step is two launches here: the collision of step k into a
- * post-collision buffer, then the stream of step k + 1 from it.
+ * tile shape).  A step is two launches here: the collision of step k of the
+ * 16 rows next to the cut into a post-collision buffer, then one launch in
+ * which the tiles next to the cut stream step k + 1 from it and the others
+ * collide and stream.
  * LBFSI_EINVAL for an even ntheta, a bad n_cut, cut nodes that do not
  * coincide, or a mesh that is not subparametric or not positively oriented. */
 int lbfsi_create_mesh_cgrid(const lbfsi_mesh_cgrid_desc* d, void* cuda_stream, lbfsi_mesh* out);
@@ -447,8 +449,9 @@ typedef struct {
 } lbfsi_solve_cgrid_desc;
 
 /* Admit a solve on a C-grid (same contract as lbfsi_batch_add).  Its tiles
- * form a third part of every lbfsi_batch_step: a collide-only launch, then
- * the stream launch from its output. */
+ * form a third part of every lbfsi_batch_step: the collision of the rows next
+ * to the cut, then the launch that streams the tiles next to the cut from its
+ * output and collides and streams the others. */
 int lbfsi_batch_add_cgrid(lbfsi_batch b, const lbfsi_solve_cgrid_desc* d, int* slot);
 
 /* Advance every active solve by up to nsteps coupled steps (one launch per

@@ -172,9 +172,10 @@ void unify_cut_copies(const lbfsi::HostMesh& h, double* user, size_t blocks, int
 }
 
 // One coupled step of every solve: one launch (collide of step k, stream of
-// k + 1), or on a C-grid a collide-only launch into ppost and a stream-only
-// launch from it, because the mirrored rows of one side need the other
-// side's post-collision populations.
+// k + 1), or on a C-grid two: the collision of the rows next to the cut into
+// ppost, because the mirrored rows of one side need the other side's
+// post-collision populations, then the launch in which the first row of tiles
+// streams from ppost and every other tile collides and streams.
 int launches_per_step(lbfsi_mesh m) { return m->host.cgrid ? 2 : 1; }
 
 cudaError_t launch_one_step(lbfsi_mesh m, lbfsi::StepArgs a, cudaStream_t s) {

@@ -340,8 +340,9 @@ lbfsi::StepArgs step_args(lbfsi_batch b, int part) {
 }
 
 // One step of every active solve: the separable-mesh table launch, the
-// general-mesh one and, for C-grids, a collide-only launch followed by a
-// stream launch from its output (independent solves, so the order of the
+// general-mesh one and, for C-grids, the collision of the rows next to the
+// cut followed by the launch that streams the first row of tiles from it and
+// collides and streams the others (independent solves, so the order of the
 // parts is free).
 cudaError_t launch_all(lbfsi_batch b, cudaStream_t s) {
     cudaError_t e = cudaSuccess;

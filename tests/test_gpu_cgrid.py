@@ -2,9 +2,10 @@
 outlet columns, an open wall chain; readings R28-R30) with the FP64 oracle on
 the same meshes and seeded inputs: an elliptic section fixed, in 1-DOF
 plunge, in 2-DOF pitch-plunge with rotation, and across the switch from forced
-to free pitching.  A C-grid step is two launches (collision into a
-post-collision buffer, then the stream from it); graph replay and
-checkpoint / resume keep it bit for bit.  Tolerances as in test_gpu_parity."""
+to free pitching.  A C-grid step is two launches (the collision of the rows
+next to the cut into a post-collision buffer, then the stream of the tiles
+next to the cut from it and a fused collide-and-stream of the others); graph
+replay and checkpoint / resume keep it bit for bit.  Tolerances as in test_gpu_parity."""
 import numpy as np
 import pytest
 
