@@ -307,7 +307,7 @@ def roofline_sweep(stream, schedule, peak, steps=50):
 
 
 def small_case_graphs(stream, steps=1000, graph_steps=100):
-    """BASELINE config 1 (fixed cylinder 128 x 64, FP64, 1000 steps): a
+    """The fixed cylinder on the 128 x 64 O-grid (FP64, 1000 steps): a
     launch-bound case, timed with plain launches and with CUDA-graph replay."""
     import torch
     from paper_2107_01370_gb300 import lbfsi

@@ -165,7 +165,7 @@ typedef struct {
     const lbfsi_body_desc* bodies;  /* [nbatch]: the body of each solve (host)      */
 } lbfsi_mesh_cgrid_desc;
 
-/* A doubly periodic box (SURVEY's Cartesian periodic kind; the mesh of the
+/* A doubly periodic box (the Cartesian periodic mesh kind; the mesh of the
  * Taylor-Green and acoustic checks of Sec. II C): node coordinates of one
  * period, X [ni][nj][2] (subparametric, positively oriented), and the
  * period vectors: node (i + ni, j) is node (i, j) + shift_i, node (i, j + nj)
