@@ -74,6 +74,16 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert b"ntheta" in lib.lbfsi_last_error()
     d = lbfsi.MeshDesc(8, 8, r, e, 0.0, 0.0, 5, 1, ctypes.pointer(body))   # bad precision
     assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
+    # the largest handle: 9 N nbatch population slots must stay within 2^31
+    # (checked before the tables are read or the device is touched)
+    big = (ctypes.c_double * (1 << 16))()
+    d = lbfsi.MeshDesc(1 << 14, 1 << 14, big, big, 0.0, 0.0, 0, 1, ctypes.pointer(body))
+    assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
+    assert b"too large" in lib.lbfsi_last_error()
+    bodies = (lbfsi.BodyDesc * 2000)()
+    d = lbfsi.MeshDesc(512, 256, big, big, 0.0, 0.0, 0, 2000, bodies)     # 2000 solves of 131072 nodes
+    assert lib.lbfsi_create_mesh(ctypes.byref(d), None, ctypes.byref(h)) == lbfsi.EINVAL
+    assert b"too large" in lib.lbfsi_last_error()
     assert lib.lbfsi_step(None, 1) == lbfsi.EINVAL
     assert lib.lbfsi_launch_count(None) == -1
     ptr = ctypes.c_void_p()
