@@ -349,12 +349,7 @@ def general_mesh_cases():
                          body=inputs.BodySpec(dof=1, r_in=0.75, r_out=2.5, m_star=10.0, v_r=5.0,
                                               length=1.2),
                          name="elliptic cylinder (0.6 x 0.35) O-grid 512x256 by node coordinates, 1-DOF")
-    body = inputs.BodySpec(dof=2, xp=-1.0, yp=0.0, r_in=0.6, r_out=2.0, m_star=100.0, v_r=0.5025,
-                           x_alpha=1.8, r_alpha=1.87, wh_wa=0.3, length=1.0,
-                           pitch_amp=math.pi / 180.0, forced_periods=2.0)
-    cg = inputs.cgrid_case(513, 128, 192, 0.5, 0.06, r_far=10.0, wake=10.0, length=1.0, ma=0.8,
-                           t_inf=0.2, re=1e5, body=body, naca=0.12,
-                           name="NACA 0012 C-grid 192x769 (cut 128), 2-DOF, Ma 0.8, forced pitch")
+    cg = inputs.naca0012_flutter_case()
     linked = inputs.BodySpec(dof=1, xc=2.0, yc=0.0, xp=2.0, yp=0.0, r_in=2.7, r_out=4.5, m_star=4.0,
                              v_r=5.0, length=1.0)
     tc = inputs.tandem_case(257, 257, 255, 256, 512, body=linked,

@@ -19,6 +19,13 @@ from __future__ import annotations
 import numpy as np
 
 XI_TOL = 1e-12       # reading R8: a cell contains a point if its local coords are within 1e-12
+# reading R8, second pass: when no adjacent cell holds the point within XI_TOL,
+# the first (in the fixed order) within XI_TOL_THIN.  The bilinear inverse in
+# absolute coordinates rounds at |X| eps / h in reference units, which passes
+# 1e-12 on cells thousands of times longer than wide far from the origin (the
+# wake of a C-grid behind a sharp trailing edge); such points lie on the edge
+# two elements share, where their Q2 interpolants agree.
+XI_TOL_THIN = 1e-9
 NEWTON_TOL = 1e-13
 NEWTON_MAX = 50
 
@@ -114,7 +121,7 @@ class Q2Mesh:
                 break
         return xi, eta
 
-    def locate_in_cell(self, a, b, P):
+    def locate_in_cell(self, a, b, P, tol=XI_TOL):
         """Reference coordinates of P in the window of cell (a, b) and whether
         P lies in that cell (with the R8 tolerance)."""
         wa, wb = self.window_of_cell(a, b)
@@ -125,8 +132,8 @@ class Q2Mesh:
         xi, eta = self.bilinear_inverse(c00, c10, c01, c11, P)
         la = a - wa
         lb = b - wb
-        inside = ((xi >= la - 1 - XI_TOL) & (xi <= la + XI_TOL)
-                  & (eta >= lb - 1 - XI_TOL) & (eta <= lb + XI_TOL))
+        inside = ((xi >= la - 1 - tol) & (xi <= la + tol)
+                  & (eta >= lb - 1 - tol) & (eta <= lb + tol))
         inside &= np.isfinite(xi) & np.isfinite(eta)
         return wa, wb, xi, eta, inside
 
@@ -146,22 +153,25 @@ class Q2Mesh:
         xi_o = np.zeros(shape)
         eta_o = np.zeros(shape)
         found = np.zeros(shape, dtype=bool)
-        for da, db in candidates:
-            a = i + da
-            b = j + db
-            ok = self.valid_cell(a, b)
-            if not np.any(ok & ~found):
-                continue
-            a_s = np.where(ok, a, 0)
-            b_s = np.where(ok, b, 0)
-            with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-                wa, wb, xi, eta, inside = self.locate_in_cell(a_s, b_s, P)
-            take = ok & inside & ~found
-            wa_o = np.where(take, wa, wa_o)
-            wb_o = np.where(take, wb, wb_o)
-            xi_o = np.where(take, xi, xi_o)
-            eta_o = np.where(take, eta, eta_o)
-            found |= take
+        for tol in (XI_TOL, XI_TOL_THIN):
+            for da, db in candidates:
+                a = i + da
+                b = j + db
+                ok = self.valid_cell(a, b)
+                if not np.any(ok & ~found):
+                    continue
+                a_s = np.where(ok, a, 0)
+                b_s = np.where(ok, b, 0)
+                with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+                    wa, wb, xi, eta, inside = self.locate_in_cell(a_s, b_s, P, tol)
+                take = ok & inside & ~found
+                wa_o = np.where(take, wa, wa_o)
+                wb_o = np.where(take, wb, wb_o)
+                xi_o = np.where(take, xi, xi_o)
+                eta_o = np.where(take, eta, eta_o)
+                found |= take
+            if found.all():
+                break
         return wa_o, wb_o, xi_o, eta_o, found
 
     # ----- Eq. SemiLagrProp: Q2 Lagrange interpolation -------------------
@@ -341,7 +351,7 @@ class CGridMesh(Q2Mesh):
     def valid_cell(self, a, b):
         return (a >= -1) & (a <= self.Ni - 2) & (b >= 0) & (b <= self.Nj - 2)
 
-    def locate_in_cell(self, a, b, P):
+    def locate_in_cell(self, a, b, P, tol=XI_TOL):
         wa, wb = self.window_of_cell(a, b)
         corner = {}
         for ca, cb in ((0, 0), (2, 0), (0, 2), (2, 2)):
@@ -350,8 +360,8 @@ class CGridMesh(Q2Mesh):
         xi, eta = self.bilinear_inverse(corner[0, 0], corner[2, 0], corner[0, 2], corner[2, 2], P)
         la = a - wa
         lb = b - wb
-        inside = ((xi >= la - 1 - XI_TOL) & (xi <= la + XI_TOL)
-                  & (eta >= lb - 1 - XI_TOL) & (eta <= lb + XI_TOL))
+        inside = ((xi >= la - 1 - tol) & (xi <= la + tol)
+                  & (eta >= lb - 1 - tol) & (eta <= lb + tol))
         inside &= np.isfinite(xi) & np.isfinite(eta)
         return wa, wb, xi, eta, inside
 

@@ -446,6 +446,20 @@ def tandem_1m_independent(v_r: float = 5.0, steps: int = 0) -> CGridCase:
     return c
 
 
+def naca0012_flutter_case(steps: int = 0) -> CGridCase:
+    """The transonic flutter workload: a NACA 0012 section (chord 1) on a
+    192 x 769 C-grid (147,648 nodes, wake cut 128 nodes per side), 2-DOF
+    pitch-plunge (m* 100, w_h/w_a 0.3, x_a 1.8, r_a 1.87, V_R 0.5025, elastic
+    axis half a chord ahead of the leading edge), Ma 0.8, T_inf 0.2, Re 1e5,
+    1 degree forced pitching for two periods then free."""
+    body = BodySpec(dof=2, xp=-1.0, yp=0.0, r_in=0.6, r_out=2.0, m_star=100.0, v_r=0.5025,
+                    x_alpha=1.8, r_alpha=1.87, wh_wa=0.3, length=1.0,
+                    pitch_amp=math.pi / 180.0, forced_periods=2.0)
+    return cgrid_case(513, 128, 192, 0.5, 0.06, r_far=10.0, wake=10.0, length=1.0, ma=0.8,
+                      t_inf=0.2, re=1e5, body=body, naca=0.12, steps=steps,
+                      name="NACA 0012 C-grid 192x769 (cut 128), 2-DOF, Ma 0.8, forced pitch")
+
+
 def cgrid_case(n_wall: int, n_cut: int, nr: int, a: float, b: float, *, r_far: float = 8.0,
                wake: float = 6.0, length: float = 1.0, ma: float = 0.2, re: float = 100.0,
                t_inf: float = 1.0 / 3.0, gamma: float = 1.4, pr: float = 0.71,

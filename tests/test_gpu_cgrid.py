@@ -394,3 +394,36 @@ def test_fp32_tandem_1m_independent_sweep_full_size_bench_launch(L):
             assert abs(states[k][b]["h"] - want[0]) < 1e-9 and abs(states[k][b]["hdot"] - want[2]) < 1e-8
     # the flow of the step does not depend on the reduced velocity
     assert np.array_equal(fields[0], fields[nb - 1])
+
+
+def test_fp32_naca0012_full_size_bench_launch(L):
+    """The transonic flutter workload at full size (NACA 0012 on the
+    192 x 769 C-grid, 2-DOF with forced pitching, Ma 0.8) in the bench's
+    launch configuration (a batch of eight identical solves, FP32): after
+    three steps the sampled nodes match the oracle's stored run
+    (tests/golden/make_naca0012_steps.py) within the FP32 tolerance, every
+    step's load within 1e-4 p_inf c and the body state to round-off."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "naca0012_steps.json")))
+    case = inputs.naca0012_flutter_case()
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0)
+    nb = 8
+    m = L.Mesh.cgrid(case.X, case.n_cut, case.bodies * nb, precision=L.FP32)
+    m.init_fields(case.flow, np.broadcast_to(M0, (nb,) + M0.shape))
+    loads, states = m.step_record(gold["steps"], states=True)
+    fields = m.get_fields()
+    m.close()
+    ii, jj = np.array(gold["samples"]).T
+    ref = np.array(gold["M"])
+    s_rho, s_u, s_T = gold["scale"]
+    p_scale = case.flow.rho_inf * case.flow.t_inf * 1.0   # p_inf times the chord
+    for k in (0, nb - 1):
+        got = fields[k][:, ii, jj].T
+        err = max(np.abs(got[:, 0] - ref[:, 0]).max() / s_rho,
+                  np.hypot(got[:, 1] - ref[:, 1], got[:, 2] - ref[:, 2]).max() / s_u,
+                  np.abs(got[:, 3] - ref[:, 3]).max() / s_T)
+        assert err < 1e-5, err
+        assert np.abs(loads[:, k] - np.array(gold["loads"])).max() < 1e-4 * p_scale
+        assert np.abs(states[-1, k] - np.array(gold["state"])).max() < 1e-9
+    assert np.array_equal(fields[0], fields[nb - 1])

@@ -359,3 +359,34 @@ def test_independent_bodies_symmetric_flow_no_lift_on_either():
         assert abs(r.forces[0][0]) > 1e-6 and abs(r.forces[1][0]) > 1e-6
     assert abs(s.S[0]["h"]) < 1e-15 and abs(s.S[0]["hdot"]) < 1e-13
     assert all(v == 0.0 for v in s.S[1].values())
+
+
+def test_departure_on_a_thin_wake_cell_edge():
+    """Reading R8's second pass: in the wake of the NACA 0012 C-grid the
+    cells behind the clustered trailing-edge columns are ~5000 times longer
+    than wide and far from the origin, so a departure point on the edge two
+    of them share comes out of the bilinear inverse ~1e-12 outside both.  It
+    is taken (a linear field interpolates exactly), while a point a
+    millionth of the cell width beyond the adjacent cells is still refused."""
+    case = inputs.naca0012_flutter_case()
+    m = OM.CGridMesh(case.X, case.n_cut)
+    X = case.X
+    i, j = 182, 642
+    d = case.flow.dt * np.array([1.0, -1.0])
+    P = X[i, j] - d
+    strict = [m.locate_in_cell(np.array([a]), np.array([b]), P[None])[4][0]
+              for a in (i - 1, i) for b in (j - 1, j)]
+    assert not any(strict)                        # outside every cell at 1e-12
+    wa, wb, xi, eta, found = m.locate(P[None], np.array([i]), np.array([j]))
+    assert found[0]
+    lin = 0.4 + 1.3 * X[..., 0] - 0.7 * X[..., 1]
+    v = m.interpolate(lin, wa, wb, xi, eta)[0]
+    assert abs(v - (0.4 + 1.3 * P[0] - 0.7 * P[1])) < 1e-9
+    # the middle of the far edge of the adjacent cells is taken; a millionth
+    # of the cell width beyond it is not
+    w = np.hypot(*(X[i, j + 1] - X[i, j]))
+    e = (X[i, j + 1] - X[i, j]) / w
+    M_edge = 0.5 * (X[i, j + 1] + X[i + 1, j + 1])
+    assert m.locate(M_edge[None], np.array([i]), np.array([j]))[4][0]
+    Q = M_edge + 1e-6 * w * e
+    assert not m.locate(Q[None], np.array([i]), np.array([j]))[4][0]
