@@ -317,6 +317,9 @@ def small_case_graphs(stream, steps=1000, graph_steps=100):
     for label, g in (("plain", 0), ("graph", graph_steps)):
         m = lbfsi.Mesh(case.r, case.e, case.bodies, precision=lbfsi.FP64, stream=stream.cuda_stream)
         m.init_fields(case.flow, M0[None])
+        # the tile shape (8, 4 or 2 rows: few tiles leave SMs idle) by the tuner
+        v, o, _ = m.autotune(20)
+        res["schedule"] = {"variant": v, "order": o}
         m.set_graph_steps(g)
         m.step(2 * max(g, 1))   # warm-up (captures the graph)
         torch.cuda.synchronize()

@@ -505,11 +505,14 @@ int64_t lbfsi_launch_count(lbfsi_mesh m);
  * summation order), so tuning never changes a solve's result. */
 
 /* Number of tile shapes ("step variants") of the step kernel for a
- * precision (LBFSI_FP32: 5, LBFSI_FP64: 1), or LBFSI_EINVAL.  Float shapes,
+ * precision (LBFSI_FP32: 5, LBFSI_FP64: 3), or LBFSI_EINVAL.  Float shapes,
  * radial x angular nodes per CTA: 0: 8 x 32, 256 threads, 2 CTAs/SM;
  * 1: 16 x 32, 256 threads; 2: 8 x 32, 3 CTAs/SM; 3: 12 x 32, 384 threads;
  * 4: 16 x 32, 512 threads (default of new mesh handles, with order 1, and of
- * new batches, with order 0). */
+ * new batches, with order 0).  Float64 shapes (separable O-grids; 256
+ * threads, one CTA per SM): 0: 8 x 32 (default), 1: 4 x 32, 2: 2 x 32 -- the
+ * smaller tiles spread a small mesh over more SMs, whose float64 rate bounds
+ * the step.  Meshes given by node coordinates have one shape (0). */
 int lbfsi_step_variants(int precision);
 
 /* Tile shape (0 .. lbfsi_step_variants - 1) and CTA order of a mesh handle's

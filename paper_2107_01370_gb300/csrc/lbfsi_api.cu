@@ -406,7 +406,7 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
         const int k = std::atoi(v);
         m->variant = (k >= 0 && k < lbfsi::step_variants(LBFSI_FP32)) ? k : 4;
     }
-    if (m->precision == LBFSI_FP64 || m->host.general) m->variant = 0;   // one tile shape
+    if (m->precision == LBFSI_FP64 || m->host.general) m->variant = 0;   // 8-row tiles (general: the one shape)
     m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
     const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows;
     m->tiles_per_solve = nti * m->host.ntj;

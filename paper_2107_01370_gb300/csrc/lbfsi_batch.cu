@@ -403,7 +403,7 @@ int lbfsi_batch_create(size_t pool_bytes, int precision, void* cuda_stream, lbfs
     b->precision = precision;
     b->esize = precision == LBFSI_FP64 ? sizeof(double) : sizeof(float);
     b->stream = static_cast<cudaStream_t>(cuda_stream);
-    if (precision == LBFSI_FP64) b->variant = 0;   // one tile shape
+    if (precision == LBFSI_FP64) b->variant = 0;   // 8-row tiles
     b->tile_rows = lbfsi::tile_rows(precision, b->variant);
     int rc = b->pool.init(pool_bytes);
     if (rc) {

@@ -195,7 +195,8 @@ struct StepArgs {
 int set_error(int code, const std::string& msg);
 
 // Launchers (defined in lbfsi_step.cu).  variant selects the tile shape of
-// the float step kernel (see tile_rows); the float64 kernel has 8-row tiles.
+// the step kernel (see tile_rows): five float shapes, float64 tiles of 8, 4
+// or 2 rows.
 cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStream_t s);
 // Uniform launch over nbatch solves of one mesh (see StepArgs).
 cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,

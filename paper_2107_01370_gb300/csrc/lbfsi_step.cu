@@ -477,8 +477,11 @@ template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM, bool GEN>
 __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     using T = Tile<TI, TJ>;
     using R2 = typename Vec2<R>::T;
-    constexpr int NPT = TI * TJ / NT;   // tile nodes streamed per thread
-    static_assert(NPT * NT == TI * TJ && NT >= TJ && NT >= 192, "tile / thread count");
+    // tile nodes streamed per thread (the float64 tiles of 2 and 4 rows have
+    // more threads than nodes: the rest only stage and collide)
+    constexpr int NPT = (TI * TJ + NT - 1) / NT;
+    constexpr bool RAGGED = NPT * NT != TI * TJ;
+    static_assert(NT >= TJ && NT >= 192 && (!RAGGED || NPT == 1), "tile / thread count");
     extern __shared__ __align__(16) unsigned char smraw[];
     R2* sp = reinterpret_cast<R2*>(smraw);          // [9][PH][PWS] (f_q, g_q) pairs
     R* sM = reinterpret_cast<R*>(sp + 9 * T::PSS);  // [4][MS]  rho, ux, uy, T of step k
@@ -910,7 +913,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int t = tid + k * NT;
                 const int ti = t / TJ, tj = t - (t / TJ) * TJ;
                 const int i = i0 + ti, j = j0 + tj;
-                if (i < nr && j < nt) {
+                if ((!RAGGED || ti < TI) && i < nr && j < nt) {
                     const int n = i * nt + j;
                     const int sn = (ti + T::HP) * T::PWS + tj + T::HP + 2;
                     // C-grid: the first copy of a cut node also writes the
@@ -945,7 +948,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const int t = tid + k * NT;
         const int ti = t / TJ, tj = t - (t / TJ) * TJ;
         const int i = i0 + ti, j = j0 + tj;
-        if (i >= nr || j >= nt) continue;
+        if ((RAGGED && ti >= TI) || i >= nr || j >= nt) continue;
         // C-grid: the second copies of the row-0 cut nodes (and of the rear
         // point) are written by their first copies; rows 1-4 also write
         // their moments into their mirrored slots below row 0
@@ -1484,7 +1487,13 @@ static cudaError_t launch_general(const StepArgs& a, int precision, int nbatch, 
 
 template <bool UNIFORM>
 static cudaError_t configure_any(int precision, int variant) {
-    if (precision == 0) return StepKernel<double, 8, 256, 1, UNIFORM>::configure();
+    if (precision == 0) {
+        switch (variant) {
+            case 1: return StepKernel<double, 4, 256, 1, UNIFORM>::configure();
+            case 2: return StepKernel<double, 2, 256, 1, UNIFORM>::configure();
+            default: return StepKernel<double, 8, 256, 1, UNIFORM>::configure();
+        }
+    }
     switch (variant) {
         case 1: return StepKernel<float, 16, 256, 2, UNIFORM>::configure();
         case 2: return StepKernel<float, 8, 256, 3, UNIFORM>::configure();
@@ -1509,11 +1518,19 @@ cudaError_t prepare_step(int precision, int variant, bool uniform, bool general)
     return uniform ? configure_any<true>(precision, variant) : configure_any<false>(precision, variant);
 }
 
-int step_variants(int precision) { return precision == 0 ? 1 : 5; }
+int step_variants(int precision) { return precision == 0 ? 3 : 5; }
 
 template <bool UNIFORM>
 static cudaError_t launch_any(const StepArgs& a, int precision, int variant, int nbatch, cudaStream_t s) {
-    if (precision == 0) return launch_step_t<double, 8, 256, 1, UNIFORM>(a, nbatch, s);
+    if (precision == 0) {
+        // float64: 8-row tiles, or 4 and 2 rows to spread a small mesh over
+        // more SMs (the float64 rate per SM bounds it)
+        switch (variant) {
+            case 1: return launch_step_t<double, 4, 256, 1, UNIFORM>(a, nbatch, s);
+            case 2: return launch_step_t<double, 2, 256, 1, UNIFORM>(a, nbatch, s);
+            default: return launch_step_t<double, 8, 256, 1, UNIFORM>(a, nbatch, s);
+        }
+    }
     switch (variant) {
         case 1: return launch_step_t<float, 16, 256, 2, UNIFORM>(a, nbatch, s);
         case 2: return launch_step_t<float, 8, 256, 3, UNIFORM>(a, nbatch, s);
@@ -1534,7 +1551,7 @@ cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, i
 }
 
 int tile_rows(int precision, int variant) {
-    if (precision == 0) return 8;
+    if (precision == 0) return variant == 1 ? 4 : variant == 2 ? 2 : 8;
     switch (variant) {
         case 1: return 16;
         case 3: return 12;

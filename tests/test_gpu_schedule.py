@@ -46,12 +46,15 @@ def _same(a, b):
     assert sa == sb
 
 
-def test_every_tile_shape_and_order_is_bit_identical(L):
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_every_tile_shape_and_order_is_bit_identical(L, precision):
+    prec = L.FP32 if precision == "fp32" else L.FP64
     case, M0 = _case()
-    ref = _run_mesh(L, case, M0, 25, L.FP32, schedule=(3, 0))
-    for v in range(L.step_variants(L.FP32)):
+    ref = _run_mesh(L, case, M0, 25, prec, schedule=(0, 0))
+    assert L.step_variants(prec) == (5 if precision == "fp32" else 3)
+    for v in range(L.step_variants(prec)):
         for o in (0, 1):
-            _same(ref, _run_mesh(L, case, M0, 25, L.FP32, schedule=(v, o)))
+            _same(ref, _run_mesh(L, case, M0, 25, prec, schedule=(v, o)))
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
