@@ -3,6 +3,7 @@
 // the launch sequence of the coupled step.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -487,8 +488,12 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     const size_t ns = m->slots();
     std::vector<BodyDev> bd(ns);
     for (size_t b = 0; b < ns; ++b) bd[b] = lbfsi::body_dev(m->bodies[b], proto.rho_inf, proto.uinf_x);
-    std::vector<double> M(nb * 4 * N);
-    if (rho_u_T) {
+    // the caller's field goes to the device as it is unless the C-grid's
+    // rows need rearranging (cut copies unified, mirrored rows added)
+    const bool direct = rho_u_T && !m->host.cgrid && !m->host.G;
+    std::vector<double> M(direct ? 0 : nb * 4 * N);
+    if (direct) {
+    } else if (rho_u_T) {
         std::memcpy(M.data(), rho_u_T, M.size() * sizeof(double));
     } else {
         for (size_t b = 0; b < nb; ++b)
@@ -501,11 +506,12 @@ int lbfsi_init_fields(lbfsi_mesh m, const lbfsi_flow_params* p, const double* rh
     }
     std::vector<BodyStateDev> zero(ns, BodyStateDev{0.0, 0.0, 0.0, 0.0});
     std::vector<double> zl(ns * 3, 0.0);
-    unify_cut_copies(m->host, M.data(), nb * 4, 1);
+    if (!direct) unify_cut_copies(m->host, M.data(), nb * 4, 1);
     if (m->host.G) M = expand_rows(m->host, M.data(), nb * 4, 1);
     cudaError_t e = cudaMemcpyAsync(m->d_bodies, bd.data(), ns * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->d_stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+        e = direct ? cudaMemcpyAsync(m->d_stage, rho_u_T, nb * 4 * N * sizeof(double), cudaMemcpyHostToDevice, m->stream)
+                   : cudaMemcpyAsync(m->d_stage, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->d_state_a, zero.data(), ns * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
@@ -622,8 +628,12 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
     const size_t nb = m->slots();   // one record per (solve, body)
-    const size_t lb = nb * 3 * sizeof(double), sbytes = nb * sizeof(BodyStateDev);
-    const size_t need = (size_t)nsteps * (lb + (states_out ? sbytes : 0));
+    const size_t lb = nb * 3 * sizeof(double);
+    // with the states: one strided copy per step of the record span from
+    // S_next to the end of loads (S_vgprev between them comes along)
+    const size_t o_s = offsetof(StepMaps, S_next), o_l = offsetof(StepMaps, loads);
+    const size_t span = o_l + 3 * sizeof(double) - o_s;
+    const size_t need = (size_t)nsteps * (states_out ? nb * span : lb);
     if (need > m->h_rec_bytes) {
         cudaError_t e = cudaStreamSynchronize(m->stream);
         if (m->h_rec) cudaFreeHost(m->h_rec);
@@ -638,7 +648,6 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
         m->h_rec_bytes = need;
     }
     char* hl = static_cast<char*>(m->h_rec);
-    char* hs = hl + (size_t)nsteps * lb;
     lbfsi::StepArgs a = make_args(m, 0);
     for (int s = 0; s < nsteps; ++s) {
         a.ustep = (int)m->host_k;
@@ -649,19 +658,25 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
         // the launch's epilogue wrote the step's loads and new body state into
         // the maps record of the next launch: strided device -> pinned copies
         const StepMaps* rec = m->d_maps[m->cur()];
-        e = cudaMemcpy2DAsync(hl + (size_t)s * lb, 3 * sizeof(double), &rec->loads[0], sizeof(StepMaps),
-                              3 * sizeof(double), nb, cudaMemcpyDeviceToHost, m->stream);
-        if (e == cudaSuccess && states_out)
-            e = cudaMemcpy2DAsync(hs + (size_t)s * sbytes, sizeof(BodyStateDev), &rec->S_next, sizeof(StepMaps),
-                                  sizeof(BodyStateDev), nb, cudaMemcpyDeviceToHost, m->stream);
+        if (states_out)
+            e = cudaMemcpy2DAsync(hl + (size_t)s * nb * span, span, reinterpret_cast<const char*>(rec) + o_s,
+                                  sizeof(StepMaps), span, nb, cudaMemcpyDeviceToHost, m->stream);
+        else
+            e = cudaMemcpy2DAsync(hl + (size_t)s * lb, 3 * sizeof(double), &rec->loads[0], sizeof(StepMaps),
+                                  3 * sizeof(double), nb, cudaMemcpyDeviceToHost, m->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step record copy");
     }
     cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step record sync");
-    std::memcpy(loads_out, hl, (size_t)nsteps * lb);
     if (states_out) {
         static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
-        std::memcpy(states_out, hs, (size_t)nsteps * sbytes);
+        for (size_t r = 0; r < (size_t)nsteps * nb; ++r) {
+            const char* src = hl + r * span;
+            std::memcpy(loads_out + 3 * r, src + (o_l - o_s), 3 * sizeof(double));
+            std::memcpy(states_out + r, src, sizeof(BodyStateDev));
+        }
+    } else {
+        std::memcpy(loads_out, hl, (size_t)nsteps * lb);
     }
     return check_status(m);
 }
