@@ -75,6 +75,8 @@ struct lbfsi_mesh_s {
     // pinned staging of lbfsi_step_record
     void* h_rec = nullptr;
     size_t h_rec_bytes = 0;
+    double* d_rec = nullptr;         // device history of lbfsi_step_record: [steps][records][7]
+    size_t d_rec_count = 0;
 
     int cur() const { return (int)(host_k & 1u); }
     bool first() const { return host_k == 0u; }
@@ -199,6 +201,7 @@ void free_all(lbfsi_mesh m) {
     if (m->graph) cudaGraphExecDestroy(m->graph);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->h_rec) cudaFreeHost(m->h_rec);
+    if (m->d_rec) cudaFree(m->d_rec);
     lbfsi::release_mesh(m->dmesh, m->mem);
 }
 
@@ -622,32 +625,55 @@ static int download_maps(lbfsi_mesh m, std::vector<StepMaps>& out) {
     return check_status(m);
 }
 
+namespace {
+// One step's records, packed: (Fx, Fy, M, h, alpha, hdot, adot) of every
+// (solve, body) from the maps records the step's epilogue wrote.
+__global__ void k_pack_records(const StepMaps* rec, int n, double* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const StepMaps& m = rec[r];
+    double* o = out + (size_t)r * 7;
+    o[0] = m.loads[0];
+    o[1] = m.loads[1];
+    o[2] = m.loads[2];
+    o[3] = m.S_next.h;
+    o[4] = m.S_next.alpha;
+    o[5] = m.S_next.hdot;
+    o[6] = m.S_next.adot;
+}
+}  // namespace
+
 int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_state* states_out) {
     lbfsi::TraceRange trace_("lbfsi_step_record");
     if (!m || !loads_out) return fail(LBFSI_EINVAL, "null argument");
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
     const size_t nb = m->slots();   // one record per (solve, body)
-    const size_t lb = nb * 3 * sizeof(double);
-    // with the states: one strided copy per step of the record span from
-    // S_next to the end of loads (S_vgprev between them comes along)
-    const size_t o_s = offsetof(StepMaps, S_next), o_l = offsetof(StepMaps, loads);
-    const size_t span = o_l + 3 * sizeof(double) - o_s;
-    const size_t need = (size_t)nsteps * (states_out ? nb * span : lb);
-    if (need > m->h_rec_bytes) {
+    // every step's records are packed on the device behind its launch (one
+    // small kernel: a strided copy of the records per step costs more), and
+    // the history comes back in one copy at the end
+    const size_t cnt = (size_t)nsteps * nb * 7;
+    if (cnt > m->d_rec_count || cnt * sizeof(double) > m->h_rec_bytes) {
         cudaError_t e = cudaStreamSynchronize(m->stream);
-        if (m->h_rec) cudaFreeHost(m->h_rec);
-        m->h_rec = nullptr;
-        m->h_rec_bytes = 0;
-        if (e == cudaSuccess) e = cudaHostAlloc(&m->h_rec, need, cudaHostAllocDefault);
-        if (e != cudaSuccess) {
-            m->h_rec = nullptr;
-            cudaGetLastError();
-            return fail(LBFSI_ENOMEM, "pinned staging for the step records");
+        if (e == cudaSuccess && cnt > m->d_rec_count) {
+            if (m->d_rec) cudaFree(m->d_rec);
+            m->d_rec = nullptr;
+            m->d_rec_count = 0;
+            e = cudaMalloc(&m->d_rec, cnt * sizeof(double));
+            if (e == cudaSuccess) m->d_rec_count = cnt;
         }
-        m->h_rec_bytes = need;
+        if (e == cudaSuccess && cnt * sizeof(double) > m->h_rec_bytes) {
+            if (m->h_rec) cudaFreeHost(m->h_rec);
+            m->h_rec = nullptr;
+            m->h_rec_bytes = 0;
+            e = cudaHostAlloc(&m->h_rec, cnt * sizeof(double), cudaHostAllocDefault);
+            if (e == cudaSuccess) m->h_rec_bytes = cnt * sizeof(double);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBFSI_ENOMEM, "staging for the step records");
+        }
     }
-    char* hl = static_cast<char*>(m->h_rec);
     lbfsi::StepArgs a = make_args(m, 0);
     for (int s = 0; s < nsteps; ++s) {
         a.ustep = (int)m->host_k;
@@ -656,27 +682,22 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         m->host_k++;
         // the launch's epilogue wrote the step's loads and new body state into
-        // the maps record of the next launch: strided device -> pinned copies
-        const StepMaps* rec = m->d_maps[m->cur()];
-        if (states_out)
-            e = cudaMemcpy2DAsync(hl + (size_t)s * nb * span, span, reinterpret_cast<const char*>(rec) + o_s,
-                                  sizeof(StepMaps), span, nb, cudaMemcpyDeviceToHost, m->stream);
-        else
-            e = cudaMemcpy2DAsync(hl + (size_t)s * lb, 3 * sizeof(double), &rec->loads[0], sizeof(StepMaps),
-                                  3 * sizeof(double), nb, cudaMemcpyDeviceToHost, m->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "step record copy");
+        // the maps record of the next launch
+        k_pack_records<<<(unsigned)((nb + 127) / 128), 128, 0, m->stream>>>(m->d_maps[m->cur()], (int)nb,
+                                                                             m->d_rec + (size_t)s * nb * 7);
+        m->launches++;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "step record kernel");
     }
-    cudaError_t e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "step record sync");
-    if (states_out) {
-        static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
-        for (size_t r = 0; r < (size_t)nsteps * nb; ++r) {
-            const char* src = hl + r * span;
-            std::memcpy(loads_out + 3 * r, src + (o_l - o_s), 3 * sizeof(double));
-            std::memcpy(states_out + r, src, sizeof(BodyStateDev));
-        }
-    } else {
-        std::memcpy(loads_out, hl, (size_t)nsteps * lb);
+    cudaError_t e = cudaSuccess;
+    if (cnt) e = cudaMemcpyAsync(m->h_rec, m->d_rec, cnt * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step record copy");
+    static_assert(sizeof(lbfsi_body_state) == sizeof(BodyStateDev), "layout");
+    const double* h = static_cast<const double*>(m->h_rec);
+    for (size_t r = 0; r < (size_t)nsteps * nb; ++r) {
+        std::memcpy(loads_out + 3 * r, h + 7 * r, 3 * sizeof(double));
+        if (states_out) std::memcpy(states_out + r, h + 7 * r + 3, sizeof(BodyStateDev));
     }
     return check_status(m);
 }
