@@ -626,12 +626,15 @@ static int download_maps(lbfsi_mesh m, std::vector<StepMaps>& out) {
 }
 
 namespace {
-// One step's records, packed: (Fx, Fy, M, h, alpha, hdot, adot) of every
-// (solve, body) from the maps records the step's epilogue wrote.
-__global__ void k_pack_records(const StepMaps* rec, int n, double* out) {
+// The records of one or two consecutive steps, packed: (Fx, Fy, M, h,
+// alpha, hdot, adot) of every (solve, body) from the maps records the steps'
+// epilogues wrote (the two ping-pong sets hold the last two steps' records):
+// prev (may be null) then cur, n records each.
+__global__ void k_pack_records(const StepMaps* prev, const StepMaps* cur, int n, double* out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const StepMaps& m = rec[r];
+    const int np = prev ? n : 0;
+    if (r >= np + n) return;
+    const StepMaps& m = r < np ? prev[r] : cur[r - np];
     double* o = out + (size_t)r * 7;
     o[0] = m.loads[0];
     o[1] = m.loads[1];
@@ -649,9 +652,9 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
     if (!m->initialized) return fail(LBFSI_ESTATE, "init_fields first");
     if (nsteps < 0) return fail(LBFSI_EINVAL, "nsteps must be >= 0");
     const size_t nb = m->slots();   // one record per (solve, body)
-    // every step's records are packed on the device behind its launch (one
-    // small kernel: a strided copy of the records per step costs more), and
-    // the history comes back in one copy at the end
+    // the records are packed on the device behind every second launch (one
+    // small kernel for two steps: a strided copy of the records per step
+    // costs more), and the history comes back in one copy at the end
     const size_t cnt = (size_t)nsteps * nb * 7;
     if (cnt > m->d_rec_count || cnt * sizeof(double) > m->h_rec_bytes) {
         cudaError_t e = cudaStreamSynchronize(m->stream);
@@ -682,12 +685,19 @@ int lbfsi_step_record(lbfsi_mesh m, int nsteps, double* loads_out, lbfsi_body_st
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         m->host_k++;
         // the launch's epilogue wrote the step's loads and new body state into
-        // the maps record of the next launch
-        k_pack_records<<<(unsigned)((nb + 127) / 128), 128, 0, m->stream>>>(m->d_maps[m->cur()], (int)nb,
-                                                                             m->d_rec + (size_t)s * nb * 7);
-        m->launches++;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "step record kernel");
+        // the maps record of the next launch; the previous step's records are
+        // in the other set until the launch after this one
+        const bool pair = (s & 1) != 0;
+        if (pair || s == nsteps - 1) {
+            const int first = pair ? s - 1 : s;
+            const unsigned nrec = (unsigned)((pair ? 2 : 1) * nb);
+            k_pack_records<<<(nrec + 127) / 128, 128, 0, m->stream>>>(
+                pair ? m->d_maps[m->cur() ^ 1] : nullptr, m->d_maps[m->cur()], (int)nb,
+                m->d_rec + (size_t)first * nb * 7);
+            m->launches++;
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "step record kernel");
+        }
     }
     cudaError_t e = cudaSuccess;
     if (cnt) e = cudaMemcpyAsync(m->h_rec, m->d_rec, cnt * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
