@@ -123,3 +123,88 @@ def test_departure_outside_the_nodes_elements_is_refused():
         inside.append(abs(xi) <= 1 + 1e-12 and abs(eta) <= 1 + 1e-12)
     assert any(inside)
     assert um.locate(perm[(i + 3) * Nj + j], P) is not None
+
+
+# ----- the whole step on an unstructured periodic mesh ----------------------
+import oracle.solver as OS   # noqa: E402
+
+
+def _box_pair(n_i, n_j, h, skew, seed):
+    sm = OM.periodic_box_mesh(n_i, n_j, n_i * h, n_j * h, skew=skew)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n_i * n_j)
+    um = OU.from_box(sm, perm, rng.permutation((n_i // 2) * (n_j // 2)))
+    return sm, um, perm
+
+
+def _to_u(A, perm):
+    """[..., Ni, Nj] grid field -> [..., N, 1] in the unstructured numbering."""
+    flat = A.reshape(A.shape[:-2] + (-1,))
+    out = np.empty_like(flat)
+    out[..., perm] = flat
+    return out[..., None]
+
+
+def _solver(mesh, M0, dt, tau=0.6):
+    mu = (tau - 0.5) * float(np.mean(M0[0])) * float(np.mean(M0[3])) * dt
+    return OS.Solver(mesh, gamma=1.4, Pr=0.71, mu=mu, dt=dt, rho_inf=1.0, u_inf=(0.0, 0.0),
+                     T_inf=float(np.mean(M0[3])), bodies=[], M0=M0, walls=False), mu
+
+
+def test_unstructured_box_step_equals_structured_step_with_its_stencil():
+    """With the structured stencil (R18) as its gradient, the oracle's step
+    on the shuffled element list of a skewed periodic box is the structured
+    step: departures across the periods, interpolation and the adapter to the
+    solver agree to round-off over several steps."""
+    n_i, n_j = 12, 8
+    sm, um, perm = _box_pair(n_i, n_j, 1.0, 0.3, 3)
+    rng = np.random.default_rng(4)
+    M0 = np.empty((4, n_i, n_j))
+    M0[0] = 1.0 + 0.01 * rng.uniform(-1, 1, (n_i, n_j))
+    M0[1] = 0.03 * rng.uniform(-1, 1, (n_i, n_j))
+    M0[2] = 0.03 * rng.uniform(-1, 1, (n_i, n_j))
+    M0[3] = 1.0 / 3.0 + 0.005 * rng.uniform(-1, 1, (n_i, n_j))
+
+    def r18(F):
+        grid = F[..., perm].reshape(F.shape[:-1] + (n_i, n_j))
+        gx, gy = sm.grad_X(grid)
+        ox = np.empty_like(F)
+        oy = np.empty_like(F)
+        ox[..., perm] = gx.reshape(F.shape)
+        oy[..., perm] = gy.reshape(F.shape)
+        return ox, oy
+
+    s_s, _ = _solver(sm, M0, 0.5, tau=0.8)
+    s_u, _ = _solver(OU.AsGrid(um, grad=r18), _to_u(M0, perm), 0.5, tau=0.8)
+    for _ in range(5):
+        a = s_s.step()
+        b = s_u.step()
+    assert np.abs(_to_u(a.f_post, perm) - b.f_post).max() < 1e-13
+    assert np.abs(_to_u(a.M, perm) - b.M).max() < 1e-13
+
+
+def test_taylor_green_decay_on_an_unstructured_box():
+    """The genuine unstructured step (gradients by reading R33) on the
+    shuffled element list of a periodic box: u = U (sin kx cos ky,
+    -cos kx sin ky) decays as exp(-2 nu k^2 t) (Sec. II C)."""
+    n = 32
+    sm, um, perm = _box_pair(n, n, 1.0, 0.0, 6)
+    x = np.arange(n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    k = 2 * np.pi / n
+    U = 0.02
+    M0 = np.empty((4, n, n))
+    M0[0] = 1.0
+    M0[1] = U * np.sin(k * X) * np.cos(k * Y)
+    M0[2] = -U * np.cos(k * X) * np.sin(k * Y)
+    M0[3] = 1.0 / 3.0
+    s, mu = _solver(OU.AsGrid(um), _to_u(M0, perm), 1.0, tau=0.6)
+    basis = _to_u(np.sin(k * X) * np.cos(k * Y), perm)
+    amps, ts = [], []
+    for step in range(1, 161):
+        r = s.step()
+        if step >= 20:
+            amps.append((r.M[1] * basis).sum())
+            ts.append(step)
+    rate = -np.polyfit(ts, np.log(np.abs(amps)), 1)[0]
+    assert abs(rate / (2 * mu * k * k) - 1) < 0.02
