@@ -142,36 +142,50 @@ class Q2Mesh:
         i.e. expressed in the node's own periodic image).  The candidates are
         the four cells sharing the node, tried in the fixed order
         (i-1, j-1), (i-1, j), (i, j-1), (i, j); the first that contains P wins
-        (reading R9).  Returns wa, wb, xi, eta, found."""
+        (reading R9); the points no candidate holds within XI_TOL go through
+        the second pass of reading R8.  Returns wa, wb, xi, eta, found."""
         i = np.asarray(i)
         j = np.asarray(j)
         if candidates is None:
             candidates = [(-1, -1), (-1, 0), (0, -1), (0, 0)]
+        out = self._locate_pass(P, i, j, candidates, XI_TOL)
+        found = out[4]
+        if not found.all():
+            shape = found.shape
+            miss = np.nonzero(~found.ravel())[0]
+            Pf = np.broadcast_to(P, shape + (2,)).reshape(-1, 2)[miss]
+            i_f = np.broadcast_to(i, shape).ravel()[miss]
+            j_f = np.broadcast_to(j, shape).ravel()[miss]
+            second = self._locate_pass(Pf, i_f, j_f, candidates, XI_TOL_THIN)
+            out = [o.ravel().copy() for o in out]
+            for o_all, o_sub in zip(out, second):
+                o_all[miss] = o_sub
+            out = [o.reshape(shape) for o in out]
+        return tuple(out)
+
+    def _locate_pass(self, P, i, j, candidates, tol):
         shape = np.broadcast(i, j).shape
         wa_o = np.zeros(shape, dtype=np.int64)
         wb_o = np.zeros(shape, dtype=np.int64)
         xi_o = np.zeros(shape)
         eta_o = np.zeros(shape)
         found = np.zeros(shape, dtype=bool)
-        for tol in (XI_TOL, XI_TOL_THIN):
-            for da, db in candidates:
-                a = i + da
-                b = j + db
-                ok = self.valid_cell(a, b)
-                if not np.any(ok & ~found):
-                    continue
-                a_s = np.where(ok, a, 0)
-                b_s = np.where(ok, b, 0)
-                with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-                    wa, wb, xi, eta, inside = self.locate_in_cell(a_s, b_s, P, tol)
-                take = ok & inside & ~found
-                wa_o = np.where(take, wa, wa_o)
-                wb_o = np.where(take, wb, wb_o)
-                xi_o = np.where(take, xi, xi_o)
-                eta_o = np.where(take, eta, eta_o)
-                found |= take
-            if found.all():
-                break
+        for da, db in candidates:
+            a = i + da
+            b = j + db
+            ok = self.valid_cell(a, b)
+            if not np.any(ok & ~found):
+                continue
+            a_s = np.where(ok, a, 0)
+            b_s = np.where(ok, b, 0)
+            with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+                wa, wb, xi, eta, inside = self.locate_in_cell(a_s, b_s, P, tol)
+            take = ok & inside & ~found
+            wa_o = np.where(take, wa, wa_o)
+            wb_o = np.where(take, wb, wb_o)
+            xi_o = np.where(take, xi, xi_o)
+            eta_o = np.where(take, eta, eta_o)
+            found |= take
         return wa_o, wb_o, xi_o, eta_o, found
 
     # ----- Eq. SemiLagrProp: Q2 Lagrange interpolation -------------------
