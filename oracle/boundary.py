@@ -82,20 +82,44 @@ def grad_populations(rho, ux, uy, T, grads, Cv, mu, dt, Pr):
     return feq + f1, geq + g1
 
 
-def far_field_targets(mesh, M_prev, u_inf, rho_inf, T_inf):
+def _outlet_values(mesh, M_prev, A, n_hat, i, j, dt):
+    """rho, u_x, u_y, T of the previous step's moment field at
+    B = A - dt n_hat, one time step inside the far field along its outward
+    unit direction, by Q2 interpolation in the cells of node (i, j) (reading
+    R20: the wall's zero-gradient construction of Sec. III A applied to the
+    outlet, for rho, T and u)."""
+    B = A - dt * n_hat
+    wa, wb, xi, eta, found = mesh.locate(B, i, j)
+    if not np.all(found):
+        raise RuntimeError("outlet point B outside the cells next to the far field")
+    return [mesh.interpolate(M_prev[c], wa, wb, xi, eta) for c in range(4)]
+
+
+def _unit(v):
+    return v / np.hypot(v[..., 0], v[..., 1])[..., None]
+
+
+def far_field_targets(mesh, M_prev, u_inf, rho_inf, T_inf, dt):
     """Inlet / outlet targets at the far-field row (Sec. III A 2).  Reading
     R20: a far-field node is an inlet where the free stream enters
-    (U_inf . n_out < 0, n_out the outward radial direction), else an outlet;
-    inlet targets are the free stream, outlet targets are copied from the
-    radially inner neighbour (zero gradient of rho, u, T) of the previous step's
-    field."""
+    (U_inf . n_out < 0, n_out the outward direction of the grid line that
+    ends there, X[last] - X[last-1]), else an outlet.  Inlet targets are the
+    free stream.  Outlet targets are built the way the wall's are (Sec. III A
+    2 refers the outlet to the wall's construction): zero normal gradient of
+    rho, u and T imposed
+    through the point B one time step inside the boundary along the outward
+    unit direction, B = A - dt n_out, whose values are the Q2 interpolation
+    of the previous step's moment field (as for the wall targets, reading
+    R19)."""
     last = mesh.Ni - 1
-    n_out = mesh.X[last] - mesh.X[last - 1]
+    Nj = mesh.Nj
+    n_out = _unit(mesh.X[last] - mesh.X[last - 1])
     inlet = (u_inf[0] * n_out[:, 0] + u_inf[1] * n_out[:, 1]) < 0.0
-    rho = np.where(inlet, rho_inf, M_prev[0, last - 1])
-    ux = np.where(inlet, u_inf[0], M_prev[1, last - 1])
-    uy = np.where(inlet, u_inf[1], M_prev[2, last - 1])
-    T = np.where(inlet, T_inf, M_prev[3, last - 1])
+    ob = _outlet_values(mesh, M_prev, mesh.X[last], n_out, np.full(Nj, last), np.arange(Nj), dt)
+    rho = np.where(inlet, rho_inf, ob[0])
+    ux = np.where(inlet, u_inf[0], ob[1])
+    uy = np.where(inlet, u_inf[1], ob[2])
+    T = np.where(inlet, T_inf, ob[3])
     return rho, ux, uy, T, inlet
 
 
@@ -143,30 +167,27 @@ def far_field_mask_cgrid(mesh):
     return far
 
 
-def far_field_targets_cgrid(mesh, M_prev, u_inf, rho_inf, T_inf):
+def far_field_targets_cgrid(mesh, M_prev, u_inf, rho_inf, T_inf, dt):
     """Inlet / outlet targets on the far field of a C-grid (reading R20 on
-    each boundary): on the last row the outward direction and the inner
-    neighbour are along i, on the outlet columns (rows below the last) along
-    j.  Returns rho, ux, uy, T on the whole [Ni, Nj] grid (meaningful on the
-    far-field mask only) and the inlet mask."""
+    each boundary): on the last row the outward direction is that of the
+    grid line along i, on the outlet columns (rows below the last) along j;
+    outlet values at B = A - dt n_out as on an O-grid.  Returns rho, ux, uy,
+    T on the whole [Ni, Nj] grid (meaningful on the far-field mask only) and
+    the inlet mask."""
     Ni, Nj = mesh.Ni, mesh.Nj
     X = mesh.X
     n_out = np.zeros((Ni, Nj, 2))
-    inner = np.zeros((Ni, Nj, 2), dtype=np.int64)
-    ii, jj = np.meshgrid(np.arange(Ni), np.arange(Nj), indexing="ij")
-    inner[..., 0] = ii
-    inner[..., 1] = jj
-    n_out[:, 0] = X[:, 0] - X[:, 1]
-    inner[:, 0, 1] = 1
-    n_out[:, Nj - 1] = X[:, Nj - 1] - X[:, Nj - 2]
-    inner[:, Nj - 1, 1] = Nj - 2
-    n_out[Ni - 1] = X[Ni - 1] - X[Ni - 2]
-    inner[Ni - 1, :, 0] = Ni - 2
-    inner[Ni - 1, :, 1] = np.arange(Nj)
+    n_out[..., 0] = 1.0          # placeholder off the far field
+    n_out[:, 0] = _unit(X[:, 0] - X[:, 1])
+    n_out[:, Nj - 1] = _unit(X[:, Nj - 1] - X[:, Nj - 2])
+    n_out[Ni - 1] = _unit(X[Ni - 1] - X[Ni - 2])
     inlet = (u_inf[0] * n_out[..., 0] + u_inf[1] * n_out[..., 1]) < 0.0
-    a, b = inner[..., 0], inner[..., 1]
-    rho = np.where(inlet, rho_inf, M_prev[0][a, b])
-    ux = np.where(inlet, u_inf[0], M_prev[1][a, b])
-    uy = np.where(inlet, u_inf[1], M_prev[2][a, b])
-    T = np.where(inlet, T_inf, M_prev[3][a, b])
-    return rho, ux, uy, T, inlet
+    far = far_field_mask_cgrid(mesh)
+    ii, jj = np.nonzero(far)
+    ob = _outlet_values(mesh, M_prev, X[ii, jj], n_out[ii, jj], ii, jj, dt)
+    out = []
+    for c, free in enumerate((rho_inf, u_inf[0], u_inf[1], T_inf)):
+        v = np.zeros((Ni, Nj))
+        v[ii, jj] = ob[c]
+        out.append(np.where(inlet, free, v))
+    return out[0], out[1], out[2], out[3], inlet & far

@@ -218,3 +218,72 @@ def test_grad_nonequilibrium_moments():
     np.testing.assert_allclose(mom(f1, 0, 2), dt * p1yy, rtol=1e-12, atol=1e-17)
     q1x = -(2 / om1) * rho * (Cv + 1) * T * dTdx + 2 * (ux * p1xx + uy * p1xy)
     np.testing.assert_allclose(mom(g1, 1, 0), dt * q1x, rtol=1e-12, atol=1e-17)
+    q1y = -(2 / om1) * rho * (Cv + 1) * T * dTdy + 2 * (ux * p1xy + uy * p1yy)
+    np.testing.assert_allclose(mom(g1, 0, 1), dt * q1y, rtol=1e-12, atol=1e-17)
+    # R^(1) (Eq. gnoneq): grad E = Cv grad T + (grad u) . u
+    E = Cv * T + 0.5 * (ux * ux + uy * uy)
+    dEdx = Cv * dTdx + ux * dudx + uy * dvdx
+    dEdy = Cv * dTdy + ux * dudy + uy * dvdy
+    pre = -(2 / om1) * rho * T
+    r1xx = pre * (2 * dudx * (E + 2 * T) + 2 * ux * dEdx)
+    r1xy = pre * ((dvdx + dudy) * (E + 2 * T) + ux * dEdy + uy * dEdx)
+    r1yy = pre * (2 * dvdy * (E + 2 * T) + 2 * uy * dEdy)
+    np.testing.assert_allclose(mom(g1, 2, 0), dt * r1xx, rtol=1e-12, atol=1e-17)
+    np.testing.assert_allclose(mom(g1, 1, 1), dt * r1xy, rtol=1e-12, atol=1e-17)
+    np.testing.assert_allclose(mom(g1, 0, 2), dt * r1yy, rtol=1e-12, atol=1e-17)
+
+
+def test_grad_stress_is_the_navier_stokes_stress():
+    """Grad's populations f^eq + dt f^(1) (Eq. fnoneq) carry the viscous stress
+    of the Navier-Stokes-Fourier equations the model recovers (Sec. II C):
+    the wall-force stress -p I - (1 - omega/2) sum (f - f^eq) c c equals
+    -p I + mu [grad u + grad u^T - (1/Cv)(div u) I] with
+    mu = (1/omega - 1/2) p dt.  This ties P^(1) to a different equation of
+    the paper than the one it is printed in: a wrong sign, factor or bulk
+    term in P^(1) fails it (T = 1/3, where the D2Q9 fourth moments are
+    isotropic)."""
+    from oracle import forces
+    Cv = 2.5
+    rng = np.random.default_rng(8)
+    n = 24
+    rho = rng.uniform(0.8, 1.2, n)
+    ux, uy = rng.uniform(-0.1, 0.1, (2, n))
+    T = np.full(n, 1.0 / 3.0)
+    dudx, dudy, dvdx, dvdy, dTdx, dTdy = 0.02 * rng.normal(size=(6, n))
+    dt, mu, Pr = 0.02, 3e-3, 0.71
+    f1, g1 = K.grad_f1(rho, ux, uy, T, Cv, dudx, dudy, dvdx, dvdy, dTdx, dTdy, mu, dt, Pr)
+    f = K.f_eq(rho, ux, uy, T) + f1
+    g = K.g_eq(rho, ux, uy, T, Cv) + g1
+    sxx, sxy, syy = forces.node_stress(f, g, Cv, mu, dt, Pr)
+    p = rho * T
+    div = dudx + dvdy
+    np.testing.assert_allclose(sxx, -p + mu * (2 * dudx - div / Cv), rtol=1e-12)
+    np.testing.assert_allclose(syy, -p + mu * (2 * dvdy - div / Cv), rtol=1e-12)
+    np.testing.assert_allclose(sxy, mu * (dvdx + dudy), rtol=1e-10, atol=1e-16)
+
+
+def test_grad_heat_flux_and_energy_moment_at_a_no_slip_wall():
+    """At a no-slip wall target (u = 0) Grad's g carries the Fourier heat
+    flux of Sec. II C: with kappa = Cp (1/omega_1 - 1/2) p dt, the flux
+    sum dt g^(1) c = dt q^(1) is -2 kappa / (1 - omega_1/2) grad T; and
+    sum dt g^(1) c c reduces to -(2/omega_1) p (Cv + 2) T dt S, the only
+    term of R^(1) left when u = 0 (E = Cv T)."""
+    Cv = 2.5
+    rng = np.random.default_rng(9)
+    n = 12
+    rho = rng.uniform(0.8, 1.2, n)
+    zero = np.zeros(n)
+    T = np.full(n, 1.0 / 3.0)
+    dudx, dudy, dvdx, dvdy, dTdx, dTdy = 0.02 * rng.normal(size=(6, n))
+    dt, mu, Pr = 0.02, 3e-3, 0.6
+    _, g1 = K.grad_f1(rho, zero, zero, T, Cv, dudx, dudy, dvdx, dvdy, dTdx, dTdy, mu, dt, Pr)
+    om, om1 = K.relaxation(rho, T, mu, dt, Pr)
+    p = rho * T
+    kappa = (Cv + 1) * (1 / om1 - 0.5) * p * dt
+    fac = -2 * kappa / (1 - 0.5 * om1)
+    np.testing.assert_allclose(mom(g1, 1, 0), fac * dTdx, rtol=1e-12)
+    np.testing.assert_allclose(mom(g1, 0, 1), fac * dTdy, rtol=1e-12)
+    r = -(2 / om1) * p * (Cv + 2) * T * dt
+    np.testing.assert_allclose(mom(g1, 2, 0), r * 2 * dudx, rtol=1e-12)
+    np.testing.assert_allclose(mom(g1, 1, 1), r * (dvdx + dudy), rtol=1e-12)
+    np.testing.assert_allclose(mom(g1, 0, 2), r * 2 * dvdy, rtol=1e-12)
