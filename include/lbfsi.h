@@ -365,15 +365,26 @@ int lbfsi_restore(lbfsi_mesh m, const void* host_buf, size_t bytes);
  *   f, g                       DEVICE [nbatch][9][nr*ntheta] post-propagation
  *                              populations (only the wall row is read)
  *   body_ref                   DEVICE [nbatch][3]: x_p, y_p, alpha of each
- *                              body (reference point, pitch angle)
+ *                              body.  x_p, y_p is the body's reference point
+ *                              (cylinder centre or elastic axis) in the
+ *                              UNDEFORMED mesh frame -- the value given to
+ *                              lbfsi_create_mesh, not its current, plunged
+ *                              position; alpha is the pitch angle at which
+ *                              the populations were streamed.  Moment arms
+ *                              are R(alpha)(X_wall - X_p) with X_wall the
+ *                              undeformed wall nodes, so a translated x_p, y_p
+ *                              gives a wrong moment without an error.
  *   mu, dt, gamma              viscosity, time step, adiabatic exponent
  *   loads                      DEVICE out [nbatch][3]: F_x, F_y, M_z
  * Limits: nbatch <= 256 and nbatch * ceil(ntheta / 32) <= 4096, else
- * LBFSI_EINVAL.  Asynchronous on cuda_stream.  The first call on a device
- * looks up the scratch array's device address and clears its counters (a
- * blocking step), so make that first call before any stream capture.  Every
- * call shares the one scratch array: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. */
+ * LBFSI_EINVAL.  Asynchronous on cuda_stream: each call clears the completion
+ * counters it uses with an asynchronous memset on that stream, then launches
+ * one kernel.  The first call on a device (with that device current) looks up
+ * the scratch array's device address (cudaGetSymbolAddress, which may load the
+ * module and block), so make that first call before any stream capture.
+ * Every call shares the one scratch array, which keeps the last call's
+ * partial sums: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
 int lbfsi_wall_loads_noalloc(int nr, int ntheta, int nbatch, int precision, const double* r,
                              const double* e, double xc, double yc, const void* f, const void* g,
                              const double* body_ref, double mu, double dt, double gamma,

@@ -100,7 +100,7 @@ int check_status(lbfsi_mesh m) {
     if (st & lbfsi::ST_DEPARTURE)
         return fail(LBFSI_EDEPARTURE, "departure point outside the cells adjacent to its node (CFL)");
     if (st & lbfsi::ST_BPOINT)
-        return fail(LBFSI_EDEPARTURE, "wall target point outside the first element row");
+        return fail(LBFSI_EDEPARTURE, "wall or outlet target point B outside the cells next to its node");
     if (st & lbfsi::ST_NONPHYS) return fail(LBFSI_ENONPHYS, "non-physical state (rho<=0, T<=0 or NaN)");
     return LBFSI_OK;
 }

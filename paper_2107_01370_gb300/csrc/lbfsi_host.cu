@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "lbfsi_device.cuh"
 #include "lbfsi_host.h"
 
 namespace lbfsi {
@@ -119,6 +120,18 @@ void geometry_tables(HostMesh& m) {
     }
 }
 
+// Scale every (x, y) pair of v to unit length: the outward directions of
+// the far field, whose outlet targets sit one time step inside along them.
+void normalise_pairs(std::vector<double>& v) {
+    for (size_t k = 0; k + 1 < v.size(); k += 2) {
+        const double l = std::hypot(v[k], v[k + 1]);
+        if (l > 0.0) {
+            v[k] /= l;
+            v[k + 1] /= l;
+        }
+    }
+}
+
 }  // namespace
 
 int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc, double yc,
@@ -159,6 +172,7 @@ int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc,
             m.xw[2 * j + c] = (c ? m.ym : m.xm) + m.r[0] * m.e[2 * j + c];
             m.fardir[2 * j + c] = (m.r[nr - 1] - m.r[nr - 2]) * m.e[2 * j + c];
         }
+    normalise_pairs(m.fardir);
     wall_geometry(m);
     geometry_tables(m);
     return LBFSI_OK;
@@ -208,6 +222,7 @@ int build_host_mesh_xy(int nr, int nt, const double* X, double xc, double yc, Ho
             m.xw[2 * j + c] = P(0, j, c);
             m.fardir[2 * j + c] = P(nr - 1, j, c) - P(nr - 2, j, c);
         }
+    normalise_pairs(m.fardir);
     wall_geometry(m);
     // inverse metric at the nodes: derivatives of X along the index
     // directions with the field's stencil (central; one-sided on the wall
@@ -404,6 +419,8 @@ int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double
             m.fardirj[4 * i + c] = P(i, 0, c) - P(i, 1, c);
             m.fardirj[4 * i + 2 + c] = P(i, nt - 1, c) - P(i, nt - 2, c);
         }
+    normalise_pairs(m.fardir);
+    normalise_pairs(m.fardirj);
     wall_geometry_chains(m);
     // node coordinates with the mirrored rows: X(-k, j) = X(k, nt-1-j)
     const size_t g0 = (size_t)G * nt;
@@ -651,6 +668,13 @@ int fill_flow(const lbfsi_flow_params& p, SolveDev& s) {
     s.uinf_x_f = (float)s.uinf_x;
     s.uinf_y_f = 0.0f;
     s.T_inf_f = (float)s.T_inf;
+    double fr[9], gr[9];
+    f_equilibrium<double>(s.rho_inf, s.uinf_x, s.uinf_y, s.T_inf, fr);
+    g_equilibrium<double>(s.rho_inf, s.uinf_x, s.uinf_y, s.T_inf, s.Cv, gr);
+    for (int q = 0; q < 9; ++q) {
+        s.fgref[2 * q] = (float)fr[q];
+        s.fgref[2 * q + 1] = (float)gr[q];
+    }
     return LBFSI_OK;
 }
 

@@ -12,7 +12,7 @@ namespace lbfsi {
 enum : unsigned {
     ST_DEPARTURE = 1u,   // departure point outside the adjacent cells
     ST_NONPHYS = 2u,     // rho <= 0, T <= 0 or NaN
-    ST_BPOINT = 4u,      // wall target point outside the first element row
+    ST_BPOINT = 4u,      // wall or outlet target point B outside the cells next to its node
     ST_BOUNDS = 8u,      // bounds-checked build: an index outside its buffer (access skipped)
 };
 
@@ -102,7 +102,7 @@ struct MeshDev {
     double emin;                   // separable O-grid: min over j of |e_j| (static-tile test)
     float emin_f;
     const double* xw;              // [nt][2] wall node coordinates
-    const double* fardir;          // [nt][2] outward direction at the far-field row
+    const double* fardir;          // [nt][2] outward unit direction at the far-field row
     // general meshes (node coordinates given): element type of the path
     int general;
     const void* nodex;             // [N][2] node coordinates
@@ -114,7 +114,7 @@ struct MeshDev {
     // and nt-1 are outlets
     int cgrid;
     const int* coltype;            // [nt]
-    const double* fardirj;         // [nr][2][2] outward directions of columns 0 and nt-1
+    const double* fardirj;         // [nr][2][2] outward unit directions of columns 0 and nt-1
     // doubly periodic box (general meshes only): rows wrap like columns,
     // every node is interior (no wall, no far field)
     int box;
@@ -137,6 +137,12 @@ struct SolveDev {
     // converts or divides in float64)
     double dt, mu, Cv, Pr, rho_inf, uinf_x, uinf_y, T_inf;
     float dt_f, mu_f, Cv_f, Pr_f, iPr_f, rho_inf_f, uinf_x_f, uinf_y_f, T_inf_f, pad_f;
+    // float path: the free-stream equilibrium pairs (f_q, g_q), q = 0..8.  The
+    // step interpolates deviations from them, so that the round-off of the
+    // float Q2 weights (their sum is 1 only to within an ulp, the same way
+    // every step at a node that does not move) scales with the deviation, not
+    // with the population
+    float fgref[18];
     void* p[2];                    // populations, (f_q, g_q) pairs [9][N]
     void* M[2];                    // moments [4][N]
     StepMaps* maps[2];             // [nbody] each

@@ -54,18 +54,19 @@ __global__ void __launch_bounds__(NA_TJ) k_wall_loads_noalloc(
     __shared__ double red[3][NA_TJ];
     double c0 = 0.0, c1 = 0.0, c2 = 0.0;
     if (j < nt) {
-        R fq[9], gq[9];
+        double fq[9], gq[9];
         for (int q = 0; q < 9; ++q) {
-            fq[q] = f[((size_t)b * 9 + q) * N + j];
-            gq[q] = g[((size_t)b * 9 + q) * N + j];
+            fq[q] = (double)f[((size_t)b * 9 + q) * N + j];
+            gq[q] = (double)g[((size_t)b * 9 + q) * N + j];
         }
-        // sigma = -p I - (1 - omega/2) P^(1), P^(1) = sum (f - f^eq) c c (Sec. III)
-        const lbfsi::Macro<R> mc = lbfsi::moments(fq, gq, (R)Cv);
-        R feq[9];
+        // sigma = -p I - (1 - omega/2) P^(1), P^(1) = sum (f - f^eq) c c (Sec. III),
+        // float64 from the populations on, as in the step kernel
+        const lbfsi::Macro<double> mc = lbfsi::moments(fq, gq, Cv);
+        double feq[9];
         lbfsi::f_equilibrium(mc.rho, mc.ux, mc.uy, mc.T, feq);
         double pxx = 0, pxy = 0, pyy = 0;
         for (int q = 0; q < 9; ++q) {
-            const double fn = (double)fq[q] - (double)feq[q];
+            const double fn = fq[q] - feq[q];
             pxx += lbfsi::cxq(q) * lbfsi::cxq(q) * fn;
             pxy += lbfsi::cxq(q) * lbfsi::cyq(q) * fn;
             pyy += lbfsi::cyq(q) * lbfsi::cyq(q) * fn;
@@ -128,8 +129,9 @@ __global__ void __launch_bounds__(NA_TJ) k_wall_loads_noalloc(
     }
 }
 
-// Device address of the scratch array on the current device, set up once per
-// device: the symbol's address is looked up and its counters cleared.
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current).  The array needs no clearing here:
+// each call clears the counters it uses on its own stream.
 int scratch_for_current_device(NoAllocScratch** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -141,12 +143,7 @@ int scratch_for_current_device(NoAllocScratch** out) {
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess)
             return lbfsi::set_error(LBFSI_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        NoAllocScratch* sp = static_cast<NoAllocScratch*>(p);
-        e = cudaMemset(sp->counter, 0, sizeof(sp->counter));
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (e != cudaSuccess)
-            return lbfsi::set_error(LBFSI_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = sp;
+        g_scratch_ptr[dev] = static_cast<NoAllocScratch*>(p);
     }
     *out = g_scratch_ptr[dev];
     return LBFSI_OK;
@@ -175,6 +172,12 @@ extern "C" int lbfsi_wall_loads_noalloc(int nr, int ntheta, int nbatch, int prec
     int rc = scratch_for_current_device(&sc);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the completion counters of this call's solves start at zero (the last
+    // CTA of a solve also leaves its counter at zero; clearing them here, in
+    // stream order, keeps a call independent of whatever the array held)
+    cudaError_t err = cudaMemsetAsync(sc->counter, 0, sizeof(unsigned) * (size_t)nbatch, s);
+    if (err != cudaSuccess)
+        return lbfsi::set_error(LBFSI_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(err));
     const dim3 grid(ntj, nbatch);
     const double Cv = 1.0 / (gamma - 1.0);
     if (precision == LBFSI_FP64)
@@ -183,7 +186,7 @@ extern "C" int lbfsi_wall_loads_noalloc(int nr, int ntheta, int nbatch, int prec
     else
         k_wall_loads_noalloc<float><<<grid, NA_TJ, 0, s>>>(nr, ntheta, r, e, xc, yc, (const float*)f,
                                                           (const float*)g, body_ref, mu, dt, Cv, loads, sc);
-    const cudaError_t err = cudaGetLastError();
+    err = cudaGetLastError();
     if (err != cudaSuccess)
         return lbfsi::set_error(LBFSI_ECUDA, std::string("wall loads launch: ") + cudaGetErrorString(err));
     return LBFSI_OK;

@@ -270,14 +270,18 @@ template <typename R, int TI, int TJ>
 __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int j, int i0, int j0,
                                            int nr, int pi0, int sj0, int PWS, R dx, R dy, int& base,
                                            R& xi, R& eta, bool below = false, bool wrap_rows = false,
-                                           unsigned* st = nullptr) {
+                                           unsigned* st = nullptr, int cbmax = -1) {
     // below: the node has cells below row 0 (the mirrored cells across a
     // C-grid's cut, or the wrapped rows of a periodic box); otherwise a row-0
-    // node only has the cells of row 0.  wrap_rows: no last window to clamp to
+    // node only has the cells of row 0.  wrap_rows: no last window to clamp to.
+    // cbmax >= 0: only the cell columns 0..cbmax exist (a C-grid's outlet
+    // columns, whose points on the column line may round to either side)
     const R di = jn[0] * dx + jn[2] * dy, dj = jn[1] * dx + jn[3] * dy;
     const bool down = i > 0 || below;
+    auto cb_ok = [&](int d) { return cbmax < 0 || (unsigned)(j + d) <= (unsigned)cbmax; };
     int da = (!(di < R(0)) || !down) ? 0 : -1;
     int db = !(dj < R(0)) ? 0 : -1;
+    if (!cb_ok(db)) db = -1 - db;
     // an element is taken when the point lies in it up to round-off (tin);
     // failing that, the first candidate within the CFL margin (lim), as for
     // a wall departure that grazes the body
@@ -327,8 +331,8 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
         bool next = false;
         if (x > tin && da == -1) { da = 0; next = true; }
         else if (x < -tin && da == 0 && down) { da = -1; next = true; }
-        if (e > tin && db == -1) { db = 0; next = true; }
-        else if (e < -tin && db == 0) { db = -1; next = true; }
+        if (e > tin && db == -1 && cb_ok(0)) { db = 0; next = true; }
+        else if (e < -tin && db == 0 && cb_ok(-1)) { db = -1; next = true; }
         if (!next) break;
     }
     base = b_base;
@@ -462,12 +466,20 @@ __device__ __forceinline__ R2 gather9_last(const R2* p, int rowstride, const R* 
 // the kernel.
 template <typename R, typename R2>
 __device__ __noinline__ R2 gather9_mirror(const R2* p, int rowstride, R lx0, R lx1, R lx2, R ly0, R ly1, R ly2,
-                                          const R2* p0, const int* ctab, int wb, int nt) {
+                                          const R2* p0, const int* ctab, int wb, int nt, R2 ref) {
+    // ref: the pair the staged tile is a deviation from (zero on the float64
+    // path); the values read from global memory are full populations
     R2 e[3];
 #pragma unroll
     for (int b2 = 0; b2 < 3; ++b2) {
         const int c = wb + b2, ct = ctab[c];
-        e[b2] = ((ct & CT_WALL) && !(ct & CT_JUNC)) ? p0[nt - 1 - c] : p[2 * rowstride + b2];
+        if ((ct & CT_WALL) && !(ct & CT_JUNC)) {
+            e[b2] = p0[nt - 1 - c];
+            e[b2].x -= ref.x;
+            e[b2].y -= ref.y;
+        } else {
+            e[b2] = p[2 * rowstride + b2];
+        }
     }
     const R Lx[3] = {lx0, lx1, lx2}, Ly[3] = {ly0, ly1, ly2};
     return gather9_last(p, rowstride, Lx, Ly, e[0], e[1], e[2]);
@@ -758,6 +770,31 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     const R dt = pick<R>(SD(dt), SD(dt_f)), mu = pick<R>(SD(mu), SD(mu_f)), Cv = pick<R>(SD(Cv), SD(Cv_f));
     const R Pr = pick<R>(SD(Pr), SD(Pr_f)), iPr = pick<R>(1.0 / SD(Pr), SD(iPr_f));
     const R xm = pick<R>(MD(xm), MD(xm_f)), ym = pick<R>(MD(ym), MD(ym_f));
+    // float path: shared memory holds the post-collision pairs as deviations
+    // from the free-stream pair of their direction, so that the Q2 weights
+    // (which sum to 1 only up to round-off, the same way at every step of a
+    // node that does not move) act on the deviation; an interpolated pair
+    // gets the reference back.  The float64 path keeps full values.
+    constexpr bool DEV = sizeof(R) == 4;
+    auto ref_of = [&](int q) -> R2 {
+        R2 r;
+        if constexpr (DEV) {
+            r.x = SD(fgref)[2 * q];
+            r.y = SD(fgref)[2 * q + 1];
+        } else {
+            r.x = R(0);
+            r.y = R(0);
+        }
+        return r;
+    };
+    auto add_ref = [&](int q, R2 v) -> R2 {
+        if constexpr (DEV) {
+            const R2 r = ref_of(q);
+            v.x += r.x;
+            v.y += r.y;
+        }
+        return v;
+    };
     const bool collide = mode != MODE_STREAM_ONLY;
     const bool stream = mode != MODE_COLLIDE_ONLY;
     // static tile: no node of the tile's +-4 region lies in the blended
@@ -901,9 +938,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
+                const R2 r = ref_of(q);
                 R2 v;
-                v.x = f[q];
-                v.y = g[q];
+                v.x = f[q] - r.x;
+                v.y = g[q] - r.y;
                 sp[q * T::PSS + sn] = v;
             }
         }
@@ -926,7 +964,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                                      in_bounds(n2 >= rlo * nt && n2 < nr * nt, a.status);
 #pragma unroll
                     for (int q = 0; q < 9; ++q) {
-                        const R2 v = sp[q * T::PSS + sn];
+                        const R2 v = add_ref(q, sp[q * T::PSS + sn]);
                         p_out[(ptrdiff_t)q * N + n] = v;
                         if (two) p_out[(ptrdiff_t)q * N + n2] = v;
                     }
@@ -940,6 +978,18 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     if (!collide) {
         cp_async_wait_all();   // the populations
         __syncthreads();
+        if constexpr (DEV) {
+            // the staged pairs are full values here (nothing collided them):
+            // make them deviations like the collided ones
+            for (int idx = tid; idx < 9 * T::PSS; idx += NT) {
+                const R2 r = ref_of(idx / T::PSS);
+                R2 v = sp[idx];
+                v.x -= r.x;
+                v.y -= r.y;
+                sp[idx] = v;
+            }
+            __syncthreads();
+        }
     }
     double fcx = 0.0, fcy = 0.0, fcm = 0.0;   // this thread's wall share (node row 0)
     int fbid = 0;                              // the body of that wall node
@@ -966,19 +1016,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const bool farj = cg && i < nr - 1 && (j == 0 || j == nt - 1);
         if ((!pb && i == nr - 1) || farj) {
             if (GEN && a.record) continue;
-            // far field (Sec. III A 2): inlet where the free stream enters,
-            // zero-gradient outlet elsewhere (targets of the previous step);
-            // on a C-grid also the outlet columns, inner neighbour along j
-            double un;
-            int mm;
-            if (farj) {
-                const double* fd = MD(fardirj) + 4 * i + (j == 0 ? 0 : 2);
-                un = SD(uinf_x) * fd[0] + SD(uinf_y) * fd[1];
-                mm = m + (j == 0 ? 1 : -1);
-            } else {
-                un = SD(uinf_x) * MD(fardir)[2 * j] + SD(uinf_y) * MD(fardir)[2 * j + 1];
-                mm = m - T::MW;
-            }
+            // far field (Sec. III A 2): inlet where the free stream enters;
+            // elsewhere an outlet whose targets are built like the wall's:
+            // zero normal gradient of rho, u and T through the point
+            // B = A - dt n_out one step inside along the outward unit
+            // direction, by Q2 interpolation of M^k (the previous step's
+            // field).  On a C-grid also the outlet columns (direction along j)
+            const double* fd = farj ? MD(fardirj) + 4 * i + (j == 0 ? 0 : 2) : MD(fardir) + 2 * j;
+            const double un = SD(uinf_x) * fd[0] + SD(uinf_y) * fd[1];
             R rho, ux, uy, Tt;
             if (un < 0.0) {
                 rho = pick<R>(SD(rho_inf), SD(rho_inf_f));
@@ -986,7 +1031,48 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 uy = pick<R>(SD(uinf_y), SD(uinf_y_f));
                 Tt = pick<R>(SD(T_inf), SD(T_inf_f));
             } else {
-                rho = sM[mm]; ux = sM[T::MS + mm]; uy = sM[2 * T::MS + mm]; Tt = sM[3 * T::MS + mm];
+                const R bx = -dt * (R)fd[0], by = -dt * (R)fd[1];
+                int base;
+                R xi, eta;
+                bool ok;
+                if constexpr (GEN) {
+                    const int dn = (ti + T::HD) * T::DW + tj + T::HD;
+                    ok = depart_gen<R, TI, TJ>(sC, sJ + 4 * dn, i, j, i0, j0, nr, pi0, sj0, T::PWS, bx, by, base, xi,
+                                               eta, dup2 || pb, pb, a.status, cg ? nt - 2 : -1);
+                } else {
+                    NodeGeo<R> fg;
+                    node_geo(i, j, nr, row, col, pi0, sj0, T::PWS, fg);
+                    ok = depart(fg, i, bx, by, base, xi, eta);
+                }
+                const int wa = base / T::PWS + pi0, wb = base - (base / T::PWS) * T::PWS + sj0;
+                const int w0 = (wa - mi0) * T::MW + (wb - mj0);
+                ok = ok && in_bounds(w0 >= 0 && w0 + 2 * T::MW + 2 < T::MS, a.status);
+                rho = sM[m]; ux = sM[T::MS + m]; uy = sM[2 * T::MS + m]; Tt = sM[3 * T::MS + m];
+                if (ok) {
+                    // interpolated as the node's own value plus the weighted
+                    // differences from it: B lies a fraction of a cell from
+                    // the node, and the weights' round-off (their sum is 1 to
+                    // an ulp, the same at every step) then acts on the small
+                    // differences, not on the values
+                    R Lx[3], Ly[3];
+                    lagrange3(xi, Lx);
+                    lagrange3(eta, Ly);
+                    R drho = R(0), dux = R(0), duy = R(0), dT = R(0);
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) {
+                            const R wgt = Lx[aa] * Ly[bb];
+                            const int o = w0 + aa * T::MW + bb;
+                            drho += wgt * (sM[o] - rho);
+                            dux += wgt * (sM[T::MS + o] - ux);
+                            duy += wgt * (sM[2 * T::MS + o] - uy);
+                            dT += wgt * (sM[3 * T::MS + o] - Tt);
+                        }
+                    rho += drho; ux += dux; uy += duy; Tt += dT;
+                } else {
+                    atomicOr(a.status, ST_BPOINT);
+                }
             }
             R f[9], g[9];
             f_equilibrium(rho, ux, uy, Tt, f);
@@ -1099,14 +1185,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R2 v;
                 if (nib & 16u) {
                     lost = true;
-                    v = sp[q * T::PSS + own];
+                    v = add_ref(q, sp[q * T::PSS + own]);
                 } else {
                     const int base = own + ((int)(nib >> 2) - 3) * T::PWS + ((int)(nib & 3u) - 3);
                     const R2 xe = sDep[q * (TI * TJ) + ti * TJ + tj];
                     R Lx[3], Ly[3];
                     lagrange3(xe.x, Lx);
                     lagrange3(xe.y, Ly);
-                    v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
+                    v = add_ref(q, gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly));
                 }
                 f[q] = v.x;
                 g[q] = v.y;
@@ -1115,7 +1201,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             // a node the blend does not move: c_hat = c, and the rest
             // population's departure point is the node itself
             {
-                const R2 v = sp[own];
+                const R2 v = add_ref(0, sp[own]);
                 f[0] = v.x;
                 g[0] = v.y;
             }
@@ -1133,6 +1219,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                     lost = true;
                     v = sp[q * T::PSS + own];
                 }
+                v = add_ref(q, v);
                 f[q] = v.x;
                 g[q] = v.y;
             };
@@ -1164,14 +1251,16 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 R2 v;
                 if (GEN && rear && base / T::PWS == rbase_row)
                     v = gather9_mirror<R, R2>(sp + q * T::PSS + base, T::PWS, Lx[0], Lx[1], Lx[2], Ly[0], Ly[1], Ly[2],
-                                              p_in + (size_t)q * N, ctab, base - rbase_row * T::PWS + sj0, nt);
+                                              p_in + (size_t)q * N, ctab, base - rbase_row * T::PWS + sj0, nt,
+                                              ref_of(q));
                 else
                     v = gather9(sp + q * T::PSS + base, T::PWS, Lx, Ly);
+                v = add_ref(q, v);
                 f[q] = v.x;
                 g[q] = v.y;
             } else {
                 lost = true;
-                const R2 v = sp[q * T::PSS + own];
+                const R2 v = add_ref(q, sp[q * T::PSS + own]);
                 f[q] = v.x;
                 g[q] = v.y;
             }
@@ -1201,6 +1290,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                         if ((c2 & CT_WALL) && !(c2 & CT_JUNC)) mw |= 1u << b2;
                     }
                 const bool wok = in_bounds(w0 >= 0 && w0 + 2 * T::MW + 2 < T::MS, a.status);
+                // the wall node's own value plus the weighted differences from
+                // it (as for the outlet targets: the weights' round-off then
+                // acts on small differences)
+                const R rhoA = sM[m], TA = sM[3 * T::MS + m];
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
@@ -1209,9 +1302,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                         const R wgt = Lx[aa] * Ly[bb];
                         const bool far = aa == 2 && ((mw >> bb) & 1u);
                         const int c2 = nt - 1 - wb - bb;
-                        rhoB += wgt * (far ? M_in[c2] : sM[w0 + aa * T::MW + bb]);
-                        TB += wgt * (far ? M_in[(size_t)3 * N + c2] : sM[3 * T::MS + w0 + aa * T::MW + bb]);
+                        rhoB += wgt * ((far ? M_in[c2] : sM[w0 + aa * T::MW + bb]) - rhoA);
+                        TB += wgt * ((far ? M_in[(size_t)3 * N + c2] : sM[3 * T::MS + w0 + aa * T::MW + bb]) - TA);
                     }
+                rhoB += rhoA;
+                TB += TA;
             } else {
                 atomicOr(a.status, ST_BPOINT);
             }
@@ -1268,18 +1363,25 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         }
         if (wall) {
             // wall stress sigma = -p I - (1 - omega/2) P^(1), P^(1) = sum (f - f^eq) c c
-            // (Sec. III), this node's Simpson share of its edges, float64
-            R feq[9];
-            f_equilibrium(mc.rho, mc.ux, mc.uy, mc.T, feq);
+            // (Sec. III), this node's Simpson share of its edges: float64 from
+            // the populations on (their moments, f^eq and f - f^eq too)
+            double fd[9], gd[9], feq[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                fd[q] = (double)f[q];
+                gd[q] = (double)g[q];
+            }
+            const Macro<double> md = moments(fd, gd, SD(Cv));
+            f_equilibrium(md.rho, md.ux, md.uy, md.T, feq);
             double pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
-                const double fn = (double)f[q] - (double)feq[q];
+                const double fn = fd[q] - feq[q];
                 pxx += cxq(q) * cxq(q) * fn;
                 pxy += cxq(q) * cyq(q) * fn;
                 pyy += cyq(q) * cyq(q) * fn;
             }
-            const double rho = mc.rho, Tn = mc.T;
+            const double rho = md.rho, Tn = md.T;
             const double om = 1.0 / (0.5 + SD(mu) / (rho * Tn * SD(dt)));
             const double p = rho * Tn, am = 1.0 - 0.5 * om;
             const double sxx = -p - am * pxx, sxy = -am * pxy, syy = -p - am * pyy;
