@@ -87,11 +87,11 @@ def _outlet_values(mesh, M_prev, A, n_hat, i, j, dt):
     B = A - dt n_hat, one time step inside the far field along its outward
     unit direction, by Q2 interpolation in the cells of node (i, j) (reading
     R20: the wall's zero-gradient construction of Sec. III A applied to the
-    outlet, for rho, T and u)."""
+    far field)."""
     B = A - dt * n_hat
     wa, wb, xi, eta, found = mesh.locate(B, i, j)
     if not np.all(found):
-        raise RuntimeError("outlet point B outside the cells next to the far field")
+        raise RuntimeError("far-field point B outside the cells next to the far field")
     return [mesh.interpolate(M_prev[c], wa, wb, xi, eta) for c in range(4)]
 
 
@@ -99,24 +99,30 @@ def _unit(v):
     return v / np.hypot(v[..., 0], v[..., 1])[..., None]
 
 
-def far_field_targets(mesh, M_prev, u_inf, rho_inf, T_inf, dt):
+def far_field_targets(mesh, M_prev, u_inf, T_inf, dt):
     """Inlet / outlet targets at the far-field row (Sec. III A 2).  Reading
     R20: a far-field node is an inlet where the free stream enters
     (U_inf . n_out < 0, n_out the outward direction of the grid line that
-    ends there, X[last] - X[last-1]), else an outlet.  Inlet targets are the
-    free stream.  Outlet targets are built the way the wall's are (Sec. III A
-    2 refers the outlet to the wall's construction): zero normal gradient of
-    rho, u and T imposed
-    through the point B one time step inside the boundary along the outward
-    unit direction, B = A - dt n_out, whose values are the Q2 interpolation
-    of the previous step's moment field (as for the wall targets, reading
-    R19)."""
+    ends there, X[last] - X[last-1]), else an outlet.  Targets are built the
+    way the wall's are (Sec. III A 2 refers the outlet to the wall's
+    zero-gradient construction): a quantity the boundary does not prescribe
+    takes a zero normal gradient, imposed through the point B one time step
+    inside the boundary along the outward unit direction, B = A - dt n_out,
+    whose value is the Q2 interpolation of the previous step's moment field
+    (as for the wall targets, reading R19).  The outlet prescribes nothing:
+    rho, u and T all take the value at B.  The inlet prescribes the free
+    stream's velocity and temperature (the paper does not list the inlet's
+    target values); its density takes the value at B, which leaves the one
+    outgoing acoustic wave of a subsonic inflow free (imposing rho as well
+    over-specifies the inflow: with it the gas in the domain is compressed
+    until the run turns non-physical after about a hundred convective
+    times)."""
     last = mesh.Ni - 1
     Nj = mesh.Nj
     n_out = _unit(mesh.X[last] - mesh.X[last - 1])
     inlet = (u_inf[0] * n_out[:, 0] + u_inf[1] * n_out[:, 1]) < 0.0
     ob = _outlet_values(mesh, M_prev, mesh.X[last], n_out, np.full(Nj, last), np.arange(Nj), dt)
-    rho = np.where(inlet, rho_inf, ob[0])
+    rho = ob[0]
     ux = np.where(inlet, u_inf[0], ob[1])
     uy = np.where(inlet, u_inf[1], ob[2])
     T = np.where(inlet, T_inf, ob[3])
@@ -167,11 +173,13 @@ def far_field_mask_cgrid(mesh):
     return far
 
 
-def far_field_targets_cgrid(mesh, M_prev, u_inf, rho_inf, T_inf, dt):
+def far_field_targets_cgrid(mesh, M_prev, u_inf, T_inf, dt):
     """Inlet / outlet targets on the far field of a C-grid (reading R20 on
     each boundary): on the last row the outward direction is that of the
     grid line along i, on the outlet columns (rows below the last) along j;
-    outlet values at B = A - dt n_out as on an O-grid.  Returns rho, ux, uy,
+    the values at B = A - dt n_out as on an O-grid (the inlet prescribes the
+    free stream's u and T, its density and every outlet quantity take the
+    value at B).  Returns rho, ux, uy,
     T on the whole [Ni, Nj] grid (meaningful on the far-field mask only) and
     the inlet mask."""
     Ni, Nj = mesh.Ni, mesh.Nj
@@ -186,8 +194,8 @@ def far_field_targets_cgrid(mesh, M_prev, u_inf, rho_inf, T_inf, dt):
     ii, jj = np.nonzero(far)
     ob = _outlet_values(mesh, M_prev, X[ii, jj], n_out[ii, jj], ii, jj, dt)
     out = []
-    for c, free in enumerate((rho_inf, u_inf[0], u_inf[1], T_inf)):
+    for c, free in enumerate((None, u_inf[0], u_inf[1], T_inf)):
         v = np.zeros((Ni, Nj))
         v[ii, jj] = ob[c]
-        out.append(np.where(inlet, free, v))
+        out.append(v if free is None else np.where(inlet, free, v))
     return out[0], out[1], out[2], out[3], inlet & far

@@ -170,7 +170,7 @@ class Solver:
         M[0, :nrows], M[1, :nrows], M[2, :nrows], M[3, :nrows] = rho, ux, uy, T
         if self.walls:
             tr, tux, tuy, tT, _ = boundary.far_field_targets(mesh, self.M_prev, self.u_inf,
-                                                             self.rho_inf, self.T_inf, dt)
+                                                             self.T_inf, dt)
             M[0, last], M[1, last], M[2, last], M[3, last] = tr, tux, tuy, tT
         # 5. correction fields
         dqx, dqy = K.delta_q(M[0], M[1], M[2], M[3])
@@ -294,7 +294,7 @@ class Solver:
             rho, ux, uy, E, T = K.moments(f_pre, g_pre, Cv)
         M = np.stack([rho, ux, uy, T])
         tr, tux, tuy, tT, _ = boundary.far_field_targets_cgrid(mesh, self.M_prev, self.u_inf,
-                                                               self.rho_inf, self.T_inf, dt)
+                                                               self.T_inf, dt)
         for c, t in enumerate((tr, tux, tuy, tT)):
             M[c] = np.where(far, t, M[c])
         f_pre[:, 0, dup] = f_pre[:, 0, own]

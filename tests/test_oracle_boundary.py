@@ -11,9 +11,10 @@ fails it:
   interpolated are all fixed; a coupled step takes them from the previous
   step's moment field;
 - far field (reading R20): the inlet set against the outward direction of
-  the boundary computed from the mesh generator's closed form; the outlet
-  targets against the linear field at B = A - dt n_out (not the inner
-  neighbour), on an O-grid and on a C-grid (last row and outlet columns).
+  the boundary computed from the mesh generator's closed form; the targets
+  against the linear field at B = A - dt n_out (not the inner neighbour),
+  the inlet's velocity and temperature against the free stream, on an
+  O-grid and on a C-grid (last row and outlet columns).
 """
 import math
 
@@ -165,14 +166,16 @@ def test_wall_targets_of_a_step_come_from_the_previous_field():
 @pytest.mark.parametrize("beta", [0.0, 0.7, math.pi])
 def test_far_field_targets_on_an_ogrid(beta):
     """Inlet exactly where the free stream enters through the far-field
-    circle, U . (cos theta, sin theta) < 0; inlet targets the free stream;
-    outlet targets the linear field at A - dt (cos theta, sin theta)."""
+    circle, U . (cos theta, sin theta) < 0.  At B = A - dt (cos theta,
+    sin theta): the inlet's density and every outlet quantity equal the
+    linear field there; the inlet's velocity and temperature are the free
+    stream's."""
     case, mesh, theta = _circle_case()
     dt = case.flow.dt
     U = 0.08
     u_inf = (U * math.cos(beta), U * math.sin(beta))
     M_prev = _linear_moments(mesh.X)
-    rho, ux, uy, T, inlet = BC.far_field_targets(mesh, M_prev, u_inf, 1.0, 1.0 / 3.0, dt)
+    rho, ux, uy, T, inlet = BC.far_field_targets(mesh, M_prev, u_inf, 1.0 / 3.0, dt)
     un = np.cos(theta - beta)
     sure = np.abs(un) > 1e-9
     np.testing.assert_array_equal(inlet[sure], (un < 0)[sure])
@@ -180,17 +183,19 @@ def test_far_field_targets_on_an_ogrid(beta):
     n = np.stack([np.cos(theta), np.sin(theta)], axis=1)
     B = mesh.X[-1] - dt * n
     for comp, v in enumerate((rho, ux, uy, T)):
-        free = (1.0, u_inf[0], u_inf[1], 1.0 / 3.0)[comp]
-        np.testing.assert_array_equal(v[inlet], free)
-        np.testing.assert_allclose(v[~inlet], _linear(LIN[comp], B[~inlet]), rtol=0, atol=1e-13)
+        free = (None, u_inf[0], u_inf[1], 1.0 / 3.0)[comp]
+        at_b = ~inlet if free is not None else np.ones_like(inlet)
+        if free is not None:
+            np.testing.assert_array_equal(v[inlet], free)
+        np.testing.assert_allclose(v[at_b], _linear(LIN[comp], B[at_b]), rtol=0, atol=1e-13)
 
 
 @pytest.mark.parametrize("beta", [0.0, math.pi])
 def test_far_field_targets_on_a_cgrid(beta):
     """C-grid from straight grid lines W_j -> C_j (the generator's closed
     form): the last row's outward direction is C_j - W_j, the outlet
-    columns' is +x.  Inlet sets and outlet targets as on an O-grid, on the
-    last row and on both outlet columns (row 0 included)."""
+    columns' is +x.  Inlet sets and targets as on an O-grid, on the last
+    row and on both outlet columns (row 0 included)."""
     n_wall, n_cut, nr = 33, 8, 12
     X = inputs.cgrid_ellipse(n_wall, n_cut, nr, 0.6, 0.3, r_far=6.0)
     mesh = OM.CGridMesh(X, n_cut)
@@ -199,7 +204,7 @@ def test_far_field_targets_on_a_cgrid(beta):
     U = 0.08
     u_inf = (U * math.cos(beta), U * math.sin(beta))
     M_prev = _linear_moments(X)
-    rho, ux, uy, T, inlet = BC.far_field_targets_cgrid(mesh, M_prev, u_inf, 1.0, 1.0 / 3.0, dt)
+    rho, ux, uy, T, inlet = BC.far_field_targets_cgrid(mesh, M_prev, u_inf, 1.0 / 3.0, dt)
     far = BC.far_field_mask_cgrid(mesh)
     n = np.zeros((Ni, Nj, 2))
     n[:, 0] = (1.0, 0.0)
@@ -212,9 +217,11 @@ def test_far_field_targets_on_a_cgrid(beta):
     outlet = far & ~inlet
     B = X - dt * n
     for comp, v in enumerate((rho, ux, uy, T)):
-        free = (1.0, u_inf[0], u_inf[1], 1.0 / 3.0)[comp]
-        np.testing.assert_array_equal(v[far & inlet], free)
-        np.testing.assert_allclose(v[outlet], _linear(LIN[comp], B[outlet]), rtol=0, atol=1e-13)
+        free = (None, u_inf[0], u_inf[1], 1.0 / 3.0)[comp]
+        at_b = outlet if free is not None else far
+        if free is not None:
+            np.testing.assert_array_equal(v[far & inlet], free)
+        np.testing.assert_allclose(v[at_b], _linear(LIN[comp], B[at_b]), rtol=0, atol=1e-13)
     # the outlet columns are outlets for a stream along +x, inlets against it
     assert (not inlet[: Ni - 1, 0].any()) if beta == 0.0 else inlet[: Ni - 1, 0].all()
 
@@ -228,7 +235,7 @@ def test_outlet_targets_inside_a_step_use_the_previous_field():
     s = OS.Solver.from_case(mesh, case, M0)
     r1 = s.step()
     r2 = s.step()
-    t = BC.far_field_targets(mesh, r1.M, s.u_inf, s.rho_inf, s.T_inf, case.flow.dt)
+    t = BC.far_field_targets(mesh, r1.M, s.u_inf, s.T_inf, case.flow.dt)
     for c in range(4):
         np.testing.assert_array_equal(r2.M[c, -1], t[c])
     np.testing.assert_allclose(r2.f_post[:, -1], K.f_eq(t[0], t[1], t[2], t[3]), rtol=1e-15)
