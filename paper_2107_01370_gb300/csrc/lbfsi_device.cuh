@@ -109,60 +109,91 @@ __host__ __device__ __forceinline__ void g_equilibrium(R rho, R ux, R uy, R T, R
     g_hermite(rho, ux, uy, T, E, H2 * ux, H2 * uy, g);
 }
 
-// Collision at one node (Eq. f_boltz): f* = f + w (f^eq - f) + dt phi,
-// g* = g + w (g^eq - g) + (w1 - w)(g^qe - g).  phi_i = -(1/2) c_i . Y on the
-// axis velocities; q* = q^eq + 2 u.(P - P^eq); 1/w = 1/2 + mu/(rho T dt),
-// 1/w1 = 1/2 + (1/w - 1/2)/Pr.  g^qe differs from g^eq only in the heat flux,
-// so both are formed from one Hermite expansion.
-template <typename R>
-__device__ __forceinline__ void collide_node(R* f, R* g, R Yx, R Yy, R mu, R dt, R Cv, R iPr) {
-    const Macro<R> m = moments(f, g, Cv);
-    const R tau = R(0.5) + mu * rcp_(m.rho * m.T * dt);
+// Lane-wise arithmetic on (f_q, g_q) pairs: packed FP32x2 instructions on the
+// float path (one instruction for both populations of a direction).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pair(double a, double b) { return make_double2(a, b); }
+
+// Collision at one node (Eq. f_boltz) on its (f_q, g_q) pairs p[9]:
+// f* = f + w (f^eq - f) + dt phi, g* = g + w (g^eq - g) + (w1 - w)(g^qe - g).
+// phi_i = -(1/2) c_i . Y on the axis velocities; q* = q^eq + 2 u.(P - P^eq);
+// 1/w = 1/2 + mu/(rho T dt), 1/w1 = 1/2 + (1/w - 1/2)/Pr.  g^qe differs from
+// g^eq only in the heat flux, so both come from one Hermite expansion, whose
+// (R^eq - 2 rho E T I):(c c - T I)/(2T^2) term takes five values (rest,
+// x-axis, y-axis and the two diagonal pairs).
+template <typename R, typename R2>
+__device__ __forceinline__ void collide_pairs(R2* p, R Yx, R Yy, R mu, R dt, R Cv, R iPr) {
+    // rho = sum f, 2 rho E = sum g, rho u = sum f c, P = sum f c c
+    R2 s = p[0];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) s = padd(s, p[q]);
+    const R rho = s.x, twoRhoE = s.y;
+    const R jx = ((p[1].x - p[3].x) + (p[5].x - p[6].x)) + (p[8].x - p[7].x);
+    const R jy = ((p[2].x - p[4].x) + (p[5].x - p[8].x)) + (p[6].x - p[7].x);
+    const R sd = (p[5].x + p[6].x) + (p[7].x + p[8].x);
+    const R pxx = (p[1].x + p[3].x) + sd, pyy = (p[2].x + p[4].x) + sd;
+    const R pxy = (p[5].x - p[6].x) + (p[7].x - p[8].x);
+    const R ir = rcp_(rho);
+    const R ux = jx * ir, uy = jy * ir;
+    const R E = R(0.5) * twoRhoE * ir;
+    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const R T = (E - R(0.5) * (uxx + uyy)) * rcp_(Cv);
+    const R tau = R(0.5) + mu * rcp_(rho * T * dt);
     const R om = rcp_(tau);
     const R om1 = rcp_(R(0.5) + (tau - R(0.5)) * iPr);
-    R pxx = 0, pxy = 0, pyy = 0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        pxx += R(cxq(q) * cxq(q)) * f[q];
-        pxy += R(cxq(q) * cyq(q)) * f[q];
-        pyy += R(cyq(q) * cyq(q)) * f[q];
-    }
-    const R ux = m.ux, uy = m.uy, T = m.T, rho = m.rho, E = m.E;
-    const R uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const R dom = om1 - om;
     const R dxx = pxx - rho * (uxx + T);
     const R dxy = pxy - rho * uxy;
     const R dyy = pyy - rho * (uyy + T);
-    const R H2 = R(2) * rho * (E + T);
-    const R qex = H2 * ux, qey = H2 * uy;
-    const R dqx = R(2) * (ux * dxx + uy * dxy), dqy = R(2) * (ux * dxy + uy * dyy);  // q* - q^eq
-    const R axx = R(2) * rho * E * uxx + R(2) * rho * T * (T + R(2) * uxx);
-    const R ayy = R(2) * rho * E * uyy + R(2) * rho * T * (T + R(2) * uyy);
-    const R axy = R(2) * rho * E * uxy + R(4) * rho * T * uxy;
     const R invT = rcp_(T);
+    // heat flux of g^eq (2 rho H u) and the quasi-equilibrium shift
+    // q* - q^eq = 2 u.(P - P^eq), both over T
+    const R H2 = R(2) * rho * (E + T) * invT;
+    const R qx = H2 * ux, qy = H2 * uy;
+    const R dqx = R(2) * (ux * dxx + uy * dxy) * invT, dqy = R(2) * (ux * dxy + uy * dyy) * invT;
+    const R rT2 = R(2) * rho * T;
+    const R axx = twoRhoE * uxx + rT2 * (T + R(2) * uxx);
+    const R ayy = twoRhoE * uyy + rT2 * (T + R(2) * uyy);
+    const R axy = twoRhoE * uxy + R(2) * rT2 * uxy;
     const R inv2T2 = R(0.5) * invT * invT;
+    const R A = axx + ayy, TA = T * A;
+    const R h0 = -TA * inv2T2, hx = (axx - TA) * inv2T2, hy = (ayy - TA) * inv2T2;
+    const R hd = (A - TA) * inv2T2, hxy = R(2) * axy * inv2T2;
     const R pre = rho * (R(1) - R(3) * T) * invT;
     const R Xx = pre * (T * T + R(2) * uxx * T + E * uxx);
     const R Xy = pre * (T * T + R(2) * uyy * T + E * uyy);
     const R ax = uxx + T, ay = uyy + T;
     const R px[3] = {R(0.5) * (ax - ux), R(1) - ax, R(0.5) * (ax + ux)};
     const R py[3] = {R(0.5) * (ay - uy), R(1) - ay, R(0.5) * (ay + uy)};
-    const R w[3] = {R(0.5) * T, R(1) - T, R(0.5) * T};
-    const R twoRhoE = R(2) * rho * E;
-    const R dom = om1 - om;
-    R df[9], dg[9];
+    const R w0 = R(0.5) * T, w1 = R(1) - T;
+    const R Wr = w1 * w1, Wa = w0 * w1, Wd = w0 * w0;
+    const R2 om2 = pair(om, om);
+    R2 d[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int cx = cxq(q), cy = cyq(q);
         const R feq = rho * px[cx + 1] * py[cy + 1];
-        const R herm = (axx * (R(cx * cx) - T) + R(2) * axy * R(cx * cy) + ayy * (R(cy * cy) - T)) * inv2T2;
-        const R W = w[cx + 1] * w[cy + 1];
-        R geq = W * (twoRhoE + (qex * R(cx) + qey * R(cy)) * invT + herm);
+        const R herm = q == 0 ? h0 : (cy == 0 ? hx : (cx == 0 ? hy : hd + R(cx * cy) * hxy));
+        const R W = q == 0 ? Wr : (cx == 0 || cy == 0 ? Wa : Wd);
+        const R flux = (cx ? R(cx) * qx : R(0)) + (cy ? R(cy) * qy : R(0));
+        R geq = W * (twoRhoE + flux + herm);
         if (q == 0) geq += Xx + Xy;
         if (q == 1 || q == 3) geq -= R(0.5) * Xx;
         if (q == 2 || q == 4) geq -= R(0.5) * Xy;
-        const R gqe = geq + W * (dqx * R(cx) + dqy * R(cy)) * invT;
-        df[q] = om * (feq - f[q]);
-        dg[q] = om * (geq - g[q]) + dom * (gqe - g[q]);
+        const R shift = (cx ? R(cx) * dqx : R(0)) + (cy ? R(cy) * dqy : R(0));
+        const R gqe = geq + W * shift;
+        // (w (f^eq - f), w (g^eq - g) + (w1 - w)(g^qe - g))
+        d[q] = pfma(om2, psub(pair(feq, geq), p[q]), pair(R(0), dom * (gqe - p[q].y)));
     }
     if constexpr (sizeof(R) == 4) {
         // The relaxation leaves mass, momentum and energy unchanged in exact
@@ -173,29 +204,25 @@ __device__ __forceinline__ void collide_node(R* f, R* g, R Yx, R Yy, R mu, R dt,
         // exact to far below the populations' ulp: take them out of the rest
         // population (mass, energy) and of the axis pairs (momentum; their
         // sum, hence the mass, unchanged).
-        R e0 = 0, ex = 0, ey = 0, eg = 0;
+        R2 e = d[0];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            e0 += df[q];
-            ex += R(cxq(q)) * df[q];
-            ey += R(cyq(q)) * df[q];
-            eg += dg[q];
-        }
-        df[0] -= e0;
-        df[1] -= R(0.5) * ex;
-        df[3] += R(0.5) * ex;
-        df[2] -= R(0.5) * ey;
-        df[4] += R(0.5) * ey;
-        dg[0] -= eg;
+        for (int q = 1; q < 9; ++q) e = padd(e, d[q]);
+        const R ex = ((d[1].x - d[3].x) + (d[5].x - d[6].x)) + (d[8].x - d[7].x);
+        const R ey = ((d[2].x - d[4].x) + (d[5].x - d[8].x)) + (d[6].x - d[7].x);
+        d[0] = psub(d[0], e);
+        d[1].x -= R(0.5) * ex;
+        d[3].x += R(0.5) * ex;
+        d[2].x -= R(0.5) * ey;
+        d[4].x += R(0.5) * ey;
     }
+    // dt phi on the axis velocities
+    const R hyx = R(0.5) * dt * Yx, hyy = R(0.5) * dt * Yy;
+    d[1].x -= hyx;
+    d[3].x += hyx;
+    d[2].x -= hyy;
+    d[4].x += hyy;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const int cx = cxq(q), cy = cyq(q);
-        R phi = 0;
-        if (q >= 1 && q <= 4) phi = -R(0.5) * (R(cx) * Yx + R(cy) * Yy);
-        f[q] = f[q] + df[q] + dt * phi;
-        g[q] = g[q] + dg[q];
-    }
+    for (int q = 0; q < 9; ++q) p[q] = padd(p[q], d[q]);
 }
 
 // Grad's approximation at wall targets (Sec. III A, Eqs. fnoneq, gnoneq,

@@ -788,11 +788,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         return r;
     };
     auto add_ref = [&](int q, R2 v) -> R2 {
-        if constexpr (DEV) {
-            const R2 r = ref_of(q);
-            v.x += r.x;
-            v.y += r.y;
-        }
+        if constexpr (DEV) v = padd(v, ref_of(q));
         return v;
     };
     const bool collide = mode != MODE_STREAM_ONLY;
@@ -905,18 +901,17 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
             if (outside(li, lj, T::HP, 0)) continue;
             const int sn = li * T::PWS + lj + 2;   // staged node
-            R f[9], g[9];
+            R2 pq[9];
             if ((!pb && i == nr - 1) || (cg && (jj == 0 || jj == nt - 1))) {
                 const int m = (li + 2) * T::MW + (lj + 2);
+                R f[9], g[9];
                 f_equilibrium(sM[m], sM[T::MS + m], sM[2 * T::MS + m], sM[3 * T::MS + m], f);
                 g_equilibrium(sM[m], sM[T::MS + m], sM[2 * T::MS + m], sM[3 * T::MS + m], Cv, g);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) pq[q] = pair(f[q], g[q]);
             } else {
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const R2 v = sp[q * T::PSS + sn];
-                    f[q] = v.x;
-                    g[q] = v.y;
-                }
+                for (int q = 0; q < 9; ++q) pq[q] = sp[q * T::PSS + sn];
                 const int d = (li + 1) * T::DW + (lj + 1);
                 R dx_xi, dx_et, dy_xi, dy_et;
                 if constexpr (GEN) {
@@ -934,16 +929,10 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 }
                 const R Yx = sG[d] * dx_xi + sG[T::DS + d] * dx_et;
                 const R Yy = sG[2 * T::DS + d] * dy_xi + sG[3 * T::DS + d] * dy_et;
-                collide_node(f, g, Yx, Yy, mu, dt, Cv, iPr);
+                collide_pairs(pq, Yx, Yy, mu, dt, Cv, iPr);
             }
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const R2 r = ref_of(q);
-                R2 v;
-                v.x = f[q] - r.x;
-                v.y = g[q] - r.y;
-                sp[q * T::PSS + sn] = v;
-            }
+            for (int q = 0; q < 9; ++q) sp[q * T::PSS + sn] = psub(pq[q], ref_of(q));
         }
         __syncthreads();
         if (!stream) {
@@ -1016,21 +1005,18 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         const bool farj = cg && i < nr - 1 && (j == 0 || j == nt - 1);
         if ((!pb && i == nr - 1) || farj) {
             if (GEN && a.record) continue;
-            // far field (Sec. III A 2): inlet where the free stream enters;
-            // elsewhere an outlet whose targets are built like the wall's:
-            // zero normal gradient of rho, u and T through the point
-            // B = A - dt n_out one step inside along the outward unit
-            // direction, by Q2 interpolation of M^k (the previous step's
-            // field).  On a C-grid also the outlet columns (direction along j)
+            // far field (Sec. III A 2), targets built like the wall's: a
+            // quantity the boundary does not prescribe takes a zero normal
+            // gradient through the point B = A - dt n_out one step inside
+            // along the outward unit direction, by Q2 interpolation of M^k
+            // (the previous step's field).  An inlet (where the free stream
+            // enters) prescribes the free stream's u and T, its density is
+            // the value at B; an outlet prescribes nothing.  On a C-grid
+            // also the outlet columns (direction along j)
             const double* fd = farj ? MD(fardirj) + 4 * i + (j == 0 ? 0 : 2) : MD(fardir) + 2 * j;
             const double un = SD(uinf_x) * fd[0] + SD(uinf_y) * fd[1];
             R rho, ux, uy, Tt;
-            if (un < 0.0) {
-                rho = pick<R>(SD(rho_inf), SD(rho_inf_f));
-                ux = pick<R>(SD(uinf_x), SD(uinf_x_f));
-                uy = pick<R>(SD(uinf_y), SD(uinf_y_f));
-                Tt = pick<R>(SD(T_inf), SD(T_inf_f));
-            } else {
+            {
                 const R bx = -dt * (R)fd[0], by = -dt * (R)fd[1];
                 int base;
                 R xi, eta;
@@ -1072,6 +1058,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                     rho += drho; ux += dux; uy += duy; Tt += dT;
                 } else {
                     atomicOr(a.status, ST_BPOINT);
+                }
+                if (un < 0.0) {
+                    ux = pick<R>(SD(uinf_x), SD(uinf_x_f));
+                    uy = pick<R>(SD(uinf_y), SD(uinf_y_f));
+                    Tt = pick<R>(SD(T_inf), SD(T_inf_f));
                 }
             }
             R f[9], g[9];
