@@ -111,6 +111,10 @@ class Solver:
         self.cgrid = isinstance(mesh, CGridMesh)
         if walls:
             self.n0 = boundary.wall_normals_cgrid(mesh) if self.cgrid else boundary.wall_normals(mesh)
+        # the O-grid step's wall-load sum (step 7): forces.wall_force unless a
+        # caller that holds only part of the wall (a rank of a split mesh)
+        # supplies the same sum assembled from every part
+        self.load_reduction = None
 
     @classmethod
     def from_case(cls, mesh, case, M0):
@@ -198,7 +202,7 @@ class Solver:
                                                self.Pr)
             x_wall = ale.mesh_position(X[0], self.bodies, self.S)
             x_ref = np.array([b["xp"], b["yp"] + st["h"]])
-            force = forces.wall_force(x_wall, sxx, sxy, syy, x_ref)
+            force = (self.load_reduction or forces.wall_force)(x_wall, sxx, sxy, syy, x_ref)
         # 8. structural update
         new_S = []
         for b, st in zip(self.bodies, self.S):
