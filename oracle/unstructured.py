@@ -24,12 +24,27 @@ reading R18.
 
 ``AsGrid`` presents such a mesh as an [N, 1] grid to ``solver.Solver`` (no
 walls: a periodic mesh), so the step of the structured oracle runs on it
-unchanged."""
+unchanged.  ``UnstructuredSolver`` is the coupled step on an element list
+with a body: a closed wall chain and a closed far-field chain of nodes.
+
+Boundaries on an element list (reading R34, the unstructured counterpart of
+R10, R19 and R20): the wall chain and the far-field chain are node lists in
+counterclockwise order (even entries the vertices of the straight element
+edges); the wall normal n0 and the far field's outward direction n_out are
+the normals of those polygons, as on a structured mesh's wall row (on an
+O-grid whose grid lines meet the far circle radially the far polygon's
+normal is the grid-line direction of R20).  The targets' points B are
+searched in the node's holding elements like a departure point."""
 from __future__ import annotations
+
+import types
 
 import numpy as np
 
-from .mesh import XI_TOL, XI_TOL_THIN, Q2Mesh
+from . import ale, boundary, forces
+from . import kinetics as K
+from .mesh import XI_TOL, XI_TOL_THIN, DepartureError, Q2Mesh
+from .solver import Solver
 
 
 def _lagrange(t):
@@ -230,3 +245,153 @@ def from_box(mesh, perm_nodes=None, perm_elements=None):
         els = els[np.asarray(perm_elements)]
         xe = xe[np.asarray(perm_elements)]
     return UnstructuredQ2Mesh(Xl, els, xe)
+
+
+def chain_normals(P):
+    """Unit normals at the nodes of a closed chain P[n, 2] (counterclockwise
+    around what it bounds; even entries the vertices of its straight edges):
+    the wall normals of boundary.wall_normals applied to the chain, out of
+    the enclosed region for a counterclockwise chain around a body, out of
+    the domain for a counterclockwise chain around the domain."""
+    return boundary.wall_normals(types.SimpleNamespace(Nj=len(P), X=np.asarray(P)[None]))
+
+
+class UnstructuredSolver(Solver):
+    """The coupled step (Sec. III: fluid step, loads, RK4) on an element list
+    with one body: wall = closed chain of node indices around the body,
+    far = closed chain around the domain (both counterclockwise), grad = the
+    nodal gradient operator ([..., N] -> (d/dX, d/dY); reading R33 by
+    default).  The step follows the structured oracle's order (solver.py)
+    with the node sets of reading R34: far-field nodes take equilibria at
+    their targets, every other node streams, wall nodes replace their
+    missing populations by Grad's approximation."""
+
+    def __init__(self, um, wall, far, *, gamma, Pr, mu, dt, rho_inf, u_inf, T_inf, bodies, M0,
+                 grad=None):
+        super().__init__(um, gamma=gamma, Pr=Pr, mu=mu, dt=dt, rho_inf=rho_inf, u_inf=u_inf,
+                         T_inf=T_inf, bodies=bodies, M0=M0, walls=False)
+        self.um = um
+        self.wall = np.asarray(wall, dtype=np.int64)
+        self.far = np.asarray(far, dtype=np.int64)
+        self.grad = grad or um.grad_X
+        self.n0 = chain_normals(um.X[self.wall])
+        self.n_far = chain_normals(um.X[self.far])
+        self.is_far = np.zeros(um.N, dtype=bool)
+        self.is_far[self.far] = True
+
+    @classmethod
+    def from_case(cls, um, wall, far, case, M0, grad=None):
+        import math
+        from .solver import body_dict
+        fl = case.flow
+        u_inf = fl.ma * math.sqrt(fl.gamma * fl.t_inf)
+        bodies = [body_dict(b, fl.rho_inf, u_inf) for b in case.bodies]
+        mu = fl.rho_inf * u_inf * fl.length / fl.re
+        return cls(um, wall, far, gamma=fl.gamma, Pr=fl.pr, mu=mu, dt=fl.dt, rho_inf=fl.rho_inf,
+                   u_inf=(u_inf, 0.0), T_inf=fl.t_inf, bodies=bodies, M0=M0, grad=grad)
+
+    def _locate(self, P, nodes):
+        e, xi, eta, found = self.um.locate_all(P, nodes)
+        return e, xi, eta, found
+
+    def _pgrad(self, F, field):
+        dX, dY = self.grad(field)
+        return ale.physical_gradient(F, dX, dY)
+
+    def step(self):
+        um, dt, Cv = self.um, self.dt, self.Cv
+        X, N = um.X, um.N
+        wall, far = self.wall, self.far
+        inner = np.nonzero(~self.is_far)[0]
+        # 1. kinematics
+        F = ale.deformation_gradient(X, self.bodies, self.S)
+        VG = ale.mesh_velocity(X, self.bodies, self.S, self.S_prev, dt)
+        chat = ale.transformed_velocities(F, VG)
+        # 2. departure points in the holding elements and Q2 interpolation
+        f_pre = np.zeros((9, N))
+        g_pre = np.zeros((9, N))
+        missing = np.zeros((9, N), dtype=bool)
+        missing[:, wall] = boundary.missing_mask(chat[:, wall], self.n0)
+        for k in range(9):
+            e, xi, eta, found = self._locate(X[inner] - dt * chat[k, inner], inner)
+            need = ~missing[k, inner]
+            if np.any(need & ~found):
+                bad = inner[np.argmax(need & ~found)]
+                raise DepartureError(f"departure point of direction {k} at node {bad} is not in "
+                                     f"an element holding the node")
+            e = np.where(need, e, 0)
+            f_pre[k, inner] = np.where(need, um.interpolate(self.f[k], e, xi, eta), 0.0)
+            g_pre[k, inner] = np.where(need, um.interpolate(self.g[k], e, xi, eta), 0.0)
+        # 3. wall: Grad's approximation at the targets (B = A + dt n0)
+        e, xi, eta, found = self._locate(X[wall] + dt * self.n0, wall)
+        if not np.all(found):
+            raise RuntimeError("wall target point B outside the elements holding its node")
+        rho_b = um.interpolate(self.M_prev[0], e, xi, eta)
+        T_b = um.interpolate(self.M_prev[3], e, xi, eta)
+        grads = []
+        for comp in (1, 2, 3):
+            gx, gy = self._pgrad(F, self.M_prev[comp])
+            grads.append((gx[wall], gy[wall]))
+        fm, gm = boundary.grad_populations(rho_b, VG[wall, 0], VG[wall, 1], T_b, grads, Cv,
+                                           self.mu, dt, self.Pr)
+        f_pre[:, wall] = np.where(missing[:, wall], fm, f_pre[:, wall])
+        g_pre[:, wall] = np.where(missing[:, wall], gm, g_pre[:, wall])
+        # 4. moments; far-field targets at B = A - dt n_out (reading R20 on
+        # the far polygon's normal)
+        M = np.empty((4, N))
+        rho, ux, uy, E, T = K.moments(f_pre[:, inner], g_pre[:, inner], Cv)
+        M[0, inner], M[1, inner], M[2, inner], M[3, inner] = rho, ux, uy, T
+        e, xi, eta, found = self._locate(X[far] - dt * self.n_far, far)
+        if not np.all(found):
+            raise RuntimeError("far-field point B outside the elements holding its node")
+        ob = [um.interpolate(self.M_prev[c], e, xi, eta) for c in range(4)]
+        inlet = (self.u_inf[0] * self.n_far[:, 0] + self.u_inf[1] * self.n_far[:, 1]) < 0.0
+        M[0, far] = ob[0]
+        M[1, far] = np.where(inlet, self.u_inf[0], ob[1])
+        M[2, far] = np.where(inlet, self.u_inf[1], ob[2])
+        M[3, far] = np.where(inlet, self.T_inf, ob[3])
+        # 5. correction fields
+        dqx, dqy = K.delta_q(M[0], M[1], M[2], M[3])
+        mu_p = self.mu / (M[0] * M[3])
+        ddx, _ = self._pgrad(F, dqx)
+        _, ddy = self._pgrad(F, dqy)
+        Yx, _ = self._pgrad(F, mu_p * ddx)
+        _, Yy = self._pgrad(F, mu_p * ddy)
+        # 6. collision; the far field takes the equilibria at its targets
+        f_post = np.empty_like(f_pre)
+        g_post = np.empty_like(g_pre)
+        f_post[:, inner], g_post[:, inner] = K.collide(f_pre[:, inner], g_pre[:, inner], Yx[inner],
+                                                       Yy[inner], self.mu, dt, Cv, self.Pr)
+        f_post[:, far] = K.f_eq(M[0, far], M[1, far], M[2, far], M[3, far])
+        g_post[:, far] = K.g_eq(M[0, far], M[1, far], M[2, far], M[3, far], Cv)
+        # 7. load on the body from the wall chain
+        force = (0.0, 0.0, 0.0)
+        if self.bodies:
+            b, st = self.bodies[0], self.S[0]
+            sxx, sxy, syy = forces.node_stress(f_pre[:, wall], g_pre[:, wall], Cv, self.mu, dt,
+                                               self.Pr)
+            x_wall = ale.mesh_position(X[wall], self.bodies, self.S)
+            x_ref = np.array([b["xp"], b["yp"] + st["h"]])
+            force = (self.load_reduction or forces.wall_force)(x_wall, sxx, sxy, syy, x_ref)
+        # 8. structural update
+        new_S = self._advance_bodies([force] * len(self.bodies))
+        self.S_prev = [dict(s) for s in self.S]
+        self.S = new_S
+        self.f, self.g = f_post, g_post
+        self.M_prev = M
+        self.n += 1
+        from .solver import StepResult
+        return StepResult(f_pre, g_pre, f_post, g_post, M, force, missing)
+
+
+def ogrid_chains(Ni, Nj, perm_nodes=None):
+    """Wall chain (row 0) and far-field chain (row Ni - 1) of a structured
+    O-grid numbered i Nj + j (relabelled by perm_nodes): both in increasing
+    j, i.e. counterclockwise for a grid whose angular index runs
+    counterclockwise."""
+    wall = np.arange(Nj)
+    far = (Ni - 1) * Nj + np.arange(Nj)
+    if perm_nodes is not None:
+        perm_nodes = np.asarray(perm_nodes)
+        wall, far = perm_nodes[wall], perm_nodes[far]
+    return wall, far

@@ -208,3 +208,110 @@ def test_taylor_green_decay_on_an_unstructured_box():
             ts.append(step)
     rate = -np.polyfit(ts, np.log(np.abs(amps)), 1)[0]
     assert abs(rate / (2 * mu * k * k) - 1) < 0.02
+
+
+# ----- the coupled step on an element list with a wall and a far field --------
+def _cyl_pair(nr=13, nt=32, seed=7, body=None):
+    """A separable cylinder O-grid (odd nr, so the elements tile it), its
+    shuffled element list, chains and the R18 stencil mapped through the
+    numbering."""
+    case = inputs.cylinder_case(nr, nt, r_far=6.0, body=body)
+    sm = OM.ogrid_mesh(case.r, case.e)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(nr * nt)
+    Xl, els = OU.from_ogrid(sm.X, perm)
+    els = els[rng.permutation(els.shape[0])]
+    um = OU.UnstructuredQ2Mesh(Xl, els)
+    wall, far = OU.ogrid_chains(nr, nt, perm)
+
+    def r18(F):
+        grid = F[..., perm].reshape(F.shape[:-1] + (nr, nt))
+        gx, gy = sm.grad_X(grid)
+        ox = np.empty_like(F)
+        oy = np.empty_like(F)
+        ox[..., perm] = gx.reshape(F.shape)
+        oy[..., perm] = gy.reshape(F.shape)
+        return ox, oy
+
+    return case, sm, um, perm, wall, far, r18
+
+
+def _flat(A, perm):
+    flat = A.reshape(A.shape[:-2] + (-1,))
+    out = np.empty_like(flat)
+    out[..., perm] = flat
+    return out
+
+
+def test_chain_normals_of_a_circle_are_radial():
+    """Reading R34: the wall chain's normals point out of the body and the
+    far chain's out of the domain, both along the node's polar angle on a
+    circle (so the far polygon's normal is the O-grid's grid-line direction
+    of reading R20)."""
+    case, sm, um, perm, wall, far, _ = _cyl_pair()
+    th = 2 * np.pi * np.arange(case.ntheta) / case.ntheta
+    radial = np.stack([np.cos(th), np.sin(th)], axis=1)
+    np.testing.assert_allclose(OU.chain_normals(um.X[wall]), radial, atol=1e-14)
+    np.testing.assert_allclose(OU.chain_normals(um.X[far]), radial, atol=1e-14)
+
+
+def test_element_list_step_with_wall_and_far_field_equals_structured_step():
+    """With the structured stencil (R18) as its gradient, the coupled step on
+    the shuffled element list of a cylinder O-grid (wall chain, far-field
+    chain, a plunging 1-DOF body whose blend moves the mesh, flow from the
+    left) is the structured oracle's step: departures and boundary targets
+    searched in holding elements, wall and far-field sets of reading R34,
+    load and RK4 agree to round-off over several steps."""
+    body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=2.0, v_r=4.0)
+    case, sm, um, perm, wall, far, r18 = _cyl_pair(body=body)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=2, noise=2e-2)
+    st = {"h": 0.02, "alpha": 0.0, "hdot": 0.004, "adot": 0.0}
+    pv = {"h": 0.0199, "alpha": 0.0, "hdot": 0.004, "adot": 0.0}
+    s_s = OS.Solver.from_case(sm, case, M0)
+    s_u = OU.UnstructuredSolver.from_case(um, wall, far, case, _flat(M0, perm), grad=r18)
+    for s in (s_s, s_u):
+        s.S, s.S_prev = [dict(st)], [dict(pv)]
+    for _ in range(5):
+        a = s_s.step()
+        b = s_u.step()
+        assert max(abs(x - y) for x, y in zip(a.force, b.force)) < 1e-13
+    for x, y in ((a.f_post, b.f_post), (a.g_post, b.g_post), (a.M, b.M)):
+        assert np.abs(_flat(x, perm) - y).max() < 1e-13 * np.abs(y).max()
+    assert np.array_equal(_flat(a.missing, perm), b.missing)
+    for k in ("h", "hdot"):
+        assert abs(s_s.S[0][k] - s_u.S[0][k]) < 1e-15
+
+
+def test_element_list_rest_state_around_wall_is_fixed_point():
+    """The genuine element-list step (gradients by reading R33): gas at rest
+    around a fixed cylinder stays at its equilibrium (wall by Grad's
+    approximation at zero gradients, far field, collision)."""
+    case, sm, um, perm, wall, far, _ = _cyl_pair(nr=9, nt=16)
+    N = um.N
+    M0 = np.empty((4, N))
+    M0[0], M0[1], M0[2], M0[3] = 1.0, 0.0, 0.0, 1.0 / 3.0
+    s = OU.UnstructuredSolver(um, wall, far, gamma=1.4, Pr=0.71, mu=1e-3, dt=case.flow.dt,
+                              rho_inf=1.0, u_inf=(0.0, 0.0), T_inf=1.0 / 3.0,
+                              bodies=[OS.body_dict(case.bodies[0], 1.0, 0.1)], M0=M0)
+    from oracle import kinetics as K
+    feq = K.f_eq(1.0, 0.0, 0.0, 1.0 / 3.0)
+    for _ in range(4):
+        r = s.step()
+    np.testing.assert_allclose(r.f_post, np.broadcast_to(feq[:, None], r.f_post.shape), atol=1e-14)
+    assert r.missing[:, wall].any() and abs(r.force[0]) < 1e-13 and abs(r.force[1]) < 1e-13
+
+
+def test_element_list_step_with_its_own_gradient_stays_close_to_structured():
+    """The two gradient readings (R18 on the structured grid, R33 on the
+    element list) are different second-order stencils: on a smooth start the
+    steps differ at the level of the discretisation, not more."""
+    body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=2.0, v_r=4.0)
+    case, sm, um, perm, wall, far, _ = _cyl_pair(body=body)
+    M0 = inputs.initial_field(case.nr, case.ntheta, case.flow, seed=2)
+    s_s = OS.Solver.from_case(sm, case, M0)
+    s_u = OU.UnstructuredSolver.from_case(um, wall, far, case, _flat(M0, perm))
+    for _ in range(3):
+        a = s_s.step()
+        b = s_u.step()
+    d = np.abs(_flat(a.M, perm) - b.M).max(axis=1)
+    assert d.max() < 1e-3 and d.max() > 1e-12
