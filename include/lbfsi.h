@@ -548,6 +548,89 @@ int lbfsi_set_graph_steps(lbfsi_mesh m, int graph_steps);
 int lbfsi_autotune(lbfsi_mesh m, int steps_per_trial, int* best_variant, int* best_order,
                    float* ms_per_step);
 
+/* ---- Unstructured Q2 meshes (the paper's mesh type, Sec. II B: second-
+ * order quadrilateral finite elements over a node list; Sec. IV meshes its
+ * cases this way).  A separate handle: the step on an element list runs as
+ * four launches per step over node lists (correction field D, collision into
+ * a post-collision buffer, stream, load reduction and body update) with the
+ * Q2 gathers read from global memory, instead of the structured meshes'
+ * one-launch tiled kernel.
+ *
+ * Mesh: N nodes, elements of 3 x 3 node indices [a][b] (entry (a, b) at
+ * reference coordinates (a - 1, b - 1)), subparametric (each element's mid
+ * nodes at the bilinear positions of its corners, reading R7).  Boundaries
+ * (reading R34): a closed wall chain of node indices counterclockwise around
+ * the body and a closed far-field chain counterclockwise around the domain,
+ * each of even length with the even entries the vertices of straight element
+ * edges; the wall normal and the far field's outward direction are the
+ * normals of those polygons, and wall loads are Simpson sums over the wall
+ * chain's edges.  A node's departure point (Eq. depPnt) and its boundary
+ * target point B are searched in the elements that hold the node, in
+ * increasing element index (readings R8, R9).  Nodal gradients (Eq. ddx+fem)
+ * are the mean over a node's elements of the element derivative at the node
+ * (reading R33), or, when grid_ij is given, the structured stencil of reading
+ * R18 on that index grid (a structured mesh renumbered into elements then
+ * steps exactly as the structured mesh). */
+typedef struct lbfsi_emesh_s* lbfsi_emesh;
+
+typedef struct {
+    int nnode;                  /* N                                                   */
+    const double* X;            /* [N][2] node coordinates (undeformed), host          */
+    int nelem;
+    const int* elements;        /* [nelem][3][3] node indices, host                    */
+    int nwall;                  /* wall chain length (even, >= 4)                      */
+    const int* wall;            /* [nwall] node indices, counterclockwise around body  */
+    int nfar;                   /* far-field chain length (even, >= 4)                 */
+    const int* far;             /* [nfar] node indices, counterclockwise around domain */
+    const int* grid_ij;         /* nullable [N][2]: (i, j) of each node on a grid of
+                                   grid_nr x grid_nt, periodic in j, row 0 the wall
+                                   and row grid_nr - 1 the far field (reading R18)     */
+    int grid_nr, grid_nt;
+    int nbatch;                 /* independent solves on this mesh                     */
+    const lbfsi_body_desc* bodies;   /* [nbatch], host                                 */
+    int precision;              /* LBFSI_FP64 or LBFSI_FP32 populations                */
+} lbfsi_mesh_elements_desc;
+
+/* Validate the element list (indices in range, every node in an element,
+ * subparametric elements with positive Jacobians, chains of distinct nodes
+ * that no element repeats, bodies' walls inside their rigid zones), build the
+ * node-to-element table and the gradient operator on the host, upload.
+ * LBFSI_EINVAL on a bad mesh; host arrays are borrowed for the call. */
+int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_stream, lbfsi_emesh* out);
+int lbfsi_emesh_destroy(lbfsi_emesh m);
+
+/* As lbfsi_init_fields: rho_u_T host [nbatch][4][N] (node order of the
+ * element list) or NULL for the free stream; populations at equilibrium,
+ * bodies at rest. */
+int lbfsi_emesh_init_fields(lbfsi_emesh m, const lbfsi_flow_params* p, const double* rho_u_T);
+
+/* As lbfsi_blend_mesh: body states [nbatch] of the next step's blended map,
+ * prev [nbatch] (nullable: = state) the previous ones (V_G). */
+int lbfsi_emesh_blend_mesh(lbfsi_emesh m, const lbfsi_body_state* state, const lbfsi_body_state* prev);
+
+/* As lbfsi_step (Sec. III weak coupling), asynchronous on the handle's
+ * stream; errors (departure point outside the node's elements, B point
+ * outside, non-physical state) surface at the next synchronising call. */
+int lbfsi_emesh_step(lbfsi_emesh m, int nsteps);
+
+/* Synchronise and return the device status (LBFSI_EDEPARTURE,
+ * LBFSI_ENONPHYS or LBFSI_OK). */
+int lbfsi_emesh_synchronize(lbfsi_emesh m);
+
+/* Loads of the last step, host out [nbatch][3] (F_x, F_y, M_z); body states
+ * host out [nbatch]; moment field host out [nbatch][4][N] (rho, u_x, u_y,
+ * T); populations host out f, g [nbatch][9][N]: which 0 the post-propagation
+ * (pre-collision) state of the current step, 1 its post-collision state
+ * (collided by this call; step 0: the initial state).  Each synchronises and
+ * returns the device status. */
+int lbfsi_emesh_body_forces(lbfsi_emesh m, double* out);
+int lbfsi_emesh_get_body_state(lbfsi_emesh m, lbfsi_body_state* out);
+int lbfsi_emesh_get_fields(lbfsi_emesh m, double* rho_u_T);
+int lbfsi_emesh_get_populations(lbfsi_emesh m, int which, double* f, double* g);
+
+/* Kernel launches issued by the handle so far. */
+int64_t lbfsi_emesh_launch_count(lbfsi_emesh m);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* lbfsi_last_error(void);
 

@@ -22,7 +22,8 @@ LIB = os.path.join(PKG, "liblbfsi.so")
 # and global slot of the step checked, a violation reported as LBFSI_EBOUNDS)
 BUILD_BOUNDS = os.path.join(ROOT, "_build_bounds")
 LIB_BOUNDS = os.path.join(PKG, "liblbfsi_bounds.so")
-SOURCES = ["lbfsi_step.cu", "lbfsi_api.cu", "lbfsi_host.cu", "lbfsi_batch.cu", "lbfsi_noalloc.cu"]
+SOURCES = ["lbfsi_step.cu", "lbfsi_api.cu", "lbfsi_host.cu", "lbfsi_batch.cu", "lbfsi_noalloc.cu",
+           "lbfsi_elements.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

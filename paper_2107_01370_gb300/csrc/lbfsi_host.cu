@@ -134,6 +134,15 @@ void normalise_pairs(std::vector<double>& v) {
 
 }  // namespace
 
+void chain_geometry(const std::vector<double>& P, std::vector<double>& n0, std::vector<double>& wgeo) {
+    HostMesh t;
+    t.nt = (int)(P.size() / 2);
+    t.xw = P;
+    wall_geometry(t);
+    n0 = t.n0;
+    wgeo = t.wall_geo;
+}
+
 int build_host_mesh(int nr, int nt, const double* r, const double* e, double xc, double yc,
                     HostMesh& m) {
     if (nr < 5) return set_error(LBFSI_EINVAL, "nr must be >= 5");

@@ -81,6 +81,14 @@ int build_host_mesh_c(int nr, int nt, int nwalls, const int* walls, const double
 int build_host_mesh_box(int ni, int nj, const double* X, const double* shift_i, const double* shift_j,
                         HostMesh& out);
 
+// Normals and Simpson shares of a closed chain of points P [n][2] (even n,
+// counterclockwise around what it bounds, even entries the vertices of its
+// straight edges): n0 [n][2] the unit normals out of the bounded region (at a
+// vertex the normalised sum of its two edge normals), wgeo [n][6] the node's
+// (weight x length, n_x, n_y) share of each of its edges (one edge for a
+// midpoint, 4/6; two for a vertex, 1/6 each).
+void chain_geometry(const std::vector<double>& P, std::vector<double>& n0, std::vector<double>& wgeo);
+
 // Check the bodies of n solves ([n][m.nbody]) against a mesh: dof range,
 // blend radii, each wall inside its own body's rigid zone and outside every
 // other body's blended region, blended regions of moving bodies disjoint.

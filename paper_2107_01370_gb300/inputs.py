@@ -492,6 +492,61 @@ def box_mesh(ni: int, nj: int, lx: float, ly: float, skew: float = 0.0):
     return X, (lx, 0.0), (skew * ly, ly)
 
 
+@dataclass
+class ElementList:
+    """An O-grid renumbered into an unstructured element list: node
+    coordinates X [N, 2], elements [Ne, 3, 3] node indices (entry (a, b) at
+    reference (a - 1, b - 1)), the wall chain and the far-field chain (node
+    indices in increasing angular index, counterclockwise), each node's (i,
+    j) on the original grid, and perm (new index of old node i Nj + j)."""
+    X: np.ndarray
+    elements: np.ndarray
+    wall: np.ndarray
+    far: np.ndarray
+    grid_ij: np.ndarray
+    perm: np.ndarray
+    nr: int
+    nt: int
+
+    def to_list(self, field):
+        """[..., nr, nt] grid field -> [..., N] in the element list's numbering."""
+        flat = np.asarray(field).reshape(np.shape(field)[:-2] + (-1,))
+        out = np.empty_like(flat)
+        out[..., self.perm] = flat
+        return out
+
+    def to_grid(self, field):
+        """[..., N] -> [..., nr, nt]."""
+        f = np.asarray(field)
+        return f[..., self.perm].reshape(f.shape[:-1] + (self.nr, self.nt))
+
+
+def ogrid_element_list(X, seed: int = 0, shuffle: bool = True) -> ElementList:
+    """The Q2 elements of a structured O-grid X [nr, nt, 2] (nr odd, so the
+    3 x 3 windows at even indices tile it; nt even, periodic), nodes and
+    elements shuffled by a seeded permutation (shuffle=False keeps the grid
+    order i nt + j)."""
+    X = np.asarray(X, dtype=np.float64)
+    nr, nt = X.shape[:2]
+    if nr % 2 == 0 or nt % 2:
+        raise ValueError("an O-grid of odd nr and even nt")
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(nr * nt) if shuffle else np.arange(nr * nt)
+    old = np.arange(nr * nt).reshape(nr, nt)
+    els = np.array([[[old[wa + a, (wb + b) % nt] for b in range(3)] for a in range(3)]
+                    for wa in range(0, nr - 2, 2) for wb in range(0, nt, 2)], dtype=np.int64)
+    if shuffle:
+        els = els[rng.permutation(els.shape[0])]
+    Xl = np.empty((nr * nt, 2))
+    Xl[perm] = X.reshape(-1, 2)
+    ij = np.empty((nr * nt, 2), dtype=np.int64)
+    ii, jj = np.meshgrid(np.arange(nr), np.arange(nt), indexing="ij")
+    ij[perm, 0] = ii.reshape(-1)
+    ij[perm, 1] = jj.reshape(-1)
+    return ElementList(X=Xl, elements=perm[els], wall=perm[old[0]], far=perm[old[nr - 1]],
+                       grid_ij=ij, perm=perm, nr=nr, nt=nt)
+
+
 def fixed_cylinder_128x64(steps: int = 1000) -> CylinderCase:
     """Fixed cylinder, 128 radial x 64 angular nodes, far field at 20 D,
     Re 100, Ma 0.2 (FP64 parity workload)."""

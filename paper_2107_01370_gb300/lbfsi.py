@@ -34,7 +34,11 @@ EXPORTED = ["lbfsi_create_mesh", "lbfsi_destroy_mesh", "lbfsi_init_fields", "lbf
             "lbfsi_batch_autotune", "lbfsi_checkpoint_bytes", "lbfsi_checkpoint", "lbfsi_restore",
             "lbfsi_create_mesh_xy", "lbfsi_step_record", "lbfsi_batch_add_xy",
             "lbfsi_create_mesh_cgrid", "lbfsi_batch_add_cgrid", "lbfsi_field_ptr",
-            "lbfsi_create_mesh_box", "lbfsi_create_mesh_cgrid_walls"]
+            "lbfsi_create_mesh_box", "lbfsi_create_mesh_cgrid_walls",
+            "lbfsi_create_mesh_elements", "lbfsi_emesh_destroy", "lbfsi_emesh_init_fields",
+            "lbfsi_emesh_blend_mesh", "lbfsi_emesh_step", "lbfsi_emesh_synchronize",
+            "lbfsi_emesh_body_forces", "lbfsi_emesh_get_body_state", "lbfsi_emesh_get_fields",
+            "lbfsi_emesh_get_populations", "lbfsi_emesh_launch_count"]
 
 
 class LbfsiError(RuntimeError):
@@ -95,6 +99,16 @@ class MeshCGridWallsDesc(ctypes.Structure):
                 ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nbatch", ctypes.c_int), ("bodies", ctypes.POINTER(BodyDesc)),
                 ("nbody", ctypes.c_int), ("wall_body", ctypes.POINTER(ctypes.c_int))]
+
+
+class MeshElementsDesc(ctypes.Structure):
+    _fields_ = [("nnode", ctypes.c_int), ("X", ctypes.POINTER(ctypes.c_double)),
+                ("nelem", ctypes.c_int), ("elements", ctypes.POINTER(ctypes.c_int)),
+                ("nwall", ctypes.c_int), ("wall", ctypes.POINTER(ctypes.c_int)),
+                ("nfar", ctypes.c_int), ("far", ctypes.POINTER(ctypes.c_int)),
+                ("grid_ij", ctypes.POINTER(ctypes.c_int)), ("grid_nr", ctypes.c_int),
+                ("grid_nt", ctypes.c_int), ("nbatch", ctypes.c_int),
+                ("bodies", ctypes.POINTER(BodyDesc)), ("precision", ctypes.c_int)]
 
 
 class MeshCGridDesc(ctypes.Structure):
@@ -177,10 +191,23 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbfsi_last_error.argtypes = []
     lib.lbfsi_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("lbfsi_launch_count", "lbfsi_last_error", "lbfsi_checkpoint_bytes"):
+        if name not in ("lbfsi_launch_count", "lbfsi_last_error", "lbfsi_checkpoint_bytes",
+                        "lbfsi_emesh_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
     lib.lbfsi_field_ptr.argtypes = [P, ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]
+    lib.lbfsi_create_mesh_elements.argtypes = [ctypes.POINTER(MeshElementsDesc), P, ctypes.POINTER(P)]
+    lib.lbfsi_emesh_destroy.argtypes = [P]
+    lib.lbfsi_emesh_init_fields.argtypes = [P, ctypes.POINTER(FlowParams), dp]
+    lib.lbfsi_emesh_blend_mesh.argtypes = [P, ctypes.POINTER(BodyState), ctypes.POINTER(BodyState)]
+    lib.lbfsi_emesh_step.argtypes = [P, ctypes.c_int]
+    lib.lbfsi_emesh_synchronize.argtypes = [P]
+    lib.lbfsi_emesh_body_forces.argtypes = [P, dp]
+    lib.lbfsi_emesh_get_body_state.argtypes = [P, ctypes.POINTER(BodyState)]
+    lib.lbfsi_emesh_get_fields.argtypes = [P, dp]
+    lib.lbfsi_emesh_get_populations.argtypes = [P, ctypes.c_int, dp, dp]
+    lib.lbfsi_emesh_launch_count.argtypes = [P]
+    lib.lbfsi_emesh_launch_count.restype = ctypes.c_int64
     lib.lbfsi_checkpoint_bytes.restype = ctypes.c_size_t
     lib.lbfsi_checkpoint_bytes.argtypes = [ctypes.c_void_p]
     lib.lbfsi_checkpoint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
@@ -616,3 +643,83 @@ class Batch:
         lg = ctypes.c_size_t(0)
         _check(self._lib.lbfsi_batch_memory(self.h, ctypes.byref(fb), ctypes.byref(lg)))
         return fb.value, lg.value
+
+
+class ElementMesh:
+    """Handle of an unstructured Q2 element list (lbfsi_create_mesh_elements):
+    X [N, 2], elements [Ne, 3, 3] node indices, wall and far chains (node
+    indices, counterclockwise), bodies (one per solve); grid_ij [N, 2] with
+    grid (nr, nt) selects the structured gradient stencil (reading R18)."""
+
+    def __init__(self, X, elements, wall, far, bodies, precision=FP64, stream=None, grid_ij=None,
+                 grid=(0, 0)):
+        lib = load()
+        self._lib = lib
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.E = np.ascontiguousarray(elements, dtype=np.int32)
+        self.wall = np.ascontiguousarray(wall, dtype=np.int32)
+        self.far = np.ascontiguousarray(far, dtype=np.int32)
+        self.N = self.X.shape[0]
+        self.nbatch = len(bodies)
+        self.precision = precision
+        ip = ctypes.POINTER(ctypes.c_int)
+        self._bodies = (BodyDesc * self.nbatch)(*[body_desc(b) for b in bodies])
+        gij = None if grid_ij is None else np.ascontiguousarray(grid_ij, dtype=np.int32)
+        d = MeshElementsDesc(self.N, _dptr(self.X), self.E.shape[0], self.E.ctypes.data_as(ip),
+                             len(self.wall), self.wall.ctypes.data_as(ip), len(self.far),
+                             self.far.ctypes.data_as(ip), None if gij is None else gij.ctypes.data_as(ip),
+                             int(grid[0]), int(grid[1]), self.nbatch, self._bodies, precision)
+        h = ctypes.c_void_p()
+        _check(lib.lbfsi_create_mesh_elements(ctypes.byref(d), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lbfsi_emesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def init_fields(self, flow, rho_u_T=None):
+        fp = flow_params(flow)
+        if rho_u_T is None:
+            _check(self._lib.lbfsi_emesh_init_fields(self.h, ctypes.byref(fp), None))
+        else:
+            a = np.ascontiguousarray(rho_u_T, dtype=np.float64).reshape(self.nbatch, 4, self.N)
+            _check(self._lib.lbfsi_emesh_init_fields(self.h, ctypes.byref(fp), _dptr(a)))
+
+    def blend_mesh(self, states, prev=None):
+        s = (BodyState * self.nbatch)(*[BodyState(*x) for x in states])
+        pv = None if prev is None else (BodyState * self.nbatch)(*[BodyState(*x) for x in prev])
+        _check(self._lib.lbfsi_emesh_blend_mesh(self.h, s, pv))
+
+    def step(self, n=1):
+        _check(self._lib.lbfsi_emesh_step(self.h, int(n)))
+
+    def synchronize(self):
+        _check(self._lib.lbfsi_emesh_synchronize(self.h))
+
+    def body_forces(self):
+        out = np.empty((self.nbatch, 3))
+        _check(self._lib.lbfsi_emesh_body_forces(self.h, _dptr(out)))
+        return out
+
+    def body_state(self):
+        out = (BodyState * self.nbatch)()
+        _check(self._lib.lbfsi_emesh_get_body_state(self.h, out))
+        return [dict(h=s.h, alpha=s.alpha, hdot=s.hdot, adot=s.adot) for s in out]
+
+    def get_fields(self):
+        out = np.empty((self.nbatch, 4, self.N))
+        _check(self._lib.lbfsi_emesh_get_fields(self.h, _dptr(out)))
+        return out
+
+    def get_populations(self, which=0):
+        f = np.empty((self.nbatch, 9, self.N))
+        g = np.empty_like(f)
+        _check(self._lib.lbfsi_emesh_get_populations(self.h, int(which), _dptr(f), _dptr(g)))
+        return f, g
+
+    def launch_count(self):
+        return int(self._lib.lbfsi_emesh_launch_count(self.h))

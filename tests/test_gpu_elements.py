@@ -1,0 +1,154 @@
+"""The step on unstructured Q2 element lists (lbfsi_create_mesh_elements)
+against the oracle's element-list step (oracle/unstructured.py) on the same
+seeded inputs, through the C ABI.
+
+Meshes: cylinder O-grids (odd radial count, so the grid's 3 x 3 windows tile
+it) renumbered into shuffled element lists; a plunging 1-DOF body moves the
+mesh through the blending function; flow from the left (inlet and outlet
+far field).  Tolerances as in test_gpu_parity.py: FP64 1e-12 relative in
+fields and populations, 1e-12 p_inf D in loads; FP32 1e-5 in fields and
+1e-4 p_inf D in loads."""
+import numpy as np
+import pytest
+
+import oracle.mesh as OM
+import oracle.solver as OS
+import oracle.unstructured as OU
+from paper_2107_01370_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+P_SCALE = 1.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def lbfsi():
+    from paper_2107_01370_gb300 import build, lbfsi as L
+    build.build()
+    L.load()
+    return L
+
+
+def field_err(a, b):
+    e_rho = np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()
+    e_u = np.hypot(a[1] - b[1], a[2] - b[2]).max() / np.hypot(b[1], b[2]).max()
+    e_T = np.abs(a[3] - b[3]).max() / np.abs(b[3]).max()
+    return max(e_rho, e_u, e_T)
+
+
+STATE = {"h": 0.02, "alpha": 0.0, "hdot": 0.004, "adot": 0.0}
+PREV = {"h": 0.0199, "alpha": 0.0, "hdot": 0.004, "adot": 0.0}
+
+
+def _case(nr=25, nt=48, seed=3):
+    body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.0, m_star=2.0, v_r=4.0)
+    case = inputs.cylinder_case(nr, nt, r_far=8.0, body=body)
+    sm = OM.ogrid_mesh(case.r, case.e)
+    el = inputs.ogrid_element_list(sm.X, seed=seed)
+    M0 = inputs.initial_field(nr, nt, case.flow, seed=seed, noise=1e-2)
+    return case, sm, el, M0
+
+
+def _gpu(L, case, el, M0, precision, grid=False, nbatch=1):
+    m = L.ElementMesh(el.X, el.elements, el.wall, el.far, case.bodies * nbatch, precision=precision,
+                      grid_ij=el.grid_ij if grid else None, grid=(el.nr, el.nt))
+    m.init_fields(case.flow, np.broadcast_to(el.to_list(M0), (nbatch, 4, el.X.shape[0])))
+    to = (STATE["h"], STATE["alpha"], STATE["hdot"], STATE["adot"])
+    tp = (PREV["h"], PREV["alpha"], PREV["hdot"], PREV["adot"])
+    m.blend_mesh([to] * nbatch, [tp] * nbatch)
+    return m
+
+
+def _oracle_unstructured(case, el, M0):
+    um = OU.UnstructuredQ2Mesh(el.X, el.elements)
+    s = OU.UnstructuredSolver.from_case(um, el.wall, el.far, case, el.to_list(M0))
+    s.S, s.S_prev = [dict(STATE)], [dict(PREV)]
+    return s
+
+
+def test_fp64_element_list_matches_the_oracle(lbfsi):
+    """Reading R33 gradients on both sides: fields, pre- and post-collision
+    populations, every step's load and the body state after 8 steps."""
+    case, sm, el, M0 = _case()
+    s = _oracle_unstructured(case, el, M0)
+    m = _gpu(lbfsi, case, el, M0, lbfsi.FP64)
+    for _ in range(8):
+        r = s.step()
+        m.step(1)
+        assert np.abs(m.body_forces()[0] - np.array(r.force)).max() < 1e-12 * P_SCALE
+    assert field_err(m.get_fields()[0], r.M) < 1e-12
+    f0, g0 = m.get_populations(0)
+    inner = ~np.isin(np.arange(el.X.shape[0]), el.far)
+    assert np.abs(f0[0][:, inner] - r.f_pre[:, inner]).max() < 1e-12 * np.abs(r.f_pre).max()
+    assert np.abs(g0[0][:, inner] - r.g_pre[:, inner]).max() < 1e-12 * np.abs(r.g_pre).max()
+    f1, g1 = m.get_populations(1)
+    assert np.abs(f1[0] - r.f_post).max() < 1e-12 * np.abs(r.f_post).max()
+    assert np.abs(g1[0] - r.g_post).max() < 1e-12 * np.abs(r.g_post).max()
+    st = m.body_state()[0]
+    for k in ("h", "hdot"):
+        assert abs(st[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+    assert m.launch_count() >= 4 * 8
+    m.close()
+
+
+def test_fp64_renumbered_grid_steps_as_the_structured_mesh(lbfsi):
+    """With the grid's index map (reading R18 gradients) the shuffled element
+    list is the structured O-grid: the structured oracle and the structured
+    GPU path give the same fields, loads and body state to 1e-12."""
+    case, sm, el, M0 = _case(nr=21, nt=40, seed=5)
+    s = OS.Solver.from_case(sm, case, M0)
+    s.S, s.S_prev = [dict(STATE)], [dict(PREV)]
+    m = _gpu(lbfsi, case, el, M0, lbfsi.FP64, grid=True)
+    ms = lbfsi.Mesh(case.r, case.e, case.bodies, precision=lbfsi.FP64)
+    ms.init_fields(case.flow, M0[None])
+    ms.blend_mesh([(STATE["h"], 0.0, STATE["hdot"], 0.0)], [(PREV["h"], 0.0, PREV["hdot"], 0.0)])
+    for _ in range(6):
+        r = s.step()
+        m.step(1)
+        ms.step(1)
+        assert np.abs(m.body_forces()[0] - np.array(r.force)).max() < 1e-12 * P_SCALE
+    got = el.to_grid(m.get_fields()[0])
+    assert field_err(got, r.M) < 1e-12
+    assert field_err(got, ms.get_fields()[0]) < 1e-12
+    assert np.abs(m.body_forces()[0] - ms.body_forces()[0]).max() < 1e-12 * P_SCALE
+    m.close()
+    ms.close()
+
+
+def test_fp32_element_list_within_tolerance(lbfsi):
+    case, sm, el, M0 = _case(nr=25, nt=48, seed=7)
+    s = _oracle_unstructured(case, el, M0)
+    m = _gpu(lbfsi, case, el, M0, lbfsi.FP32)
+    for _ in range(40):
+        r = s.step()
+    m.step(40)
+    assert field_err(m.get_fields()[0], r.M) < 1e-5
+    assert np.abs(m.body_forces()[0] - np.array(r.force)).max() < 1e-4 * P_SCALE
+    m.close()
+
+
+def test_batch_of_solves_equals_each_alone(lbfsi):
+    """Two solves in one handle (one launch per kernel for both) end
+    bit-identical to the same solve alone."""
+    case, sm, el, M0 = _case(nr=17, nt=32, seed=9)
+    a = _gpu(lbfsi, case, el, M0, lbfsi.FP32, nbatch=2)
+    b = _gpu(lbfsi, case, el, M0, lbfsi.FP32, nbatch=1)
+    a.step(20)
+    b.step(20)
+    fa, fb = a.get_fields(), b.get_fields()
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[0])
+    assert np.array_equal(a.body_forces()[1], b.body_forces()[0])
+    a.close()
+    b.close()
+
+
+def test_cfl_violation_reported_on_element_list(lbfsi):
+    case, sm, el, M0 = _case(nr=13, nt=24, seed=1)
+    case.flow.dt *= 12.0
+    m = lbfsi.ElementMesh(el.X, el.elements, el.wall, el.far, case.bodies, precision=lbfsi.FP64)
+    m.init_fields(case.flow)
+    m.step(1)
+    with pytest.raises(lbfsi.LbfsiError) as ei:
+        m.synchronize()
+    assert ei.value.code == lbfsi.EDEPARTURE
+    m.close()
