@@ -417,6 +417,50 @@ def general_mesh_throughput(stream, peak, steps=200, warmup=5, batch=(8, 8, 1, 6
     return out
 
 
+def element_mesh_throughput(stream, peak, steps=100, warmup=5, batch=8):
+    """MLUPS of the step on an unstructured Q2 element list: the 1-DOF VIV
+    cylinder of the bench workload on a 513 x 256 O-grid (odd radial count,
+    so its 3 x 3 windows tile it) renumbered into a shuffled element list,
+    FP32, gradients of the element average (reading R33); four launches per
+    step, timed with CUDA events on the library's stream.  HBM fraction
+    against the algorithmic 144 B per node update."""
+    import torch
+    from paper_2107_01370_gb300 import lbfsi
+    body = inputs.BodySpec(dof=1, r_in=0.75, r_out=2.5, m_star=10.0, v_r=5.0)
+    case = inputs.cylinder_case(513, 256, body=body)
+    X = np.stack([case.r[:, None] * case.e[None, :, 0], case.r[:, None] * case.e[None, :, 1]], axis=-1)
+    el = inputs.ogrid_element_list(X, seed=0)
+    M0 = el.to_list(inputs.initial_field(case.nr, case.ntheta, case.flow, seed=0))
+    m = lbfsi.ElementMesh(el.X, el.elements, el.wall, el.far, case.bodies * batch, precision=lbfsi.FP32,
+                          stream=stream.cuda_stream)
+    m.init_fields(case.flow, np.ascontiguousarray(np.broadcast_to(M0, (batch,) + M0.shape)))
+    m.step(warmup)
+    m.synchronize()
+    l0 = m.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    m.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = True
+    try:
+        m.synchronize()
+    except lbfsi.LbfsiError as e:
+        ok = str(e)
+    launches = m.launch_count() - l0
+    m.close()
+    nodes = case.nodes * batch
+    gbs = BYTES_PER_NODE_FP32 * nodes * steps / (ms * 1e-3) / 1e9
+    return {"workload": "1-DOF VIV cylinder (m* 10, V_R 5, Re 100, Ma 0.2), O-grid 513x256 renumbered "
+                        "into a shuffled Q2 element list, FP32, reading R33 gradients",
+            "nodes": case.nodes, "batch": batch, "steps": steps, "launches_per_step": launches // steps,
+            "ms_per_step": round(ms / steps, 4), "MLUPS": round(nodes * steps / ms / 1e3, 1),
+            "hbm_frac_of_measured": round(gbs / peak, 4), "physical": ok}
+
+
 def issue_roofline(nodes, kernel_s, sm_mhz):
     """Instruction-issue ceiling of the step kernel: warp instructions per
     node from the committed ncu capture (current source only) against one
@@ -630,11 +674,12 @@ def main():
         m2.close()
         del fields
 
-    sweep = small = general = None
+    sweep = small = general = elements = None
     if not args.no_sweep and world == 1:
         sweep = roofline_sweep(stream, (variant, order), peak)
         small = small_case_graphs(stream)
         general = general_mesh_throughput(stream, peak)
+        elements = element_mesh_throughput(stream, peak)
     issue = issue_roofline(nodes, kavg_s, clocks.get("sm_mhz") or 2070.0) if clocks else None
 
     serving_out = None
@@ -659,7 +704,7 @@ def main():
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "serving": serving_out,
                "issue_roofline": issue, "roofline_sweep": sweep, "small_case": small,
-               "general_meshes": general,
+               "general_meshes": general, "element_mesh": elements,
                "solves_per_s": round(B * world / (case.steps * region_ms / args.steps * 1e-3), 4)}
         print(json.dumps(out), flush=True)
     mesh.close()

@@ -247,3 +247,45 @@ def test_cgrid_walls_struct_layout_and_independent_bodies_validation_without_gpu
     assert create([[rear, front]], [1, 0, 1])[0] == lbfsi.EINVAL               # bodies swapped
     small_front = inputs.BodySpec(dof=1, xc=0.0, r_in=0.45, r_out=1.8)
     assert "rigid zone" in create([[small_front, inputs.BodySpec(dof=0)]], [1, 0, 1])[1]
+
+
+def test_element_mesh_layout_and_validation_without_a_gpu(lib, tmp_path):
+    """The element-list descriptor matches its C layout, and a bad element
+    list is refused before any CUDA call: an out-of-range node, a node in no
+    element, an element whose mid nodes are off the bilinear positions, a
+    chain of odd length, a node on both chains."""
+    import numpy as np
+    from paper_2107_01370_gb300 import inputs, lbfsi
+    src = tmp_path / "el.c"
+    src.write_text('#include "lbfsi.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu\\n", sizeof(lbfsi_mesh_elements_desc),'
+                   'offsetof(lbfsi_mesh_elements_desc, bodies), offsetof(lbfsi_mesh_elements_desc, grid_ij));'
+                   'return 0;}\n')
+    exe = tmp_path / "el"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(lbfsi.MeshElementsDesc), lbfsi.MeshElementsDesc.bodies.offset,
+                   lbfsi.MeshElementsDesc.grid_ij.offset]
+    case = inputs.cylinder_case(9, 16, r_far=6.0)
+    X = np.stack([case.r[:, None] * case.e[None, :, 0], case.r[:, None] * case.e[None, :, 1]], axis=-1)
+    el = inputs.ogrid_element_list(X, seed=2)
+
+    def make(X=el.X, E=el.elements, wall=el.wall, far=el.far):
+        with pytest.raises(lbfsi.LbfsiError) as ei:
+            lbfsi.ElementMesh(X, E, wall, far, case.bodies, precision=lbfsi.FP64)
+        return ei.value.code, str(ei.value)
+
+    E = el.elements.copy()
+    E[0, 0, 0] = el.X.shape[0]
+    assert make(E=E)[0] == lbfsi.EINVAL
+    X2 = np.vstack([el.X, [[30.0, 30.0]]])
+    code, msg = make(X=X2)
+    assert code == lbfsi.EINVAL and "every node" in msg
+    X3 = el.X.copy()
+    X3[el.elements[3, 1, 1]] += 0.01
+    code, msg = make(X=X3)
+    assert code == lbfsi.EINVAL and "subparametric" in msg
+    assert make(wall=el.wall[:-1])[0] == lbfsi.EINVAL
+    far = el.far.copy()
+    far[0] = el.wall[0]
+    assert make(far=far)[0] == lbfsi.EINVAL
