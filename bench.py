@@ -553,6 +553,9 @@ def main():
                     help="time only one general-mesh workload (0: O-grid by coordinates, 1: NACA C-grid, "
                          "2: linked tandem cylinders, 3: independent tandem cylinders) "
                          "with --steps, --warmup and --batch, print its JSON and exit")
+    ap.add_argument("--elements-only", action="store_true",
+                    help="time only the unstructured element-list workload with --steps, --warmup and "
+                         "--batch, print its JSON and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -583,6 +586,13 @@ def main():
         res = general_mesh_throughput(torch.cuda.Stream(device=dev), peak, steps=args.steps,
                                       warmup=args.warmup, batch=args.batch, only=args.general_only)
         print(json.dumps(res[0]), flush=True)
+        return
+
+    if args.elements_only:
+        peak, _ = measured_peaks()
+        res = element_mesh_throughput(torch.cuda.Stream(device=dev), peak, steps=args.steps,
+                                      warmup=args.warmup, batch=args.batch)
+        print(json.dumps(res), flush=True)
         return
 
     case = inputs.viv_cylinder_512x256()

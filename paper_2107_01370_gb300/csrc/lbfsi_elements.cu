@@ -133,7 +133,7 @@ __device__ bool em_locate(const EArgs& a, int n, R dx, R dy, int& elem, R& xi, R
         const R tin = R(1) + (pass ? R(1e-9) : (sizeof(R) == 4 ? R(1e-5) : R(1e-12)));
 #pragma unroll 1
         for (int h = h0; h < h1; ++h) {
-            const int code = a.hold[h], e = code >> 4, ent = code & 15;
+            const int code = __ldg(a.hold + h), e = code >> 4, ent = code & 15;
             const R xi0 = R(ent / 3 - 1), et0 = R(ent % 3 - 1);
             const R* c = ec + 6 * (size_t)e;
             const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
@@ -265,12 +265,15 @@ __device__ __forceinline__ typename EVec<R>::T2 em_gather(const EArgs& a, const 
     Ly[1] = R(1) - eta * eta;
     Ly[2] = eta * (R(0.5) * eta + R(0.5));
     const int* en = a.E + 9 * (size_t)e;
+    int nd[9];
+#pragma unroll
+    for (int s = 0; s < 9; ++s) nd[s] = __ldg(en + s);
     R2 acc = pair(R(0), R(0));
 #pragma unroll
     for (int aa = 0; aa < 3; ++aa) {
-        R2 t = pmul(pair(Ly[0], Ly[0]), pp[en[3 * aa]]);
-        t = pfma(pair(Ly[1], Ly[1]), pp[en[3 * aa + 1]], t);
-        t = pfma(pair(Ly[2], Ly[2]), pp[en[3 * aa + 2]], t);
+        R2 t = pmul(pair(Ly[0], Ly[0]), pp[nd[3 * aa]]);
+        t = pfma(pair(Ly[1], Ly[1]), pp[nd[3 * aa + 1]], t);
+        t = pfma(pair(Ly[2], Ly[2]), pp[nd[3 * aa + 2]], t);
         acc = pfma(pair(Lx[aa], Lx[aa]), t, acc);
     }
     return acc;
@@ -489,15 +492,19 @@ __global__ void __launch_bounds__(EM_THREADS) k_em_stream(const EArgs a) {
     }
 }
 
-// ---- launch 4: per solve, the load in block order, RK4 (Sec. III B) and the
-// next step's blended maps
+// ---- launch 4: one warp per solve: the load from the block partials in a
+// fixed order (lane t sums blocks t, t + 32, ...; then the lanes in order),
+// RK4 (Sec. III B) and the next step's blended maps
 __global__ void k_em_finish(const EArgs a) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.nbatch) return;
-    double F[3] = {0.0, 0.0, 0.0};
+    const int b = blockIdx.x, l = threadIdx.x;
     const double* pt = a.part + (size_t)b * a.nblk * 3;
-    for (int k = 0; k < a.nblk; ++k)
-        for (int c = 0; c < 3; ++c) F[c] += pt[3 * k + c];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int k = l; k < a.nblk; k += 32)
+        for (int c = 0; c < 3; ++c) v[c] += pt[3 * k + c];
+    double F[3] = {0.0, 0.0, 0.0};
+    for (int t = 0; t < 32; ++t)
+        for (int c = 0; c < 3; ++c) F[c] += __shfl_sync(0xffffffffu, v[c], t);
+    if (l != 0) return;
     const BodyDev bd = a.bodies[b];
     const BodyStateDev Sn = a.maps_in[b].S_next;
     const BodyStateDev Snew = rk4_body(bd, Sn, F[1], F[2], a.flow.dt, (long long)a.kstep);
@@ -767,7 +774,7 @@ cudaError_t launch_em_step(lbfsi_emesh m) {
     const lbfsi::EArgs a = make_eargs<R>(m);
     const dim3 grid((unsigned)m->nblk, (unsigned)m->nbatch);
     lbfsi::k_em_stream<R><<<grid, lbfsi::EM_THREADS, 0, m->stream>>>(a);
-    lbfsi::k_em_finish<<<(m->nbatch + 63) / 64, 64, 0, m->stream>>>(a);
+    lbfsi::k_em_finish<<<m->nbatch, 32, 0, m->stream>>>(a);
     m->launches += 2;
     return cudaGetLastError();
 }
