@@ -117,41 +117,56 @@ __device__ __forceinline__ void inv_map(const BodyMap<R>& bm, R X, R Y, R& i00, 
     i11 = F00 * idF;
 }
 
+// Newton's method for the point (dx, dy) relative to a node at reference
+// position (xi0, eta0) of an element with bilinear map X0 + b xi + c eta +
+// d xi eta, c = (b_x, b_y, c_x, c_y, d_x, d_y): (b + d eta0) u + (c + d xi0) v
+// + d u v = (dx, dy).  Returns the point's reference coordinates.
+template <typename R>
+__device__ __forceinline__ void em_newton(const R* c, R xi0, R et0, R dx, R dy, R& x, R& y) {
+    const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
+    const R Cx = c[2] + c[4] * xi0, Cy = c[3] + c[5] * xi0;
+    R u = R(0), v = R(0);
+    constexpr int ITS = sizeof(R) == 4 ? 4 : 20;
+#pragma unroll 1
+    for (int it = 0; it < ITS; ++it) {
+        const R rx = Bx * u + Cx * v + c[4] * u * v - dx;
+        const R ry = By * u + Cy * v + c[5] * u * v - dy;
+        const R a11 = Bx + c[4] * v, a12 = Cx + c[4] * u, a21 = By + c[5] * v, a22 = Cy + c[5] * u;
+        const R idet = rcp_(a11 * a22 - a12 * a21);
+        const R du = (a22 * rx - a12 * ry) * idet, dv = (a11 * ry - a21 * rx) * idet;
+        u -= du;
+        v -= dv;
+        if (sizeof(R) == 8 && abs_(du) + abs_(dv) < R(1e-15)) break;
+    }
+    x = xi0 + u;
+    y = et0 + v;
+}
+
+// Containment tolerance of pass 0 / 1 (reading R8): 1e-12 of the element
+// (float: 1e-5), then 1e-9.
+template <typename R>
+__device__ __forceinline__ R em_tol(int pass) {
+    return R(1) + (pass ? R(1e-9) : (sizeof(R) == 4 ? R(1e-5) : R(1e-12)));
+}
+template <typename R>
+__host__ __device__ constexpr int em_passes() {
+    return sizeof(R) == 4 ? 1 : 2;
+}
+
 // Departure point of node n displaced by (dx, dy): the first element holding
-// the node (increasing index) that contains it, by Newton's method on the
-// element's bilinear map relative to the node's own reference position
-// (xi0, eta0): (b + d eta0) u + (c + d xi0) v + d u v = (dx, dy).  Two
-// containment passes (reading R8): 1e-12 of the element (float: 1e-5),
-// then 1e-9.
+// the node (increasing index) that contains it (Eq. depPnt; readings R8, R9).
 template <typename R>
 __device__ bool em_locate(const EArgs& a, int n, R dx, R dy, int& elem, R& xi, R& eta) {
     const R* ec = static_cast<const R*>(a.ecoef);
     const int h0 = a.hptr[n], h1 = a.hptr[n + 1];
-    constexpr int PASSES = sizeof(R) == 4 ? 1 : 2;
 #pragma unroll 1
-    for (int pass = 0; pass < PASSES; ++pass) {
-        const R tin = R(1) + (pass ? R(1e-9) : (sizeof(R) == 4 ? R(1e-5) : R(1e-12)));
+    for (int pass = 0; pass < em_passes<R>(); ++pass) {
+        const R tin = em_tol<R>(pass);
 #pragma unroll 1
         for (int h = h0; h < h1; ++h) {
             const int code = __ldg(a.hold + h), e = code >> 4, ent = code & 15;
-            const R xi0 = R(ent / 3 - 1), et0 = R(ent % 3 - 1);
-            const R* c = ec + 6 * (size_t)e;
-            const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
-            const R Cx = c[2] + c[4] * xi0, Cy = c[3] + c[5] * xi0;
-            R u = R(0), v = R(0);
-            constexpr int ITS = sizeof(R) == 4 ? 4 : 20;
-#pragma unroll 1
-            for (int it = 0; it < ITS; ++it) {
-                const R rx = Bx * u + Cx * v + c[4] * u * v - dx;
-                const R ry = By * u + Cy * v + c[5] * u * v - dy;
-                const R a11 = Bx + c[4] * v, a12 = Cx + c[4] * u, a21 = By + c[5] * v, a22 = Cy + c[5] * u;
-                const R idet = rcp_(a11 * a22 - a12 * a21);
-                const R du = (a22 * rx - a12 * ry) * idet, dv = (a11 * ry - a21 * rx) * idet;
-                u -= du;
-                v -= dv;
-                if (sizeof(R) == 8 && abs_(du) + abs_(dv) < R(1e-15)) break;
-            }
-            const R x = xi0 + u, y = et0 + v;
+            R x, y;
+            em_newton<R>(ec + 6 * (size_t)e, R(ent / 3 - 1), R(ent % 3 - 1), dx, dy, x, y);
             if (abs_(x) <= tin && abs_(y) <= tin) {
                 elem = e;
                 xi = x;

@@ -547,6 +547,44 @@ def ogrid_element_list(X, seed: int = 0, shuffle: bool = True) -> ElementList:
                        grid_ij=ij, perm=perm, nr=nr, nt=nt)
 
 
+def cgrid_element_list(X, n_cut: int, seed: int = 0, shuffle: bool = True) -> ElementList:
+    """The Q2 elements of a C-grid X [nr, nt, 2] (nr and nt odd) as an
+    element list with the wake cut merged: row-0 nodes j and nt-1-j are one
+    node for j <= n_cut (the cut and the two ends of the wall), so the cells
+    on both sides of the cut share its nodes and no mirrored rows are
+    needed.  Wall chain: row 0 from n_cut around the body to nt-2-n_cut
+    (counterclockwise; its end meets its start at the rear point).
+    Far-field chain, counterclockwise around the domain: up the outlet column
+    j = 0, along the last row, down the outlet column j = nt-1.  grid_ij is
+    the first copy's (i, j) (no one-to-one grid map: R33 gradients only)."""
+    X = np.asarray(X, dtype=np.float64)
+    nr, nt = X.shape[:2]
+    if nr % 2 == 0 or nt % 2 == 0:
+        raise ValueError("a C-grid of odd nr and odd nt")
+    canon = np.arange(nr * nt).reshape(nr, nt)
+    for j in range(n_cut + 1):
+        canon[0, nt - 1 - j] = canon[0, j]
+    keep = np.unique(canon)
+    rng = np.random.default_rng(seed)
+    newid = np.full(nr * nt, -1, dtype=np.int64)
+    newid[keep] = rng.permutation(len(keep)) if shuffle else np.arange(len(keep))
+    node = newid[canon]
+    els = np.array([[[node[wa + a, wb + b] for b in range(3)] for a in range(3)]
+                    for wa in range(0, nr - 2, 2) for wb in range(0, nt - 2, 2)], dtype=np.int64)
+    if shuffle:
+        els = els[rng.permutation(els.shape[0])]
+    N = len(keep)
+    Xl = np.empty((N, 2))
+    ij = np.empty((N, 2), dtype=np.int64)
+    flat = X.reshape(-1, 2)
+    for old in keep:
+        Xl[newid[old]] = flat[old]
+        ij[newid[old]] = divmod(int(old), nt)
+    wall = node[0, n_cut:nt - 1 - n_cut]
+    far = np.concatenate([node[:nr - 1, 0], node[nr - 1, :nt - 1], node[nr - 1:0:-1, nt - 1]])
+    return ElementList(X=Xl, elements=els, wall=wall, far=far, grid_ij=ij, perm=newid, nr=nr, nt=nt)
+
+
 def fixed_cylinder_128x64(steps: int = 1000) -> CylinderCase:
     """Fixed cylinder, 128 radial x 64 angular nodes, far field at 20 D,
     Re 100, Ma 0.2 (FP64 parity workload)."""

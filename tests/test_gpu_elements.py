@@ -152,3 +152,40 @@ def test_cfl_violation_reported_on_element_list(lbfsi):
         m.synchronize()
     assert ei.value.code == lbfsi.EDEPARTURE
     m.close()
+
+
+def test_fp64_cgrid_element_list_with_a_pitching_section(lbfsi):
+    """A C-grid around an elliptic section as an element list, its wake cut
+    merged (the two sides share the cut's nodes), shuffled; a pitch-plunge
+    body about an axis ahead of the section, already pitched and moving, so
+    that g != I and the wall's normals rotate: fields, every step's load and
+    the body state match the oracle's element-list step to 1e-12."""
+    body = inputs.BodySpec(dof=2, xp=-0.2, yp=0.0, r_in=0.7, r_out=2.5, m_star=20.0, v_r=2.0,
+                           x_alpha=0.3, r_alpha=0.5, wh_wa=0.5)
+    case = inputs.cgrid_case(33, 8, 17, 0.5, 0.25, r_far=5.0, wake=4.0, body=body)
+    el = inputs.cgrid_element_list(case.X, case.n_cut, seed=4)
+    N = el.X.shape[0]
+    rng = np.random.default_rng(4)
+    M0 = np.empty((4, N))
+    M0[0] = 1.0
+    M0[1] = case.flow.u_inf * (1 + 1e-2 * rng.uniform(-1, 1, N))
+    M0[2] = 1e-2 * case.flow.u_inf * rng.uniform(-1, 1, N)
+    M0[3] = case.flow.t_inf
+    st = {"h": 0.01, "alpha": 0.04, "hdot": 0.002, "adot": 0.01}
+    pv = {"h": 0.00998, "alpha": 0.03996, "hdot": 0.002, "adot": 0.01}
+    um = OU.UnstructuredQ2Mesh(el.X, el.elements)
+    s = OU.UnstructuredSolver.from_case(um, el.wall, el.far, case, M0)
+    s.S, s.S_prev = [dict(st)], [dict(pv)]
+    m = lbfsi.ElementMesh(el.X, el.elements, el.wall, el.far, case.bodies, precision=lbfsi.FP64)
+    m.init_fields(case.flow, M0[None])
+    m.blend_mesh([tuple(st[k] for k in ("h", "alpha", "hdot", "adot"))],
+                 [tuple(pv[k] for k in ("h", "alpha", "hdot", "adot"))])
+    for _ in range(8):
+        r = s.step()
+        m.step(1)
+        assert np.abs(m.body_forces()[0] - np.array(r.force)).max() < 1e-12 * P_SCALE
+    assert field_err(m.get_fields()[0], r.M) < 1e-12
+    st_g = m.body_state()[0]
+    for k in ("h", "alpha", "hdot", "adot"):
+        assert abs(st_g[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
+    m.close()

@@ -315,3 +315,34 @@ def test_element_list_step_with_its_own_gradient_stays_close_to_structured():
         b = s_u.step()
     d = np.abs(_flat(a.M, perm) - b.M).max(axis=1)
     assert d.max() < 1e-3 and d.max() > 1e-12
+
+
+def test_cgrid_element_list_keeps_a_symmetric_flow_symmetric():
+    """A C-grid as an element list with its wake cut merged (the two sides
+    share the cut's nodes; no mirrored rows): uniform flow along the axis of
+    a symmetric section stays mirror-symmetric, rho, u_x and T even and u_y
+    odd in y, to round-off over several steps of the element-list step (R33
+    gradients, R34 chains) -- the cut is an ordinary interior line."""
+    case = inputs.cgrid_case(33, 8, 13, 0.5, 0.25, r_far=5.0, wake=4.0)
+    el = inputs.cgrid_element_list(case.X, case.n_cut, seed=3)
+    um = OU.UnstructuredQ2Mesh(el.X, el.elements)
+    N = um.N
+    nr, nt = el.nr, el.nt
+    canon = np.arange(nr * nt).reshape(nr, nt)
+    for j in range(case.n_cut + 1):
+        canon[0, nt - 1 - j] = canon[0, j]
+    mirror = np.empty(N, dtype=np.int64)
+    for i in range(nr):
+        for j in range(nt):
+            mirror[el.perm[canon[i, j]]] = el.perm[canon[i, nt - 1 - j]]
+    np.testing.assert_allclose(el.X[mirror, 0], el.X[:, 0], atol=1e-14)
+    np.testing.assert_allclose(el.X[mirror, 1], -el.X[:, 1], atol=1e-14)
+    M0 = np.empty((4, N))
+    M0[0], M0[1], M0[2], M0[3] = 1.0, case.flow.u_inf, 0.0, case.flow.t_inf
+    s = OU.UnstructuredSolver.from_case(um, el.wall, el.far, case, M0)
+    for _ in range(4):
+        r = s.step()
+    M = r.M
+    assert np.abs(M[2]).max() > 1e-6                    # the flow is not trivial
+    for c, sign in ((0, 1), (1, 1), (2, -1), (3, 1)):
+        np.testing.assert_allclose(M[c][mirror], sign * M[c], rtol=0, atol=1e-13 * np.abs(M[c]).max() + 1e-16)
