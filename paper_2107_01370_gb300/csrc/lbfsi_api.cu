@@ -411,7 +411,7 @@ int create_common(lbfsi_mesh m, int precision, int nbatch, const lbfsi_body_desc
         m->variant = (k >= 0 && k < lbfsi::step_variants(LBFSI_FP32)) ? k : 4;
     }
     if (m->precision == LBFSI_FP64 || m->host.general) m->variant = 0;   // 8-row tiles (general: the one shape)
-    m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
+    m->tile_rows = m->host.general ? lbfsi::general_tile_rows(m->precision) : lbfsi::tile_rows(m->precision, m->variant);
     const int nti = (m->host.nr + m->tile_rows - 1) / m->tile_rows;
     m->tiles_per_solve = nti * m->host.ntj;
     m->bodies.assign(bodies, bodies + m->slots());
@@ -954,7 +954,7 @@ int lbfsi_set_schedule(lbfsi_mesh m, int variant, int order) {
     drop_graph(m);
     m->variant = variant;
     m->order = order;
-    m->tile_rows = lbfsi::tile_rows(m->precision, m->variant);
+    m->tile_rows = m->host.general ? lbfsi::general_tile_rows(m->precision) : lbfsi::tile_rows(m->precision, m->variant);
     m->tiles_per_solve = ((m->host.nr + m->tile_rows - 1) / m->tile_rows) * m->host.ntj;
     return m->initialized ? upload_solves(m) : LBFSI_OK;
 }

@@ -232,11 +232,11 @@ int rebuild_tiles(lbfsi_batch b) {
     lbfsi::TraceRange trace_("lbfsi tile table");
     drop_graph(b);
     // separable-mesh tiles first (tile rows of the batch's shape), then the
-    // general-mesh tiles and the C-grid tiles (the GEN kernel's 8-row tile)
+    // general-mesh tiles and the C-grid tiles (the general kernel's tile)
     std::vector<TileDev> tiles;
     auto build = [&](int part) {
         const bool general = part > 0;
-        const int rows = general ? lbfsi::GEN_TILE_ROWS : b->tile_rows;
+        const int rows = general ? lbfsi::general_tile_rows(b->precision) : b->tile_rows;
         auto push = [&](size_t k, int ti, int tj) {
             const Slot& s = b->slots[k];
             TileDev t{};
@@ -521,7 +521,7 @@ int add_solve(lbfsi_batch b, const lbfsi_body_desc& body_desc, const lbfsi_flow_
     }
     sd.body = body;
     sd.mesh = mk;
-    const int rows = h.general ? lbfsi::GEN_TILE_ROWS : b->tile_rows;
+    const int rows = h.general ? lbfsi::general_tile_rows(b->precision) : b->tile_rows;
     sd.ntiles = ((h.nr + rows - 1) / rows) * h.ntj;
     // initial state: equilibria of the initial field, bodies at rest
     std::vector<double> M(4 * N);

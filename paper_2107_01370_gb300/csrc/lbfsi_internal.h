@@ -208,8 +208,13 @@ cudaError_t launch_step(const StepArgs& a, int precision, int variant, cudaStrea
 cudaError_t launch_step_uniform(const StepArgs& a, int precision, int variant, int nbatch,
                                 cudaStream_t s);
 int tile_rows(int precision, int variant);
-// Tile rows of the general-geometry kernel (one shape).
+// Tile rows of the general-geometry kernel, in uniform (mesh handle) and
+// table (batch runtime) launches alike: 8 in float64 (256 threads, one CTA
+// per SM), 12 in float (384 threads, two CTAs per SM: 24 resident warps
+// where an 8-row tile's registers and shared memory allowed 16).
 constexpr int GEN_TILE_ROWS = 8;
+constexpr int GEN_TILE_ROWS_FP32 = 12;
+inline int general_tile_rows(int precision) { return precision == 0 ? GEN_TILE_ROWS : GEN_TILE_ROWS_FP32; }
 // Table launch of the general-geometry kernel (the batch runtime's solves on
 // meshes given by node coordinates).
 cudaError_t launch_step_general_table(const StepArgs& a, int precision, cudaStream_t s);

@@ -88,8 +88,7 @@ template <typename R, int TI, int TJ, bool GEN>
 constexpr size_t step_smem_bytes() {
     using T = Tile<TI, TJ>;
     return sizeof(R) * (size_t)(18 * T::PSS + 4 * T::MS + 2 * T::MS + 4 * T::DS + 2 * T::DS +
-                                (GEN ? 6 * T::DS + (TI + 1) * (TJ + 1) * CELLC : T::MH * RS + T::MW * CS)) +
-           (GEN ? (size_t)TI * TJ * (9 * 2 * sizeof(R) + sizeof(unsigned long long)) : 0);
+                                (GEN ? 6 * T::DS + (TI + 1) * (TJ + 1) * CELLC : T::MH * RS + T::MW * CS));
 }
 
 // Bounds-checked build (LBFSI_BOUNDS_CHECK): the shared-memory windows the
@@ -276,7 +275,8 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
     // node only has the cells of row 0.  wrap_rows: no last window to clamp to.
     // cbmax >= 0: only the cell columns 0..cbmax exist (a C-grid's outlet
     // columns, whose points on the column line may round to either side)
-    const R di = jn[0] * dx + jn[2] * dy, dj = jn[1] * dx + jn[3] * dy;
+    // (written with fixed rounding: see fma_rn)
+    const R di = fma_rn(jn[0], dx, mul_rn(jn[2], dy)), dj = fma_rn(jn[1], dx, mul_rn(jn[3], dy));
     const bool down = i > 0 || below;
     auto cb_ok = [&](int d) { return cbmax < 0 || (unsigned)(j + d) <= (unsigned)cbmax; };
     int da = (!(di < R(0)) || !down) ? 0 : -1;
@@ -298,22 +298,25 @@ __device__ __forceinline__ bool depart_gen(const R* sC, const R* jn, int i, int 
             break;
         const R* c = sC + ((ca - (i0 - 1)) * (TJ + 1) + (cb - (j0 - 1))) * CELLC;
         const R xi0 = R(i - wa - 1), et0 = R(j - wb - 1);
-        const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
-        const R Cx = c[2] + c[4] * xi0, Cy = c[3] + c[5] * xi0;
+        const R Bx = fma_rn(c[4], et0, c[0]), By = fma_rn(c[5], et0, c[1]);
+        const R Cx = fma_rn(c[4], xi0, c[2]), Cy = fma_rn(c[5], xi0, c[3]);
         R u = R(0), v = R(0);
         constexpr int ITS = sizeof(R) == 4 ? 3 : 16;
 #pragma unroll 1
         for (int it = 0; it < ITS; ++it) {
-            const R rx = Bx * u + Cx * v + c[4] * u * v - dx;
-            const R ry = By * u + Cy * v + c[5] * u * v - dy;
-            const R a11 = Bx + c[4] * v, a12 = Cx + c[4] * u, a21 = By + c[5] * v, a22 = Cy + c[5] * u;
-            const R idet = rcp_(a11 * a22 - a12 * a21);
-            const R du = (a22 * rx - a12 * ry) * idet, dv = (a11 * ry - a21 * rx) * idet;
-            u -= du;
-            v -= dv;
+            const R uv = mul_rn(u, v);
+            const R rx = fma_rn(c[4], uv, fma_rn(Cx, v, fma_rn(Bx, u, -dx)));
+            const R ry = fma_rn(c[5], uv, fma_rn(Cy, v, fma_rn(By, u, -dy)));
+            const R a11 = fma_rn(c[4], v, Bx), a12 = fma_rn(c[4], u, Cx);
+            const R a21 = fma_rn(c[5], v, By), a22 = fma_rn(c[5], u, Cy);
+            const R idet = rcp_(fma_rn(a11, a22, -mul_rn(a12, a21)));
+            const R du = mul_rn(fma_rn(a22, rx, -mul_rn(a12, ry)), idet);
+            const R dv = mul_rn(fma_rn(a11, ry, -mul_rn(a21, rx)), idet);
+            u = add_rn(u, -du);
+            v = add_rn(v, -dv);
             if (sizeof(R) == 8 && abs_(du) + abs_(dv) < R(1e-15)) break;
         }
-        const R x = xi0 + u, e = et0 + v;
+        const R x = add_rn(xi0, u), e = add_rn(et0, v);
         const R du = max(abs_(u), abs_(v));   // displacement in cells (CFL)
         if (abs_(x) <= tin && abs_(e) <= tin) {
             base = (wa - pi0) * PWS + (wb - sj0);
@@ -505,8 +508,6 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     R* sX = sD + 2 * T::DS;                         // general: [DS][2] node coordinates
     R* sJ = sX + 2 * T::DS;                         // general: [DS][4] inverse metric
     R* sC = sJ + 4 * T::DS;                         // general: [TI+1][TJ+1][CELLC] cells
-    R2* sDep = reinterpret_cast<R2*>(sC + (TI + 1) * (TJ + 1) * CELLC);   // general: [9][TI TJ] cached departures
-    unsigned long long* sCode = reinterpret_cast<unsigned long long*>(sDep + 9 * TI * TJ);   // [TI TJ]
 
     // blended maps of the solve's bodies (several only on general meshes)
     constexpr int MB = GEN ? MAX_BODIES : 1;
@@ -720,21 +721,20 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             }
         }
     }
-    // general meshes: the tile's cached static departures (uniform launches)
+    // general meshes: the cached static departures are read per node in the
+    // stream phase (the solves of a handle share them, so they are mostly
+    // L2 hits); here a prefetch of the tile's entries into L2
     const bool dcache = GEN && UNIFORM && !a.record && mode != MODE_COLLIDE_ONLY && a.usol.dep_code != nullptr;
     if (dcache) {
-        const R2* gxe = reinterpret_cast<const R2*>(a.usol.dep_xe);
-        for (int idx = tid; idx < 10 * TI * TJ; idx += NT) {
-            const int q = idx / (TI * TJ), t = idx - q * (TI * TJ);
-            const int i = i0 + t / TJ, j = j0 + t % TJ;
-            if (i <= 0 || i >= nr || j >= nt) continue;
-            const ptrdiff_t n = (ptrdiff_t)i * nt + j;
-            if (q == 9) {
-                cp_async8(sCode + t, a.usol.dep_code + n);
-            } else {
-                if constexpr (sizeof(R2) == 16) cp_async16(sDep + idx, gxe + (size_t)q * N + n);
-                else cp_async8(sDep + idx, gxe + (size_t)q * N + n);
-            }
+        const int len = min(TJ, nt - j0);
+        for (int t = tid; t < 2 * 10 * TI; t += NT) {
+            const int c = t / (2 * TI), r = (t >> 1) % TI, end = t & 1;
+            const int i = i0 + r;
+            if (i >= nr || len <= 0) continue;
+            const size_t off = (size_t)i * nt + j0 + (end ? len - 1 : 0);
+            const void* ad = c < 9 ? (const void*)(reinterpret_cast<const R2*>(a.usol.dep_xe) + (size_t)c * N + off)
+                                   : (const void*)(a.usol.dep_code + off);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ad));
         }
     }
     if constexpr (UNIFORM) {
@@ -1167,7 +1167,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 }
                 continue;
             }
-            if (dcache && !moved && i > 0) dcode = sCode[(ti)*TJ + tj];
+            if (dcache && !moved && i > 0) dcode = __ldg(a.usol.dep_code + n);
         }
         if (GEN && dcode != ~0ull) {
 #pragma unroll
@@ -1179,7 +1179,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                     v = add_ref(q, sp[q * T::PSS + own]);
                 } else {
                     const int base = own + ((int)(nib >> 2) - 3) * T::PWS + ((int)(nib & 3u) - 3);
-                    const R2 xe = sDep[q * (TI * TJ) + ti * TJ + tj];
+                    const R2 xe = __ldg(reinterpret_cast<const R2*>(a.usol.dep_xe) + (size_t)q * N + n);
                     R Lx[3], Ly[3];
                     lagrange3(xe.x, Lx);
                     lagrange3(xe.y, Ly);
@@ -1556,7 +1556,7 @@ struct StepKernel {
             StepArgs b = a;
             b.pf_dist = resident;
             int nti = (a.umesh.nr + TI - 1) / TI;
-            if (GEN && a.collide_only && a.cgrid_pre) nti = std::min(nti, CGRID_PRE_ROWS / TI);
+            if (GEN && a.collide_only && a.cgrid_pre) nti = std::min(nti, (CGRID_PRE_ROWS + TI - 1) / TI);
             const dim3 grid = a.uorder ? dim3(nbatch, a.umesh.ntj, nti) : dim3(a.umesh.ntj, nti, nbatch);
             k_step<R, TI, TJ, NT, MINB, UNIFORM, GEN><<<grid, NT, smem, s>>>(b);
         } else {
@@ -1571,11 +1571,12 @@ static cudaError_t launch_step_t(const StepArgs& a, int nbatch, cudaStream_t s) 
     return StepKernel<R, TI, NT, MINB, UNIFORM>::launch(a, nbatch, s);
 }
 
-// General meshes (node coordinates given): one tile shape (GEN_TILE_ROWS rows).
+// General meshes (node coordinates given): one tile shape per precision
+// (general_tile_rows rows), in uniform and in table launches.
 static cudaError_t launch_general(const StepArgs& a, int precision, int nbatch, cudaStream_t s) {
-    static_assert(GEN_TILE_ROWS == 8, "tile shape of the general kernel");
+    static_assert(GEN_TILE_ROWS == 8 && GEN_TILE_ROWS_FP32 == 12, "tile shapes of the general kernel");
     if (precision == 0) return StepKernel<double, 8, 256, 1, true, true>::launch(a, nbatch, s);
-    return StepKernel<float, 8, 256, 2, true, true>::launch(a, nbatch, s);
+    return StepKernel<float, 12, 384, 2, true, true>::launch(a, nbatch, s);
 }
 
 template <bool UNIFORM>
@@ -1598,16 +1599,16 @@ static cudaError_t configure_any(int precision, int variant) {
 
 cudaError_t launch_step_general_table(const StepArgs& a, int precision, cudaStream_t s) {
     if (precision == 0) return StepKernel<double, 8, 256, 1, false, true>::launch(a, 0, s);
-    return StepKernel<float, 8, 256, 2, false, true>::launch(a, 0, s);
+    return StepKernel<float, 12, 384, 2, false, true>::launch(a, 0, s);
 }
 
 cudaError_t prepare_step(int precision, int variant, bool uniform, bool general) {
     if (general && !uniform)
         return precision == 0 ? StepKernel<double, 8, 256, 1, false, true>::configure()
-                              : StepKernel<float, 8, 256, 2, false, true>::configure();
+                              : StepKernel<float, 12, 384, 2, false, true>::configure();
     if (general)
         return precision == 0 ? StepKernel<double, 8, 256, 1, true, true>::configure()
-                              : StepKernel<float, 8, 256, 2, true, true>::configure();
+                              : StepKernel<float, 12, 384, 2, true, true>::configure();
     return uniform ? configure_any<true>(precision, variant) : configure_any<false>(precision, variant);
 }
 
