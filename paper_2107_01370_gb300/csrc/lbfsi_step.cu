@@ -33,6 +33,7 @@
 // chunks and the stream writes one 64-bit pair per direction.  The redundant
 // work is the collision of the 2-node halo; the HBM traffic per node is the
 // 18 populations read and written once plus the 4-value moment field.
+#include <climits>
 #include <cstdio>
 #include <type_traits>
 
@@ -819,13 +820,19 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // correction field D and the gradient maps on +-2 (a junction's or an
     // outlet's one-sided stencil along j reaches two nodes), dQ on +-4
     const bool shrink = GEN && mode == MODE_COLLIDE_ONLY;
+    // a C-grid step's collide-only launch: the tiles that stream its output
+    // are the first row of tiles, whose windows reach row TI + 1, so rows
+    // from TI + 2 on are neither collided nor written (nor D and the maps
+    // from TI + 3, nor dQ from TI + 4); ci: the row, e: 0 collision, 1 D, 2 dQ
+    const int rcap = (GEN && a.collide_only && a.cgrid_pre) ? TI + 2 : INT_MAX;
+    auto capped = [&](int ci, int e) { return ci - e >= rcap; };
     auto outside = [&](int li, int lj, int h, int w) {
         return shrink && (li < h - w || li >= h + TI + w || lj < h - w || lj >= h + TJ + w);
     };
     if (collide) {
         for (int idx = tid; idx < T::MS; idx += NT) {
             const int i = mi0 + idx / T::MW;
-            if (!rowok(i)) continue;
+            if (!rowok(i) || capped(i, 2)) continue;
             if (cg && (unsigned)(mj0 + idx % T::MW) >= (unsigned)nt) continue;
             const R rho = sM[idx], ux = sM[T::MS + idx], uy = sM[2 * T::MS + idx], Tn = sM[3 * T::MS + idx];
             sQ[idx] = rho * ux * (R(1) - R(3) * Tn) - rho * ux * ux * ux;
@@ -835,7 +842,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
-            if (!rowok(i)) continue;
+            if (!rowok(i) || capped(i, 1)) continue;
             if (cg && (unsigned)(j0 - T::HD + lj) >= (unsigned)nt) continue;
             if (outside(li, lj, T::HD, 2)) continue;
             R F00, F01, F10, F11, vx, vy;
@@ -870,7 +877,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li, jj = j0 - T::HD + lj;
-            if (!rowok(i)) continue;
+            if (!rowok(i) || capped(i, 1)) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
             if (outside(li, lj, T::HD, 2)) continue;
             const int m = (li + 1) * T::MW + (lj + 1);
@@ -897,7 +904,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
         for (int idx = tid; idx < T::PS; idx += NT) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
             const int i = pi0 + li, jj = j0 - T::HP + lj;
-            if (!(pb || (i >= 0 && i < nr))) continue;
+            if (!(pb || (i >= 0 && i < nr)) || capped(i, 0)) continue;
             if (cg && (unsigned)jj >= (unsigned)nt) continue;
             if (outside(li, lj, T::HP, 0)) continue;
             const int sn = li * T::PWS + lj + 2;   // staged node
@@ -940,7 +947,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
                 const int t = tid + k * NT;
                 const int ti = t / TJ, tj = t - (t / TJ) * TJ;
                 const int i = i0 + ti, j = j0 + tj;
-                if ((!RAGGED || ti < TI) && i < nr && j < nt) {
+                if ((!RAGGED || ti < TI) && i < nr && j < nt && !capped(i, 0)) {
                     const int n = i * nt + j;
                     const int sn = (ti + T::HP) * T::PWS + tj + T::HP + 2;
                     // C-grid: the first copy of a cut node also writes the
