@@ -4,7 +4,9 @@ same seeded inputs.
 Tolerances (relative error of a field = max over nodes of |gpu - oracle|
 divided by max over nodes of |oracle|, for rho and T; for the velocity the
 Euclidean norm of the vector u at each node is used in both places):
-  FP64 path   fields, populations <= 1e-12; loads: |dF| <= 1e-12 * p_inf * D
+  FP64 path   fields, populations <= 1e-12 (and the velocity of the four
+              rows next to the wall within 1e-10 of its own magnitude at
+              every node); loads: |dF| <= 1e-12 * p_inf * D
               (the scale of the pressure terms whose sum the load is, so
               cancellation in small lift values does not inflate a relative
               error); body states 1e-12 relative to their scale.
@@ -36,6 +38,18 @@ def field_err(a, b):
     e_u = np.hypot(a[1] - b[1], a[2] - b[2]).max() / np.hypot(b[1], b[2]).max()
     e_T = np.abs(a[3] - b[3]).max() / np.abs(b[3]).max()
     return max(e_rho, e_u, e_T)
+
+
+def near_wall_velocity_err(a, b, rows=4):
+    """Node-wise relative error of the velocity vector on the first rows
+    (the wall and the three rows above it), where the speed is far below
+    the free stream's and the field-wide scale would hide an error: max over
+    those nodes of |u_gpu - u_oracle| / |u_oracle| (nodes slower than 1e-9
+    excluded)."""
+    du = np.hypot(a[1, :rows] - b[1, :rows], a[2, :rows] - b[2, :rows])
+    sp = np.hypot(b[1, :rows], b[2, :rows])
+    ok = sp > 1e-9
+    return (du[ok] / sp[ok]).max()
 
 
 def run_oracle(case, M0, steps, state=None, prev=None):
@@ -79,6 +93,7 @@ def test_fp64_fixed_cylinder_128x64(lbfsi):
     s, r, hist = run_oracle(case, M0, case.steps)
     mesh, ghist = run_gpu(lbfsi, case, M0, case.steps, lbfsi.FP64, per_step_loads=True)
     assert field_err(mesh.get_fields()[0], r.M) < 1e-12
+    assert near_wall_velocity_err(mesh.get_fields()[0], r.M) < 1e-10
     f0, g0 = mesh.get_populations(0)
     last = case.nr - 1
     assert np.abs(f0[0, :, :last] - r.f_pre[:, :last]).max() < 1e-12 * np.abs(r.f_pre).max()
@@ -109,6 +124,7 @@ def test_fp64_moving_body_blended_mesh(lbfsi, dof):
     s, r, hist = run_oracle(case, M0, case.steps, state, prev)
     mesh, ghist = run_gpu(lbfsi, case, M0, case.steps, lbfsi.FP64, state, prev, per_step_loads=True)
     assert field_err(mesh.get_fields()[0], r.M) < 1e-12
+    assert near_wall_velocity_err(mesh.get_fields()[0], r.M) < 1e-10
     f1, g1 = mesh.get_populations(1)
     assert np.abs(f1[0] - r.f_post).max() < 1e-12 * np.abs(r.f_post).max()
     assert np.abs(ghist - hist).max() < 1e-12 * P_SCALE
