@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -43,13 +44,15 @@ namespace lbfsi {
 namespace {
 
 constexpr int EM_THREADS = 256;
+constexpr int EN_STRIDE = 12;
 
 // Node kinds (kind[n]): 0 interior, w + 1 the wall chain's node w, -(f + 1)
 // the far-field chain's node f.
 struct EArgs {
     int N, nbatch, nblk, kstep, collide;
     const void* X;        // [N][2] node coordinates (element type of the path)
-    const int* E;         // [Ne][9] element nodes, entry a * 3 + b
+    const int* E;         // [Ne][EN_STRIDE] element nodes, entry a * 3 + b (then padding, so
+                          // that a gather reads an element's nodes in three 16-byte loads)
     const void* ecoef;    // [Ne][6] bilinear map: (b_x, b_y, c_x, c_y, d_x, d_y)
     const int* hptr;      // [N + 1] holding elements of each node
     const int* hold;      // [.] element * 16 + the node's entry in it
@@ -61,6 +64,13 @@ struct EArgs {
     const double* n0;     // [nwall][2] wall normals (undeformed)
     const double* wgeo;   // [nwall][6] Simpson shares
     const double* nfar;   // [nfar][2] outward directions of the far field
+    // departures of the interior nodes for a node the blend does not move
+    // (the displacement of direction q is then -dt c_q at every step),
+    // solved once for the flow's dt: the holding element [9][N] (-1: none
+    // holds the point) and (xi, eta) [9][N]; null: solved every step
+    int* dep_e;
+    void* dep_xe;
+    int record;           // 1: fill dep_e / dep_xe (k_em_record)
     const void* p_in;     // [nbatch][9][N] pairs: pre-collision state of step k
     void* ppost;          // [nbatch][9][N] pairs: post-collision (float: deviations)
     void* p_out;          // [nbatch][9][N] pairs: pre-collision state of step k + 1
@@ -104,42 +114,49 @@ __device__ __forceinline__ const BodyMap<float>& smap<float>(const StepMaps& m) 
 template <>
 __device__ __forceinline__ const BodyMap<double>& smap<double>(const StepMaps& m) { return m.Sd; }
 
-// F^{-1} of the blended map at node n for a map (Sec. II A, II D).
+// F^{-1} of the blended map at node n for a map (Sec. II A, II D); false
+// where the blend does not move the node (F = I, V_G = 0).
 template <typename R>
-__device__ __forceinline__ void inv_map(const BodyMap<R>& bm, R X, R Y, R& i00, R& i01, R& i10, R& i11, R& vx,
+__device__ __forceinline__ bool inv_map(const BodyMap<R>& bm, R X, R Y, R& i00, R& i01, R& i10, R& i11, R& vx,
                                         R& vy) {
     R F00, F01, F10, F11;
-    kinematics(bm, X, Y, F00, F01, F10, F11, vx, vy);
+    const bool moved = kinematics(bm, X, Y, F00, F01, F10, F11, vx, vy);
     const R idF = rcp_(F00 * F11 - F01 * F10);
     i00 = F11 * idF;
     i01 = -F01 * idF;
     i10 = -F10 * idF;
     i11 = F00 * idF;
+    return moved;
 }
 
 // Newton's method for the point (dx, dy) relative to a node at reference
 // position (xi0, eta0) of an element with bilinear map X0 + b xi + c eta +
 // d xi eta, c = (b_x, b_y, c_x, c_y, d_x, d_y): (b + d eta0) u + (c + d xi0) v
-// + d u v = (dx, dy).  Returns the point's reference coordinates.
+// + d u v = (dx, dy).  Returns the point's reference coordinates.  Written
+// with fixed rounding (fma_rn, mul_rn, add_rn) so that the departures cached
+// by k_em_record equal, bit for bit, the ones k_em_stream solves.
 template <typename R>
 __device__ __forceinline__ void em_newton(const R* c, R xi0, R et0, R dx, R dy, R& x, R& y) {
-    const R Bx = c[0] + c[4] * et0, By = c[1] + c[5] * et0;
-    const R Cx = c[2] + c[4] * xi0, Cy = c[3] + c[5] * xi0;
+    const R Bx = fma_rn(c[4], et0, c[0]), By = fma_rn(c[5], et0, c[1]);
+    const R Cx = fma_rn(c[4], xi0, c[2]), Cy = fma_rn(c[5], xi0, c[3]);
     R u = R(0), v = R(0);
     constexpr int ITS = sizeof(R) == 4 ? 4 : 20;
 #pragma unroll 1
     for (int it = 0; it < ITS; ++it) {
-        const R rx = Bx * u + Cx * v + c[4] * u * v - dx;
-        const R ry = By * u + Cy * v + c[5] * u * v - dy;
-        const R a11 = Bx + c[4] * v, a12 = Cx + c[4] * u, a21 = By + c[5] * v, a22 = Cy + c[5] * u;
-        const R idet = rcp_(a11 * a22 - a12 * a21);
-        const R du = (a22 * rx - a12 * ry) * idet, dv = (a11 * ry - a21 * rx) * idet;
-        u -= du;
-        v -= dv;
+        const R uv = mul_rn(u, v);
+        const R rx = fma_rn(c[4], uv, fma_rn(Cx, v, fma_rn(Bx, u, -dx)));
+        const R ry = fma_rn(c[5], uv, fma_rn(Cy, v, fma_rn(By, u, -dy)));
+        const R a11 = fma_rn(c[4], v, Bx), a12 = fma_rn(c[4], u, Cx);
+        const R a21 = fma_rn(c[5], v, By), a22 = fma_rn(c[5], u, Cy);
+        const R idet = rcp_(fma_rn(a11, a22, -mul_rn(a12, a21)));
+        const R du = mul_rn(fma_rn(a22, rx, -mul_rn(a12, ry)), idet);
+        const R dv = mul_rn(fma_rn(a11, ry, -mul_rn(a21, rx)), idet);
+        u = add_rn(u, -du);
+        v = add_rn(v, -dv);
         if (sizeof(R) == 8 && abs_(du) + abs_(dv) < R(1e-15)) break;
     }
-    x = xi0 + u;
-    y = et0 + v;
+    x = add_rn(xi0, u);
+    y = add_rn(et0, v);
 }
 
 // Containment tolerance of pass 0 / 1 (reading R8): 1e-12 of the element
@@ -279,10 +296,9 @@ __device__ __forceinline__ typename EVec<R>::T2 em_gather(const EArgs& a, const 
     Ly[0] = eta * (R(0.5) * eta - R(0.5));
     Ly[1] = R(1) - eta * eta;
     Ly[2] = eta * (R(0.5) * eta + R(0.5));
-    const int* en = a.E + 9 * (size_t)e;
-    int nd[9];
-#pragma unroll
-    for (int s = 0; s < 9; ++s) nd[s] = __ldg(en + s);
+    const int4* e4 = reinterpret_cast<const int4*>(a.E + EN_STRIDE * (size_t)e);
+    const int4 n0 = __ldg(e4), n1 = __ldg(e4 + 1), n2 = __ldg(e4 + 2);
+    const int nd[9] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w, n2.x};
     R2 acc = pair(R(0), R(0));
 #pragma unroll
     for (int aa = 0; aa < 3; ++aa) {
@@ -307,7 +323,7 @@ __device__ __forceinline__ void em_interp_M(const EArgs& a, const R* M, size_t N
     Ly[0] = eta * (R(0.5) * eta - R(0.5));
     Ly[1] = R(1) - eta * eta;
     Ly[2] = eta * (R(0.5) * eta + R(0.5));
-    const int* en = a.E + 9 * (size_t)e;
+    const int* en = a.E + EN_STRIDE * (size_t)e;
     R d[4] = {R(0), R(0), R(0), R(0)};
     R own[4];
 #pragma unroll
@@ -367,7 +383,11 @@ __global__ void __launch_bounds__(EM_THREADS) k_em_stream(const EArgs a) {
         } else {
             const StepMaps& mp = a.maps_in[b];
             R i00, i01, i10, i11, vx, vy;
-            inv_map(smap<R>(mp), X[2 * n], X[2 * n + 1], i00, i01, i10, i11, vx, vy);
+            const bool moved = inv_map(smap<R>(mp), X[2 * n], X[2 * n + 1], i00, i01, i10, i11, vx, vy);
+            // an interior node the blend does not move takes its cached
+            // departures (the same solves, made once for the flow's dt)
+            const bool cached = a.dep_e != nullptr && kd == 0 && !moved;
+            const R2* dxe = static_cast<const R2*>(a.dep_xe);
             unsigned missing = 0u;
             const int w = kd - 1;
             if (kd > 0) {
@@ -396,7 +416,17 @@ __global__ void __launch_bounds__(EM_THREADS) k_em_stream(const EArgs a) {
                 int e;
                 R xi, eta;
                 R2 v;
-                if (em_locate<R>(a, n, -dt * hx, -dt * hy, e, xi, eta)) {
+                bool found;
+                if (cached) {
+                    e = __ldg(a.dep_e + (size_t)q * N + n);
+                    found = e >= 0;
+                    const R2 xe = __ldg(dxe + (size_t)q * N + n);
+                    xi = xe.x;
+                    eta = xe.y;
+                } else {
+                    found = em_locate<R>(a, n, -dt * hx, -dt * hy, e, xi, eta);
+                }
+                if (found) {
                     v = em_gather<R>(a, pp + (size_t)q * N, e, xi, eta);
                 } else {
                     lost = true;
@@ -510,6 +540,46 @@ __global__ void __launch_bounds__(EM_THREADS) k_em_stream(const EArgs a) {
 // ---- launch 4: one warp per solve: the load from the block partials in a
 // fixed order (lane t sums blocks t, t + 32, ...; then the lanes in order),
 // RK4 (Sec. III B) and the next step's blended maps
+// ---- once per flow dt (init_fields): the departures of every interior node
+// for the displacement of a node the blend does not move, by the same solves
+// as k_em_stream (an inactive map gives its F = I and V_G = 0)
+template <typename R>
+__global__ void __launch_bounds__(EM_THREADS) k_em_record(const EArgs a) {
+    using R2 = typename EVec<R>::T2;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N) return;
+    const size_t N = (size_t)a.N;
+    R2* dxe = static_cast<R2*>(a.dep_xe);
+    if (a.kind[n] != 0) {
+        for (int q = 0; q < 9; ++q) {
+            a.dep_e[q * N + n] = -1;
+            dxe[q * N + n] = pair(R(0), R(0));
+        }
+        return;
+    }
+    const SolveDev& fl = a.flow;
+    const R dt = flowv<R>(fl, fl.dt, fl.dt_f);
+    const R* X = static_cast<const R*>(a.X);
+    BodyMap<R> still{};
+    still.active = 0;
+    R i00, i01, i10, i11, vx, vy;
+    inv_map(still, X[2 * n], X[2 * n + 1], i00, i01, i10, i11, vx, vy);
+#pragma unroll 1
+    for (int q = 0; q < 9; ++q) {
+        const R cx = (R)cxq(q), cy = (R)cyq(q);
+        const R hx = i00 * cx + i01 * cy - vx, hy = i10 * cx + i11 * cy - vy;
+        int e;
+        R xi, eta;
+        if (em_locate<R>(a, n, -dt * hx, -dt * hy, e, xi, eta)) {
+            a.dep_e[q * N + n] = e;
+            dxe[q * N + n] = pair(xi, eta);
+        } else {
+            a.dep_e[q * N + n] = -1;
+            dxe[q * N + n] = pair(R(0), R(0));
+        }
+    }
+}
+
 __global__ void k_em_finish(const EArgs a) {
     const int b = blockIdx.x, l = threadIdx.x;
     const double* pt = a.part + (size_t)b * a.nblk * 3;
@@ -550,6 +620,10 @@ struct lbfsi_emesh_s {
     int *hptr = nullptr, *hold = nullptr, *gptr = nullptr, *gcol = nullptr, *kind = nullptr;
     void* gw = nullptr;
     double *xw = nullptr, *n0 = nullptr, *wgeo = nullptr, *nfar = nullptr;
+    // cached departures of the interior nodes the blend does not move
+    // ([9][N] holding element, [9][N] (xi, eta)), or null
+    int* dep_e = nullptr;
+    void* dep_xe = nullptr;
     // solves
     void* p[2] = {nullptr, nullptr};
     void* ppost = nullptr;
@@ -751,6 +825,8 @@ lbfsi::EArgs make_eargs(lbfsi_emesh m) {
     a.n0 = m->n0;
     a.wgeo = m->wgeo;
     a.nfar = m->nfar;
+    a.dep_e = m->dep_e;
+    a.dep_xe = m->dep_xe;
     const int c = m->cur();
     a.p_in = m->p[c];
     a.ppost = m->ppost;
@@ -944,7 +1020,10 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     const std::vector<unsigned char> Xt = typed(Xv, d->precision), ect = typed(ecoef, d->precision),
                                      gwt = typed(gw, d->precision);
     cudaError_t e = put(&m->X, Xt.data(), Xt.size());
-    if (e == cudaSuccess) e = put((void**)&m->E, E.data(), E.size() * sizeof(int));
+    std::vector<int> Ep((size_t)Ne * lbfsi::EN_STRIDE, 0);
+    for (size_t k = 0; k < (size_t)Ne; ++k)
+        for (int s = 0; s < 9; ++s) Ep[k * lbfsi::EN_STRIDE + s] = E[9 * k + s];
+    if (e == cudaSuccess) e = put((void**)&m->E, Ep.data(), Ep.size() * sizeof(int));
     if (e == cudaSuccess) e = put(&m->ecoef, ect.data(), ect.size());
     if (e == cudaSuccess) e = put((void**)&m->hptr, hptr.data(), hptr.size() * sizeof(int));
     if (e == cudaSuccess) e = put((void**)&m->hold, hold.data(), hold.size() * sizeof(int));
@@ -976,6 +1055,15 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     if (e == cudaSuccess) e = ealloc(m, &m->zl, nb * 3);
     if (e == cudaSuccess) e = ealloc(m, &m->status, 1);
     if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(unsigned));
+    // departures of the static interior nodes, solved once per time step
+    // size (LBFSI_NO_DEPARTURE_CACHE=1 solves them every step instead; the
+    // results are the same)
+    const char* nc = std::getenv("LBFSI_NO_DEPARTURE_CACHE");
+    if (e == cudaSuccess && !(nc && std::atoi(nc) != 0)) {
+        e = ealloc(m, &m->dep_e, 9 * (size_t)N);
+        if (e == cudaSuccess) e = ealloc(m, &q, 9 * (size_t)N * 2 * es);
+        m->dep_xe = q;
+    }
     if (e != cudaSuccess) {
         release(m);
         delete m;
@@ -1033,6 +1121,15 @@ int lbfsi_emesh_init_fields(lbfsi_emesh m, const lbfsi_flow_params* p, const dou
         e = lbfsi::launch_prepare(m->dbodies, m->st_a, m->st_a, m->st_a, m->zl, proto.dt, m->nbatch, m->maps[0],
                                   m->stream);
     m->launches += 2;
+    if (e == cudaSuccess && m->dep_e) {
+        const unsigned blocks = (unsigned)m->nblk;
+        if (m->precision == LBFSI_FP64)
+            lbfsi::k_em_record<double><<<blocks, lbfsi::EM_THREADS, 0, m->stream>>>(make_eargs<double>(m));
+        else
+            lbfsi::k_em_record<float><<<blocks, lbfsi::EM_THREADS, 0, m->stream>>>(make_eargs<float>(m));
+        m->launches++;
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return ecuda(e, "init_fields");
     m->initialized = true;
