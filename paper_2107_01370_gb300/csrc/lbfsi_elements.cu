@@ -637,6 +637,7 @@ struct lbfsi_emesh_s {
     double* zl = nullptr;
     unsigned* status = nullptr;
     SolveDev flow{};
+    std::vector<int> perm;   // library node i is the caller's node perm[i]
     bool initialized = false;
     unsigned k = 0;
     int64_t launches = 0;
@@ -692,6 +693,40 @@ void lagrange_d(double t, double* d) {
 // holding elements of the element's Q2 derivative at the node's reference
 // position mapped by that element's Q2 metric there.  Rows: node -> (col,
 // w_X, w_Y) with repeated columns merged in first-seen order.
+// Z-order (Morton) numbering of N points: perm[i] is the point at position
+// i of the curve through the bounding box quantised to 2^16 x 2^16 cells
+// (ties in input order), inv its inverse.
+void zorder(int N, const double* X, std::vector<int>& perm, std::vector<int>& inv) {
+    double lo[2] = {X[0], X[1]}, hi[2] = {X[0], X[1]};
+    for (int n = 0; n < N; ++n)
+        for (int c = 0; c < 2; ++c) {
+            lo[c] = std::min(lo[c], X[2 * (size_t)n + c]);
+            hi[c] = std::max(hi[c], X[2 * (size_t)n + c]);
+        }
+    auto spread = [](unsigned v) {   // the 16 bits of v to the even bit positions
+        v &= 0xffffu;
+        v = (v | (v << 8)) & 0x00ff00ffu;
+        v = (v | (v << 4)) & 0x0f0f0f0fu;
+        v = (v | (v << 2)) & 0x33333333u;
+        v = (v | (v << 1)) & 0x55555555u;
+        return v;
+    };
+    std::vector<unsigned> code((size_t)N);
+    for (int n = 0; n < N; ++n) {
+        unsigned qc[2];
+        for (int c = 0; c < 2; ++c) {
+            const double w = hi[c] > lo[c] ? (X[2 * (size_t)n + c] - lo[c]) / (hi[c] - lo[c]) : 0.0;
+            qc[c] = (unsigned)std::min(65535.0, std::max(0.0, std::floor(w * 65536.0)));
+        }
+        code[n] = spread(qc[0]) | (spread(qc[1]) << 1);
+    }
+    perm.resize((size_t)N);
+    for (int n = 0; n < N; ++n) perm[n] = n;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return code[a] < code[b]; });
+    inv.assign((size_t)N, 0);
+    for (int i = 0; i < N; ++i) inv[perm[i]] = i;
+}
+
 int gradient_r33(int N, const std::vector<int>& E, const double* X, const std::vector<int>& hptr,
                  const std::vector<int>& hold, std::vector<int>& gptr, std::vector<int>& gcol,
                  std::vector<double>& gw) {
@@ -915,15 +950,37 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     if (d->nwall < 4 || d->nwall % 2 || !d->wall || d->nfar < 4 || d->nfar % 2 || !d->far)
         return efail(LBFSI_EINVAL, "wall and far-field chains must have an even length >= 4");
     if ((long long)N * 9 > (1ll << 31) / 2) return efail(LBFSI_EINVAL, "mesh too large");
-    const double* X = d->X;
     double scale = 0.0;
     for (int k = 0; k < 2 * N; ++k) {
-        if (!std::isfinite(X[k])) return efail(LBFSI_EINVAL, "node coordinates must be finite");
-        scale = std::max(scale, std::fabs(X[k]));
+        if (!std::isfinite(d->X[k])) return efail(LBFSI_EINVAL, "node coordinates must be finite");
+        scale = std::max(scale, std::fabs(d->X[k]));
     }
     std::vector<int> E(d->elements, d->elements + 9 * (size_t)Ne);
     for (int v : E)
         if (v < 0 || v >= N) return efail(LBFSI_EINVAL, "element node index out of range");
+    // The library numbers the nodes along a Z-order curve of their
+    // coordinates: the EM_THREADS consecutive nodes of a stream block are then
+    // close in space, so the nodes of their elements (the block's staged set)
+    // stay few and the block's writes coalesce.  Elements keep the caller's
+    // order (the departure search visits them in it); the calls that take or
+    // return node fields map between the two numberings.
+    std::vector<int> perm, inv;
+    zorder(N, d->X, perm, inv);
+    std::vector<double> Xr(2 * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        Xr[2 * (size_t)i] = d->X[2 * (size_t)perm[i]];
+        Xr[2 * (size_t)i + 1] = d->X[2 * (size_t)perm[i] + 1];
+    }
+    const double* X = Xr.data();
+    for (int& v : E) v = inv[v];
+    std::vector<int> ijr;
+    if (d->grid_ij) {
+        ijr.resize(2 * (size_t)N);
+        for (int i = 0; i < N; ++i) {
+            ijr[2 * (size_t)i] = d->grid_ij[2 * (size_t)perm[i]];
+            ijr[2 * (size_t)i + 1] = d->grid_ij[2 * (size_t)perm[i] + 1];
+        }
+    }
     // subparametric elements: every node at the bilinear position of the corners
     std::vector<double> ecoef(6 * (size_t)Ne);
     for (int e = 0; e < Ne; ++e) {
@@ -963,22 +1020,22 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     // gradient operator
     std::vector<int> gptr, gcol;
     std::vector<double> gw;
-    int rc = d->grid_ij ? gradient_r18(N, d->grid_ij, d->grid_nr, d->grid_nt, X, gptr, gcol, gw)
+    int rc = d->grid_ij ? gradient_r18(N, ijr.data(), d->grid_nr, d->grid_nt, X, gptr, gcol, gw)
                         : gradient_r33(N, E, X, hptr, hold, gptr, gcol, gw);
     if (rc) return rc;
     // chains
     std::vector<int> kind(N, 0);
     std::vector<double> pw(2 * (size_t)d->nwall), pf(2 * (size_t)d->nfar);
     for (int w = 0; w < d->nwall; ++w) {
-        const int n = d->wall[w];
-        if (n < 0 || n >= N || kind[n] != 0) return efail(LBFSI_EINVAL, "wall chain: bad or repeated node");
+        const int n = d->wall[w] >= 0 && d->wall[w] < N ? inv[d->wall[w]] : -1;
+        if (n < 0 || kind[n] != 0) return efail(LBFSI_EINVAL, "wall chain: bad or repeated node");
         kind[n] = w + 1;
         pw[2 * w] = X[2 * n];
         pw[2 * w + 1] = X[2 * n + 1];
     }
     for (int f = 0; f < d->nfar; ++f) {
-        const int n = d->far[f];
-        if (n < 0 || n >= N || kind[n] != 0) return efail(LBFSI_EINVAL, "far-field chain: bad or repeated node");
+        const int n = d->far[f] >= 0 && d->far[f] < N ? inv[d->far[f]] : -1;
+        if (n < 0 || kind[n] != 0) return efail(LBFSI_EINVAL, "far-field chain: bad or repeated node");
         kind[n] = -(f + 1);
         pf[2 * f] = X[2 * n];
         pf[2 * f + 1] = X[2 * n + 1];
@@ -1008,6 +1065,7 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     m->nblk = (N + lbfsi::EM_THREADS - 1) / lbfsi::EM_THREADS;
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     m->bodies.assign(d->bodies, d->bodies + d->nbatch);
+    m->perm = perm;
     const size_t es = m->es, nb = (size_t)d->nbatch;
     std::vector<double> Xv(X, X + 2 * (size_t)N);
     auto put = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
@@ -1094,7 +1152,12 @@ int lbfsi_emesh_init_fields(lbfsi_emesh m, const lbfsi_flow_params* p, const dou
     std::vector<BodyDev> bd(nb);
     for (size_t b = 0; b < nb; ++b) bd[b] = lbfsi::body_dev(m->bodies[b], proto.rho_inf, proto.uinf_x);
     std::vector<double> Mh;
-    if (!rho_u_T) {
+    if (rho_u_T) {
+        // the caller's node order -> the library's
+        Mh.resize(nb * 4 * N);
+        for (size_t r = 0; r < nb * 4; ++r)
+            for (size_t i = 0; i < N; ++i) Mh[r * N + i] = rho_u_T[r * N + (size_t)m->perm[i]];
+    } else {
         Mh.resize(nb * 4 * N);
         for (size_t b = 0; b < nb; ++b)
             for (size_t n = 0; n < N; ++n) {
@@ -1108,8 +1171,7 @@ int lbfsi_emesh_init_fields(lbfsi_emesh m, const lbfsi_flow_params* p, const dou
     std::vector<double> zl(nb * 3, 0.0);
     cudaError_t e = cudaMemcpyAsync(m->dbodies, bd.data(), nb * sizeof(BodyDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(m->stage, rho_u_T ? rho_u_T : Mh.data(), nb * 4 * N * sizeof(double),
-                            cudaMemcpyHostToDevice, m->stream);
+        e = cudaMemcpyAsync(m->stage, Mh.data(), nb * 4 * N * sizeof(double), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(m->st_a, zero.data(), nb * sizeof(BodyStateDev), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->zl, zl.data(), zl.size() * sizeof(double), cudaMemcpyHostToDevice, m->stream);
@@ -1202,7 +1264,13 @@ int lbfsi_emesh_get_body_state(lbfsi_emesh m, lbfsi_body_state* out) {
 
 int lbfsi_emesh_get_fields(lbfsi_emesh m, double* rho_u_T) {
     if (!m || !rho_u_T) return efail(LBFSI_EINVAL, "null argument");
-    return download(m, m->M[m->cur()], rho_u_T, (size_t)m->nbatch * 4 * m->N);
+    const size_t N = (size_t)m->N, rows = (size_t)m->nbatch * 4;
+    std::vector<double> v(rows * N);
+    const int rc = download(m, m->M[m->cur()], v.data(), rows * N);
+    if (rc) return rc;
+    for (size_t r = 0; r < rows; ++r)
+        for (size_t i = 0; i < N; ++i) rho_u_T[r * N + (size_t)m->perm[i]] = v[r * N + i];
+    return LBFSI_OK;
 }
 
 int lbfsi_emesh_get_populations(lbfsi_emesh m, int which, double* f, double* g) {
@@ -1228,8 +1296,9 @@ int lbfsi_emesh_get_populations(lbfsi_emesh m, int which, double* f, double* g) 
             fv += (double)m->flow.fgref[2 * q];
             gv += (double)m->flow.fgref[2 * q + 1];
         }
-        f[k] = fv;
-        g[k] = gv;
+        const size_t row = k / m->N, to = row * m->N + (size_t)m->perm[k - row * m->N];
+        f[to] = fv;
+        g[to] = gv;
     }
     return LBFSI_OK;
 }
