@@ -1023,6 +1023,25 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     int rc = d->grid_ij ? gradient_r18(N, ijr.data(), d->grid_nr, d->grid_nt, X, gptr, gcol, gw)
                         : gradient_r33(N, E, X, hptr, hold, gptr, gcol, gw);
     if (rc) return rc;
+    // elements stored in the order of their centre nodes (so along the same
+    // curve as the nodes); each node's list of holding elements keeps the
+    // caller's element order, the order of the departure search
+    std::vector<int> eperm((size_t)Ne), einv((size_t)Ne);
+    for (int e2 = 0; e2 < Ne; ++e2) eperm[e2] = e2;
+    std::stable_sort(eperm.begin(), eperm.end(),
+                     [&](int a, int b) { return E[9 * (size_t)a + 4] < E[9 * (size_t)b + 4]; });
+    for (int k = 0; k < Ne; ++k) einv[eperm[k]] = k;
+    {
+        std::vector<int> Es(E.size());
+        std::vector<double> cs(ecoef.size());
+        for (int k = 0; k < Ne; ++k) {
+            std::copy_n(&E[9 * (size_t)eperm[k]], 9, &Es[9 * (size_t)k]);
+            std::copy_n(&ecoef[6 * (size_t)eperm[k]], 6, &cs[6 * (size_t)k]);
+        }
+        E.swap(Es);
+        ecoef.swap(cs);
+        for (int& h : hold) h = einv[h >> 4] * 16 + (h & 15);
+    }
     // chains
     std::vector<int> kind(N, 0);
     std::vector<double> pw(2 * (size_t)d->nwall), pf(2 * (size_t)d->nfar);
