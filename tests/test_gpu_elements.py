@@ -189,3 +189,83 @@ def test_fp64_cgrid_element_list_with_a_pitching_section(lbfsi):
     for k in ("h", "alpha", "hdot", "adot"):
         assert abs(st_g[k] - s.S[0][k]) < 1e-12 * (1 + abs(s.S[0][k])), k
     m.close()
+
+
+def _golden_elements():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "elements513_steps.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def _bench_element_run(L, precision, nbatch, gold):
+    """The bench's element-list workload (tests/golden/make_elements513_steps.py
+    builds the same inputs) stepped gold['steps'] times; every step's load
+    and body state of solve 0 and the fields after the checked steps."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "make_el", os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_elements513_steps.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    case, el, M0 = mk.workload()
+    m = L.ElementMesh(el.X, el.elements, el.wall, el.far, case.bodies * nbatch, precision=precision)
+    m.init_fields(case.flow, np.ascontiguousarray(np.broadcast_to(M0, (nbatch,) + M0.shape)))
+    loads, states, fields = [], [], {}
+    for n in range(1, gold["steps"] + 1):
+        m.step(1)
+        loads.append(m.body_forces()[0].copy())
+        st = m.body_state()[0]
+        states.append((st["h"], st["hdot"]))
+        if n in gold["check"]:
+            fields[n] = m.get_fields()
+    m.close()
+    return np.array(loads), np.array(states), fields
+
+
+def _sampled_err(M, gold, n):
+    pts = np.array(gold["samples"])
+    ref = np.array(gold["fields"][str(n)])
+    got = M[:, pts].T
+    s_rho, s_u, s_T = gold["scale"][str(n)]
+    return max(np.abs(got[:, 0] - ref[:, 0]).max() / s_rho,
+               np.hypot(got[:, 1] - ref[:, 1], got[:, 2] - ref[:, 2]).max() / s_u,
+               np.abs(got[:, 3] - ref[:, 3]).max() / s_T)
+
+
+def test_bench_element_workload_fp32_against_stored_oracle(lbfsi):
+    """The bench's element-list workload at full size (513 x 256 O-grid as a
+    shuffled element list, 131,328 nodes) in the bench's launch
+    configuration (eight solves, FP32), against the oracle's stored first 20
+    steps: sampled fields within 1e-5, every step's C_D within 1e-4
+    relative, C_L within 1e-4 of its amplitude, the displacement within
+    1e-6 D; the eight solves bit-identical.  Measured on a GB300: fields
+    6.5e-7, C_D 1.2e-7, C_L 7.2e-6, h 2e-12 D."""
+    gold = _golden_elements()
+    loads, states, fields = _bench_element_run(lbfsi, lbfsi.FP32, 8, gold)
+    errs = {n: _sampled_err(fields[n][0], gold, n) for n in gold["check"]}
+    for n in gold["check"]:
+        for b in range(1, 8):
+            assert np.array_equal(fields[n][b], fields[n][0])
+    qd = gold["q_inf_d"]
+    a, g = loads / qd, np.array(gold["loads"]) / qd
+    cd = (np.abs(a[:, 0] - g[:, 0]) / np.abs(g[:, 0])).max()
+    cl = np.abs(a[:, 1] - g[:, 1]).max() / np.abs(g[:, 1]).max()
+    dh = np.abs(states[:, 0] - np.array(gold["states"])[:, 0]).max()
+    assert max(errs.values()) < 1e-5, errs
+    assert cd < 1e-4, cd
+    assert cl < 1e-4, cl
+    assert dh < 1e-6, dh
+
+
+def test_bench_element_workload_fp64_against_stored_oracle(lbfsi):
+    """The same workload, one FP64 solve: sampled fields within 1e-12 and
+    every step's load within 1e-12 p_inf D of the oracle's stored run
+    (measured: 4.5e-14 and 7e-15 p_inf D)."""
+    gold = _golden_elements()
+    loads, states, fields = _bench_element_run(lbfsi, lbfsi.FP64, 1, gold)
+    errs = {n: _sampled_err(fields[n][0], gold, n) for n in gold["check"]}
+    dl = np.abs(loads - np.array(gold["loads"])).max()
+    assert max(errs.values()) < 1e-12, errs
+    assert dl < 1e-12 * P_SCALE, dl
