@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
     const int n = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     const size_t N = (size_t)a.N;
     double fcx = 0.0, fcy = 0.0, fcm = 0.0;
+    bool wallnode = false;
     if (n < a.N) {
         const SolveDev& fl = a.flow;
         const R dt = flowv<R>(fl, fl.dt, fl.dt_f), Cv = flowv<R>(fl, fl.Cv, fl.Cv_f);
@@ -383,6 +384,7 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
         R* Mo = static_cast<R*>(a.M_out) + (size_t)b * 4 * N;
         const R* X = static_cast<const R*>(a.X);
         const int kd = a.kind[n];
+        wallnode = kd > 0;
         if (kd < 0) {
             // far field: targets at B = A - dt n_out; the inlet prescribes the
             // free stream's u and T (reading R20)
@@ -545,8 +547,14 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
             }
         }
     }
-    // this block's share of the load, summed in thread order
+    // this block's share of the load, summed in thread order (a block with
+    // no wall node writes the zeros that sum would give)
     __shared__ double red[3][EM_THREADS];
+    double* pt0 = a.part + ((size_t)b * a.nblk + blockIdx.x) * 3;
+    if (!__syncthreads_or(wallnode)) {
+        if (threadIdx.x == 0) pt0[0] = pt0[1] = pt0[2] = 0.0;
+        return;
+    }
     red[0][threadIdx.x] = fcx;
     red[1][threadIdx.x] = fcy;
     red[2][threadIdx.x] = fcm;
@@ -565,9 +573,6 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
     }
 }
 
-// ---- launch 4: one warp per solve: the load from the block partials in a
-// fixed order (lane t sums blocks t, t + 32, ...; then the lanes in order),
-// RK4 (Sec. III B) and the next step's blended maps
 // ---- once per flow dt (init_fields): the departures of every interior node
 // for the displacement of a node the blend does not move, by the same solves
 // as k_em_stream (an inactive map gives its F = I and V_G = 0)
@@ -608,6 +613,9 @@ __global__ void __launch_bounds__(EM_THREADS) k_em_record(const EArgs a) {
     }
 }
 
+// ---- launch 4: one warp per solve: the load from the block partials in a
+// fixed order (lane t sums blocks t, t + 32, ...; then the lanes in order),
+// RK4 (Sec. III B) and the next step's blended maps
 __global__ void k_em_finish(const EArgs a) {
     const int b = blockIdx.x, l = threadIdx.x;
     const double* pt = a.part + (size_t)b * a.nblk * 3;
