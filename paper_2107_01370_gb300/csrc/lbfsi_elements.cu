@@ -77,6 +77,8 @@ struct EArgs {
     const void* M_in;     // [nbatch][4][N] moments of step k
     void* M_out;          // [nbatch][4][N] moments of step k + 1
     void* D;              // [nbatch][2][N]
+    void* dQ;             // [nbatch][2][N] dQ of the moments the stream writes (the next
+                          // step's correction field reads it at every neighbour)
     const StepMaps* maps_in;   // [nbatch]
     StepMaps* maps_out;        // [nbatch]
     const BodyDev* bodies;     // [nbatch]
@@ -243,6 +245,7 @@ __device__ __forceinline__ typename EVec<R>::T2 ref_pair(const SolveDev& s, int 
 }
 
 // ---- launch 1: D = (mu/p) grad dQ (Sec. II C), dQ_a = rho u_a (1 - 3T) - rho u_a^3
+// (dQ written with the moments by the previous stream launch, em_dq)
 template <typename R>
 __global__ void __launch_bounds__(EM_THREADS) k_em_D(const EArgs a) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
@@ -252,19 +255,23 @@ __global__ void __launch_bounds__(EM_THREADS) k_em_D(const EArgs a) {
     const R* X = static_cast<const R*>(a.X);
     R i00, i01, i10, i11, vx, vy;
     inv_map(kmap<R>(a.maps_in[b]), X[2 * n], X[2 * n + 1], i00, i01, i10, i11, vx, vy);
-    auto dq = [&](int m, int c) {
-        const R rho = M[m], u = M[(1 + c) * N + m], T = M[3 * N + m];
-        return rho * u * (R(1) - R(3) * T) - rho * u * u * u;
-    };
+    const R* Q = static_cast<const R*>(a.dQ) + (size_t)b * 2 * N;
     R xX, xY, yX, yY;
     em_grad2<R>(a, n, [&](int m, R& v0, R& v1) {
-        v0 = dq(m, 0);
-        v1 = dq(m, 1);
+        v0 = Q[m];
+        v1 = Q[N + m];
     }, xX, xY, yX, yY);
     const R mup = flowv<R>(a.flow, a.flow.mu, a.flow.mu_f) * rcp_(M[n] * M[3 * N + n]);
     R* D = static_cast<R*>(a.D) + (size_t)b * 2 * N;
     D[n] = mup * (i00 * xX + i10 * xY);
     D[N + n] = mup * (i01 * yX + i11 * yY);
+}
+
+// dQ_a = rho u_a (1 - 3T) - rho u_a^3 of a node's moments (Sec. II C).
+template <typename R>
+__device__ __forceinline__ void em_dq(R* Q, size_t N, int n, R rho, R ux, R uy, R T) {
+    Q[n] = rho * ux * (R(1) - R(3) * T) - rho * ux * ux * ux;
+    Q[N + n] = rho * uy * (R(1) - R(3) * T) - rho * uy * uy * uy;
 }
 
 // ---- launch 2: Y = grad D and the collision (Eq. f_boltz) into ppost;
@@ -382,6 +389,7 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
         const R2* pp = static_cast<const R2*>(a.ppost) + (size_t)b * 9 * N;
         R2* po = static_cast<R2*>(a.p_out) + (size_t)b * 9 * N;
         R* Mo = static_cast<R*>(a.M_out) + (size_t)b * 4 * N;
+        R* Qo = static_cast<R*>(a.dQ) + (size_t)b * 2 * N;
         const R* X = static_cast<const R*>(a.X);
         const int kd = a.kind[n];
         wallnode = kd > 0;
@@ -410,6 +418,7 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
             for (int q = 0; q < 9; ++q) po[q * N + n] = pair(f[q], g[q]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) Mo[c * N + n] = t[c];
+            em_dq<R>(Qo, N, n, t[0], t[1], t[2], t[3]);
         } else {
             const StepMaps& mp = a.maps_in[b];
             R i00, i01, i10, i11, vx, vy;
@@ -507,6 +516,7 @@ __global__ void __launch_bounds__(EM_THREADS, sizeof(R) == 4 ? 6 : 2) k_em_strea
             Mo[N + n] = mc.ux;
             Mo[2 * N + n] = mc.uy;
             Mo[3 * N + n] = mc.T;
+            em_dq<R>(Qo, N, n, mc.rho, mc.ux, mc.uy, mc.T);
             if (kd > 0) {
                 // wall stress sigma = -p I - (1 - omega/2) sum (f - f^eq) c c
                 // (Sec. III) in float64, this node's Simpson shares
@@ -665,6 +675,7 @@ struct lbfsi_emesh_s {
     void* ppost = nullptr;
     void* M[2] = {nullptr, nullptr};
     void* D = nullptr;
+    void* dQ = nullptr;   // [nbatch][2][N] dQ of the last streamed moments
     StepMaps* maps[2] = {nullptr, nullptr};
     BodyDev* dbodies = nullptr;
     double* part = nullptr;
@@ -905,6 +916,7 @@ lbfsi::EArgs make_eargs(lbfsi_emesh m) {
     a.M_in = m->M[c];
     a.M_out = m->M[c ^ 1];
     a.D = m->D;
+    a.dQ = m->dQ;
     a.maps_in = m->maps[c];
     a.maps_out = m->maps[c ^ 1];
     a.bodies = m->dbodies;
@@ -1160,6 +1172,8 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
     m->ppost = q;
     if (e == cudaSuccess) e = ealloc(m, &q, nb * 2 * N * es);
     m->D = q;
+    if (e == cudaSuccess) e = ealloc(m, &q, nb * 2 * N * es);
+    m->dQ = q;
     if (e == cudaSuccess) e = ealloc(m, &m->dbodies, nb);
     if (e == cudaSuccess) e = ealloc(m, &m->part, nb * m->nblk * 3);
     if (e == cudaSuccess) e = ealloc(m, &m->stage, nb * 4 * N);
