@@ -595,13 +595,22 @@ typedef struct {
  * subparametric elements with positive Jacobians, chains of distinct nodes
  * that no element repeats, bodies' walls inside their rigid zones), build the
  * node-to-element table and the gradient operator on the host, upload.
- * LBFSI_EINVAL on a bad mesh; host arrays are borrowed for the call. */
+ * Inside the handle the nodes are numbered along a Z-order curve of their
+ * coordinates (and the elements in the order of their centre nodes) for
+ * memory locality; every call that takes or returns node fields uses the
+ * caller's node order, and each node's elements are searched in the
+ * caller's element order.  LBFSI_EINVAL on a bad mesh; host arrays are
+ * borrowed for the call. */
 int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_stream, lbfsi_emesh* out);
 int lbfsi_emesh_destroy(lbfsi_emesh m);
 
 /* As lbfsi_init_fields: rho_u_T host [nbatch][4][N] (node order of the
  * element list) or NULL for the free stream; populations at equilibrium,
- * bodies at rest. */
+ * bodies at rest.  Also solves, once for the flow's dt, the departure points
+ * of the interior nodes that no blended region moves (a device buffer of
+ * 108 B per node in FP32, 180 B in FP64, allocated at creation unless the
+ * environment sets LBFSI_NO_DEPARTURE_CACHE=1; the steps then read them back
+ * instead of solving them, with the same results). */
 int lbfsi_emesh_init_fields(lbfsi_emesh m, const lbfsi_flow_params* p, const double* rho_u_T);
 
 /* As lbfsi_blend_mesh: body states [nbatch] of the next step's blended map,
