@@ -66,11 +66,11 @@ struct EArgs {
     const double* nfar;   // [nfar][2] outward directions of the far field
     // departures of the interior nodes for a node the blend does not move
     // (the displacement of direction q is then -dt c_q at every step),
-    // solved once for the flow's dt: the holding element [9][N] (-1: none
-    // holds the point) and (xi, eta) [9][N]; null: solved every step
+    // solved once for the flow's dt: the position in hold of the holding
+    // element [9][N] (-1: none holds the point) and (xi, eta) [9][N]; null:
+    // solved every step
     int* dep_e;
     void* dep_xe;
-    int record;           // 1: fill dep_e / dep_xe (k_em_record)
     const void* p_in;     // [nbatch][9][N] pairs: pre-collision state of step k
     void* ppost;          // [nbatch][9][N] pairs: post-collision (float: deviations)
     void* p_out;          // [nbatch][9][N] pairs: pre-collision state of step k + 1
@@ -667,7 +667,8 @@ struct lbfsi_emesh_s {
     void* gw = nullptr;
     double *xw = nullptr, *n0 = nullptr, *wgeo = nullptr, *nfar = nullptr;
     // cached departures of the interior nodes the blend does not move
-    // ([9][N] holding element, [9][N] (xi, eta)), or null
+    // ([9][N] position in hold of the holding element, [9][N] (xi, eta)),
+    // or null
     int* dep_e = nullptr;
     void* dep_xe = nullptr;
     // solves
@@ -1008,8 +1009,8 @@ int lbfsi_create_mesh_elements(const lbfsi_mesh_elements_desc* d, void* cuda_str
         if (v < 0 || v >= N) return efail(LBFSI_EINVAL, "element node index out of range");
     // The library numbers the nodes along a Z-order curve of their
     // coordinates: the EM_THREADS consecutive nodes of a stream block are then
-    // close in space, so the nodes of their elements (the block's staged set)
-    // stay few and the block's writes coalesce.  Elements keep the caller's
+    // close in space, so the nodes their gathers read stay few (and in
+    // cache) and the block's writes coalesce.  Elements keep the caller's
     // order (the departure search visits them in it); the calls that take or
     // return node fields map between the two numberings.
     std::vector<int> perm, inv;
