@@ -269,3 +269,26 @@ def test_bench_element_workload_fp64_against_stored_oracle(lbfsi):
     dl = np.abs(loads - np.array(gold["loads"])).max()
     assert max(errs.values()) < 1e-12, errs
     assert dl < 1e-12 * P_SCALE, dl
+
+
+def test_node_order_round_trip(lbfsi):
+    """The handle numbers nodes along a Z-order curve internally; the caller
+    sees its own order: fields given to init_fields come back unchanged from
+    get_fields (FP64), and after one step the shuffled list's fields equal
+    the same mesh's unshuffled list's fields node by node."""
+    case, sm, el, M0 = _case(nr=25, nt=48, seed=13)
+    rng = np.random.default_rng(13)
+    Mr = el.to_list(M0) * (1 + 1e-3 * rng.uniform(-1, 1, (4, el.X.shape[0])))
+    m = lbfsi.ElementMesh(el.X, el.elements, el.wall, el.far, case.bodies, precision=lbfsi.FP64)
+    m.init_fields(case.flow, Mr[None])
+    assert np.array_equal(m.get_fields()[0], Mr)
+    m.step(1)
+    shuffled = el.to_grid(m.get_fields()[0])
+    m.close()
+    plain = inputs.ogrid_element_list(sm.X, seed=13, shuffle=False)
+    m = lbfsi.ElementMesh(plain.X, plain.elements, plain.wall, plain.far, case.bodies, precision=lbfsi.FP64)
+    m.init_fields(case.flow, plain.to_list(el.to_grid(Mr))[None])
+    m.step(1)
+    unshuffled = plain.to_grid(m.get_fields()[0])
+    m.close()
+    assert np.abs(shuffled - unshuffled).max() < 1e-13 * np.abs(unshuffled).max()
