@@ -77,6 +77,11 @@ struct lbfsi_mesh_s {
     size_t h_rec_bytes = 0;
     double* d_rec = nullptr;         // device history of lbfsi_step_record: [steps][records][7]
     size_t d_rec_count = 0;
+    // tensor maps of the float separable step (StepArgs::tm_p, tm_M) for tiles
+    // of tma_rows rows: -1 not built yet, 0 not used (float64, general
+    // meshes, Ntheta not a multiple of 4, LBFSI_TMA=0, or no encoder)
+    int tma_rows = -1;
+    CUtensorMap tm_p[2], tm_M[2];
 
     int cur() const { return (int)(host_k & 1u); }
     bool first() const { return host_k == 0u; }
@@ -97,6 +102,8 @@ int check_status(lbfsi_mesh m) {
     if (e != cudaSuccess) return cuda_fail(e, "status read");
     if (st & lbfsi::ST_BOUNDS)
         return lbfsi::set_error(LBFSI_EBOUNDS, "an index of the step outside its buffer (bounds-checked build)");
+    if (st & lbfsi::ST_TMA)
+        return lbfsi::set_error(LBFSI_ECUDA, "a tensor copy of the step did not complete within its wait limit");
     if (st & lbfsi::ST_DEPARTURE)
         return fail(LBFSI_EDEPARTURE, "departure point outside the cells adjacent to its node (CFL)");
     if (st & lbfsi::ST_BPOINT)
@@ -236,8 +243,73 @@ int upload_solves(lbfsi_mesh m) {
     return LBFSI_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return static_cast<EncodeTiledFn>(nullptr);
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// A float array of dims (dx, dy, dz, dw), x fastest and dense, read in boxes
+// of (bx, by, bz, 1); elements outside the array arrive as zeros.
+bool encode_box4(CUtensorMap* map, void* base, size_t dx, size_t dy, size_t dz, size_t dw, unsigned bx,
+                 unsigned by, unsigned bz) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {dx, dy, dz, dw};
+    const cuuint64_t strides[3] = {dx * 4, dx * dy * 4, dx * dy * dz * 4};   // bytes, dims 1..3
+    const cuuint32_t box[4] = {bx, by, bz, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of the handle's two population and moment buffers for its
+// current tile shape (built again after a schedule change); false where the
+// step stages by per-thread copies.  Populations: (f, g) float pairs as
+// (2 Ntheta, nr, 9, nbatch) floats, box (2 (32 + 8), rows + 4, 9, 1);
+// moments: (Ntheta, nr, 4, nbatch), box (32 + 8, rows + 8, 4, 1) -- the
+// staged tiles of the step kernel (+-2 and +-4 nodes around the tile).
+bool tma_maps(lbfsi_mesh m) {
+    if (m->tma_rows == m->tile_rows) return true;
+    if (m->tma_rows == 0) return false;
+    const char* env = std::getenv("LBFSI_TMA");
+    const bool eligible = m->precision == LBFSI_FP32 && !m->host.general && !m->host.cgrid && !m->host.box &&
+                          m->host.nt % 4 == 0 && !(env && std::atoi(env) == 0);
+    bool ok = eligible;
+    const size_t nt = (size_t)m->host.nt, nr = (size_t)m->host.nr, nb = (size_t)m->nbatch;
+    const unsigned rows = (unsigned)m->tile_rows, w = (unsigned)(lbfsi::TILE_J + 8);
+    for (int c = 0; c < 2 && ok; ++c) {
+        ok = encode_box4(&m->tm_p[c], m->d_p[c], 2 * nt, nr, 9, nb, 2 * w, rows + 4, 9) &&
+             encode_box4(&m->tm_M[c], m->d_M[c], nt, nr, 4, nb, w, rows + 8, 4);
+    }
+    m->tma_rows = ok ? m->tile_rows : 0;
+    return ok;
+}
+
 lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
     lbfsi::StepArgs a{};
+    if (tma_maps(m)) {
+        a.tma = 1;
+        for (int c = 0; c < 2; ++c) {
+            a.tm_p[c] = m->tm_p[c];
+            a.tm_M[c] = m->tm_M[c];
+        }
+    }
     a.umesh = m->dmesh.dev;
     a.usol = m->solves[0];
     a.meshes = m->d_meshdev;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernels and the C-ABI layer.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,6 +15,7 @@ enum : unsigned {
     ST_NONPHYS = 2u,     // rho <= 0, T <= 0 or NaN
     ST_BPOINT = 4u,      // wall or outlet target point B outside the cells next to its node
     ST_BOUNDS = 8u,      // bounds-checked build: an index outside its buffer (access skipped)
+    ST_TMA = 16u,        // a tensor-copy wait of the step ran out of iterations
 };
 
 // Body model with dimensional ODE coefficients (Sec. III, Sec. IV).
@@ -194,6 +196,15 @@ struct StepArgs {
     int record;                    // general meshes, uniform: fill usol.dep_* (departures of
                                    // the static nodes of solve 0) and write nothing else
     unsigned* status;
+    // uniform launch of the float separable kernel: stage the populations and
+    // M^k of a tile whose columns do not wrap by two tensor copies (TMA) into
+    // shared memory instead of per-thread copies.  tm_p[c] / tm_M[c] describe
+    // buffer c (c = k & 1) of all solves as 4-D float arrays: populations
+    // (2 nt, nr, 9, nbatch) with boxes (2 (TJ + 8), TI + 4, 9, 1), moments
+    // (nt, nr, 4, nbatch) with boxes (TJ + 8, TI + 8, 4, 1) (lbfsi_api.cu).
+    int tma;
+    alignas(64) CUtensorMap tm_p[2];
+    alignas(64) CUtensorMap tm_M[2];
 };
 
 // Record msg as the calling thread's last error and return code (defined in

@@ -376,6 +376,53 @@ __device__ __forceinline__ void cp_async_words(void* dst, const void* src, int w
         cp_async4(static_cast<unsigned*>(dst) + q, static_cast<const unsigned*>(src) + q);
 }
 
+// Tensor copies (TMA): one thread moves a whole 4-D box global -> shared, the
+// bytes arriving on a shared-memory transaction barrier (mbarrier) that every
+// reader waits on.  Each barrier of a CTA is used for one phase (parity 0).
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+}
+// make the initialised barriers visible to the tensor-copy (async) proxy
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\nfence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// the one arrival of the phase, announcing the bytes the copies will deliver
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait0(unsigned long long* bar) {
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(b)
+        : "memory");
+    return done != 0u;
+}
+// Wait for phase 0 of a barrier with an iteration limit; a wait that runs out
+// flags the launch (the host then reports the step as failed) and returns.
+constexpr int TMA_WAIT_LIMIT = 1 << 22;
+__device__ __forceinline__ void mbar_wait0(unsigned long long* bar, unsigned* status) {
+    for (int it = 0; it < TMA_WAIT_LIMIT; ++it)
+        if (mbar_try_wait0(bar)) return;
+    atomicOr(status, ST_TMA);
+}
+// Box of a 4-D tensor map at element coordinates (x innermost) into shared
+// memory; x times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x,
+                                            int y, int z, int w) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(d),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(b)
+        : "memory");
+}
+
 // Angular index modulo nt (the tile's halo may wrap more than once on very
 // coarse rings).
 __device__ __forceinline__ int wrap_nt(int j, int nt) {
@@ -490,7 +537,7 @@ __device__ __noinline__ R2 gather9_mirror(const R2* p, int rowstride, R lx0, R l
 }
 
 template <typename R, int TI, int TJ, int NT, int MINB, bool UNIFORM, bool GEN>
-__global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepArgs a) {
     using T = Tile<TI, TJ>;
     using R2 = typename Vec2<R>::T;
     // tile nodes streamed per thread (the float64 tiles of 2 and 4 rows have
@@ -498,7 +545,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     constexpr int NPT = (TI * TJ + NT - 1) / NT;
     constexpr bool RAGGED = NPT * NT != TI * TJ;
     static_assert(NT >= TJ && NT >= 192 && (!RAGGED || NPT == 1), "tile / thread count");
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     R2* sp = reinterpret_cast<R2*>(smraw);          // [9][PH][PWS] (f_q, g_q) pairs
     R* sM = reinterpret_cast<R*>(sp + 9 * T::PSS);  // [4][MS]  rho, ux, uy, T of step k
     R* sQ = sM + 4 * T::MS;                         // [2][MS]  dQ_x, dQ_y
@@ -518,6 +565,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     __shared__ int s_bid[GEN ? TJ : 1];
     __shared__ SolveDev s_sol;
     __shared__ MeshDev s_mesh;
+    __shared__ __align__(8) unsigned long long s_bar[2];   // tensor copies: [0] M^k, [1] populations
 
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     // ---- prologue: this CTA's tile and solve; the solve's step number k
@@ -611,6 +659,26 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     const R* __restrict__ coltab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.coltab : mg->coltab);
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
     const int pi0 = i0 - T::HP, sj0 = j0 - 4;       // global index of sp row 0, column 0
+    // float separable uniform launch: the M^k and population boxes of a tile
+    // whose columns do not wrap come by two tensor copies that one thread
+    // issues (rows outside the mesh arrive as zeros and are never read); the
+    // other tiles, and every other kernel form, stage by per-thread copies
+    bool use_tma = false;
+    if constexpr (UNIFORM && !GEN && sizeof(R) == 4) {
+        // (the boxes' shared-memory destinations are 128-byte aligned by the
+        // layout; checked, so that another layout falls back instead of faulting)
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(sp), ma = (unsigned)__cvta_generic_to_shared(sM);
+        use_tma = a.tma != 0 && mj0 >= 0 && mj0 + T::MW <= nt && ((sa | ma) & 127u) == 0u;
+        if (use_tma && tid == 0) {
+            mbar_init(&s_bar[0]);
+            mbar_init(&s_bar[1]);
+            mbar_fence_init();
+            mbar_expect_tx(&s_bar[0], 4u * T::MS * (unsigned)sizeof(R));
+            tma_load_4d(sM, &a.tm_M[cur], &s_bar[0], mj0, mi0, 0, sb);
+            mbar_expect_tx(&s_bar[1], 9u * T::PSS * (unsigned)sizeof(R2));
+            tma_load_4d(sp, &a.tm_p[cur], &s_bar[1], 2 * sj0, pi0, 0, sb);
+        }
+    }
 
     // ---- phase 1: stage the geometry tables, M^k and the populations ------
     if constexpr (GEN) {
@@ -663,7 +731,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     {
         constexpr int CM = 16 / (int)sizeof(R), NCH = T::MW / CM;
         const bool vec = nt % CM == 0 && !cg;
-        for (int idx = tid; idx < T::MH * NCH; idx += NT) {
+        for (int idx = use_tma ? T::MH * NCH : tid; idx < T::MH * NCH; idx += NT) {
             const int ch = idx % NCH, li = idx / NCH;
             const int i = mi0 + li;
             if (!rowok(i)) continue;
@@ -695,7 +763,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     {
         constexpr int CP = 16 / (int)sizeof(R2), NCH = T::PWS / CP;
         const bool vec = nt % CP == 0 && !cg;
-        for (int idx = tid; idx < T::PH * NCH; idx += NT) {
+        for (int idx = use_tma ? T::PH * NCH : tid; idx < T::PH * NCH; idx += NT) {
             const int ch = idx % NCH, li = idx / NCH;
             const int i = pi0 + li;
             if (!rowok(i)) continue;
@@ -766,6 +834,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     cp_async_commit();
     cp_async_wait_group<1>();
     __syncthreads();
+    if (use_tma) mbar_wait0(&s_bar[0], a.status);   // M^k (the barrier above ordered the init)
     R2* __restrict__ p_out = reinterpret_cast<R2*>(mode == MODE_COLLIDE_ONLY ? SD(ppost) : SD(p[cur ^ 1])) + o9;
     R* __restrict__ M_out = reinterpret_cast<R*>(SD(M[cur ^ 1])) + o4;
     const R dt = pick<R>(SD(dt), SD(dt_f)), mu = pick<R>(SD(mu), SD(mu_f)), Cv = pick<R>(SD(Cv), SD(Cv_f));
@@ -900,6 +969,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
             sD[T::DS + idx] = mup * (sG[2 * T::DS + idx] * qy_xi + sG[3 * T::DS + idx] * qy_et);
         }
         cp_async_wait_all();   // the populations
+        if (use_tma) mbar_wait0(&s_bar[1], a.status);
         __syncthreads();
         for (int idx = tid; idx < T::PS; idx += NT) {
             const int li = idx / T::PW, lj = idx - li * T::PW;
@@ -973,6 +1043,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const StepArgs a) {
     // ---- phase 3: stream step k+1 ----------------------------------------
     if (!collide) {
         cp_async_wait_all();   // the populations
+        if (use_tma) mbar_wait0(&s_bar[1], a.status);
         __syncthreads();
         if constexpr (DEV) {
             // the staged pairs are full values here (nothing collided them):

@@ -119,3 +119,17 @@ def test_batch_schedule_graph_and_autotune_keep_every_result(L):
     assert np.all(ns > 0)
     for a, b in zip(ref, got):
         _same(a, b)
+
+
+def test_tensor_copy_staging_is_bit_identical_to_per_thread_copies(L, monkeypatch):
+    """The float kernel stages the populations and moments of a tile whose
+    columns do not wrap by tensor copies (TMA); LBFSI_TMA=0 at handle creation
+    stages every tile by per-thread copies.  Ntheta = 128 gives two such tiles
+    of four per tile row; every float tile shape, with a moving body, must
+    give the same bits either way."""
+    case, M0 = _case(64, 128)
+    for v in range(L.step_variants(L.FP32)):
+        monkeypatch.setenv("LBFSI_TMA", "0")
+        ref = _run_mesh(L, case, M0, 25, L.FP32, schedule=(v, 1))
+        monkeypatch.delenv("LBFSI_TMA")
+        _same(ref, _run_mesh(L, case, M0, 25, L.FP32, schedule=(v, 1)))
