@@ -77,9 +77,9 @@ struct lbfsi_mesh_s {
     size_t h_rec_bytes = 0;
     double* d_rec = nullptr;         // device history of lbfsi_step_record: [steps][records][7]
     size_t d_rec_count = 0;
-    // tensor maps of the float separable step (StepArgs::tm_p, tm_M) for tiles
-    // of tma_rows rows: -1 not built yet, 0 not used (float64, general
-    // meshes, Ntheta not a multiple of 4, LBFSI_TMA=0, or no encoder)
+    // tensor maps of the float step (StepArgs::tm_p, tm_M) for tiles of
+    // tma_rows rows: -1 not built yet, 0 not used (float64, periodic boxes,
+    // Ntheta not a multiple of 4, LBFSI_TMA=0, or no encoder)
     int tma_rows = -1;
     CUtensorMap tm_p[2], tm_M[2];
 
@@ -281,17 +281,18 @@ bool encode_box4(CUtensorMap* map, void* base, size_t dx, size_t dy, size_t dz, 
 // Tensor maps of the handle's two population and moment buffers for its
 // current tile shape (built again after a schedule change); false where the
 // step stages by per-thread copies.  Populations: (f, g) float pairs as
-// (2 Ntheta, nr, 9, nbatch) floats, box (2 (32 + 8), rows + 4, 9, 1);
-// moments: (Ntheta, nr, 4, nbatch), box (32 + 8, rows + 8, 4, 1) -- the
-// staged tiles of the step kernel (+-2 and +-4 nodes around the tile).
+// (2 Ntheta, rows stored, 9, nbatch) floats, box (2 (32 + 8), rows + 4, 9, 1);
+// moments: (Ntheta, rows stored, 4, nbatch), box (32 + 8, rows + 8, 4, 1) --
+// the staged tiles of the step kernel (+-2 and +-4 nodes around the tile).
+// The rows stored are nr, and on a C-grid its G mirrored rows below row 0.
 bool tma_maps(lbfsi_mesh m) {
     if (m->tma_rows == m->tile_rows) return true;
     if (m->tma_rows == 0) return false;
     const char* env = std::getenv("LBFSI_TMA");
-    const bool eligible = m->precision == LBFSI_FP32 && !m->host.general && !m->host.cgrid && !m->host.box &&
-                          m->host.nt % 4 == 0 && !(env && std::atoi(env) == 0);
+    const bool eligible = m->precision == LBFSI_FP32 && !m->host.box && m->host.nt % 4 == 0 &&
+                          !(env && std::atoi(env) == 0);
     bool ok = eligible;
-    const size_t nt = (size_t)m->host.nt, nr = (size_t)m->host.nr, nb = (size_t)m->nbatch;
+    const size_t nt = (size_t)m->host.nt, nr = (size_t)(m->host.nr + m->host.G), nb = (size_t)m->nbatch;
     const unsigned rows = (unsigned)m->tile_rows, w = (unsigned)(lbfsi::TILE_J + 8);
     for (int c = 0; c < 2 && ok; ++c) {
         ok = encode_box4(&m->tm_p[c], m->d_p[c], 2 * nt, nr, 9, nb, 2 * w, rows + 4, 9) &&
@@ -305,6 +306,7 @@ lbfsi::StepArgs make_args(lbfsi_mesh m, int collide_only) {
     lbfsi::StepArgs a{};
     if (tma_maps(m)) {
         a.tma = 1;
+        a.tma_g = m->host.G;
         for (int c = 0; c < 2; ++c) {
             a.tm_p[c] = m->tm_p[c];
             a.tm_M[c] = m->tm_M[c];

@@ -196,13 +196,15 @@ struct StepArgs {
     int record;                    // general meshes, uniform: fill usol.dep_* (departures of
                                    // the static nodes of solve 0) and write nothing else
     unsigned* status;
-    // uniform launch of the float separable kernel: stage the populations and
-    // M^k of a tile whose columns do not wrap by two tensor copies (TMA) into
-    // shared memory instead of per-thread copies.  tm_p[c] / tm_M[c] describe
-    // buffer c (c = k & 1) of all solves as 4-D float arrays: populations
-    // (2 nt, nr, 9, nbatch) with boxes (2 (TJ + 8), TI + 4, 9, 1), moments
-    // (nt, nr, 4, nbatch) with boxes (TJ + 8, TI + 8, 4, 1) (lbfsi_api.cu).
+    // uniform launch of the float kernel: stage the populations and M^k of a
+    // tile whose columns do not wrap by two tensor copies (TMA) into shared
+    // memory instead of per-thread copies.  tm_p[c] / tm_M[c] describe buffer
+    // c (c = k & 1) of all solves as 4-D float arrays: populations
+    // (2 nt, nr + tma_g, 9, nbatch) with boxes (2 (TJ + 8), TI + 4, 9, 1),
+    // moments (nt, nr + tma_g, 4, nbatch) with boxes (TJ + 8, TI + 8, 4, 1);
+    // tma_g: the mirrored rows a C-grid stores below row 0 (lbfsi_api.cu).
     int tma;
+    int tma_g;
     alignas(64) CUtensorMap tm_p[2];
     alignas(64) CUtensorMap tm_M[2];
 };

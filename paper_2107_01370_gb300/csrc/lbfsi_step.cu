@@ -659,24 +659,28 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     const R* __restrict__ coltab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.coltab : mg->coltab);
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
     const int pi0 = i0 - T::HP, sj0 = j0 - 4;       // global index of sp row 0, column 0
-    // float separable uniform launch: the M^k and population boxes of a tile
-    // whose columns do not wrap come by two tensor copies that one thread
-    // issues (rows outside the mesh arrive as zeros and are never read); the
-    // other tiles, and every other kernel form, stage by per-thread copies
+    // float uniform launch: the M^k and population boxes of a tile whose
+    // columns do not wrap (every tile of a C-grid, whose columns never wrap)
+    // come by two tensor copies that one thread issues (rows and columns
+    // outside the mesh arrive as zeros and are never read; a C-grid's arrays
+    // start tma_g mirrored rows below row 0); the other tiles, a step that
+    // streams the collide-only buffer, the departure-cache pass and the table
+    // launches stage by per-thread copies
     bool use_tma = false;
-    if constexpr (UNIFORM && !GEN && sizeof(R) == 4) {
+    if constexpr (UNIFORM && sizeof(R) == 4) {
         // (the boxes' shared-memory destinations are 128-byte aligned by the
         // layout; checked, so that another layout falls back instead of faulting)
         const unsigned sa = (unsigned)__cvta_generic_to_shared(sp), ma = (unsigned)__cvta_generic_to_shared(sM);
-        use_tma = a.tma != 0 && mj0 >= 0 && mj0 + T::MW <= nt && ((sa | ma) & 127u) == 0u;
+        use_tma = a.tma != 0 && (cg || (mj0 >= 0 && mj0 + T::MW <= nt)) && !pb && !from_post &&
+                  !(GEN && a.record) && ((sa | ma) & 127u) == 0u;
         if (use_tma && tid == 0) {
             mbar_init(&s_bar[0]);
             mbar_init(&s_bar[1]);
             mbar_fence_init();
             mbar_expect_tx(&s_bar[0], 4u * T::MS * (unsigned)sizeof(R));
-            tma_load_4d(sM, &a.tm_M[cur], &s_bar[0], mj0, mi0, 0, sb);
+            tma_load_4d(sM, &a.tm_M[cur], &s_bar[0], mj0, mi0 + a.tma_g, 0, sb);
             mbar_expect_tx(&s_bar[1], 9u * T::PSS * (unsigned)sizeof(R2));
-            tma_load_4d(sp, &a.tm_p[cur], &s_bar[1], 2 * sj0, pi0, 0, sb);
+            tma_load_4d(sp, &a.tm_p[cur], &s_bar[1], 2 * sj0, pi0 + a.tma_g, 0, sb);
         }
     }
 
