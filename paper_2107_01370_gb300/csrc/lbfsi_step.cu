@@ -1634,9 +1634,10 @@ struct StepKernel {
         if (e != cudaSuccess) return e;
         const size_t smem = step_smem_bytes<R, TI, TJ, GEN>();
         if (UNIFORM) {
-            // prefetch distance: one resident wave
+            // prefetch distance: one resident wave; none where the tiles are
+            // staged by tensor copies (measured faster without)
             StepArgs b = a;
-            b.pf_dist = resident;
+            b.pf_dist = a.tma ? 0 : resident;
             int nti = (a.umesh.nr + TI - 1) / TI;
             if (GEN && a.collide_only && a.cgrid_pre) nti = std::min(nti, (CGRID_PRE_ROWS + TI - 1) / TI);
             const dim3 grid = a.uorder ? dim3(nbatch, a.umesh.ntj, nti) : dim3(a.umesh.ntj, nti, nbatch);
