@@ -1634,10 +1634,12 @@ struct StepKernel {
         if (e != cudaSuccess) return e;
         const size_t smem = step_smem_bytes<R, TI, TJ, GEN>();
         if (UNIFORM) {
-            // prefetch distance: one resident wave; none where the tiles are
-            // staged by tensor copies (measured faster without)
+            // prefetch distance: one resident wave for the separable kernel
+            // staging by per-thread copies only; none where tensor copies
+            // stage the tiles, nor in the general kernel (measured faster
+            // without, C-grids included)
             StepArgs b = a;
-            b.pf_dist = a.tma ? 0 : resident;
+            b.pf_dist = (a.tma || GEN) ? 0 : resident;
             int nti = (a.umesh.nr + TI - 1) / TI;
             if (GEN && a.collide_only && a.cgrid_pre) nti = std::min(nti, (CGRID_PRE_ROWS + TI - 1) / TI);
             const dim3 grid = a.uorder ? dim3(nbatch, a.umesh.ntj, nti) : dim3(a.umesh.ntj, nti, nbatch);
