@@ -523,7 +523,13 @@ int64_t lbfsi_launch_count(lbfsi_mesh m);
  * new batches, with order 0).  Float64 shapes (separable O-grids; 256
  * threads, one CTA per SM): 0: 8 x 32 (default), 1: 4 x 32, 2: 2 x 32 -- the
  * smaller tiles spread a small mesh over more SMs, whose float64 rate bounds
- * the step.  Meshes given by node coordinates have one shape (0). */
+ * the step.  Meshes given by node coordinates have one shape (0).
+ * Staging (every shape): in a float mesh handle whose Ntheta is a multiple
+ * of 4, the moments and populations of each tile whose angular range does
+ * not wrap are moved into shared memory by two tensor copies (TMA), the
+ * other tiles by per-thread copies; LBFSI_TMA=0 in the environment when a
+ * handle first steps stages every tile by per-thread copies.  Both give the
+ * same bits. */
 int lbfsi_step_variants(int precision);
 
 /* Tile shape (0 .. lbfsi_step_variants - 1) and CTA order of a mesh handle's
