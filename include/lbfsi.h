@@ -525,11 +525,12 @@ int64_t lbfsi_launch_count(lbfsi_mesh m);
  * smaller tiles spread a small mesh over more SMs, whose float64 rate bounds
  * the step.  Meshes given by node coordinates have one shape (0).
  * Staging (every shape): in a float mesh handle whose Ntheta is a multiple
- * of 4, the moments and populations of each tile whose angular range does
- * not wrap are moved into shared memory by two tensor copies (TMA), the
- * other tiles by per-thread copies; LBFSI_TMA=0 in the environment when a
- * handle first steps stages every tile by per-thread copies.  Both give the
- * same bits. */
+ * of 4, and for the float solves of a batch on separable O-grids whose Ntheta
+ * is a multiple of 4, the moments and populations of each tile whose angular
+ * range does not wrap are moved into shared memory by two tensor copies
+ * (TMA), the other tiles by per-thread copies; LBFSI_TMA=0 in the environment
+ * when a handle first steps (when a batch rebuilds its tile table) stages
+ * every tile by per-thread copies.  Both give the same bits. */
 int lbfsi_step_variants(int precision);
 
 /* Tile shape (0 .. lbfsi_step_variants - 1) and CTA order of a mesh handle's

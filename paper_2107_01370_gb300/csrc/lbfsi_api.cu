@@ -19,6 +19,45 @@ using lbfsi::SolveDev;
 using lbfsi::StepMaps;
 using lbfsi::TileDev;
 
+namespace lbfsi {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return static_cast<EncodeTiledFn>(nullptr);
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// A float array of dims (dx, dy, dz, dw), x fastest and dense, read in boxes
+// of (bx, by, bz, 1); elements outside the array arrive as zeros.
+bool encode_box4(CUtensorMap* map, void* base, size_t dx, size_t dy, size_t dz, size_t dw, unsigned bx,
+                 unsigned by, unsigned bz) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {dx, dy, dz, dw};
+    const cuuint64_t strides[3] = {dx * 4, dx * dy * 4, dx * dy * dz * 4};   // bytes, dims 1..3
+    const cuuint32_t box[4] = {bx, by, bz, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace lbfsi
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -243,41 +282,6 @@ int upload_solves(lbfsi_mesh m) {
     return LBFSI_OK;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library)
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_tiled() {
-    static const EncodeTiledFn fn = [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return static_cast<EncodeTiledFn>(nullptr);
-        }
-        return reinterpret_cast<EncodeTiledFn>(p);
-    }();
-    return fn;
-}
-
-// A float array of dims (dx, dy, dz, dw), x fastest and dense, read in boxes
-// of (bx, by, bz, 1); elements outside the array arrive as zeros.
-bool encode_box4(CUtensorMap* map, void* base, size_t dx, size_t dy, size_t dz, size_t dw, unsigned bx,
-                 unsigned by, unsigned bz) {
-    const EncodeTiledFn fn = encode_tiled();
-    if (!fn) return false;
-    const cuuint64_t dims[4] = {dx, dy, dz, dw};
-    const cuuint64_t strides[3] = {dx * 4, dx * dy * 4, dx * dy * dz * 4};   // bytes, dims 1..3
-    const cuuint32_t box[4] = {bx, by, bz, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // Tensor maps of the handle's two population and moment buffers for its
 // current tile shape (built again after a schedule change); false where the
 // step stages by per-thread copies.  Populations: (f, g) float pairs as
@@ -295,8 +299,8 @@ bool tma_maps(lbfsi_mesh m) {
     const size_t nt = (size_t)m->host.nt, nr = (size_t)(m->host.nr + m->host.G), nb = (size_t)m->nbatch;
     const unsigned rows = (unsigned)m->tile_rows, w = (unsigned)(lbfsi::TILE_J + 8);
     for (int c = 0; c < 2 && ok; ++c) {
-        ok = encode_box4(&m->tm_p[c], m->d_p[c], 2 * nt, nr, 9, nb, 2 * w, rows + 4, 9) &&
-             encode_box4(&m->tm_M[c], m->d_M[c], nt, nr, 4, nb, w, rows + 8, 4);
+        ok = lbfsi::encode_box4(&m->tm_p[c], m->d_p[c], 2 * nt, nr, 9, nb, 2 * w, rows + 4, 9) &&
+             lbfsi::encode_box4(&m->tm_M[c], m->d_M[c], nt, nr, 4, nb, w, rows + 8, 4);
     }
     m->tma_rows = ok ? m->tile_rows : 0;
     return ok;

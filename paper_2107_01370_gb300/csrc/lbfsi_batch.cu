@@ -5,6 +5,7 @@
 // cache of device mesh geometry shared by solves on identical O-grids, slot
 // bookkeeping and the tile table (the node-to-CTA schedule) of each launch.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -108,6 +109,8 @@ struct Slot {
     int ntiles = 0;
     SolveDev dev{};
     std::vector<void*> blocks;
+    // the tile rows its tensor maps were made for (-1: none yet, 0: not used)
+    int tma_rows = -1;
 };
 
 }  // namespace
@@ -125,6 +128,9 @@ struct lbfsi_batch_s {
     size_t tiles_cap = 0;
     int max_meshes = 256, max_slots = 4096;
     unsigned* d_status = nullptr;
+    // float separable solves: tensor maps of each slot's populations and
+    // moments, [max_slots][4] (StepArgs::tmaps)
+    CUtensorMap* d_tmaps = nullptr;
     BodyStateDev* d_zero_state = nullptr;
     double* d_zero_loads = nullptr;
     int ntiles = 0;    // separable-mesh tiles of the table (first part)
@@ -234,6 +240,28 @@ int rebuild_tiles(lbfsi_batch b) {
     // separable-mesh tiles first (tile rows of the batch's shape), then the
     // general-mesh tiles and the C-grid tiles (the general kernel's tile)
     std::vector<TileDev> tiles;
+    // float separable solves: tensor maps for the current tile shape (made
+    // once per slot and shape, uploaded behind the launches already queued)
+    cudaError_t e = cudaSuccess;
+    const char* tenv = std::getenv("LBFSI_TMA");
+    const bool tma_on = b->precision == LBFSI_FP32 && b->d_tmaps && !(tenv && std::atoi(tenv) == 0);
+    for (size_t k = 0; k < b->slots.size() && tma_on; ++k) {
+        Slot& s = b->slots[k];
+        if (!s.used || s.finished || s.general || s.tma_rows == b->tile_rows) continue;
+        const lbfsi::HostMesh& h = b->meshes[s.mesh].host;
+        bool ok = h.nt % 4 == 0;
+        CUtensorMap maps[4];
+        const size_t nt = (size_t)h.nt, nr = (size_t)h.nr;
+        const unsigned rows = (unsigned)b->tile_rows, w = (unsigned)(lbfsi::TILE_J + 8);
+        for (int c = 0; c < 2 && ok; ++c)
+            ok = lbfsi::encode_box4(&maps[c], s.dev.p[c], 2 * nt, nr, 9, 1, 2 * w, rows + 4, 9) &&
+                 lbfsi::encode_box4(&maps[2 + c], s.dev.M[c], nt, nr, 4, 1, w, rows + 8, 4);
+        if (ok) {
+            e = cudaMemcpyAsync(b->d_tmaps + 4 * k, maps, sizeof(maps), cudaMemcpyHostToDevice, b->stream);
+            if (e != cudaSuccess) return cuda_err(e, "tensor map upload");
+        }
+        s.tma_rows = ok ? b->tile_rows : 0;
+    }
     auto build = [&](int part) {
         const bool general = part > 0;
         const int rows = general ? lbfsi::general_tile_rows(b->precision) : b->tile_rows;
@@ -245,6 +273,9 @@ int rebuild_tiles(lbfsi_batch b) {
             t.i0 = ti * rows;
             t.j0 = tj * lbfsi::TILE_J;
             t.tj = tj;
+            // a separable tile whose columns do not wrap, of a solve with maps
+            const int ntm = b->meshes[s.mesh].host.nt;
+            t.tma = part == 0 && tma_on && s.tma_rows == rows && t.j0 >= 4 && t.j0 + lbfsi::TILE_J + 4 <= ntm;
             t.counter = s.dev.counter;
             t.maps[0] = s.dev.maps[0];
             t.maps[1] = s.dev.maps[1];
@@ -279,7 +310,6 @@ int rebuild_tiles(lbfsi_batch b) {
     build(1);
     const size_t ngen = tiles.size() - nsep;
     build(2);
-    cudaError_t e = cudaSuccess;
     if (tiles.size() > b->tiles_cap) {
         e = cudaStreamSynchronize(b->stream);
         if (b->d_tiles) cudaFree(b->d_tiles);
@@ -322,6 +352,8 @@ int check_status(lbfsi_batch b) {
         return lbfsi::set_error(LBFSI_EBOUNDS, "an index of the step outside its buffer (bounds-checked build)");
     if (st & (lbfsi::ST_DEPARTURE | lbfsi::ST_BPOINT))
         return lbfsi::set_error(LBFSI_EDEPARTURE, "departure point outside the cells adjacent to its node (CFL)");
+    if (st & lbfsi::ST_TMA)
+        return lbfsi::set_error(LBFSI_ECUDA, "a tensor copy of the step did not complete within its wait limit");
     if (st & lbfsi::ST_NONPHYS) return lbfsi::set_error(LBFSI_ENONPHYS, "non-physical state (rho<=0, T<=0 or NaN)");
     return LBFSI_OK;
 }
@@ -336,6 +368,7 @@ lbfsi::StepArgs step_args(lbfsi_batch b, int part) {
     a.collide_only = 0;
     a.ustep = -1;
     a.status = b->d_status;
+    a.tmaps = part == 0 && b->precision == LBFSI_FP32 ? b->d_tmaps : nullptr;
     return a;
 }
 
@@ -413,6 +446,8 @@ int lbfsi_batch_create(size_t pool_bytes, int precision, void* cuda_stream, lbfs
     cudaError_t e = cudaMalloc(&b->d_meshes, b->max_meshes * sizeof(MeshDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_solves, b->max_slots * sizeof(SolveDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(unsigned));
+    if (e == cudaSuccess && precision == LBFSI_FP32)
+        e = cudaMalloc(&b->d_tmaps, (size_t)b->max_slots * 4 * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_zero_state, sizeof(BodyStateDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_zero_loads, 3 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(unsigned));
@@ -430,7 +465,7 @@ int lbfsi_batch_destroy(lbfsi_batch b) {
     if (!b) return lbfsi::set_error(LBFSI_EINVAL, "null batch");
     cudaStreamSynchronize(b->stream);
     void* ptrs[] = {b->d_meshes, b->d_solves, b->d_tiles, b->d_status, b->d_zero_state,
-                    b->d_zero_loads};
+                    b->d_zero_loads, b->d_tmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->graph) cudaGraphExecDestroy(b->graph);

@@ -165,9 +165,10 @@ struct SolveDev {
 
 // One CTA of a step launch: a tile of one solve.  The entry repeats the
 // solve's counter and maps pointers so that a CTA can read its step number
-// and fetch its maps without first loading the solve record.
+// and fetch its maps without first loading the solve record.  tma: stage the
+// tile's M^k and populations by tensor copies (StepArgs::tmaps).
 struct TileDev {
-    int solve, mesh, i0, j0, tj, pad;
+    int solve, mesh, i0, j0, tj, tma;
     unsigned* counter;
     StepMaps* maps[2];
 };
@@ -205,9 +206,20 @@ struct StepArgs {
     // tma_g: the mirrored rows a C-grid stores below row 0 (lbfsi_api.cu).
     int tma;
     int tma_g;
+    // table launch of the float separable kernel: per solve the tensor maps of
+    // its populations (buffers 0, 1) and moments (buffers 0, 1), in device
+    // memory, [solve][4], each a (2 nt, nr, 9, 1) or (nt, nr, 4, 1) float
+    // array with the boxes above; used by the tiles whose TileDev::tma is set
+    const CUtensorMap* tmaps;
     alignas(64) CUtensorMap tm_p[2];
     alignas(64) CUtensorMap tm_M[2];
 };
+
+// Tensor map of a float array of dims (dx, dy, dz, dw), x fastest and dense,
+// read in boxes of (bx, by, bz, 1), elements outside the array as zeros;
+// false if the map cannot be made (defined in lbfsi_api.cu).
+bool encode_box4(CUtensorMap* map, void* base, size_t dx, size_t dy, size_t dz, size_t dw, unsigned bx,
+                 unsigned by, unsigned bz);
 
 // Record msg as the calling thread's last error and return code (defined in
 // lbfsi_api.cu).

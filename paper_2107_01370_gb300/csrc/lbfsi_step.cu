@@ -574,6 +574,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     // itself, so the whole staging below is one batch of asynchronous copies
     // and one barrier.
     int sb, i0, j0, tjx, nr, nt, N;
+    int ttma = 0, tsol = 0;   // table launch: the tile's tensor-copy flag and solve
     const SolveDev* sg = nullptr;   // table launch: the solve and mesh records
     const MeshDev* mg = nullptr;
     unsigned* ctr;
@@ -590,6 +591,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
         const TileDev* tg = a.tiles + blockIdx.x;
         sb = 0;
         tjx = tg->tj; j0 = tg->j0; i0 = tg->i0;
+        ttma = tg->tma; tsol = tg->solve;
         sg = a.solves + tg->solve;
         mg = a.meshes + tg->mesh;
         nr = mg->nr; nt = mg->nt; N = mg->N;
@@ -667,20 +669,34 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     // streams the collide-only buffer, the departure-cache pass and the table
     // launches stage by per-thread copies
     bool use_tma = false;
-    if constexpr (UNIFORM && sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && (UNIFORM || !GEN)) {
         // (the boxes' shared-memory destinations are 128-byte aligned by the
         // layout; checked, so that another layout falls back instead of faulting)
         const unsigned sa = (unsigned)__cvta_generic_to_shared(sp), ma = (unsigned)__cvta_generic_to_shared(sM);
-        use_tma = a.tma != 0 && (cg || (mj0 >= 0 && mj0 + T::MW <= nt)) && !pb && !from_post &&
-                  !(GEN && a.record) && ((sa | ma) & 127u) == 0u;
+        const bool aligned = ((sa | ma) & 127u) == 0u;
+        const CUtensorMap *tmM, *tmP;
+        int g = 0, w = 0;
+        if constexpr (UNIFORM) {
+            use_tma = a.tma != 0 && (cg || (mj0 >= 0 && mj0 + T::MW <= nt)) && !pb && !from_post &&
+                      !(GEN && a.record) && aligned;
+            tmM = &a.tm_M[cur];
+            tmP = &a.tm_p[cur];
+            g = a.tma_g;
+            w = sb;
+        } else {
+            // a separable solve of the batch runtime: its own maps, one solve each
+            use_tma = ttma != 0 && a.tmaps != nullptr && mj0 >= 0 && mj0 + T::MW <= nt && aligned;
+            tmP = a.tmaps + 4 * tsol + cur;
+            tmM = a.tmaps + 4 * tsol + 2 + cur;
+        }
         if (use_tma && tid == 0) {
             mbar_init(&s_bar[0]);
             mbar_init(&s_bar[1]);
             mbar_fence_init();
             mbar_expect_tx(&s_bar[0], 4u * T::MS * (unsigned)sizeof(R));
-            tma_load_4d(sM, &a.tm_M[cur], &s_bar[0], mj0, mi0 + a.tma_g, 0, sb);
+            tma_load_4d(sM, tmM, &s_bar[0], mj0, mi0 + g, 0, w);
             mbar_expect_tx(&s_bar[1], 9u * T::PSS * (unsigned)sizeof(R2));
-            tma_load_4d(sp, &a.tm_p[cur], &s_bar[1], 2 * sj0, pi0 + a.tma_g, 0, sb);
+            tma_load_4d(sp, tmP, &s_bar[1], 2 * sj0, pi0 + g, 0, w);
         }
     }
 

@@ -209,3 +209,35 @@ def test_cgrid_solves_in_the_batch(L, precision):
         assert np.array_equal(got[k][0], alone[k][0]), k
         assert np.array_equal(got[k][1], alone[k][1]), k
         assert got[k][2] == alone[k][2], k
+
+
+def test_batch_tensor_copy_staging_is_bit_identical(L, monkeypatch):
+    """The batch's float table launch stages the populations and moments of a
+    tile whose columns do not wrap by tensor copies, through per-solve tensor
+    maps; LBFSI_TMA=0 stages every tile by per-thread copies.  Three solves
+    with Ntheta 64, 128 and 256 (no, two and six such tiles per tile row)
+    advanced together: the same bits either way, for every solve."""
+    specs = [(32, 64, 3.0, 2.0, 1, 9), (48, 128, 5.0, 10.0, 2, 12), (40, 256, 8.0, 20.0, 3, 10)]
+
+    def run():
+        batch = L.Batch(256 << 20, precision=L.FP32)
+        slots = []
+        for nr, nt, vr, ms, seed, n in specs:
+            case, M0 = _case(nr, nt, vr, ms, seed)
+            slots.append(batch.add(case.r, case.e, case.bodies[0], case.flow, n, M0))
+        while batch.step(1) > 0:
+            pass
+        out = [batch.get(s) for s in slots]
+        for s in slots:
+            batch.remove(s)
+        batch.close()
+        return out
+
+    monkeypatch.setenv("LBFSI_TMA", "0")
+    ref = run()
+    monkeypatch.delenv("LBFSI_TMA")
+    got = run()
+    for k, ((fa, la, sa), (fb, lb, sb)) in enumerate(zip(ref, got)):
+        assert np.array_equal(fa, fb), k
+        assert np.array_equal(la, lb), k
+        assert sa == sb, k
