@@ -927,8 +927,21 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
             sQ[idx] = rho * ux * (R(1) - R(3) * Tn) - rho * ux * ux * ux;
             sQ[T::MS + idx] = rho * uy * (R(1) - R(3) * Tn) - rho * uy * uy * uy;
         }
+        // static separable tile (F = I): the gradient maps are products of the
+        // mesh tables, formed where they are used instead of stored
+        const bool gtab = !GEN && tile_static;
+        auto gstatic = [&](int li, int lj, R* G) {   // li, lj: coordinates in the +-3 region
+            const R* row = srow + (li + 1) * RS;
+            const R* col = scol + (lj + 1) * CS;
+            R c0, c1, c2, c3;
+            ld4(col + CT_G, c0, c1, c2, c3);
+            G[0] = row[RT_IDRC] * c0;
+            G[1] = -row[RT_IR] * c1;
+            G[2] = -row[RT_IDRC] * c2;
+            G[3] = row[RT_IR] * c3;
+        };
         // gradient maps on the +-3 region with the step-k kinematics
-        for (int idx = tid; idx < T::DS; idx += NT) {
+        for (int idx = gtab ? T::DS : tid; idx < T::DS; idx += NT) {
             const int li = idx / T::DW, lj = idx - li * T::DW;
             const int i = i0 - T::HD + li;
             if (!rowok(i) || capped(i, 1)) continue;
@@ -985,8 +998,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
                 qy_xi = d_row(sQ + T::MS + m, T::MW, i, nr);
                 qy_et = d_col(sQ + T::MS + m);
             }
-            sD[idx] = mup * (sG[idx] * qx_xi + sG[T::DS + idx] * qx_et);
-            sD[T::DS + idx] = mup * (sG[2 * T::DS + idx] * qy_xi + sG[3 * T::DS + idx] * qy_et);
+            R G[4];
+            if (gtab) {
+                gstatic(li, lj, G);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) G[c] = sG[c * T::DS + idx];
+            }
+            sD[idx] = mup * (G[0] * qx_xi + G[1] * qx_et);
+            sD[T::DS + idx] = mup * (G[2] * qy_xi + G[3] * qy_et);
         }
         cp_async_wait_all();   // the populations
         if (use_tma) mbar_wait0(&s_bar[1], a.status);
@@ -1024,8 +1044,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
                     dy_xi = d_row(sD + T::DS + d, T::DW, i, nr);
                     dy_et = d_col(sD + T::DS + d);
                 }
-                const R Yx = sG[d] * dx_xi + sG[T::DS + d] * dx_et;
-                const R Yy = sG[2 * T::DS + d] * dy_xi + sG[3 * T::DS + d] * dy_et;
+                R G[4];
+                if (gtab) {
+                    gstatic(li + 1, lj + 1, G);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) G[c] = sG[c * T::DS + d];
+                }
+                const R Yx = G[0] * dx_xi + G[1] * dx_et;
+                const R Yy = G[2] * dy_xi + G[3] * dy_et;
                 collide_pairs(pq, Yx, Yy, mu, dt, Cv, iPr);
             }
 #pragma unroll
