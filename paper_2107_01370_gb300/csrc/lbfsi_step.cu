@@ -661,13 +661,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const __grid_constant__ StepA
     const R* __restrict__ coltab = reinterpret_cast<const R*>(UNIFORM ? a.umesh.coltab : mg->coltab);
     const int mi0 = i0 - T::HM, mj0 = j0 - T::HM;   // global index of sM entry (0,0)
     const int pi0 = i0 - T::HP, sj0 = j0 - 4;       // global index of sp row 0, column 0
-    // float uniform launch: the M^k and population boxes of a tile whose
-    // columns do not wrap (every tile of a C-grid, whose columns never wrap)
-    // come by two tensor copies that one thread issues (rows and columns
-    // outside the mesh arrive as zeros and are never read; a C-grid's arrays
-    // start tma_g mirrored rows below row 0); the other tiles, a step that
-    // streams the collide-only buffer, the departure-cache pass and the table
-    // launches stage by per-thread copies
+    // float launches: the M^k and population boxes of a tile whose columns do
+    // not wrap (every tile of a C-grid, whose columns never wrap) come by two
+    // tensor copies that one thread issues (rows and columns outside the mesh
+    // arrive as zeros and are never read; a C-grid's arrays start tma_g
+    // mirrored rows below row 0); uniform launches through the handle's maps,
+    // the batch's separable table launches through each solve's own.  The
+    // other tiles, a step that streams the collide-only buffer, the
+    // departure-cache pass and the general kernel's table launches stage by
+    // per-thread copies
     bool use_tma = false;
     if constexpr (sizeof(R) == 4 && (UNIFORM || !GEN)) {
         // (the boxes' shared-memory destinations are 128-byte aligned by the
